@@ -1,0 +1,142 @@
+/*
+ * oracle.h -- plain FP64 CPU reference of the sparse vertex-star relaxation
+ * (Brubeck & Farrell, "A scalable and robust vertex-star relaxation for
+ * high-order FEM", arXiv 2107.14758).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link or call
+ * this library: only the test suite, the smoke check and the CPU-baseline leg
+ * of the benchmark use it.  It shares no code, header or table with the CUDA
+ * library; it is written to be slow and obviously correct.
+ *
+ * Conventions (all functions):
+ *   - p >= 1 is the polynomial degree, n = p + 1 GLL points per direction.
+ *   - The mesh is a structured nx x ny x nz hexahedral mesh.  Vertex
+ *     coordinates per axis are given (tensor-product "box" cells), and
+ *     optionally a Jacobian per Gauss point for curved cells.
+ *   - Vectors are full-grid GLL nodal arrays of length
+ *     (nx p + 1)(ny p + 1)(nz p + 1), x fastest.  Entries on the Dirichlet
+ *     boundary are ignored on input and written as 0 on output (Section 2.1,
+ *     homogeneous Dirichlet data).
+ *   - Vertex-star patches are numbered by mesh vertex, x fastest.
+ *   - Every function returning int returns 0 on success, a negative value on
+ *     error (message in or_last_error()).
+ *
+ * Parity unpinned: none (every function is pinned by a test against closed
+ * forms, brute-force dense solves or invariants; see tests/test_oracle_*.py).
+ */
+#ifndef FDM_ORACLE_H
+#define FDM_ORACLE_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OR_PMAX 31
+
+/* ---- 1D building blocks (Section 2.1, eq. for l_j; Section 2.3 eq:eig;
+ *      Section 2.4 FDM basis) ------------------------------------------- */
+
+/* Gauss-Legendre rule with q points on [-1,1] (ascending). */
+int or_gauss(int q, double *x, double *w);
+/* Gauss-Lobatto-Legendre nodes (roots of (1-x^2) P'_p) and weights. */
+int or_gll(int p, double *xi, double *w);
+/* Lagrange basis on the nodes xi[0..p] evaluated at m points:
+ * V[t*(p+1)+j] = l_j(x_t), D[t*(p+1)+j] = l_j'(x_t). */
+void or_lagrange(int p, const double *xi, int m, const double *x, double *V, double *D);
+/* Reference 1D stiffness A and mass B in the GLL Lagrange basis ((p+1)^2,
+ * row-major), interior generalised eigenpairs (S: (p-1)^2 row-major,
+ * S[i*(p-1)+j] = value of eigenvector j at interior node i+1; lam ascending),
+ * the basis change T ((p+1)^2, u_gll = T u_fdm) and the FDM-basis matrices
+ * Af = T^T A T, Bf = T^T B T with their structural zeros set to 0 after
+ * checking that they are below 1e-12 relative.  Any output may be NULL. */
+int or_basis1d(int p, double *xi, double *A, double *B, double *S, double *lam,
+               double *T, double *Af, double *Bf);
+
+/* ---- problem context ------------------------------------------------ */
+typedef struct or_ctx or_ctx;
+
+/* Create a problem.  xv/yv/zv: nx+1, ny+1, nz+1 vertex coordinates.
+ * jac: NULL for box cells; else J = dx/dxhat (row-major 3x3) at the
+ *   (p+1)^3 Gauss-Legendre points of every cell (points x fastest), cells x
+ *   fastest: 9*(p+1)^3*nx*ny*nz doubles.
+ * kappa: NULL for kappa = 1; else kappa at the same points.
+ * The stiffness uses a(v,u) = int kappa grad v . grad u with Gauss-Legendre
+ * quadrature of p+1 points per direction (exact on box cells, where the
+ * Kronecker form of eq. (kron) is used instead). */
+or_ctx *or_create(int p, int nx, int ny, int nz, const double *xv, const double *yv,
+                  const double *zv, const double *jac, const double *kappa);
+void or_free(or_ctx *c);
+const char *or_last_error(void);
+long or_ndof(const or_ctx *c);
+int or_npatch(const or_ctx *c);
+
+/* Per-cell separable surrogate coefficients mu (3 per cell, x,y,z).  Box
+ * cells: mu_j = prod_i L_i / L_j^2 (Section 2.2); curved cells: cell average
+ * of kappa*Ghat_jj (Section 2.7).  get copies out, set overrides (e.g. with
+ * learned values). */
+void or_get_mu(const or_ctx *c, double *mu);
+void or_set_mu(or_ctx *c, const double *mu);
+
+/* y = A u (FP64), matrix-free, Dirichlet rows/cols removed. */
+void or_stiffness_apply(const or_ctx *c, const double *u, double *y);
+/* b = M f (mass matrix, same quadrature), Dirichlet rows removed. */
+void or_mass_apply(const or_ctx *c, const double *f, double *b);
+
+/* Patch set-up: assemble every vertex-star patch matrix in the FDM basis
+ * from mu, form the interface Schur complement and its dense Cholesky
+ * factor (Section 2.6, eq:LDLT).  vertices = NULL: all vertices; else the
+ * listed vertex ids only (patch solves are then available for those only).
+ * nthreads <= 0: OpenMP default. */
+int or_setup_patches(or_ctx *c, const int *vertices, int nvert, int nthreads);
+/* Star of a vertex: number of dofs and their global grid indices in the
+ * oracle's order (lexicographic over the star box, x fastest), plus the
+ * number of cell-interior dofs.  gidx may be NULL. */
+int or_patch_dofs(const or_ctx *c, int vertex, int *nd, int *nI, long *gidx);
+/* Dense patch matrix A_j in the FDM basis (nd x nd, oracle order). */
+int or_patch_matrix(const or_ctx *c, int vertex, double *Aj);
+/* Interface Schur complement S_G (nG x nG, oracle Gamma order = the
+ * interface dofs in star order) -- requires or_setup_patches. */
+int or_patch_schur(const or_ctx *c, int vertex, double *S);
+/* x = A_j^{-1} r on the star (FDM basis, oracle order). */
+int or_patch_solve(const or_ctx *c, int vertex, const double *r, double *x);
+/* Dense Cholesky S = L L^T of a given SPD matrix in place (lower triangle
+ * of S holds L on return, upper set to 0).  Returns -1 on a pivot <= 0. */
+int or_cholesky(int m, double *S);
+/* Structural fill of the Cholesky factor of a pattern (dense char matrix,
+ * symmetric, m x m): on return pat holds the pattern of L (lower). */
+void or_symbolic_fill(int m, unsigned char *pat);
+
+/* Global basis changes (Section 2.4 "interpolation and restriction"):
+ * r_fdm = T_g^T r and u = T_g u_fdm on the full grid. */
+void or_restrict_fdm(const or_ctx *c, const double *r, double *r_fdm);
+void or_interp_fdm(const or_ctx *c, const double *u_fdm, double *u);
+
+/* z = omega * P_ASM^{-1} r  (Section 2.5, additive over all set-up patches). */
+int or_asm_apply(const or_ctx *c, const double *r, double *z);
+void or_set_omega(or_ctx *c, double omega);
+double or_get_omega(const or_ctx *c);
+
+/* Q1 coarse space on the same mesh (Section 2.5): Galerkin A_c = P^T A P,
+ * dense Cholesky.  z = P A_c^{-1} P^T r. */
+int or_setup_coarse(or_ctx *c);
+int or_coarse_apply(const or_ctx *c, const double *r, double *z);
+int or_coarse_matrix(const or_ctx *c, int *nc, double *Ac);
+
+/* Hybrid multiplicative V(1,1): z = P^{-1} r (Section 2.5). */
+int or_pc_apply(const or_ctx *c, const double *r, double *z);
+
+/* Damping from k CG-Lanczos steps on P_ASM^{-1} A started from b0
+ * (Section 2.5, omega = 2/[(1+a) lmax + (1-a) lmin], a = 1/4).  Sets the
+ * context's omega.  lmin/lmax/omega may be NULL. */
+int or_lanczos_omega(or_ctx *c, const double *b0, int k, double *lmin, double *lmax,
+                     double *omega);
+
+/* PCG from x0 = 0 until ||r||_2 <= rtol ||b||_2 (Section 2.8).
+ * pc: 0 none, 1 omega*ASM, 2 V(1,1).  hist (maxit+1 doubles, may be NULL)
+ * receives ||r_k||_2.  Returns 0 on convergence, 1 if maxit was reached. */
+int or_pcg(const or_ctx *c, const double *b, double *x, double rtol, int maxit, int pc,
+           int *iters, double *hist);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
