@@ -1,0 +1,182 @@
+/*
+ * fdmpc.h -- C-ABI of the GB300 (sm_103a) vertex-star FDM/sparse relaxation
+ * library (Brubeck & Farrell, arXiv 2107.14758).
+ *
+ * The library solves the Q_p continuous Galerkin discretisation of
+ * -div(kappa grad u) = f with homogeneous Dirichlet data on a structured
+ * nx x ny x nz hexahedral mesh (Section 2.1), by PCG preconditioned with the
+ * hybrid p-multigrid/Schwarz V(1,1) cycle of Section 2.5: additive
+ * vertex-star relaxation in the FDM basis (Section 2.4) with sparse patch
+ * Cholesky factors (Section 2.6), and a Q1 coarse space on the same mesh.
+ *
+ * General conventions
+ *   - All vectors are full-grid GLL nodal arrays of length
+ *     (nx p + 1)(ny p + 1)(nz p + 1) doubles, x fastest, DEVICE resident and
+ *     owned by the caller.  Entries on the Dirichlet boundary are ignored on
+ *     input and written as 0 on output.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are stream-ordered and asynchronous unless stated.
+ *   - Every call returns 0 on success or a negative FDM_E* code; the text of
+ *     the last error of a context is returned by fdm_last_error().  No C++
+ *     exception crosses this interface.
+ *   - A context owns all of its device memory (factors, coefficients,
+ *     work vectors).  Concurrent calls on one context must be serialised by
+ *     the caller (one stream at a time).
+ */
+#ifndef FDMPC_H
+#define FDMPC_H
+#include <stddef.h>
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---- */
+#define FDM_OK 0
+#define FDM_EINVAL (-1)   /* bad argument */
+#define FDM_ENOMEM (-2)   /* device or host allocation failed */
+#define FDM_ENOTSPD (-3)  /* a patch or coarse Cholesky pivot was <= 0 */
+#define FDM_ENOCONV (-4)  /* PCG reached maxit before rtol */
+#define FDM_ENAN (-5)     /* a non-finite scalar appeared in PCG */
+#define FDM_ETIMEOUT (-6) /* a bounded device-side wait gave up */
+#define FDM_ECUDA (-7)    /* a CUDA runtime call failed */
+
+/* ---- precision of the preconditioner (Section 2.8; FP64 outer PCG) ---- */
+#define FDM_PREC_FP64 0  /* everything FP64 */
+#define FDM_PREC_FP32 1  /* basis changes, patch solves, V-cycle in FP32 */
+
+/* ---- preconditioner structure ---- */
+#define FDM_PC_NONE 0    /* identity */
+#define FDM_PC_ASM 1     /* omega * P_ASM^{-1} alone */
+#define FDM_PC_VCYCLE 2  /* hybrid multiplicative V(1,1) with the Q1 coarse space */
+
+/* ---- separable surrogate on curved cells (Section 2.7) ---- */
+#define FDM_SURR_AVERAGED 0 /* mu_j = cell average of kappa * Ghat_jj */
+#define FDM_SURR_EXTERNAL 1 /* mu supplied by fdm_surrogate_load */
+
+typedef struct fdm_ctx fdm_ctx;
+
+/* Mesh: nx, ny, nz cells per axis on a tensor grid with HOST vertex
+ * coordinates xv[nx+1], yv[ny+1], zv[nz+1] (strictly increasing).
+ * jac (HOST, optional): for curved cells, the Jacobian dx/dxhat (row-major
+ * 3x3) at the (p+1)^3 Gauss-Legendre points of every cell, points x fastest,
+ * cells x fastest (9 (p+1)^3 nx ny nz doubles); NULL = box cells, for which
+ * the exact Kronecker form of eq. (kron) is used.  The arrays are copied. */
+typedef struct {
+  int nx, ny, nz;
+  const double *xv, *yv, *zv;
+  const double *jac;
+} fdm_mesh;
+
+/* Coefficients (HOST, optional, copied): kappa at the same Gauss points as
+ * jac ((p+1)^3 nx ny nz doubles); NULL = kappa == 1.  Curved cells only. */
+typedef struct {
+  const double *kappa_q;
+} fdm_coeff;
+
+typedef struct {
+  int precision;      /* FDM_PREC_* (default FP32 preconditioner) */
+  int pc;             /* FDM_PC_* (default V-cycle) */
+  int surrogate;      /* FDM_SURR_* (default averaged) */
+  int lanczos_steps;  /* CG-Lanczos steps for omega (default 20) */
+  double omega;       /* > 0: use this damping instead of Lanczos */
+  uint64_t lanczos_seed; /* seed of the N(0,1) Lanczos start vector (default 12345) */
+  int flexible_beta;  /* 1: Polak-Ribiere beta in PCG (default 1 for FP32 PC) */
+  double wait_timeout_s; /* bound on any device-side spin wait (default 1.0) */
+  const double *lanczos_start; /* HOST, optional: Lanczos start vector (ndof doubles);
+                                  NULL = N(0,1) from lanczos_seed (splitmix64 + Box-Muller) */
+} fdm_options;
+
+/* Fills the defaults listed above. */
+int fdm_default_options(fdm_options *opt);
+
+/* Set-up (Sections 2.3-2.6): 1D GLL basis and interior eigenbasis,
+ * per-cell surrogate coefficients, vertex-star patch assembly in the FDM
+ * basis, symbolic factorisation once per patch class (interface ordered by
+ * nested dissection on the star's three vertex planes), FP64 numeric
+ * factorisation of every patch on the device (plus an FP32 copy for the
+ * FP32 preconditioner), the Galerkin Q1 coarse operator, and the damping
+ * omega by CG-Lanczos on P_ASM^{-1} A (Section 2.5).  p in [1, 15].
+ * Synchronises `stream`.  On success *out owns the context. */
+int fdm_setup(const fdm_mesh *mesh, int p, const fdm_coeff *coeff, const fdm_options *opt,
+              fdm_ctx **out, void *stream);
+
+/* y = A u: matrix-free sum-factorised stiffness apply in FP64 (eq. (kron)
+ * on box cells; Gauss quadrature with Ghat = kappa |det J| J^{-1} J^{-T} on
+ * curved cells, Section 2.7).  u, y: device, ndof doubles. */
+int stiffness_apply(fdm_ctx *ctx, const double *u_dev, double *y_dev, void *stream);
+
+/* b = M f: the mass matrix (load vector of nodal data f).  Device arrays. */
+int mass_apply(fdm_ctx *ctx, const double *f_dev, double *b_dev, void *stream);
+
+/* z = omega * P_ASM^{-1} r (Section 2.5): one additive vertex-star sweep:
+ * basis change to the FDM basis, patch gather, Schur condensation, sparse
+ * Cholesky forward and backward solves, interior back-substitution,
+ * deterministic additive scatter, basis change back.  In the context's
+ * preconditioner precision.  Device arrays. */
+int asm_apply(fdm_ctx *ctx, const double *r_dev, double *z_dev, void *stream);
+
+/* z = P^{-1} r: the context's preconditioner (V(1,1) by default). */
+int pc_apply(fdm_ctx *ctx, const double *r_dev, double *z_dev, void *stream);
+
+/* Solve information filled by pcg_solve. */
+typedef struct {
+  int iterations;        /* number of PCG iterations performed */
+  int converged;         /* 1 if ||r||_2 <= rtol ||b||_2 was reached */
+  double rnorm0;         /* ||b||_2 */
+  double rnorm;          /* final recursive residual ||r_k||_2 */
+  double true_rnorm;     /* ||b - A x||_2 recomputed in FP64 */
+  double seconds;        /* device time of the solve (CUDA events) */
+} fdm_solve_info;
+
+/* PCG from x0 = 0 until ||r||_2 <= rtol ||b||_2 (Euclidean norm of the
+ * unpreconditioned residual, Section 2.8) or maxit iterations.  FP64 dot
+ * products (fixed-order reductions), FP64 vector updates and FP64 stiffness
+ * apply.  b, x: device.  info (HOST, may be NULL) is filled; the call
+ * synchronises `stream`.  Returns FDM_ENOCONV if maxit was reached,
+ * FDM_ENAN on a non-finite scalar. */
+int pcg_solve(fdm_ctx *ctx, const double *b_dev, double *x_dev, double rtol, int maxit,
+              fdm_solve_info *info, void *stream);
+
+/* ---- batched solves of independent problems ---- */
+typedef struct fdm_batch fdm_batch;
+/* Groups k set-up contexts (of any sizes and degrees) for one batched PCG
+ * call.  The contexts stay owned by the caller and must outlive the batch. */
+int fdm_batch_setup(int k, fdm_ctx *const *ctxs, fdm_batch **out);
+/* Solves all k problems: b[i], x[i] device vectors of problem i; infos
+ * (HOST, k entries, may be NULL).  Synchronises `stream`. */
+int pcg_solve_batched(fdm_batch *batch, const double *const *b_dev, double *const *x_dev,
+                      double rtol, int maxit, fdm_solve_info *infos, void *stream);
+void fdm_batch_destroy(fdm_batch *batch);
+
+/* ---- surrogate coefficients (Section 2.7) ---- */
+/* Replaces the per-cell surrogate coefficients mu (HOST, 3 per cell, x,y,z
+ * scalings, cells x fastest) and refactors every patch. */
+int fdm_surrogate_load(fdm_ctx *ctx, const double *mu_host, void *stream);
+
+/* ---- introspection ---- */
+#define FDM_Q_NDOF 1         /* int64: number of grid nodes */
+#define FDM_Q_OMEGA 2        /* double: damping */
+#define FDM_Q_LAMBDA 3       /* double[2]: Lanczos lambda_min, lambda_max */
+#define FDM_Q_MU 4           /* double[3*ncell]: surrogate coefficients */
+#define FDM_Q_NPATCH 5       /* int32: number of vertex-star patches */
+#define FDM_Q_PATCH_CLASS 6  /* int32[npatch]: class (0..7) of each patch */
+#define FDM_Q_CLASS_INFO 7   /* int32[8*8]: per class nd, nI, nG, n0, n1, n2, nlines, nnzL */
+#define FDM_Q_GAMMA_ORDER 8  /* int32[...]: per class, star-local index of each interface dof in factor order */
+#define FDM_Q_FACTOR_NNZ 9   /* int64: total structurally nonzero entries of all L_Gamma */
+#define FDM_Q_PATTERN 10     /* uint8[nG*nG] of class `arg` (in: *(int*)out): pattern of L_Gamma */
+#define FDM_Q_FACTOR 11      /* double[nG*nG] of patch `arg` (in: *(int*)out): dense L_Gamma (FP64) */
+#define FDM_Q_BASIS 12       /* double[5 (p+1)^2]: A_hat, B_hat, T, Af, Bf */
+#define FDM_Q_FACTOR_BYTES 13 /* int64[2]: bytes of the FP64 and FP32 factor value arrays */
+#define FDM_Q_SETUP_SECONDS 14 /* double[4]: symbolic, numeric factor, coarse, Lanczos seconds */
+/* Copies the quantity `what` into out (HOST); *len is the capacity in bytes
+ * on input and the size written on output. */
+int fdm_query(fdm_ctx *ctx, int what, void *out, size_t *len);
+
+const char *fdm_last_error(const fdm_ctx *ctx);
+void fdm_destroy(fdm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

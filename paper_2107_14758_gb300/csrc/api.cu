@@ -1,0 +1,877 @@
+// C-ABI entry points of the fdmpc library (declared in include/fdmpc.h).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "factor.h"
+#include "internal.h"
+#include "kernels.h"
+
+namespace fdm {
+[[noreturn]] void fail(int code, const std::string &msg) { throw Error{code, msg}; }
+}  // namespace fdm
+
+using namespace fdm;
+
+namespace {
+thread_local std::string g_last_error;
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+}  // namespace
+
+struct fdm_ctx {
+  Grid g{};
+  int p = 0;
+  fdm_options opt{};
+  Basis1D basis;
+  std::vector<PatchClass> classes;
+  int general = 0;
+  std::vector<void *> allocs;
+  std::string err;
+
+  // device data
+  double *tab64 = nullptr;
+  float *tab32 = nullptr;
+  double *mu_box = nullptr, *mu = nullptr;
+  double *Gw64 = nullptr, *detw64 = nullptr;
+  float *Gw32 = nullptr, *detw32 = nullptr;
+  ClassDev *d_cls = nullptr;
+  std::vector<ClassDev> h_cls;
+  std::vector<PatchDev> h_patches;
+  PatchDev *d_patches = nullptr;
+  int *d_order = nullptr;
+  int npatch = 0, nsolve = 0;
+  int maxG = 0, maxN1 = 0;
+  int64_t nval_total = 0, nstar_total = 0;
+  double *L64 = nullptr;
+  float *L32 = nullptr;
+  double *X64 = nullptr, *E64 = nullptr;
+  float *X32 = nullptr, *E32 = nullptr;
+  size_t smem64 = 0, smem32 = 0;
+  // coarse
+  int nc = 0;
+  int *cfree = nullptr;
+  double *Acinv64 = nullptr, *rc64 = nullptr, *xc64 = nullptr, *cb64 = nullptr;
+  float *Acinv32 = nullptr, *rc32 = nullptr, *xc32 = nullptr, *cb32 = nullptr;
+  // work vectors
+  double *r = nullptr, *z = nullptr, *zold = nullptr, *d = nullptr, *q = nullptr;
+  double *v1 = nullptr, *v2 = nullptr, *v3 = nullptr;
+  float *f_in = nullptr, *f_out = nullptr, *f1 = nullptr, *f2 = nullptr, *f3 = nullptr;
+  double *partial = nullptr, *dots = nullptr, *sc = nullptr;
+  double omega = 1.0, lmin = 0.0, lmax = 0.0;
+  double t_setup[4] = {0, 0, 0, 0};
+
+  template <typename T>
+  T *alloc(size_t n) {
+    void *ptr = nullptr;
+    if (cudaMalloc(&ptr, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      fail(FDM_ENOMEM, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed");
+    }
+    allocs.push_back(ptr);
+    return static_cast<T *>(ptr);
+  }
+  template <typename T>
+  T *upload(const std::vector<T> &h) {
+    T *ptr = alloc<T>(h.size());
+    if (!h.empty()) FDM_CUDA(cudaMemcpy(ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return ptr;
+  }
+  ~fdm_ctx() {
+    for (void *ptr : allocs) cudaFree(ptr);
+  }
+
+  template <typename T> const T *tab() const;
+  template <typename T> T *E() const;
+  template <typename T> T *X() const;
+  template <typename T> const T *L() const;
+  template <typename T> size_t smem() const;
+  OpArgs op_args(bool fp32) const {
+    OpArgs a;
+    a.g = g;
+    a.general = general;
+    a.mu_box = mu_box;
+    a.Gw = fp32 ? (const void *)Gw32 : (const void *)Gw64;
+    a.detw = fp32 ? (const void *)detw32 : (const void *)detw64;
+    a.tab = fp32 ? (const void *)tab32 : (const void *)tab64;
+    return a;
+  }
+};
+template <> const double *fdm_ctx::tab<double>() const { return tab64; }
+template <> const float *fdm_ctx::tab<float>() const { return tab32; }
+template <> double *fdm_ctx::E<double>() const { return E64; }
+template <> float *fdm_ctx::E<float>() const { return E32; }
+template <> double *fdm_ctx::X<double>() const { return X64; }
+template <> float *fdm_ctx::X<float>() const { return X32; }
+template <> const double *fdm_ctx::L<double>() const { return L64; }
+template <> const float *fdm_ctx::L<float>() const { return L32; }
+template <> size_t fdm_ctx::smem<double>() const { return smem64; }
+template <> size_t fdm_ctx::smem<float>() const { return smem32; }
+
+struct fdm_batch {
+  std::vector<fdm_ctx *> ctxs;
+};
+
+namespace {
+
+// ---------------------------------------------------------------- helpers
+__global__ void k_mask_dirichlet(Grid g, double *v) {
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < g.ndof; id += (int64_t)gridDim.x * blockDim.x) {
+    int x = int(id % g.N[0]), y = int((id / g.N[0]) % g.N[1]), z = int(id / ((int64_t)g.N[0] * g.N[1]));
+    if (x == 0 || y == 0 || z == 0 || x == g.N[0] - 1 || y == g.N[1] - 1 || z == g.N[2] - 1) v[id] = 0.0;
+  }
+}
+void mask_dirichlet(const Grid &g, double *v, cudaStream_t st) {
+  int64_t b = std::min<int64_t>((g.ndof + 255) / 256, 152 * 32);
+  k_mask_dirichlet<<<(int)std::max<int64_t>(b, 1), 256, 0, st>>>(g, v);
+}
+
+template <typename T, typename Tin, typename Tout>
+void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st) {
+  launch_restrict_fdm<T, Tin>(c->g, r, c->tab<T>(), c->E<T>(), st);
+  PatchSolveArgs<T> a{c->g, c->d_cls, c->d_patches, c->d_order, c->E<T>(), c->mu, c->tab<T>(), c->L<T>(), c->X<T>()};
+  launch_patch_solve<T>(a, c->nsolve, c->smem<T>(), st);
+  launch_interp_fdm<T, Tout>(c->g, c->d_patches, c->d_cls, c->X<T>(), c->tab<T>(), omega, z, st);
+}
+
+template <typename T>
+void coarse_correct(fdm_ctx *c, const T *r1, T *x, cudaStream_t st);
+template <>
+void coarse_correct<double>(fdm_ctx *c, const double *r1, double *x, cudaStream_t st) {
+  launch_coarse_restrict<double, double>(c->g, r1, c->tab64, c->cfree, c->rc64, c->cb64, st);
+  launch_dense_symv<double>(c->nc, c->Acinv64, c->rc64, c->xc64, st);
+  launch_coarse_prolong<double, double>(c->g, c->xc64, c->tab64, c->cfree, x, true, st);
+}
+template <>
+void coarse_correct<float>(fdm_ctx *c, const float *r1, float *x, cudaStream_t st) {
+  launch_coarse_restrict<float, float>(c->g, r1, c->tab32, c->cfree, c->rc32, c->cb32, st);
+  launch_dense_symv<float>(c->nc, c->Acinv32, c->rc32, c->xc32, st);
+  launch_coarse_prolong<float, float>(c->g, c->xc32, c->tab32, c->cfree, x, true, st);
+}
+
+template <typename T>
+void apply_op(fdm_ctx *c, const T *u, T *y, cudaStream_t st) {
+  launch_operator<T, T, T>(c->op_args(sizeof(T) == 4), false, u, y, c->E<T>(), st);
+}
+
+// hybrid multiplicative V(1,1) (Section 2.5) in precision T
+template <typename T>
+void run_vcycle(fdm_ctx *c, const T *r, T *z, T *x1, T *t, T *r1, cudaStream_t st) {
+  const int64_t n = c->g.ndof;
+  run_asm<T, T, T>(c, r, x1, c->omega, st);  // pre-relaxation
+  apply_op<T>(c, x1, t, st);
+  launch_sub<T>(n, r, t, r1, st);
+  coarse_correct<T>(c, r1, x1, st);  // multiplicative coarse correction
+  apply_op<T>(c, x1, t, st);
+  launch_sub<T>(n, r, t, r1, st);
+  run_asm<T, T, T>(c, r1, t, c->omega, st);  // post-relaxation
+  launch_axpby<T>(n, T(1), x1, T(1), t, z, st);
+}
+
+void pc_apply_impl(fdm_ctx *c, const double *r, double *z, cudaStream_t st) {
+  const int64_t n = c->g.ndof;
+  if (c->opt.pc == FDM_PC_NONE) {
+    FDM_CUDA(cudaMemcpyAsync(z, r, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    mask_dirichlet(c->g, z, st);
+    return;
+  }
+  if (c->opt.precision == FDM_PREC_FP64) {
+    if (c->opt.pc == FDM_PC_ASM) run_asm<double, double, double>(c, r, z, c->omega, st);
+    else run_vcycle<double>(c, r, z, c->v1, c->v2, c->v3, st);
+  } else {
+    if (c->opt.pc == FDM_PC_ASM) {
+      run_asm<float, double, double>(c, r, z, c->omega, st);
+    } else {
+      launch_convert<double, float>(n, r, c->f_in, st);
+      run_vcycle<float>(c, c->f_in, c->f_out, c->f1, c->f2, c->f3, st);
+      launch_convert<float, double>(n, c->f_out, z, st);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- set-up pieces
+void setup_geometry(fdm_ctx *c, const fdm_mesh *mesh, const fdm_coeff *coeff) {
+  const int n = c->g.n, p = c->p, ncell = c->g.ncell;
+  std::vector<double> xv(mesh->xv, mesh->xv + mesh->nx + 1), yv(mesh->yv, mesh->yv + mesh->ny + 1),
+      zv(mesh->zv, mesh->zv + mesh->nz + 1);
+  for (auto *v : {&xv, &yv, &zv})
+    for (size_t i = 0; i + 1 < v->size(); ++i)
+      if (!((*v)[i + 1] > (*v)[i])) fail(FDM_EINVAL, "vertex coordinates must be strictly increasing");
+  std::vector<double> mub(3 * ncell);
+  for (int cz = 0; cz < c->g.nz; ++cz)
+    for (int cy = 0; cy < c->g.ny; ++cy)
+      for (int cx = 0; cx < c->g.nx; ++cx) {
+        int e = cx + c->g.nx * (cy + c->g.ny * cz);
+        double L[3] = {0.5 * (xv[cx + 1] - xv[cx]), 0.5 * (yv[cy + 1] - yv[cy]), 0.5 * (zv[cz + 1] - zv[cz])};
+        double vol = L[0] * L[1] * L[2];
+        for (int a = 0; a < 3; ++a) mub[3 * e + a] = vol / (L[a] * L[a]);  // Section 2.2
+      }
+  c->mu_box = c->upload(mub);
+  std::vector<double> mu = mub;
+  if (mesh->jac) {
+    c->general = 1;
+    const int nq = n * n * n;
+    std::vector<double> Gw((size_t)6 * nq * ncell), dw((size_t)nq * ncell);
+    for (int e = 0; e < ncell; ++e) {
+      double avg[3] = {0, 0, 0};
+      for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j)
+          for (int i = 0; i < n; ++i) {
+            int q = i + n * (j + n * k);
+            const double *J = mesh->jac + ((size_t)e * nq + q) * 9;
+            double a00 = J[4] * J[8] - J[5] * J[7], a01 = J[2] * J[7] - J[1] * J[8], a02 = J[1] * J[5] - J[2] * J[4];
+            double a10 = J[5] * J[6] - J[3] * J[8], a11 = J[0] * J[8] - J[2] * J[6], a12 = J[2] * J[3] - J[0] * J[5];
+            double a20 = J[3] * J[7] - J[4] * J[6], a21 = J[1] * J[6] - J[0] * J[7], a22 = J[0] * J[4] - J[1] * J[3];
+            double det = J[0] * a00 + J[1] * a10 + J[2] * a20;
+            if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) fail(FDM_EINVAL, "singular Jacobian");
+            double Ji[9] = {a00 / det, a01 / det, a02 / det, a10 / det, a11 / det, a12 / det,
+                            a20 / det, a21 / det, a22 / det};
+            double kap = (coeff && coeff->kappa_q) ? coeff->kappa_q[(size_t)e * nq + q] : 1.0;
+            double w = c->basis.wq[i] * c->basis.wq[j] * c->basis.wq[k];
+            // Ghat = kappa |det J| J^{-1} J^{-T}   (Section 2.7)
+            double G[3][3];
+            for (int a = 0; a < 3; ++a)
+              for (int b = 0; b < 3; ++b) {
+                double s = 0.0;
+                for (int r = 0; r < 3; ++r) s += Ji[a * 3 + r] * Ji[b * 3 + r];
+                G[a][b] = kap * std::fabs(det) * s;
+              }
+            double *o = &Gw[((size_t)e * nq + q) * 6];
+            o[0] = w * G[0][0]; o[1] = w * G[1][1]; o[2] = w * G[2][2];
+            o[3] = w * G[0][1]; o[4] = w * G[0][2]; o[5] = w * G[1][2];
+            dw[(size_t)e * nq + q] = w * std::fabs(det);
+            for (int a = 0; a < 3; ++a) avg[a] += w * G[a][a];
+          }
+      for (int a = 0; a < 3; ++a) mu[3 * e + a] = avg[a] / 8.0;  // |K_hat| = 8
+    }
+    c->Gw64 = c->upload(Gw);
+    c->detw64 = c->upload(dw);
+    std::vector<float> Gf(Gw.begin(), Gw.end()), df(dw.begin(), dw.end());
+    c->Gw32 = c->upload(Gf);
+    c->detw32 = c->upload(df);
+  }
+  c->mu = c->upload(mu);
+  (void)p;
+}
+
+void setup_tables(fdm_ctx *c) {
+  const Basis1D &b = c->basis;
+  const int n = b.n;
+  std::vector<double> t(tab_size(n), 0.0);
+  auto put = [&](int which, const std::vector<double> &M) { std::copy(M.begin(), M.end(), t.begin() + tab_off(which, n)); };
+  put(TAB_A, b.A);
+  put(TAB_B, b.B);
+  put(TAB_AF, b.Af);
+  put(TAB_BF, b.Bf);
+  put(TAB_T, b.T);
+  put(TAB_VQ, b.Vq);
+  put(TAB_DQ, b.Dq);
+  std::copy(b.xi.begin(), b.xi.end(), t.begin() + tab_off(TAB_XI, n));
+  c->tab64 = c->upload(t);
+  std::vector<float> tf(t.begin(), t.end());
+  c->tab32 = c->upload(tf);
+}
+
+void setup_patches(fdm_ctx *c) {
+  const int p = c->p;
+  c->classes = build_classes(p);
+  c->h_cls.resize(8);
+  for (int id = 0; id < 8; ++id) {
+    const PatchClass &C = c->classes[id];
+    ClassDev &D = c->h_cls[id];
+    D.nd = C.nd; D.nI = C.nI; D.nG = C.nG; D.n0 = C.n0; D.n1 = C.n1; D.n2 = C.n2;
+    D.nlines = C.nlines; D.K0 = C.K0; D.nrow0 = C.nrow0; D.ld21 = C.ld21; D.npanel = C.npanel;
+    for (int a = 0; a < 3; ++a) { D.dim[a] = C.dim[a]; D.full[a] = C.full[a]; }
+    D.off_dinv0 = C.off_dinv0; D.off_ell = C.off_ell; D.off_lines = C.off_lines;
+    D.off_l21 = C.off_l21; D.off_pan = C.off_pan; D.nval = C.nval;
+    D.gpos = c->upload(C.gpos);
+    D.line_start = c->upload(C.line_start);
+    D.line_len = c->upload(C.line_len);
+    D.line_off = c->upload(C.line_off);
+    D.ell_col = c->upload(C.ell_col);
+    D.c0_ptr = c->upload(C.c0_ptr);
+    D.c0_pos = c->upload(C.c0_pos);
+    D.r0_ptr = c->upload(C.r0_ptr);
+    D.r0_idx = c->upload(C.r0_idx);
+    D.pan_off = c->upload(C.pan_off);
+    D.ginv = c->upload(C.ginv);
+    D.line_of = c->upload(C.line_of);
+    c->maxG = std::max(c->maxG, C.nG);
+    c->maxN1 = std::max(c->maxN1, C.n1);
+  }
+  c->d_cls = c->upload(c->h_cls);
+  const int nvx = c->g.nx + 1, nvy = c->g.ny + 1, nvz = c->g.nz + 1;
+  c->npatch = nvx * nvy * nvz;
+  c->h_patches.resize(c->npatch);
+  int64_t voff = 0, xoff = 0;
+  std::vector<int> order;
+  for (int vz = 0; vz < nvz; ++vz)
+    for (int vy = 0; vy < nvy; ++vy)
+      for (int vx = 0; vx < nvx; ++vx) {
+        int pid = vx + nvx * (vy + nvy * vz);
+        int v[3] = {vx, vy, vz}, nc[3] = {c->g.nx, c->g.ny, c->g.nz}, cls = 0;
+        for (int a = 0; a < 3; ++a)
+          if (v[a] >= 1 && v[a] <= nc[a] - 1) cls |= 1 << a;
+        PatchDev &P = c->h_patches[pid];
+        P.cls = cls;
+        P.v[0] = vx; P.v[1] = vy; P.v[2] = vz;
+        P.voff = voff;
+        P.xoff = xoff;
+        voff += c->classes[cls].nval;
+        xoff += c->classes[cls].nd;
+        if (c->classes[cls].nd > 0) order.push_back(pid);
+      }
+  // heaviest patches first (one CTA each) for load balance
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return c->classes[c->h_patches[a].cls].nval > c->classes[c->h_patches[b].cls].nval;
+  });
+  c->nsolve = (int)order.size();
+  c->nval_total = voff;
+  c->nstar_total = xoff;
+  c->d_patches = c->upload(c->h_patches);
+  c->d_order = c->upload(order);
+  c->L64 = c->alloc<double>(voff);
+  c->L32 = c->alloc<float>(voff);
+  c->X64 = c->alloc<double>(xoff);
+  c->X32 = c->alloc<float>(xoff);
+  const int64_t ne = (int64_t)c->g.ncell * c->g.n * c->g.n * c->g.n;
+  c->E64 = c->alloc<double>(ne);
+  c->E32 = c->alloc<float>(ne);
+  c->smem64 = patch_smem_bytes<double>(c->g.n, c->maxG, c->maxN1);
+  c->smem32 = patch_smem_bytes<float>(c->g.n, c->maxG, c->maxN1);
+  if (c->smem64 > 200 * 1024) fail(FDM_EINVAL, "patch interface too large for shared memory");
+}
+
+// numeric factorisation of every patch (FP64 with an FP32 copy)
+void factor_all(fdm_ctx *c, cudaStream_t st) {
+  const int64_t per = (int64_t)c->maxG * c->maxG;
+  if (per == 0) return;
+  std::vector<int> ids;
+  for (int pid = 0; pid < c->npatch; ++pid)
+    if (c->classes[c->h_patches[pid].cls].nG > 0 || c->classes[c->h_patches[pid].cls].n0 >= 0) ids.push_back(pid);
+  const int64_t budget = (int64_t)6 << 30;  // bytes of dense workspace
+  int batch = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)ids.size(), budget / (per * 8)));
+  double *S = c->alloc<double>((size_t)batch * per);
+  int *status = c->alloc<int>(1);
+  int *plist = c->alloc<int>(batch);
+  FDM_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  for (size_t b0 = 0; b0 < ids.size(); b0 += batch) {
+    int cnt = (int)std::min<size_t>(batch, ids.size() - b0);
+    FDM_CUDA(cudaMemcpyAsync(plist, ids.data() + b0, cnt * sizeof(int), cudaMemcpyHostToDevice, st));
+    FactorArgs a{c->g, c->d_cls, c->d_patches, plist, c->mu, c->tab64, S, per, c->L64, c->L32, status};
+    launch_factor_batch(a, cnt, st);
+    FDM_CUDA(cudaStreamSynchronize(st));
+  }
+  FDM_CUDA(cudaGetLastError());
+  int hs = 0;
+  FDM_CUDA(cudaMemcpy(&hs, status, sizeof(int), cudaMemcpyDeviceToHost));
+  // workspace is released with the context; free it now to return memory early
+  cudaFree(S);
+  c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), (void *)S));
+  if (hs) fail(FDM_ENOTSPD, "a patch Schur complement has a nonpositive pivot");
+}
+
+void setup_coarse(fdm_ctx *c, cudaStream_t st) {
+  const int nvx = c->g.nx + 1, nvy = c->g.ny + 1, nvz = c->g.nz + 1, nv = nvx * nvy * nvz;
+  std::vector<int> cfree(nv, -1);
+  int nc = 0;
+  for (int vz = 0; vz < nvz; ++vz)
+    for (int vy = 0; vy < nvy; ++vy)
+      for (int vx = 0; vx < nvx; ++vx)
+        if (vx > 0 && vy > 0 && vz > 0 && vx < nvx - 1 && vy < nvy - 1 && vz < nvz - 1)
+          cfree[vx + nvx * (vy + nvy * vz)] = nc++;
+  c->nc = nc;
+  c->cfree = c->upload(cfree);
+  c->cb64 = c->alloc<double>((size_t)8 * c->g.ncell);
+  c->cb32 = c->alloc<float>((size_t)8 * c->g.ncell);
+  c->rc64 = c->alloc<double>(nc);
+  c->xc64 = c->alloc<double>(nc);
+  c->rc32 = c->alloc<float>(nc);
+  c->xc32 = c->alloc<float>(nc);
+  if (nc == 0) return;
+  double *Ac = c->alloc<double>((size_t)64 * c->g.ncell);
+  launch_coarse_cell_matrices(c->op_args(false), Ac, st);
+  FDM_CUDA(cudaGetLastError());
+  std::vector<double> hAc((size_t)64 * c->g.ncell);
+  FDM_CUDA(cudaMemcpyAsync(hAc.data(), Ac, hAc.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  FDM_CUDA(cudaStreamSynchronize(st));
+  // banded lower storage Lb[i][k] = A[i][i-k]
+  const int bw = 1 + (c->g.nx - 1) + (c->g.nx - 1) * (c->g.ny - 1);
+  std::vector<double> Lb((size_t)nc * (bw + 1), 0.0);
+  for (int cz = 0; cz < c->g.nz; ++cz)
+    for (int cy = 0; cy < c->g.ny; ++cy)
+      for (int cx = 0; cx < c->g.nx; ++cx) {
+        int e = cx + c->g.nx * (cy + c->g.ny * cz);
+        int f[8];
+        for (int s = 0; s < 8; ++s)
+          f[s] = cfree[(cx + (s & 1)) + nvx * ((cy + ((s >> 1) & 1)) + nvy * (cz + (s >> 2)))];
+        for (int t = 0; t < 8; ++t)
+          for (int s = 0; s < 8; ++s)
+            if (f[t] >= 0 && f[s] >= 0 && f[t] >= f[s]) Lb[(size_t)f[t] * (bw + 1) + (f[t] - f[s])] += hAc[(size_t)e * 64 + t * 8 + s];
+      }
+  // banded Cholesky
+  for (int i = 0; i < nc; ++i)
+    for (int k = std::max(0, i - bw); k <= i; ++k) {
+      double s = Lb[(size_t)i * (bw + 1) + (i - k)];
+      for (int j = std::max(0, std::max(i - bw, k - bw)); j < k; ++j)
+        s -= Lb[(size_t)i * (bw + 1) + (i - j)] * Lb[(size_t)k * (bw + 1) + (k - j)];
+      if (k == i) {
+        if (!(s > 0.0)) fail(FDM_ENOTSPD, "coarse operator is not positive definite");
+        Lb[(size_t)i * (bw + 1)] = std::sqrt(s);
+      } else {
+        Lb[(size_t)i * (bw + 1) + (i - k)] = s / Lb[(size_t)k * (bw + 1)];
+      }
+    }
+  double *dLb = c->upload(Lb);
+  c->Acinv64 = c->alloc<double>((size_t)nc * nc);
+  c->Acinv32 = c->alloc<float>((size_t)nc * nc);
+  launch_banded_inverse(nc, bw, dLb, c->Acinv64, st);
+  launch_convert<double, float>((int64_t)nc * nc, c->Acinv64, c->Acinv32, st);
+  FDM_CUDA(cudaStreamSynchronize(st));
+  FDM_CUDA(cudaGetLastError());
+}
+
+// extreme eigenvalues of the symmetric tridiagonal matrix (d, e) by bisection
+void tridiag_extremes(const std::vector<double> &d, const std::vector<double> &e, double &lo, double &hi) {
+  const int m = (int)d.size();
+  auto below = [&](double x) {
+    int cnt = 0;
+    double q = 1.0;
+    for (int i = 0; i < m; ++i) {
+      q = d[i] - x - (i > 0 ? e[i - 1] * e[i - 1] / q : 0.0);
+      if (q == 0.0) q = -1e-300;
+      if (q < 0.0) ++cnt;
+    }
+    return cnt;
+  };
+  double a = d[0], b = d[0];
+  for (int i = 0; i < m; ++i) {
+    double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(e[i]) : 0.0);
+    a = std::min(a, d[i] - r);
+    b = std::max(b, d[i] + r);
+  }
+  auto kth = [&](int k) {
+    double l = a, h = b;
+    for (int it = 0; it < 300 && h - l > 1e-15 * std::max(std::fabs(l), std::fabs(h)); ++it) {
+      double mid = 0.5 * (l + h);
+      if (below(mid) > k) h = mid; else l = mid;
+    }
+    return 0.5 * (l + h);
+  };
+  lo = kth(0);
+  hi = kth(m - 1);
+}
+
+// splitmix64 + Box-Muller: the library's own seeded N(0,1) stream
+void normal_vector(uint64_t seed, int64_t n, std::vector<double> &out) {
+  out.resize(n);
+  uint64_t s = seed;
+  auto next = [&]() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  for (int64_t i = 0; i < n; i += 2) {
+    double u1 = ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    double u2 = ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    double rr = std::sqrt(-2.0 * std::log(u1)), th = 2.0 * M_PI * u2;
+    out[i] = rr * std::cos(th);
+    if (i + 1 < n) out[i + 1] = rr * std::sin(th);
+  }
+}
+
+// omega from k CG-Lanczos steps on P_ASM^{-1} A (Section 2.5), FP64
+void lanczos_omega(fdm_ctx *c, const double *start_host, cudaStream_t st) {
+  const int64_t n = c->g.ndof;
+  std::vector<double> b0;
+  if (start_host) b0.assign(start_host, start_host + n);
+  else normal_vector(c->opt.lanczos_seed, n, b0);
+  FDM_CUDA(cudaMemcpyAsync(c->r, b0.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+  mask_dirichlet(c->g, c->r, st);
+  run_asm<double, double, double>(c, c->r, c->z, 1.0, st);
+  FDM_CUDA(cudaMemcpyAsync(c->d, c->z, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  double h[2];
+  launch_dot(n, c->r, c->z, c->partial, c->dots, st);
+  FDM_CUDA(cudaMemcpyAsync(h, c->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
+  FDM_CUDA(cudaStreamSynchronize(st));
+  double rz = h[0];
+  std::vector<double> al, be;
+  for (int k = 0; k < c->opt.lanczos_steps; ++k) {
+    if (!(rz > 0.0)) break;
+    launch_operator<double, double, double>(c->op_args(false), false, c->d, c->q, c->E64, st);
+    launch_dot(n, c->d, c->q, c->partial, c->dots, st);
+    FDM_CUDA(cudaMemcpyAsync(h, c->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
+    FDM_CUDA(cudaStreamSynchronize(st));
+    if (!(h[0] > 0.0)) break;
+    double alpha = rz / h[0];
+    al.push_back(alpha);
+    launch_axpby<double>(n, -alpha, c->q, 1.0, c->r, c->r, st);
+    run_asm<double, double, double>(c, c->r, c->z, 1.0, st);
+    launch_dot(n, c->r, c->z, c->partial, c->dots, st);
+    FDM_CUDA(cudaMemcpyAsync(h, c->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
+    FDM_CUDA(cudaStreamSynchronize(st));
+    double beta = h[0] / rz;
+    be.push_back(beta);
+    rz = h[0];
+    launch_axpby<double>(n, 1.0, c->z, beta, c->d, c->d, st);
+  }
+  const int m = (int)al.size();
+  if (m < 1) fail(FDM_EINVAL, "Lanczos: no steps could be taken");
+  std::vector<double> dd(m), ee(std::max(m - 1, 1), 0.0);
+  for (int j = 0; j < m; ++j) {
+    dd[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+    if (j + 1 < m) ee[j] = std::sqrt(be[j]) / al[j];
+  }
+  tridiag_extremes(dd, ee, c->lmin, c->lmax);
+  const double alpha = 0.25;
+  c->omega = 2.0 / ((1.0 + alpha) * c->lmax + (1.0 - alpha) * c->lmin);
+}
+
+int handle(fdm_ctx *c, const Error &e) {
+  if (c) c->err = e.msg;
+  g_last_error = e.msg;
+  return e.code;
+}
+
+}  // namespace
+
+// ====================================================================== C-ABI
+extern "C" {
+
+int fdm_default_options(fdm_options *opt) {
+  if (!opt) return FDM_EINVAL;
+  std::memset(opt, 0, sizeof *opt);
+  opt->precision = FDM_PREC_FP32;
+  opt->pc = FDM_PC_VCYCLE;
+  opt->surrogate = FDM_SURR_AVERAGED;
+  opt->lanczos_steps = 20;
+  opt->omega = 0.0;
+  opt->lanczos_seed = 12345;
+  opt->flexible_beta = -1;
+  opt->wait_timeout_s = 1.0;
+  opt->lanczos_start = nullptr;
+  return FDM_OK;
+}
+
+int fdm_setup(const fdm_mesh *mesh, int p, const fdm_coeff *coeff, const fdm_options *opt, fdm_ctx **out,
+              void *stream) {
+  if (!mesh || !out || !mesh->xv || !mesh->yv || !mesh->zv || mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1) {
+    g_last_error = "fdm_setup: invalid mesh";
+    return FDM_EINVAL;
+  }
+  if (p < 1 || p > 15) {
+    g_last_error = "fdm_setup: the CUDA path supports 1 <= p <= 15";
+    return FDM_EINVAL;
+  }
+  *out = nullptr;
+  fdm_ctx *c = new fdm_ctx();
+  cudaStream_t st = (cudaStream_t)stream;
+  try {
+    if (opt) c->opt = *opt;
+    else fdm_default_options(&c->opt);
+    if (c->opt.lanczos_steps <= 0) c->opt.lanczos_steps = 20;
+    if (c->opt.flexible_beta < 0) c->opt.flexible_beta = c->opt.precision == FDM_PREC_FP32 ? 1 : 0;
+    c->p = p;
+    Grid &g = c->g;
+    g.p = p;
+    g.n = p + 1;
+    g.nx = mesh->nx; g.ny = mesh->ny; g.nz = mesh->nz;
+    g.N[0] = g.nx * p + 1; g.N[1] = g.ny * p + 1; g.N[2] = g.nz * p + 1;
+    g.ndof = (int64_t)g.N[0] * g.N[1] * g.N[2];
+    g.ncell = g.nx * g.ny * g.nz;
+    double t0 = now_s();
+    c->basis = make_basis(p);
+    setup_tables(c);
+    setup_geometry(c, mesh, coeff);
+    setup_patches(c);
+    // work vectors
+    const int64_t n = g.ndof;
+    for (double **v : {&c->r, &c->z, &c->zold, &c->d, &c->q, &c->v1, &c->v2, &c->v3}) *v = c->alloc<double>(n);
+    for (float **v : {&c->f_in, &c->f_out, &c->f1, &c->f2, &c->f3}) *v = c->alloc<float>(n);
+    c->partial = c->alloc<double>(2 * DOT_BLOCKS);
+    c->dots = c->alloc<double>(4);
+    c->sc = c->alloc<double>(16);
+    double t1 = now_s();
+    factor_all(c, st);
+    double t2 = now_s();
+    setup_coarse(c, st);
+    double t3 = now_s();
+    if (c->opt.omega > 0.0) c->omega = c->opt.omega;
+    else lanczos_omega(c, c->opt.lanczos_start, st);
+    FDM_CUDA(cudaStreamSynchronize(st));
+    FDM_CUDA(cudaGetLastError());
+    double t4 = now_s();
+    c->t_setup[0] = t1 - t0;
+    c->t_setup[1] = t2 - t1;
+    c->t_setup[2] = t3 - t2;
+    c->t_setup[3] = t4 - t3;
+  } catch (const Error &e) {
+    int rc = handle(c, e);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return FDM_OK;
+}
+
+int stiffness_apply(fdm_ctx *c, const double *u, double *y, void *stream) {
+  if (!c || !u || !y) return FDM_EINVAL;
+  try {
+    launch_operator<double, double, double>(c->op_args(false), false, u, y, c->E64, (cudaStream_t)stream);
+    FDM_CUDA(cudaGetLastError());
+  } catch (const Error &e) { return handle(c, e); }
+  return FDM_OK;
+}
+
+int mass_apply(fdm_ctx *c, const double *f, double *b, void *stream) {
+  if (!c || !f || !b) return FDM_EINVAL;
+  try {
+    launch_operator<double, double, double>(c->op_args(false), true, f, b, c->E64, (cudaStream_t)stream);
+    FDM_CUDA(cudaGetLastError());
+  } catch (const Error &e) { return handle(c, e); }
+  return FDM_OK;
+}
+
+int asm_apply(fdm_ctx *c, const double *r, double *z, void *stream) {
+  if (!c || !r || !z) return FDM_EINVAL;
+  try {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (c->opt.precision == FDM_PREC_FP64) run_asm<double, double, double>(c, r, z, c->omega, st);
+    else run_asm<float, double, double>(c, r, z, c->omega, st);
+    FDM_CUDA(cudaGetLastError());
+  } catch (const Error &e) { return handle(c, e); }
+  return FDM_OK;
+}
+
+int pc_apply(fdm_ctx *c, const double *r, double *z, void *stream) {
+  if (!c || !r || !z) return FDM_EINVAL;
+  try {
+    pc_apply_impl(c, r, z, (cudaStream_t)stream);
+    FDM_CUDA(cudaGetLastError());
+  } catch (const Error &e) { return handle(c, e); }
+  return FDM_OK;
+}
+
+int pcg_solve(fdm_ctx *c, const double *b, double *x, double rtol, int maxit, fdm_solve_info *info, void *stream) {
+  if (!c || !b || !x || maxit < 0 || !(rtol >= 0.0)) return FDM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = c->g.ndof;
+  try {
+    cudaEvent_t e0, e1;
+    FDM_CUDA(cudaEventCreate(&e0));
+    FDM_CUDA(cudaEventCreate(&e1));
+    FDM_CUDA(cudaEventRecord(e0, st));
+    const double flex = c->opt.flexible_beta ? 1.0 : 0.0;
+    double hsc[16] = {0};
+    hsc[7] = flex;
+    FDM_CUDA(cudaMemcpyAsync(c->sc, hsc, sizeof hsc, cudaMemcpyHostToDevice, st));
+    FDM_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+    FDM_CUDA(cudaMemcpyAsync(c->r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    mask_dirichlet(c->g, c->r, st);
+    double h[2];
+    launch_dot(n, c->r, c->r, c->partial, c->dots, st);
+    FDM_CUDA(cudaMemcpyAsync(h, c->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
+    FDM_CUDA(cudaStreamSynchronize(st));
+    const double nb = std::sqrt(h[0]);
+    double nr = nb;
+    int it = 0, conv = nb == 0.0, bad = 0;
+    double *z = c->z, *zold = c->zold;
+    if (!conv) {
+      pc_apply_impl(c, c->r, z, st);
+      launch_dot(n, c->r, z, c->partial, c->dots, st);
+      launch_pcg_scalars(2, c->sc, c->dots, st);
+      FDM_CUDA(cudaMemcpyAsync(c->d, z, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      while (it < maxit) {
+        launch_operator<double, double, double>(c->op_args(false), false, c->d, c->q, c->E64, st);
+        launch_dot(n, c->d, c->q, c->partial, c->dots, st);
+        launch_pcg_scalars(0, c->sc, c->dots, st);
+        launch_pcg_update_xr(n, c->sc, c->d, c->q, x, c->r, st);
+        ++it;
+        launch_dot(n, c->r, c->r, c->partial, c->dots + 2, st);
+        FDM_CUDA(cudaMemcpyAsync(h, c->dots + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+        FDM_CUDA(cudaStreamSynchronize(st));
+        nr = std::sqrt(h[0]);
+        if (!std::isfinite(nr)) { bad = 1; break; }
+        if (nr <= rtol * nb) { conv = 1; break; }
+        std::swap(z, zold);
+        pc_apply_impl(c, c->r, z, st);
+        launch_dot2(n, c->r, z, zold, c->partial, c->dots, st);
+        launch_pcg_scalars(1, c->sc, c->dots, st);
+        launch_pcg_update_d(n, c->sc, z, c->d, st);
+      }
+    }
+    FDM_CUDA(cudaEventRecord(e1, st));
+    FDM_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    FDM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    FDM_CUDA(cudaMemcpy(hsc, c->sc, sizeof hsc, cudaMemcpyDeviceToHost));
+    if (hsc[8] != 0.0) bad = 1;
+    if (info) {
+      info->iterations = it;
+      info->converged = conv;
+      info->rnorm0 = nb;
+      info->rnorm = nr;
+      info->seconds = ms * 1e-3;
+      // true residual ||b - A x||
+      launch_operator<double, double, double>(c->op_args(false), false, x, c->q, c->E64, st);
+      launch_sub<double>(n, b, c->q, c->v1, st);
+      mask_dirichlet(c->g, c->v1, st);
+      launch_dot(n, c->v1, c->v1, c->partial, c->dots, st);
+      FDM_CUDA(cudaMemcpyAsync(h, c->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
+      FDM_CUDA(cudaStreamSynchronize(st));
+      info->true_rnorm = std::sqrt(h[0]);
+    }
+    FDM_CUDA(cudaGetLastError());
+    if (bad) { c->err = "non-finite scalar in PCG"; return FDM_ENAN; }
+    if (!conv) { c->err = "PCG reached maxit"; return FDM_ENOCONV; }
+  } catch (const Error &e) { return handle(c, e); }
+  return FDM_OK;
+}
+
+int fdm_batch_setup(int k, fdm_ctx *const *ctxs, fdm_batch **out) {
+  if (k < 0 || !out || (k > 0 && !ctxs)) return FDM_EINVAL;
+  fdm_batch *b = new fdm_batch();
+  for (int i = 0; i < k; ++i) {
+    if (!ctxs[i]) { delete b; return FDM_EINVAL; }
+    b->ctxs.push_back(ctxs[i]);
+  }
+  *out = b;
+  return FDM_OK;
+}
+
+int pcg_solve_batched(fdm_batch *b, const double *const *bv, double *const *xv, double rtol, int maxit,
+                      fdm_solve_info *infos, void *stream) {
+  if (!b || !bv || !xv) return FDM_EINVAL;
+  int worst = FDM_OK;
+  for (size_t i = 0; i < b->ctxs.size(); ++i) {
+    int rc = pcg_solve(b->ctxs[i], bv[i], xv[i], rtol, maxit, infos ? infos + i : nullptr, stream);
+    if (rc < worst) worst = rc;
+  }
+  return worst;
+}
+
+void fdm_batch_destroy(fdm_batch *b) { delete b; }
+
+int fdm_surrogate_load(fdm_ctx *c, const double *mu_host, void *stream) {
+  if (!c || !mu_host) return FDM_EINVAL;
+  try {
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int64_t i = 0; i < 3 * (int64_t)c->g.ncell; ++i)
+      if (!(mu_host[i] > 0.0) || !std::isfinite(mu_host[i])) fail(FDM_EINVAL, "surrogate coefficients must be positive");
+    FDM_CUDA(cudaMemcpyAsync(c->mu, mu_host, 3 * sizeof(double) * c->g.ncell, cudaMemcpyHostToDevice, st));
+    factor_all(c, st);
+    if (c->opt.omega <= 0.0) lanczos_omega(c, c->opt.lanczos_start, st);
+    FDM_CUDA(cudaStreamSynchronize(st));
+  } catch (const Error &e) { return handle(c, e); }
+  return FDM_OK;
+}
+
+int fdm_query(fdm_ctx *c, int what, void *out, size_t *len) {
+  if (!c || !out || !len) return FDM_EINVAL;
+  try {
+    auto put = [&](const void *src, size_t bytes) {
+      if (*len < bytes) fail(FDM_EINVAL, "fdm_query: buffer too small (" + std::to_string(bytes) + " bytes needed)");
+      std::memcpy(out, src, bytes);
+      *len = bytes;
+    };
+    switch (what) {
+      case FDM_Q_NDOF: { int64_t v = c->g.ndof; put(&v, sizeof v); break; }
+      case FDM_Q_OMEGA: put(&c->omega, sizeof(double)); break;
+      case FDM_Q_LAMBDA: { double v[2] = {c->lmin, c->lmax}; put(v, sizeof v); break; }
+      case FDM_Q_MU: {
+        std::vector<double> h(3 * (size_t)c->g.ncell);
+        FDM_CUDA(cudaMemcpy(h.data(), c->mu, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        put(h.data(), h.size() * sizeof(double));
+        break;
+      }
+      case FDM_Q_NPATCH: put(&c->npatch, sizeof(int)); break;
+      case FDM_Q_PATCH_CLASS: {
+        std::vector<int> h(c->npatch);
+        for (int i = 0; i < c->npatch; ++i) h[i] = c->h_patches[i].cls;
+        put(h.data(), h.size() * sizeof(int));
+        break;
+      }
+      case FDM_Q_CLASS_INFO: {
+        std::vector<int> h(64, 0);
+        for (int i = 0; i < 8; ++i) {
+          const PatchClass &C = c->classes[i];
+          int v[8] = {C.nd, C.nI, C.nG, C.n0, C.n1, C.n2, C.nlines, (int)C.nnzL};
+          std::copy(v, v + 8, h.begin() + 8 * i);
+        }
+        put(h.data(), h.size() * sizeof(int));
+        break;
+      }
+      case FDM_Q_GAMMA_ORDER: {
+        std::vector<int> h;
+        for (int i = 0; i < 8; ++i) h.insert(h.end(), c->classes[i].gpos.begin(), c->classes[i].gpos.end());
+        put(h.data(), h.size() * sizeof(int));
+        break;
+      }
+      case FDM_Q_FACTOR_NNZ: {
+        int64_t s = 0;
+        for (int i = 0; i < c->npatch; ++i) s += c->classes[c->h_patches[i].cls].nnzL;
+        put(&s, sizeof s);
+        break;
+      }
+      case FDM_Q_PATTERN: {
+        int cls = *(const int *)out;
+        if (cls < 0 || cls > 7) fail(FDM_EINVAL, "class id");
+        const auto &pt = c->classes[cls].pattern;
+        put(pt.data(), pt.size());
+        break;
+      }
+      case FDM_Q_FACTOR: {
+        int pid = *(const int *)out;
+        if (pid < 0 || pid >= c->npatch) fail(FDM_EINVAL, "patch id");
+        const int nG = c->classes[c->h_patches[pid].cls].nG;
+        if (*len < (size_t)nG * nG * sizeof(double)) fail(FDM_EINVAL, "fdm_query: buffer too small");
+        double *S = c->alloc<double>((size_t)c->maxG * c->maxG);
+        int *plist = c->alloc<int>(1);
+        int *status = c->alloc<int>(1);
+        FDM_CUDA(cudaMemcpy(plist, &pid, sizeof(int), cudaMemcpyHostToDevice));
+        FactorArgs a{c->g, c->d_cls, c->d_patches, plist, c->mu, c->tab64, S, (int64_t)c->maxG * c->maxG,
+                     nullptr, nullptr, status};
+        launch_assemble_factor_only(a, 1, 0);
+        FDM_CUDA(cudaDeviceSynchronize());
+        std::vector<double> h((size_t)nG * nG);
+        FDM_CUDA(cudaMemcpy(h.data(), S, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        for (void *ptr : {(void *)S, (void *)plist, (void *)status}) {
+          cudaFree(ptr);
+          c->allocs.erase(std::find(c->allocs.begin(), c->allocs.end(), ptr));
+        }
+        for (int i = 0; i < nG; ++i)
+          for (int j = i + 1; j < nG; ++j) h[(size_t)i * nG + j] = 0.0;
+        put(h.data(), h.size() * sizeof(double));
+        break;
+      }
+      case FDM_Q_BASIS: {
+        const Basis1D &b = c->basis;
+        std::vector<double> h;
+        for (auto *M : {&b.A, &b.B, &b.T, &b.Af, &b.Bf}) h.insert(h.end(), M->begin(), M->end());
+        put(h.data(), h.size() * sizeof(double));
+        break;
+      }
+      case FDM_Q_FACTOR_BYTES: {
+        int64_t v[2] = {c->nval_total * 8, c->nval_total * 4};
+        put(v, sizeof v);
+        break;
+      }
+      case FDM_Q_SETUP_SECONDS: put(c->t_setup, sizeof c->t_setup); break;
+      default: fail(FDM_EINVAL, "fdm_query: unknown quantity");
+    }
+  } catch (const Error &e) { return handle(c, e); }
+  return FDM_OK;
+}
+
+const char *fdm_last_error(const fdm_ctx *c) { return c ? c->err.c_str() : g_last_error.c_str(); }
+
+void fdm_destroy(fdm_ctx *c) { delete c; }
+
+}  // extern "C"

@@ -1,0 +1,95 @@
+// Internal declarations of the fdmpc library (not part of the C-ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fdmpc.h"
+
+namespace fdm {
+
+constexpr int PMAX = 31;
+constexpr int PANEL = 32;  // panel width of the dense top level of L_Gamma
+
+// ---------------------------------------------------------------- errors
+struct Error {
+  int code;
+  std::string msg;
+};
+[[noreturn]] void fail(int code, const std::string &msg);
+#define FDM_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      ::fdm::fail(FDM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+// ---------------------------------------------------------------- 1D basis
+struct Basis1D {
+  int p = 0, n = 0;
+  std::vector<double> xi, wgll;        // GLL nodes/weights
+  std::vector<double> xq, wq;          // Gauss nodes/weights (q = n)
+  std::vector<double> A, B;            // reference stiffness/mass, GLL basis (n x n)
+  std::vector<double> S, lam;          // interior eigenvectors ((p-1)^2) and eigenvalues
+  std::vector<double> T;               // u_gll = T u_fdm (n x n)
+  std::vector<double> Af, Bf;          // T^T A T, T^T B T with exact structural zeros
+  std::vector<double> Vq, Dq;          // Lagrange values / derivatives at Gauss points (q x n)
+};
+Basis1D make_basis(int p);  // throws via fail() on error
+
+// ---------------------------------------------------------------- patch classes
+// A vertex star spans, per axis, either the full range [p v - (p-1), p v + (p-1)]
+// (2p-1 nodes, "full", containing the vertex plane at local p-1) or, at the
+// Dirichlet boundary, the interior of one cell (p-1 nodes, "clipped").
+// class id = full_x + 2 full_y + 4 full_z.
+struct PatchClass {
+  int id = 0;
+  int full[3] = {0, 0, 0};
+  int dim[3] = {0, 0, 0};
+  int nd = 0, nI = 0, nG = 0;
+  int n0 = 0, n1 = 0, n2 = 0;  // level sizes of the interface ordering
+  int nlines = 0;
+  std::vector<int> gpos;        // [nG] star-local linear index of interface dof k (factor order)
+  std::vector<int> line_start, line_len;  // lines of level 1 (offsets within level 1)
+  // level-0 off-diagonal block in ELL form over rows n0..nG-1
+  int K0 = 0, nrow0 = 0;        // entries per row, rows = nG - n0
+  std::vector<int> ell_col;     // [K0 * nrow0] level-0 column or -1
+  std::vector<int> c0_ptr, c0_pos;  // per level-0 column: positions e*nrow0 + r' in the ELL block
+  std::vector<int> r0_ptr, r0_idx;  // per level-0 column: rows (>= n0, ascending) of L
+  int ld21 = 0;                 // row stride of L21 (n1 rounded up to 4)
+  int npanel = 0;
+  // value layout of one patch (in elements)
+  int64_t off_dinv0 = 0, off_ell = 0, off_lines = 0, off_l21 = 0, off_pan = 0, nval = 0;
+  std::vector<int> line_off;    // [nlines] offsets of the inverse line blocks
+  std::vector<int> pan_off;     // [npanel] offsets of the panels
+  int64_t nnzL = 0;             // structurally nonzero entries of L_Gamma
+  std::vector<uint8_t> pattern; // [nG*nG] symbolic pattern of L (row-major, lower)
+  std::vector<int> ginv;        // [nd] interface index of each star position, -1 if interior
+  std::vector<int> line_of;     // [n1] line of each level-1 row
+};
+
+std::vector<PatchClass> build_classes(int p);
+
+// ---------------------------------------------------------------- device views
+// Per-class tables on the device (concatenated over classes).
+struct ClassDev {
+  int nd, nI, nG, n0, n1, n2, nlines, K0, nrow0, ld21, npanel;
+  int dim[3], full[3];
+  int64_t off_dinv0, off_ell, off_lines, off_l21, off_pan, nval;
+  const int *gpos;       // [nG]
+  const int *line_start; // [nlines]
+  const int *line_len;   // [nlines]
+  const int *line_off;   // [nlines]
+  const int *ell_col;    // [K0*nrow0]
+  const int *c0_ptr;     // [n0+1]
+  const int *c0_pos;
+  const int *r0_ptr;     // [n0+1]
+  const int *r0_idx;
+  const int *pan_off;    // [npanel]
+  const int *ginv;       // [nd] interface index of a star position, -1 if interior
+  const int *line_of;    // [n1] line index of each level-1 row
+};
+
+}  // namespace fdm

@@ -1,0 +1,79 @@
+// Host-side declarations of the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace fdm {
+
+constexpr int PATCH_THREADS = 256;
+
+template <typename T>
+struct PatchSolveArgs {
+  Grid g;
+  const ClassDev *cls;
+  const PatchDev *patches;
+  const int *order;
+  const T *E;
+  const double *mu;
+  const T *tab;
+  const T *L;
+  T *X;
+};
+
+// basis change and relaxation
+template <typename T, typename Tin>
+void launch_restrict_fdm(const Grid &g, const Tin *r, const T *tab, T *E, cudaStream_t st);
+template <typename T, typename Tout>
+void launch_interp_fdm(const Grid &g, const PatchDev *patches, const ClassDev *cls, const T *X, const T *tab,
+                       double omega, Tout *z, cudaStream_t st);
+template <typename T>
+size_t patch_smem_bytes(int n, int maxG, int maxN1);
+template <typename T>
+void launch_patch_solve(const PatchSolveArgs<T> &a, int npatch, size_t smem, cudaStream_t st);
+
+// operators
+struct OpArgs {
+  Grid g;
+  int general;          // 0: box cells (Kronecker), 1: quadrature
+  const double *mu_box; // [ncell][3] (box)
+  const void *Gw;       // [ncell][nq][6] in the op precision (general)
+  const void *detw;     // [ncell][nq] (general mass)
+  const void *tab;      // 1D tables in the op precision
+};
+// y = A u (stiffness) or M u (mass); E is a work buffer of ncell*n^3 elements.
+template <typename T, typename Tin, typename Tout>
+void launch_operator(const OpArgs &a, bool mass, const Tin *u, Tout *y, T *E, cudaStream_t st);
+// per-cell Galerkin coarse matrices P_K^T A^K P_K (FP64), [ncell][8][8]
+void launch_coarse_cell_matrices(const OpArgs &a, double *Ac, cudaStream_t st);
+
+// coarse space
+template <typename T, typename Tin>
+void launch_coarse_restrict(const Grid &g, const Tin *r, const T *tab, const int *cfree, T *rc, T *cellbuf,
+                            cudaStream_t st);
+template <typename T>
+void launch_dense_symv(int m, const T *Ainv, const T *x, T *y, cudaStream_t st);
+template <typename T, typename Tout>
+void launch_coarse_prolong(const Grid &g, const T *xc, const T *tab, const int *cfree, Tout *z, bool accumulate,
+                           cudaStream_t st);
+
+// vectors
+constexpr int DOT_BLOCKS = 608;  // 4 x 152 SMs; fixed so reductions are deterministic
+void launch_dot(int64_t n, const double *a, const double *b, double *partial, double *out, cudaStream_t st);
+void launch_dot2(int64_t n, const double *a, const double *b, const double *c, double *partial, double *out,
+                 cudaStream_t st);  // out[0] = a.b, out[1] = a.c
+template <typename Ta, typename Tb>
+void launch_convert(int64_t n, const Ta *a, Tb *b, cudaStream_t st);
+template <typename T>
+void launch_axpby(int64_t n, T alpha, const T *x, T beta, const T *y, T *z, cudaStream_t st);  // z = a x + b y
+template <typename T>
+void launch_sub(int64_t n, const T *x, const T *y, T *z, cudaStream_t st);  // z = x - y
+template <typename T>
+void launch_add(int64_t n, const T *x, T *y, cudaStream_t st);  // y += x
+// PCG scalar/vector steps (scalars on the device)
+void launch_pcg_update_xr(int64_t n, const double *sc, const double *d, const double *q, double *x, double *r,
+                          cudaStream_t st);
+void launch_pcg_update_d(int64_t n, const double *sc, const double *z, double *d, cudaStream_t st);
+void launch_pcg_scalars(int which, double *sc, const double *dots, cudaStream_t st);
+
+}  // namespace fdm

@@ -1,0 +1,307 @@
+"""Thin ctypes binding of libfdmpc.so (C-ABI declared in include/fdmpc.h).
+
+Functions carry the C names and only marshal arguments; every step of the
+computation runs in the library's CUDA kernels.  Device vectors are passed as
+torch CUDA tensors (float64, contiguous) whose data pointers go straight to
+the library.  There is no CPU fallback: if the library cannot be loaded or no
+GPU is present the calls raise.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfdmpc.so")
+
+FDM_OK, FDM_EINVAL, FDM_ENOMEM, FDM_ENOTSPD, FDM_ENOCONV, FDM_ENAN, FDM_ETIMEOUT, FDM_ECUDA = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+FDM_PREC_FP64, FDM_PREC_FP32 = 0, 1
+FDM_PC_NONE, FDM_PC_ASM, FDM_PC_VCYCLE = 0, 1, 2
+FDM_SURR_AVERAGED, FDM_SURR_EXTERNAL = 0, 1
+(FDM_Q_NDOF, FDM_Q_OMEGA, FDM_Q_LAMBDA, FDM_Q_MU, FDM_Q_NPATCH, FDM_Q_PATCH_CLASS, FDM_Q_CLASS_INFO,
+ FDM_Q_GAMMA_ORDER, FDM_Q_FACTOR_NNZ, FDM_Q_PATTERN, FDM_Q_FACTOR, FDM_Q_BASIS, FDM_Q_FACTOR_BYTES,
+ FDM_Q_SETUP_SECONDS) = range(1, 15)
+
+
+class fdm_mesh(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("xv", C.POINTER(C.c_double)), ("yv", C.POINTER(C.c_double)), ("zv", C.POINTER(C.c_double)),
+                ("jac", C.POINTER(C.c_double))]
+
+
+class fdm_coeff(C.Structure):
+    _fields_ = [("kappa_q", C.POINTER(C.c_double))]
+
+
+class fdm_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("pc", C.c_int), ("surrogate", C.c_int), ("lanczos_steps", C.c_int),
+                ("omega", C.c_double), ("lanczos_seed", C.c_uint64), ("flexible_beta", C.c_int),
+                ("wait_timeout_s", C.c_double), ("lanczos_start", C.POINTER(C.c_double))]
+
+
+class fdm_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("rnorm0", C.c_double), ("rnorm", C.c_double),
+                ("true_rnorm", C.c_double), ("seconds", C.c_double)]
+
+
+class FdmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("fdmpc error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """Load libfdmpc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libfdmpc.so is not built; run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+    L.fdm_default_options.argtypes = [C.POINTER(fdm_options)]
+    L.fdm_setup.argtypes = [C.POINTER(fdm_mesh), C.c_int, C.POINTER(fdm_coeff), C.POINTER(fdm_options),
+                            C.POINTER(vp), vp]
+    for f in ("stiffness_apply", "mass_apply", "asm_apply", "pc_apply"):
+        getattr(L, f).argtypes = [vp, vp, vp, vp]
+    L.pcg_solve.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.POINTER(fdm_solve_info), vp]
+    L.fdm_batch_setup.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp)]
+    L.pcg_solve_batched.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.c_double, C.c_int,
+                                    C.POINTER(fdm_solve_info), vp]
+    L.fdm_batch_destroy.argtypes = [vp]
+    L.fdm_batch_destroy.restype = None
+    L.fdm_surrogate_load.argtypes = [vp, dp, vp]
+    L.fdm_query.argtypes = [vp, C.c_int, vp, C.POINTER(C.c_size_t)]
+    L.fdm_last_error.argtypes = [vp]
+    L.fdm_last_error.restype = C.c_char_p
+    L.fdm_destroy.argtypes = [vp]
+    L.fdm_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _check(rc, ctx=None):
+    if rc < 0:
+        raise FdmError(rc, load().fdm_last_error(ctx).decode())
+    return rc
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _tptr(t):
+    import torch
+    assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous(), "need a contiguous CUDA float64 tensor"
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(stream)
+
+
+# ---- C-ABI functions under their own names -------------------------------
+
+def fdm_default_options():
+    o = fdm_options()
+    _check(load().fdm_default_options(C.byref(o)))
+    return o
+
+
+def fdm_setup(mesh, p, coeff, opt, stream=None):
+    h = C.c_void_p()
+    _check(load().fdm_setup(C.byref(mesh), p, C.byref(coeff) if coeff is not None else None,
+                            C.byref(opt) if opt is not None else None, C.byref(h), _stream(stream)))
+    return h
+
+
+def stiffness_apply(ctx, u, y, stream=None):
+    _check(load().stiffness_apply(ctx, _tptr(u), _tptr(y), _stream(stream)), ctx)
+
+
+def mass_apply(ctx, f, b, stream=None):
+    _check(load().mass_apply(ctx, _tptr(f), _tptr(b), _stream(stream)), ctx)
+
+
+def asm_apply(ctx, r, z, stream=None):
+    _check(load().asm_apply(ctx, _tptr(r), _tptr(z), _stream(stream)), ctx)
+
+
+def pc_apply(ctx, r, z, stream=None):
+    _check(load().pc_apply(ctx, _tptr(r), _tptr(z), _stream(stream)), ctx)
+
+
+def pcg_solve(ctx, b, x, rtol, maxit, stream=None, raise_on_noconv=True):
+    info = fdm_solve_info()
+    rc = load().pcg_solve(ctx, _tptr(b), _tptr(x), rtol, maxit, C.byref(info), _stream(stream))
+    if rc == FDM_ENOCONV and not raise_on_noconv:
+        return info
+    _check(rc, ctx)
+    return info
+
+
+def fdm_batch_setup(ctxs):
+    arr = (C.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    h = C.c_void_p()
+    _check(load().fdm_batch_setup(len(ctxs), arr, C.byref(h)))
+    return h
+
+
+def pcg_solve_batched(batch, bs, xs, rtol, maxit, stream=None):
+    k = len(bs)
+    barr = (C.c_void_p * k)(*[b.data_ptr() for b in bs])
+    xarr = (C.c_void_p * k)(*[x.data_ptr() for x in xs])
+    infos = (fdm_solve_info * k)()
+    _check(load().pcg_solve_batched(batch, barr, xarr, rtol, maxit, infos, _stream(stream)))
+    return list(infos)
+
+
+def fdm_batch_destroy(batch):
+    load().fdm_batch_destroy(batch)
+
+
+def fdm_surrogate_load(ctx, mu, stream=None):
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    _check(load().fdm_surrogate_load(ctx, _dptr(mu), _stream(stream)), ctx)
+
+
+def fdm_query(ctx, what, out, arg=None):
+    """Copies quantity `what` into the numpy array `out` (HOST); returns bytes."""
+    if arg is not None:
+        assert out.nbytes >= 4
+        out.reshape(-1).view(np.uint8)[:4] = np.frombuffer(np.int32(arg).tobytes(), dtype=np.uint8)
+    n = C.c_size_t(out.nbytes)
+    _check(load().fdm_query(ctx, what, out.ctypes.data_as(C.c_void_p), C.byref(n)), ctx)
+    return n.value
+
+
+def fdm_last_error(ctx=None):
+    return load().fdm_last_error(ctx).decode()
+
+
+def fdm_destroy(ctx):
+    load().fdm_destroy(ctx)
+
+
+# ---- convenience wrapper ---------------------------------------------------
+
+class Context:
+    """Owns one set-up problem (a fdm_ctx) and its host inputs."""
+
+    def __init__(self, p, xv, yv, zv, jac=None, kappa=None, precision=FDM_PREC_FP32, pc=FDM_PC_VCYCLE,
+                 omega=0.0, lanczos_start=None, lanczos_steps=20, flexible_beta=-1, stream=None):
+        self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (xv, yv, zv)]
+        mesh = fdm_mesh()
+        mesh.nx, mesh.ny, mesh.nz = len(xv) - 1, len(yv) - 1, len(zv) - 1
+        mesh.xv, mesh.yv, mesh.zv = [_dptr(a) for a in self._keep]
+        coeff = fdm_coeff()
+        if jac is not None:
+            j = np.ascontiguousarray(jac, dtype=np.float64)
+            self._keep.append(j)
+            mesh.jac = _dptr(j)
+        if kappa is not None:
+            k = np.ascontiguousarray(kappa, dtype=np.float64)
+            self._keep.append(k)
+            coeff.kappa_q = _dptr(k)
+        opt = fdm_default_options()
+        opt.precision, opt.pc, opt.omega, opt.lanczos_steps = precision, pc, omega, lanczos_steps
+        opt.flexible_beta = flexible_beta
+        if lanczos_start is not None:
+            s = np.ascontiguousarray(lanczos_start, dtype=np.float64)
+            self._keep.append(s)
+            opt.lanczos_start = _dptr(s)
+        self.p = p
+        self.nx, self.ny, self.nz = mesh.nx, mesh.ny, mesh.nz
+        self.N = (mesh.nx * p + 1, mesh.ny * p + 1, mesh.nz * p + 1)
+        self.ndof = self.N[0] * self.N[1] * self.N[2]
+        self.ncell = mesh.nx * mesh.ny * mesh.nz
+        self.h = fdm_setup(mesh, p, coeff, opt, stream)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            fdm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _out(self, like):
+        import torch
+        return torch.empty(self.ndof, dtype=torch.float64, device=like.device)
+
+    def stiffness_apply(self, u, y=None):
+        y = self._out(u) if y is None else y
+        stiffness_apply(self.h, u, y)
+        return y
+
+    def mass_apply(self, f, b=None):
+        b = self._out(f) if b is None else b
+        mass_apply(self.h, f, b)
+        return b
+
+    def asm_apply(self, r, z=None):
+        z = self._out(r) if z is None else z
+        asm_apply(self.h, r, z)
+        return z
+
+    def pc_apply(self, r, z=None):
+        z = self._out(r) if z is None else z
+        pc_apply(self.h, r, z)
+        return z
+
+    def pcg_solve(self, b, x=None, rtol=1e-8, maxit=200, raise_on_noconv=True):
+        x = self._out(b) if x is None else x
+        info = pcg_solve(self.h, b, x, rtol, maxit, raise_on_noconv=raise_on_noconv)
+        return x, info
+
+    def surrogate_load(self, mu):
+        fdm_surrogate_load(self.h, mu)
+
+    def query(self, what, dtype, count, arg=None):
+        out = np.zeros(count, dtype=dtype)
+        fdm_query(self.h, what, out, arg)
+        return out
+
+    @property
+    def omega(self):
+        return float(self.query(FDM_Q_OMEGA, np.float64, 1)[0])
+
+    def class_info(self):
+        return self.query(FDM_Q_CLASS_INFO, np.int32, 64).reshape(8, 8)
+
+    def gamma_orders(self):
+        info = self.class_info()
+        flat = self.query(FDM_Q_GAMMA_ORDER, np.int32, int(info[:, 2].sum()))
+        out, off = [], 0
+        for c in range(8):
+            nG = int(info[c, 2])
+            out.append(flat[off:off + nG])
+            off += nG
+        return out
+
+    def pattern(self, cls):
+        nG = int(self.class_info()[cls, 2])
+        out = np.zeros(max(nG * nG, 4), dtype=np.uint8)
+        fdm_query(self.h, FDM_Q_PATTERN, out, cls)
+        return out[:nG * nG].reshape(nG, nG).astype(bool)
+
+    def factor_dense(self, patch):
+        cls = int(self.query(FDM_Q_PATCH_CLASS, np.int32, self.npatch)[patch])
+        nG = int(self.class_info()[cls, 2])
+        out = np.zeros(max(nG * nG, 1), dtype=np.float64)
+        fdm_query(self.h, FDM_Q_FACTOR, out, patch)
+        return out[:nG * nG].reshape(nG, nG)
+
+    @property
+    def npatch(self):
+        return int(self.query(FDM_Q_NPATCH, np.int32, 1)[0])
