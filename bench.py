@@ -1,0 +1,363 @@
+"""Benchmark: PCG solve throughput (free DoF/s to a 1e-8 relative residual).
+
+Default workload (N=1): Poisson on a 16^3 graded tensor hex mesh (per-axis
+widths U(0.5, 1.5), normalised), Q7 on GLL nodes (113^3 = 1,442,897 nodes,
+1,367,631 free dofs), f = seeded N(0,1) nodal values, b = M f; PCG with the
+hybrid V(1,1) vertex-star FDM/sparse relaxation, FP32 preconditioner inside
+FP64 PCG, rtol 1e-8 from x0 = 0.  A step is one full PCG solve.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank solves its own instance (different right-hand
+side) of the same problem: independent problems, weak scaling, no
+collective on the data path (the barrier and the max over ranks of the
+timing are the only collectives).
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "q7_graded16"
+RTOL = 1e-8
+MAXIT = 200
+CPU_SAMPLE_N = 10  # CPU-baseline sample: the same family on a 10^3 graded mesh
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _traffic_from_profile(kernel_src):
+    """Per-launch DRAM bytes of the patch-solve kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "patch_solve_q7_graded16.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_sha = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
+    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not (m_sha and m_b):
+        return None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
+    return float(m_b.group(1)) if m_sha.group(1) == sha else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nme, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nme)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _free_dofs(N):
+    return (N[0] - 2) * (N[1] - 2) * (N[2] - 2)
+
+
+def cpu_sample_problem():
+    from paper_2107_14758_gb300 import inputs
+    xv, yv, zv = inputs.graded_vertices(CPU_SAMPLE_N, 2)
+    return 7, xv, yv, zv
+
+
+def run_oracle_solve(P, b):
+    t0 = time.perf_counter()
+    x, it, _, conv = P.pcg(b, rtol=RTOL, maxit=MAXIT)
+    return time.perf_counter() - t0, it, conv
+
+
+def oracle_problem():
+    import oracle
+    from paper_2107_14758_gb300 import inputs
+    oracle.build()
+    p, xv, yv, zv = cpu_sample_problem()
+    P = oracle.Problem(p, xv, yv, zv)
+    P.setup_patches()
+    P.setup_coarse()
+    P.lanczos_omega(inputs.lanczos_start(P.ndof))
+    b = P.mass_apply(inputs.normal_rhs(P.ndof, 2))
+    return P, b
+
+
+def cpu_cores():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+SAMPLE_TEXT = ("the same problem family (graded tensor mesh, Q7, N(0,1) nodal f, PCG + V(1,1), rtol 1e-8) "
+               "on a %d^3 mesh instead of 16^3; DoF/s = free dofs / solve wall time, set-up excluded" % CPU_SAMPLE_N)
+
+
+def bench_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    P, b = oracle_problem()
+    free = _free_dofs(P.N)
+    for _ in range(args.warmup):
+        run_oracle_solve(P, b)
+    times, its = [], []
+    for _ in range(args.steps):
+        t, it, conv = run_oracle_solve(P, b)
+        times.append(t)
+        its.append(it)
+    tot = sum(times)
+    value = free * args.steps / tot
+    line = {"impl": "reference", "metric": "pcg_solve_dofs_per_s", "value": value, "unit": "DoF/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": SAMPLE_TEXT, "iterations": int(np.median(its))},
+            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": SAMPLE_TEXT},
+            "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def bench_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__ as ge
+    if rank == 0 or ws == 1:
+        ge.build()
+    if ws > 1:
+        dist.barrier()
+    from paper_2107_14758_gb300 import fdmpc, inputs
+
+    w = inputs.workload(WORKLOAD)
+    ctx = fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP32, kernel_timing=1)
+    setup_s = list(ctx.setup_seconds())
+    free = _free_dofs(ctx.N)
+    f = torch.tensor(inputs.normal_rhs(ctx.ndof, w["seed"] + 1000 * rank), device=dev)
+    b = ctx.mass_apply(f)
+    x = torch.empty_like(b)
+
+    def step():
+        return ctx.pcg_solve(b, x, rtol=RTOL, maxit=MAXIT)[1]
+
+    args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up solves
+    for _ in range(args.warmup):
+        info = step()
+    ctx.kernel_times()
+    ctx.launches()
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(dev.index)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters = []
+    for _ in range(args.steps):
+        info = step()
+        iters.append(info.iterations)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    kt = ctx.kernel_times()
+    launches = ctx.launches()
+    t_tensor = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
+    ms_max = float(t_tensor.item())
+    value = ws * free * args.steps / (ms_max * 1e-3)
+    rel = info.true_rnorm / info.rnorm0
+
+    # ---- end to end through the C-ABI with host buffers (copies timed)
+    hb = torch.empty(ctx.ndof, dtype=torch.float64, pin_memory=True)
+    hb.copy_(b.cpu())
+    hx = torch.empty(ctx.ndof, dtype=torch.float64, pin_memory=True)
+    db = torch.empty_like(b)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        db.copy_(hb, non_blocking=True)
+        fdmpc.pcg_solve(ctx.h, db, x, RTOL, MAXIT)
+        hx.copy_(x, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = torch.tensor([e2.elapsed_time(e3)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+    e2e_value = ws * free * args.steps / (float(t_e2e.item()) * 1e-3)
+
+    # ---- roofline of the dominant kernel (patch solve), FP32 factors
+    ab = ctx.algo_bytes()
+    pcount, pms = kt["patch"]
+    patch_ms = pms / max(pcount, 1)
+    peak, peak_kind = _peak_hbm()
+    achieved = ab["patch32"] / (patch_ms * 1e-3) / 1e9
+    traffic = _traffic_from_profile(os.path.join(ROOT, "paper_2107_14758_gb300", "csrc", "k_asm.cu"))
+
+    # ---- secondary numbers (same workload): pc_apply throughput and the FP64 form
+    r = torch.randn(ctx.ndof, dtype=torch.float64, device=dev)
+    z = torch.empty_like(r)
+    for _ in range(3):
+        ctx.pc_apply(r, z)
+    torch.cuda.synchronize()
+    e4 = torch.cuda.Event(enable_timing=True)
+    e5 = torch.cuda.Event(enable_timing=True)
+    e4.record(stream)
+    for _ in range(20):
+        ctx.pc_apply(r, z)
+    e5.record(stream)
+    torch.cuda.synchronize()
+    pc_ms = e4.elapsed_time(e5) / 20
+    ctx.kernel_times()
+    ctx.launches()
+    secondary = {"pc_apply_gdofs": free / (pc_ms * 1e-3) / 1e9, "pc_apply_ms": pc_ms}
+    if not args.no_fp64:
+        ctx64 = fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP64)
+        for _ in range(2):
+            ctx64.pcg_solve(b, x, rtol=RTOL, maxit=MAXIT)
+        torch.cuda.synchronize()
+        e6 = torch.cuda.Event(enable_timing=True)
+        e7 = torch.cuda.Event(enable_timing=True)
+        e6.record(stream)
+        k64 = max(2, args.steps // 2)
+        for _ in range(k64):
+            info64 = ctx64.pcg_solve(b, x, rtol=RTOL, maxit=MAXIT)[1]
+        e7.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e6.elapsed_time(e7) / k64
+        secondary["fp64_pc_solve_dofs_per_s"] = free / (ms64 * 1e-3)
+        secondary["fp64_pc_iterations"] = info64.iterations
+        secondary["mixed_over_fp64"] = (free / (ms_max * 1e-3 / args.steps)) / secondary["fp64_pc_solve_dofs_per_s"]
+        ctx64.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        P, bc = oracle_problem()
+        t, it, conv = run_oracle_solve(P, bc)
+        cpu = {"value": _free_dofs(P.N) / t, "unit": "DoF/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": SAMPLE_TEXT}
+
+    if rank == 0:
+        line = {"metric": "pcg_solve_dofs_per_s", "value": value, "unit": "DoF/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD + ": 16^3 graded hex mesh, Q7, 1,367,631 free dofs, N(0,1) nodal f, "
+                                       "FP32 V(1,1) preconditioner in FP64 PCG, rtol 1e-8",
+                           "global_batch": ws, "parallelism": "independent problems per GPU" if ws > 1 else "1 GPU",
+                           "l2": "inputs larger than L2 (%.0f MB of FP32 patch factors per solve sweep)" %
+                                 (ab["patch32"] / 1e6),
+                           "iterations": int(np.median(iters)), "true_rel_residual": rel,
+                           "setup_seconds": sum(setup_s)},
+                "clocks": clocks,
+                "e2e": {"value": e2e_value, "unit": "DoF/s", "h2d_bytes_per_step": 8 * ctx.ndof,
+                        "d2h_bytes_per_step": 8 * ctx.ndof},
+                "gpu_launches": int(launches),
+                "roofline": {"kernel": "k_patch_solve<float>", "bound": "hbm", "achieved": achieved, "peak": peak,
+                             "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                             "algorithmic_bytes_per_launch": ab["patch32"], "avg_launch_ms": patch_ms,
+                             "launches": pcount},
+                "kernel_ms_per_step": {k: v[1] / args.steps for k, v in kt.items()},
+                "secondary": secondary,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-preconditioner comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return bench_reference(args)
+    return bench_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -85,6 +85,19 @@ typedef struct {
   double wait_timeout_s; /* bound on any device-side spin wait (default 1.0) */
   const double *lanczos_start; /* HOST, optional: Lanczos start vector (ndof doubles);
                                   NULL = N(0,1) from lanczos_seed (splitmix64 + Box-Muller) */
+  int kernel_timing;  /* 1: record CUDA events around every kernel group (FDM_Q_KERNEL_TIMES) */
+  int patch_ctas_per_sm; /* resident patch-solve CTAs per SM (0 = automatic); bounds the
+                            patch factors in flight so that both solves find them in L2 */
+  int patch_threads;  /* threads per patch-solve CTA: 256, 512 or 1024 (0 = 256, or 1024 when
+                         an interface exceeds 1000 dofs) */
+  int patch_kernel;   /* 0 = automatic (= 1), 1 = one CTA per patch reading the factor
+                         directly, 2 = streamed: bulk copies into a shared-memory ring */
+  int stream_buffers; /* ring buffers of the streamed solve (0 = 4) */
+  int stream_buffer_kb; /* size of each ring buffer in KiB (0 = 16) */
+  int inject_stall;   /* test hook: the streamed solve waits on a barrier that is never
+                         completed, gives up after wait_timeout_s and reports FDM_ETIMEOUT */
+  int patch_prefetch; /* one-CTA-per-patch solve: L2 bulk prefetch of the factor, 1 = all at
+                         the start, 2 = one section ahead of use, 3 = none (0 = 3) */
 } fdm_options;
 
 /* Fills the defaults listed above. */
@@ -169,6 +182,22 @@ int fdm_surrogate_load(fdm_ctx *ctx, const double *mu_host, void *stream);
 #define FDM_Q_BASIS 12       /* double[5 (p+1)^2]: A_hat, B_hat, T, Af, Bf */
 #define FDM_Q_FACTOR_BYTES 13 /* int64[2]: bytes of the FP64 and FP32 factor value arrays */
 #define FDM_Q_SETUP_SECONDS 14 /* double[4]: symbolic, numeric factor, coarse, Lanczos seconds */
+#define FDM_Q_KERNEL_TIMES 15  /* double[2*FDM_NTIMER]: per timer (launch count, total ms) since the
+                                  last query; needs opt.kernel_timing; synchronises the device */
+#define FDM_Q_LAUNCHES 16      /* int64: kernels launched by this context since the last query */
+#define FDM_Q_ALGO_BYTES 17    /* double[4]: algorithmic bytes of one patch-solve launch (FP64, FP32),
+                                  and of one asm_apply (FP64, FP32) */
+#define FDM_Q_STATUS 18        /* int32: device status word (1 = a bounded wait ran out); reading
+                                  it clears it; synchronises the device */
+/* timers of FDM_Q_KERNEL_TIMES */
+#define FDM_T_RESTRICT 0  /* basis change to the FDM basis */
+#define FDM_T_PATCH 1     /* patch gather + condense + triangular solves + back-substitution */
+#define FDM_T_INTERP 2    /* scatter + basis change back */
+#define FDM_T_OP64 3      /* FP64 stiffness apply (2 kernels) */
+#define FDM_T_OP32 4      /* FP32 stiffness apply inside the preconditioner */
+#define FDM_T_COARSE 5    /* coarse restriction + dense solve + prolongation */
+#define FDM_T_VEC 6       /* PCG dot products and vector updates */
+#define FDM_NTIMER 7
 /* Copies the quantity `what` into out (HOST); *len is the capacity in bytes
  * on input and the size written on output. */
 int fdm_query(fdm_ctx *ctx, int what, void *out, size_t *len);

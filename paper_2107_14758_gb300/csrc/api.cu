@@ -45,7 +45,14 @@ struct fdm_ctx {
   PatchDev *d_patches = nullptr;
   int *d_order = nullptr;
   int npatch = 0, nsolve = 0;
-  int maxG = 0, maxN1 = 0;
+  int maxG = 0, maxN0 = 0, maxN1 = 0, maxN2 = 0;
+  int patch_threads = 256;
+  // streamed patch solve
+  bool stream = true;
+  int nbuf = 4, buf_bytes = 16384;
+  int *status = nullptr;
+  int *d_order_nz = nullptr;  // patches with an interface, heaviest first
+  int nsolve_nz = 0;
   int64_t nval_total = 0, nstar_total = 0;
   double *L64 = nullptr;
   float *L32 = nullptr;
@@ -64,6 +71,28 @@ struct fdm_ctx {
   double *partial = nullptr, *dots = nullptr, *sc = nullptr;
   double omega = 1.0, lmin = 0.0, lmax = 0.0;
   double t_setup[4] = {0, 0, 0, 0};
+  // instrumentation: launch counter and optional per-group CUDA-event timers
+  int64_t launches = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_tag;  // tag of each recorded (begin, end) pair
+  size_t ev_used = 0;
+  void tmark(int tag, bool begin, cudaStream_t st) {
+    if (!opt.kernel_timing) return;
+    if (begin) {
+      if (ev_used + 2 > ev_pool.size()) {
+        for (int i = 0; i < 256; ++i) {
+          cudaEvent_t e;
+          FDM_CUDA(cudaEventCreate(&e));
+          ev_pool.push_back(e);
+        }
+      }
+      ev_tag.push_back(tag);
+      FDM_CUDA(cudaEventRecord(ev_pool[ev_used], st));
+    } else {
+      FDM_CUDA(cudaEventRecord(ev_pool[ev_used + 1], st));
+      ev_used += 2;
+    }
+  }
 
   template <typename T>
   T *alloc(size_t n) {
@@ -82,6 +111,7 @@ struct fdm_ctx {
     return ptr;
   }
   ~fdm_ctx() {
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (void *ptr : allocs) cudaFree(ptr);
   }
 
@@ -130,32 +160,82 @@ void mask_dirichlet(const Grid &g, double *v, cudaStream_t st) {
   k_mask_dirichlet<<<(int)std::max<int64_t>(b, 1), 256, 0, st>>>(g, v);
 }
 
+template <typename T>
+StreamArgs<T> stream_args(fdm_ctx *c) {
+  StreamArgs<T> s;
+  s.g = c->g;
+  s.cls = c->d_cls;
+  s.patches = c->d_patches;
+  s.order = c->d_order_nz;
+  s.npatch = c->nsolve_nz;
+  s.E = c->E<T>();
+  s.L = c->L<T>();
+  s.X = c->X<T>();
+  s.maxG = c->maxG;
+  s.maxN0 = c->maxN0;
+  s.maxN1 = c->maxN1;
+  // scratch of the transposed products: slices * row length <= 4 * consumer threads
+  s.tmpcap = std::max({4 * std::max(c->patch_threads, 128), (c->maxN1 + 3) & ~3, (c->maxN2 + 3) & ~3});
+  s.nbuf = c->nbuf;
+  s.buf_bytes = c->buf_bytes;
+  s.ctas_per_sm = c->opt.patch_ctas_per_sm;
+  s.timeout_ns = (uint64_t)(std::max(c->opt.wait_timeout_s, 0.0) * 1e9);
+  s.inject_stall = c->opt.inject_stall;
+  s.status = c->status;
+  return s;
+}
+
 template <typename T, typename Tin, typename Tout>
 void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st) {
-  launch_restrict_fdm<T, Tin>(c->g, r, c->tab<T>(), c->E<T>(), st);
-  PatchSolveArgs<T> a{c->g, c->d_cls, c->d_patches, c->d_order, c->E<T>(), c->mu, c->tab<T>(), c->L<T>(), c->X<T>()};
-  launch_patch_solve<T>(a, c->nsolve, c->smem<T>(), st);
-  launch_interp_fdm<T, Tout>(c->g, c->d_patches, c->d_cls, c->X<T>(), c->tab<T>(), omega, z, st);
+  c->tmark(FDM_T_RESTRICT, true, st);
+  launch_restrict_fdm<T, Tin>(c->g, r, c->tab<T>(), c->mu, c->E<T>(), st);
+  c->tmark(FDM_T_RESTRICT, false, st);
+  c->tmark(FDM_T_PATCH, true, st);
+  if (c->stream) {
+    if (launch_patch_stream<T>(stream_args<T>(c), c->patch_threads, st) != 0)
+      fail(FDM_ECUDA, "streamed patch solve: launch configuration rejected");
+  } else {
+    PatchSolveArgs<T> a{c->g, c->d_cls, c->d_patches, c->d_order, c->E<T>(), c->mu, c->tab<T>(), c->L<T>(), c->X<T>(),
+                        patch_tmp_elems(c->maxN1, c->maxN2), c->opt.patch_prefetch > 0 ? c->opt.patch_prefetch : 3};
+    launch_patch_solve<T>(a, c->nsolve, c->smem<T>(), c->patch_threads, st);
+  }
+  c->tmark(FDM_T_PATCH, false, st);
+  c->tmark(FDM_T_INTERP, true, st);
+  InterpArgs<T> ia{c->g, c->d_patches, c->d_cls, c->X<T>(), c->E<T>(), c->mu, c->tab<T>()};
+  launch_interp_fdm<T, Tout>(ia, omega, z, st);
+  c->tmark(FDM_T_INTERP, false, st);
+  c->launches += 3;
 }
 
 template <typename T>
 void coarse_correct(fdm_ctx *c, const T *r1, T *x, cudaStream_t st);
 template <>
 void coarse_correct<double>(fdm_ctx *c, const double *r1, double *x, cudaStream_t st) {
+  c->tmark(FDM_T_COARSE, true, st);
   launch_coarse_restrict<double, double>(c->g, r1, c->tab64, c->cfree, c->rc64, c->cb64, st);
   launch_dense_symv<double>(c->nc, c->Acinv64, c->rc64, c->xc64, st);
   launch_coarse_prolong<double, double>(c->g, c->xc64, c->tab64, c->cfree, x, true, st);
+  c->tmark(FDM_T_COARSE, false, st);
+  c->launches += c->nc > 0 ? 4 : 3;
 }
 template <>
 void coarse_correct<float>(fdm_ctx *c, const float *r1, float *x, cudaStream_t st) {
+  c->tmark(FDM_T_COARSE, true, st);
   launch_coarse_restrict<float, float>(c->g, r1, c->tab32, c->cfree, c->rc32, c->cb32, st);
   launch_dense_symv<float>(c->nc, c->Acinv32, c->rc32, c->xc32, st);
   launch_coarse_prolong<float, float>(c->g, c->xc32, c->tab32, c->cfree, x, true, st);
+  c->tmark(FDM_T_COARSE, false, st);
+  c->launches += c->nc > 0 ? 4 : 3;
 }
 
+// y = A u with the FP64 operator (PCG residual) or the FP32 one (inside the preconditioner)
 template <typename T>
 void apply_op(fdm_ctx *c, const T *u, T *y, cudaStream_t st) {
+  const int tag = sizeof(T) == 4 ? FDM_T_OP32 : FDM_T_OP64;
+  c->tmark(tag, true, st);
   launch_operator<T, T, T>(c->op_args(sizeof(T) == 4), false, u, y, c->E<T>(), st);
+  c->tmark(tag, false, st);
+  c->launches += 2;
 }
 
 // hybrid multiplicative V(1,1) (Section 2.5) in precision T
@@ -170,6 +250,7 @@ void run_vcycle(fdm_ctx *c, const T *r, T *z, T *x1, T *t, T *r1, cudaStream_t s
   launch_sub<T>(n, r, t, r1, st);
   run_asm<T, T, T>(c, r1, t, c->omega, st);  // post-relaxation
   launch_axpby<T>(n, T(1), x1, T(1), t, z, st);
+  c->launches += 3;
 }
 
 void pc_apply_impl(fdm_ctx *c, const double *r, double *z, cudaStream_t st) {
@@ -177,6 +258,7 @@ void pc_apply_impl(fdm_ctx *c, const double *r, double *z, cudaStream_t st) {
   if (c->opt.pc == FDM_PC_NONE) {
     FDM_CUDA(cudaMemcpyAsync(z, r, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     mask_dirichlet(c->g, z, st);
+    c->launches += 1;
     return;
   }
   if (c->opt.precision == FDM_PREC_FP64) {
@@ -189,6 +271,7 @@ void pc_apply_impl(fdm_ctx *c, const double *r, double *z, cudaStream_t st) {
       launch_convert<double, float>(n, r, c->f_in, st);
       run_vcycle<float>(c, c->f_in, c->f_out, c->f1, c->f2, c->f3, st);
       launch_convert<float, double>(n, c->f_out, z, st);
+      c->launches += 2;
     }
   }
 }
@@ -279,15 +362,22 @@ void setup_tables(fdm_ctx *c) {
 void setup_patches(fdm_ctx *c) {
   const int p = c->p;
   c->classes = build_classes(p);
+  c->nbuf = c->opt.stream_buffers > 0 ? c->opt.stream_buffers : 4;
+  c->buf_bytes = 1024 * (c->opt.stream_buffer_kb > 0 ? c->opt.stream_buffer_kb : 16);
+  // default: one CTA per patch reading the factor directly (measured fastest on
+  // GB300 for p <= 15); the streamed ring (patch_kernel = 2) reads the factor
+  // from DRAM once but is latency-bound per chunk
+  c->stream = c->opt.patch_kernel == 2;
+  if (c->nbuf < 2 || c->nbuf > 16 || c->buf_bytes > 96 * 1024) fail(FDM_EINVAL, "stream buffers out of range");
   c->h_cls.resize(8);
   for (int id = 0; id < 8; ++id) {
     const PatchClass &C = c->classes[id];
     ClassDev &D = c->h_cls[id];
     D.nd = C.nd; D.nI = C.nI; D.nG = C.nG; D.n0 = C.n0; D.n1 = C.n1; D.n2 = C.n2;
-    D.nlines = C.nlines; D.K0 = C.K0; D.nrow0 = C.nrow0; D.ld21 = C.ld21; D.npanel = C.npanel;
+    D.nlines = C.nlines; D.K0 = C.K0; D.nrow0 = C.nrow0; D.ldr0 = C.ldr0; D.ld21 = C.ld21;
     for (int a = 0; a < 3; ++a) { D.dim[a] = C.dim[a]; D.full[a] = C.full[a]; }
     D.off_dinv0 = C.off_dinv0; D.off_ell = C.off_ell; D.off_lines = C.off_lines;
-    D.off_l21 = C.off_l21; D.off_pan = C.off_pan; D.nval = C.nval;
+    D.off_l21 = C.off_l21; D.off_z = C.off_z; D.nval = C.nval;
     D.gpos = c->upload(C.gpos);
     D.line_start = c->upload(C.line_start);
     D.line_len = c->upload(C.line_len);
@@ -297,11 +387,21 @@ void setup_patches(fdm_ctx *c) {
     D.c0_pos = c->upload(C.c0_pos);
     D.r0_ptr = c->upload(C.r0_ptr);
     D.r0_idx = c->upload(C.r0_idx);
-    D.pan_off = c->upload(C.pan_off);
+    D.zoff = c->upload(C.zoff);
     D.ginv = c->upload(C.ginv);
     D.line_of = c->upload(C.line_of);
+    D.gsrc = c->upload(C.gsrc);
+    {
+      std::vector<ChunkDev> s32 = build_schedule(C, 4, c->buf_bytes), s64 = build_schedule(C, 8, c->buf_bytes);
+      D.sched32 = c->upload(s32);
+      D.sched64 = c->upload(s64);
+      D.nsched32 = (int)s32.size();
+      D.nsched64 = (int)s64.size();
+    }
     c->maxG = std::max(c->maxG, C.nG);
+    c->maxN0 = std::max(c->maxN0, C.n0);
     c->maxN1 = std::max(c->maxN1, C.n1);
+    c->maxN2 = std::max(c->maxN2, C.n2);
   }
   c->d_cls = c->upload(c->h_cls);
   const int nvx = c->g.nx + 1, nvy = c->g.ny + 1, nvz = c->g.nz + 1;
@@ -322,7 +422,7 @@ void setup_patches(fdm_ctx *c) {
         P.voff = voff;
         P.xoff = xoff;
         voff += c->classes[cls].nval;
-        xoff += c->classes[cls].nd;
+        xoff += c->classes[cls].nG;  // the stars' interface solutions
         if (c->classes[cls].nd > 0) order.push_back(pid);
       }
   // heaviest patches first (one CTA each) for load balance
@@ -330,6 +430,13 @@ void setup_patches(fdm_ctx *c) {
     return c->classes[c->h_patches[a].cls].nval > c->classes[c->h_patches[b].cls].nval;
   });
   c->nsolve = (int)order.size();
+  std::vector<int> order_nz;
+  for (int pid : order)
+    if (c->classes[c->h_patches[pid].cls].nG > 0) order_nz.push_back(pid);
+  c->nsolve_nz = (int)order_nz.size();
+  c->d_order_nz = c->upload(order_nz);
+  c->status = c->alloc<int>(1);
+  FDM_CUDA(cudaMemset(c->status, 0, sizeof(int)));
   c->nval_total = voff;
   c->nstar_total = xoff;
   c->d_patches = c->upload(c->h_patches);
@@ -341,9 +448,16 @@ void setup_patches(fdm_ctx *c) {
   const int64_t ne = (int64_t)c->g.ncell * c->g.n * c->g.n * c->g.n;
   c->E64 = c->alloc<double>(ne);
   c->E32 = c->alloc<float>(ne);
-  c->smem64 = patch_smem_bytes<double>(c->g.n, c->maxG, c->maxN1);
-  c->smem32 = patch_smem_bytes<float>(c->g.n, c->maxG, c->maxN1);
+  c->smem64 = patch_smem_bytes<double>(c->g.n, c->maxG, c->maxN1, c->maxN2);
+  c->smem32 = patch_smem_bytes<float>(c->g.n, c->maxG, c->maxN1, c->maxN2);
+  c->patch_threads = c->opt.patch_threads > 0 ? c->opt.patch_threads : (c->maxG > 1000 ? 1024 : 256);
+  c->smem64 = patch_smem_for_occupancy<double>(c->smem64, c->opt.patch_ctas_per_sm);
+  c->smem32 = patch_smem_for_occupancy<float>(c->smem32, c->opt.patch_ctas_per_sm);
   if (c->smem64 > 200 * 1024) fail(FDM_EINVAL, "patch interface too large for shared memory");
+  if (c->stream) {
+    size_t need = std::max(stream_smem_bytes<double>(stream_args<double>(c)), stream_smem_bytes<float>(stream_args<float>(c)));
+    if (need > 220 * 1024) fail(FDM_EINVAL, "streamed patch solve needs too much shared memory; use fewer or smaller buffers");
+  }
 }
 
 // numeric factorisation of every patch (FP64 with an FP32 copy)
@@ -555,6 +669,13 @@ int fdm_default_options(fdm_options *opt) {
   opt->flexible_beta = -1;
   opt->wait_timeout_s = 1.0;
   opt->lanczos_start = nullptr;
+  opt->kernel_timing = 0;
+  opt->patch_ctas_per_sm = 0;
+  opt->patch_threads = 0;
+  opt->patch_kernel = 0;
+  opt->stream_buffers = 0;
+  opt->stream_buffer_kb = 0;
+  opt->inject_stall = 0;
   return FDM_OK;
 }
 
@@ -622,7 +743,7 @@ int fdm_setup(const fdm_mesh *mesh, int p, const fdm_coeff *coeff, const fdm_opt
 int stiffness_apply(fdm_ctx *c, const double *u, double *y, void *stream) {
   if (!c || !u || !y) return FDM_EINVAL;
   try {
-    launch_operator<double, double, double>(c->op_args(false), false, u, y, c->E64, (cudaStream_t)stream);
+    apply_op<double>(c, u, y, (cudaStream_t)stream);
     FDM_CUDA(cudaGetLastError());
   } catch (const Error &e) { return handle(c, e); }
   return FDM_OK;
@@ -632,6 +753,7 @@ int mass_apply(fdm_ctx *c, const double *f, double *b, void *stream) {
   if (!c || !f || !b) return FDM_EINVAL;
   try {
     launch_operator<double, double, double>(c->op_args(false), true, f, b, c->E64, (cudaStream_t)stream);
+    c->launches += 2;
     FDM_CUDA(cudaGetLastError());
   } catch (const Error &e) { return handle(c, e); }
   return FDM_OK;
@@ -675,6 +797,7 @@ int pcg_solve(fdm_ctx *c, const double *b, double *x, double rtol, int maxit, fd
     mask_dirichlet(c->g, c->r, st);
     double h[2];
     launch_dot(n, c->r, c->r, c->partial, c->dots, st);
+    c->launches += 3;
     FDM_CUDA(cudaMemcpyAsync(h, c->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
     FDM_CUDA(cudaStreamSynchronize(st));
     const double nb = std::sqrt(h[0]);
@@ -686,13 +809,17 @@ int pcg_solve(fdm_ctx *c, const double *b, double *x, double rtol, int maxit, fd
       launch_dot(n, c->r, z, c->partial, c->dots, st);
       launch_pcg_scalars(2, c->sc, c->dots, st);
       FDM_CUDA(cudaMemcpyAsync(c->d, z, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      c->launches += 6;
       while (it < maxit) {
-        launch_operator<double, double, double>(c->op_args(false), false, c->d, c->q, c->E64, st);
+        apply_op<double>(c, c->d, c->q, st);
+        c->tmark(FDM_T_VEC, true, st);
         launch_dot(n, c->d, c->q, c->partial, c->dots, st);
         launch_pcg_scalars(0, c->sc, c->dots, st);
         launch_pcg_update_xr(n, c->sc, c->d, c->q, x, c->r, st);
         ++it;
         launch_dot(n, c->r, c->r, c->partial, c->dots + 2, st);
+        c->tmark(FDM_T_VEC, false, st);
+        c->launches += 6;
         FDM_CUDA(cudaMemcpyAsync(h, c->dots + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
         FDM_CUDA(cudaStreamSynchronize(st));
         nr = std::sqrt(h[0]);
@@ -700,9 +827,12 @@ int pcg_solve(fdm_ctx *c, const double *b, double *x, double rtol, int maxit, fd
         if (nr <= rtol * nb) { conv = 1; break; }
         std::swap(z, zold);
         pc_apply_impl(c, c->r, z, st);
+        c->tmark(FDM_T_VEC, true, st);
         launch_dot2(n, c->r, z, zold, c->partial, c->dots, st);
         launch_pcg_scalars(1, c->sc, c->dots, st);
         launch_pcg_update_d(n, c->sc, z, c->d, st);
+        c->tmark(FDM_T_VEC, false, st);
+        c->launches += 4;
       }
     }
     FDM_CUDA(cudaEventRecord(e1, st));
@@ -713,6 +843,12 @@ int pcg_solve(fdm_ctx *c, const double *b, double *x, double rtol, int maxit, fd
     cudaEventDestroy(e1);
     FDM_CUDA(cudaMemcpy(hsc, c->sc, sizeof hsc, cudaMemcpyDeviceToHost));
     if (hsc[8] != 0.0) bad = 1;
+    int hstat = 0;
+    FDM_CUDA(cudaMemcpy(&hstat, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (hstat) {
+      FDM_CUDA(cudaMemset(c->status, 0, sizeof(int)));
+      fail(FDM_ETIMEOUT, "a bounded device-side wait of the patch solve ran out");
+    }
     if (info) {
       info->iterations = it;
       info->converged = conv;
@@ -723,6 +859,7 @@ int pcg_solve(fdm_ctx *c, const double *b, double *x, double rtol, int maxit, fd
       launch_operator<double, double, double>(c->op_args(false), false, x, c->q, c->E64, st);
       launch_sub<double>(n, b, c->q, c->v1, st);
       mask_dirichlet(c->g, c->v1, st);
+      c->launches += 6;
       launch_dot(n, c->v1, c->v1, c->partial, c->dots, st);
       FDM_CUDA(cudaMemcpyAsync(h, c->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
       FDM_CUDA(cudaStreamSynchronize(st));
@@ -864,6 +1001,53 @@ int fdm_query(fdm_ctx *c, int what, void *out, size_t *len) {
         break;
       }
       case FDM_Q_SETUP_SECONDS: put(c->t_setup, sizeof c->t_setup); break;
+      case FDM_Q_STATUS: {
+        int v = 0;
+        FDM_CUDA(cudaMemcpy(&v, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+        FDM_CUDA(cudaMemset(c->status, 0, sizeof(int)));
+        put(&v, sizeof v);
+        break;
+      }
+      case FDM_Q_KERNEL_TIMES: {
+        std::vector<double> h(2 * FDM_NTIMER, 0.0);
+        if (c->ev_used > 0) FDM_CUDA(cudaEventSynchronize(c->ev_pool[c->ev_used - 1]));
+        for (size_t i = 0; i < c->ev_used / 2; ++i) {
+          float ms = 0.f;
+          FDM_CUDA(cudaEventElapsedTime(&ms, c->ev_pool[2 * i], c->ev_pool[2 * i + 1]));
+          h[2 * c->ev_tag[i]] += 1.0;
+          h[2 * c->ev_tag[i] + 1] += ms;
+        }
+        c->ev_used = 0;
+        c->ev_tag.clear();
+        put(h.data(), h.size() * sizeof(double));
+        break;
+      }
+      case FDM_Q_LAUNCHES: {
+        int64_t v = c->launches;
+        c->launches = 0;
+        put(&v, sizeof v);
+        break;
+      }
+      case FDM_Q_ALGO_BYTES: {
+        // one patch-solve launch reads every structurally nonzero entry of every
+        // L_Gamma once, reads the cell-local FDM residual once and writes every
+        // star solution once; one asm_apply adds the FP64 input and output vectors
+        // and the 3 surrogate coefficients per cell.
+        double nnz = 0.0, nd = 0.0;
+        for (int i = 0; i < c->npatch; ++i) {
+          nnz += (double)c->classes[c->h_patches[i].cls].nnzL;
+          nd += (double)c->classes[c->h_patches[i].cls].nd;
+        }
+        double ne = (double)c->g.ncell * c->g.n * c->g.n * c->g.n;
+        double v[4];
+        for (int s = 0; s < 2; ++s) {
+          double w = s == 0 ? 8.0 : 4.0;
+          v[s] = w * (nnz + ne + nd);
+          v[2 + s] = v[s] + 16.0 * (double)c->g.ndof + 24.0 * c->g.ncell;
+        }
+        put(v, sizeof v);
+        break;
+      }
       default: fail(FDM_EINVAL, "fdm_query: unknown quantity");
     }
   } catch (const Error &e) { return handle(c, e); }

@@ -11,7 +11,7 @@
 namespace fdm {
 
 constexpr int PMAX = 31;
-constexpr int PANEL = 32;  // panel width of the dense top level of L_Gamma
+constexpr int PANEL = 32;  // tile width of the dense set-up factorisation
 
 // ---------------------------------------------------------------- errors
 struct Error {
@@ -39,6 +39,15 @@ struct Basis1D {
 };
 Basis1D make_basis(int p);  // throws via fail() on error
 
+// one bulk copy of the streamed patch solve: kind | first << 8 | last << 9,
+// item range [a0, a1) (rows, lines or ELL slices), byte count, element offset
+enum { CK_DINV = 0, CK_ELL_F = 1, CK_LINES_F = 2, CK_L21_F = 3, CK_Z_F = 4, CK_Z_B = 5, CK_L21_B = 6,
+       CK_LINES_B = 7, CK_ELL_B = 8 };
+struct ChunkDev {
+  int kind, a0, a1, bytes;
+  int64_t off;
+};
+
 // ---------------------------------------------------------------- patch classes
 // A vertex star spans, per axis, either the full range [p v - (p-1), p v + (p-1)]
 // (2p-1 nodes, "full", containing the vertex plane at local p-1) or, at the
@@ -55,19 +64,20 @@ struct PatchClass {
   std::vector<int> line_start, line_len;  // lines of level 1 (offsets within level 1)
   // level-0 off-diagonal block in ELL form over rows n0..nG-1
   int K0 = 0, nrow0 = 0;        // entries per row, rows = nG - n0
-  std::vector<int> ell_col;     // [K0 * nrow0] level-0 column or -1
-  std::vector<int> c0_ptr, c0_pos;  // per level-0 column: positions e*nrow0 + r' in the ELL block
+  int ldr0 = 0;                 // ELL slice stride (nrow0 rounded up to 4: 16-byte aligned slices)
+  std::vector<int> ell_col;     // [K0 * ldr0] level-0 column or -1
+  std::vector<int> c0_ptr, c0_pos;  // per level-0 column: positions e*ldr0 + r in the ELL block
   std::vector<int> r0_ptr, r0_idx;  // per level-0 column: rows (>= n0, ascending) of L
   int ld21 = 0;                 // row stride of L21 (n1 rounded up to 4)
-  int npanel = 0;
   // value layout of one patch (in elements)
-  int64_t off_dinv0 = 0, off_ell = 0, off_lines = 0, off_l21 = 0, off_pan = 0, nval = 0;
+  int64_t off_dinv0 = 0, off_ell = 0, off_lines = 0, off_l21 = 0, off_z = 0, nval = 0;
   std::vector<int> line_off;    // [nlines] offsets of the inverse line blocks
-  std::vector<int> pan_off;     // [npanel] offsets of the panels
+  std::vector<int> zoff;        // [n2+1] row offsets of Z = L_top^{-1} (rows padded to 4)
   int64_t nnzL = 0;             // structurally nonzero entries of L_Gamma
   std::vector<uint8_t> pattern; // [nG*nG] symbolic pattern of L (row-major, lower)
   std::vector<int> ginv;        // [nd] interface index of each star position, -1 if interior
   std::vector<int> line_of;     // [n1] line of each level-1 row
+  std::vector<int> gsrc;        // [8*nG] cells containing each interface dof (slot << 16 | local)
 };
 
 std::vector<PatchClass> build_classes(int p);
@@ -75,21 +85,26 @@ std::vector<PatchClass> build_classes(int p);
 // ---------------------------------------------------------------- device views
 // Per-class tables on the device (concatenated over classes).
 struct ClassDev {
-  int nd, nI, nG, n0, n1, n2, nlines, K0, nrow0, ld21, npanel;
+  int nd, nI, nG, n0, n1, n2, nlines, K0, nrow0, ld21;
   int dim[3], full[3];
-  int64_t off_dinv0, off_ell, off_lines, off_l21, off_pan, nval;
+  int64_t off_dinv0, off_ell, off_lines, off_l21, off_z, nval;
   const int *gpos;       // [nG]
   const int *line_start; // [nlines]
   const int *line_len;   // [nlines]
   const int *line_off;   // [nlines]
-  const int *ell_col;    // [K0*nrow0]
+  int ldr0;              // ELL slice stride
+  const int *ell_col;    // [K0*ldr0]
   const int *c0_ptr;     // [n0+1]
   const int *c0_pos;
   const int *r0_ptr;     // [n0+1]
   const int *r0_idx;
-  const int *pan_off;    // [npanel]
+  const int *zoff;       // [n2+1]
   const int *ginv;       // [nd] interface index of a star position, -1 if interior
   const int *line_of;    // [n1] line index of each level-1 row
+  const int *gsrc;       // [8*nG] (star cell slot << 16 | cell-local index), -1 terminated
+  const ChunkDev *sched32, *sched64;  // streamed-solve schedules (FP32 / FP64 values)
+  int nsched32, nsched64;
 };
+std::vector<ChunkDev> build_schedule(const struct PatchClass &C, int elem_bytes, int cap_bytes);
 
 }  // namespace fdm

@@ -1,47 +1,64 @@
-// Additive vertex-star relaxation kernels (Sections 2.4-2.6 of the paper):
-//   restrict: per cell, E_K = (T^T (x) T^T (x) T^T)(W_K r_K)  (FDM-basis residual)
-//   patch:    per vertex star, gather + Schur condensation + sparse Cholesky
-//             forward/backward solves + interior back-substitution
-//   interp:   per cell, sum of the star solutions covering each node (fixed
-//             order), z_K = (T (x) T (x) T) z_fdm, omega scaling, owner write.
+// Additive vertex-star relaxation kernels (Sections 2.4-2.6 of the paper).
+//
+// One sweep z = omega sum_j R_j^T A_j^{-1} R_j r runs as three kernels:
+//   restrict: per cell, E_K = (T^T (x) T^T (x) T^T)(W_K r_K) (the FDM-basis
+//             residual, W = 1/multiplicity), then the cell's share of the
+//             Schur condensation g_G = r_G - A_GI A_II^{-1} r_I (eq:LDLT): every
+//             face node f of K gets E_K(f) - sum_i A_fi E_K(i) / A_ii over the
+//             interior line through f.  A_II is diagonal in the FDM basis and the
+//             coupling of f to that line is mu_a Af[f][i] Bf Bf, so this is a
+//             cell-local, patch-independent quantity.
+//   patch:    per vertex star, gather of the condensed interface residual (sum
+//             over the star's cells), forward and backward solves with the
+//             sparse Cholesky factor of the interface Schur complement; writes
+//             the interface solution x_G only.
+//   interp:   per cell, the additive sum over the 8 stars of the cell's
+//             vertices: interface nodes directly from the stars' x_G; interior
+//             nodes by the back-substitution x_I = A_II^{-1}(r_I - A_IG x_G)
+//             summed over the stars, which needs only the summed face values
+//             (the 4 stars containing a face node are exactly the stars whose
+//             back-substitution uses that face):
+//               z(m) = (8 r(m) - sum_faces A_mf z(f)) / A_mm;
+//             then z_K = (T (x) T (x) T) z_fdm, omega, owner write.
 #include "device.cuh"
 #include "kernels.h"
 
 namespace fdm {
 
-// ------------------------------------------------------------------ helpers
 template <typename T>
-__device__ __forceinline__ void contract_axis(const T *__restrict__ in, T *__restrict__ out,
-                                              const T *__restrict__ M, bool transpose, int axis, int n,
-                                              int tid, int nt) {
-  // out[.., i, ..] = sum_m M'[i][m] in[.., m, ..] along `axis`, with
-  // M' = M (transpose = false) or M^T (transpose = true); M row-major n x n.
-  const int n3 = n * n * n;
-  const int stride = axis == 0 ? 1 : (axis == 1 ? n : n * n);
-  for (int idx = tid; idx < n3; idx += nt) {
-    int i = (idx / stride) % n;
-    int base = idx - i * stride;
-    T acc = 0;
-    if (transpose) {
-      for (int m = 0; m < n; ++m) acc += M[m * n + i] * in[base + m * stride];
-    } else {
-      for (int m = 0; m < n; ++m) acc += M[i * n + m] * in[base + m * stride];
-    }
-    out[idx] = acc;
-  }
+__device__ __forceinline__ T interior_diag(const T *sAf, const T *sBf, const T *mu, int n, int i, int j, int k) {
+  T ai = sAf[i * n + i], aj = sAf[j * n + j], ak = sAf[k * n + k];
+  T bi = sBf[i * n + i], bj = sBf[j * n + j], bk = sBf[k * n + k];
+  return mu[0] * ai * bj * bk + mu[1] * bi * aj * bk + mu[2] * bi * bj * ak;
+}
+
+// face coupling A(f, m) of a face node f (local lf along axis ax) to the
+// interior node m = l (same tangential coordinates) of one cell
+template <typename T>
+__device__ __forceinline__ T face_coupling(const T *sAf, const T *sBf, const T *mu, int n, int ax, int lf,
+                                           const int l[3]) {
+  const int b1 = ax == 0 ? 1 : 0, b2 = ax == 2 ? 1 : 2;
+  return mu[ax] * sAf[lf * n + l[ax]] * sBf[l[b1] * n + l[b1]] * sBf[l[b2] * n + l[b2]];
 }
 
 // ------------------------------------------------------------------ restrict
 template <typename T, typename Tin>
 __global__ void __launch_bounds__(256) k_restrict_fdm(Grid g, const Tin *__restrict__ r, const T *__restrict__ tab,
-                                                      T *__restrict__ E) {
+                                                      const double *__restrict__ mug, T *__restrict__ E) {
   extern __shared__ unsigned char smem_[];
   T *sT = reinterpret_cast<T *>(smem_);
   const int n = g.n, p = g.p, n3 = n * n * n;
-  T *b0 = sT + n * n, *b1 = b0 + n3;
+  T *sAf = sT + n * n, *sBf = sAf + n * n;
+  T *b0 = sBf + n * n, *b1 = b0 + n3;
+  __shared__ T mu[3];
   const int cell = blockIdx.x;
   const int cx = cell % g.nx, cy = (cell / g.nx) % g.ny, cz = cell / (g.nx * g.ny);
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x) sT[i] = tab[tab_off(TAB_T, n) + i];
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    sT[i] = tab[tab_off(TAB_T, n) + i];
+    sAf[i] = tab[tab_off(TAB_AF, n) + i];
+    sBf[i] = tab[tab_off(TAB_BF, n) + i];
+  }
+  if (threadIdx.x < 3) mu[threadIdx.x] = T(mug[3 * cell + threadIdx.x]);
   for (int idx = threadIdx.x; idx < n3; idx += blockDim.x) {
     int i = idx % n, j = (idx / n) % n, k = idx / (n * n);
     int gx = cx * p + i, gy = cy * p + j, gz = cz * p + k;
@@ -52,63 +69,82 @@ __global__ void __launch_bounds__(256) k_restrict_fdm(Grid g, const Tin *__restr
     b0[idx] = dir ? T(0) : T(r[gidx(g, gx, gy, gz)]) / T(mult);
   }
   __syncthreads();
-  contract_axis(b0, b1, sT, true, 0, n, threadIdx.x, blockDim.x);
+  contract(b0, b1, sT, true, 0, n, T(1), false);
   __syncthreads();
-  contract_axis(b1, b0, sT, true, 1, n, threadIdx.x, blockDim.x);
+  contract(b1, b0, sT, true, 1, n, T(1), false);
   __syncthreads();
-  contract_axis(b0, b1, sT, true, 2, n, threadIdx.x, blockDim.x);
+  contract(b0, b1, sT, true, 2, n, T(1), false);
+  __syncthreads();
+  // 1/A_ii of the interior nodes, once per node (b0 is free now)
+  for (int idx = threadIdx.x; idx < n3; idx += blockDim.x) {
+    int l[3] = {idx % n, (idx / n) % n, idx / (n * n)};
+    bool in = l[0] > 0 && l[0] < p && l[1] > 0 && l[1] < p && l[2] > 0 && l[2] < p;
+    b0[idx] = in ? T(1) / interior_diag(sAf, sBf, mu, n, l[0], l[1], l[2]) : T(0);
+  }
   __syncthreads();
   T *out = E + (int64_t)cell * n3;
-  for (int idx = threadIdx.x; idx < n3; idx += blockDim.x) out[idx] = b1[idx];
+  for (int idx = threadIdx.x; idx < n3; idx += blockDim.x) {
+    int l[3] = {idx % n, (idx / n) % n, idx / (n * n)};
+    int nb = 0, ax = -1;
+    for (int a = 0; a < 3; ++a)
+      if (l[a] == 0 || l[a] == p) { ++nb; ax = a; }
+    T v = b1[idx];
+    if (nb == 1) {  // face node: subtract A_fI A_II^{-1} E_I along the interior line
+      const int lf = l[ax], stride = ax == 0 ? 1 : (ax == 1 ? n : n * n);
+      const int b1x = ax == 0 ? 1 : 0, b2x = ax == 2 ? 1 : 2;
+      const T tang = mu[ax] * sBf[l[b1x] * n + l[b1x]] * sBf[l[b2x] * n + l[b2x]];
+      T s = 0;
+      for (int ii = 1; ii < p; ++ii) {
+        const int m = idx + (ii - lf) * stride;
+        s += sAf[lf * n + ii] * b1[m] * b0[m];
+      }
+      v -= tang * s;
+    }
+    out[idx] = v;
+  }
 }
 
 // ------------------------------------------------------------------ patch solve
-// cell and cell-local index of star coordinate t along one axis for a side
-__device__ __forceinline__ bool star_local(int full, int p, int t, int side, int &loc) {
-  const int c = p - 1;
-  if (!full) {
-    if (side != 0) return false;
-    loc = t + 1;
-    return true;
-  }
-  if (side == 0) {
-    if (t > c) return false;
-    loc = t + 1;
-  } else {
-    if (t < c) return false;
-    loc = t - c;
-  }
-  return true;
+// four consecutive elements with 128-bit loads (16-byte aligned address)
+template <typename T> struct V4 { T x, y, z, w; };
+__device__ __forceinline__ V4<float> load4(const float *p) {
+  float4 v = *reinterpret_cast<const float4 *>(p);
+  return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ V4<double> load4(const double *p) {
+  double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+  return {a.x, a.y, b.x, b.y};
 }
 
-template <typename T>
-__device__ __forceinline__ T interior_diag(const T *sAf, const T *sBf, const T *mu, int n, int i, int j, int k) {
-  T ai = sAf[i * n + i], aj = sAf[j * n + j], ak = sAf[k * n + k];
-  T bi = sBf[i * n + i], bj = sBf[j * n + j], bk = sBf[k * n + k];
-  return mu[0] * ai * bj * bk + mu[1] * bi * aj * bk + mu[2] * bi * bj * ak;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(PATCH_THREADS) k_patch_solve(PatchSolveArgs<T> a) {
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_patch_solve(PatchSolveArgs<T> a) {
   extern __shared__ unsigned char smem_[];
-  constexpr int NT = PATCH_THREADS, NW = NT / 32;
+  constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const PatchDev P = a.patches[a.order[blockIdx.x]];
   const ClassDev &C = a.cls[P.cls];
   const Grid &g = a.g;
-  const int p = g.p, n = g.n, n3 = n * n * n, c = p - 1;
+  const int n = g.n, n3 = n * n * n;
   const int nG = C.nG, n0 = C.n0, n1 = C.n1, n2 = C.n2;
-  const int dim0 = C.dim[0], dim1 = C.dim[1];
-  T *sAf = reinterpret_cast<T *>(smem_);
-  T *sBf = sAf + n * n;
-  T *sMu = sBf + n * n;   // [8][3]
-  int *sCell = reinterpret_cast<int *>(sMu + 24);  // [8]
-  T *gv = reinterpret_cast<T *>(sCell + 8);
-  T *yv = gv + nG, *xv = yv + nG, *tmp = xv + nG;  // tmp: max(n1, NW*32)
-  for (int i = tid; i < n * n; i += NT) {
-    sAf[i] = a.tab[tab_off(TAB_AF, n) + i];
-    sBf[i] = a.tab[tab_off(TAB_BF, n) + i];
-  }
+  __shared__ int sCell[8];
+  T *gv = reinterpret_cast<T *>(smem_);
+  T *yv = gv + nG, *xv = yv + nG, *tmp = xv + nG;  // tmp: a.tmpcap elements
+  const T *Lv = a.L + P.voff;
+  // bring the factor into L2 a section ahead of its use (not all at once, so
+  // that the sections are still resident when the backward solve re-reads them)
+  auto prefetch_l2 = [&](int64_t e0, int64_t e1) {
+    if (tid != 0 || a.prefetch == 0) return;
+    const char *src = reinterpret_cast<const char *>(Lv + e0);
+    const int64_t bytes = (e1 - e0) * (int64_t)sizeof(T);
+    for (int64_t off = 0; off < bytes; off += 32768) {
+      uint32_t chunk = (uint32_t)(bytes - off < 32768 ? bytes - off : 32768);
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src + off), "r"(chunk) : "memory");
+    }
+  };
+  if (a.prefetch == 1) prefetch_l2(0, C.nval);  // whole factor at the start
+  else if (a.prefetch == 2) prefetch_l2(0, C.off_l21);  // level 0 and lines; L21 and Z follow later
+  // g, y, x and tmp start at zero: zero-padded factor columns multiply finite values only
+  for (int i = tid; i < 3 * nG + a.tmpcap; i += NT) gv[i] = T(0);
   if (tid < 8) {
     int s[3] = {tid & 1, (tid >> 1) & 1, tid >> 2};
     int ncl[3] = {g.nx, g.ny, g.nz};
@@ -118,69 +154,39 @@ __global__ void __launch_bounds__(PATCH_THREADS) k_patch_solve(PatchSolveArgs<T>
       if (!C.full[ax] && s[ax]) ok = false;
       cc[ax] = star_cell_along(C.full[ax], P.v[ax], ncl[ax], s[ax]);
     }
-    int cell = ok ? cc[0] + g.nx * (cc[1] + g.ny * cc[2]) : -1;
-    sCell[tid] = cell;
-    for (int q = 0; q < 3; ++q) sMu[tid * 3 + q] = ok ? T(a.mu[3 * cell + q]) : T(0);
+    sCell[tid] = ok ? cc[0] + g.nx * (cc[1] + g.ny * cc[2]) : -1;
   }
   __syncthreads();
-  const T *E = a.E;
-  const T *Lv = a.L + P.voff;
 
-  // ---- gather the FDM residual on the interface and condense the interior
+  // ---- gather the condensed FDM residual on the interface (fixed cell order)
+  const T *E = a.E;
   for (int k = tid; k < nG; k += NT) {
-    int pos = C.gpos[k];
-    int t[3] = {pos % dim0, (pos / dim0) % dim1, pos / (dim0 * dim1)};
+    const int *src = C.gsrc + 8 * k;
     T r = 0;
-    for (int sd = 0; sd < 8; ++sd) {
-      int s[3] = {sd & 1, (sd >> 1) & 1, sd >> 2};
-      int l[3];
-      bool ok = sCell[sd] >= 0;
-      for (int ax = 0; ax < 3 && ok; ++ax) ok = star_local(C.full[ax], p, t[ax], s[ax], l[ax]);
-      if (ok) r += E[(int64_t)sCell[sd] * n3 + l[0] + n * (l[1] + n * l[2])];
-    }
-    int nc = 0, an = -1;
-    for (int ax = 0; ax < 3; ++ax)
-      if (C.full[ax] && t[ax] == c) { ++nc; an = ax; }
-    if (nc == 1) {  // face dof with normal an: A_GI A_II^{-1} r_I from both cells
-      for (int s = 0; s < 2; ++s) {
-        int sd = 0, l[3];
-        for (int ax = 0; ax < 3; ++ax) {
-          int side = ax == an ? s : ((C.full[ax] && t[ax] > c) ? 1 : 0);
-          sd |= side << ax;
-          if (ax != an) star_local(C.full[ax], p, t[ax], side, l[ax]);
-        }
-        const T *mu = sMu + 3 * sd;
-        const T *Ek = E + (int64_t)sCell[sd] * n3;
-        int lf = s == 0 ? p : 0;
-        int b1 = an == 0 ? 1 : 0, b2 = an == 2 ? 1 : 2;
-        T tang = sBf[l[b1] * n + l[b1]] * sBf[l[b2] * n + l[b2]];
-        for (int ii = 1; ii < p; ++ii) {
-          l[an] = ii;
-          T coef = mu[an] * sAf[lf * n + ii] * tang;
-          T D = interior_diag(sAf, sBf, mu, n, l[0], l[1], l[2]);
-          r -= coef * Ek[l[0] + n * (l[1] + n * l[2])] / D;
-        }
-      }
+    for (int e = 0; e < 8; ++e) {
+      int code = src[e];
+      if (code < 0) break;
+      r += E[(int64_t)sCell[code >> 16] * n3 + (code & 0xffff)];
     }
     gv[k] = r;
   }
   __syncthreads();
 
-  // ---- forward solve L y = g
+  if (a.prefetch == 2) prefetch_l2(C.off_l21, C.nval);  // L21 and Z, needed after level 0 and the lines
+  // ---- forward solve L y = g (level 0 diagonal, level-1 lines, dense top block)
   const T *dinv0 = Lv + C.off_dinv0;
   const T *ell = Lv + C.off_ell;
   for (int j = tid; j < n0; j += NT) yv[j] = gv[j] * dinv0[j];
-  __syncthreads();
-  for (int r = tid; r < C.nrow0; r += NT) {
+  for (int r = tid; r < C.nrow0; r += NT) {  // g_{>0} -= L_{>0,0} y_0, y_0 formed on the fly
     T acc = 0;
     for (int e = 0; e < C.K0; ++e) {
-      int col = C.ell_col[e * C.nrow0 + r];
-      if (col >= 0) acc += ell[e * C.nrow0 + r] * yv[col];
+      int col = C.ell_col[e * C.ldr0 + r];
+      if (col >= 0) acc += ell[e * C.ldr0 + r] * (gv[col] * dinv0[col]);
     }
     gv[n0 + r] -= acc;
   }
   __syncthreads();
-  for (int i = tid; i < n1; i += NT) {
+  for (int i = tid; i < n1; i += NT) {  // y_1 = L_11^{-1} g_1, line by line
     int b = C.line_of[i], s0 = C.line_start[b], w = C.line_len[b];
     const T *Li = Lv + C.off_lines + C.line_off[b] + (int64_t)(i - s0) * w;
     T acc = 0;
@@ -190,63 +196,90 @@ __global__ void __launch_bounds__(PATCH_THREADS) k_patch_solve(PatchSolveArgs<T>
   __syncthreads();
   if (n2 > 0) {
     const T *L21 = Lv + C.off_l21;
-    for (int r = warp; r < n2; r += NW) {
-      const T *row = L21 + (int64_t)r * C.ld21;
-      T acc = 0;
-      for (int cc = lane; cc < n1; cc += 32) acc += row[cc] * yv[n0 + cc];
-      acc = warp_sum(acc);
-      if (lane == 0) gv[n0 + n1 + r] -= acc;
-    }
-    __syncthreads();
-    for (int q = 0; q < C.npanel; ++q) {
-      const int base = n0 + n1 + q * PANEL, w = min(PANEL, n2 - q * PANEL), rows = n2 - q * PANEL;
-      const T *pan = Lv + C.off_pan + C.pan_off[q];
-      for (int i = tid; i < w; i += NT) {
+    const T *Z = Lv + C.off_z;
+    const int base = n0 + n1;
+    if (n1 > 0) {  // g_2 -= L21 y_1: one warp per row, 128-bit loads
+      const int ng = C.ld21 / 4;
+      for (int r = warp; r < n2; r += NW) {
+        const T *row = L21 + (int64_t)r * C.ld21;
         T acc = 0;
-        for (int cc = 0; cc <= i; ++cc) acc += pan[i * PANEL + cc] * gv[base + cc];
-        yv[base + i] = acc;
-      }
-      __syncthreads();
-      for (int r = w + warp; r < rows; r += NW) {
-        T v = lane < w ? pan[(int64_t)r * PANEL + lane] * yv[base + lane] : T(0);
-        v = warp_sum(v);
-        if (lane == 0) gv[base + r] -= v;
+        for (int q4 = lane; q4 < ng; q4 += 32) {
+          V4<T> v = load4(row + 4 * q4);
+          const T *yy = yv + n0 + 4 * q4;  // padding columns of L21 are zero, yv is finite there
+          acc += v.x * yy[0] + v.y * yy[1] + v.z * yy[2] + v.w * yy[3];
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) gv[base + r] -= acc;
       }
       __syncthreads();
     }
-    // ---- backward solve L^T x = y, top level
-    for (int q = C.npanel - 1; q >= 0; --q) {
-      const int base = n0 + n1 + q * PANEL, w = min(PANEL, n2 - q * PANEL), rows = n2 - q * PANEL;
-      const T *pan = Lv + C.off_pan + C.pan_off[q];
+    // y_2 = Z g_2 with Z = L_top^{-1}: one warp per row (rows zero-padded to 4)
+    for (int r = warp; r < n2; r += NW) {
+      const T *row = Z + C.zoff[r];
+      const int ng = (C.zoff[r + 1] - C.zoff[r]) / 4;
       T acc = 0;
-      for (int r = w + warp; r < rows; r += NW) acc += pan[(int64_t)r * PANEL + lane] * xv[base + r];
-      tmp[warp * 32 + lane] = acc;
-      __syncthreads();
-      if (tid < w) {
-        T s = 0;
-        for (int ww = 0; ww < NW; ++ww) s += tmp[ww * 32 + tid];
-        tmp[NW * 32 + tid] = yv[base + tid] - s;
+      for (int q4 = lane; q4 < ng; q4 += 32) {
+        V4<T> v = load4(row + 4 * q4);
+        const T *gg = gv + base + 4 * q4;
+        acc += v.x * gg[0] + v.y * gg[1] + v.z * gg[2] + v.w * gg[3];
       }
-      __syncthreads();
-      if (tid < w) {
-        T s = 0;
-        for (int cc = tid; cc < w; ++cc) s += pan[cc * PANEL + tid] * tmp[NW * 32 + cc];
-        xv[base + tid] = s;
-      }
-      __syncthreads();
-    }
-    // t1 = L21^T x2
-    for (int cc = tid; cc < n1; cc += NT) {
-      T s = 0;
-      for (int r = 0; r < n2; ++r) s += L21[(int64_t)r * C.ld21 + cc] * xv[n0 + n1 + r];
-      tmp[cc] = s;
+      acc = warp_sum(acc);
+      if (lane == 0) yv[base + r] = acc;
     }
     __syncthreads();
+    // ---- backward solve L^T x = y
+    // x_2 = Z^T y_2: threads own 4-column groups, rows split into slices
+    {
+      const int ngz = (n2 + 3) / 4, ldz = 4 * ngz;
+      const int slices = max(1, min(NT / ngz, a.tmpcap / ldz));
+      const int gq = tid % ngz, sl = tid / ngz;
+      if (sl < slices) {
+        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int r = 4 * gq + sl; r < n2; r += slices) {  // Z[r][c] = 0 for c > r
+          V4<T> v = load4(Z + C.zoff[r] + 4 * gq);
+          T yr = yv[base + r];
+          a0 += v.x * yr; a1 += v.y * yr; a2 += v.z * yr; a3 += v.w * yr;
+        }
+        T *dst = tmp + (int64_t)sl * ldz + 4 * gq;
+        dst[0] = a0; dst[1] = a1; dst[2] = a2; dst[3] = a3;
+      }
+      __syncthreads();
+      for (int cc = tid; cc < n2; cc += NT) {
+        T s = 0;
+        for (int q = 0; q < slices; ++q) s += tmp[q * ldz + cc];
+        xv[base + cc] = s;
+      }
+      __syncthreads();
+    }
+    // t1 = L21^T x2: threads own 4-column groups, rows split into slices
+    // (no level-1 rows, e.g. p = 1: nothing to do)
+    if (n1 > 0) {
+      const int ng = C.ld21 / 4;
+      const int slices = max(1, min(NT / ng, a.tmpcap / C.ld21));
+      const int gq = tid % ng, sl = tid / ng;
+      if (sl < slices) {
+        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int r = sl; r < n2; r += slices) {
+          V4<T> v = load4(L21 + (int64_t)r * C.ld21 + 4 * gq);
+          T xr = xv[base + r];
+          a0 += v.x * xr; a1 += v.y * xr; a2 += v.z * xr; a3 += v.w * xr;
+        }
+        T *dst = tmp + (int64_t)sl * C.ld21 + 4 * gq;
+        dst[0] = a0; dst[1] = a1; dst[2] = a2; dst[3] = a3;
+      }
+      __syncthreads();
+      for (int cc = tid; cc < n1; cc += NT) {
+        T s = 0;
+        for (int q = 0; q < slices; ++q) s += tmp[q * C.ld21 + cc];
+        tmp[cc] = s;  // only this thread reads column cc of the slices
+      }
+      __syncthreads();
+    }
   } else {
     for (int cc = tid; cc < n1; cc += NT) tmp[cc] = 0;
     __syncthreads();
   }
-  for (int i = tid; i < n1; i += NT) {
+  for (int i = tid; i < n1; i += NT) {  // x_1 = L_11^{-T} (y_1 - L21^T x_2)
     int b = C.line_of[i], s0 = C.line_start[b], w = C.line_len[b];
     const T *Lb = Lv + C.off_lines + C.line_off[b];
     T s = 0;
@@ -254,59 +287,46 @@ __global__ void __launch_bounds__(PATCH_THREADS) k_patch_solve(PatchSolveArgs<T>
     xv[n0 + i] = s;
   }
   __syncthreads();
-  for (int j = tid; j < n0; j += NT) {
+  for (int j = tid; j < n0; j += NT) {  // x_0 = D_0^{-1} (y_0 - L_{>0,0}^T x_{>0})
     T s = yv[j];
     for (int q = C.c0_ptr[j]; q < C.c0_ptr[j + 1]; ++q) {
       int pos = C.c0_pos[q];
-      s -= ell[pos] * xv[n0 + pos % C.nrow0];
+      s -= ell[pos] * xv[n0 + pos % C.ldr0];
     }
     xv[j] = s * dinv0[j];
   }
   __syncthreads();
 
-  // ---- write the star solution: interface values and back-substituted interior
+  // ---- the interface solution, in factor order
   T *X = a.X + P.xoff;
-  for (int k = tid; k < nG; k += NT) X[C.gpos[k]] = xv[k];
-  for (int pos = tid; pos < C.nd; pos += NT) {
-    if (C.ginv[pos] >= 0) continue;
-    int t[3] = {pos % dim0, (pos / dim0) % dim1, pos / (dim0 * dim1)};
-    int sd = 0, l[3];
-    for (int ax = 0; ax < 3; ++ax) {
-      int side = (C.full[ax] && t[ax] > c) ? 1 : 0;
-      sd |= side << ax;
-      star_local(C.full[ax], p, t[ax], side, l[ax]);
-    }
-    const T *mu = sMu + 3 * sd;
-    T r = E[(int64_t)sCell[sd] * n3 + l[0] + n * (l[1] + n * l[2])];
-    for (int ax = 0; ax < 3; ++ax) {
-      if (!C.full[ax]) continue;
-      int tt[3] = {t[0], t[1], t[2]};
-      tt[ax] = c;
-      int fk = C.ginv[tt[0] + dim0 * (tt[1] + dim1 * tt[2])];
-      int lf = ((sd >> ax) & 1) ? 0 : p;
-      int b1 = ax == 0 ? 1 : 0, b2 = ax == 2 ? 1 : 2;
-      T coef = mu[ax] * sAf[lf * n + l[ax]] * sBf[l[b1] * n + l[b1]] * sBf[l[b2] * n + l[b2]];
-      r -= coef * xv[fk];
-    }
-    X[pos] = r / interior_diag(sAf, sBf, mu, n, l[0], l[1], l[2]);
-  }
+  for (int k = tid; k < nG; k += NT) X[k] = xv[k];
 }
 
 // ------------------------------------------------------------------ interpolate
 template <typename T, typename Tout>
-__global__ void __launch_bounds__(256) k_interp_fdm(Grid g, const PatchDev *__restrict__ patches,
-                                                    const ClassDev *__restrict__ cls, const T *__restrict__ X,
-                                                    const T *__restrict__ tab, double omega, Tout *__restrict__ z) {
+__global__ void __launch_bounds__(256) k_interp_fdm(InterpArgs<T> a, double omega, Tout *__restrict__ z) {
   extern __shared__ unsigned char smem_[];
-  T *sT = reinterpret_cast<T *>(smem_);
+  const Grid &g = a.g;
   const int n = g.n, p = g.p, n3 = n * n * n, c = p - 1;
-  T *b0 = sT + n * n, *b1 = b0 + n3;
+  T *sT = reinterpret_cast<T *>(smem_);
+  T *sAf = sT + n * n, *sBf = sAf + n * n;
+  T *b0 = sBf + n * n, *b1 = b0 + n3;
+  __shared__ T mu[3];
   const int cell = blockIdx.x;
   const int ce[3] = {cell % g.nx, (cell / g.nx) % g.ny, cell / (g.nx * g.ny)};
   const int ncl[3] = {g.nx, g.ny, g.nz};
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x) sT[i] = tab[tab_off(TAB_T, n) + i];
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    sT[i] = a.tab[tab_off(TAB_T, n) + i];
+    sAf[i] = a.tab[tab_off(TAB_AF, n) + i];
+    sBf[i] = a.tab[tab_off(TAB_BF, n) + i];
+  }
+  if (threadIdx.x < 3) mu[threadIdx.x] = T(a.mu[3 * cell + threadIdx.x]);
+  // interface-type nodes of the cell: sum of the stars' interface solutions
   for (int idx = threadIdx.x; idx < n3; idx += blockDim.x) {
     int li[3] = {idx % n, (idx / n) % n, idx / (n * n)};
+    bool onb = false;
+    for (int ax = 0; ax < 3; ++ax) onb |= (li[ax] == 0 || li[ax] == p);
+    if (!onb) continue;
     T acc = 0;
     for (int o = 0; o < 8; ++o) {
       int oo[3] = {o & 1, (o >> 1) & 1, o >> 2};
@@ -325,19 +345,35 @@ __global__ void __launch_bounds__(256) k_interp_fdm(Grid g, const PatchDev *__re
         }
       }
       if (!ok) continue;
-      int pid = v[0] + (g.nx + 1) * (v[1] + (g.ny + 1) * v[2]);
-      const PatchDev P = patches[pid];
-      const ClassDev &C = cls[P.cls];
-      acc += X[P.xoff + t[0] + C.dim[0] * (t[1] + C.dim[1] * t[2])];
+      const PatchDev P = a.patches[v[0] + (g.nx + 1) * (v[1] + (g.ny + 1) * v[2])];
+      const ClassDev &C = a.cls[P.cls];
+      int k = C.ginv[t[0] + C.dim[0] * (t[1] + C.dim[1] * t[2])];
+      if (k >= 0) acc += a.X[P.xoff + k];
     }
     b0[idx] = acc;
   }
   __syncthreads();
-  contract_axis(b0, b1, sT, false, 0, n, threadIdx.x, blockDim.x);
+  // interior nodes: (8 r(m) - sum over the 6 face nodes of A_mf z(f)) / A_mm
+  const T *Ek = a.E + (int64_t)cell * n3;
+  for (int idx = threadIdx.x; idx < n3; idx += blockDim.x) {
+    int l[3] = {idx % n, (idx / n) % n, idx / (n * n)};
+    bool onb = false;
+    for (int ax = 0; ax < 3; ++ax) onb |= (l[ax] == 0 || l[ax] == p);
+    if (onb) continue;
+    T s = T(8) * Ek[idx];
+    for (int ax = 0; ax < 3; ++ax) {
+      const int stride = ax == 0 ? 1 : (ax == 1 ? n : n * n);
+      s -= face_coupling(sAf, sBf, mu, n, ax, 0, l) * b0[idx - l[ax] * stride];
+      s -= face_coupling(sAf, sBf, mu, n, ax, p, l) * b0[idx + (p - l[ax]) * stride];
+    }
+    b0[idx] = s / interior_diag(sAf, sBf, mu, n, l[0], l[1], l[2]);
+  }
   __syncthreads();
-  contract_axis(b1, b0, sT, false, 1, n, threadIdx.x, blockDim.x);
+  contract(b0, b1, sT, false, 0, n, T(1), false);
   __syncthreads();
-  contract_axis(b0, b1, sT, false, 2, n, threadIdx.x, blockDim.x);
+  contract(b1, b0, sT, false, 1, n, T(1), false);
+  __syncthreads();
+  contract(b0, b1, sT, false, 2, n, T(1), false);
   __syncthreads();
   for (int idx = threadIdx.x; idx < n3; idx += blockDim.x) {
     int i = idx % n, j = (idx / n) % n, k = idx / (n * n);
@@ -350,53 +386,82 @@ __global__ void __launch_bounds__(256) k_interp_fdm(Grid g, const PatchDev *__re
 
 // ------------------------------------------------------------------ launchers
 template <typename T, typename Tin>
-void launch_restrict_fdm(const Grid &g, const Tin *r, const T *tab, T *E, cudaStream_t st) {
-  size_t sm = sizeof(T) * (g.n * g.n + 2 * g.n * g.n * g.n);
+void launch_restrict_fdm(const Grid &g, const Tin *r, const T *tab, const double *mu, T *E, cudaStream_t st) {
+  size_t sm = sizeof(T) * (3 * g.n * g.n + 2 * g.n * g.n * g.n);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_restrict_fdm<T, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  k_restrict_fdm<T, Tin><<<g.ncell, 256, sm, st>>>(g, r, tab, E);
+  k_restrict_fdm<T, Tin><<<g.ncell, 256, sm, st>>>(g, r, tab, mu, E);
 }
 
 template <typename T, typename Tout>
-void launch_interp_fdm(const Grid &g, const PatchDev *patches, const ClassDev *cls, const T *X, const T *tab,
-                       double omega, Tout *z, cudaStream_t st) {
-  size_t sm = sizeof(T) * (g.n * g.n + 2 * g.n * g.n * g.n);
+void launch_interp_fdm(const InterpArgs<T> &a, double omega, Tout *z, cudaStream_t st) {
+  size_t sm = sizeof(T) * (3 * a.g.n * a.g.n + 2 * a.g.n * a.g.n * a.g.n);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_interp_fdm<T, Tout>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  k_interp_fdm<T, Tout><<<g.ncell, 256, sm, st>>>(g, patches, cls, X, tab, omega, z);
+  k_interp_fdm<T, Tout><<<a.g.ncell, 256, sm, st>>>(a, omega, z);
+}
+
+int patch_tmp_elems(int maxN1, int maxN2) {
+  // tmp holds a level-1 vector (n1) or the sliced partial sums of L21^T x_2
+  // and Z^T y_2 (slices * row length, slices clamped to fit)
+  int tmpn = 4 * PATCH_THREADS_MAX;
+  int l1 = (maxN1 + 3) & ~3, l2 = (maxN2 + 3) & ~3;
+  if (l1 > tmpn) tmpn = l1;
+  if (l2 > tmpn) tmpn = l2;
+  return tmpn;
 }
 
 template <typename T>
-size_t patch_smem_bytes(int n, int maxG, int maxN1) {
-  int tmpn = maxN1 > (PATCH_THREADS / 32) * 32 + PANEL ? maxN1 : (PATCH_THREADS / 32) * 32 + PANEL;
-  return sizeof(T) * (2 * n * n + 24) + sizeof(int) * 8 + sizeof(T) * (3 * maxG + tmpn) + 64;
+size_t patch_smem_bytes(int n, int maxG, int maxN1, int maxN2) {
+  (void)n;
+  return sizeof(T) * (3 * maxG + patch_tmp_elems(maxN1, maxN2));
 }
 
+// ctas_per_sm > 0 pads the dynamic shared memory so that at most that many
+// patch CTAs are resident per SM (bounds the factors in flight in L2)
 template <typename T>
-void launch_patch_solve(const PatchSolveArgs<T> &a, int npatch, size_t smem, cudaStream_t st) {
+size_t patch_smem_for_occupancy(size_t need, int ctas_per_sm) {
+  if (ctas_per_sm <= 0) return need;
+  size_t cap = (size_t)(227 * 1024) / ctas_per_sm;
+  if (cap > 200 * 1024) cap = 200 * 1024;
+  cap = cap > 1024 ? cap - 1024 : cap;  // room for static shared memory and the per-CTA reserve
+  return need > cap ? need : cap;
+}
+
+template <typename T, int NT>
+void launch_patch_nt(const PatchSolveArgs<T> &a, int npatch, size_t smem, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_patch_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_patch_solve<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  if (npatch > 0) k_patch_solve<T><<<npatch, PATCH_THREADS, smem, st>>>(a);
+  k_patch_solve<T, NT><<<npatch, NT, smem, st>>>(a);
+}
+
+template <typename T>
+void launch_patch_solve(const PatchSolveArgs<T> &a, int npatch, size_t smem, int threads, cudaStream_t st) {
+  if (npatch <= 0) return;
+  if (threads >= 1024) launch_patch_nt<T, 1024>(a, npatch, smem, st);
+  else if (threads >= 512) launch_patch_nt<T, 512>(a, npatch, smem, st);
+  else launch_patch_nt<T, 256>(a, npatch, smem, st);
 }
 
 #define INST(T)                                                                                          \
-  template void launch_restrict_fdm<T, double>(const Grid &, const double *, const T *, T *, cudaStream_t); \
-  template void launch_restrict_fdm<T, float>(const Grid &, const float *, const T *, T *, cudaStream_t);   \
-  template void launch_interp_fdm<T, double>(const Grid &, const PatchDev *, const ClassDev *, const T *,    \
-                                             const T *, double, double *, cudaStream_t);                     \
-  template void launch_interp_fdm<T, float>(const Grid &, const PatchDev *, const ClassDev *, const T *,     \
-                                            const T *, double, float *, cudaStream_t);                       \
-  template size_t patch_smem_bytes<T>(int, int, int);                                                       \
-  template void launch_patch_solve<T>(const PatchSolveArgs<T> &, int, size_t, cudaStream_t);
+  template void launch_restrict_fdm<T, double>(const Grid &, const double *, const T *, const double *, T *, \
+                                               cudaStream_t);                                                \
+  template void launch_restrict_fdm<T, float>(const Grid &, const float *, const T *, const double *, T *,   \
+                                              cudaStream_t);                                                 \
+  template void launch_interp_fdm<T, double>(const InterpArgs<T> &, double, double *, cudaStream_t);        \
+  template void launch_interp_fdm<T, float>(const InterpArgs<T> &, double, float *, cudaStream_t);          \
+  template size_t patch_smem_bytes<T>(int, int, int, int);                                                       \
+  template void launch_patch_solve<T>(const PatchSolveArgs<T> &, int, size_t, int, cudaStream_t);        \
+  template size_t patch_smem_for_occupancy<T>(size_t, int);
 INST(float)
 INST(double)
 #undef INST

@@ -302,8 +302,8 @@ __global__ void __launch_bounds__(256) k_pack(FactorArgs a) {
     if (W) W[off] = (float)v;
   };
   for (int j = threadIdx.x; j < n0; j += blockDim.x) put(C.off_dinv0 + j, 1.0 / S[(int64_t)j * nG + j]);
-  for (int q = threadIdx.x; q < C.K0 * C.nrow0; q += blockDim.x) {
-    int col = C.ell_col[q], r = q % C.nrow0;
+  for (int q = threadIdx.x; q < C.K0 * C.ldr0; q += blockDim.x) {
+    int col = C.ell_col[q], r = q % C.ldr0;
     put(C.off_ell + q, col >= 0 ? S[(int64_t)(n0 + r) * nG + col] : 0.0);
   }
   for (int b = 0; b < C.nlines; ++b) {
@@ -315,20 +315,31 @@ __global__ void __launch_bounds__(256) k_pack(FactorArgs a) {
     int r = (int)(q / C.ld21), cc = (int)(q % C.ld21);
     put(C.off_l21 + q, cc < n1 ? S[(int64_t)(n0 + n1 + r) * nG + n0 + cc] : 0.0);
   }
-  for (int qp = 0; qp < C.npanel; ++qp) {
-    const int base = n0 + n1 + qp * PANEL, w = min(PANEL, n2 - qp * PANEL), rows = n2 - qp * PANEL;
-    const int64_t off = C.off_pan + C.pan_off[qp];
-    for (int64_t q = threadIdx.x; q < (int64_t)rows * PANEL; q += blockDim.x) {
-      int r = (int)(q / PANEL), cc = (int)(q % PANEL);
-      if (r < w) {
-        if (cc >= w) put(off + q, 0.0);  // diagonal inverse written below
-      } else {
-        put(off + q, cc < w ? S[(int64_t)(base + r) * nG + base + cc] : 0.0);
-      }
+  // top level: Z = L_top^{-1} by forward substitution, one column per thread;
+  // column c of Z (below the diagonal) is kept in row c of the strict upper
+  // triangle of the workspace, which the factorisation no longer uses.
+  const int base = n0 + n1;
+  double *Sw = a.S + (int64_t)slot * a.ldS;
+  for (int cc = threadIdx.x; cc < n2; cc += blockDim.x) {
+    double *zc = Sw + (int64_t)(base + cc) * nG + base;  // zc[i] = Z[i][cc], i > cc
+    const double zdiag = 1.0 / S[(int64_t)(base + cc) * nG + base + cc];
+    for (int i = cc + 1; i < n2; ++i) {
+      const double *Li = S + (int64_t)(base + i) * nG + base;
+      double s = Li[cc] * zdiag;
+      for (int k = cc + 1; k < i; ++k) s += Li[k] * zc[k];
+      zc[i] = -s / Li[i];
     }
-    tri_inverse(S + (int64_t)base * nG + base, nG, w, V + off, PANEL, W != nullptr, W ? W + off : nullptr);
-    __syncthreads();
-    // zero the strictly upper part of the stored inverse (tri_inverse wrote zeros already)
+  }
+  __syncthreads();
+  for (int r = 0; r < n2; ++r) {
+    const int len = C.zoff[r + 1] - C.zoff[r];
+    const int64_t off = C.off_z + C.zoff[r];
+    for (int cc = threadIdx.x; cc < len; cc += blockDim.x) {
+      double v = 0.0;
+      if (cc == r) v = 1.0 / S[(int64_t)(base + r) * nG + base + r];
+      else if (cc < r) v = S[(int64_t)(base + cc) * nG + base + r];
+      put(off + cc, v);
+    }
   }
 }
 

@@ -6,7 +6,7 @@
 
 namespace fdm {
 
-constexpr int PATCH_THREADS = 256;
+constexpr int PATCH_THREADS_MAX = 1024;  // largest patch-solve block (tmp sizing)
 
 template <typename T>
 struct PatchSolveArgs {
@@ -19,18 +19,56 @@ struct PatchSolveArgs {
   const T *tab;
   const T *L;
   T *X;
+  int tmpcap;    // elements of the tmp shared-memory area
+  int prefetch;  // L2 bulk prefetch of the factor: 0 none, 1 all at start, 2 section ahead of use
 };
+int patch_tmp_elems(int maxN1, int maxN2);
+
+template <typename T>
+struct InterpArgs {
+  Grid g;
+  const PatchDev *patches;
+  const ClassDev *cls;
+  const T *X;       // interface solutions of all stars
+  const T *E;       // condensed cell-local FDM residual (interior entries unchanged)
+  const double *mu; // surrogate coefficients
+  const T *tab;
+};
+
+// streamed patch solve: per-class chunk schedules over the factor values
+template <typename T>
+struct StreamArgs {
+  Grid g;
+  const ClassDev *cls;
+  const PatchDev *patches;
+  const int *order;   // patches with an interface, heaviest first
+  int npatch;
+  const T *E;
+  const T *L;
+  T *X;
+  int maxG, maxN0, maxN1, tmpcap;
+  int nbuf, buf_bytes;  // ring of shared-memory chunk buffers
+  int ctas_per_sm;      // 0 = as many as fit
+  uint64_t timeout_ns;  // bound of every mbarrier wait
+  int inject_stall;     // test hook: wait on a barrier that nothing completes
+  int *status;          // set to 1 when a bounded wait ran out
+};
+template <typename T>
+size_t stream_smem_bytes(const StreamArgs<T> &a);
+template <typename T>
+int launch_patch_stream(const StreamArgs<T> &a, int threads, cudaStream_t st);
 
 // basis change and relaxation
 template <typename T, typename Tin>
-void launch_restrict_fdm(const Grid &g, const Tin *r, const T *tab, T *E, cudaStream_t st);
+void launch_restrict_fdm(const Grid &g, const Tin *r, const T *tab, const double *mu, T *E, cudaStream_t st);
 template <typename T, typename Tout>
-void launch_interp_fdm(const Grid &g, const PatchDev *patches, const ClassDev *cls, const T *X, const T *tab,
-                       double omega, Tout *z, cudaStream_t st);
+void launch_interp_fdm(const InterpArgs<T> &a, double omega, Tout *z, cudaStream_t st);
 template <typename T>
-size_t patch_smem_bytes(int n, int maxG, int maxN1);
+size_t patch_smem_bytes(int n, int maxG, int maxN1, int maxN2);
 template <typename T>
-void launch_patch_solve(const PatchSolveArgs<T> &a, int npatch, size_t smem, cudaStream_t st);
+void launch_patch_solve(const PatchSolveArgs<T> &a, int npatch, size_t smem, int threads, cudaStream_t st);
+template <typename T>
+size_t patch_smem_for_occupancy(size_t need, int ctas_per_sm);
 
 // operators
 struct OpArgs {

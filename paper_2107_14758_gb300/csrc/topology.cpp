@@ -15,6 +15,7 @@
 // patch.
 #include <algorithm>
 #include <cstring>
+#include <functional>
 #include <map>
 
 #include "internal.h"
@@ -114,6 +115,25 @@ std::vector<PatchClass> build_classes(int p) {
     }
     C.nlines = (int)C.line_start.size();
     C.ginv = gindex;
+    // gather sources of every interface dof: the star cells whose closure holds it
+    // (slot = side_x + 2 side_y + 4 side_z), in slot order
+    C.gsrc.assign((size_t)8 * C.nG, -1);
+    for (int i = 0; i < C.nG; ++i) {
+      int pos = C.gpos[i];
+      int tt[3] = {pos % C.dim[0], (pos / C.dim[0]) % C.dim[1], pos / (C.dim[0] * C.dim[1])};
+      int cnt = 0;
+      for (int slot = 0; slot < 8; ++slot) {
+        int l[3];
+        bool ok = true;
+        for (int a = 0; a < 3 && ok; ++a) {
+          int side = (slot >> a) & 1;
+          if (!C.full[a]) { ok = side == 0; l[a] = tt[a] + 1; }
+          else if (side == 0) { ok = tt[a] <= c; l[a] = tt[a] + 1; }
+          else { ok = tt[a] >= c; l[a] = tt[a] - c; }
+        }
+        if (ok) C.gsrc[(size_t)8 * i + cnt++] = (slot << 16) | (l[0] + (p + 1) * (l[1] + (p + 1) * l[2]));
+      }
+    }
     C.line_of.assign(C.n1, 0);
     for (int b = 0; b < C.nlines; ++b)
       for (int i = 0; i < C.line_len[b]; ++i) C.line_of[C.line_start[b] + i] = b;
@@ -231,27 +251,28 @@ std::vector<PatchClass> build_classes(int p) {
     }
     C.K0 = 0;
     for (auto &v : rowcols) C.K0 = std::max(C.K0, (int)v.size());
-    C.ell_col.assign((size_t)C.K0 * C.nrow0, -1);
+    C.ldr0 = (C.nrow0 + 3) & ~3;
+    C.ell_col.assign((size_t)C.K0 * C.ldr0, -1);
     std::vector<std::vector<int>> colpos(C.n0);
     for (int r = 0; r < C.nrow0; ++r)
       for (size_t e = 0; e < rowcols[r].size(); ++e) {
-        C.ell_col[e * C.nrow0 + r] = rowcols[r][e];
-        colpos[rowcols[r][e]].push_back((int)(e * C.nrow0 + r));
+        C.ell_col[e * C.ldr0 + r] = rowcols[r][e];
+        colpos[rowcols[r][e]].push_back((int)(e * C.ldr0 + r));
       }
     C.c0_ptr.assign(C.n0 + 1, 0);
     for (int j = 0; j < C.n0; ++j) {
+      std::sort(colpos[j].begin(), colpos[j].end());  // ascending slice, then row
       for (int q : colpos[j]) C.c0_pos.push_back(q);
       C.c0_ptr[j + 1] = (int)C.c0_pos.size();
     }
     // --- value layout of one patch (elements), 16-byte aligned sections ---
     auto up4 = [](int64_t x) { return (x + 3) & ~int64_t(3); };
     C.ld21 = (int)up4(C.n1);
-    C.npanel = (C.n2 + PANEL - 1) / PANEL;
     int64_t off = 0;
     C.off_dinv0 = off;
     off = up4(off + C.n0);
     C.off_ell = off;
-    off = up4(off + (int64_t)C.K0 * C.nrow0);
+    off = up4(off + (int64_t)C.K0 * C.ldr0);
     C.off_lines = off;
     for (int b = 0; b < C.nlines; ++b) {
       C.line_off.push_back((int)(off - C.off_lines));
@@ -259,12 +280,71 @@ std::vector<PatchClass> build_classes(int p) {
     }
     C.off_l21 = off;
     off = up4(off + (int64_t)C.n2 * C.ld21);
-    C.off_pan = off;
-    for (int q = 0; q < C.npanel; ++q) {
-      C.pan_off.push_back((int)(off - C.off_pan));
-      off += (int64_t)(C.n2 - q * PANEL) * PANEL;
-    }
+    // top level: Z = L_top^{-1} (lower triangular) by rows, each padded to 4
+    C.off_z = off;
+    C.zoff.assign(C.n2 + 1, 0);
+    for (int r = 0; r < C.n2; ++r) C.zoff[r + 1] = C.zoff[r] + (int)up4(r + 1);
+    off += C.zoff[C.n2];
     C.nval = up4(off);
+  }
+  return out;
+}
+
+// Chunk schedule of the streamed patch solve for one class: the factor
+// sections in the order the forward solve reads them, then the backward
+// solve's sections in reverse, cut into bulk copies of at most cap_bytes
+// (whole rows, lines or ELL slices; 16-byte multiples, 16-byte aligned).
+std::vector<ChunkDev> build_schedule(const PatchClass &C, int es, int cap) {
+  std::vector<ChunkDev> f, out;
+  if (C.nG == 0) return out;
+  auto up16 = [](int64_t b) { return (int)((b + 15) & ~int64_t(15)); };
+  auto need = [&](int64_t b) {
+    if (b > cap) fail(FDM_EINVAL, "stream schedule: one row does not fit a chunk buffer");
+  };
+  // groups [i, j) of consecutive items of sizes sz(i) into chunks
+  auto cut = [&](int kind, int nitems, std::function<int64_t(int)> off, std::function<int64_t(int)> sz) {
+    std::vector<ChunkDev> v;
+    int i = 0;
+    while (i < nitems) {
+      int64_t b = 0;
+      int j = i;
+      while (j < nitems && b + sz(j) * es <= cap) b += sz(j++) * es;
+      if (j == i) need(sz(i) * es);
+      v.push_back({kind, i, j, up16(b), off(i)});
+      i = j;
+    }
+    return v;
+  };
+  std::vector<ChunkDev> ell, lines, l21, z;
+  if (C.n0 > 0) {
+    need((int64_t)C.n0 * es);
+    f.push_back({CK_DINV, 0, C.n0, up16((int64_t)C.n0 * es), C.off_dinv0});
+  }
+  if (C.K0 > 0 && C.nrow0 > 0)
+    ell = cut(CK_ELL_F, C.K0, [&](int e) { return C.off_ell + (int64_t)e * C.ldr0; },
+              [&](int) { return (int64_t)C.ldr0; });
+  if (C.nlines > 0)
+    lines = cut(CK_LINES_F, C.nlines, [&](int b) { return C.off_lines + C.line_off[b]; },
+                [&](int b) { return (int64_t)((C.line_len[b] * C.line_len[b] + 3) & ~3); });
+  if (C.n2 > 0 && C.n1 > 0)
+    l21 = cut(CK_L21_F, C.n2, [&](int r) { return C.off_l21 + (int64_t)r * C.ld21; },
+              [&](int) { return (int64_t)C.ld21; });
+  if (C.n2 > 0)
+    z = cut(CK_Z_F, C.n2, [&](int r) { return C.off_z + C.zoff[r]; },
+            [&](int r) { return (int64_t)(C.zoff[r + 1] - C.zoff[r]); });
+  auto flag = [](std::vector<ChunkDev> &v, int kind) {
+    for (size_t i = 0; i < v.size(); ++i)
+      v[i].kind = kind | ((i == 0) << 8) | ((i + 1 == v.size()) << 9);
+  };
+  out = f;
+  for (auto *sec : {&ell, &lines, &l21, &z}) out.insert(out.end(), sec->begin(), sec->end());
+  // backward: Z, L21, lines, ELL, each visited from its last chunk
+  const std::pair<std::vector<ChunkDev> *, int> back[4] = {{&z, CK_Z_B}, {&l21, CK_L21_B}, {&lines, CK_LINES_B},
+                                                           {&ell, CK_ELL_B}};
+  for (auto &bk : back) {
+    std::vector<ChunkDev> v(bk.first->rbegin(), bk.first->rend());
+    flag(v, bk.second);
+    out.insert(out.end(), v.begin(), v.end());
   }
   return out;
 }

@@ -21,7 +21,8 @@ FDM_PC_NONE, FDM_PC_ASM, FDM_PC_VCYCLE = 0, 1, 2
 FDM_SURR_AVERAGED, FDM_SURR_EXTERNAL = 0, 1
 (FDM_Q_NDOF, FDM_Q_OMEGA, FDM_Q_LAMBDA, FDM_Q_MU, FDM_Q_NPATCH, FDM_Q_PATCH_CLASS, FDM_Q_CLASS_INFO,
  FDM_Q_GAMMA_ORDER, FDM_Q_FACTOR_NNZ, FDM_Q_PATTERN, FDM_Q_FACTOR, FDM_Q_BASIS, FDM_Q_FACTOR_BYTES,
- FDM_Q_SETUP_SECONDS) = range(1, 15)
+ FDM_Q_SETUP_SECONDS, FDM_Q_KERNEL_TIMES, FDM_Q_LAUNCHES, FDM_Q_ALGO_BYTES, FDM_Q_STATUS) = range(1, 19)
+TIMERS = ("restrict", "patch", "interp", "op64", "op32", "coarse", "vec")
 
 
 class fdm_mesh(C.Structure):
@@ -37,7 +38,10 @@ class fdm_coeff(C.Structure):
 class fdm_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("pc", C.c_int), ("surrogate", C.c_int), ("lanczos_steps", C.c_int),
                 ("omega", C.c_double), ("lanczos_seed", C.c_uint64), ("flexible_beta", C.c_int),
-                ("wait_timeout_s", C.c_double), ("lanczos_start", C.POINTER(C.c_double))]
+                ("wait_timeout_s", C.c_double), ("lanczos_start", C.POINTER(C.c_double)),
+                ("kernel_timing", C.c_int), ("patch_ctas_per_sm", C.c_int), ("patch_threads", C.c_int),
+                ("patch_kernel", C.c_int), ("stream_buffers", C.c_int), ("stream_buffer_kb", C.c_int),
+                ("inject_stall", C.c_int), ("patch_prefetch", C.c_int)]
 
 
 class fdm_solve_info(C.Structure):
@@ -196,7 +200,9 @@ class Context:
     """Owns one set-up problem (a fdm_ctx) and its host inputs."""
 
     def __init__(self, p, xv, yv, zv, jac=None, kappa=None, precision=FDM_PREC_FP32, pc=FDM_PC_VCYCLE,
-                 omega=0.0, lanczos_start=None, lanczos_steps=20, flexible_beta=-1, stream=None):
+                 omega=0.0, lanczos_start=None, lanczos_steps=20, flexible_beta=-1, kernel_timing=0,
+                 patch_ctas_per_sm=0, patch_threads=0, patch_kernel=0, stream_buffers=0, stream_buffer_kb=0,
+                 inject_stall=0, wait_timeout_s=1.0, patch_prefetch=0, stream=None):
         self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (xv, yv, zv)]
         mesh = fdm_mesh()
         mesh.nx, mesh.ny, mesh.nz = len(xv) - 1, len(yv) - 1, len(zv) - 1
@@ -213,6 +219,15 @@ class Context:
         opt = fdm_default_options()
         opt.precision, opt.pc, opt.omega, opt.lanczos_steps = precision, pc, omega, lanczos_steps
         opt.flexible_beta = flexible_beta
+        opt.kernel_timing = kernel_timing
+        opt.patch_ctas_per_sm = patch_ctas_per_sm
+        opt.patch_threads = patch_threads
+        opt.patch_kernel = patch_kernel
+        opt.stream_buffers = stream_buffers
+        opt.stream_buffer_kb = stream_buffer_kb
+        opt.inject_stall = inject_stall
+        opt.patch_prefetch = patch_prefetch
+        opt.wait_timeout_s = wait_timeout_s
         if lanczos_start is not None:
             s = np.ascontiguousarray(lanczos_start, dtype=np.float64)
             self._keep.append(s)
@@ -301,6 +316,24 @@ class Context:
         out = np.zeros(max(nG * nG, 1), dtype=np.float64)
         fdm_query(self.h, FDM_Q_FACTOR, out, patch)
         return out[:nG * nG].reshape(nG, nG)
+
+    def kernel_times(self):
+        """{timer: (launches, total ms)} since the last call (needs kernel_timing=1)."""
+        h = self.query(FDM_Q_KERNEL_TIMES, np.float64, 2 * len(TIMERS)).reshape(-1, 2)
+        return {name: (int(h[i, 0]), float(h[i, 1])) for i, name in enumerate(TIMERS)}
+
+    def status(self):
+        return int(self.query(FDM_Q_STATUS, np.int32, 1)[0])
+
+    def launches(self):
+        return int(self.query(FDM_Q_LAUNCHES, np.int64, 1)[0])
+
+    def algo_bytes(self):
+        v = self.query(FDM_Q_ALGO_BYTES, np.float64, 4)
+        return dict(patch64=v[0], patch32=v[1], asm64=v[2], asm32=v[3])
+
+    def setup_seconds(self):
+        return self.query(FDM_Q_SETUP_SECONDS, np.float64, 4)
 
     @property
     def npatch(self):

@@ -332,3 +332,49 @@ def test_full_size_sampled(name):
         tol = 1e-11 if precision == FP64 else 1e-4
         assert relerr(z, z_ref) <= tol, (name, precision)
         ctx.close()
+
+
+# ---------------------------------------------------------------- kernels and failure detection
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_both_patch_kernels_agree(kernel):
+    """The classic (one CTA per patch) and the streamed (bulk copies into a
+    shared-memory ring) patch solves give the oracle's relaxation."""
+    xv, yv, zv = inputs.graded_vertices(3, 21)
+    for p in (2, 5):
+        ctx = fdmpc.Context(p, xv, yv, zv, precision=FP64, pc=fdmpc.FDM_PC_ASM, omega=1.0, patch_kernel=kernel)
+        ref = oracle.Problem(p, xv, yv, zv)
+        ref.setup_patches()
+        ref.set_omega(1.0)
+        r = np.random.default_rng(22).standard_normal(ref.ndof)
+        assert relerr(N(ctx.asm_apply(T(r))), ref.asm_apply(r)) <= 1e-11
+        ctx.close()
+
+
+@pytest.mark.parametrize("nbuf,kb", [(2, 8), (3, 16), (6, 24)])
+def test_stream_ring_shapes(nbuf, kb):
+    w = inputs.workload("q4_uniform4")
+    ctx = fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=FP32, pc=fdmpc.FDM_PC_ASM, omega=1.0,
+                        stream_buffers=nbuf, stream_buffer_kb=kb, patch_kernel=2)
+    ref = oracle.Problem(w["p"], w["xv"], w["yv"], w["zv"])
+    ref.setup_patches()
+    ref.set_omega(1.0)
+    r = np.random.default_rng(23).standard_normal(ref.ndof)
+    assert relerr(N(ctx.asm_apply(T(r))), ref.asm_apply(r)) <= 1e-4
+    assert ctx.status() == 0
+
+
+def test_bounded_wait_reports_timeout():
+    """Failure detection without a GPU fault: the streamed solve is made to
+    wait on a barrier that nothing completes; the wait gives up after the
+    configured limit, the kernel drains its copies and returns, and the host
+    sees FDM_ETIMEOUT.  The context stays usable afterwards."""
+    xv, yv, zv = inputs.graded_vertices(2, 3)
+    ctx = fdmpc.Context(3, xv, yv, zv, precision=FP32, omega=0.2, inject_stall=1, wait_timeout_s=0.02,
+                        patch_kernel=2)
+    b = T(np.random.default_rng(0).standard_normal(ctx.ndof))
+    with pytest.raises(fdmpc.FdmError) as e:
+        ctx.pcg_solve(b, rtol=1e-8, maxit=2)
+    assert e.value.code == fdmpc.FDM_ETIMEOUT
+    y = ctx.stiffness_apply(b)  # the CUDA context is still healthy
+    torch.cuda.synchronize()
+    assert torch.isfinite(y).all()
