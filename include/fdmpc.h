@@ -119,6 +119,22 @@ int fdm_setup(const fdm_mesh *mesh, int p, const fdm_coeff *coeff, const fdm_opt
  * curved cells, Section 2.7).  u, y: device, ndof doubles. */
 int stiffness_apply(fdm_ctx *ctx, const double *u_dev, double *y_dev, void *stream);
 
+/* y = A u exactly as stiffness_apply, for callers that must not allocate
+ * device memory when they call (for example code that runs inside a
+ * memory-pool-free or allocation-forbidden section, or a runtime that owns
+ * all device memory and forbids cudaMalloc after start-up).  No counterpart
+ * in the paper: the method does not depend on where scratch memory lives.
+ * The cell-local partial results go to a fixed 16 MiB device array of the
+ * library (2^21 doubles, reserved on every GPU that loads the library until
+ * the process exits) instead of the context's buffer; calls with
+ * nx*ny*nz*(p+1)^3 > 2^21 are rejected with FDM_EINVAL.  This call performs
+ * no cudaMalloc/cudaFree and no allocating library call.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents (every entry is written before it is
+ * read, nothing needs clearing); calls that overlap on the GPU race on it. */
+int stiffness_apply_noalloc(fdm_ctx *ctx, const double *u_dev, double *y_dev, void *stream);
+
 /* b = M f: the mass matrix (load vector of nodal data f).  Device arrays. */
 int mass_apply(fdm_ctx *ctx, const double *f_dev, double *b_dev, void *stream);
 

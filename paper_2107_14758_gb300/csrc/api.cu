@@ -654,6 +654,13 @@ int handle(fdm_ctx *c, const Error &e) {
 
 }  // namespace
 
+namespace fdm {
+// accessors used by other translation units of the library
+OpArgs ctx_op_args64(const fdm_ctx *c) { return c->op_args(false); }
+void ctx_count_launches(fdm_ctx *c, int k) { c->launches += k; }
+int ctx_fail(fdm_ctx *c, int code, const std::string &msg) { return handle(c, Error{code, msg}); }
+}  // namespace fdm
+
 // ====================================================================== C-ABI
 extern "C" {
 

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "device.cuh"
 
 namespace fdm {
@@ -84,6 +86,11 @@ template <typename T, typename Tin, typename Tout>
 void launch_operator(const OpArgs &a, bool mass, const Tin *u, Tout *y, T *E, cudaStream_t st);
 // per-cell Galerkin coarse matrices P_K^T A^K P_K (FP64), [ncell][8][8]
 void launch_coarse_cell_matrices(const OpArgs &a, double *Ac, cudaStream_t st);
+
+// context accessors (defined with the C-ABI)
+OpArgs ctx_op_args64(const fdm_ctx *c);
+void ctx_count_launches(fdm_ctx *c, int k);
+int ctx_fail(fdm_ctx *c, int code, const std::string &msg);
 
 // coarse space
 template <typename T, typename Tin>

@@ -70,7 +70,7 @@ def load():
     L.fdm_default_options.argtypes = [C.POINTER(fdm_options)]
     L.fdm_setup.argtypes = [C.POINTER(fdm_mesh), C.c_int, C.POINTER(fdm_coeff), C.POINTER(fdm_options),
                             C.POINTER(vp), vp]
-    for f in ("stiffness_apply", "mass_apply", "asm_apply", "pc_apply"):
+    for f in ("stiffness_apply", "stiffness_apply_noalloc", "mass_apply", "asm_apply", "pc_apply"):
         getattr(L, f).argtypes = [vp, vp, vp, vp]
     L.pcg_solve.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.POINTER(fdm_solve_info), vp]
     L.fdm_batch_setup.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp)]
@@ -128,6 +128,10 @@ def fdm_setup(mesh, p, coeff, opt, stream=None):
 
 def stiffness_apply(ctx, u, y, stream=None):
     _check(load().stiffness_apply(ctx, _tptr(u), _tptr(y), _stream(stream)), ctx)
+
+
+def stiffness_apply_noalloc(ctx, u, y, stream=None):
+    _check(load().stiffness_apply_noalloc(ctx, _tptr(u), _tptr(y), _stream(stream)), ctx)
 
 
 def mass_apply(ctx, f, b, stream=None):
