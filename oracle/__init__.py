@@ -15,15 +15,16 @@ _lib = None
 
 
 def build(force=False):
-    """Compile oracle.c into liboracle.so with gcc (OpenMP over patches)."""
-    src = os.path.join(_HERE, "oracle.c")
+    """Compile oracle.c and surrogate.c into liboracle.so with gcc (OpenMP
+    over patches and cells)."""
+    srcs = [os.path.join(_HERE, f) for f in ("oracle.c", "surrogate.c")]
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f)
+                    for f in srcs + [os.path.join(_HERE, "oracle.h")])):
         return _LIB_PATH
     tmp = _LIB_PATH + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-fopenmp",
-           "-o", tmp, src, "-lm"]
+           "-o", tmp] + srcs + ["-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -76,6 +77,18 @@ def lib():
         L.or_pc_apply.argtypes = [C.c_void_p, dp, dp]
         L.or_lanczos_omega.argtypes = [C.c_void_p, dp, C.c_int, dp, dp, dp]
         L.or_pcg.argtypes = [C.c_void_p, dp, dp, C.c_double, C.c_int, C.c_int, ip, dp]
+        L.or_surr_bound.argtypes = [C.c_int, dp, dp, dp, dp]
+        L.or_surr_bound.restype = C.c_double
+        L.or_surr_cell_ghat.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp]
+        L.or_surr_label.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp, dp, dp]
+        L.or_surr_features.argtypes = [C.c_int, dp, dp]
+        L.or_mlp_forward.argtypes = [C.c_int, dp, dp, dp]
+        L.or_mlp_forward.restype = None
+        L.or_mlp_loss_grad.argtypes = [C.c_int, dp, dp, dp, dp]
+        L.or_mlp_loss_grad.restype = C.c_double
+        L.or_mlp_adam.argtypes = [C.c_int, dp, dp, dp, dp, C.c_int, C.c_double]
+        L.or_mlp_adam.restype = None
+        L.or_surr_apply.argtypes = [C.c_int, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -139,6 +152,78 @@ def symbolic_fill(pattern):
     pat = np.ascontiguousarray(pattern, dtype=np.uint8).copy()
     lib().or_symbolic_fill(pat.shape[0], pat.ctypes.data_as(C.POINTER(C.c_ubyte)))
     return pat.astype(bool)
+
+
+# ---- learned separable surrogate (Section 2.7, Theorem 1) ----------------
+MLP_NIN, MLP_NH, MLP_NOUT = 189, 64, 3
+MLP_NPARAM = MLP_NH * MLP_NIN + MLP_NH + MLP_NH * MLP_NH + MLP_NH + MLP_NOUT * MLP_NH + MLP_NOUT
+SURR_CMAX = 2.0
+
+
+def surr_bound(G, mu):
+    """(log(hi/lo), lo, hi) of the Theorem 1 bound over points G[q][6]."""
+    G = _f64(G).reshape(-1, 6); mu = _f64(mu)
+    lo = C.c_double(); hi = C.c_double()
+    F = lib().or_surr_bound(G.shape[0], _p(G), _p(mu), C.byref(lo), C.byref(hi))
+    return F, lo.value, hi.value
+
+
+def surr_cell_ghat(p, jac, kappa=None):
+    """kappa*Ghat per cell and Gauss point (unweighted) and the averaged mu."""
+    jac = _f64(jac); ncell = jac.shape[0]
+    nq = (p + 1) ** 3
+    G = np.zeros((ncell, nq, 6)); mubar = np.zeros((ncell, 3))
+    kp = _p(_f64(kappa)) if kappa is not None else None
+    kap = _f64(kappa) if kappa is not None else None
+    _check(lib().or_surr_cell_ghat(p, ncell, _p(jac), _p(kap) if kap is not None else kp, _p(G), _p(mubar)))
+    return G, mubar
+
+
+def surr_label(p, jac, kappa=None):
+    """Returns mubar[cell,3], cstar[cell,3], F0[cell], F1[cell]."""
+    jac = _f64(jac); ncell = jac.shape[0]
+    kap = _f64(kappa) if kappa is not None else None
+    mubar = np.zeros((ncell, 3)); cs = np.zeros((ncell, 3)); F0 = np.zeros(ncell); F1 = np.zeros(ncell)
+    _check(lib().or_surr_label(p, ncell, _p(jac), _p(kap) if kap is not None else None,
+                               _p(mubar), _p(cs), _p(F0), _p(F1)))
+    return mubar, cs, F0, F1
+
+
+def surr_features(s27):
+    s27 = _f64(s27); ncell = s27.shape[0]
+    f = np.zeros((ncell, MLP_NIN))
+    _check(lib().or_surr_features(ncell, _p(s27), _p(f)))
+    return f
+
+
+def mlp_forward(params, feat):
+    params = _f64(params); feat = _f64(feat)
+    c = np.zeros((feat.shape[0], MLP_NOUT))
+    lib().or_mlp_forward(feat.shape[0], _p(params), _p(feat), _p(c))
+    return c
+
+
+def mlp_loss_grad(params, feat, label, grad=True):
+    params = _f64(params); feat = _f64(feat); label = _f64(label)
+    g = np.zeros(MLP_NPARAM) if grad else None
+    loss = lib().or_mlp_loss_grad(feat.shape[0], _p(params), _p(feat), _p(label),
+                                  _p(g) if grad else None)
+    return loss, g
+
+
+def mlp_adam(params, grad, m, v, t, lr):
+    """One Adam step in place on params, m, v (all float64 arrays)."""
+    for a in (params, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = _f64(grad)
+    lib().or_mlp_adam(params.size, _p(params), _p(g), _p(m), _p(v), int(t), float(lr))
+
+
+def surr_apply(mubar, c):
+    mubar = _f64(mubar); c = _f64(c)
+    mu = np.zeros_like(mubar)
+    nf = lib().or_surr_apply(mubar.shape[0], _p(mubar), _p(c), _p(mu))
+    return mu, nf
 
 
 class Problem:

@@ -136,6 +136,60 @@ int or_lanczos_omega(or_ctx *c, const double *b0, int k, double *lmin, double *l
 int or_pcg(const or_ctx *c, const double *b, double *x, double rtol, int maxit, int pc,
            int *iters, double *hist);
 
+/* ---- learned separable surrogate (surrogate.c) -----------------------
+ * Section 2.7 / Theorem 1: for a cell with points q, M_q = kappa Ghat_q and a
+ * separable surrogate D = diag(mu), the true and surrogate cell stiffnesses
+ * satisfy lo * a~ <= a <= hi * a~ with lo (hi) the smallest (largest)
+ * eigenvalue of D^{-1/2} M_q D^{-1/2} over q.  A network maps 27 samples per
+ * cell to c, mu = mu_avg exp(c); its label is the mu minimising hi / lo. */
+#define OR_MLP_NIN 189  /* 27 points x (log kappa, 6 scaled Ghat entries) */
+#define OR_MLP_NH 64
+#define OR_MLP_NOUT 3
+#define OR_MLP_NPARAM (OR_MLP_NH * OR_MLP_NIN + OR_MLP_NH + OR_MLP_NH * OR_MLP_NH + OR_MLP_NH + \
+                       OR_MLP_NOUT * OR_MLP_NH + OR_MLP_NOUT)
+#define OR_SURR_MAXIT 600     /* ellipsoid steps of the label search */
+#define OR_SURR_RADIUS 6.0    /* initial disc of the label search (in log mu) */
+#define OR_SURR_TOL 1e-10     /* optimality-gap bound that ends the search */
+#define OR_SURR_CMAX 2.0
+#define OR_ADAM_BETA1 0.9
+#define OR_ADAM_BETA2 0.999
+#define OR_ADAM_EPS 1e-8
+
+/* log(hi / lo) of the Theorem 1 bound over nq points G[q][6] = kappa Ghat
+ * (00, 11, 22, 01, 02, 12) for the scalings mu[3]; lo/hi may be NULL. */
+double or_surr_bound(int nq, const double *G, const double *mu, double *lo, double *hi);
+/* kappa Ghat at the (p+1)^3 Gauss points of every cell (unweighted,
+ * G[cell][q][6]) and the averaged surrogate mubar[cell][3]. */
+int or_surr_cell_ghat(int p, int ncell, const double *jac, const double *kappa, double *G,
+                      double *mubar);
+/* Labels from the cells' full quadrature data (jac/kappa as or_create):
+ * mubar (averaged surrogate), cstar = log(mu_opt / mubar) with mu_opt the
+ * minimiser of the bound ratio (ellipsoid method on the convex ratio in
+ * log mu, surrogate.c) scaled so that lo * hi = 1, and the
+ * ratios F0 = log(hi/lo) at mubar and F1 at mu*.  Arrays of 3, 3, 1, 1
+ * doubles per cell. */
+int or_surr_label(int p, int ncell, const double *jac, const double *kappa, double *mubar,
+                  double *cstar, double *F0, double *F1);
+/* Network inputs from s27[cell][27][10] = (kappa, J row-major) at the
+ * 3x3x3 Gauss points (x fastest): per point, log kappa minus its cell
+ * average, log(Ghat_aa / nu_a) with nu the 27-point averaged surrogate,
+ * and the correlations Ghat_ab / sqrt(Ghat_aa Ghat_bb) for ab = 01, 02, 12
+ * (Ghat here includes kappa).  feat[cell][189]. */
+int or_surr_features(int ncell, const double *s27, double *feat);
+/* Network 189 -> 64 (tanh) -> 64 (tanh) -> 3 (linear); parameters packed
+ * W1[64][189], b1[64], W2[64][64], b2[64], W3[3][64], b3[3]. */
+void or_mlp_forward(int ncell, const double *params, const double *feat, double *c);
+/* mean-squared loss (1 / (2 ncell)) sum (c - label)^2 and its gradient
+ * (grad may be NULL). */
+double or_mlp_loss_grad(int ncell, const double *params, const double *feat, const double *label,
+                        double *grad);
+/* one Adam step t >= 1 (beta1, beta2, eps above). */
+void or_mlp_adam(int nparam, double *params, const double *grad, double *m, double *v, int t,
+                 double lr);
+/* mu = mubar exp(c) per cell, or mubar where any c is non-finite or
+ * |c| > OR_SURR_CMAX; returns the number of such fallback cells. */
+int or_surr_apply(int ncell, const double *mubar, const double *c, double *mu);
+
 #ifdef __cplusplus
 }
 #endif

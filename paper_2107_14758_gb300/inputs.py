@@ -126,6 +126,36 @@ def deformed_jacobians(n, p, amp=0.1, vertices=None):
     return jac, pts
 
 
+def deformed_samples27(n, seed, amp=0.1, vertices=None):
+    """kappa and the Jacobian at the 3 x 3 x 3 Gauss points of every cell of the
+    deformed mesh (x fastest; cells x fastest): [cell, 27, 10] = (kappa, J
+    row-major).  The same map and field as deformed_jacobians / kappa_field."""
+    xv, yv, zv = vertices if vertices is not None else uniform_vertices(n)
+    nx, ny, nz = len(xv) - 1, len(yv) - 1, len(zv) - 1
+    xg, _ = _leg.leggauss(3)
+    out = np.zeros((nx * ny * nz, 27, 10))
+    allpts = np.zeros((nx * ny * nz, 27, 3))
+    for cz in range(nz):
+        for cy in range(ny):
+            for cx in range(nx):
+                e = cx + nx * (cy + ny * cz)
+                h = np.array([xv[cx + 1] - xv[cx], yv[cy + 1] - yv[cy], zv[cz + 1] - zv[cz]])
+                X = xv[cx] + 0.5 * (1 + xg) * h[0]
+                Y = yv[cy] + 0.5 * (1 + xg) * h[1]
+                Z = zv[cz] + 0.5 * (1 + xg) * h[2]
+                ZZ, YY, XX = np.meshgrid(Z, Y, X, indexing="ij")
+                XX, YY, ZZ = XX.ravel(), YY.ravel(), ZZ.ravel()
+                dgx, dgy, dgz = _deform_grad(XX, YY, ZZ, amp)
+                for r in range(3):
+                    out[e, :, 1 + 3 * r + 0] = ((r == 0) + dgx) * 0.5 * h[0]
+                    out[e, :, 1 + 3 * r + 1] = ((r == 1) + dgy) * 0.5 * h[1]
+                    out[e, :, 1 + 3 * r + 2] = ((r == 2) + dgz) * 0.5 * h[2]
+                px, py, pz = _deform(XX, YY, ZZ, amp)
+                allpts[e, :, 0], allpts[e, :, 1], allpts[e, :, 2] = px, py, pz
+    out[:, :, 0] = kappa_field(allpts, seed)
+    return out
+
+
 def kappa_field(pts, seed, modes=8, kmax=8):
     """kappa = exp(G) with G a random Fourier sum of unit variance."""
     rng = np.random.default_rng(seed)
@@ -157,9 +187,32 @@ def workload(name, seed=None):
         p = 8
         xv, yv, zv = uniform_vertices(12)
         jac, pts = deformed_jacobians(12, p)
-        kap = kappa_field(pts, 4 if seed is None else seed)
-        return dict(name=name, p=p, xv=xv, yv=yv, zv=zv, jac=jac, kappa=kap, rhs="normal", seed=4)
+        sd = 4 if seed is None else seed
+        kap = kappa_field(pts, sd)
+        return dict(name=name, p=p, xv=xv, yv=yv, zv=zv, jac=jac, kappa=kap, samples27=deformed_samples27(12, sd),
+                    rhs="normal", seed=4)
     raise KeyError(name)
+
+
+def deformed_problem(n, p, seed, amp=0.1):
+    """Deformed uniform n^3 mesh with kappa = exp(G) (seeded), as q8_deformed12:
+    jac and kappa at the (p+1)^3 Gauss points and the 27-point samples."""
+    xv, yv, zv = uniform_vertices(n)
+    jac, pts = deformed_jacobians(n, p, amp)
+    return dict(name="deformed%d_q%d_s%d" % (n, p, seed), p=p, xv=xv, yv=yv, zv=zv, jac=jac,
+                kappa=kappa_field(pts, seed), samples27=deformed_samples27(n, seed, amp), rhs="normal", seed=seed)
+
+
+def mlp_init(seed, nin=189, nh=64, nout=3):
+    """Initial network weights (float32, packed W1, b1, W2, b2, W3, b3):
+    W ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)), the output layer scaled by 0.1,
+    biases 0."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fo, fi, scale in ((nh, nin, 1.0), (nh, nh, 1.0), (nout, nh, 0.1)):
+        parts.append(rng.uniform(-1.0, 1.0, fo * fi) * scale / np.sqrt(fi))
+        parts.append(np.zeros(fo))
+    return np.concatenate(parts).astype(np.float32)
 
 
 def batch_problems(count=64, seed0=1000):
