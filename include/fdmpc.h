@@ -69,9 +69,14 @@ typedef struct {
 } fdm_mesh;
 
 /* Coefficients (HOST, optional, copied): kappa at the same Gauss points as
- * jac ((p+1)^3 nx ny nz doubles); NULL = kappa == 1.  Curved cells only. */
+ * jac ((p+1)^3 nx ny nz doubles); NULL = kappa == 1.  Curved cells only.
+ * samples27 (HOST, optional, copied): inputs of the learned surrogate,
+ * kappa and J (row-major) at the 3x3x3 Gauss-Legendre points of every cell
+ * (points x fastest, cells x fastest): 270 nx ny nz doubles, kappa > 0;
+ * curved cells only. */
 typedef struct {
   const double *kappa_q;
+  const double *samples27;
 } fdm_coeff;
 
 typedef struct {
@@ -183,6 +188,52 @@ void fdm_batch_destroy(fdm_batch *batch);
  * scalings, cells x fastest) and refactors every patch. */
 int fdm_surrogate_load(fdm_ctx *ctx, const double *mu_host, void *stream);
 
+/* ---- learned separable surrogate (Section 2.7, Theorem 1) ----
+ * Not in the paper: the paper's surrogate on curved cells is the cell
+ * average mu_avg of kappa Ghat_jj.  Here a network predicts a per-direction
+ * correction c per cell, mu = mu_avg exp(c), from the 27 samples of
+ * fdm_coeff.samples27.  Inputs (189 per cell, per sample point): log kappa
+ * minus its cell average; log(M_aa / nu_a), with M = kappa Ghat and nu the
+ * 27-point average of M_aa; and the correlations M_ab / sqrt(M_aa M_bb) for
+ * ab = 01, 02, 12.  Network: 189 -> 64 (tanh) -> 64 (tanh) -> 3 (linear),
+ * FP32 weights packed as W1[64][189], b1[64], W2[64][64], b2[64], W3[3][64],
+ * b3[3] (FDM_MLP_NPARAM floats; W[out][in]).  Training label per cell:
+ * c* = log(mu_opt / mu_avg) with mu_opt the scalings that minimise the ratio hi/lo
+ * of Theorem 1's bound lo a~ <= a <= hi a~ (the extreme eigenvalues of
+ * diag(mu)^{-1/2} M_q diag(mu)^{-1/2} over the cell's (p+1)^3 Gauss points),
+ * found by the central-cut ellipsoid method on the ratio, which is convex in
+ * log mu (start mu_avg, disc radius 6 in log mu, at most 600 steps, optimality
+ * gap bound 1e-10), and scaled so that lo hi = 1.  Loss:
+ * (1/(2 N)) sum over the N cells of |c - c*|^2.  All calls need a context set
+ * up with curved cells and samples27 (else FDM_EINVAL). */
+#define FDM_MLP_NPARAM 16515
+
+/* Loss and gradient (HOST, FDM_MLP_NPARAM floats) at the weights w (HOST)
+ * over the cells of ctx, computed by the library's FP32 training kernels.
+ * loss (HOST, may be NULL).  Synchronises `stream`. */
+int fdm_surrogate_grad(fdm_ctx *ctx, const float *w, float *grad, double *loss, void *stream);
+
+/* Trains the network on every cell of the k contexts (all on the current
+ * device): `steps` full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8,
+ * bias-corrected, step size lr, decoupled weight decay weight_decay >= 0)
+ * from w_init (HOST).  w_out (HOST) receives the weights, loss_hist (HOST,
+ * steps + 1 doubles, may be NULL) the loss before each step and after the
+ * last.  Device scratch is allocated and freed inside the call.
+ * Synchronises `stream`. */
+int fdm_surrogate_train(int k, fdm_ctx *const *ctxs, const float *w_init, int steps, double lr,
+                        double weight_decay, float *w_out, double *loss_hist, void *stream);
+
+/* Inference: mu = mu_avg exp(c) per cell with the network w (HOST); a cell
+ * whose outputs are not finite or exceed 2 in magnitude keeps mu_avg.  Then
+ * every patch is refactored and omega re-estimated (unless fixed).  With
+ * judge = 1 the averaged surrogate judges the result: if the Lanczos
+ * estimate lmax/lmin of P_ASM^{-1} A grew, mu_avg is restored (needs omega
+ * not fixed).  nfallback (HOST, may be NULL): number of fallback cells;
+ * kept (HOST, may be NULL): 1 if the network's scalings were kept.
+ * Synchronises `stream`. */
+int fdm_surrogate_apply(fdm_ctx *ctx, const float *w, int judge, int *nfallback, int *kept,
+                        void *stream);
+
 /* ---- introspection ---- */
 #define FDM_Q_NDOF 1         /* int64: number of grid nodes */
 #define FDM_Q_OMEGA 2        /* double: damping */
@@ -205,6 +256,12 @@ int fdm_surrogate_load(fdm_ctx *ctx, const double *mu_host, void *stream);
                                   and of one asm_apply (FP64, FP32) */
 #define FDM_Q_STATUS 18        /* int32: device status word (1 = a bounded wait ran out); reading
                                   it clears it; synchronises the device */
+#define FDM_Q_SURR_FEATURES 19 /* float[189*ncell]: network inputs */
+#define FDM_Q_SURR_LABELS 20   /* double[3*ncell]: labels c* (computed on first use) */
+#define FDM_Q_SURR_BOUNDS 21   /* double[3*ncell]: per cell log(hi/lo) of Theorem 1's bound at mu_avg,
+                                  at mu* (NaN without samples27) and at the current mu */
+#define FDM_Q_MUBAR 22         /* double[3*ncell]: averaged surrogate mu_avg (curved cells) */
+#define FDM_Q_SURR_OUTPUT 23   /* float[3*ncell]: network outputs c of the last fdm_surrogate_apply */
 /* timers of FDM_Q_KERNEL_TIMES */
 #define FDM_T_RESTRICT 0  /* basis change to the FDM basis */
 #define FDM_T_PATCH 1     /* patch gather + condense + triangular solves + back-substitution */

@@ -12,6 +12,7 @@
 
 namespace fdm {
 [[noreturn]] void fail(int code, const std::string &msg) { throw Error{code, msg}; }
+static_assert(MLP_NPARAM == FDM_MLP_NPARAM, "network size of the public header");
 }  // namespace fdm
 
 using namespace fdm;
@@ -71,6 +72,16 @@ struct fdm_ctx {
   double *partial = nullptr, *dots = nullptr, *sc = nullptr;
   double omega = 1.0, lmin = 0.0, lmax = 0.0;
   double t_setup[4] = {0, 0, 0, 0};
+  // learned surrogate (curved cells)
+  double *mubar = nullptr;      // averaged surrogate of Section 2.7, [ncell][3]
+  double *wq64 = nullptr;       // Gauss weights (n)
+  float *feat = nullptr;        // network inputs [ncell][189] (with samples27)
+  double *cstar = nullptr, *F0 = nullptr, *F1 = nullptr;  // labels and bound ratios (on first use)
+  float *label32 = nullptr;
+  float *surr_c = nullptr;      // network outputs of the last fdm_surrogate_apply
+  int *d_count = nullptr;
+  double *Fcur = nullptr;       // bound ratios at the current mu (queries)
+  double kappa_avg = 0.0;       // Lanczos lmax / lmin with the averaged surrogate (0: not run)
   // instrumentation: launch counter and optional per-group CUDA-event timers
   int64_t launches = 0;
   std::vector<cudaEvent_t> ev_pool;
@@ -336,6 +347,20 @@ void setup_geometry(fdm_ctx *c, const fdm_mesh *mesh, const fdm_coeff *coeff) {
     std::vector<float> Gf(Gw.begin(), Gw.end()), df(dw.begin(), dw.end());
     c->Gw32 = c->upload(Gf);
     c->detw32 = c->upload(df);
+    c->mubar = c->upload(mu);
+    c->wq64 = c->upload(c->basis.wq);
+    if (coeff && coeff->samples27) {
+      for (size_t i = 0; i < (size_t)ncell * 27; ++i)
+        if (!(coeff->samples27[10 * i] > 0.0)) fail(FDM_EINVAL, "samples27: kappa must be positive");
+      std::vector<double> s27(coeff->samples27, coeff->samples27 + (size_t)ncell * 270);
+      double *d_s27 = c->upload(s27);
+      c->feat = c->alloc<float>((size_t)ncell * MLP_NIN);
+      const Basis1D b3 = make_basis(2);  // its Gauss rule has 3 points
+      launch_surr_features(ncell, d_s27, b3.wq.data(), c->feat, 0);
+      FDM_CUDA(cudaDeviceSynchronize());
+    }
+  } else if (coeff && coeff->samples27) {
+    fail(FDM_EINVAL, "samples27 needs curved cells (mesh->jac)");
   }
   c->mu = c->upload(mu);
   (void)p;
@@ -646,6 +671,44 @@ void lanczos_omega(fdm_ctx *c, const double *start_host, cudaStream_t st) {
   c->omega = 2.0 / ((1.0 + alpha) * c->lmax + (1.0 - alpha) * c->lmin);
 }
 
+// ---- learned surrogate helpers
+void need_surrogate_data(const fdm_ctx *c) {
+  if (!c->general || !c->feat) fail(FDM_EINVAL, "the learned surrogate needs curved cells and samples27");
+}
+
+// per-cell Theorem 1 labels, computed once per context
+void ensure_labels(fdm_ctx *c, cudaStream_t st) {
+  if (c->cstar) return;
+  const int ncell = c->g.ncell;
+  double *cs = c->alloc<double>(3 * (size_t)ncell);
+  c->F0 = c->alloc<double>(ncell);
+  c->F1 = c->alloc<double>(ncell);
+  c->label32 = c->alloc<float>(3 * (size_t)ncell);
+  launch_surr_label(ncell, c->g.n, c->Gw64, c->wq64, c->mubar, cs, c->F0, c->F1, st);
+  launch_convert<double, float>(3 * (int64_t)ncell, cs, c->label32, st);
+  FDM_CUDA(cudaStreamSynchronize(st));
+  c->launches += 2;
+  c->cstar = cs;
+}
+
+// device buffers of one training run, released on every exit path
+struct DevScratch {
+  std::vector<void *> p;
+  template <typename T>
+  T *get(size_t n) {
+    void *ptr = nullptr;
+    if (cudaMalloc(&ptr, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      fail(FDM_ENOMEM, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed");
+    }
+    p.push_back(ptr);
+    return static_cast<T *>(ptr);
+  }
+  ~DevScratch() {
+    for (void *x : p) cudaFree(x);
+  }
+};
+
 int handle(fdm_ctx *c, const Error &e) {
   if (c) c->err = e.msg;
   g_last_error = e.msg;
@@ -730,7 +793,10 @@ int fdm_setup(const fdm_mesh *mesh, int p, const fdm_coeff *coeff, const fdm_opt
     setup_coarse(c, st);
     double t3 = now_s();
     if (c->opt.omega > 0.0) c->omega = c->opt.omega;
-    else lanczos_omega(c, c->opt.lanczos_start, st);
+    else {
+      lanczos_omega(c, c->opt.lanczos_start, st);
+      c->kappa_avg = c->lmax / c->lmin;
+    }
     FDM_CUDA(cudaStreamSynchronize(st));
     FDM_CUDA(cudaGetLastError());
     double t4 = now_s();
@@ -917,6 +983,122 @@ int fdm_surrogate_load(fdm_ctx *c, const double *mu_host, void *stream) {
   return FDM_OK;
 }
 
+int fdm_surrogate_grad(fdm_ctx *c, const float *w_host, float *grad_host, double *loss, void *stream) {
+  if (!c || !w_host || !grad_host) return FDM_EINVAL;
+  try {
+    need_surrogate_data(c);
+    cudaStream_t st = (cudaStream_t)stream;
+    ensure_labels(c, st);
+    const int ncell = c->g.ncell, nblk = mlp_blocks(ncell);
+    DevScratch s;
+    float *P = s.get<float>(MLP_NPARAM), *g = s.get<float>(MLP_NPARAM), *out = s.get<float>(3 * (size_t)ncell);
+    float *partial = s.get<float>((size_t)nblk * MLP_NPARAM), *lossp = s.get<float>(nblk);
+    double *dl = s.get<double>(1);
+    FDM_CUDA(cudaMemcpyAsync(P, w_host, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice, st));
+    launch_mlp(ncell, P, c->feat, c->label32, out, partial, lossp, st);
+    launch_mlp_reduce(nblk, partial, lossp, g, dl, st);
+    c->launches += 2;
+    FDM_CUDA(cudaMemcpyAsync(grad_host, g, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost, st));
+    double l = 0.0;
+    FDM_CUDA(cudaMemcpyAsync(&l, dl, sizeof(double), cudaMemcpyDeviceToHost, st));
+    FDM_CUDA(cudaStreamSynchronize(st));
+    if (loss) *loss = l;
+  } catch (const Error &e) { return handle(c, e); }
+  return FDM_OK;
+}
+
+int fdm_surrogate_train(int k, fdm_ctx *const *ctxs, const float *w_init, int steps, double lr, double weight_decay,
+                        float *w_out, double *loss_hist, void *stream) {
+  if (k < 1 || !ctxs || !w_init || !w_out || steps < 0 || !(lr > 0.0) || !(weight_decay >= 0.0)) {
+    g_last_error = "fdm_surrogate_train: invalid arguments";
+    return FDM_EINVAL;
+  }
+  fdm_ctx *c0 = ctxs[0];
+  try {
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t ntot = 0;
+    for (int i = 0; i < k; ++i) {
+      if (!ctxs[i]) fail(FDM_EINVAL, "fdm_surrogate_train: null context");
+      need_surrogate_data(ctxs[i]);
+      ensure_labels(ctxs[i], st);
+      ntot += ctxs[i]->g.ncell;
+    }
+    if (ntot > (int64_t)1 << 26) fail(FDM_EINVAL, "fdm_surrogate_train: too many cells");
+    const int ncell = (int)ntot, nblk = mlp_blocks(ncell);
+    DevScratch s;
+    float *X = s.get<float>((size_t)ncell * MLP_NIN), *Y = s.get<float>(3 * (size_t)ncell);
+    int64_t off = 0;
+    for (int i = 0; i < k; ++i) {  // the training set: every cell of every context
+      const int nc = ctxs[i]->g.ncell;
+      FDM_CUDA(cudaMemcpyAsync(X + off * MLP_NIN, ctxs[i]->feat, sizeof(float) * MLP_NIN * nc,
+                               cudaMemcpyDeviceToDevice, st));
+      FDM_CUDA(cudaMemcpyAsync(Y + off * 3, ctxs[i]->label32, sizeof(float) * 3 * nc, cudaMemcpyDeviceToDevice,
+                               st));
+      off += nc;
+    }
+    float *P = s.get<float>(MLP_NPARAM), *g = s.get<float>(MLP_NPARAM), *m = s.get<float>(MLP_NPARAM),
+          *v = s.get<float>(MLP_NPARAM), *out = s.get<float>(3 * (size_t)ncell);
+    float *partial = s.get<float>((size_t)nblk * MLP_NPARAM), *lossp = s.get<float>(nblk);
+    double *hist = s.get<double>((size_t)steps + 1);
+    FDM_CUDA(cudaMemcpyAsync(P, w_init, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice, st));
+    FDM_CUDA(cudaMemsetAsync(m, 0, sizeof(float) * MLP_NPARAM, st));
+    FDM_CUDA(cudaMemsetAsync(v, 0, sizeof(float) * MLP_NPARAM, st));
+    // full-batch Adam: loss and gradient over all cells, then one update
+    for (int t = 1; t <= steps; ++t) {
+      launch_mlp(ncell, P, X, Y, out, partial, lossp, st);
+      launch_mlp_reduce(nblk, partial, lossp, g, hist + (t - 1), st);
+      launch_adam(P, g, m, v, t, lr, weight_decay, st);
+    }
+    launch_mlp(ncell, P, X, Y, out, partial, lossp, st);
+    launch_mlp_reduce(nblk, partial, lossp, g, hist + steps, st);
+    c0->launches += 3 * (int64_t)steps + 2;
+    FDM_CUDA(cudaMemcpyAsync(w_out, P, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost, st));
+    std::vector<double> h((size_t)steps + 1);
+    FDM_CUDA(cudaMemcpyAsync(h.data(), hist, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
+    FDM_CUDA(cudaStreamSynchronize(st));
+    if (loss_hist) std::copy(h.begin(), h.end(), loss_hist);
+  } catch (const Error &e) { return handle(c0, e); }
+  return FDM_OK;
+}
+
+int fdm_surrogate_apply(fdm_ctx *c, const float *w_host, int judge, int *nfallback, int *kept, void *stream) {
+  if (!c || !w_host) return FDM_EINVAL;
+  try {
+    need_surrogate_data(c);
+    if (judge && !(c->kappa_avg > 0.0))
+      fail(FDM_EINVAL, "fdm_surrogate_apply: judging needs the Lanczos estimate (omega must not be fixed)");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ncell = c->g.ncell;
+    if (!c->surr_c) c->surr_c = c->alloc<float>(3 * (size_t)ncell);
+    if (!c->d_count) c->d_count = c->alloc<int>(4);
+    DevScratch s;
+    float *P = s.get<float>(MLP_NPARAM);
+    FDM_CUDA(cudaMemcpyAsync(P, w_host, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice, st));
+    FDM_CUDA(cudaMemsetAsync(c->d_count, 0, sizeof(int), st));
+    launch_mlp(ncell, P, c->feat, nullptr, c->surr_c, nullptr, nullptr, st);
+    launch_surr_apply(ncell, c->surr_c, c->mubar, c->mu, c->d_count, st);
+    c->launches += 2;
+    int nf = 0;
+    FDM_CUDA(cudaMemcpyAsync(&nf, c->d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    factor_all(c, st);
+    if (c->opt.omega <= 0.0) lanczos_omega(c, c->opt.lanczos_start, st);
+    FDM_CUDA(cudaStreamSynchronize(st));
+    int keep = 1;
+    if (judge && c->lmax / c->lmin > c->kappa_avg) {
+      // the averaged surrogate judges: keep the network's scalings only if the
+      // Lanczos estimate of the preconditioned condition number did not grow
+      keep = 0;
+      FDM_CUDA(cudaMemcpyAsync(c->mu, c->mubar, 3 * sizeof(double) * ncell, cudaMemcpyDeviceToDevice, st));
+      factor_all(c, st);
+      lanczos_omega(c, c->opt.lanczos_start, st);
+      FDM_CUDA(cudaStreamSynchronize(st));
+    }
+    if (nfallback) *nfallback = nf;
+    if (kept) *kept = keep;
+  } catch (const Error &e) { return handle(c, e); }
+  return FDM_OK;
+}
+
 int fdm_query(fdm_ctx *c, int what, void *out, size_t *len) {
   if (!c || !out || !len) return FDM_EINVAL;
   try {
@@ -1008,6 +1190,55 @@ int fdm_query(fdm_ctx *c, int what, void *out, size_t *len) {
         break;
       }
       case FDM_Q_SETUP_SECONDS: put(c->t_setup, sizeof c->t_setup); break;
+      case FDM_Q_SURR_FEATURES: {
+        need_surrogate_data(c);
+        std::vector<float> h((size_t)c->g.ncell * MLP_NIN);
+        FDM_CUDA(cudaMemcpy(h.data(), c->feat, h.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        put(h.data(), h.size() * sizeof(float));
+        break;
+      }
+      case FDM_Q_SURR_LABELS: {
+        need_surrogate_data(c);
+        ensure_labels(c, 0);
+        std::vector<double> h(3 * (size_t)c->g.ncell);
+        FDM_CUDA(cudaMemcpy(h.data(), c->cstar, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        put(h.data(), h.size() * sizeof(double));
+        break;
+      }
+      case FDM_Q_SURR_BOUNDS: {
+        if (!c->general) fail(FDM_EINVAL, "bounds need curved cells");
+        const int ncell = c->g.ncell;
+        std::vector<double> h(3 * (size_t)ncell);
+        if (!c->Fcur) c->Fcur = c->alloc<double>(ncell);
+        double *Fc = c->Fcur;
+        if (c->feat) {
+          ensure_labels(c, 0);
+          FDM_CUDA(cudaMemcpy(h.data(), c->F0, ncell * sizeof(double), cudaMemcpyDeviceToHost));
+          FDM_CUDA(cudaMemcpy(h.data() + ncell, c->F1, ncell * sizeof(double), cudaMemcpyDeviceToHost));
+        } else {
+          launch_surr_bound(ncell, c->g.n, c->Gw64, c->wq64, c->mubar, Fc, 0);
+          FDM_CUDA(cudaMemcpy(h.data(), Fc, ncell * sizeof(double), cudaMemcpyDeviceToHost));
+          for (int e = 0; e < ncell; ++e) h[ncell + e] = NAN;
+        }
+        launch_surr_bound(ncell, c->g.n, c->Gw64, c->wq64, c->mu, Fc, 0);
+        FDM_CUDA(cudaMemcpy(h.data() + 2 * (size_t)ncell, Fc, ncell * sizeof(double), cudaMemcpyDeviceToHost));
+        put(h.data(), h.size() * sizeof(double));
+        break;
+      }
+      case FDM_Q_MUBAR: {
+        if (!c->general) fail(FDM_EINVAL, "the averaged surrogate is defined on curved cells");
+        std::vector<double> h(3 * (size_t)c->g.ncell);
+        FDM_CUDA(cudaMemcpy(h.data(), c->mubar, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        put(h.data(), h.size() * sizeof(double));
+        break;
+      }
+      case FDM_Q_SURR_OUTPUT: {
+        if (!c->surr_c) fail(FDM_EINVAL, "no network output yet (call fdm_surrogate_apply)");
+        std::vector<float> h(3 * (size_t)c->g.ncell);
+        FDM_CUDA(cudaMemcpy(h.data(), c->surr_c, h.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        put(h.data(), h.size() * sizeof(float));
+        break;
+      }
       case FDM_Q_STATUS: {
         int v = 0;
         FDM_CUDA(cudaMemcpy(&v, c->status, sizeof(int), cudaMemcpyDeviceToHost));

@@ -121,4 +121,26 @@ void launch_pcg_update_xr(int64_t n, const double *sc, const double *d, const do
 void launch_pcg_update_d(int64_t n, const double *sc, const double *z, double *d, cudaStream_t st);
 void launch_pcg_scalars(int which, double *sc, const double *dots, cudaStream_t st);
 
+// learned separable surrogate: network 189 -> 64 -> 64 -> 3 (FP32 weights)
+constexpr int MLP_NIN = 189, MLP_NH = 64, MLP_NOUT = 3;
+constexpr int MLP_NPARAM = MLP_NH * MLP_NIN + MLP_NH + MLP_NH * MLP_NH + MLP_NH + MLP_NOUT * MLP_NH + MLP_NOUT;
+constexpr int SURR_MAXIT = 600;       // ellipsoid steps of the label search
+constexpr double SURR_RADIUS = 6.0;   // initial disc of the label search (log mu)
+constexpr double SURR_TOL = 1e-10;    // optimality-gap bound that ends the search
+constexpr float SURR_CMAX = 2.0f;   // |c| above this falls back to the averaged surrogate
+constexpr float ADAM_BETA1 = 0.9f, ADAM_BETA2 = 0.999f, ADAM_EPS = 1e-8f;
+void launch_surr_features(int ncell, const double *s27, const double w3[3], float *feat, cudaStream_t st);
+void launch_surr_label(int ncell, int n, const double *Gw, const double *wq, const double *mubar, double *cstar,
+                       double *F0, double *F1, cudaStream_t st);
+void launch_surr_bound(int ncell, int n, const double *Gw, const double *wq, const double *mu, double *F,
+                       cudaStream_t st);
+int mlp_blocks(int ncell);
+// forward (label == nullptr) or forward + loss + per-CTA partial gradient
+void launch_mlp(int ncell, const float *P, const float *feat, const float *label, float *out, float *partial,
+                float *lossp, cudaStream_t st);
+void launch_mlp_reduce(int nblk, const float *partial, const float *lossp, float *grad, double *loss,
+                       cudaStream_t st);
+void launch_adam(float *P, const float *g, float *m, float *v, int t, double lr, double wd, cudaStream_t st);
+void launch_surr_apply(int ncell, const float *c, const double *mubar, double *mu, int *nfall, cudaStream_t st);
+
 }  // namespace fdm

@@ -21,7 +21,9 @@ FDM_PC_NONE, FDM_PC_ASM, FDM_PC_VCYCLE = 0, 1, 2
 FDM_SURR_AVERAGED, FDM_SURR_EXTERNAL = 0, 1
 (FDM_Q_NDOF, FDM_Q_OMEGA, FDM_Q_LAMBDA, FDM_Q_MU, FDM_Q_NPATCH, FDM_Q_PATCH_CLASS, FDM_Q_CLASS_INFO,
  FDM_Q_GAMMA_ORDER, FDM_Q_FACTOR_NNZ, FDM_Q_PATTERN, FDM_Q_FACTOR, FDM_Q_BASIS, FDM_Q_FACTOR_BYTES,
- FDM_Q_SETUP_SECONDS, FDM_Q_KERNEL_TIMES, FDM_Q_LAUNCHES, FDM_Q_ALGO_BYTES, FDM_Q_STATUS) = range(1, 19)
+ FDM_Q_SETUP_SECONDS, FDM_Q_KERNEL_TIMES, FDM_Q_LAUNCHES, FDM_Q_ALGO_BYTES, FDM_Q_STATUS,
+ FDM_Q_SURR_FEATURES, FDM_Q_SURR_LABELS, FDM_Q_SURR_BOUNDS, FDM_Q_MUBAR, FDM_Q_SURR_OUTPUT) = range(1, 24)
+FDM_MLP_NPARAM = 16515
 TIMERS = ("restrict", "patch", "interp", "op64", "op32", "coarse", "vec")
 
 
@@ -32,7 +34,7 @@ class fdm_mesh(C.Structure):
 
 
 class fdm_coeff(C.Structure):
-    _fields_ = [("kappa_q", C.POINTER(C.c_double))]
+    _fields_ = [("kappa_q", C.POINTER(C.c_double)), ("samples27", C.POINTER(C.c_double))]
 
 
 class fdm_options(C.Structure):
@@ -79,6 +81,10 @@ def load():
     L.fdm_batch_destroy.argtypes = [vp]
     L.fdm_batch_destroy.restype = None
     L.fdm_surrogate_load.argtypes = [vp, dp, vp]
+    fp = C.POINTER(C.c_float)
+    L.fdm_surrogate_grad.argtypes = [vp, fp, fp, dp, vp]
+    L.fdm_surrogate_train.argtypes = [C.c_int, C.POINTER(vp), fp, C.c_int, C.c_double, C.c_double, fp, dp, vp]
+    L.fdm_surrogate_apply.argtypes = [vp, fp, C.c_int, ip, ip, vp]
     L.fdm_query.argtypes = [vp, C.c_int, vp, C.POINTER(C.c_size_t)]
     L.fdm_last_error.argtypes = [vp]
     L.fdm_last_error.restype = C.c_char_p
@@ -180,6 +186,44 @@ def fdm_surrogate_load(ctx, mu, stream=None):
     _check(load().fdm_surrogate_load(ctx, _dptr(mu), _stream(stream)), ctx)
 
 
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def _weights(w):
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    assert w.size == FDM_MLP_NPARAM, "network weights: %d floats" % FDM_MLP_NPARAM
+    return w
+
+
+def fdm_surrogate_grad(ctx, w, stream=None):
+    """(gradient float32[FDM_MLP_NPARAM], loss) of the surrogate network."""
+    w = _weights(w)
+    g = np.zeros(FDM_MLP_NPARAM, dtype=np.float32)
+    loss = C.c_double()
+    _check(load().fdm_surrogate_grad(ctx, _fptr(w), _fptr(g), C.byref(loss), _stream(stream)), ctx)
+    return g, loss.value
+
+
+def fdm_surrogate_train(ctxs, w_init, steps, lr, weight_decay=0.0, stream=None):
+    """Trains on every cell of the contexts; returns (weights, loss history)."""
+    w = _weights(w_init)
+    out = np.zeros(FDM_MLP_NPARAM, dtype=np.float32)
+    hist = np.zeros(steps + 1)
+    arr = (C.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    _check(load().fdm_surrogate_train(len(ctxs), arr, _fptr(w), steps, lr, weight_decay, _fptr(out), _dptr(hist),
+                                      _stream(stream)), ctxs[0])
+    return out, hist
+
+
+def fdm_surrogate_apply(ctx, w, judge=1, stream=None):
+    """Inference + refactorisation; returns (fallback cells, kept)."""
+    w = _weights(w)
+    nf = C.c_int(); kept = C.c_int()
+    _check(load().fdm_surrogate_apply(ctx, _fptr(w), judge, C.byref(nf), C.byref(kept), _stream(stream)), ctx)
+    return nf.value, bool(kept.value)
+
+
 def fdm_query(ctx, what, out, arg=None):
     """Copies quantity `what` into the numpy array `out` (HOST); returns bytes."""
     if arg is not None:
@@ -203,7 +247,7 @@ def fdm_destroy(ctx):
 class Context:
     """Owns one set-up problem (a fdm_ctx) and its host inputs."""
 
-    def __init__(self, p, xv, yv, zv, jac=None, kappa=None, precision=FDM_PREC_FP32, pc=FDM_PC_VCYCLE,
+    def __init__(self, p, xv, yv, zv, jac=None, kappa=None, samples27=None, precision=FDM_PREC_FP32, pc=FDM_PC_VCYCLE,
                  omega=0.0, lanczos_start=None, lanczos_steps=20, flexible_beta=-1, kernel_timing=0,
                  patch_ctas_per_sm=0, patch_threads=0, patch_kernel=0, stream_buffers=0, stream_buffer_kb=0,
                  inject_stall=0, wait_timeout_s=1.0, patch_prefetch=0, stream=None):
@@ -220,6 +264,10 @@ class Context:
             k = np.ascontiguousarray(kappa, dtype=np.float64)
             self._keep.append(k)
             coeff.kappa_q = _dptr(k)
+        if samples27 is not None:
+            s27 = np.ascontiguousarray(samples27, dtype=np.float64)
+            self._keep.append(s27)
+            coeff.samples27 = _dptr(s27)
         opt = fdm_default_options()
         opt.precision, opt.pc, opt.omega, opt.lanczos_steps = precision, pc, omega, lanczos_steps
         opt.flexible_beta = flexible_beta
@@ -285,6 +333,34 @@ class Context:
 
     def surrogate_load(self, mu):
         fdm_surrogate_load(self.h, mu)
+
+    def surrogate_grad(self, w):
+        return fdm_surrogate_grad(self.h, w)
+
+    def surrogate_apply(self, w, judge=1):
+        return fdm_surrogate_apply(self.h, w, judge)
+
+    def surrogate_features(self):
+        return self.query(FDM_Q_SURR_FEATURES, np.float32, 189 * self.ncell).reshape(self.ncell, 189)
+
+    def surrogate_labels(self):
+        return self.query(FDM_Q_SURR_LABELS, np.float64, 3 * self.ncell).reshape(self.ncell, 3)
+
+    def surrogate_bounds(self):
+        """(F at mu_avg, F at the label, F at the current mu), F = log(hi/lo) per cell."""
+        return self.query(FDM_Q_SURR_BOUNDS, np.float64, 3 * self.ncell).reshape(3, self.ncell)
+
+    def mubar(self):
+        return self.query(FDM_Q_MUBAR, np.float64, 3 * self.ncell).reshape(self.ncell, 3)
+
+    def mu(self):
+        return self.query(FDM_Q_MU, np.float64, 3 * self.ncell).reshape(self.ncell, 3)
+
+    def surrogate_output(self):
+        return self.query(FDM_Q_SURR_OUTPUT, np.float32, 3 * self.ncell).reshape(self.ncell, 3)
+
+    def lanczos_extremes(self):
+        return tuple(self.query(FDM_Q_LAMBDA, np.float64, 2))
 
     def query(self, what, dtype, count, arg=None):
         out = np.zeros(count, dtype=dtype)

@@ -1,0 +1,199 @@
+"""GPU parity of the learned separable surrogate (Section 2.7, Theorem 1)
+against the FP64 oracle, through the C-ABI.
+
+Tolerances: network inputs <= 1e-6 (stored in FP32); bound ratios at the
+averaged surrogate <= 1e-12 relative; label searches reach the same optimum
+(<= 1e-8; the minimiser itself is not unique where the ratio is flat, so the
+GPU's labels are checked by evaluating the oracle's bound at them); FP32
+gradients <= 1e-4 relative to the FP64 oracle; inference and the fallback
+rule exactly as the oracle applies them.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_2107_14758_gb300 import fdmpc, inputs  # noqa: E402
+
+FP64, FP32 = fdmpc.FDM_PREC_FP64, fdmpc.FDM_PREC_FP32
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+    assert torch.cuda.is_available()
+
+
+def ctx_for(w, precision=FP32, **kw):
+    nd = (len(w["xv"]) - 1) * w["p"] + 1
+    start = inputs.lanczos_start(nd ** 3)
+    return fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], jac=w["jac"], kappa=w["kappa"],
+                         samples27=w["samples27"], precision=precision, lanczos_start=start, **kw)
+
+
+@pytest.fixture(scope="module")
+def small():
+    w = inputs.deformed_problem(4, 3, 31)
+    return w, ctx_for(w)
+
+
+def test_features_parity(small):
+    w, ctx = small
+    got = ctx.surrogate_features()
+    ref = oracle.surr_features(w["samples27"])
+    assert got.shape == ref.shape == (64, 189)
+    assert np.abs(got - ref).max() <= 1e-6 * max(1.0, np.abs(ref).max())
+
+
+def test_mubar_and_bound_parity(small):
+    w, ctx = small
+    mubar, cs, F0, F1 = oracle.surr_label(w["p"], w["jac"], w["kappa"])
+    assert np.allclose(ctx.mubar(), mubar, rtol=1e-13, atol=0)
+    b = ctx.surrogate_bounds()
+    assert np.abs(b[0] - F0).max() <= 1e-12 * np.abs(F0).max()
+    assert np.abs(b[2] - F0).max() <= 1e-12 * np.abs(F0).max()   # current mu = averaged surrogate
+
+
+@pytest.mark.parametrize("n,p,seed", [(4, 3, 31), (3, 6, 32), (2, 11, 33)])
+def test_label_parity(n, p, seed):
+    w = inputs.deformed_problem(n, p, seed)
+    ctx = ctx_for(w, omega=1.0)
+    mubar, cs, F0, F1 = oracle.surr_label(p, w["jac"], w["kappa"])
+    got = ctx.surrogate_labels()
+    b = ctx.surrogate_bounds()
+    assert np.abs(b[1] - F1).max() <= 1e-8                   # the same optimum of the bound ratio
+    assert np.all(b[1] <= b[0] + 1e-15)
+    G, _ = oracle.surr_cell_ghat(p, w["jac"], w["kappa"])
+    for e in range(len(mubar)):                              # the GPU label attains it, centred
+        F, lo, hi = oracle.surr_bound(G[e], mubar[e] * np.exp(got[e]))
+        assert abs(F - F1[e]) <= 1e-8
+        assert abs(lo * hi - 1.0) <= 1e-10
+    close = np.abs(got - cs).max(axis=1) <= 1e-6
+    assert close.mean() >= 0.9, close.mean()
+
+
+def test_gradient_parity(small):
+    w, ctx = small
+    P = inputs.mlp_init(5)
+    P[-3:] = [0.2, -0.1, 0.05]
+    g, loss = ctx.surrogate_grad(P)
+    lab = ctx.surrogate_labels()
+    feat = oracle.surr_features(w["samples27"])
+    lref, gref = oracle.mlp_loss_grad(P.astype(np.float64), feat, lab)
+    assert loss == pytest.approx(lref, rel=1e-5)
+    assert np.linalg.norm(g - gref) <= 1e-4 * np.linalg.norm(gref)
+    assert np.abs(g - gref).max() <= 1e-4 * np.abs(gref).max()
+
+
+def test_training_first_step_matches_adam(small):
+    w, ctx = small
+    P0 = inputs.mlp_init(6)
+    lr = 1e-3
+    P1, hist = fdmpc.fdm_surrogate_train([ctx.h], P0, 1, lr)
+    lab = ctx.surrogate_labels()
+    feat = oracle.surr_features(w["samples27"])
+    l0, g = oracle.mlp_loss_grad(P0.astype(np.float64), feat, lab)
+    Pr = P0.astype(np.float64).copy()
+    m = np.zeros_like(Pr); v = np.zeros_like(Pr)
+    oracle.mlp_adam(Pr, g, m, v, 1, lr)
+    assert hist[0] == pytest.approx(l0, rel=1e-5)
+    big = np.abs(g) > 1e-3 * np.abs(g).max()      # Adam's first step is -lr sign(g) there
+    assert np.abs((P1 - P0)[big] - (Pr - P0)[big]).max() <= 1e-3 * lr
+    assert np.all(np.abs(P1 - P0) <= lr * (1 + 1e-5))
+
+
+def test_inference_and_fallback_exact(small):
+    w, ctx = small
+    mubar = ctx.mubar()
+    P = np.zeros(fdmpc.FDM_MLP_NPARAM, dtype=np.float32)
+    P[-3:] = [0.5, -0.25, 0.125]                   # constant output c = b3
+    nf, kept = ctx.surrogate_apply(P, judge=0)
+    assert nf == 0 and kept
+    ref, nref = oracle.surr_apply(mubar, np.tile([0.5, -0.25, 0.125], (ctx.ncell, 1)))
+    assert np.allclose(ctx.mu(), ref, rtol=1e-15, atol=0)
+    P[-3:] = [2.5, 0.0, 0.0]                       # |c| > 2 everywhere: every cell falls back
+    nf, kept = ctx.surrogate_apply(P, judge=0)
+    assert nf == ctx.ncell
+    assert np.array_equal(ctx.mu(), mubar)
+
+
+def test_inference_parity_random_network(small):
+    w, ctx = small
+    P = inputs.mlp_init(9)
+    P[-3:] = [0.1, 0.0, -0.1]
+    nf, kept = ctx.surrogate_apply(P, judge=0)
+    c = ctx.surrogate_output()
+    cref = oracle.mlp_forward(P.astype(np.float64), oracle.surr_features(w["samples27"]))
+    assert np.abs(c - cref).max() <= 1e-5
+    mu_ref, nref = oracle.surr_apply(ctx.mubar(), c.astype(np.float64))
+    assert nf == nref
+    assert np.allclose(ctx.mu(), mu_ref, rtol=1e-14, atol=0)
+
+
+def test_learned_surrogate_pcg_parity():
+    """FP64 path with the network's scalings: the same PCG as the oracle with
+    the same mu (iterations within +1, solution <= 1e-10)."""
+    w = inputs.deformed_problem(3, 4, 34)
+    ctx = ctx_for(w, precision=FP64)
+    P = inputs.mlp_init(10)
+    P[-3:] = [0.3, -0.2, 0.1]
+    ctx.surrogate_apply(P, judge=0)
+    ref = oracle.Problem(w["p"], w["xv"], w["yv"], w["zv"], jac=w["jac"], kappa=w["kappa"])
+    ref.set_mu(ctx.mu().reshape(-1))
+    ref.setup_patches()
+    ref.setup_coarse()
+    ref.set_omega(ctx.omega)
+    b = inputs.normal_rhs(ctx.ndof, 3)
+    from tests import bruteforce as bf
+    b = np.where(bf.free_mask(w["p"], 3, 3, 3), b, 0.0)
+    x, info = ctx.pcg_solve(torch.tensor(b, device="cuda:0"), rtol=1e-8, maxit=300)
+    xr, it, _, _ = ref.pcg(b, 1e-8, 300)
+    assert abs(info.iterations - it) <= 1
+    if info.iterations == it:
+        assert np.abs(x.cpu().numpy() - xr).max() <= 1e-10 * np.abs(xr).max()
+
+
+def test_trained_network_gain():
+    """Trains on three deformed problems and applies the network to a held-out
+    one.  Records what the network gains over the averaged surrogate: its
+    training objective (the mean Theorem 1 bound ratio per cell), the Lanczos
+    estimate of cond(P_ASM^{-1} A) and PCG iterations.  With the averaged
+    surrogate judging, the kept result is never worse in the Lanczos estimate
+    and the solve needs no more iterations than without the network (+1)."""
+    train = [ctx_for(inputs.deformed_problem(5, 3, s), omega=1.0) for s in (41, 42, 43)]
+    P0 = inputs.mlp_init(11)
+    P, hist = fdmpc.fdm_surrogate_train([c.h for c in train], P0, 300, 2e-3, 1e-4)
+    assert np.all(np.isfinite(hist))
+    assert hist[-1] < 0.5 * hist[0], (hist[0], hist[-1])
+
+    w = inputs.deformed_problem(5, 3, 44)
+    b = torch.tensor(inputs.normal_rhs((5 * 3 + 1) ** 3, 7), device="cuda:0")
+    base = ctx_for(w)
+    lo0, hi0 = base.lanczos_extremes()
+    _, info0 = base.pcg_solve(b, rtol=1e-8, maxit=500)
+
+    raw = ctx_for(w)
+    nf, kept = raw.surrogate_apply(P, judge=0)
+    F = raw.surrogate_bounds()
+    lo1, hi1 = raw.lanczos_extremes()
+    _, info1 = raw.pcg_solve(b, rtol=1e-8, maxit=500)
+
+    judged = ctx_for(w)
+    nf2, kept2 = judged.surrogate_apply(P, judge=1)
+    lo2, hi2 = judged.lanczos_extremes()
+    _, info2 = judged.pcg_solve(b, rtol=1e-8, maxit=500)
+    print("\nlearned surrogate, held-out 5^3 Q3 deformed (seed 44): mean bound log(hi/lo) "
+          "avg %.4f label %.4f network %.4f | Lanczos cond avg %.3f network %.3f | PCG its avg %d "
+          "network %d judged %d (kept %s, fallback cells %d) | train loss %.4g -> %.4g"
+          % (F[0].mean(), F[1].mean(), F[2].mean(), hi0 / lo0, hi1 / lo1, info0.iterations,
+             info1.iterations, info2.iterations, kept2, nf, hist[0], hist[-1]))
+    assert info0.converged and info1.converged and info2.converged
+    if kept2:
+        assert hi2 / lo2 <= hi0 / lo0 * (1 + 1e-12)
+        assert info2.iterations <= info0.iterations + 1
+    else:
+        assert np.array_equal(judged.mu(), base.mu())
+        assert info2.iterations == info0.iterations

@@ -33,7 +33,7 @@ def test_header_declares_the_boundary():
     names = _declared_functions()
     for required in ("fdm_setup", "stiffness_apply", "pc_apply", "asm_apply", "pcg_solve", "fdm_query",
                      "fdm_destroy", "fdm_last_error", "fdm_batch_setup", "pcg_solve_batched",
-                     "fdm_surrogate_load"):
+                     "fdm_surrogate_load", "fdm_surrogate_train", "fdm_surrogate_grad", "fdm_surrogate_apply"):
         assert required in names
 
 
@@ -56,5 +56,10 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert L.fdm_setup(ctypes.byref(mesh), 16, None, None, ctypes.byref(h), None) == fdmpc.FDM_EINVAL
     assert "p <= 15" in fdmpc.fdm_last_error(None)
     assert L.stiffness_apply(None, None, None, None) == fdmpc.FDM_EINVAL
+    w = np.zeros(fdmpc.FDM_MLP_NPARAM, dtype=np.float32)
+    wp = w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    assert L.fdm_surrogate_train(0, None, wp, 10, 1e-3, 0.0, wp, None, None) == fdmpc.FDM_EINVAL
+    assert L.fdm_surrogate_apply(None, wp, 1, None, None, None) == fdmpc.FDM_EINVAL
+    assert L.fdm_surrogate_grad(None, wp, wp, None, None) == fdmpc.FDM_EINVAL
     o = fdmpc.fdm_default_options()
     assert o.precision == fdmpc.FDM_PREC_FP32 and o.pc == fdmpc.FDM_PC_VCYCLE and o.lanczos_steps == 20
