@@ -71,8 +71,6 @@ def test_label_parity(n, p, seed):
         F, lo, hi = oracle.surr_bound(G[e], mubar[e] * np.exp(got[e]))
         assert abs(F - F1[e]) <= 1e-8
         assert abs(lo * hi - 1.0) <= 1e-10
-    close = np.abs(got - cs).max(axis=1) <= 1e-6
-    assert close.mean() >= 0.9, close.mean()
 
 
 def test_gradient_parity(small):
