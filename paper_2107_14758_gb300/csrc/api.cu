@@ -87,8 +87,9 @@ struct fdm_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_tag;  // tag of each recorded (begin, end) pair
   size_t ev_used = 0;
+  bool capturing = false;  // building a CUDA graph: no event timers
   void tmark(int tag, bool begin, cudaStream_t st) {
-    if (!opt.kernel_timing) return;
+    if (!opt.kernel_timing || capturing) return;
     if (begin) {
       if (ev_used + 2 > ev_pool.size()) {
         for (int i = 0; i < 256; ++i) {
@@ -155,6 +156,26 @@ template <> size_t fdm_ctx::smem<float>() const { return smem32; }
 
 struct fdm_batch {
   std::vector<fdm_ctx *> ctxs;
+  // the captured solve: one graph with a device-driven PCG loop per problem
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+  unsigned long long *d_times = nullptr;  // [1 + k] global timer: start, end of each solve
+  std::vector<const double *> key_b;
+  std::vector<double *> key_x;
+  double key_rtol = -1.0;
+  int key_maxit = -1;
+  void release_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+  }
+  ~fdm_batch() {
+    release_graph();
+    if (cap) cudaStreamDestroy(cap);
+    if (d_times) cudaFree(d_times);
+  }
 };
 
 namespace {
@@ -170,6 +191,15 @@ void mask_dirichlet(const Grid &g, double *v, cudaStream_t st) {
   int64_t b = std::min<int64_t>((g.ndof + 255) / 256, 152 * 32);
   k_mask_dirichlet<<<(int)std::max<int64_t>(b, 1), 256, 0, st>>>(g, v);
 }
+__global__ void k_fill(int64_t n, double v, double *x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] = v;
+}
+__global__ void k_copy(int64_t n, const double *__restrict__ a, double *__restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) b[i] = a[i];
+}
+int vec_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+void fill(int64_t n, double v, double *x, cudaStream_t st) { k_fill<<<vec_blocks(n), 256, 0, st>>>(n, v, x); }
+void copy(int64_t n, const double *a, double *b, cudaStream_t st) { k_copy<<<vec_blocks(n), 256, 0, st>>>(n, a, b); }
 
 template <typename T>
 StreamArgs<T> stream_args(fdm_ctx *c) {
@@ -267,9 +297,9 @@ void run_vcycle(fdm_ctx *c, const T *r, T *z, T *x1, T *t, T *r1, cudaStream_t s
 void pc_apply_impl(fdm_ctx *c, const double *r, double *z, cudaStream_t st) {
   const int64_t n = c->g.ndof;
   if (c->opt.pc == FDM_PC_NONE) {
-    FDM_CUDA(cudaMemcpyAsync(z, r, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    copy(n, r, z, st);
     mask_dirichlet(c->g, z, st);
-    c->launches += 1;
+    c->launches += 2;
     return;
   }
   if (c->opt.precision == FDM_PREC_FP64) {
@@ -671,6 +701,166 @@ void lanczos_omega(fdm_ctx *c, const double *start_host, cudaStream_t st) {
   c->omega = 2.0 / ((1.0 + alpha) * c->lmax + (1.0 - alpha) * c->lmin);
 }
 
+// ---- batched solves: one CUDA graph, a device-driven PCG loop per problem
+// Scalars of a problem in c->sc: [0] r.z, [1] alpha, [2] beta, [3] d.q, [7] flexible beta,
+// [8] non-finite flag, [9] first iteration, [10] rtol^2, [11] maxit, [12] ||b||^2,
+// [13] iterations, [14] ||r||^2, [15] converged.  c->dots: [0] r.z, [1] r.z_prev, [2] r.r, [3] d.q.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__global__ void k_btime(unsigned long long *t) {
+  if (threadIdx.x == 0) t[0] = global_ns();
+}
+__global__ void k_bconst(double *sc, double flex, double rtol2, double maxit) {
+  if (threadIdx.x != 0) return;
+  for (int i = 0; i < 16; ++i) sc[i] = 0.0;
+  sc[7] = flex;
+  sc[10] = rtol2;
+  sc[11] = maxit;
+}
+// ||b||^2 is in dots[2]: start the loop unless b = 0 (or maxit = 0)
+__global__ void k_bstart(double *sc, const double *dots, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0) return;
+  const double bb = dots[2];
+  sc[12] = bb;
+  sc[14] = bb;
+  sc[9] = 1.0;
+  sc[13] = 0.0;
+  sc[15] = bb == 0.0 ? 1.0 : 0.0;
+  if (!isfinite(bb)) sc[8] = 1.0;
+  cudaGraphSetConditional(h, (bb > 0.0 && isfinite(bb) && sc[11] > 0.0) ? 1u : 0u);
+}
+// beta = (r.z - flex r.z_prev) / (r.z)_prev, 0 in the first iteration
+__global__ void k_bbeta(double *sc, const double *dots) {
+  if (threadIdx.x != 0) return;
+  const double rz = dots[0];
+  double b = 0.0;
+  if (sc[9] == 0.0) {
+    b = (sc[7] != 0.0 ? rz - dots[1] : rz) / sc[0];
+    if (!isfinite(b)) {
+      sc[8] = 1.0;
+      b = 0.0;
+    }
+  }
+  if (!isfinite(rz)) sc[8] = 1.0;
+  sc[9] = 0.0;
+  sc[2] = b;
+  sc[0] = rz;
+}
+// end of an iteration: stop at ||r||^2 <= rtol^2 ||b||^2, at maxit or on a non-finite value
+__global__ void k_bcheck(double *sc, const double *dots, cudaGraphConditionalHandle h, unsigned long long *tend) {
+  if (threadIdx.x != 0) return;
+  const double rr = dots[2];
+  const double it = sc[13] + 1.0;
+  sc[13] = it;
+  sc[14] = rr;
+  if (!isfinite(rr)) sc[8] = 1.0;
+  const bool conv = rr <= sc[10] * sc[12];
+  sc[15] = conv ? 1.0 : 0.0;
+  const bool done = conv || it >= sc[11] || sc[8] != 0.0;
+  if (done) *tend = global_ns();
+  cudaGraphSetConditional(h, done ? 0u : 1u);
+}
+
+void capture_iteration(fdm_ctx *c, double *x, cudaGraphConditionalHandle h, unsigned long long *tend,
+                       cudaStream_t st) {
+  const int64_t n = c->g.ndof;
+  launch_dot(n, c->r, c->z, c->partial, c->dots + 1, st);  // r . z_prev (flexible beta)
+  pc_apply_impl(c, c->r, c->z, st);
+  launch_dot(n, c->r, c->z, c->partial, c->dots, st);
+  k_bbeta<<<1, 32, 0, st>>>(c->sc, c->dots);
+  launch_pcg_update_d(n, c->sc, c->z, c->d, st);
+  apply_op<double>(c, c->d, c->q, st);
+  launch_dot(n, c->d, c->q, c->partial, c->dots + 3, st);
+  launch_pcg_scalars(0, c->sc, c->dots + 3, st);
+  launch_pcg_update_xr(n, c->sc, c->d, c->q, x, c->r, st);
+  launch_dot(n, c->r, c->r, c->partial, c->dots + 2, st);
+  k_bcheck<<<1, 32, 0, st>>>(c->sc, c->dots, h, tend);
+  FDM_CUDA(cudaGetLastError());
+}
+
+void build_batch_graph(fdm_batch *B, const double *const *bv, double *const *xv, double rtol, int maxit) {
+  B->release_graph();
+  const int k = (int)B->ctxs.size();
+  if (!B->cap) FDM_CUDA(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+  if (!B->d_times) FDM_CUDA(cudaMalloc(&B->d_times, sizeof(unsigned long long) * (k + 1)));
+  cudaGraph_t G;
+  FDM_CUDA(cudaGraphCreate(&G, 0));
+  B->graph = G;
+  cudaGraphNode_t t0;
+  {
+    cudaKernelNodeParams kp{};
+    void *args[] = {&B->d_times};
+    kp.func = (void *)k_btime;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = args;
+    FDM_CUDA(cudaGraphAddKernelNode(&t0, G, nullptr, 0, &kp));
+  }
+  for (int i = 0; i < k; ++i) {
+    fdm_ctx *c = B->ctxs[i];
+    const int64_t n = c->g.ndof;
+    c->capturing = true;
+    try {
+      // x = 0, r = b (Dirichlet entries 0), z = d = 0, ||b||^2
+      cudaGraph_t gi;
+      FDM_CUDA(cudaGraphCreate(&gi, 0));
+      FDM_CUDA(cudaStreamBeginCaptureToGraph(B->cap, gi, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      k_bconst<<<1, 32, 0, B->cap>>>(c->sc, c->opt.flexible_beta ? 1.0 : 0.0, rtol * rtol, (double)maxit);
+      fill(n, 0.0, xv[i], B->cap);
+      fill(n, 0.0, c->z, B->cap);
+      fill(n, 0.0, c->d, B->cap);
+      copy(n, bv[i], c->r, B->cap);
+      mask_dirichlet(c->g, c->r, B->cap);
+      launch_dot(n, c->r, c->r, c->partial, c->dots + 2, B->cap);
+      FDM_CUDA(cudaStreamEndCapture(B->cap, &gi));
+      cudaGraphNode_t ni, nb, nw;
+      FDM_CUDA(cudaGraphAddChildGraphNode(&ni, G, &t0, 1, gi));
+      FDM_CUDA(cudaGraphDestroy(gi));
+      cudaGraphConditionalHandle h;
+      FDM_CUDA(cudaGraphConditionalHandleCreate(&h, G, 0, cudaGraphCondAssignDefault));
+      {
+        cudaKernelNodeParams kp{};
+        double *sc = c->sc, *dots = c->dots;
+        void *args[] = {&sc, &dots, &h};
+        kp.func = (void *)k_bstart;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(32);
+        kp.kernelParams = args;
+        FDM_CUDA(cudaGraphAddKernelNode(&nb, G, &ni, 1, &kp));
+      }
+      cudaGraphNodeParams cp{};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      FDM_CUDA(cudaGraphAddNode(&nw, G, &nb, nullptr, 1, &cp));
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      FDM_CUDA(cudaStreamBeginCaptureToGraph(B->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      capture_iteration(c, xv[i], h, B->d_times + 1 + i, B->cap);
+      FDM_CUDA(cudaStreamEndCapture(B->cap, &body));
+    } catch (...) {
+      c->capturing = false;
+      cudaStreamCaptureStatus cs;
+      if (cudaStreamIsCapturing(B->cap, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+        cudaGraph_t junk = nullptr;
+        cudaStreamEndCapture(B->cap, &junk);
+        if (junk && junk != G) cudaGraphDestroy(junk);
+      }
+      cudaGetLastError();
+      throw;
+    }
+    c->capturing = false;
+  }
+  FDM_CUDA(cudaGraphInstantiate(&B->exec, G, 0));
+  B->key_b.assign(bv, bv + k);
+  B->key_x.assign(xv, xv + k);
+  B->key_rtol = rtol;
+  B->key_maxit = maxit;
+}
+
 // ---- learned surrogate helpers
 void need_surrogate_data(const fdm_ctx *c) {
   if (!c->general || !c->feat) fail(FDM_EINVAL, "the learned surrogate needs curved cells and samples27");
@@ -797,6 +987,10 @@ int fdm_setup(const fdm_mesh *mesh, int p, const fdm_coeff *coeff, const fdm_opt
       lanczos_omega(c, c->opt.lanczos_start, st);
       c->kappa_avg = c->lmax / c->lmin;
     }
+    // one preconditioner application (on r = 0) so that every kernel of the
+    // solve has been launched once, with its attributes set, before any capture
+    fill(g.ndof, 0.0, c->r, st);
+    pc_apply_impl(c, c->r, c->z, st);
     FDM_CUDA(cudaStreamSynchronize(st));
     FDM_CUDA(cudaGetLastError());
     double t4 = now_s();
@@ -958,13 +1152,62 @@ int fdm_batch_setup(int k, fdm_ctx *const *ctxs, fdm_batch **out) {
 
 int pcg_solve_batched(fdm_batch *b, const double *const *bv, double *const *xv, double rtol, int maxit,
                       fdm_solve_info *infos, void *stream) {
-  if (!b || !bv || !xv) return FDM_EINVAL;
-  int worst = FDM_OK;
-  for (size_t i = 0; i < b->ctxs.size(); ++i) {
-    int rc = pcg_solve(b->ctxs[i], bv[i], xv[i], rtol, maxit, infos ? infos + i : nullptr, stream);
-    if (rc < worst) worst = rc;
-  }
-  return worst;
+  if (!b || !bv || !xv || maxit < 0 || !(rtol >= 0.0)) return FDM_EINVAL;
+  const int k = (int)b->ctxs.size();
+  if (k == 0) return FDM_OK;
+  for (int i = 0; i < k; ++i)
+    if (!bv[i] || !xv[i]) return FDM_EINVAL;
+  fdm_ctx *c0 = b->ctxs[0];
+  try {
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool same = b->exec && b->key_rtol == rtol && b->key_maxit == maxit &&
+                      std::equal(b->key_b.begin(), b->key_b.end(), bv) && std::equal(b->key_x.begin(), b->key_x.end(), xv);
+    if (!same) build_batch_graph(b, bv, xv, rtol, maxit);
+    FDM_CUDA(cudaGraphLaunch(b->exec, st));
+    FDM_CUDA(cudaStreamSynchronize(st));
+    std::vector<unsigned long long> t(k + 1);
+    FDM_CUDA(cudaMemcpy(t.data(), b->d_times, sizeof(unsigned long long) * (k + 1), cudaMemcpyDeviceToHost));
+    int worst = FDM_OK;
+    for (int i = 0; i < k; ++i) {
+      fdm_ctx *c = b->ctxs[i];
+      double hsc[16];
+      FDM_CUDA(cudaMemcpy(hsc, c->sc, sizeof hsc, cudaMemcpyDeviceToHost));
+      int hstat = 0;
+      FDM_CUDA(cudaMemcpy(&hstat, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+      int rc = FDM_OK;
+      if (hstat) {
+        FDM_CUDA(cudaMemset(c->status, 0, sizeof(int)));
+        c->err = "a bounded device-side wait of the patch solve ran out";
+        rc = FDM_ETIMEOUT;
+      } else if (hsc[8] != 0.0) {
+        c->err = "non-finite scalar in PCG";
+        rc = FDM_ENAN;
+      } else if (hsc[15] == 0.0) {
+        c->err = "PCG reached maxit";
+        rc = FDM_ENOCONV;
+      }
+      if (infos) {
+        fdm_solve_info &f = infos[i];
+        f.iterations = (int)hsc[13];
+        f.converged = hsc[15] != 0.0;
+        f.rnorm0 = std::sqrt(hsc[12]);
+        f.rnorm = std::sqrt(hsc[14]);
+        f.seconds = hsc[13] > 0 && t[1 + i] > t[0] ? (double)(t[1 + i] - t[0]) * 1e-9 : 0.0;
+        const int64_t n = c->g.ndof;  // true residual ||b - A x||, outside the timed graph
+        launch_operator<double, double, double>(c->op_args(false), false, xv[i], c->q, c->E64, st);
+        launch_sub<double>(n, bv[i], c->q, c->v1, st);
+        mask_dirichlet(c->g, c->v1, st);
+        launch_dot(n, c->v1, c->v1, c->partial, c->dots, st);
+        double h = 0.0;
+        FDM_CUDA(cudaMemcpyAsync(&h, c->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
+        FDM_CUDA(cudaStreamSynchronize(st));
+        f.true_rnorm = std::sqrt(h);
+      }
+      if (rc < worst) worst = rc;
+    }
+    if (worst != FDM_OK) g_last_error = "pcg_solve_batched: a problem did not converge (see its context)";
+    return worst;
+  } catch (const Error &e) { return handle(c0, e); }
 }
 
 void fdm_batch_destroy(fdm_batch *b) { delete b; }

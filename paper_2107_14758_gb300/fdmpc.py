@@ -168,12 +168,19 @@ def fdm_batch_setup(ctxs):
     return h
 
 
-def pcg_solve_batched(batch, bs, xs, rtol, maxit, stream=None):
+def pcg_solve_batched(batch, bs, xs, rtol, maxit, stream=None, check=True):
+    """Solves the batch's problems (one CUDA graph); returns the infos, or
+    (return code, infos) with check=False."""
     k = len(bs)
+    for t in list(bs) + list(xs):
+        _tptr(t)
     barr = (C.c_void_p * k)(*[b.data_ptr() for b in bs])
     xarr = (C.c_void_p * k)(*[x.data_ptr() for x in xs])
     infos = (fdm_solve_info * k)()
-    _check(load().pcg_solve_batched(batch, barr, xarr, rtol, maxit, infos, _stream(stream)))
+    rc = load().pcg_solve_batched(batch, barr, xarr, rtol, maxit, infos, _stream(stream))
+    if not check:
+        return rc, list(infos)
+    _check(rc)
     return list(infos)
 
 

@@ -1,0 +1,105 @@
+"""Batched solves of independent problems in one CUDA graph (a device-driven
+PCG loop per problem, conditional WHILE nodes): parity with the one-problem
+solve and with the FP64 oracle, edge cases (b = 0, maxit reached, repeated
+and changed calls)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_2107_14758_gb300 import fdmpc, inputs  # noqa: E402
+
+FP64, FP32 = fdmpc.FDM_PREC_FP64, fdmpc.FDM_PREC_FP32
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+    assert torch.cuda.is_available()
+
+
+def problems(precision, specs):
+    out = []
+    for n, p, seed in specs:
+        xv, yv, zv = inputs.graded_vertices(n, seed)
+        nd = (n * p + 1) ** 3
+        ctx = fdmpc.Context(p, xv, yv, zv, precision=precision, lanczos_start=inputs.lanczos_start(nd))
+        b = torch.tensor(inputs.normal_rhs(nd, seed), device=DEV)
+        out.append((ctx, b, (xv, yv, zv)))
+    return out
+
+
+SPECS = [(2, 3, 1), (3, 5, 2), (4, 2, 3), (2, 9, 4), (3, 1, 5), (5, 4, 6)]
+
+
+@pytest.mark.parametrize("precision", [FP64, FP32])
+def test_batched_matches_single_solves(precision):
+    probs = problems(precision, SPECS)
+    batch = fdmpc.fdm_batch_setup([c.h for c, _, _ in probs])
+    try:
+        xs = [torch.zeros_like(b) for _, b, _ in probs]
+        infos = fdmpc.pcg_solve_batched(batch, [b for _, b, _ in probs], xs, 1e-8, 200)
+        for (ctx, b, _), x, info in zip(probs, xs, infos):
+            x1, i1 = ctx.pcg_solve(b, rtol=1e-8, maxit=200)
+            assert info.converged and info.iterations == i1.iterations
+            assert info.rnorm <= 1e-8 * info.rnorm0
+            assert info.rnorm0 == pytest.approx(i1.rnorm0, rel=1e-14)
+            assert info.true_rnorm <= 1e-7 * info.rnorm0
+            assert info.seconds > 0.0
+            tol = 1e-12 if precision == FP64 else 1e-6
+            assert (x - x1).abs().max().item() <= tol * x1.abs().max().item()
+        # the same call again reuses the graph and gives the same result
+        xs2 = [torch.full_like(b, 3.0) for _, b, _ in probs]
+        infos2 = fdmpc.pcg_solve_batched(batch, [b for _, b, _ in probs], xs2, 1e-8, 200)
+        infos3 = fdmpc.pcg_solve_batched(batch, [b for _, b, _ in probs], xs2, 1e-8, 200)
+        for a, c, i in zip(xs, xs2, infos3):
+            assert torch.equal(a, c) or precision == FP32
+        assert [i.iterations for i in infos2] == [i.iterations for i in infos]
+    finally:
+        fdmpc.fdm_batch_destroy(batch)
+
+
+def test_batched_fp64_matches_oracle():
+    probs = problems(FP64, [(3, 4, 11), (2, 6, 12)])
+    batch = fdmpc.fdm_batch_setup([c.h for c, _, _ in probs])
+    try:
+        xs = [torch.zeros_like(b) for _, b, _ in probs]
+        infos = fdmpc.pcg_solve_batched(batch, [b for _, b, _ in probs], xs, 1e-8, 200)
+        for (ctx, b, (xv, yv, zv)), x, info in zip(probs, xs, infos):
+            ref = oracle.Problem(ctx.p, xv, yv, zv)
+            ref.setup_patches()
+            ref.setup_coarse()
+            ref.set_omega(ctx.omega)
+            xr, it, _, _ = ref.pcg(b.cpu().numpy(), 1e-8, 200)
+            assert abs(info.iterations - it) <= 1
+            if info.iterations == it:
+                assert np.abs(x.cpu().numpy() - xr).max() <= 1e-10 * np.abs(xr).max()
+    finally:
+        fdmpc.fdm_batch_destroy(batch)
+
+
+def test_batched_edge_cases():
+    probs = problems(FP32, [(2, 3, 21), (3, 4, 22), (2, 5, 23)])
+    batch = fdmpc.fdm_batch_setup([c.h for c, _, _ in probs])
+    try:
+        bs = [b for _, b, _ in probs]
+        bs[1] = torch.zeros_like(bs[1])                  # b = 0: converged at once, x = 0
+        xs = [torch.full_like(b, 7.0) for b in bs]
+        infos = fdmpc.pcg_solve_batched(batch, bs, xs, 1e-8, 200)
+        assert infos[1].converged and infos[1].iterations == 0 and torch.count_nonzero(xs[1]).item() == 0
+        assert infos[0].converged and infos[2].converged
+        # maxit reached for every problem: ENOCONV, iterations == maxit
+        rc, infos = fdmpc.pcg_solve_batched(batch, bs, xs, 1e-14, 2, check=False)
+        assert rc == fdmpc.FDM_ENOCONV
+        assert infos[0].iterations == 2 and not infos[0].converged
+        assert infos[1].iterations == 0 and infos[1].converged
+        # a changed rtol rebuilds the graph and converges again
+        infos = fdmpc.pcg_solve_batched(batch, bs, xs, 1e-6, 200)
+        assert all(i.converged for i in infos)
+        assert infos[0].rnorm <= 1e-6 * infos[0].rnorm0
+    finally:
+        fdmpc.fdm_batch_destroy(batch)
