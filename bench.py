@@ -308,6 +308,11 @@ def bench_gpu(args):
         secondary["mixed_over_fp64"] = (free / (ms_max * 1e-3 / args.steps)) / secondary["fp64_pc_solve_dofs_per_s"]
         ctx64.close()
 
+    if rank == 0 and ws == 1 and not args.no_extra:
+        secondary["p15"] = bench_p15(dev, fdmpc, inputs, peak)
+        secondary["deformed"] = bench_deformed(dev, fdmpc, inputs)
+        secondary["batched"] = bench_batched(dev, fdmpc, inputs)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         P, bc = oracle_problem()
@@ -345,6 +350,164 @@ def bench_gpu(args):
     return 0
 
 
+def _timed_solves(ctx, b, x, k, maxit=None):
+    """(ms per solve, last info) of k PCG solves after 2 untimed ones (CUDA events)."""
+    import torch
+    maxit = maxit or MAXIT
+    for _ in range(2):
+        ctx.pcg_solve(b, x, rtol=RTOL, maxit=maxit)
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(torch.cuda.current_stream())
+    for _ in range(k):
+        info = ctx.pcg_solve(b, x, rtol=RTOL, maxit=maxit)[1]
+    s1.record(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    return s0.elapsed_time(s1) / k, info
+
+
+def bench_p15(dev, fdmpc, inputs, peak):
+    """High-order Poisson at p = 15 (8^3 uniform, manufactured sine): mixed and
+    FP64 solves, pc_apply throughput and its HBM fraction."""
+    import torch
+    w = inputs.workload("q15_uniform8")
+    ctx = fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP32)
+    free = _free_dofs(ctx.N)
+    b = ctx.mass_apply(torch.tensor(inputs.manufactured_f(w["xv"], w["yv"], w["zv"], w["p"]), device=dev))
+    x = torch.empty_like(b)
+    ms, info = _timed_solves(ctx, b, x, 3)
+    r = torch.randn(ctx.ndof, dtype=torch.float64, device=dev)
+    z = torch.empty_like(r)
+    for _ in range(3):
+        ctx.pc_apply(r, z)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(torch.cuda.current_stream())
+    for _ in range(10):
+        ctx.pc_apply(r, z)
+    e1.record(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    pc_ms = e0.elapsed_time(e1) / 10
+    ab = ctx.algo_bytes()
+    out = {"workload": "q15_uniform8: 8^3 uniform hex mesh, Q15, %d free dofs, manufactured sine" % free,
+           "mixed_solve_dofs_per_s": free / (ms * 1e-3), "mixed_iterations": info.iterations,
+           "mixed_true_rel_residual": info.true_rnorm / info.rnorm0,
+           "pc_apply_ms": pc_ms, "pc_apply_gdofs": free / (pc_ms * 1e-3) / 1e9,
+           # two FP32 relaxation sweeps' algorithmic bytes (a lower bound of pc_apply's)
+           "pc_apply_sweep_bytes": 2 * ab["asm32"],
+           "pc_apply_hbm_frac_of_measured": 2 * ab["asm32"] / (pc_ms * 1e-3) / 1e9 / peak}
+    ctx.close()
+    ctx64 = fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP64)
+    ms64, info64 = _timed_solves(ctx64, b, x, 2)
+    out["fp64_solve_dofs_per_s"] = free / (ms64 * 1e-3)
+    out["fp64_iterations"] = info64.iterations
+    out["mixed_over_fp64"] = ms64 / ms
+    ctx64.close()
+    return out
+
+
+DEFORMED_MAXIT = 2000  # kappa = exp(G) needs far more iterations than the Poisson cases
+
+
+def bench_deformed(dev, fdmpc, inputs):
+    """Non-separable Poisson (12^3 deformed mesh, kappa = exp(G), Q8): averaged
+    surrogate (mixed and FP64) and the learned surrogate judged by it."""
+    import torch
+    w = inputs.workload("q8_deformed12")
+    nd = (12 * 8 + 1) ** 3
+
+    def make(precision):
+        return fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], jac=w["jac"], kappa=w["kappa"],
+                             samples27=w["samples27"], precision=precision, lanczos_start=inputs.lanczos_start(nd))
+    ctx = make(fdmpc.FDM_PREC_FP32)
+    free = _free_dofs(ctx.N)
+    b = torch.tensor(inputs.normal_rhs(ctx.ndof, w["seed"]), device=dev)
+    x = torch.empty_like(b)
+    ms, info = _timed_solves(ctx, b, x, 3, DEFORMED_MAXIT)
+    lo, hi = ctx.lanczos_extremes()
+    out = {"workload": "q8_deformed12: 12^3 deformed hex mesh, kappa = exp(G), Q8, %d free dofs, N(0,1) load" % free,
+           "mixed_solve_dofs_per_s": free / (ms * 1e-3), "mixed_iterations": info.iterations,
+           "lanczos_cond_averaged": hi / lo}
+    # learned surrogate: trained on the GPU on three smaller problems of the family, applied here
+    train = [fdmpc.Context(8, *inputs.uniform_vertices(4), jac=t["jac"], kappa=t["kappa"], samples27=t["samples27"],
+                           omega=1.0) for t in (inputs.deformed_problem(4, 8, s) for s in (101, 102, 103))]
+    torch.cuda.synchronize()
+    t0 = time.time()
+    wts, hist = fdmpc.fdm_surrogate_train([t.h for t in train], inputs.mlp_init(7), 300, 2e-3, 1e-4)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    for t in train:
+        t.close()
+    raw = make(fdmpc.FDM_PREC_FP32)
+    nf, _ = raw.surrogate_apply(wts, judge=0)
+    lo1, hi1 = raw.lanczos_extremes()
+    F = raw.surrogate_bounds()
+    _, info_raw = _timed_solves(raw, b, x, 1, DEFORMED_MAXIT)
+    raw.close()
+    nf2, kept = ctx.surrogate_apply(wts, judge=1)
+    ms2, info2 = _timed_solves(ctx, b, x, 3, DEFORMED_MAXIT)
+    out.update({"learned": {"train_cells": 3 * 64, "train_steps": 300, "train_seconds": train_s,
+                            "train_loss_first_last": [hist[0], hist[-1]],
+                            "mean_cell_bound_log_ratio": {"averaged": float(F[0].mean()), "label": float(F[1].mean()),
+                                                          "network": float(F[2].mean())},
+                            "lanczos_cond_network": hi1 / lo1, "network_iterations": info_raw.iterations,
+                            "fallback_cells": nf, "kept_by_judge": bool(kept),
+                            "judged_iterations": info2.iterations,
+                            "judged_solve_dofs_per_s": free / (ms2 * 1e-3)}})
+    ctx.close()
+    ctx64 = make(fdmpc.FDM_PREC_FP64)
+    ms64, info64 = _timed_solves(ctx64, b, x, 2, DEFORMED_MAXIT)
+    out["fp64_solve_dofs_per_s"] = free / (ms64 * 1e-3)
+    out["fp64_iterations"] = info64.iterations
+    out["mixed_over_fp64"] = ms64 / ms
+    ctx64.close()
+    return out
+
+
+def bench_batched(dev, fdmpc, inputs, reps=3):
+    """64 independent graded problems (n in 2..10, p in 3..15) solved in one CUDA
+    graph: aggregate DoF/s and per-solve latency (device timer)."""
+    import torch
+    probs = inputs.batch_problems(64, 1000)
+    ctxs, bs = [], []
+    t0 = time.time()
+    for w in probs:
+        n, p = len(w["xv"]) - 1, w["p"]
+        nd = (n * p + 1) ** 3
+        ctxs.append(fdmpc.Context(p, w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP32,
+                                  lanczos_start=inputs.lanczos_start(nd)))
+        bs.append(torch.tensor(inputs.normal_rhs(nd, w["seed"]), device=dev))
+    setup_s = time.time() - t0
+    free = sum(_free_dofs(c.N) for c in ctxs)
+    batch = fdmpc.fdm_batch_setup([c.h for c in ctxs])
+    xs = [torch.empty_like(b) for b in bs]
+    fdmpc.pcg_solve_batched(batch, bs, xs, RTOL, MAXIT)  # capture + first run
+    times, lat = [], []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(torch.cuda.current_stream())
+        infos = fdmpc.pcg_solve_batched(batch, bs, xs, RTOL, MAXIT)
+        e1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        lat += [i.seconds * 1e3 for i in infos]
+    ms = float(np.median(times))
+    worst = max(i.true_rnorm / i.rnorm0 for i in infos)
+    fdmpc.fdm_batch_destroy(batch)
+    for c in ctxs:
+        c.close()
+    return {"workload": "64 graded problems, n^3 cells n in 2..10, Q_p p in 3..15 (seeds 1000..1063), "
+                        "%d free dofs in total, mixed precision, one CUDA graph" % free,
+            "aggregate_dofs_per_s": free / (ms * 1e-3), "batch_ms": ms,
+            "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+            "iterations_min_max": [min(i.iterations for i in infos), max(i.iterations for i in infos)],
+            "worst_true_rel_residual": worst, "setup_seconds": setup_s}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -353,6 +516,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-preconditioner comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the p = 15, deformed (learned surrogate) and 64-problem batched workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return bench_reference(args)
