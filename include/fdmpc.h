@@ -96,7 +96,9 @@ typedef struct {
   int patch_threads;  /* threads per patch-solve CTA: 256, 512 or 1024 (0 = 256, or 1024 when
                          an interface exceeds 1000 dofs) */
   int patch_kernel;   /* 0 = automatic (= 1), 1 = one CTA per patch reading the factor
-                         directly, 2 = streamed: bulk copies into a shared-memory ring */
+                         directly, 2 = streamed: bulk copies into a shared-memory ring,
+                         3 = resident: persistent CTAs that bulk-copy each patch's whole factor
+                         into shared memory (falls back to 1 where it does not fit) */
   int stream_buffers; /* ring buffers of the streamed solve (0 = 4) */
   int stream_buffer_kb; /* size of each ring buffer in KiB (0 = 16) */
   int inject_stall;   /* test hook: the streamed solve waits on a barrier that is never

@@ -60,6 +60,10 @@ struct fdm_ctx {
   double *X64 = nullptr, *E64 = nullptr;
   float *X32 = nullptr, *E32 = nullptr;
   size_t smem64 = 0, smem32 = 0;
+  // resident patch solve (whole factor of a patch in shared memory), per precision
+  bool res64 = false, res32 = false;
+  int fcap = 0, res_threads = 512, res_tmp = 0;
+  size_t rsmem64 = 0, rsmem32 = 0;
   // coarse
   int nc = 0;
   int *cfree = nullptr;
@@ -232,12 +236,19 @@ void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st) {
   launch_restrict_fdm<T, Tin>(c->g, r, c->tab<T>(), c->mu, c->E<T>(), st);
   c->tmark(FDM_T_RESTRICT, false, st);
   c->tmark(FDM_T_PATCH, true, st);
+  const bool resident = sizeof(T) == 4 ? c->res32 : c->res64;
   if (c->stream) {
     if (launch_patch_stream<T>(stream_args<T>(c), c->patch_threads, st) != 0)
       fail(FDM_ECUDA, "streamed patch solve: launch configuration rejected");
+  } else if (resident) {
+    PatchSolveArgs<T> a{c->g, c->d_cls, c->d_patches, c->d_order, c->E<T>(), c->mu, c->tab<T>(), c->L<T>(), c->X<T>(),
+                        c->res_tmp, 0, (uint64_t)(std::max(c->opt.wait_timeout_s, 0.0) * 1e9), c->status,
+                        c->opt.inject_stall};
+    launch_patch_resident<T>(a, c->nsolve, c->fcap, sizeof(T) == 4 ? c->rsmem32 : c->rsmem64, c->res_threads, st);
   } else {
     PatchSolveArgs<T> a{c->g, c->d_cls, c->d_patches, c->d_order, c->E<T>(), c->mu, c->tab<T>(), c->L<T>(), c->X<T>(),
-                        patch_tmp_elems(c->maxN1, c->maxN2), c->opt.patch_prefetch > 0 ? c->opt.patch_prefetch : 3};
+                        patch_tmp_elems(c->maxN1, c->maxN2), c->opt.patch_prefetch > 0 ? c->opt.patch_prefetch : 3,
+                        0, c->status, 0};
     launch_patch_solve<T>(a, c->nsolve, c->smem<T>(), c->patch_threads, st);
   }
   c->tmark(FDM_T_PATCH, false, st);
@@ -509,6 +520,21 @@ void setup_patches(fdm_ctx *c) {
   c->smem64 = patch_smem_for_occupancy<double>(c->smem64, c->opt.patch_ctas_per_sm);
   c->smem32 = patch_smem_for_occupancy<float>(c->smem32, c->opt.patch_ctas_per_sm);
   if (c->smem64 > 200 * 1024) fail(FDM_EINVAL, "patch interface too large for shared memory");
+  // resident variant (patch_kernel = 3) where one patch's whole factor fits in
+  // shared memory; not the default: with one 184 KB factor per SM (Q7) no other
+  // patch overlaps the latency of the solve phases, and it measured slower
+  // than the one-CTA-per-patch kernel
+  int64_t maxval = 0;
+  for (const PatchClass &C : c->classes) maxval = std::max<int64_t>(maxval, C.nval);
+  c->fcap = (int)((maxval + 3) & ~3);
+  c->res_threads = c->opt.patch_threads > 0 ? c->opt.patch_threads : 512;
+  c->res_tmp = patch_resident_tmp(c->maxN1, c->maxN2, c->res_threads);
+  c->rsmem32 = patch_resident_smem<float>(c->fcap, c->maxG, c->res_tmp);
+  c->rsmem64 = patch_resident_smem<double>(c->fcap, c->maxG, c->res_tmp);
+  const bool want_res = !c->stream && c->opt.patch_kernel == 3;
+  const size_t res_cap = 225 * 1024;
+  c->res32 = want_res && c->rsmem32 <= res_cap;
+  c->res64 = want_res && c->rsmem64 <= res_cap;
   if (c->stream) {
     size_t need = std::max(stream_smem_bytes<double>(stream_args<double>(c)), stream_smem_bytes<float>(stream_args<float>(c)));
     if (need > 220 * 1024) fail(FDM_EINVAL, "streamed patch solve needs too much shared memory; use fewer or smaller buffers");
@@ -989,8 +1015,10 @@ int fdm_setup(const fdm_mesh *mesh, int p, const fdm_coeff *coeff, const fdm_opt
     }
     // one preconditioner application (on r = 0) so that every kernel of the
     // solve has been launched once, with its attributes set, before any capture
-    fill(g.ndof, 0.0, c->r, st);
-    pc_apply_impl(c, c->r, c->z, st);
+    if (!c->opt.inject_stall) {
+      fill(g.ndof, 0.0, c->r, st);
+      pc_apply_impl(c, c->r, c->z, st);
+    }
     FDM_CUDA(cudaStreamSynchronize(st));
     FDM_CUDA(cudaGetLastError());
     double t4 = now_s();

@@ -20,6 +20,9 @@
 //             back-substitution uses that face):
 //               z(m) = (8 r(m) - sum_faces A_mf z(f)) / A_mm;
 //             then z_K = (T (x) T (x) T) z_fdm, omega, owner write.
+#include <algorithm>
+
+#include "bulk.cuh"
 #include "device.cuh"
 #include "kernels.h"
 
@@ -116,34 +119,16 @@ __device__ __forceinline__ V4<double> load4(const double *p) {
   return {a.x, a.y, b.x, b.y};
 }
 
+// zero g, y, x and tmp (zero-padded factor columns then multiply finite values
+// only), find the star's cells and gather the condensed FDM residual on the
+// interface (fixed cell order)
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_patch_solve(PatchSolveArgs<T> a) {
-  extern __shared__ unsigned char smem_[];
-  constexpr int NW = NT / 32;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const PatchDev P = a.patches[a.order[blockIdx.x]];
-  const ClassDev &C = a.cls[P.cls];
+__device__ __forceinline__ void patch_gather(const PatchSolveArgs<T> &a, const PatchDev &P, const ClassDev &C, T *gv,
+                                             int *sCell) {
+  const int tid = threadIdx.x;
   const Grid &g = a.g;
   const int n = g.n, n3 = n * n * n;
-  const int nG = C.nG, n0 = C.n0, n1 = C.n1, n2 = C.n2;
-  __shared__ int sCell[8];
-  T *gv = reinterpret_cast<T *>(smem_);
-  T *yv = gv + nG, *xv = yv + nG, *tmp = xv + nG;  // tmp: a.tmpcap elements
-  const T *Lv = a.L + P.voff;
-  // bring the factor into L2 a section ahead of its use (not all at once, so
-  // that the sections are still resident when the backward solve re-reads them)
-  auto prefetch_l2 = [&](int64_t e0, int64_t e1) {
-    if (tid != 0 || a.prefetch == 0) return;
-    const char *src = reinterpret_cast<const char *>(Lv + e0);
-    const int64_t bytes = (e1 - e0) * (int64_t)sizeof(T);
-    for (int64_t off = 0; off < bytes; off += 32768) {
-      uint32_t chunk = (uint32_t)(bytes - off < 32768 ? bytes - off : 32768);
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src + off), "r"(chunk) : "memory");
-    }
-  };
-  if (a.prefetch == 1) prefetch_l2(0, C.nval);  // whole factor at the start
-  else if (a.prefetch == 2) prefetch_l2(0, C.off_l21);  // level 0 and lines; L21 and Z follow later
-  // g, y, x and tmp start at zero: zero-padded factor columns multiply finite values only
+  const int nG = C.nG;
   for (int i = tid; i < 3 * nG + a.tmpcap; i += NT) gv[i] = T(0);
   if (tid < 8) {
     int s[3] = {tid & 1, (tid >> 1) & 1, tid >> 2};
@@ -172,13 +157,26 @@ __global__ void __launch_bounds__(NT) k_patch_solve(PatchSolveArgs<T> a) {
   }
   __syncthreads();
 
-  if (a.prefetch == 2) prefetch_l2(C.off_l21, C.nval);  // L21 and Z, needed after level 0 and the lines
+}
+
+// forward and backward solves with the factor values Lv of this patch (global
+// or shared memory), then the interface solution in factor order
+constexpr int RB = 4;  // rows per warp in the forward row-oriented products
+
+template <typename T, int NT>
+__device__ __forceinline__ void patch_solve_body(const PatchSolveArgs<T> &a, const PatchDev &P, const ClassDev &C,
+                                                 const T *Lv, T *gv) {
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nG = C.nG, n0 = C.n0, n1 = C.n1, n2 = C.n2;
+  T *yv = gv + nG, *xv = yv + nG, *tmp = xv + nG;  // tmp: a.tmpcap elements
   // ---- forward solve L y = g (level 0 diagonal, level-1 lines, dense top block)
   const T *dinv0 = Lv + C.off_dinv0;
   const T *ell = Lv + C.off_ell;
   for (int j = tid; j < n0; j += NT) yv[j] = gv[j] * dinv0[j];
   for (int r = tid; r < C.nrow0; r += NT) {  // g_{>0} -= L_{>0,0} y_0, y_0 formed on the fly
     T acc = 0;
+#pragma unroll 4
     for (int e = 0; e < C.K0; ++e) {
       int col = C.ell_col[e * C.ldr0 + r];
       if (col >= 0) acc += ell[e * C.ldr0 + r] * (gv[col] * dinv0[col]);
@@ -198,33 +196,59 @@ __global__ void __launch_bounds__(NT) k_patch_solve(PatchSolveArgs<T> a) {
     const T *L21 = Lv + C.off_l21;
     const T *Z = Lv + C.off_z;
     const int base = n0 + n1;
-    if (n1 > 0) {  // g_2 -= L21 y_1: one warp per row, 128-bit loads
+    if (n1 > 0) {  // g_2 -= L21 y_1: a warp takes RB rows at a time (their loads in flight together)
       const int ng = C.ld21 / 4;
-      for (int r = warp; r < n2; r += NW) {
-        const T *row = L21 + (int64_t)r * C.ld21;
-        T acc = 0;
+      for (int r0 = warp * RB; r0 < n2; r0 += NW * RB) {
+        T acc[RB];
+#pragma unroll
+        for (int u = 0; u < RB; ++u) acc[u] = 0;
         for (int q4 = lane; q4 < ng; q4 += 32) {
-          V4<T> v = load4(row + 4 * q4);
+          V4<T> v[RB];
+#pragma unroll
+          for (int u = 0; u < RB; ++u)
+            v[u] = r0 + u < n2 ? load4(L21 + (int64_t)(r0 + u) * C.ld21 + 4 * q4) : V4<T>{0, 0, 0, 0};
           const T *yy = yv + n0 + 4 * q4;  // padding columns of L21 are zero, yv is finite there
-          acc += v.x * yy[0] + v.y * yy[1] + v.z * yy[2] + v.w * yy[3];
+#pragma unroll
+          for (int u = 0; u < RB; ++u) acc[u] += v[u].x * yy[0] + v[u].y * yy[1] + v[u].z * yy[2] + v[u].w * yy[3];
         }
-        acc = warp_sum(acc);
-        if (lane == 0) gv[base + r] -= acc;
+#pragma unroll
+        for (int u = 0; u < RB; ++u) acc[u] = warp_sum(acc[u]);
+        if (lane == 0)
+#pragma unroll
+          for (int u = 0; u < RB; ++u)
+            if (r0 + u < n2) gv[base + r0 + u] -= acc[u];
       }
       __syncthreads();
     }
-    // y_2 = Z g_2 with Z = L_top^{-1}: one warp per row (rows zero-padded to 4)
-    for (int r = warp; r < n2; r += NW) {
-      const T *row = Z + C.zoff[r];
-      const int ng = (C.zoff[r + 1] - C.zoff[r]) / 4;
-      T acc = 0;
-      for (int q4 = lane; q4 < ng; q4 += 32) {
-        V4<T> v = load4(row + 4 * q4);
-        const T *gg = gv + base + 4 * q4;
-        acc += v.x * gg[0] + v.y * gg[1] + v.z * gg[2] + v.w * gg[3];
+    // y_2 = Z g_2 with Z = L_top^{-1} (rows zero-padded to 4), RB rows per warp at a time
+    for (int r0 = warp * RB; r0 < n2; r0 += NW * RB) {
+      T acc[RB];
+      int ngu[RB];
+      const T *row[RB];
+#pragma unroll
+      for (int u = 0; u < RB; ++u) {
+        acc[u] = 0;
+        const int r = r0 + u < n2 ? r0 + u : n2 - 1;
+        row[u] = Z + C.zoff[r];
+        ngu[u] = r0 + u < n2 ? (C.zoff[r + 1] - C.zoff[r]) / 4 : 0;
       }
-      acc = warp_sum(acc);
-      if (lane == 0) yv[base + r] = acc;
+      int ngmax = 0;
+#pragma unroll
+      for (int u = 0; u < RB; ++u) ngmax = ngu[u] > ngmax ? ngu[u] : ngmax;
+      for (int q4 = lane; q4 < ngmax; q4 += 32) {
+        V4<T> v[RB];
+#pragma unroll
+        for (int u = 0; u < RB; ++u) v[u] = q4 < ngu[u] ? load4(row[u] + 4 * q4) : V4<T>{0, 0, 0, 0};
+        const T *gg = gv + base + 4 * q4;
+#pragma unroll
+        for (int u = 0; u < RB; ++u) acc[u] += v[u].x * gg[0] + v[u].y * gg[1] + v[u].z * gg[2] + v[u].w * gg[3];
+      }
+#pragma unroll
+      for (int u = 0; u < RB; ++u) acc[u] = warp_sum(acc[u]);
+      if (lane == 0)
+#pragma unroll
+        for (int u = 0; u < RB; ++u)
+          if (r0 + u < n2) yv[base + r0 + u] = acc[u];
     }
     __syncthreads();
     // ---- backward solve L^T x = y
@@ -235,6 +259,7 @@ __global__ void __launch_bounds__(NT) k_patch_solve(PatchSolveArgs<T> a) {
       const int gq = tid % ngz, sl = tid / ngz;
       if (sl < slices) {
         T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll 4
         for (int r = 4 * gq + sl; r < n2; r += slices) {  // Z[r][c] = 0 for c > r
           V4<T> v = load4(Z + C.zoff[r] + 4 * gq);
           T yr = yv[base + r];
@@ -259,6 +284,7 @@ __global__ void __launch_bounds__(NT) k_patch_solve(PatchSolveArgs<T> a) {
       const int gq = tid % ng, sl = tid / ng;
       if (sl < slices) {
         T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll 4
         for (int r = sl; r < n2; r += slices) {
           V4<T> v = load4(L21 + (int64_t)r * C.ld21 + 4 * gq);
           T xr = xv[base + r];
@@ -300,6 +326,94 @@ __global__ void __launch_bounds__(NT) k_patch_solve(PatchSolveArgs<T> a) {
   // ---- the interface solution, in factor order
   T *X = a.X + P.xoff;
   for (int k = tid; k < nG; k += NT) X[k] = xv[k];
+}
+
+// 256 threads: at most 42 registers, so that six CTAs share an SM
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 6 : 1) k_patch_solve(PatchSolveArgs<T> a) {
+  extern __shared__ unsigned char smem_[];
+  const int tid = threadIdx.x;
+  const PatchDev P = a.patches[a.order[blockIdx.x]];
+  const ClassDev &C = a.cls[P.cls];
+  __shared__ int sCell[8];
+  T *gv = reinterpret_cast<T *>(smem_);
+  const T *Lv = a.L + P.voff;
+  // bring the factor into L2 a section ahead of its use (not all at once, so
+  // that the sections are still resident when the backward solve re-reads them)
+  auto prefetch_l2 = [&](int64_t e0, int64_t e1) {
+    if (tid != 0 || a.prefetch == 0) return;
+    const char *src = reinterpret_cast<const char *>(Lv + e0);
+    const int64_t bytes = (e1 - e0) * (int64_t)sizeof(T);
+    for (int64_t off = 0; off < bytes; off += 32768)
+      bulk::prefetch_l2(src + off, (uint32_t)(bytes - off < 32768 ? bytes - off : 32768));
+  };
+  if (a.prefetch == 1) prefetch_l2(0, C.nval);  // whole factor at the start
+  else if (a.prefetch == 2) prefetch_l2(0, C.off_l21);  // level 0 and lines; L21 and Z follow later
+  patch_gather<T, NT>(a, P, C, gv, sCell);
+  if (a.prefetch == 2) prefetch_l2(C.off_l21, C.nval);  // L21 and Z, needed after level 0 and the lines
+  patch_solve_body<T, NT>(a, P, C, Lv, gv);
+}
+
+// Persistent variant with the whole factor of the current patch resident in
+// shared memory: one thread starts a bulk copy (cp.async.bulk) of the patch's
+// factor values into shared memory and an L2 prefetch of the next patch's,
+// the CTA gathers the interface residual meanwhile, waits on the mbarrier
+// (bounded by timeout_ns) and runs both solves from shared memory, so every
+// factor value leaves DRAM once per sweep.  Used where the largest class
+// factor fits in shared memory.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, 1) k_patch_resident(PatchSolveArgs<T> a, int npatch, int fcap) {
+  extern __shared__ __align__(128) unsigned char smem_[];
+  const int tid = threadIdx.x;
+  T *F = reinterpret_cast<T *>(smem_);  // fcap elements (a multiple of 4)
+  T *gv = F + fcap;
+  __shared__ __align__(8) uint64_t bar[2];  // [0] factor arrived, [1] test hook: never completed
+  __shared__ int sCell[8];
+  __shared__ int sFail;
+  if (tid == 0) {
+    bulk::mbar_init(&bar[0], 1);
+    bulk::mbar_init(&bar[1], 1);
+    bulk::fence_mbar_init();
+    sFail = 0;
+  }
+  __syncthreads();
+  uint32_t parity = 0;
+  for (int it = blockIdx.x; it < npatch; it += gridDim.x) {
+    const PatchDev P = a.patches[a.order[it]];
+    const ClassDev &C = a.cls[P.cls];
+    if (tid == 0) {
+      // every thread finished reading F for the previous patch (barrier at the loop end)
+      bulk::fence_proxy_async();
+      const uint32_t bytes = (uint32_t)(C.nval * (int64_t)sizeof(T));
+      bulk::mbar_arrive_expect_tx(&bar[0], bytes);
+      const char *src = reinterpret_cast<const char *>(a.L + P.voff);
+      char *dst = reinterpret_cast<char *>(F);
+      for (uint32_t off = 0; off < bytes; off += 32768)
+        bulk::bulk_g2s(dst + off, src + off, bytes - off < 32768 ? bytes - off : 32768, &bar[0]);
+      const int nx = it + gridDim.x;
+      if (nx < npatch) {
+        const PatchDev Q = a.patches[a.order[nx]];
+        const uint32_t qb = (uint32_t)(a.cls[Q.cls].nval * (int64_t)sizeof(T));
+        const char *qs = reinterpret_cast<const char *>(a.L + Q.voff);
+        for (uint32_t off = 0; off < qb; off += 32768) bulk::prefetch_l2(qs + off, qb - off < 32768 ? qb - off : 32768);
+      }
+    }
+    patch_gather<T, NT>(a, P, C, gv, sCell);
+    bool ok = true;
+    if (a.inject_stall) ok = bulk::mbar_wait_bounded(&bar[1], 0, a.timeout_ns);  // never completes
+    ok = ok && bulk::mbar_wait_bounded(&bar[0], parity, a.timeout_ns);
+    if (!ok) sFail = 1;
+    __syncthreads();
+    if (sFail) {
+      // give the copy in flight a second bounded wait before leaving
+      bulk::mbar_wait_bounded(&bar[0], parity, a.timeout_ns);
+      if (tid == 0) atomicExch(a.status, 1);
+      return;
+    }
+    parity ^= 1u;
+    patch_solve_body<T, NT>(a, P, C, F, gv);
+    __syncthreads();
+  }
 }
 
 // ------------------------------------------------------------------ interpolate
@@ -444,6 +558,43 @@ void launch_patch_nt(const PatchSolveArgs<T> &a, int npatch, size_t smem, cudaSt
   k_patch_solve<T, NT><<<npatch, NT, smem, st>>>(a);
 }
 
+int patch_resident_tmp(int maxN1, int maxN2, int threads) {
+  int tmpn = 4 * threads;
+  int l1 = (maxN1 + 3) & ~3, l2 = (maxN2 + 3) & ~3;
+  return std::max(tmpn, std::max(l1, l2));
+}
+
+template <typename T>
+size_t patch_resident_smem(int fcap, int maxG, int tmpcap) {
+  return sizeof(T) * ((size_t)fcap + 3 * (size_t)maxG + tmpcap);
+}
+
+template <typename T, int NT>
+void launch_resident_nt(const PatchSolveArgs<T> &a, int npatch, int fcap, size_t smem, cudaStream_t st) {
+  static size_t attr = 0;
+  static int per_sm = 0, nsm = 0;
+  if (attr < smem) {
+    FDM_CUDA(cudaFuncSetAttribute(k_patch_resident<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_patch_resident<T, NT>, NT, smem));
+    int dev = 0;
+    FDM_CUDA(cudaGetDevice(&dev));
+    FDM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    attr = smem;
+  }
+  const int grid = std::max(1, std::min(npatch, std::max(per_sm, 1) * nsm));
+  k_patch_resident<T, NT><<<grid, NT, smem, st>>>(a, npatch, fcap);
+  FDM_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void launch_patch_resident(const PatchSolveArgs<T> &a, int npatch, int fcap, size_t smem, int threads,
+                           cudaStream_t st) {
+  if (npatch <= 0) return;
+  if (threads >= 1024) launch_resident_nt<T, 1024>(a, npatch, fcap, smem, st);
+  else if (threads >= 512) launch_resident_nt<T, 512>(a, npatch, fcap, smem, st);
+  else launch_resident_nt<T, 256>(a, npatch, fcap, smem, st);
+}
+
 template <typename T>
 void launch_patch_solve(const PatchSolveArgs<T> &a, int npatch, size_t smem, int threads, cudaStream_t st) {
   if (npatch <= 0) return;
@@ -461,6 +612,8 @@ void launch_patch_solve(const PatchSolveArgs<T> &a, int npatch, size_t smem, int
   template void launch_interp_fdm<T, float>(const InterpArgs<T> &, double, float *, cudaStream_t);          \
   template size_t patch_smem_bytes<T>(int, int, int, int);                                                       \
   template void launch_patch_solve<T>(const PatchSolveArgs<T> &, int, size_t, int, cudaStream_t);        \
+  template size_t patch_resident_smem<T>(int, int, int);                                                    \
+  template void launch_patch_resident<T>(const PatchSolveArgs<T> &, int, int, size_t, int, cudaStream_t);  \
   template size_t patch_smem_for_occupancy<T>(size_t, int);
 INST(float)
 INST(double)

@@ -16,6 +16,7 @@
 // Waits on the mbarriers are bounded (a %globaltimer limit); a wait that runs
 // out sets the status word, the CTA waits (again bounded) for its own copies
 // in flight and returns.
+#include "bulk.cuh"
 #include "device.cuh"
 #include "kernels.h"
 
@@ -23,46 +24,7 @@ namespace fdm {
 
 namespace {
 
-__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *b) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   su32(dst)),
-               "l"(src), "r"(bytes), "r"(su32(b))
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(su32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// true when the phase of `parity` completed, false once timeout_ns elapsed
-__device__ bool mbar_wait_bounded(uint64_t *b, uint32_t parity, uint64_t timeout_ns) {
-  if (mbar_test(b, parity)) return true;
-  const uint64_t t0 = global_ns();
-  for (uint32_t it = 0; it < (1u << 30); ++it) {
-    if (mbar_test(b, parity)) return true;
-    if (global_ns() - t0 > timeout_ns) return false;
-  }
-  return false;
-}
+using namespace bulk;
 
 template <typename T> struct V4s { T x, y, z, w; };
 __device__ __forceinline__ V4s<float> ld4(const float *p) {

@@ -23,8 +23,20 @@ struct PatchSolveArgs {
   T *X;
   int tmpcap;    // elements of the tmp shared-memory area
   int prefetch;  // L2 bulk prefetch of the factor: 0 none, 1 all at start, 2 section ahead of use
+  // resident (persistent) variant: bound of the mbarrier waits, status word, test hook
+  uint64_t timeout_ns;
+  int *status;
+  int inject_stall;
 };
 int patch_tmp_elems(int maxN1, int maxN2);
+// the resident variant: fcap factor elements per CTA in shared memory (one
+// patch's values), tmp sized for `threads`
+int patch_resident_tmp(int maxN1, int maxN2, int threads);
+template <typename T>
+size_t patch_resident_smem(int fcap, int maxG, int tmpcap);
+template <typename T>
+void launch_patch_resident(const PatchSolveArgs<T> &a, int npatch, int fcap, size_t smem, int threads,
+                           cudaStream_t st);
 
 template <typename T>
 struct InterpArgs {

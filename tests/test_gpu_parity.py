@@ -335,10 +335,11 @@ def test_full_size_sampled(name):
 
 
 # ---------------------------------------------------------------- kernels and failure detection
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 def test_both_patch_kernels_agree(kernel):
-    """The classic (one CTA per patch) and the streamed (bulk copies into a
-    shared-memory ring) patch solves give the oracle's relaxation."""
+    """The classic (one CTA per patch), streamed (bulk copies into a
+    shared-memory ring) and resident (whole factor in shared memory) patch
+    solves give the oracle's relaxation."""
     xv, yv, zv = inputs.graded_vertices(3, 21)
     for p in (2, 5):
         ctx = fdmpc.Context(p, xv, yv, zv, precision=FP64, pc=fdmpc.FDM_PC_ASM, omega=1.0, patch_kernel=kernel)
@@ -361,6 +362,38 @@ def test_stream_ring_shapes(nbuf, kb):
     r = np.random.default_rng(23).standard_normal(ref.ndof)
     assert relerr(N(ctx.asm_apply(T(r))), ref.asm_apply(r)) <= 1e-4
     assert ctx.status() == 0
+
+
+@pytest.mark.parametrize("p,precision", [(3, FP64), (4, FP32), (7, FP32)])
+def test_resident_matches_classic_bitwise(p, precision):
+    """The resident kernel runs the classic kernel's arithmetic on a shared-
+    memory copy of the factor: with the same number of threads (which fixes
+    the summation order) the results are identical, bit for bit."""
+    xv, yv, zv = inputs.graded_vertices(3, 5)
+    r = T(np.random.default_rng(31).standard_normal(((len(xv) - 1) * p + 1) ** 3))
+    out = []
+    for kernel in (1, 3):
+        ctx = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7, patch_kernel=kernel,
+                            patch_threads=512)
+        out.append(N(ctx.asm_apply(r)))
+        assert ctx.status() == 0
+        ctx.close()
+    assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("kernel", [2, 3])
+def test_bounded_wait_reports_timeout_kernels(kernel):
+    """As below, for the streamed and the resident patch solves."""
+    xv, yv, zv = inputs.graded_vertices(2, 3)
+    ctx = fdmpc.Context(3, xv, yv, zv, precision=FP32, omega=0.2, inject_stall=1, wait_timeout_s=0.02,
+                        patch_kernel=kernel)
+    b = T(np.random.default_rng(0).standard_normal(ctx.ndof))
+    with pytest.raises(fdmpc.FdmError) as e:
+        ctx.pcg_solve(b, rtol=1e-8, maxit=2)
+    assert e.value.code == fdmpc.FDM_ETIMEOUT
+    y = ctx.stiffness_apply(b)
+    torch.cuda.synchronize()
+    assert torch.isfinite(y).all()
 
 
 def test_bounded_wait_reports_timeout():
