@@ -501,6 +501,7 @@ __global__ void __launch_bounds__(256) k_interp_fdm(InterpArgs<T> a, double omeg
 // ------------------------------------------------------------------ launchers
 template <typename T, typename Tin>
 void launch_restrict_fdm(const Grid &g, const Tin *r, const T *tab, const double *mu, T *E, cudaStream_t st) {
+  if (launch_restrict_fast<T, Tin>(g, r, tab, mu, E, st)) return;
   size_t sm = sizeof(T) * (3 * g.n * g.n + 2 * g.n * g.n * g.n);
   static bool attr = false;
   if (!attr) {
@@ -512,6 +513,7 @@ void launch_restrict_fdm(const Grid &g, const Tin *r, const T *tab, const double
 
 template <typename T, typename Tout>
 void launch_interp_fdm(const InterpArgs<T> &a, double omega, Tout *z, cudaStream_t st) {
+  if (launch_interp_fast<T, Tout>(a, omega, z, st)) return;
   size_t sm = sizeof(T) * (3 * a.g.n * a.g.n + 2 * a.g.n * a.g.n * a.g.n);
   static bool attr = false;
   if (!attr) {

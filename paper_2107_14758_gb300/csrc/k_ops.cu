@@ -186,6 +186,7 @@ inline int gs_blocks(int64_t n) {
 
 template <typename T, typename Tin, typename Tout>
 void launch_operator(const OpArgs &a, bool mass, const Tin *u, Tout *y, T *E, cudaStream_t st) {
+  if (!mass && launch_box_op_fast<T, Tin, Tout>(a, u, y, E, st)) return;
   const int n = a.g.n, n3 = n * n * n;
   // box cells use 5 n^3 buffers, curved cells 6
   size_t sm = sizeof(T) * (3 * n * n + (a.general ? 6 : 5) * n3);

@@ -96,6 +96,14 @@ struct OpArgs {
 // y = A u (stiffness) or M u (mass); E is a work buffer of ncell*n^3 elements.
 template <typename T, typename Tin, typename Tout>
 void launch_operator(const OpArgs &a, bool mass, const Tin *u, Tout *y, T *E, cudaStream_t st);
+// cell kernels specialised on n (k_cell.cu); false when no specialisation applies
+template <typename T, typename Tin, typename Tout>
+bool launch_box_op_fast(const OpArgs &a, const Tin *u, Tout *y, T *E, cudaStream_t st);
+template <typename T, typename Tin>
+bool launch_restrict_fast(const Grid &g, const Tin *r, const T *tab, const double *mu, T *E, cudaStream_t st);
+template <typename T, typename Tout>
+bool launch_interp_fast(const InterpArgs<T> &a, double omega, Tout *z, cudaStream_t st);
+
 // per-cell Galerkin coarse matrices P_K^T A^K P_K (FP64), [ncell][8][8]
 void launch_coarse_cell_matrices(const OpArgs &a, double *Ac, cudaStream_t st);
 
