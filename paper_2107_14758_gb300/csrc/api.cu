@@ -41,6 +41,7 @@ struct fdm_ctx {
   double *Gw64 = nullptr, *detw64 = nullptr;
   float *Gw32 = nullptr, *detw32 = nullptr;
   ClassDev *d_cls = nullptr;
+  int *cmap = nullptr;  // cell node -> star interface index per (class, corner)
   std::vector<ClassDev> h_cls;
   std::vector<PatchDev> h_patches;
   PatchDev *d_patches = nullptr;
@@ -253,7 +254,7 @@ void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st) {
   }
   c->tmark(FDM_T_PATCH, false, st);
   c->tmark(FDM_T_INTERP, true, st);
-  InterpArgs<T> ia{c->g, c->d_patches, c->d_cls, c->X<T>(), c->E<T>(), c->mu, c->tab<T>()};
+  InterpArgs<T> ia{c->g, c->d_patches, c->d_cls, c->X<T>(), c->E<T>(), c->mu, c->tab<T>(), c->cmap};
   launch_interp_fdm<T, Tout>(ia, omega, z, st);
   c->tmark(FDM_T_INTERP, false, st);
   c->launches += 3;
@@ -470,6 +471,31 @@ void setup_patches(fdm_ctx *c) {
     c->maxN2 = std::max(c->maxN2, C.n2);
   }
   c->d_cls = c->upload(c->h_cls);
+  {  // cell-to-star map: node (i, j, k) of a cell in the star of its corner o
+    const int n = c->g.n, n3 = n * n * n, p1 = c->p - 1;
+    std::vector<int> cm((size_t)64 * n3, -1);
+    for (int id = 0; id < 8; ++id) {
+      const PatchClass &C = c->classes[id];
+      for (int o = 0; o < 8; ++o)
+        for (int idx = 0; idx < n3; ++idx) {
+          const int li[3] = {idx % n, (idx / n) % n, idx / (n * n)};
+          int t[3];
+          bool ok = true;
+          for (int ax = 0; ax < 3; ++ax) {
+            const int side = (o >> ax) & 1, i = li[ax];
+            if (C.full[ax]) {
+              if (side == 0) { ok = ok && i <= c->p - 1; t[ax] = i + p1; }
+              else { ok = ok && i >= 1; t[ax] = i - 1; }
+            } else {
+              ok = ok && i >= 1 && i <= c->p - 1;
+              t[ax] = i - 1;
+            }
+          }
+          if (ok && C.nd > 0) cm[((size_t)id * 8 + o) * n3 + idx] = C.ginv[t[0] + C.dim[0] * (t[1] + C.dim[1] * t[2])];
+        }
+    }
+    c->cmap = c->upload(cm);
+  }
   const int nvx = c->g.nx + 1, nvy = c->g.ny + 1, nvz = c->g.nz + 1;
   c->npatch = nvx * nvy * nvz;
   c->h_patches.resize(c->npatch);

@@ -64,21 +64,83 @@ __device__ __forceinline__ void line_pass(const T *src, T *dst, const T *M, int 
 }
 
 // ------------------------------------------------------------------ box stiffness
+// Even-odd form of a centrosymmetric 1D matrix (M[i][j] = M[n-1-i][n-1-j],
+// true of the GLL stiffness and mass matrices by the symmetry of the nodes):
+// with h = n/2, x_e = x_m + x_{n-1-m}, x_o = x_m - x_{n-1-m} (m < h),
+//   y_i       = sum_m Me[i][m] x_e + Mo[i][m] x_o (+ M[i][h] x_h for odd n),
+//   y_{n-1-i} = sum_m Me[i][m] x_e - Mo[i][m] x_o (+ M[i][h] x_h),
+//   y_h       = sum_m M[h][m] x_e + M[h][h] x_h     (odd n),
+// Me = (M[i][m] + M[i][n-1-m]) / 2, Mo = (M[i][m] - M[i][n-1-m]) / 2:
+// about n^2 / 2 multiply-adds per line instead of n^2.
+template <typename T, int N>
+struct EO {
+  static constexpr int H = N / 2, S = 2 * H * H + 2 * (H + 1);
+  // layout in shared memory: e[H][H], o[H][H], c[H+1] (M[i][h], i < H; M[h][h] at H), r[H+1] (M[h][m])
+  static __device__ __forceinline__ void build(const T *M, T *t, int tid, int nthreads) {
+    for (int q = tid; q < H * H; q += nthreads) {
+      const int i = q / H, m = q % H;
+      t[q] = T(0.5) * (M[i * N + m] + M[i * N + (N - 1 - m)]);
+      t[H * H + q] = T(0.5) * (M[i * N + m] - M[i * N + (N - 1 - m)]);
+    }
+    if (N % 2 == 1)
+      for (int q = tid; q <= H; q += nthreads) {
+        t[2 * H * H + q] = M[q * N + H];
+        t[2 * H * H + H + 1 + q] = M[H * N + q];
+      }
+  }
+};
+
+template <typename T, int N>
+struct Line {  // a line split into even and odd parts
+  static constexpr int H = N / 2;
+  T e[H > 0 ? H : 1], o[H > 0 ? H : 1], mid;
+  __device__ __forceinline__ void split(const T (&x)[N]) {
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+      e[m] = x[m] + x[N - 1 - m];
+      o[m] = x[m] - x[N - 1 - m];
+    }
+    mid = N % 2 == 1 ? x[H] : T(0);
+  }
+};
+
+// rows i and n-1-i of y = M x (i < h), and the middle row for odd n
+template <typename T, int N>
+__device__ __forceinline__ void eo_pair(const T *t, int i, const Line<T, N> &x, T &yi, T &yj) {
+  constexpr int H = N / 2;
+  T se = 0, so = 0;
+#pragma unroll
+  for (int m = 0; m < H; ++m) {
+    se = mad(t[i * H + m], x.e[m], se);
+    so = mad(t[H * H + i * H + m], x.o[m], so);
+  }
+  if (N % 2 == 1) se = mad(t[2 * H * H + i], x.mid, se);
+  yi = se + so;
+  yj = se - so;
+}
+template <typename T, int N>
+__device__ __forceinline__ T eo_mid(const T *t, const Line<T, N> &x) {
+  constexpr int H = N / 2;
+  T s = t[2 * H * H + H] * x.mid;
+#pragma unroll
+  for (int m = 0; m < H; ++m) s = mad(t[2 * H * H + H + 1 + m], x.e[m], s);
+  return s;
+}
+
 template <typename T, typename Tin, int N>
 __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_box_op(Grid g, const double *__restrict__ mub,
                                                                        const T *__restrict__ tab,
                                                                        const Tin *__restrict__ u, T *__restrict__ E) {
   extern __shared__ __align__(16) unsigned char smem_[];
-  constexpr int P = N - 1, L = N * N, CPB = cells_per_cta<N>(), PS = psize<N>(), N3 = N * N * N;
-  T *sA = reinterpret_cast<T *>(smem_), *sB = sA + N * N;
+  constexpr int P = N - 1, L = N * N, CPB = cells_per_cta<N>(), PS = psize<N>(), N3 = N * N * N, H = N / 2;
+  constexpr int ES = EO<T, N>::S;
+  T *tA = reinterpret_cast<T *>(smem_), *tB = tA + ES;
   const int c = threadIdx.x / L, l = threadIdx.x % L;
-  T *U = sB + N * N + c * 4 * PS, *B1 = U + PS, *B2 = B1 + PS, *B3 = B2 + PS;
+  T *U = tB + ES + c * 4 * PS, *B1 = U + PS, *B2 = B1 + PS, *B3 = B2 + PS;
   const int cell = blockIdx.x * CPB + c;
   const bool valid = cell < g.ncell;
-  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-    sA[i] = tab[tab_off(TAB_A, N) + i];
-    sB[i] = tab[tab_off(TAB_B, N) + i];
-  }
+  EO<T, N>::build(tab + tab_off(TAB_A, N), tA, threadIdx.x, blockDim.x);
+  EO<T, N>::build(tab + tab_off(TAB_B, N), tB, threadIdx.x, blockDim.x);
   T mu0 = 0, mu1 = 0, mu2 = 0;
   if (valid) {
     const int cx = cell % g.nx, cy = (cell / g.nx) % g.ny, cz = cell / (g.nx * g.ny);
@@ -93,86 +155,113 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_box_op(Grid g, c
     }
   }
   __syncthreads();
+  const int a = l % N, b = l / N;
   {  // x: B1 = Bx u, B2 = Ax u
-    const int a = l % N, b = l / N;
     T x[N];
 #pragma unroll
     for (int m = 0; m < N; ++m) x[m] = U[pid<N>(m, a, b)];
+    Line<T, N> xs;
+    xs.split(x);
 #pragma unroll
-    for (int r = 0; r < N; ++r) {
-      B1[pid<N>(r, a, b)] = row_dot<T, N, false>(sB, r, x);
-      B2[pid<N>(r, a, b)] = row_dot<T, N, false>(sA, r, x);
+    for (int i = 0; i < H; ++i) {
+      T y0, y1;
+      eo_pair<T, N>(tB, i, xs, y0, y1);
+      B1[pid<N>(i, a, b)] = y0;
+      B1[pid<N>(N - 1 - i, a, b)] = y1;
+      eo_pair<T, N>(tA, i, xs, y0, y1);
+      B2[pid<N>(i, a, b)] = y0;
+      B2[pid<N>(N - 1 - i, a, b)] = y1;
+    }
+    if (N % 2 == 1) {
+      B1[pid<N>(H, a, b)] = eo_mid<T, N>(tB, xs);
+      B2[pid<N>(H, a, b)] = eo_mid<T, N>(tA, xs);
     }
   }
   __syncthreads();
   {  // y: U = By Bx u, B3 = mu2 Ay Bx u + mu1 By Ax u
-    const int a = l % N, b = l / N;
     T x1[N], x2[N];
 #pragma unroll
     for (int m = 0; m < N; ++m) {
       x1[m] = B1[pid<N>(a, m, b)];
       x2[m] = B2[pid<N>(a, m, b)];
     }
+    Line<T, N> s1, s2;
+    s1.split(x1);
+    s2.split(x2);
 #pragma unroll
-    for (int r = 0; r < N; ++r) {
-      U[pid<N>(a, r, b)] = row_dot<T, N, false>(sB, r, x1);
-      B3[pid<N>(a, r, b)] = mu1 * row_dot<T, N, false>(sA, r, x1) + mu0 * row_dot<T, N, false>(sB, r, x2);
+    for (int i = 0; i < H; ++i) {
+      T p0, p1, q0, q1, r0, r1;
+      eo_pair<T, N>(tB, i, s1, p0, p1);
+      eo_pair<T, N>(tA, i, s1, q0, q1);
+      eo_pair<T, N>(tB, i, s2, r0, r1);
+      U[pid<N>(a, i, b)] = p0;
+      U[pid<N>(a, N - 1 - i, b)] = p1;
+      B3[pid<N>(a, i, b)] = mu1 * q0 + mu0 * r0;
+      B3[pid<N>(a, N - 1 - i, b)] = mu1 * q1 + mu0 * r1;
+    }
+    if (N % 2 == 1) {
+      U[pid<N>(a, H, b)] = eo_mid<T, N>(tB, s1);
+      B3[pid<N>(a, H, b)] = mu1 * eo_mid<T, N>(tA, s1) + mu0 * eo_mid<T, N>(tB, s2);
     }
   }
   __syncthreads();
   if (valid) {  // z: y = Bz B3 + mu3 Az U, cell-local, natural layout
-    const int a = l % N, b = l / N;
     T x3[N], x0[N];
 #pragma unroll
     for (int m = 0; m < N; ++m) {
       x3[m] = B3[pid<N>(a, b, m)];
       x0[m] = U[pid<N>(a, b, m)];
     }
+    Line<T, N> s3, s0;
+    s3.split(x3);
+    s0.split(x0);
     T *out = E + (int64_t)cell * N3;
 #pragma unroll
-    for (int r = 0; r < N; ++r)
-      out[a + N * (b + N * r)] = row_dot<T, N, false>(sB, r, x3) + mu2 * row_dot<T, N, false>(sA, r, x0);
+    for (int i = 0; i < H; ++i) {
+      T p0, p1, q0, q1;
+      eo_pair<T, N>(tB, i, s3, p0, p1);
+      eo_pair<T, N>(tA, i, s0, q0, q1);
+      out[a + N * (b + N * i)] = p0 + mu2 * q0;
+      out[a + N * (b + N * (N - 1 - i))] = p1 + mu2 * q1;
+    }
+    if (N % 2 == 1) out[a + N * (b + N * H)] = eo_mid<T, N>(tB, s3) + mu2 * eo_mid<T, N>(tA, s0);
   }
 }
 
-// direct stiffness summation over the cells containing each node (fixed order)
+// direct stiffness summation over the cells containing each node (fixed
+// order); grid = (x blocks, y, z): no index divisions beyond constants
 template <typename T, typename Tout, int N>
-__global__ void __launch_bounds__(256) k_gather_t(Grid g, const T *__restrict__ E, Tout *__restrict__ y) {
+__global__ void __launch_bounds__(128) k_gather_t(Grid g, const T *__restrict__ E, Tout *__restrict__ y) {
   constexpr int P = N - 1, N3 = N * N * N;
-  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < g.ndof;
-       id += (int64_t)gridDim.x * blockDim.x) {
-    const int gc[3] = {int(id % g.N[0]), int((id / g.N[0]) % g.N[1]), int(id / ((int64_t)g.N[0] * g.N[1]))};
-    const int ncl[3] = {g.nx, g.ny, g.nz};
-    bool dir = false;
-    int cA[3][2], lA[3][2], cnt[3];
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-      const int v = gc[ax];
-      dir |= v == 0 || v == g.N[ax] - 1;
-      const int q = v / P, rm = v - q * P;
-      if (rm == 0) {
-        cnt[ax] = 0;
-        if (q > 0) { cA[ax][cnt[ax]] = q - 1; lA[ax][cnt[ax]++] = P; }
-        if (q < ncl[ax]) { cA[ax][cnt[ax]] = q; lA[ax][cnt[ax]++] = 0; }
-      } else {
-        cA[ax][0] = q;
-        lA[ax][0] = rm;
-        cnt[ax] = 1;
-      }
-    }
-    if (dir) {
-      y[id] = Tout(0);
-      continue;
-    }
-    T s = 0;
-    for (int a2 = 0; a2 < cnt[2]; ++a2)
-      for (int a1 = 0; a1 < cnt[1]; ++a1)
-        for (int a0 = 0; a0 < cnt[0]; ++a0) {
-          const int cell = cA[0][a0] + g.nx * (cA[1][a1] + g.ny * cA[2][a2]);
-          s += E[(int64_t)cell * N3 + lA[0][a0] + N * (lA[1][a1] + N * lA[2][a2])];
-        }
-    y[id] = Tout(s);
+  const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y, gz = blockIdx.z;
+  if (gx >= g.N[0]) return;
+  const int64_t id = gx + (int64_t)g.N[0] * (gy + (int64_t)g.N[1] * gz);
+  if (gx == 0 || gy == 0 || gz == 0 || gx == g.N[0] - 1 || gy == g.N[1] - 1 || gz == g.N[2] - 1) {
+    y[id] = Tout(0);
+    return;
   }
+  const int gc[3] = {gx, gy, gz};
+  int cA[3][2], lA[3][2], cnt[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const int q = gc[ax] / P, rm = gc[ax] - q * P;
+    if (rm == 0) {  // on a cell face along this axis (interior node: both neighbours exist)
+      cA[ax][0] = q - 1; lA[ax][0] = P;
+      cA[ax][1] = q;     lA[ax][1] = 0;
+      cnt[ax] = 2;
+    } else {
+      cA[ax][0] = q; lA[ax][0] = rm;
+      cnt[ax] = 1;
+    }
+  }
+  T s = 0;
+  for (int a2 = 0; a2 < cnt[2]; ++a2)
+    for (int a1 = 0; a1 < cnt[1]; ++a1)
+      for (int a0 = 0; a0 < cnt[0]; ++a0) {
+        const int cell = cA[0][a0] + g.nx * (cA[1][a1] + g.ny * cA[2][a2]);
+        s += E[(int64_t)cell * N3 + lA[0][a0] + N * (lA[1][a1] + N * lA[2][a2])];
+      }
+  y[id] = Tout(s);
 }
 
 // A_mm of an interior node (FDM basis: diagonal) and the coupling of face node
@@ -228,37 +317,42 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_restrict_t(Grid 
   __syncthreads();
   line_pass<T, N, true>(U, V, sT, 2, l);
   __syncthreads();
-  // V holds the FDM-basis residual; U <- t(m) / A_mm on interior nodes
+  // V holds the FDM-basis residual t; U <- t(m) / A_mm on interior nodes
   for (int idx = l; idx < N3; idx += L) {
     const int i = idx % N, j = (idx / N) % N, k = idx / (N * N);
     const bool in = i > 0 && i < P && j > 0 && j < P && k > 0 && k < P;
-    U[pid<N>(i, j, k)] = in ? V[pid<N>(i, j, k)] / diag_ii<T, N>(sAf, sBf, m0, m1, m2, i, j, k) : T(0);
+    if (in) U[pid<N>(i, j, k)] = V[pid<N>(i, j, k)] / diag_ii<T, N>(sAf, sBf, m0, m1, m2, i, j, k);
+  }
+  __syncthreads();
+  // face nodes: t(f) -= A_fI A_II^{-1} t_I along the interior line through f;
+  // thread l owns, for each axis, the line with tangential indices (a, b)
+  {
+    const int a = l % N, b = l / N;
+    if (a > 0 && a < P && b > 0 && b < P) {
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        const T mu_ax = ax == 0 ? m0 : (ax == 1 ? m1 : m2);
+        const T tang = mu_ax * sBf[a * N + a] * sBf[b * N + b];
+        T s0 = 0, sp = 0;
+#pragma unroll
+        for (int ii = 1; ii < P; ++ii) {
+          const T w = U[ax == 0 ? pid<N>(ii, a, b) : (ax == 1 ? pid<N>(a, ii, b) : pid<N>(a, b, ii))];
+          s0 += sAf[0 * N + ii] * w;
+          sp += sAf[P * N + ii] * w;
+        }
+        const int f0 = ax == 0 ? pid<N>(0, a, b) : (ax == 1 ? pid<N>(a, 0, b) : pid<N>(a, b, 0));
+        const int fp = ax == 0 ? pid<N>(P, a, b) : (ax == 1 ? pid<N>(a, P, b) : pid<N>(a, b, P));
+        V[f0] -= tang * s0;
+        V[fp] -= tang * sp;
+      }
+    }
   }
   __syncthreads();
   if (!valid) return;
   T *out = E + (int64_t)cell * N3;
   for (int idx = l; idx < N3; idx += L) {
-    const int li[3] = {idx % N, (idx / N) % N, idx / (N * N)};
-    int nb = 0, ax = -1;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      if (li[a] == 0 || li[a] == P) { ++nb; ax = a; }
-    T v = V[pid<N>(li[0], li[1], li[2])];
-    if (nb == 1) {  // face node: subtract A_fI A_II^{-1} t_I along the interior line through it
-      const int lf = li[ax];
-      const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
-      const T mu_ax = ax == 0 ? m0 : (ax == 1 ? m1 : m2);
-      const T tang = mu_ax * sBf[li[t1] * N + li[t1]] * sBf[li[t2] * N + li[t2]];
-      T s = 0;
-#pragma unroll
-      for (int ii = 1; ii < P; ++ii) {
-        int q[3] = {li[0], li[1], li[2]};
-        q[ax] = ii;
-        s += sAf[lf * N + ii] * U[pid<N>(q[0], q[1], q[2])];
-      }
-      v -= tang * s;
-    }
-    out[idx] = v;
+    const int i = idx % N, j = (idx / N) % N, k = idx / (N * N);
+    out[idx] = V[pid<N>(i, j, k)];
   }
 }
 
@@ -267,7 +361,7 @@ template <typename T, typename Tout, int N>
 __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_interp_t(InterpArgs<T> a, double omega,
                                                                          Tout *__restrict__ z) {
   extern __shared__ __align__(16) unsigned char smem_[];
-  constexpr int P = N - 1, L = N * N, CPB = cells_per_cta<N>(), PS = psize<N>(), N3 = N * N * N, CI = P - 1;
+  constexpr int P = N - 1, L = N * N, CPB = cells_per_cta<N>(), PS = psize<N>(), N3 = N * N * N;
   const Grid &g = a.g;
   T *sT = reinterpret_cast<T *>(smem_), *sAf = sT + N * N, *sBf = sAf + N * N;
   const int c = threadIdx.x / L, l = threadIdx.x % L;
@@ -281,7 +375,6 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_interp_t(InterpA
   }
   int ce[3] = {0, 0, 0};
   T m0 = 0, m1 = 0, m2 = 0;
-  const int ncl[3] = {g.nx, g.ny, g.nz};
   if (valid) {
     ce[0] = cell % g.nx;
     ce[1] = (cell / g.nx) % g.ny;
@@ -289,34 +382,31 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_interp_t(InterpA
     m0 = T(a.mu[3 * cell]);
     m1 = T(a.mu[3 * cell + 1]);
     m2 = T(a.mu[3 * cell + 2]);
-    // interface-type nodes: the sum of the stars' interface solutions
+  }
+  // the stars of the cell's 8 corners: class and offset of their solutions
+  __shared__ int sCls[cells_per_cta<N>()][8];
+  __shared__ int64_t sOff[cells_per_cta<N>()][8];
+  for (int o = l; o < 8; o += L) {  // L = n^2 >= 4: one or two corners per thread
+    sCls[c][o] = 0;
+    sOff[c][o] = 0;
+    if (valid) {
+      const int v0 = ce[0] + (o & 1), v1 = ce[1] + ((o >> 1) & 1), v2 = ce[2] + (o >> 2);
+      const PatchDev Pd = a.patches[v0 + (g.nx + 1) * (v1 + (g.ny + 1) * v2)];
+      sCls[c][o] = Pd.cls;
+      sOff[c][o] = Pd.xoff;
+    }
+  }
+  __syncthreads();
+  if (valid) {  // interface-type nodes: the sum of the stars' interface solutions
     for (int idx = l; idx < N3; idx += L) {
       const int li[3] = {idx % N, (idx / N) % N, idx / (N * N)};
       const bool onb = li[0] == 0 || li[0] == P || li[1] == 0 || li[1] == P || li[2] == 0 || li[2] == P;
       if (!onb) continue;
       T acc = 0;
-      for (int o = 0; o < 8; ++o) {
-        const int oo[3] = {o & 1, (o >> 1) & 1, o >> 2};
-        int v[3], t[3];
-        bool ok = true;
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-          v[ax] = ce[ax] + oo[ax];
-          const bool full = v[ax] >= 1 && v[ax] <= ncl[ax] - 1;
-          const int i = li[ax];
-          if (full) {
-            if (oo[ax] == 0) { ok = ok && i <= P - 1; t[ax] = i + CI; }
-            else { ok = ok && i >= 1; t[ax] = i - 1; }
-          } else {
-            ok = ok && i >= 1 && i <= P - 1;
-            t[ax] = i - 1;
-          }
-        }
-        if (!ok) continue;
-        const PatchDev Pd = a.patches[v[0] + (g.nx + 1) * (v[1] + (g.ny + 1) * v[2])];
-        const ClassDev &C = a.cls[Pd.cls];
-        const int k = C.ginv[t[0] + C.dim[0] * (t[1] + C.dim[1] * t[2])];
-        if (k >= 0) acc += a.X[Pd.xoff + k];
+      for (int o = 0; o < 8; ++o) {
+        const int k = a.cmap[(sCls[c][o] * 8 + o) * N3 + idx];
+        if (k >= 0) acc += a.X[sOff[c][o] + k];
       }
       U[pid<N>(li[0], li[1], li[2])] = acc;
     }
@@ -388,11 +478,6 @@ void set_smem(K kernel, size_t bytes) {
   if (bytes > 48 * 1024) FDM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
 }
 
-inline int gather_blocks(int64_t n) {
-  int64_t b = (n + 255) / 256;
-  return (int)(b < 4 * 152 * 8 ? (b > 0 ? b : 1) : 4 * 152 * 8);
-}
-
 }  // namespace
 
 template <typename T, typename Tin, typename Tout>
@@ -405,10 +490,10 @@ bool launch_box_op_fast(const OpArgs &a, const Tin *u, Tout *y, T *E, cudaStream
     return dispatch_n(a.g.n, [&](auto nc) {
       constexpr int N = decltype(nc)::value;
       constexpr int CPB = cells_per_cta<N>();
-      const size_t sm = sizeof(T) * (2 * N * N + (size_t)CPB * 4 * psize<N>());
+      const size_t sm = sizeof(T) * (2 * EO<T, N>::S + (size_t)CPB * 4 * psize<N>());
       set_smem(k_box_op<T, Tin, N>, sm);
       k_box_op<T, Tin, N><<<(a.g.ncell + CPB - 1) / CPB, CPB * N * N, sm, st>>>(a.g, a.mu_box, tab, u, E);
-      k_gather_t<T, Tout, N><<<gather_blocks(a.g.ndof), 256, 0, st>>>(a.g, E, y);
+      k_gather_t<T, Tout, N><<<dim3((a.g.N[0] + 127) / 128, a.g.N[1], a.g.N[2]), 128, 0, st>>>(a.g, E, y);
     });
   }
 }

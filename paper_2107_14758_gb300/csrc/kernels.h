@@ -47,6 +47,9 @@ struct InterpArgs {
   const T *E;       // condensed cell-local FDM residual (interior entries unchanged)
   const double *mu; // surrogate coefficients
   const T *tab;
+  // [8 classes][8 corners][n^3]: star-interface index of each cell node in the
+  // star of the cell's corner (bit 0: +x, bit 1: +y, bit 2: +z), -1 if none
+  const int *cmap;
 };
 
 // streamed patch solve: per-class chunk schedules over the factor values
