@@ -41,6 +41,29 @@ def _dist():
     return ws, rank, local
 
 
+def reduce_max(value, device=None):
+    """Maximum over the ranks of a per-rank number (identity without a process
+    group): the slowest rank's time is the job's time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world_size, units_per_rank, steps, ms_max):
+    """Whole-job units per second: every rank processes units_per_rank per step
+    (independent problems, weak scaling) and the job takes the slowest rank's time."""
+    return world_size * units_per_rank * steps / (ms_max * 1e-3)
+
+
+def rank_rhs_seed(base_seed, rank):
+    """Seed of a rank's right-hand side: every rank solves its own instance."""
+    return base_seed + 1000 * rank
+
+
 def _peak_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -202,7 +225,7 @@ def bench_gpu(args):
     ctx = fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP32, kernel_timing=1)
     setup_s = list(ctx.setup_seconds())
     free = _free_dofs(ctx.N)
-    f = torch.tensor(inputs.normal_rhs(ctx.ndof, w["seed"] + 1000 * rank), device=dev)
+    f = torch.tensor(inputs.normal_rhs(ctx.ndof, rank_rhs_seed(w["seed"], rank)), device=dev)
     b = ctx.mass_apply(f)
     x = torch.empty_like(b)
 
@@ -235,11 +258,8 @@ def bench_gpu(args):
     ms = e0.elapsed_time(e1)
     kt = ctx.kernel_times()
     launches = ctx.launches()
-    t_tensor = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
-    ms_max = float(t_tensor.item())
-    value = ws * free * args.steps / (ms_max * 1e-3)
+    ms_max = reduce_max(ms, dev)
+    value = job_throughput(ws, free, args.steps, ms_max)
     rel = info.true_rnorm / info.rnorm0
 
     # ---- end to end through the C-ABI with host buffers (copies timed)
@@ -259,10 +279,7 @@ def bench_gpu(args):
         hx.copy_(x, non_blocking=True)
     e3.record(stream)
     torch.cuda.synchronize()
-    t_e2e = torch.tensor([e2.elapsed_time(e3)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-    e2e_value = ws * free * args.steps / (float(t_e2e.item()) * 1e-3)
+    e2e_value = job_throughput(ws, free, args.steps, reduce_max(e2.elapsed_time(e3), dev))
 
     # ---- roofline of the dominant kernel (patch solve), FP32 factors
     ab = ctx.algo_bytes()
