@@ -105,6 +105,10 @@ typedef struct {
                          completed, gives up after wait_timeout_s and reports FDM_ETIMEOUT */
   int patch_prefetch; /* one-CTA-per-patch solve: L2 bulk prefetch of the factor, 1 = all at
                          the start, 2 = one section ahead of use, 3 = none (0 = 3) */
+  int pcg_graph;      /* 1 (default): pcg_solve runs its loop on the device in a captured CUDA
+                         graph (as pcg_solve_batched, a batch of one; the graph is rebuilt when
+                         b, x, rtol or maxit change); 0, or kernel_timing = 1: a host loop with one
+                         synchronisation per iteration */
 } fdm_options;
 
 /* Fills the defaults listed above. */

@@ -93,6 +93,7 @@ struct fdm_ctx {
   std::vector<int> ev_tag;  // tag of each recorded (begin, end) pair
   size_t ev_used = 0;
   bool capturing = false;  // building a CUDA graph: no event timers
+  struct fdm_batch *solo = nullptr;  // one-problem batch of the graph-driven pcg_solve
   void tmark(int tag, bool begin, cudaStream_t st) {
     if (!opt.kernel_timing || capturing) return;
     if (begin) {
@@ -168,6 +169,7 @@ struct fdm_batch {
   unsigned long long *d_times = nullptr;  // [1 + k] global timer: start, end of each solve
   std::vector<const double *> key_b;
   std::vector<double *> key_x;
+  std::vector<size_t> init_kernels, body_kernels;  // kernel nodes per problem: set-up, one iteration
   double key_rtol = -1.0;
   int key_maxit = -1;
   void release_graph() {
@@ -835,6 +837,8 @@ void capture_iteration(fdm_ctx *c, double *x, cudaGraphConditionalHandle h, unsi
 
 void build_batch_graph(fdm_batch *B, const double *const *bv, double *const *xv, double rtol, int maxit) {
   B->release_graph();
+  B->init_kernels.clear();
+  B->body_kernels.clear();
   const int k = (int)B->ctxs.size();
   if (!B->cap) FDM_CUDA(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
   if (!B->d_times) FDM_CUDA(cudaMalloc(&B->d_times, sizeof(unsigned long long) * (k + 1)));
@@ -854,6 +858,7 @@ void build_batch_graph(fdm_batch *B, const double *const *bv, double *const *xv,
   for (int i = 0; i < k; ++i) {
     fdm_ctx *c = B->ctxs[i];
     const int64_t n = c->g.ndof;
+    const int64_t counted = c->launches;  // captured launches do not run now
     c->capturing = true;
     try {
       // x = 0, r = b (Dirichlet entries 0), z = d = 0, ||b||^2
@@ -869,6 +874,9 @@ void build_batch_graph(fdm_batch *B, const double *const *bv, double *const *xv,
       launch_dot(n, c->r, c->r, c->partial, c->dots + 2, B->cap);
       FDM_CUDA(cudaStreamEndCapture(B->cap, &gi));
       cudaGraphNode_t ni, nb, nw;
+      size_t nk = 0;
+      FDM_CUDA(cudaGraphGetNodes(gi, nullptr, &nk));
+      B->init_kernels.push_back(nk + 1);  // + the start kernel below
       FDM_CUDA(cudaGraphAddChildGraphNode(&ni, G, &t0, 1, gi));
       FDM_CUDA(cudaGraphDestroy(gi));
       cudaGraphConditionalHandle h;
@@ -893,6 +901,9 @@ void build_batch_graph(fdm_batch *B, const double *const *bv, double *const *xv,
       FDM_CUDA(cudaStreamBeginCaptureToGraph(B->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
       capture_iteration(c, xv[i], h, B->d_times + 1 + i, B->cap);
       FDM_CUDA(cudaStreamEndCapture(B->cap, &body));
+      size_t nbk = 0;
+      FDM_CUDA(cudaGraphGetNodes(body, nullptr, &nbk));
+      B->body_kernels.push_back(nbk);
     } catch (...) {
       c->capturing = false;
       cudaStreamCaptureStatus cs;
@@ -905,6 +916,7 @@ void build_batch_graph(fdm_batch *B, const double *const *bv, double *const *xv,
       throw;
     }
     c->capturing = false;
+    c->launches = counted;
   }
   FDM_CUDA(cudaGraphInstantiate(&B->exec, G, 0));
   B->key_b.assign(bv, bv + k);
@@ -912,6 +924,67 @@ void build_batch_graph(fdm_batch *B, const double *const *bv, double *const *xv,
   B->key_rtol = rtol;
   B->key_maxit = maxit;
 }
+
+int handle(fdm_ctx *c, const Error &e);
+
+// the captured batched solve (one graph, a device-driven PCG loop per problem)
+int solve_batch(fdm_batch *b, const double *const *bv, double *const *xv, double rtol, int maxit,
+                fdm_solve_info *infos, cudaStream_t st) {
+  const int k = (int)b->ctxs.size();
+  fdm_ctx *c0 = b->ctxs[0];
+  try {
+    const bool same = b->exec && b->key_rtol == rtol && b->key_maxit == maxit &&
+                      std::equal(b->key_b.begin(), b->key_b.end(), bv) && std::equal(b->key_x.begin(), b->key_x.end(), xv);
+    if (!same) build_batch_graph(b, bv, xv, rtol, maxit);
+    FDM_CUDA(cudaGraphLaunch(b->exec, st));
+    FDM_CUDA(cudaStreamSynchronize(st));
+    std::vector<unsigned long long> t(k + 1);
+    FDM_CUDA(cudaMemcpy(t.data(), b->d_times, sizeof(unsigned long long) * (k + 1), cudaMemcpyDeviceToHost));
+    int worst = FDM_OK;
+    for (int i = 0; i < k; ++i) {
+      fdm_ctx *c = b->ctxs[i];
+      double hsc[16];
+      FDM_CUDA(cudaMemcpy(hsc, c->sc, sizeof hsc, cudaMemcpyDeviceToHost));
+      // kernels this problem ran inside the graph (the timer kernel counts for the first)
+      c->launches += (int64_t)b->init_kernels[i] + (int64_t)hsc[13] * (int64_t)b->body_kernels[i] + (i == 0);
+      int hstat = 0;
+      FDM_CUDA(cudaMemcpy(&hstat, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+      int rc = FDM_OK;
+      if (hstat) {
+        FDM_CUDA(cudaMemset(c->status, 0, sizeof(int)));
+        c->err = "a bounded device-side wait of the patch solve ran out";
+        rc = FDM_ETIMEOUT;
+      } else if (hsc[8] != 0.0) {
+        c->err = "non-finite scalar in PCG";
+        rc = FDM_ENAN;
+      } else if (hsc[15] == 0.0) {
+        c->err = "PCG reached maxit";
+        rc = FDM_ENOCONV;
+      }
+      if (infos) {
+        fdm_solve_info &f = infos[i];
+        f.iterations = (int)hsc[13];
+        f.converged = hsc[15] != 0.0;
+        f.rnorm0 = std::sqrt(hsc[12]);
+        f.rnorm = std::sqrt(hsc[14]);
+        f.seconds = hsc[13] > 0 && t[1 + i] > t[0] ? (double)(t[1 + i] - t[0]) * 1e-9 : 0.0;
+        const int64_t n = c->g.ndof;  // true residual ||b - A x||, outside the timed graph
+        launch_operator<double, double, double>(c->op_args(false), false, xv[i], c->q, c->E64, st);
+        launch_sub<double>(n, bv[i], c->q, c->v1, st);
+        mask_dirichlet(c->g, c->v1, st);
+        launch_dot(n, c->v1, c->v1, c->partial, c->dots, st);
+        double h = 0.0;
+        FDM_CUDA(cudaMemcpyAsync(&h, c->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
+        FDM_CUDA(cudaStreamSynchronize(st));
+        f.true_rnorm = std::sqrt(h);
+      }
+      if (rc < worst) worst = rc;
+    }
+    if (worst != FDM_OK) g_last_error = "pcg_solve_batched: a problem did not converge (see its context)";
+    return worst;
+  } catch (const Error &e) { return handle(c0, e); }
+}
+
 
 // ---- learned surrogate helpers
 void need_surrogate_data(const fdm_ctx *c) {
@@ -988,6 +1061,7 @@ int fdm_default_options(fdm_options *opt) {
   opt->stream_buffers = 0;
   opt->stream_buffer_kb = 0;
   opt->inject_stall = 0;
+  opt->pcg_graph = 1;
   return FDM_OK;
 }
 
@@ -1103,6 +1177,17 @@ int pc_apply(fdm_ctx *c, const double *r, double *z, void *stream) {
 int pcg_solve(fdm_ctx *c, const double *b, double *x, double rtol, int maxit, fdm_solve_info *info, void *stream) {
   if (!c || !b || !x || maxit < 0 || !(rtol >= 0.0)) return FDM_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
+  if (c->opt.pcg_graph && !c->opt.kernel_timing) {
+    // the device-driven loop of the batched solve, for a batch of one (its
+    // graph is kept and reused while b, x, rtol and maxit stay the same)
+    if (!c->solo) {
+      c->solo = new fdm_batch();
+      c->solo->ctxs.push_back(c);
+    }
+    const double *bv[1] = {b};
+    double *xv[1] = {x};
+    return solve_batch(c->solo, bv, xv, rtol, maxit, info, st);
+  }
   const int64_t n = c->g.ndof;
   try {
     cudaEvent_t e0, e1;
@@ -1211,57 +1296,7 @@ int pcg_solve_batched(fdm_batch *b, const double *const *bv, double *const *xv, 
   if (k == 0) return FDM_OK;
   for (int i = 0; i < k; ++i)
     if (!bv[i] || !xv[i]) return FDM_EINVAL;
-  fdm_ctx *c0 = b->ctxs[0];
-  try {
-    cudaStream_t st = (cudaStream_t)stream;
-    const bool same = b->exec && b->key_rtol == rtol && b->key_maxit == maxit &&
-                      std::equal(b->key_b.begin(), b->key_b.end(), bv) && std::equal(b->key_x.begin(), b->key_x.end(), xv);
-    if (!same) build_batch_graph(b, bv, xv, rtol, maxit);
-    FDM_CUDA(cudaGraphLaunch(b->exec, st));
-    FDM_CUDA(cudaStreamSynchronize(st));
-    std::vector<unsigned long long> t(k + 1);
-    FDM_CUDA(cudaMemcpy(t.data(), b->d_times, sizeof(unsigned long long) * (k + 1), cudaMemcpyDeviceToHost));
-    int worst = FDM_OK;
-    for (int i = 0; i < k; ++i) {
-      fdm_ctx *c = b->ctxs[i];
-      double hsc[16];
-      FDM_CUDA(cudaMemcpy(hsc, c->sc, sizeof hsc, cudaMemcpyDeviceToHost));
-      int hstat = 0;
-      FDM_CUDA(cudaMemcpy(&hstat, c->status, sizeof(int), cudaMemcpyDeviceToHost));
-      int rc = FDM_OK;
-      if (hstat) {
-        FDM_CUDA(cudaMemset(c->status, 0, sizeof(int)));
-        c->err = "a bounded device-side wait of the patch solve ran out";
-        rc = FDM_ETIMEOUT;
-      } else if (hsc[8] != 0.0) {
-        c->err = "non-finite scalar in PCG";
-        rc = FDM_ENAN;
-      } else if (hsc[15] == 0.0) {
-        c->err = "PCG reached maxit";
-        rc = FDM_ENOCONV;
-      }
-      if (infos) {
-        fdm_solve_info &f = infos[i];
-        f.iterations = (int)hsc[13];
-        f.converged = hsc[15] != 0.0;
-        f.rnorm0 = std::sqrt(hsc[12]);
-        f.rnorm = std::sqrt(hsc[14]);
-        f.seconds = hsc[13] > 0 && t[1 + i] > t[0] ? (double)(t[1 + i] - t[0]) * 1e-9 : 0.0;
-        const int64_t n = c->g.ndof;  // true residual ||b - A x||, outside the timed graph
-        launch_operator<double, double, double>(c->op_args(false), false, xv[i], c->q, c->E64, st);
-        launch_sub<double>(n, bv[i], c->q, c->v1, st);
-        mask_dirichlet(c->g, c->v1, st);
-        launch_dot(n, c->v1, c->v1, c->partial, c->dots, st);
-        double h = 0.0;
-        FDM_CUDA(cudaMemcpyAsync(&h, c->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
-        FDM_CUDA(cudaStreamSynchronize(st));
-        f.true_rnorm = std::sqrt(h);
-      }
-      if (rc < worst) worst = rc;
-    }
-    if (worst != FDM_OK) g_last_error = "pcg_solve_batched: a problem did not converge (see its context)";
-    return worst;
-  } catch (const Error &e) { return handle(c0, e); }
+  return solve_batch(b, bv, xv, rtol, maxit, infos, (cudaStream_t)stream);
 }
 
 void fdm_batch_destroy(fdm_batch *b) { delete b; }
@@ -1591,6 +1626,10 @@ int fdm_query(fdm_ctx *c, int what, void *out, size_t *len) {
 
 const char *fdm_last_error(const fdm_ctx *c) { return c ? c->err.c_str() : g_last_error.c_str(); }
 
-void fdm_destroy(fdm_ctx *c) { delete c; }
+void fdm_destroy(fdm_ctx *c) {
+  if (!c) return;
+  delete c->solo;
+  delete c;
+}
 
 }  // extern "C"
