@@ -28,6 +28,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "q7_graded16"
+WORKLOAD_TEXT = ("q7_graded16: 16^3 graded hex mesh, Q7, 1,367,631 free dofs, N(0,1) nodal f, "
+                 "FP32 V(1,1) preconditioner in FP64 PCG, rtol 1e-8")
 RTOL = 1e-8
 MAXIT = 200
 CPU_SAMPLE_N = 10  # CPU-baseline sample: the same family on a 10^3 graded mesh
@@ -105,10 +107,26 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # wait for the first sample so that the timed region is covered, and keep
+        # only the samples taken after it (the GPU may idle at lower clocks before)
+        t0 = time.time()
+        self.skip = 0
+        while time.time() - t0 < 5.0:
+            self.f.flush()
+            try:
+                with open(self.path) as g:
+                    n = sum(1 for _ in g)
+            except OSError:
+                n = 0
+            if n > 0:
+                self.skip = n
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -121,7 +139,9 @@ class ClockSampler:
         self.f.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for ln, line in enumerate(open(self.path)):
+            if ln < getattr(self, "skip", 0):
+                continue
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -195,7 +215,7 @@ def bench_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": SAMPLE_TEXT, "iterations": int(np.median(its))},
+            "config": {"workload": WORKLOAD_TEXT, "sample": SAMPLE_TEXT, "iterations": int(np.median(its))},
             "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": cpu_cores(), "kind": "oracle",
                              "sample": SAMPLE_TEXT},
             "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -360,8 +380,7 @@ def bench_gpu(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD + ": 16^3 graded hex mesh, Q7, 1,367,631 free dofs, N(0,1) nodal f, "
-                                       "FP32 V(1,1) preconditioner in FP64 PCG, rtol 1e-8",
+                "config": {"workload": WORKLOAD_TEXT,
                            "global_batch": ws, "parallelism": "independent problems per GPU" if ws > 1 else "1 GPU",
                            "l2": "inputs larger than L2 (%.0f MB of FP32 patch factors per solve sweep)" %
                                  (ab["patch32"] / 1e6),
@@ -547,7 +566,8 @@ def bench_batched(dev, fdmpc, inputs, reps=3):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 40 solves on the GPU, 5 oracle solves for --impl reference)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-preconditioner comparison")
@@ -556,7 +576,11 @@ def main():
                     help="skip the p = 15, deformed (learned surrogate) and 64-problem batched workloads")
     args = ap.parse_args()
     if args.impl == "reference":
+        if args.steps is None:
+            args.steps = 5
         return bench_reference(args)
+    if args.steps is None:
+        args.steps = 40
     return bench_gpu(args)
 
 
