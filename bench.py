@@ -124,9 +124,17 @@ class ClockSampler:
             except OSError:
                 n = 0
             if n > 0:
-                self.skip = n
                 break
             time.sleep(0.01)
+        # let the sampler settle (its first queries can stall the GPU briefly), then
+        # keep only the samples taken from here on
+        time.sleep(0.5)
+        self.f.flush()
+        try:
+            with open(self.path) as g:
+                self.skip = sum(1 for _ in g)
+        except OSError:
+            self.skip = 0
 
     def stop(self):
         if self.proc is None:

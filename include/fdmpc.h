@@ -109,6 +109,9 @@ typedef struct {
                          graph (as pcg_solve_batched, a batch of one; the graph is rebuilt when
                          b, x, rtol or maxit change); 0, or kernel_timing = 1: a host loop with one
                          synchronisation per iteration */
+  int patch_l2_hints; /* one-CTA-per-patch solve: 0 (default) or 1 = L2 eviction priorities
+                         (forward solve reads the large factor sections evict-last, backward
+                         solve evict-first), 2 = none */
 } fdm_options;
 
 /* Fills the defaults listed above. */

@@ -64,6 +64,7 @@ struct fdm_ctx {
   // resident patch solve (whole factor of a patch in shared memory), per precision
   bool res64 = false, res32 = false;
   int fcap = 0, res_threads = 512, res_tmp = 0;
+  int rows8 = 0;  // forward products of the classic patch solve: eight rows per warp
   size_t rsmem64 = 0, rsmem32 = 0;
   // coarse
   int nc = 0;
@@ -246,12 +247,12 @@ void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st) {
   } else if (resident) {
     PatchSolveArgs<T> a{c->g, c->d_cls, c->d_patches, c->d_order, c->E<T>(), c->mu, c->tab<T>(), c->L<T>(), c->X<T>(),
                         c->res_tmp, 0, (uint64_t)(std::max(c->opt.wait_timeout_s, 0.0) * 1e9), c->status,
-                        c->opt.inject_stall};
+                        c->opt.inject_stall, 0, 0};
     launch_patch_resident<T>(a, c->nsolve, c->fcap, sizeof(T) == 4 ? c->rsmem32 : c->rsmem64, c->res_threads, st);
   } else {
     PatchSolveArgs<T> a{c->g, c->d_cls, c->d_patches, c->d_order, c->E<T>(), c->mu, c->tab<T>(), c->L<T>(), c->X<T>(),
                         patch_tmp_elems(c->maxN1, c->maxN2), c->opt.patch_prefetch > 0 ? c->opt.patch_prefetch : 3,
-                        0, c->status, 0};
+                        0, c->status, 0, c->opt.patch_l2_hints != 2 ? 1 : 0, c->rows8};
     launch_patch_solve<T>(a, c->nsolve, c->smem<T>(), c->patch_threads, st);
   }
   c->tmark(FDM_T_PATCH, false, st);
@@ -545,6 +546,13 @@ void setup_patches(fdm_ctx *c) {
   c->smem64 = patch_smem_bytes<double>(c->g.n, c->maxG, c->maxN1, c->maxN2);
   c->smem32 = patch_smem_bytes<float>(c->g.n, c->maxG, c->maxN1, c->maxN2);
   c->patch_threads = c->opt.patch_threads > 0 ? c->opt.patch_threads : (c->maxG > 1000 ? 1024 : 256);
+  // eight rows per warp in flight pay off for long L21 rows with 256 threads (measured:
+  // 10 % at Q8, neutral at Q7, slower with 1024 threads at Q15)
+  {
+    int ld21 = 0;
+    for (const PatchClass &C : c->classes) ld21 = std::max(ld21, C.ld21);
+    c->rows8 = c->patch_threads == 256 && ld21 >= 200 ? 1 : 0;
+  }
   c->smem64 = patch_smem_for_occupancy<double>(c->smem64, c->opt.patch_ctas_per_sm);
   c->smem32 = patch_smem_for_occupancy<float>(c->smem32, c->opt.patch_ctas_per_sm);
   if (c->smem64 > 200 * 1024) fail(FDM_EINVAL, "patch interface too large for shared memory");
@@ -1062,6 +1070,7 @@ int fdm_default_options(fdm_options *opt) {
   opt->stream_buffer_kb = 0;
   opt->inject_stall = 0;
   opt->pcg_graph = 1;
+  opt->patch_l2_hints = 0;
   return FDM_OK;
 }
 

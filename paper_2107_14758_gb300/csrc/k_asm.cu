@@ -119,6 +119,40 @@ __device__ __forceinline__ V4<double> load4(const double *p) {
   return {a.x, a.y, b.x, b.y};
 }
 
+// L2 eviction-priority policies: the forward solve reads the factor's large
+// sections (L21, Z) as evict-last so that they survive until the backward
+// solve, which reads them as evict-first (their last use in this sweep)
+__device__ __forceinline__ uint64_t policy_keep() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t policy_normal() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t policy_drop() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ V4<float> load4h(const float *p, uint64_t pol) {
+  if (!__isGlobal(p)) return load4(p);
+  float4 v;
+  asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p), "l"(pol));
+  return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ V4<double> load4h(const double *p, uint64_t pol) {
+  if (!__isGlobal(p)) return load4(p);
+  double2 a, b;
+  asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(a.x), "=d"(a.y) : "l"(p), "l"(pol));
+  asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(b.x), "=d"(b.y) : "l"(p + 2), "l"(pol));
+  return {a.x, a.y, b.x, b.y};
+}
+
 // zero g, y, x and tmp (zero-padded factor columns then multiply finite values
 // only), find the star's cells and gather the condensed FDM residual on the
 // interface (fixed cell order)
@@ -161,25 +195,27 @@ __device__ __forceinline__ void patch_gather(const PatchSolveArgs<T> &a, const P
 
 // forward and backward solves with the factor values Lv of this patch (global
 // or shared memory), then the interface solution in factor order
-constexpr int RB = 4;  // rows per warp in the forward row-oriented products
-
-template <typename T, int NT>
+// RB: rows per warp in the forward row-oriented products (their loads in flight together)
+template <typename T, int NT, int RB>
 __device__ __forceinline__ void patch_solve_body(const PatchSolveArgs<T> &a, const PatchDev &P, const ClassDev &C,
                                                  const T *Lv, T *gv) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nG = C.nG, n0 = C.n0, n1 = C.n1, n2 = C.n2;
   T *yv = gv + nG, *xv = yv + nG, *tmp = xv + nG;  // tmp: a.tmpcap elements
+  // L2 policies of the large factor sections (evict_normal both ways when hints are off)
+  const uint64_t keep = a.l2hint ? policy_keep() : policy_normal(), drop = a.l2hint ? policy_drop() : policy_normal();
   // ---- forward solve L y = g (level 0 diagonal, level-1 lines, dense top block)
   const T *dinv0 = Lv + C.off_dinv0;
   const T *ell = Lv + C.off_ell;
   for (int j = tid; j < n0; j += NT) yv[j] = gv[j] * dinv0[j];
-  for (int r = tid; r < C.nrow0; r += NT) {  // g_{>0} -= L_{>0,0} y_0, y_0 formed on the fly
+  __syncthreads();
+  for (int r = tid; r < C.nrow0; r += NT) {  // g_{>0} -= L_{>0,0} y_0
     T acc = 0;
 #pragma unroll 4
     for (int e = 0; e < C.K0; ++e) {
       int col = C.ell_col[e * C.ldr0 + r];
-      if (col >= 0) acc += ell[e * C.ldr0 + r] * (gv[col] * dinv0[col]);
+      if (col >= 0) acc += ell[e * C.ldr0 + r] * yv[col];
     }
     gv[n0 + r] -= acc;
   }
@@ -206,7 +242,7 @@ __device__ __forceinline__ void patch_solve_body(const PatchSolveArgs<T> &a, con
           V4<T> v[RB];
 #pragma unroll
           for (int u = 0; u < RB; ++u)
-            v[u] = r0 + u < n2 ? load4(L21 + (int64_t)(r0 + u) * C.ld21 + 4 * q4) : V4<T>{0, 0, 0, 0};
+            v[u] = r0 + u < n2 ? load4h(L21 + (int64_t)(r0 + u) * C.ld21 + 4 * q4, keep) : V4<T>{0, 0, 0, 0};
           const T *yy = yv + n0 + 4 * q4;  // padding columns of L21 are zero, yv is finite there
 #pragma unroll
           for (int u = 0; u < RB; ++u) acc[u] += v[u].x * yy[0] + v[u].y * yy[1] + v[u].z * yy[2] + v[u].w * yy[3];
@@ -238,7 +274,7 @@ __device__ __forceinline__ void patch_solve_body(const PatchSolveArgs<T> &a, con
       for (int q4 = lane; q4 < ngmax; q4 += 32) {
         V4<T> v[RB];
 #pragma unroll
-        for (int u = 0; u < RB; ++u) v[u] = q4 < ngu[u] ? load4(row[u] + 4 * q4) : V4<T>{0, 0, 0, 0};
+        for (int u = 0; u < RB; ++u) v[u] = q4 < ngu[u] ? load4h(row[u] + 4 * q4, keep) : V4<T>{0, 0, 0, 0};
         const T *gg = gv + base + 4 * q4;
 #pragma unroll
         for (int u = 0; u < RB; ++u) acc[u] += v[u].x * gg[0] + v[u].y * gg[1] + v[u].z * gg[2] + v[u].w * gg[3];
@@ -259,9 +295,12 @@ __device__ __forceinline__ void patch_solve_body(const PatchSolveArgs<T> &a, con
       const int gq = tid % ngz, sl = tid / ngz;
       if (sl < slices) {
         T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        // rows r = sl (mod slices) with r >= 4 gq (Z[r][c] = 0 for c > r): the threads of
+        // a slice walk the same rows, so a warp reads contiguous groups of one row
+        const int lo = 4 * gq > sl ? sl + (4 * gq - sl + slices - 1) / slices * slices : sl;
 #pragma unroll 4
-        for (int r = 4 * gq + sl; r < n2; r += slices) {  // Z[r][c] = 0 for c > r
-          V4<T> v = load4(Z + C.zoff[r] + 4 * gq);
+        for (int r = lo; r < n2; r += slices) {
+          V4<T> v = load4h(Z + C.zoff[r] + 4 * gq, drop);
           T yr = yv[base + r];
           a0 += v.x * yr; a1 += v.y * yr; a2 += v.z * yr; a3 += v.w * yr;
         }
@@ -286,7 +325,7 @@ __device__ __forceinline__ void patch_solve_body(const PatchSolveArgs<T> &a, con
         T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
 #pragma unroll 4
         for (int r = sl; r < n2; r += slices) {
-          V4<T> v = load4(L21 + (int64_t)r * C.ld21 + 4 * gq);
+          V4<T> v = load4h(L21 + (int64_t)r * C.ld21 + 4 * gq, drop);
           T xr = xv[base + r];
           a0 += v.x * xr; a1 += v.y * xr; a2 += v.z * xr; a3 += v.w * xr;
         }
@@ -328,9 +367,10 @@ __device__ __forceinline__ void patch_solve_body(const PatchSolveArgs<T> &a, con
   for (int k = tid; k < nG; k += NT) X[k] = xv[k];
 }
 
-// 256 threads: at most 42 registers, so that six CTAs share an SM
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT, NT == 256 ? 6 : 1) k_patch_solve(PatchSolveArgs<T> a) {
+// 256 threads: at most 42 registers with four rows per warp (six CTAs per SM),
+// 51 with eight (five CTAs per SM)
+template <typename T, int NT, int RB>
+__global__ void __launch_bounds__(NT, NT == 256 ? (RB == 4 ? 6 : 5) : 1) k_patch_solve(PatchSolveArgs<T> a) {
   extern __shared__ unsigned char smem_[];
   const int tid = threadIdx.x;
   const PatchDev P = a.patches[a.order[blockIdx.x]];
@@ -351,7 +391,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 6 : 1) k_patch_solve(PatchSolv
   else if (a.prefetch == 2) prefetch_l2(0, C.off_l21);  // level 0 and lines; L21 and Z follow later
   patch_gather<T, NT>(a, P, C, gv, sCell);
   if (a.prefetch == 2) prefetch_l2(C.off_l21, C.nval);  // L21 and Z, needed after level 0 and the lines
-  patch_solve_body<T, NT>(a, P, C, Lv, gv);
+  patch_solve_body<T, NT, RB>(a, P, C, Lv, gv);
 }
 
 // Persistent variant with the whole factor of the current patch resident in
@@ -411,7 +451,7 @@ __global__ void __launch_bounds__(NT, 1) k_patch_resident(PatchSolveArgs<T> a, i
       return;
     }
     parity ^= 1u;
-    patch_solve_body<T, NT>(a, P, C, F, gv);
+    patch_solve_body<T, NT, 4>(a, P, C, F, gv);
     __syncthreads();
   }
 }
@@ -554,10 +594,12 @@ template <typename T, int NT>
 void launch_patch_nt(const PatchSolveArgs<T> &a, int npatch, size_t smem, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_patch_solve<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_patch_solve<T, NT, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_patch_solve<T, NT, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  k_patch_solve<T, NT><<<npatch, NT, smem, st>>>(a);
+  if (a.rows8) k_patch_solve<T, NT, 8><<<npatch, NT, smem, st>>>(a);
+  else k_patch_solve<T, NT, 4><<<npatch, NT, smem, st>>>(a);
 }
 
 int patch_resident_tmp(int maxN1, int maxN2, int threads) {

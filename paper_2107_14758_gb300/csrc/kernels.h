@@ -27,6 +27,8 @@ struct PatchSolveArgs {
   uint64_t timeout_ns;
   int *status;
   int inject_stall;
+  int l2hint;  // L2 eviction priorities: forward reads evict-last, backward reads evict-first
+  int rows8;   // eight rows per warp in the forward products (else four)
 };
 int patch_tmp_elems(int maxN1, int maxN2);
 // the resident variant: fcap factor elements per CTA in shared memory (one

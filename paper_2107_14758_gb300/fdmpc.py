@@ -43,7 +43,8 @@ class fdm_options(C.Structure):
                 ("wait_timeout_s", C.c_double), ("lanczos_start", C.POINTER(C.c_double)),
                 ("kernel_timing", C.c_int), ("patch_ctas_per_sm", C.c_int), ("patch_threads", C.c_int),
                 ("patch_kernel", C.c_int), ("stream_buffers", C.c_int), ("stream_buffer_kb", C.c_int),
-                ("inject_stall", C.c_int), ("patch_prefetch", C.c_int), ("pcg_graph", C.c_int)]
+                ("inject_stall", C.c_int), ("patch_prefetch", C.c_int), ("pcg_graph", C.c_int),
+                ("patch_l2_hints", C.c_int)]
 
 
 class fdm_solve_info(C.Structure):
@@ -257,7 +258,7 @@ class Context:
     def __init__(self, p, xv, yv, zv, jac=None, kappa=None, samples27=None, precision=FDM_PREC_FP32, pc=FDM_PC_VCYCLE,
                  omega=0.0, lanczos_start=None, lanczos_steps=20, flexible_beta=-1, kernel_timing=0,
                  patch_ctas_per_sm=0, patch_threads=0, patch_kernel=0, stream_buffers=0, stream_buffer_kb=0,
-                 inject_stall=0, wait_timeout_s=1.0, patch_prefetch=0, pcg_graph=1, stream=None):
+                 inject_stall=0, wait_timeout_s=1.0, patch_prefetch=0, pcg_graph=1, patch_l2_hints=0, stream=None):
         self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (xv, yv, zv)]
         mesh = fdm_mesh()
         mesh.nx, mesh.ny, mesh.nz = len(xv) - 1, len(yv) - 1, len(zv) - 1
@@ -287,6 +288,7 @@ class Context:
         opt.inject_stall = inject_stall
         opt.patch_prefetch = patch_prefetch
         opt.pcg_graph = pcg_graph
+        opt.patch_l2_hints = patch_l2_hints
         opt.wait_timeout_s = wait_timeout_s
         if lanczos_start is not None:
             s = np.ascontiguousarray(lanczos_start, dtype=np.float64)
