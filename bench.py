@@ -251,8 +251,9 @@ def bench_gpu(args):
 
     w = inputs.workload(WORKLOAD)
     # the timed solves: the device-driven PCG loop (captured graph), no per-kernel events
-    ctx = fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP32)
+    ctx = fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP32, autotune=1)
     setup_s = list(ctx.setup_seconds())
+    tuning = ctx.tuning()
     free = _free_dofs(ctx.N)
     f = torch.tensor(inputs.normal_rhs(ctx.ndof, rank_rhs_seed(w["seed"], rank)), device=dev)
     b = ctx.mass_apply(f)
@@ -313,7 +314,9 @@ def bench_gpu(args):
 
     # ---- roofline of the dominant kernel (patch solve), FP32 factors: the same
     # solves through the host loop with CUDA events around every kernel group
-    ctx_kt = fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP32, kernel_timing=1)
+    ctx_kt = fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP32, kernel_timing=1,
+                           patch_kernel=3 if tuning[0] == 3 else 1, patch_threads=tuning[1],
+                           patch_rows_per_warp=8 if tuning[2] else 4)
     for _ in range(args.warmup):
         ctx_kt.pcg_solve(b, x, rtol=RTOL, maxit=MAXIT)
     ctx_kt.kernel_times()
@@ -393,12 +396,16 @@ def bench_gpu(args):
                            "l2": "inputs larger than L2 (%.0f MB of FP32 patch factors per solve sweep)" %
                                  (ab["patch32"] / 1e6),
                            "iterations": int(np.median(iters)), "true_rel_residual": rel,
-                           "setup_seconds": sum(setup_s)},
+                           "setup_seconds": sum(setup_s),
+                           "autotuned_patch_solve": {"kernel": "resident" if tuning[0] == 3 else "one CTA per patch",
+                                                     "threads": tuning[1], "rows_per_warp": 8 if tuning[2] else 4,
+                                                     "sweep_us": tuning[3], "candidates": tuning[4]}},
                 "clocks": clocks,
                 "e2e": {"value": e2e_value, "unit": "DoF/s", "h2d_bytes_per_step": 8 * ctx.ndof,
                         "d2h_bytes_per_step": 8 * ctx.ndof},
                 "gpu_launches": int(launches),
-                "roofline": {"kernel": "k_patch_solve<float>", "bound": "hbm", "achieved": achieved, "peak": peak,
+                "roofline": {"kernel": "k_patch_resident<float>" if tuning[0] == 3 else "k_patch_solve<float>",
+                             "bound": "hbm", "achieved": achieved, "peak": peak,
                              "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                              "algorithmic_bytes_per_launch": ab["patch32"], "avg_launch_ms": patch_ms,
                              "launches": pcount},
@@ -435,7 +442,7 @@ def bench_p15(dev, fdmpc, inputs, peak):
     FP64 solves, pc_apply throughput and its HBM fraction."""
     import torch
     w = inputs.workload("q15_uniform8")
-    ctx = fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP32)
+    ctx = fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP32, autotune=1)
     free = _free_dofs(ctx.N)
     b = ctx.mass_apply(torch.tensor(inputs.manufactured_f(w["xv"], w["yv"], w["zv"], w["p"]), device=dev))
     x = torch.empty_like(b)
@@ -540,7 +547,7 @@ def bench_batched(dev, fdmpc, inputs, reps=3):
         n, p = len(w["xv"]) - 1, w["p"]
         nd = (n * p + 1) ** 3
         ctxs.append(fdmpc.Context(p, w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP32,
-                                  lanczos_start=inputs.lanczos_start(nd)))
+                                  lanczos_start=inputs.lanczos_start(nd), autotune=1))
         bs.append(torch.tensor(inputs.normal_rhs(nd, w["seed"]), device=dev))
     setup_s = time.time() - t0
     free = sum(_free_dofs(c.N) for c in ctxs)

@@ -112,6 +112,15 @@ typedef struct {
   int patch_l2_hints; /* one-CTA-per-patch solve: 0 (default) or 1 = L2 eviction priorities
                          (forward solve reads the large factor sections evict-last, backward
                          solve evict-first), 2 = none */
+  int autotune;       /* 1: at set-up, time one relaxation sweep with each patch-solve variant
+                         (256 threads with four or eight rows per warp in the forward products,
+                         512, 1024 threads, the resident kernel where it fits) and keep the
+                         fastest (FDM_Q_TUNING); 0 (default): the fixed rule (patch_threads,
+                         patch_kernel).  Variants sum in different orders: results of contexts
+                         tuned differently agree to rounding, not bit for bit */
+  int patch_rows_per_warp; /* rows a warp keeps in flight in the forward products of the
+                              one-CTA-per-patch solve: 4 or 8 (0 = 8 for 256 threads and L21
+                              rows of 200 or more, else 4) */
 } fdm_options;
 
 /* Fills the defaults listed above. */
@@ -271,6 +280,9 @@ int fdm_surrogate_apply(fdm_ctx *ctx, const float *w, int judge, int *nfallback,
                                   at mu* (NaN without samples27) and at the current mu */
 #define FDM_Q_MUBAR 22         /* double[3*ncell]: averaged surrogate mu_avg (curved cells) */
 #define FDM_Q_SURR_OUTPUT 23   /* float[3*ncell]: network outputs c of the last fdm_surrogate_apply */
+#define FDM_Q_TUNING 24        /* double[8]: autotuner choice: patch kernel (1 classic, 3 resident),
+                                  threads, eight rows per warp (0/1), sweep time (us), candidates
+                                  timed; zeros without autotune */
 /* timers of FDM_Q_KERNEL_TIMES */
 #define FDM_T_RESTRICT 0  /* basis change to the FDM basis */
 #define FDM_T_PATCH 1     /* patch gather + condense + triangular solves + back-substitution */

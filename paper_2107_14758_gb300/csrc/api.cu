@@ -65,6 +65,7 @@ struct fdm_ctx {
   bool res64 = false, res32 = false;
   int fcap = 0, res_threads = 512, res_tmp = 0;
   int rows8 = 0;  // forward products of the classic patch solve: eight rows per warp
+  double tuning[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // autotuner: kernel, threads, rows8, best us, candidates tried
   size_t rsmem64 = 0, rsmem32 = 0;
   // coarse
   int nc = 0;
@@ -551,7 +552,9 @@ void setup_patches(fdm_ctx *c) {
   {
     int ld21 = 0;
     for (const PatchClass &C : c->classes) ld21 = std::max(ld21, C.ld21);
-    c->rows8 = c->patch_threads == 256 && ld21 >= 200 ? 1 : 0;
+    c->rows8 = c->opt.patch_rows_per_warp == 8   ? 1
+               : c->opt.patch_rows_per_warp == 4 ? 0
+                                                   : (c->patch_threads == 256 && ld21 >= 200 ? 1 : 0);
   }
   c->smem64 = patch_smem_for_occupancy<double>(c->smem64, c->opt.patch_ctas_per_sm);
   c->smem32 = patch_smem_for_occupancy<float>(c->smem32, c->opt.patch_ctas_per_sm);
@@ -761,6 +764,66 @@ void lanczos_omega(fdm_ctx *c, const double *start_host, cudaStream_t st) {
   tridiag_extremes(dd, ee, c->lmin, c->lmax);
   const double alpha = 0.25;
   c->omega = 2.0 / ((1.0 + alpha) * c->lmax + (1.0 - alpha) * c->lmin);
+}
+
+// ---- autotuner: the patch-solve variant with the shortest relaxation sweep
+// Candidates: one CTA per patch with 256 threads (four or eight rows per warp
+// in the forward products), 512 or 1024 threads, and the resident kernel where
+// a patch factor fits in shared memory.  Each is timed with CUDA events over
+// `reps` sweeps in the context's preconditioner precision after two untimed
+// ones, on the set-up's work vectors; the fastest is kept.
+void autotune_patch(fdm_ctx *c, cudaStream_t st) {
+  struct Cand { int kernel, threads, rows8; };
+  std::vector<Cand> cands = {{1, 256, 0}, {1, 256, 1}, {1, 512, 0}, {1, 1024, 0}};
+  const bool fp32 = c->opt.precision == FDM_PREC_FP32;
+  const size_t rs = fp32 ? c->rsmem32 : c->rsmem64;
+  if (rs <= 225 * 1024) cands.push_back({3, 512, 0});
+  const int64_t n = c->g.ndof;
+  fill(n, 1.0, c->r, st);
+  mask_dirichlet(c->g, c->r, st);
+  cudaEvent_t e0, e1;
+  FDM_CUDA(cudaEventCreate(&e0));
+  FDM_CUDA(cudaEventCreate(&e1));
+  const int reps = 5;
+  double best = 1e300;
+  Cand pick = {1, c->patch_threads, c->rows8};
+  const int rthreads = c->res_threads;
+  for (const Cand &k : cands) {
+    c->patch_threads = k.threads;
+    c->rows8 = k.rows8;
+    c->res32 = fp32 && k.kernel == 3;
+    c->res64 = !fp32 && k.kernel == 3;
+    c->res_threads = k.threads;
+    auto sweep = [&]() {
+      if (fp32) run_asm<float, double, double>(c, c->r, c->z, c->omega, st);
+      else run_asm<double, double, double>(c, c->r, c->z, c->omega, st);
+    };
+    sweep();
+    sweep();
+    FDM_CUDA(cudaEventRecord(e0, st));
+    for (int i = 0; i < reps; ++i) sweep();
+    FDM_CUDA(cudaEventRecord(e1, st));
+    FDM_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    FDM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    const double us = 1e3 * ms / reps;
+    if (us < best) {
+      best = us;
+      pick = k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->patch_threads = pick.threads;
+  c->rows8 = pick.rows8;
+  c->res32 = fp32 && pick.kernel == 3;
+  c->res64 = !fp32 && pick.kernel == 3;
+  c->res_threads = pick.kernel == 3 ? pick.threads : rthreads;
+  c->tuning[0] = pick.kernel;
+  c->tuning[1] = pick.threads;
+  c->tuning[2] = pick.rows8;
+  c->tuning[3] = best;
+  c->tuning[4] = (double)cands.size();
 }
 
 // ---- batched solves: one CUDA graph, a device-driven PCG loop per problem
@@ -1071,6 +1134,8 @@ int fdm_default_options(fdm_options *opt) {
   opt->inject_stall = 0;
   opt->pcg_graph = 1;
   opt->patch_l2_hints = 0;
+  opt->autotune = 0;
+  opt->patch_rows_per_warp = 0;
   return FDM_OK;
 }
 
@@ -1124,6 +1189,7 @@ int fdm_setup(const fdm_mesh *mesh, int p, const fdm_coeff *coeff, const fdm_opt
     }
     // one preconditioner application (on r = 0) so that every kernel of the
     // solve has been launched once, with its attributes set, before any capture
+    if (c->opt.autotune && !c->opt.inject_stall && !c->stream) autotune_patch(c, st);
     if (!c->opt.inject_stall) {
       fill(g.ndof, 0.0, c->r, st);
       pc_apply_impl(c, c->r, c->z, st);
@@ -1580,6 +1646,7 @@ int fdm_query(fdm_ctx *c, int what, void *out, size_t *len) {
         put(h.data(), h.size() * sizeof(float));
         break;
       }
+      case FDM_Q_TUNING: put(c->tuning, sizeof c->tuning); break;
       case FDM_Q_STATUS: {
         int v = 0;
         FDM_CUDA(cudaMemcpy(&v, c->status, sizeof(int), cudaMemcpyDeviceToHost));

@@ -22,7 +22,7 @@ FDM_SURR_AVERAGED, FDM_SURR_EXTERNAL = 0, 1
 (FDM_Q_NDOF, FDM_Q_OMEGA, FDM_Q_LAMBDA, FDM_Q_MU, FDM_Q_NPATCH, FDM_Q_PATCH_CLASS, FDM_Q_CLASS_INFO,
  FDM_Q_GAMMA_ORDER, FDM_Q_FACTOR_NNZ, FDM_Q_PATTERN, FDM_Q_FACTOR, FDM_Q_BASIS, FDM_Q_FACTOR_BYTES,
  FDM_Q_SETUP_SECONDS, FDM_Q_KERNEL_TIMES, FDM_Q_LAUNCHES, FDM_Q_ALGO_BYTES, FDM_Q_STATUS,
- FDM_Q_SURR_FEATURES, FDM_Q_SURR_LABELS, FDM_Q_SURR_BOUNDS, FDM_Q_MUBAR, FDM_Q_SURR_OUTPUT) = range(1, 24)
+ FDM_Q_SURR_FEATURES, FDM_Q_SURR_LABELS, FDM_Q_SURR_BOUNDS, FDM_Q_MUBAR, FDM_Q_SURR_OUTPUT, FDM_Q_TUNING) = range(1, 25)
 FDM_MLP_NPARAM = 16515
 TIMERS = ("restrict", "patch", "interp", "op64", "op32", "coarse", "vec")
 
@@ -44,7 +44,7 @@ class fdm_options(C.Structure):
                 ("kernel_timing", C.c_int), ("patch_ctas_per_sm", C.c_int), ("patch_threads", C.c_int),
                 ("patch_kernel", C.c_int), ("stream_buffers", C.c_int), ("stream_buffer_kb", C.c_int),
                 ("inject_stall", C.c_int), ("patch_prefetch", C.c_int), ("pcg_graph", C.c_int),
-                ("patch_l2_hints", C.c_int)]
+                ("patch_l2_hints", C.c_int), ("autotune", C.c_int), ("patch_rows_per_warp", C.c_int)]
 
 
 class fdm_solve_info(C.Structure):
@@ -258,7 +258,8 @@ class Context:
     def __init__(self, p, xv, yv, zv, jac=None, kappa=None, samples27=None, precision=FDM_PREC_FP32, pc=FDM_PC_VCYCLE,
                  omega=0.0, lanczos_start=None, lanczos_steps=20, flexible_beta=-1, kernel_timing=0,
                  patch_ctas_per_sm=0, patch_threads=0, patch_kernel=0, stream_buffers=0, stream_buffer_kb=0,
-                 inject_stall=0, wait_timeout_s=1.0, patch_prefetch=0, pcg_graph=1, patch_l2_hints=0, stream=None):
+                 inject_stall=0, wait_timeout_s=1.0, patch_prefetch=0, pcg_graph=1, patch_l2_hints=0, autotune=0, patch_rows_per_warp=0,
+                 stream=None):
         self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (xv, yv, zv)]
         mesh = fdm_mesh()
         mesh.nx, mesh.ny, mesh.nz = len(xv) - 1, len(yv) - 1, len(zv) - 1
@@ -289,6 +290,8 @@ class Context:
         opt.patch_prefetch = patch_prefetch
         opt.pcg_graph = pcg_graph
         opt.patch_l2_hints = patch_l2_hints
+        opt.autotune = autotune
+        opt.patch_rows_per_warp = patch_rows_per_warp
         opt.wait_timeout_s = wait_timeout_s
         if lanczos_start is not None:
             s = np.ascontiguousarray(lanczos_start, dtype=np.float64)
@@ -368,6 +371,11 @@ class Context:
 
     def surrogate_output(self):
         return self.query(FDM_Q_SURR_OUTPUT, np.float32, 3 * self.ncell).reshape(self.ncell, 3)
+
+    def tuning(self):
+        """(kernel, threads, rows8, sweep us, candidates) chosen by the autotuner."""
+        t = self.query(FDM_Q_TUNING, np.float64, 8)
+        return int(t[0]), int(t[1]), int(t[2]), float(t[3]), int(t[4])
 
     def lanczos_extremes(self):
         return tuple(self.query(FDM_Q_LAMBDA, np.float64, 2))

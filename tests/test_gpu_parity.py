@@ -396,6 +396,23 @@ def test_bounded_wait_reports_timeout_kernels(kernel):
     assert torch.isfinite(y).all()
 
 
+@pytest.mark.parametrize("p,precision", [(4, FP32), (7, FP32), (3, FP64)])
+def test_autotuned_context_matches(p, precision):
+    """The autotuner keeps one of its candidates; the tuned context gives the
+    default context's relaxation to rounding (the variants sum in different
+    orders) and the same PCG solution."""
+    xv, yv, zv = inputs.graded_vertices(3, 8)
+    r = T(np.random.default_rng(41).standard_normal(((len(xv) - 1) * p + 1) ** 3))
+    a = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7)
+    b = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7, autotune=1)
+    kernel, threads, rows8, us, ncand = b.tuning()
+    assert kernel in (1, 3) and threads in (256, 512, 1024) and rows8 in (0, 1) and us > 0 and ncand >= 4
+    assert a.tuning()[4] == 0
+    tol = 1e-12 if precision == FP64 else 1e-5
+    assert relerr(N(b.asm_apply(r)), N(a.asm_apply(r))) <= tol
+    assert b.status() == 0
+
+
 def test_bounded_wait_reports_timeout():
     """Failure detection without a GPU fault: the streamed solve is made to
     wait on a barrier that nothing completes; the wait gives up after the
