@@ -98,7 +98,9 @@ typedef struct {
   int patch_kernel;   /* 0 = automatic (= 1), 1 = one CTA per patch reading the factor
                          directly, 2 = streamed: bulk copies into a shared-memory ring,
                          3 = resident: persistent CTAs that bulk-copy each patch's whole factor
-                         into shared memory (falls back to 1 where it does not fit) */
+                         into shared memory (falls back to 1 where it does not fit), 4 = cluster:
+                         the interior stars on thread-block clusters that hold L21 in shared
+                         memory across both solves, the other stars as 1 */
   int stream_buffers; /* ring buffers of the streamed solve (0 = 4) */
   int stream_buffer_kb; /* size of each ring buffer in KiB (0 = 16) */
   int inject_stall;   /* test hook: the streamed solve waits on a barrier that is never

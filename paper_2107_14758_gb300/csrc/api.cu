@@ -65,6 +65,11 @@ struct fdm_ctx {
   bool res64 = false, res32 = false;
   int fcap = 0, res_threads = 512, res_tmp = 0;
   int rows8 = 0;  // forward products of the classic patch solve: eight rows per warp
+  // cluster patch solve for the classes with a dense top level (a prefix of the order)
+  int n_heavy = 0, cl_threads = 256;
+  bool cl32 = false, cl64 = false;
+  ClusterArgs<float> cla32{};
+  ClusterArgs<double> cla64{};
   double tuning[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // autotuner: kernel, threads, rows8, best us, candidates tried
   size_t rsmem64 = 0, rsmem32 = 0;
   // coarse
@@ -160,6 +165,9 @@ template <> float *fdm_ctx::X<float>() const { return X32; }
 template <> const double *fdm_ctx::L<double>() const { return L64; }
 template <> const float *fdm_ctx::L<float>() const { return L32; }
 template <> size_t fdm_ctx::smem<double>() const { return smem64; }
+template <typename T> ClusterArgs<T> cluster_args(const fdm_ctx *c);
+template <> ClusterArgs<float> cluster_args<float>(const fdm_ctx *c) { return c->cla32; }
+template <> ClusterArgs<double> cluster_args<double>(const fdm_ctx *c) { return c->cla64; }
 template <> size_t fdm_ctx::smem<float>() const { return smem32; }
 
 struct fdm_batch {
@@ -251,10 +259,24 @@ void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st) {
                         c->opt.inject_stall, 0, 0};
     launch_patch_resident<T>(a, c->nsolve, c->fcap, sizeof(T) == 4 ? c->rsmem32 : c->rsmem64, c->res_threads, st);
   } else {
-    PatchSolveArgs<T> a{c->g, c->d_cls, c->d_patches, c->d_order, c->E<T>(), c->mu, c->tab<T>(), c->L<T>(), c->X<T>(),
-                        patch_tmp_elems(c->maxN1, c->maxN2), c->opt.patch_prefetch > 0 ? c->opt.patch_prefetch : 3,
-                        0, c->status, 0, c->opt.patch_l2_hints != 2 ? 1 : 0, c->rows8};
-    launch_patch_solve<T>(a, c->nsolve, c->smem<T>(), c->patch_threads, st);
+    const bool clus = sizeof(T) == 4 ? c->cl32 : c->cl64;
+    const int skip = clus ? c->n_heavy : 0;
+    if (clus) {
+      ClusterArgs<T> ca = cluster_args<T>(c);
+      ca.cls = c->d_cls;
+      ca.patches = c->d_patches;
+      ca.order = c->d_order;
+      ca.E = c->E<T>();
+      ca.L = c->L<T>();
+      ca.X = c->X<T>();
+      ca.status = c->status;
+      launch_patch_cluster<T>(ca, c->cl_threads, st);
+    }
+    PatchSolveArgs<T> a{c->g, c->d_cls, c->d_patches, c->d_order + skip, c->E<T>(), c->mu, c->tab<T>(), c->L<T>(),
+                        c->X<T>(), patch_tmp_elems(c->maxN1, c->maxN2),
+                        c->opt.patch_prefetch > 0 ? c->opt.patch_prefetch : 3, 0, c->status, 0,
+                        c->opt.patch_l2_hints != 2 ? 1 : 0, c->rows8};
+    launch_patch_solve<T>(a, c->nsolve - skip, c->smem<T>(), c->patch_threads, st);
   }
   c->tmark(FDM_T_PATCH, false, st);
   c->tmark(FDM_T_INTERP, true, st);
@@ -430,6 +452,58 @@ void setup_tables(fdm_ctx *c) {
   c->tab32 = c->upload(tf);
 }
 
+// Cluster patch solve: the patches of the classes with n1 > 0 and n2 > 0 come
+// first in the order (heaviest first); the smallest cluster (2, 4, 8 or 16 CTAs)
+// whose share of L21 rows fits in shared memory is used, if the GPU can host it.
+template <typename T>
+bool cluster_config(fdm_ctx *c, ClusterArgs<T> &a) {
+  int n2max = 0, ldmax = 0;
+  for (const PatchClass &C : c->classes)
+    if (C.n1 > 0 && C.n2 > 0) {
+      n2max = std::max(n2max, C.n2);
+      ldmax = std::max(ldmax, C.ld21);
+    }
+  if (c->n_heavy == 0 || n2max == 0) return false;
+  const int thr = c->cl_threads;
+  a.g = c->g;
+  a.npatch = c->n_heavy;
+  a.ld_cap = ldmax;
+  a.n2_cap = (n2max + 3) & ~3;
+  a.maxG = c->maxG;
+  a.tmpcap = std::max({4 * thr, a.n2_cap, a.ld_cap});
+  if (a.n2_cap / 4 > thr || a.ld_cap / 4 > thr) return false;  // one thread per 4-column group
+  a.timeout_ns = (uint64_t)(std::max(c->opt.wait_timeout_s, 0.0) * 1e9);
+  a.inject_stall = c->opt.inject_stall;
+  for (int cs : {2, 4, 8, 16}) {
+    a.cs = cs;
+    a.rows_cap = (n2max + cs - 1) / cs;
+    if (patch_cluster_smem<T>(a) > 224 * 1024) continue;
+    return patch_cluster_fits<T>(a, thr) > 0;
+  }
+  return false;
+}
+
+void setup_cluster(fdm_ctx *c) {
+  // the prefix of the order with a dense top level; the rest must have none
+  int nh = 0;
+  std::vector<int> order(c->nsolve);
+  FDM_CUDA(cudaMemcpy(order.data(), c->d_order, sizeof(int) * c->nsolve, cudaMemcpyDeviceToHost));
+  while (nh < c->nsolve) {
+    const PatchClass &C = c->classes[c->h_patches[order[nh]].cls];
+    if (!(C.n1 > 0 && C.n2 > 0)) break;
+    ++nh;
+  }
+  for (int i = nh; i < c->nsolve; ++i)
+    if (c->classes[c->h_patches[order[i]].cls].n2 > 0) nh = 0;
+  c->n_heavy = nh;
+  int n2max = 0;
+  for (const PatchClass &C : c->classes) n2max = std::max(n2max, C.n2);
+  c->cl_threads = n2max > 400 ? 512 : 256;
+  const bool want = c->opt.patch_kernel == 4;
+  c->cl32 = want && cluster_config<float>(c, c->cla32);
+  c->cl64 = want && cluster_config<double>(c, c->cla64);
+}
+
 void setup_patches(fdm_ctx *c) {
   const int p = c->p;
   c->classes = build_classes(p);
@@ -556,6 +630,7 @@ void setup_patches(fdm_ctx *c) {
                : c->opt.patch_rows_per_warp == 4 ? 0
                                                    : (c->patch_threads == 256 && ld21 >= 200 ? 1 : 0);
   }
+  setup_cluster(c);
   c->smem64 = patch_smem_for_occupancy<double>(c->smem64, c->opt.patch_ctas_per_sm);
   c->smem32 = patch_smem_for_occupancy<float>(c->smem32, c->opt.patch_ctas_per_sm);
   if (c->smem64 > 200 * 1024) fail(FDM_EINVAL, "patch interface too large for shared memory");

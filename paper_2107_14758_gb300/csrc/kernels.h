@@ -77,6 +77,35 @@ size_t stream_smem_bytes(const StreamArgs<T> &a);
 template <typename T>
 int launch_patch_stream(const StreamArgs<T> &a, int threads, cudaStream_t st);
 
+// patch solve on a thread-block cluster (classes with a dense top level), k_cluster.cu
+template <typename T>
+struct ClusterArgs {
+  Grid g;
+  const ClassDev *cls;
+  const PatchDev *patches;
+  const int *order;  // the patches solved by clusters
+  int npatch;
+  const T *E;
+  const T *L;
+  T *X;
+  int cs;        // CTAs per cluster (one patch per cluster)
+  int rows_cap;  // L21 rows held per CTA (>= ceil(n2 / cs))
+  int ld_cap;    // >= ld21
+  int n2_cap;    // >= n2, a multiple of 4
+  int maxG;
+  int tmpcap;    // >= max(n2_cap, ld_cap), >= 4 * threads
+  uint64_t timeout_ns;
+  int *status;
+  int inject_stall;
+};
+template <typename T>
+size_t patch_cluster_smem(const ClusterArgs<T> &a);
+// clusters that can be resident at once (0: the configuration cannot run)
+template <typename T>
+int patch_cluster_fits(const ClusterArgs<T> &a, int threads);
+template <typename T>
+void launch_patch_cluster(const ClusterArgs<T> &a, int threads, cudaStream_t st);
+
 // basis change and relaxation
 template <typename T, typename Tin>
 void launch_restrict_fdm(const Grid &g, const Tin *r, const T *tab, const double *mu, T *E, cudaStream_t st);

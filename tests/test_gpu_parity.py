@@ -335,7 +335,7 @@ def test_full_size_sampled(name):
 
 
 # ---------------------------------------------------------------- kernels and failure detection
-@pytest.mark.parametrize("kernel", [1, 2, 3])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4])
 def test_both_patch_kernels_agree(kernel):
     """The classic (one CTA per patch), streamed (bulk copies into a
     shared-memory ring) and resident (whole factor in shared memory) patch
@@ -381,7 +381,7 @@ def test_resident_matches_classic_bitwise(p, precision):
     assert np.array_equal(out[0], out[1])
 
 
-@pytest.mark.parametrize("kernel", [2, 3])
+@pytest.mark.parametrize("kernel", [2, 3, 4])
 def test_bounded_wait_reports_timeout_kernels(kernel):
     """As below, for the streamed and the resident patch solves."""
     xv, yv, zv = inputs.graded_vertices(2, 3)
@@ -411,6 +411,21 @@ def test_autotuned_context_matches(p, precision):
     tol = 1e-12 if precision == FP64 else 1e-5
     assert relerr(N(b.asm_apply(r)), N(a.asm_apply(r))) <= tol
     assert b.status() == 0
+
+
+@pytest.mark.parametrize("p,precision", [(3, FP64), (5, FP64), (4, FP32), (7, FP32), (8, FP32)])
+def test_cluster_kernel_matches_classic(p, precision):
+    """The cluster patch solve (L21 held in shared memory across a cluster)
+    gives the classic kernel's relaxation to rounding."""
+    xv, yv, zv = inputs.graded_vertices(3, 9)
+    r = T(np.random.default_rng(51).standard_normal(((len(xv) - 1) * p + 1) ** 3))
+    out = []
+    for kernel in (1, 4):
+        ctx = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7, patch_kernel=kernel)
+        out.append(N(ctx.asm_apply(r)))
+        assert ctx.status() == 0
+        ctx.close()
+    assert relerr(out[1], out[0]) <= (1e-12 if precision == FP64 else 1e-5)
 
 
 def test_bounded_wait_reports_timeout():
