@@ -244,7 +244,7 @@ StreamArgs<T> stream_args(fdm_ctx *c) {
 }
 
 template <typename T, typename Tin, typename Tout>
-void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st) {
+void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st, const T *addv = nullptr) {
   c->tmark(FDM_T_RESTRICT, true, st);
   launch_restrict_fdm<T, Tin>(c->g, r, c->tab<T>(), c->mu, c->E<T>(), st);
   c->tmark(FDM_T_RESTRICT, false, st);
@@ -280,7 +280,7 @@ void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st) {
   }
   c->tmark(FDM_T_PATCH, false, st);
   c->tmark(FDM_T_INTERP, true, st);
-  InterpArgs<T> ia{c->g, c->d_patches, c->d_cls, c->X<T>(), c->E<T>(), c->mu, c->tab<T>(), c->cmap};
+  InterpArgs<T> ia{c->g, c->d_patches, c->d_cls, c->X<T>(), c->E<T>(), c->mu, c->tab<T>(), c->cmap, addv};
   launch_interp_fdm<T, Tout>(ia, omega, z, st);
   c->tmark(FDM_T_INTERP, false, st);
   c->launches += 3;
@@ -317,19 +317,43 @@ void apply_op(fdm_ctx *c, const T *u, T *y, cudaStream_t st) {
   c->launches += 2;
 }
 
-// hybrid multiplicative V(1,1) (Section 2.5) in precision T
+__global__ void k_rsub(int64_t n, const double *__restrict__ r, float *__restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = float(r[i]) - y[i];
+}
+__global__ void k_rsub(int64_t n, const double *__restrict__ r, double *__restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = r[i] - y[i];
+}
+
+// r1 = r - A u in precision T (r: the FP64 preconditioner input, Dirichlet
+// entries 0); on box cells fused into the node gather of the stiffness apply
 template <typename T>
-void run_vcycle(fdm_ctx *c, const T *r, T *z, T *x1, T *t, T *r1, cudaStream_t st) {
-  const int64_t n = c->g.ndof;
-  run_asm<T, T, T>(c, r, x1, c->omega, st);  // pre-relaxation
-  apply_op<T>(c, x1, t, st);
-  launch_sub<T>(n, r, t, r1, st);
+void apply_residual(fdm_ctx *c, const T *u, const double *r, T *r1, cudaStream_t st) {
+  const int tag = sizeof(T) == 4 ? FDM_T_OP32 : FDM_T_OP64;
+  c->tmark(tag, true, st);
+  if (!launch_box_op_fast<T, T, T>(c->op_args(sizeof(T) == 4), u, r1, c->E<T>(), st, r)) {
+    launch_operator<T, T, T>(c->op_args(sizeof(T) == 4), false, u, r1, c->E<T>(), st);
+    k_rsub<<<vec_blocks(c->g.ndof), 256, 0, st>>>(c->g.ndof, r, r1);
+    c->launches += 1;
+  }
+  c->tmark(tag, false, st);
+  c->launches += 2;
+}
+
+// hybrid multiplicative V(1,1) (Section 2.5) computed in precision T from the
+// FP64 input r to the FP64 output z:
+//   x1 = omega ASM(r); r1 = r - A x1; x1 += P A_c^{-1} P^T r1; r1 = r - A x1;
+//   z = x1 + omega ASM(r1)
+// (the conversions, residual subtractions and the final sum are fused into the
+// restriction, the node gather and the interpolation)
+template <typename T>
+void run_vcycle(fdm_ctx *c, const double *r, double *z, T *x1, T *r1, cudaStream_t st) {
+  run_asm<T, double, T>(c, r, x1, c->omega, st);  // pre-relaxation
+  apply_residual<T>(c, x1, r, r1, st);
   coarse_correct<T>(c, r1, x1, st);  // multiplicative coarse correction
-  apply_op<T>(c, x1, t, st);
-  launch_sub<T>(n, r, t, r1, st);
-  run_asm<T, T, T>(c, r1, t, c->omega, st);  // post-relaxation
-  launch_axpby<T>(n, T(1), x1, T(1), t, z, st);
-  c->launches += 3;
+  apply_residual<T>(c, x1, r, r1, st);
+  run_asm<T, T, double>(c, r1, z, c->omega, st, x1);  // post-relaxation, z = x1 + omega ASM(r1)
 }
 
 void pc_apply_impl(fdm_ctx *c, const double *r, double *z, cudaStream_t st) {
@@ -342,15 +366,12 @@ void pc_apply_impl(fdm_ctx *c, const double *r, double *z, cudaStream_t st) {
   }
   if (c->opt.precision == FDM_PREC_FP64) {
     if (c->opt.pc == FDM_PC_ASM) run_asm<double, double, double>(c, r, z, c->omega, st);
-    else run_vcycle<double>(c, r, z, c->v1, c->v2, c->v3, st);
+    else run_vcycle<double>(c, r, z, c->v1, c->v3, st);
   } else {
     if (c->opt.pc == FDM_PC_ASM) {
       run_asm<float, double, double>(c, r, z, c->omega, st);
     } else {
-      launch_convert<double, float>(n, r, c->f_in, st);
-      run_vcycle<float>(c, c->f_in, c->f_out, c->f1, c->f2, c->f3, st);
-      launch_convert<float, double>(n, c->f_out, z, st);
-      c->launches += 2;
+      run_vcycle<float>(c, r, z, c->f1, c->f3, st);
     }
   }
 }

@@ -554,6 +554,7 @@ void launch_restrict_fdm(const Grid &g, const Tin *r, const T *tab, const double
 template <typename T, typename Tout>
 void launch_interp_fdm(const InterpArgs<T> &a, double omega, Tout *z, cudaStream_t st) {
   if (launch_interp_fast<T, Tout>(a, omega, z, st)) return;
+  if (a.addv) fail(FDM_EINVAL, "interpolation with an added vector needs the specialised kernel");
   size_t sm = sizeof(T) * (3 * a.g.n * a.g.n + 2 * a.g.n * a.g.n * a.g.n);
   static bool attr = false;
   if (!attr) {

@@ -231,7 +231,8 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_box_op(Grid g, c
 // direct stiffness summation over the cells containing each node (fixed
 // order); grid = (x blocks, y, z): no index divisions beyond constants
 template <typename T, typename Tout, int N>
-__global__ void __launch_bounds__(128) k_gather_t(Grid g, const T *__restrict__ E, Tout *__restrict__ y) {
+__global__ void __launch_bounds__(128) k_gather_t(Grid g, const T *__restrict__ E, const double *__restrict__ rsub,
+                                                  Tout *__restrict__ y) {
   constexpr int P = N - 1, N3 = N * N * N;
   const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y, gz = blockIdx.z;
   if (gx >= g.N[0]) return;
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(128) k_gather_t(Grid g, const T *__restrict__ 
         const int cell = cA[0][a0] + g.nx * (cA[1][a1] + g.ny * cA[2][a2]);
         s += E[(int64_t)cell * N3 + lA[0][a0] + N * (lA[1][a1] + N * lA[2][a2])];
       }
-  y[id] = Tout(s);
+  y[id] = rsub ? Tout(T(rsub[id]) - s) : Tout(s);  // rsub: the residual r - A u
 }
 
 // A_mm of an interior node (FDM basis: diagonal) and the coupling of face node
@@ -446,7 +447,9 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_interp_t(InterpA
     if ((i == 0 && ce[0] > 0) || (j == 0 && ce[1] > 0) || (k == 0 && ce[2] > 0)) continue;  // not owner
     const int gx = ce[0] * P + i, gy = ce[1] * P + j, gz = ce[2] * P + k;
     const bool dir = gx == 0 || gy == 0 || gz == 0 || gx == g.N[0] - 1 || gy == g.N[1] - 1 || gz == g.N[2] - 1;
-    z[gidx(g, gx, gy, gz)] = dir ? Tout(0) : Tout(omega * V[pid<N>(i, j, k)]);
+    const int64_t id = gidx(g, gx, gy, gz);
+    // z = omega * relaxation, plus a.addv where given (the V-cycle's pre-smoothed x1)
+    z[id] = dir ? Tout(0) : (a.addv ? Tout(a.addv[id] + T(omega) * V[pid<N>(i, j, k)]) : Tout(omega * V[pid<N>(i, j, k)]));
   }
 }
 
@@ -481,7 +484,7 @@ void set_smem(K kernel, size_t bytes) {
 }  // namespace
 
 template <typename T, typename Tin, typename Tout>
-bool launch_box_op_fast(const OpArgs &a, const Tin *u, Tout *y, T *E, cudaStream_t st) {
+bool launch_box_op_fast(const OpArgs &a, const Tin *u, Tout *y, T *E, cudaStream_t st, const double *rsub) {
   if constexpr (!std::is_same<T, Tin>::value) {
     return false;
   } else {
@@ -493,14 +496,14 @@ bool launch_box_op_fast(const OpArgs &a, const Tin *u, Tout *y, T *E, cudaStream
       const size_t sm = sizeof(T) * (2 * EO<T, N>::S + (size_t)CPB * 4 * psize<N>());
       set_smem(k_box_op<T, Tin, N>, sm);
       k_box_op<T, Tin, N><<<(a.g.ncell + CPB - 1) / CPB, CPB * N * N, sm, st>>>(a.g, a.mu_box, tab, u, E);
-      k_gather_t<T, Tout, N><<<dim3((a.g.N[0] + 127) / 128, a.g.N[1], a.g.N[2]), 128, 0, st>>>(a.g, E, y);
+      k_gather_t<T, Tout, N><<<dim3((a.g.N[0] + 127) / 128, a.g.N[1], a.g.N[2]), 128, 0, st>>>(a.g, E, rsub, y);
     });
   }
 }
 
 template <typename T, typename Tin>
 bool launch_restrict_fast(const Grid &g, const Tin *r, const T *tab, const double *mu, T *E, cudaStream_t st) {
-  if constexpr (!std::is_same<T, Tin>::value) {
+  if constexpr (!std::is_same<T, Tin>::value && !std::is_same<Tin, double>::value) {
     return false;
   } else {
     return dispatch_n(g.n, [&](auto nc) {
@@ -515,7 +518,7 @@ bool launch_restrict_fast(const Grid &g, const Tin *r, const T *tab, const doubl
 
 template <typename T, typename Tout>
 bool launch_interp_fast(const InterpArgs<T> &a, double omega, Tout *z, cudaStream_t st) {
-  if constexpr (!std::is_same<T, Tout>::value) {
+  if constexpr (!std::is_same<T, Tout>::value && !std::is_same<Tout, double>::value) {
     return false;
   } else {
     return dispatch_n(a.g.n, [&](auto nc) {
@@ -529,10 +532,11 @@ bool launch_interp_fast(const InterpArgs<T> &a, double omega, Tout *z, cudaStrea
 }
 
 template bool launch_box_op_fast<double, double, double>(const OpArgs &, const double *, double *, double *,
-                                                         cudaStream_t);
-template bool launch_box_op_fast<float, float, float>(const OpArgs &, const float *, float *, float *, cudaStream_t);
+                                                         cudaStream_t, const double *);
+template bool launch_box_op_fast<float, float, float>(const OpArgs &, const float *, float *, float *, cudaStream_t,
+                                                      const double *);
 template bool launch_box_op_fast<double, double, float>(const OpArgs &, const double *, float *, double *,
-                                                        cudaStream_t);
+                                                        cudaStream_t, const double *);
 template bool launch_restrict_fast<float, float>(const Grid &, const float *, const float *, const double *, float *,
                                                  cudaStream_t);
 template bool launch_restrict_fast<double, double>(const Grid &, const double *, const double *, const double *,

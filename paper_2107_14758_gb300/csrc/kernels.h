@@ -52,6 +52,7 @@ struct InterpArgs {
   // [8 classes][8 corners][n^3]: star-interface index of each cell node in the
   // star of the cell's corner (bit 0: +x, bit 1: +y, bit 2: +z), -1 if none
   const int *cmap;
+  const T *addv;  // optional: z = addv + omega * relaxation (grid vector)
 };
 
 // streamed patch solve: per-class chunk schedules over the factor values
@@ -132,7 +133,7 @@ template <typename T, typename Tin, typename Tout>
 void launch_operator(const OpArgs &a, bool mass, const Tin *u, Tout *y, T *E, cudaStream_t st);
 // cell kernels specialised on n (k_cell.cu); false when no specialisation applies
 template <typename T, typename Tin, typename Tout>
-bool launch_box_op_fast(const OpArgs &a, const Tin *u, Tout *y, T *E, cudaStream_t st);
+bool launch_box_op_fast(const OpArgs &a, const Tin *u, Tout *y, T *E, cudaStream_t st, const double *rsub = nullptr);
 template <typename T, typename Tin>
 bool launch_restrict_fast(const Grid &g, const Tin *r, const T *tab, const double *mu, T *E, cudaStream_t st);
 template <typename T, typename Tout>
