@@ -453,6 +453,99 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_interp_t(InterpA
   }
 }
 
+// ------------------------------------------------------------------ coarse space
+// trilinear hat functions of the Q1 coarse space at the GLL nodes: h0 = (1 - xi)/2, h1 = (1 + xi)/2
+// Restriction, per cell: the 8 corner sums of h_a(x_i) h_b(y_j) h_c(z_k) (W r)_ijk,
+// W = 1 / multiplicity; thread l sums one y-line of its cell.
+template <typename T, typename Tin, int N>
+__global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_coarse_restrict_t(Grid g, const Tin *__restrict__ r,
+                                                                                  const T *__restrict__ tab,
+                                                                                  T *__restrict__ cellbuf) {
+  constexpr int P = N - 1, L = N * N, CPB = cells_per_cta<N>();
+  const int c = threadIdx.x / L, l = threadIdx.x % L;
+  const int cell = blockIdx.x * CPB + c;
+  const bool valid = cell < g.ncell;
+  const T *xi = tab + tab_off(TAB_XI, N);
+  T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (valid) {  // thread l sums the y-line (i, k): consecutive threads read consecutive x
+    const int cx = cell % g.nx, cy = (cell / g.nx) % g.ny, cz = cell / (g.nx * g.ny);
+    const int i = l % N, k = l / N;
+    const int gx = cx * P + i, gz = cz * P + k;
+    const bool dxz = gx == 0 || gz == 0 || gx == g.N[0] - 1 || gz == g.N[2] - 1;
+    if (!dxz) {
+      const int mxz = ((i == 0 && cx > 0) || (i == P && cx < g.nx - 1) ? 2 : 1) *
+                      ((k == 0 && cz > 0) || (k == P && cz < g.nz - 1) ? 2 : 1);
+      T s0 = 0, s1 = 0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        const int gy = cy * P + j;
+        if (gy == 0 || gy == g.N[1] - 1) continue;
+        const int m = mxz * ((j == 0 && cy > 0) || (j == P && cy < g.ny - 1) ? 2 : 1);
+        const T v = T(r[gidx(g, gx, gy, gz)]) / T(m);
+        s0 += T(0.5) * (T(1) - xi[j]) * v;
+        s1 += T(0.5) * (T(1) + xi[j]) * v;
+      }
+      const T hx[2] = {T(0.5) * (T(1) - xi[i]), T(0.5) * (T(1) + xi[i])};
+      const T hz[2] = {T(0.5) * (T(1) - xi[k]), T(0.5) * (T(1) + xi[k])};
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = hx[q & 1] * (((q >> 1) & 1) ? s1 : s0) * hz[q >> 2];
+    }
+  }
+  // sum over the cell's lines in line order (deterministic)
+  __shared__ T red[CPB * L][8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) red[threadIdx.x][q] = acc[q];
+  __syncthreads();
+  if (valid)
+    for (int q = l; q < 8; q += L) {  // L = n^2 >= 4
+      T v = 0;
+      for (int t = 0; t < L; ++t) v += red[c * L + t][q];
+      cellbuf[(int64_t)cell * 8 + q] = v;
+    }
+}
+
+// Prolongation z (+)= P x_c: thread l evaluates one y-line of its cell from the
+// 8 corner values, written by the owning cell.
+template <typename T, typename Tout, int N>
+__global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_coarse_prolong_t(Grid g, const T *__restrict__ xc,
+                                                                                 const T *__restrict__ tab,
+                                                                                 const int *__restrict__ cfree,
+                                                                                 Tout *__restrict__ z, int accumulate) {
+  constexpr int P = N - 1, L = N * N, CPB = cells_per_cta<N>();
+  const int c = threadIdx.x / L, l = threadIdx.x % L;
+  const int cell = blockIdx.x * CPB + c;
+  if (cell >= g.ncell) return;
+  const int ce[3] = {cell % g.nx, (cell / g.nx) % g.ny, cell / (g.nx * g.ny)};
+  const T *xi = tab + tab_off(TAB_XI, N);
+  T cv[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int v = (ce[0] + (q & 1)) + (g.nx + 1) * ((ce[1] + ((q >> 1) & 1)) + (g.ny + 1) * (ce[2] + (q >> 2)));
+    const int f = cfree[v];
+    cv[q] = f >= 0 ? xc[f] : T(0);
+  }
+  const int i = l % N, k = l / N;  // the y-line (i, k): consecutive threads write consecutive x
+  if ((i == 0 && ce[0] > 0) || (k == 0 && ce[2] > 0)) return;  // not the owner of this line
+  const int gx = ce[0] * P + i, gz = ce[2] * P + k;
+  const bool dxz = gx == 0 || gz == 0 || gx == g.N[0] - 1 || gz == g.N[2] - 1;
+  const T hx[2] = {T(0.5) * (T(1) - xi[i]), T(0.5) * (T(1) + xi[i])};
+  const T hz[2] = {T(0.5) * (T(1) - xi[k]), T(0.5) * (T(1) + xi[k])};
+  T e[2];  // the corner values combined along x and z, for the y = 0 and y = 1 corners
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+    e[b] = cv[2 * b] * hx[0] * hz[0] + cv[2 * b + 1] * hx[1] * hz[0] + cv[2 * b + 4] * hx[0] * hz[1] +
+           cv[2 * b + 5] * hx[1] * hz[1];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    if (j == 0 && ce[1] > 0) continue;
+    const int gy = ce[1] * P + j;
+    const T s = (dxz || gy == 0 || gy == g.N[1] - 1) ? T(0)
+                                                      : T(0.5) * (T(1) - xi[j]) * e[0] + T(0.5) * (T(1) + xi[j]) * e[1];
+    const int64_t id = gidx(g, gx, gy, gz);
+    z[id] = accumulate ? Tout(z[id] + s) : Tout(s);
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 template <typename F>
 bool dispatch_n(int n, F &&f) {
@@ -531,6 +624,42 @@ bool launch_interp_fast(const InterpArgs<T> &a, double omega, Tout *z, cudaStrea
   }
 }
 
+template <typename T, typename Tin>
+bool launch_coarse_restrict_fast(const Grid &g, const Tin *r, const T *tab, T *cellbuf, cudaStream_t st) {
+  if constexpr (!std::is_same<T, Tin>::value) {
+    return false;
+  } else {
+    return dispatch_n(g.n, [&](auto nc) {
+      constexpr int N = decltype(nc)::value;
+      constexpr int CPB = cells_per_cta<N>();
+      k_coarse_restrict_t<T, Tin, N><<<(g.ncell + CPB - 1) / CPB, CPB * N * N, 0, st>>>(g, r, tab, cellbuf);
+    });
+  }
+}
+
+template <typename T, typename Tout>
+bool launch_coarse_prolong_fast(const Grid &g, const T *xc, const T *tab, const int *cfree, Tout *z, bool accumulate,
+                                cudaStream_t st) {
+  if constexpr (!std::is_same<T, Tout>::value) {
+    return false;
+  } else {
+    return dispatch_n(g.n, [&](auto nc) {
+      constexpr int N = decltype(nc)::value;
+      constexpr int CPB = cells_per_cta<N>();
+      k_coarse_prolong_t<T, Tout, N><<<(g.ncell + CPB - 1) / CPB, CPB * N * N, 0, st>>>(g, xc, tab, cfree, z,
+                                                                                        accumulate ? 1 : 0);
+    });
+  }
+}
+
+template bool launch_coarse_restrict_fast<float, float>(const Grid &, const float *, const float *, float *,
+                                                        cudaStream_t);
+template bool launch_coarse_restrict_fast<double, double>(const Grid &, const double *, const double *, double *,
+                                                          cudaStream_t);
+template bool launch_coarse_prolong_fast<float, float>(const Grid &, const float *, const float *, const int *,
+                                                       float *, bool, cudaStream_t);
+template bool launch_coarse_prolong_fast<double, double>(const Grid &, const double *, const double *, const int *,
+                                                         double *, bool, cudaStream_t);
 template bool launch_box_op_fast<double, double, double>(const OpArgs &, const double *, double *, double *,
                                                          cudaStream_t, const double *);
 template bool launch_box_op_fast<float, float, float>(const OpArgs &, const float *, float *, float *, cudaStream_t,

@@ -322,7 +322,8 @@ __global__ void k_coarse_restrict_vertices(Grid g, const int *__restrict__ cfree
 template <typename T, typename Tin>
 void launch_coarse_restrict(const Grid &g, const Tin *r, const T *tab, const int *cfree, T *rc, T *cellbuf,
                             cudaStream_t st) {
-  k_coarse_restrict_cells<T, Tin><<<g.ncell, 256, 0, st>>>(g, r, tab, cellbuf);
+  if (!launch_coarse_restrict_fast<T, Tin>(g, r, tab, cellbuf, st))
+    k_coarse_restrict_cells<T, Tin><<<g.ncell, 256, 0, st>>>(g, r, tab, cellbuf);
   int nv = (g.nx + 1) * (g.ny + 1) * (g.nz + 1);
   k_coarse_restrict_vertices<T><<<(nv + 255) / 256, 256, 0, st>>>(g, cfree, cellbuf, rc);
 }
@@ -341,12 +342,43 @@ __global__ void k_dense_symv(int m, const T *__restrict__ A, const T *__restrict
   }
 }
 
+// the same with 16-byte loads: a row starts at an arbitrary element offset r m,
+// so each warp reads the unaligned head and the tail element by element and the
+// body in 16-byte vectors (VW = 16 / sizeof(T) elements)
+template <typename T>
+__global__ void k_dense_symv_vec(int m, const T *__restrict__ A, const T *__restrict__ x, T *__restrict__ y) {
+  constexpr int VW = 16 / sizeof(T);
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < m; r += warps) {
+    const T *row = A + (int64_t)r * m;
+    const int head = (int)((VW - ((int64_t)r * m) % VW) % VW);
+    const int body = (m - head) / VW;
+    T s = 0;
+    if (lane < head && lane < m) s += row[lane] * x[lane];
+    for (int q = lane; q < body; q += 32) {
+      const int c = head + q * VW;
+      if constexpr (VW == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(row + c);
+        s += v.x * x[c] + v.y * x[c + 1] + v.z * x[c + 2] + v.w * x[c + 3];
+      } else {
+        const double2 v = *reinterpret_cast<const double2 *>(row + c);
+        s += v.x * x[c] + v.y * x[c + 1];
+      }
+    }
+    const int t0 = head + body * VW;
+    if (t0 + lane < m) s += row[t0 + lane] * x[t0 + lane];
+    s = warp_sum(s);
+    if (lane == 0) y[r] = s;
+  }
+}
+
 template <typename T>
 void launch_dense_symv(int m, const T *Ainv, const T *x, T *y, cudaStream_t st) {
   if (m <= 0) return;
   int blocks = (m * 32 + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_dense_symv<T><<<blocks, 256, 0, st>>>(m, Ainv, x, y);
+  k_dense_symv_vec<T><<<blocks, 256, 0, st>>>(m, Ainv, x, y);
 }
 
 // z (+)= P x_c: per cell, trilinear interpolation of the corner values at the
@@ -384,7 +416,8 @@ __global__ void k_coarse_prolong(Grid g, const T *__restrict__ xc, const T *__re
 template <typename T, typename Tout>
 void launch_coarse_prolong(const Grid &g, const T *xc, const T *tab, const int *cfree, Tout *z, bool accumulate,
                            cudaStream_t st) {
-  k_coarse_prolong<T, Tout><<<g.ncell, 128, 0, st>>>(g, xc, tab, cfree, z, accumulate ? 1 : 0);
+  if (!launch_coarse_prolong_fast<T, Tout>(g, xc, tab, cfree, z, accumulate, st))
+    k_coarse_prolong<T, Tout><<<g.ncell, 128, 0, st>>>(g, xc, tab, cfree, z, accumulate ? 1 : 0);
 }
 
 // ------------------------------------------------------------------ vectors

@@ -139,6 +139,12 @@ bool launch_restrict_fast(const Grid &g, const Tin *r, const T *tab, const doubl
 template <typename T, typename Tout>
 bool launch_interp_fast(const InterpArgs<T> &a, double omega, Tout *z, cudaStream_t st);
 
+template <typename T, typename Tin>
+bool launch_coarse_restrict_fast(const Grid &g, const Tin *r, const T *tab, T *cellbuf, cudaStream_t st);
+template <typename T, typename Tout>
+bool launch_coarse_prolong_fast(const Grid &g, const T *xc, const T *tab, const int *cfree, Tout *z, bool accumulate,
+                                cudaStream_t st);
+
 // per-cell Galerkin coarse matrices P_K^T A^K P_K (FP64), [ncell][8][8]
 void launch_coarse_cell_matrices(const OpArgs &a, double *Ac, cudaStream_t st);
 
