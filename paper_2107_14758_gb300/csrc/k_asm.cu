@@ -140,7 +140,7 @@ __device__ __forceinline__ uint64_t policy_drop() {
 __device__ __forceinline__ V4<float> load4h(const float *p, uint64_t pol) {
   if (!__isGlobal(p)) return load4(p);
   float4 v;
-  asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+  asm("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
                : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                : "l"(p), "l"(pol));
   return {v.x, v.y, v.z, v.w};
@@ -148,8 +148,8 @@ __device__ __forceinline__ V4<float> load4h(const float *p, uint64_t pol) {
 __device__ __forceinline__ V4<double> load4h(const double *p, uint64_t pol) {
   if (!__isGlobal(p)) return load4(p);
   double2 a, b;
-  asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(a.x), "=d"(a.y) : "l"(p), "l"(pol));
-  asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(b.x), "=d"(b.y) : "l"(p + 2), "l"(pol));
+  asm("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(a.x), "=d"(a.y) : "l"(p), "l"(pol));
+  asm("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(b.x), "=d"(b.y) : "l"(p + 2), "l"(pol));
   return {a.x, a.y, b.x, b.y};
 }
 
@@ -195,6 +195,33 @@ __device__ __forceinline__ void patch_gather(const PatchSolveArgs<T> &a, const P
 
 // forward and backward solves with the factor values Lv of this patch (global
 // or shared memory), then the interface solution in factor order
+
+// Sums over the 32 lanes of RB values per lane (RB = 4 or 8) with a butterfly
+// that halves the number of values per lane at each of the first log2(RB)
+// stages: 2 + 1 + 3 shuffles for RB = 4 (4 + 2 + 1 + 2 for RB = 8) instead of
+// 5 per value.  On return lane l holds the total of value index
+// rb_slot<RB>(l) in acc[0]; the lanes l with (l & (32 / RB - 1)) == 0 hold the
+// RB totals.
+template <int RB>
+__device__ __forceinline__ int rb_slot(int lane) {
+  return RB == 4 ? (lane >> 3) : (lane >> 2);
+}
+template <typename T, int RB>
+__device__ __forceinline__ void multi_warp_sum(T (&acc)[RB], int lane) {
+#pragma unroll
+  for (int half = RB / 2, o = 16; half >= 1; half >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;  // the upper lane keeps the upper half of the values
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      const T send = up ? acc[j] : acc[j + half];
+      const T keep = up ? acc[j + half] : acc[j];
+      acc[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+#pragma unroll
+  for (int o = 32 / RB / 2; o > 0; o >>= 1) acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+}
+
 // RB: rows per warp in the forward row-oriented products (their loads in flight together)
 template <typename T, int NT, int RB>
 __device__ __forceinline__ void patch_solve_body(const PatchSolveArgs<T> &a, const PatchDev &P, const ClassDev &C,
@@ -247,12 +274,20 @@ __device__ __forceinline__ void patch_solve_body(const PatchSolveArgs<T> &a, con
 #pragma unroll
           for (int u = 0; u < RB; ++u) acc[u] += v[u].x * yy[0] + v[u].y * yy[1] + v[u].z * yy[2] + v[u].w * yy[3];
         }
+        if (RB == 4) {  // butterfly (measured faster for four rows, slower for eight)
+          multi_warp_sum<T, RB>(acc, lane);
+          if ((lane & (32 / RB - 1)) == 0) {
+            const int u = rb_slot<RB>(lane);
+            if (r0 + u < n2) gv[base + r0 + u] -= acc[0];
+          }
+        } else {
 #pragma unroll
-        for (int u = 0; u < RB; ++u) acc[u] = warp_sum(acc[u]);
-        if (lane == 0)
+          for (int u = 0; u < RB; ++u) acc[u] = warp_sum(acc[u]);
+          if (lane == 0)
 #pragma unroll
-          for (int u = 0; u < RB; ++u)
-            if (r0 + u < n2) gv[base + r0 + u] -= acc[u];
+            for (int u = 0; u < RB; ++u)
+              if (r0 + u < n2) gv[base + r0 + u] -= acc[u];
+        }
       }
       __syncthreads();
     }
@@ -279,12 +314,20 @@ __device__ __forceinline__ void patch_solve_body(const PatchSolveArgs<T> &a, con
 #pragma unroll
         for (int u = 0; u < RB; ++u) acc[u] += v[u].x * gg[0] + v[u].y * gg[1] + v[u].z * gg[2] + v[u].w * gg[3];
       }
+      if (RB == 4) {
+        multi_warp_sum<T, RB>(acc, lane);
+        if ((lane & (32 / RB - 1)) == 0) {
+          const int u = rb_slot<RB>(lane);
+          if (r0 + u < n2) yv[base + r0 + u] = acc[0];
+        }
+      } else {
 #pragma unroll
-      for (int u = 0; u < RB; ++u) acc[u] = warp_sum(acc[u]);
-      if (lane == 0)
+        for (int u = 0; u < RB; ++u) acc[u] = warp_sum(acc[u]);
+        if (lane == 0)
 #pragma unroll
-        for (int u = 0; u < RB; ++u)
-          if (r0 + u < n2) yv[base + r0 + u] = acc[u];
+          for (int u = 0; u < RB; ++u)
+            if (r0 + u < n2) yv[base + r0 + u] = acc[u];
+      }
     }
     __syncthreads();
     // ---- backward solve L^T x = y
@@ -354,8 +397,10 @@ __device__ __forceinline__ void patch_solve_body(const PatchSolveArgs<T> &a, con
   __syncthreads();
   for (int j = tid; j < n0; j += NT) {  // x_0 = D_0^{-1} (y_0 - L_{>0,0}^T x_{>0})
     T s = yv[j];
-    for (int q = C.c0_ptr[j]; q < C.c0_ptr[j + 1]; ++q) {
-      int pos = C.c0_pos[q];
+    const int q1 = C.c0_ptr[j + 1];
+#pragma unroll 4
+    for (int q = C.c0_ptr[j]; q < q1; ++q) {
+      const int pos = C.c0_pos[q];
       s -= ell[pos] * xv[n0 + pos % C.ldr0];
     }
     xv[j] = s * dinv0[j];
