@@ -1,269 +1,10 @@
-// Cell-local kernels specialised on the number of GLL points n = p + 1 (a
-// template parameter), so that index arithmetic folds into constants and the
-// one-dimensional contractions unroll completely.
-//
-// Layout: one thread per line of a cell ("pencil").  The n x n x n values of a
-// cell sit in shared memory with padded pitches, node (i, j, k) at
-// i + (n+1) j + (n+1)^2 k, so that lines along x, y and z are read without
-// bank conflicts; a line's n values go to registers and each of its n outputs
-// is one dot product with a row of a 1D matrix (read as a shared-memory
-// broadcast).  Several cells share a CTA when n is small.
-//
-//   box stiffness (eq. (kron), Section 2.2): y_K = mu1 (B (x) B (x) A) u_K
-//     + mu2 (B (x) A (x) B) u_K + mu3 (A (x) B (x) B) u_K in 7 line passes;
-//     cell-local results, summed over cells by a node gather.
-//   restrict (Section 2.4): E_K = (T^T)^{(x)3} (W_K r_K), then the cell's share
-//     of the Schur condensation on its face nodes.
-//   interp (Sections 2.4-2.6): interface values summed over the 8 stars,
-//     interior values by the summed back-substitution, then T^{(x)3}, omega
-//     and an owner write.
-#include <type_traits>
-
-#include "device.cuh"
-#include "kernels.h"
+// Relaxation and coarse-space cell kernels specialised on n: restriction to the
+// FDM basis with condensation, interpolation back, Q1 restriction and
+// prolongation; helpers in k_cell.cuh.
+#include "k_cell.cuh"
 
 namespace fdm {
 namespace {
-
-template <int N>
-__device__ __forceinline__ int pid(int i, int j, int k) {
-  return i + (N + 1) * (j + (N + 1) * k);
-}
-template <int N>
-constexpr int psize() {
-  return (N + 1) * (N + 1) * N;
-}
-template <int N>
-constexpr int cells_per_cta() {
-  return N * N >= 128 ? 1 : 128 / (N * N);
-}
-
-__device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double mad(double a, double b, double c) { return ::fma(a, b, c); }
-
-// sum_m M[r][m] x[m] (TR: sum_m M[m][r] x[m]), M row-major N x N
-template <typename T, int N, bool TR>
-__device__ __forceinline__ T row_dot(const T *M, int r, const T (&x)[N]) {
-  T s = 0;
-#pragma unroll
-  for (int m = 0; m < N; ++m) s = mad(TR ? M[m * N + r] : M[r * N + m], x[m], s);
-  return s;
-}
-
-// one pass along `axis` for the line `l` of a cell: dst = M' src (M' = M or M^T)
-template <typename T, int N, bool TR>
-__device__ __forceinline__ void line_pass(const T *src, T *dst, const T *M, int axis, int l) {
-  const int a = l % N, b = l / N;
-  T x[N];
-#pragma unroll
-  for (int m = 0; m < N; ++m)
-    x[m] = src[axis == 0 ? pid<N>(m, a, b) : (axis == 1 ? pid<N>(a, m, b) : pid<N>(a, b, m))];
-#pragma unroll
-  for (int r = 0; r < N; ++r)
-    dst[axis == 0 ? pid<N>(r, a, b) : (axis == 1 ? pid<N>(a, r, b) : pid<N>(a, b, r))] = row_dot<T, N, TR>(M, r, x);
-}
-
-// ------------------------------------------------------------------ box stiffness
-// Even-odd form of a centrosymmetric 1D matrix (M[i][j] = M[n-1-i][n-1-j],
-// true of the GLL stiffness and mass matrices by the symmetry of the nodes):
-// with h = n/2, x_e = x_m + x_{n-1-m}, x_o = x_m - x_{n-1-m} (m < h),
-//   y_i       = sum_m Me[i][m] x_e + Mo[i][m] x_o (+ M[i][h] x_h for odd n),
-//   y_{n-1-i} = sum_m Me[i][m] x_e - Mo[i][m] x_o (+ M[i][h] x_h),
-//   y_h       = sum_m M[h][m] x_e + M[h][h] x_h     (odd n),
-// Me = (M[i][m] + M[i][n-1-m]) / 2, Mo = (M[i][m] - M[i][n-1-m]) / 2:
-// about n^2 / 2 multiply-adds per line instead of n^2.
-template <typename T, int N>
-struct EO {
-  static constexpr int H = N / 2, S = 2 * H * H + 2 * (H + 1);
-  // layout in shared memory: e[H][H], o[H][H], c[H+1] (M[i][h], i < H; M[h][h] at H), r[H+1] (M[h][m])
-  static __device__ __forceinline__ void build(const T *M, T *t, int tid, int nthreads) {
-    for (int q = tid; q < H * H; q += nthreads) {
-      const int i = q / H, m = q % H;
-      t[q] = T(0.5) * (M[i * N + m] + M[i * N + (N - 1 - m)]);
-      t[H * H + q] = T(0.5) * (M[i * N + m] - M[i * N + (N - 1 - m)]);
-    }
-    if (N % 2 == 1)
-      for (int q = tid; q <= H; q += nthreads) {
-        t[2 * H * H + q] = M[q * N + H];
-        t[2 * H * H + H + 1 + q] = M[H * N + q];
-      }
-  }
-};
-
-template <typename T, int N>
-struct Line {  // a line split into even and odd parts
-  static constexpr int H = N / 2;
-  T e[H > 0 ? H : 1], o[H > 0 ? H : 1], mid;
-  __device__ __forceinline__ void split(const T (&x)[N]) {
-#pragma unroll
-    for (int m = 0; m < H; ++m) {
-      e[m] = x[m] + x[N - 1 - m];
-      o[m] = x[m] - x[N - 1 - m];
-    }
-    mid = N % 2 == 1 ? x[H] : T(0);
-  }
-};
-
-// rows i and n-1-i of y = M x (i < h), and the middle row for odd n
-template <typename T, int N>
-__device__ __forceinline__ void eo_pair(const T *t, int i, const Line<T, N> &x, T &yi, T &yj) {
-  constexpr int H = N / 2;
-  T se = 0, so = 0;
-#pragma unroll
-  for (int m = 0; m < H; ++m) {
-    se = mad(t[i * H + m], x.e[m], se);
-    so = mad(t[H * H + i * H + m], x.o[m], so);
-  }
-  if (N % 2 == 1) se = mad(t[2 * H * H + i], x.mid, se);
-  yi = se + so;
-  yj = se - so;
-}
-template <typename T, int N>
-__device__ __forceinline__ T eo_mid(const T *t, const Line<T, N> &x) {
-  constexpr int H = N / 2;
-  T s = t[2 * H * H + H] * x.mid;
-#pragma unroll
-  for (int m = 0; m < H; ++m) s = mad(t[2 * H * H + H + 1 + m], x.e[m], s);
-  return s;
-}
-
-template <typename T, typename Tin, int N>
-__global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_box_op(Grid g, const double *__restrict__ mub,
-                                                                       const T *__restrict__ tab,
-                                                                       const Tin *__restrict__ u, T *__restrict__ E) {
-  extern __shared__ __align__(16) unsigned char smem_[];
-  constexpr int P = N - 1, L = N * N, CPB = cells_per_cta<N>(), PS = psize<N>(), N3 = N * N * N, H = N / 2;
-  constexpr int ES = EO<T, N>::S;
-  T *tA = reinterpret_cast<T *>(smem_), *tB = tA + ES;
-  const int c = threadIdx.x / L, l = threadIdx.x % L;
-  T *U = tB + ES + c * 4 * PS, *B1 = U + PS, *B2 = B1 + PS, *B3 = B2 + PS;
-  const int cell = blockIdx.x * CPB + c;
-  const bool valid = cell < g.ncell;
-  EO<T, N>::build(tab + tab_off(TAB_A, N), tA, threadIdx.x, blockDim.x);
-  EO<T, N>::build(tab + tab_off(TAB_B, N), tB, threadIdx.x, blockDim.x);
-  T mu0 = 0, mu1 = 0, mu2 = 0;
-  if (valid) {
-    const int cx = cell % g.nx, cy = (cell / g.nx) % g.ny, cz = cell / (g.nx * g.ny);
-    mu0 = T(mub[3 * cell]);
-    mu1 = T(mub[3 * cell + 1]);
-    mu2 = T(mub[3 * cell + 2]);
-    for (int idx = l; idx < N3; idx += L) {
-      const int i = idx % N, j = (idx / N) % N, k = idx / (N * N);
-      const int gx = cx * P + i, gy = cy * P + j, gz = cz * P + k;
-      const bool dir = gx == 0 || gy == 0 || gz == 0 || gx == g.N[0] - 1 || gy == g.N[1] - 1 || gz == g.N[2] - 1;
-      U[pid<N>(i, j, k)] = dir ? T(0) : T(u[gidx(g, gx, gy, gz)]);
-    }
-  }
-  __syncthreads();
-  const int a = l % N, b = l / N;
-  {  // x: B1 = Bx u, B2 = Ax u
-    T x[N];
-#pragma unroll
-    for (int m = 0; m < N; ++m) x[m] = U[pid<N>(m, a, b)];
-    Line<T, N> xs;
-    xs.split(x);
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-      T y0, y1;
-      eo_pair<T, N>(tB, i, xs, y0, y1);
-      B1[pid<N>(i, a, b)] = y0;
-      B1[pid<N>(N - 1 - i, a, b)] = y1;
-      eo_pair<T, N>(tA, i, xs, y0, y1);
-      B2[pid<N>(i, a, b)] = y0;
-      B2[pid<N>(N - 1 - i, a, b)] = y1;
-    }
-    if (N % 2 == 1) {
-      B1[pid<N>(H, a, b)] = eo_mid<T, N>(tB, xs);
-      B2[pid<N>(H, a, b)] = eo_mid<T, N>(tA, xs);
-    }
-  }
-  __syncthreads();
-  {  // y: U = By Bx u, B3 = mu2 Ay Bx u + mu1 By Ax u
-    T x1[N], x2[N];
-#pragma unroll
-    for (int m = 0; m < N; ++m) {
-      x1[m] = B1[pid<N>(a, m, b)];
-      x2[m] = B2[pid<N>(a, m, b)];
-    }
-    Line<T, N> s1, s2;
-    s1.split(x1);
-    s2.split(x2);
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-      T p0, p1, q0, q1, r0, r1;
-      eo_pair<T, N>(tB, i, s1, p0, p1);
-      eo_pair<T, N>(tA, i, s1, q0, q1);
-      eo_pair<T, N>(tB, i, s2, r0, r1);
-      U[pid<N>(a, i, b)] = p0;
-      U[pid<N>(a, N - 1 - i, b)] = p1;
-      B3[pid<N>(a, i, b)] = mu1 * q0 + mu0 * r0;
-      B3[pid<N>(a, N - 1 - i, b)] = mu1 * q1 + mu0 * r1;
-    }
-    if (N % 2 == 1) {
-      U[pid<N>(a, H, b)] = eo_mid<T, N>(tB, s1);
-      B3[pid<N>(a, H, b)] = mu1 * eo_mid<T, N>(tA, s1) + mu0 * eo_mid<T, N>(tB, s2);
-    }
-  }
-  __syncthreads();
-  if (valid) {  // z: y = Bz B3 + mu3 Az U, cell-local, natural layout
-    T x3[N], x0[N];
-#pragma unroll
-    for (int m = 0; m < N; ++m) {
-      x3[m] = B3[pid<N>(a, b, m)];
-      x0[m] = U[pid<N>(a, b, m)];
-    }
-    Line<T, N> s3, s0;
-    s3.split(x3);
-    s0.split(x0);
-    T *out = E + (int64_t)cell * N3;
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-      T p0, p1, q0, q1;
-      eo_pair<T, N>(tB, i, s3, p0, p1);
-      eo_pair<T, N>(tA, i, s0, q0, q1);
-      out[a + N * (b + N * i)] = p0 + mu2 * q0;
-      out[a + N * (b + N * (N - 1 - i))] = p1 + mu2 * q1;
-    }
-    if (N % 2 == 1) out[a + N * (b + N * H)] = eo_mid<T, N>(tB, s3) + mu2 * eo_mid<T, N>(tA, s0);
-  }
-}
-
-// direct stiffness summation over the cells containing each node (fixed
-// order); grid = (x blocks, y, z): no index divisions beyond constants
-template <typename T, typename Tout, int N>
-__global__ void __launch_bounds__(128) k_gather_t(Grid g, const T *__restrict__ E, const double *__restrict__ rsub,
-                                                  Tout *__restrict__ y) {
-  constexpr int P = N - 1, N3 = N * N * N;
-  const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y, gz = blockIdx.z;
-  if (gx >= g.N[0]) return;
-  const int64_t id = gx + (int64_t)g.N[0] * (gy + (int64_t)g.N[1] * gz);
-  if (gx == 0 || gy == 0 || gz == 0 || gx == g.N[0] - 1 || gy == g.N[1] - 1 || gz == g.N[2] - 1) {
-    y[id] = Tout(0);
-    return;
-  }
-  const int gc[3] = {gx, gy, gz};
-  int cA[3][2], lA[3][2], cnt[3];
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) {
-    const int q = gc[ax] / P, rm = gc[ax] - q * P;
-    if (rm == 0) {  // on a cell face along this axis (interior node: both neighbours exist)
-      cA[ax][0] = q - 1; lA[ax][0] = P;
-      cA[ax][1] = q;     lA[ax][1] = 0;
-      cnt[ax] = 2;
-    } else {
-      cA[ax][0] = q; lA[ax][0] = rm;
-      cnt[ax] = 1;
-    }
-  }
-  T s = 0;
-  for (int a2 = 0; a2 < cnt[2]; ++a2)
-    for (int a1 = 0; a1 < cnt[1]; ++a1)
-      for (int a0 = 0; a0 < cnt[0]; ++a0) {
-        const int cell = cA[0][a0] + g.nx * (cA[1][a1] + g.ny * cA[2][a2]);
-        s += E[(int64_t)cell * N3 + lA[0][a0] + N * (lA[1][a1] + N * lA[2][a2])];
-      }
-  y[id] = rsub ? Tout(T(rsub[id]) - s) : Tout(s);  // rsub: the residual r - A u
-}
 
 // A_mm of an interior node (FDM basis: diagonal) and the coupling of face node
 // (local lf along axis ax) to the interior node with the same tangential indices
@@ -546,53 +287,7 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_coarse_prolong_t
   }
 }
 
-// ------------------------------------------------------------------ launchers
-template <typename F>
-bool dispatch_n(int n, F &&f) {
-  switch (n) {
-    case 2: f(std::integral_constant<int, 2>{}); return true;
-    case 3: f(std::integral_constant<int, 3>{}); return true;
-    case 4: f(std::integral_constant<int, 4>{}); return true;
-    case 5: f(std::integral_constant<int, 5>{}); return true;
-    case 6: f(std::integral_constant<int, 6>{}); return true;
-    case 7: f(std::integral_constant<int, 7>{}); return true;
-    case 8: f(std::integral_constant<int, 8>{}); return true;
-    case 9: f(std::integral_constant<int, 9>{}); return true;
-    case 10: f(std::integral_constant<int, 10>{}); return true;
-    case 11: f(std::integral_constant<int, 11>{}); return true;
-    case 12: f(std::integral_constant<int, 12>{}); return true;
-    case 13: f(std::integral_constant<int, 13>{}); return true;
-    case 14: f(std::integral_constant<int, 14>{}); return true;
-    case 15: f(std::integral_constant<int, 15>{}); return true;
-    case 16: f(std::integral_constant<int, 16>{}); return true;
-    default: return false;
-  }
-}
-
-template <typename K>
-void set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) FDM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-}
-
 }  // namespace
-
-template <typename T, typename Tin, typename Tout>
-bool launch_box_op_fast(const OpArgs &a, const Tin *u, Tout *y, T *E, cudaStream_t st, const double *rsub) {
-  if constexpr (!std::is_same<T, Tin>::value) {
-    return false;
-  } else {
-    if (a.general) return false;
-    const T *tab = reinterpret_cast<const T *>(a.tab);
-    return dispatch_n(a.g.n, [&](auto nc) {
-      constexpr int N = decltype(nc)::value;
-      constexpr int CPB = cells_per_cta<N>();
-      const size_t sm = sizeof(T) * (2 * EO<T, N>::S + (size_t)CPB * 4 * psize<N>());
-      set_smem(k_box_op<T, Tin, N>, sm);
-      k_box_op<T, Tin, N><<<(a.g.ncell + CPB - 1) / CPB, CPB * N * N, sm, st>>>(a.g, a.mu_box, tab, u, E);
-      k_gather_t<T, Tout, N><<<dim3((a.g.N[0] + 127) / 128, a.g.N[1], a.g.N[2]), 128, 0, st>>>(a.g, E, rsub, y);
-    });
-  }
-}
 
 template <typename T, typename Tin>
 bool launch_restrict_fast(const Grid &g, const Tin *r, const T *tab, const double *mu, T *E, cudaStream_t st) {
@@ -660,12 +355,6 @@ template bool launch_coarse_prolong_fast<float, float>(const Grid &, const float
                                                        float *, bool, cudaStream_t);
 template bool launch_coarse_prolong_fast<double, double>(const Grid &, const double *, const double *, const int *,
                                                          double *, bool, cudaStream_t);
-template bool launch_box_op_fast<double, double, double>(const OpArgs &, const double *, double *, double *,
-                                                         cudaStream_t, const double *);
-template bool launch_box_op_fast<float, float, float>(const OpArgs &, const float *, float *, float *, cudaStream_t,
-                                                      const double *);
-template bool launch_box_op_fast<double, double, float>(const OpArgs &, const double *, float *, double *,
-                                                        cudaStream_t, const double *);
 template bool launch_restrict_fast<float, float>(const Grid &, const float *, const float *, const double *, float *,
                                                  cudaStream_t);
 template bool launch_restrict_fast<double, double>(const Grid &, const double *, const double *, const double *,
