@@ -75,6 +75,9 @@ def lib():
         L.or_coarse_apply.argtypes = [C.c_void_p, dp, dp]
         L.or_coarse_matrix.argtypes = [C.c_void_p, ip, dp]
         L.or_pc_apply.argtypes = [C.c_void_p, dp, dp]
+        L.or_setup_coarse_gmg.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double]
+        L.or_gmg_level.argtypes = [C.c_void_p, C.c_int, ip, dp]
+        L.or_gmg_vcycle.argtypes = [C.c_void_p, dp, dp]
         L.or_lanczos_omega.argtypes = [C.c_void_p, dp, C.c_int, dp, dp, dp]
         L.or_pcg.argtypes = [C.c_void_p, dp, dp, C.c_double, C.c_int, C.c_int, ip, dp]
         L.or_surr_bound.argtypes = [C.c_int, dp, dp, dp, dp]
@@ -340,6 +343,23 @@ class Problem:
         A = np.zeros((nc.value, nc.value))
         _check(lib().or_coarse_matrix(self.h, C.byref(nc), _p(A)))
         return A
+
+    def setup_coarse_gmg(self, levels, nu=2, omega=2.0 / 3.0):
+        """Geometric multigrid V-cycle for the Q1 problem; returns the levels built."""
+        return _check(lib().or_setup_coarse_gmg(self.h, levels, nu, omega))
+
+    def gmg_level(self, l):
+        nf = C.c_int()
+        _check(lib().or_gmg_level(self.h, l, C.byref(nf), None))
+        A = np.zeros((nf.value, nf.value))
+        _check(lib().or_gmg_level(self.h, l, C.byref(nf), _p(A)))
+        return A
+
+    def gmg_vcycle(self, b):
+        b = _f64(b)
+        x = np.zeros_like(b)
+        _check(lib().or_gmg_vcycle(self.h, _p(b), _p(x)))
+        return x
 
     def pc_apply(self, r):
         r = _f64(r); z = np.zeros(self.ndof)

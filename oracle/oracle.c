@@ -376,6 +376,21 @@ struct or_ctx {
   int nc;          /* number of free coarse dofs */
   int *cfree;      /* vertex -> free index or -1 */
   double *Lc;      /* dense Cholesky of A_c */
+  double *Ac;      /* A_c itself (before factorisation) */
+  /* geometric multigrid on the Q1 problem (0 levels: exact solve with Lc) */
+  int gmg_levels, gmg_nu;
+  double gmg_omega;
+  struct or_level *lev; /* gmg_levels + 1 levels, level 0 = the Q1 problem on the mesh */
+};
+
+/* one level of the Q1 hierarchy: vertex grid nv[3] (free = interior vertices),
+ * dense operator A (nf x nf), prolongation P from the next coarser level
+ * (nf x nf_coarse, dense), Cholesky factor on the coarsest level */
+struct or_level {
+  int n[3];        /* cells per axis */
+  double *x[3];    /* vertex coordinates per axis */
+  int nf;          /* free vertices */
+  double *A, *P, *L;
 };
 
 static void set_mu_box(or_ctx *c);
@@ -472,7 +487,14 @@ void or_free(or_ctx *c) {
   free(c->patches);
   free(c->xv); free(c->yv); free(c->zv);
   free(c->Gw); free(c->detw); free(c->mu_box); free(c->mu);
-  free(c->cfree); free(c->Lc);
+  free(c->cfree); free(c->Lc); free(c->Ac);
+  if (c->lev) {
+    for (int l = 0; l <= c->gmg_levels; ++l) {
+      for (int a = 0; a < 3; ++a) free(c->lev[l].x[a]);
+      free(c->lev[l].A); free(c->lev[l].P); free(c->lev[l].L);
+    }
+    free(c->lev);
+  }
   free(c);
 }
 
@@ -1041,7 +1063,159 @@ int or_setup_coarse(or_ctx *c) {
       }
   free(u);
   free(y);
+  free(c->Ac);
+  c->Ac = (double *)malloc(sizeof(double) * (size_t)nc * nc);
+  memcpy(c->Ac, c->Lc, sizeof(double) * (size_t)nc * nc);
   return or_cholesky(nc, c->Lc);
+}
+
+/* ---- geometric multigrid on the Q1 problem (the paper's solver for the
+ * p-coarse problem: damped point-Jacobi on every level, Cholesky on the
+ * coarsest).  Levels are nested: level l+1 keeps every other vertex of level l
+ * along each axis; P interpolates linearly along each axis in the level's own
+ * vertex coordinates (exact for Q1 on nested meshes), and A_{l+1} = P^T A_l P. */
+static int lev_index(const struct or_level *L, int vx, int vy, int vz) {
+  if (vx <= 0 || vy <= 0 || vz <= 0 || vx >= L->n[0] || vy >= L->n[1] || vz >= L->n[2]) return -1;
+  return (vx - 1) + (L->n[0] - 1) * ((vy - 1) + (L->n[1] - 1) * (vz - 1));
+}
+
+/* weight of coarse vertex I (coordinates xc) at fine vertex i (coordinates xf), one axis */
+static double interp1(const double *xf, int i, int I) {
+  if (i % 2 == 0) return i / 2 == I ? 1.0 : 0.0;
+  const int l = (i - 1) / 2, r = (i + 1) / 2;
+  const double t = (xf[i] - xf[i - 1]) / (xf[i + 1] - xf[i - 1]);
+  if (I == l) return 1.0 - t;
+  if (I == r) return t;
+  return 0.0;
+}
+
+int or_setup_coarse_gmg(or_ctx *c, int levels, int nu, double omega) {
+  if (!c->Ac) { set_err("gmg: set up the coarse space first"); return -1; }
+  if (c->lev) {
+    for (int l = 0; l <= c->gmg_levels; ++l) {
+      for (int a = 0; a < 3; ++a) free(c->lev[l].x[a]);
+      free(c->lev[l].A); free(c->lev[l].P); free(c->lev[l].L);
+    }
+    free(c->lev);
+    c->lev = NULL;
+  }
+  c->gmg_levels = 0;
+  if (levels <= 0) return 0;
+  c->lev = (struct or_level *)calloc(levels + 1, sizeof(struct or_level));
+  struct or_level *L0 = &c->lev[0];
+  L0->n[0] = c->nx; L0->n[1] = c->ny; L0->n[2] = c->nz;
+  const double *v0[3] = {c->xv, c->yv, c->zv};
+  for (int a = 0; a < 3; ++a) {
+    L0->x[a] = (double *)malloc(sizeof(double) * (L0->n[a] + 1));
+    memcpy(L0->x[a], v0[a], sizeof(double) * (L0->n[a] + 1));
+  }
+  L0->nf = c->nc;
+  L0->A = (double *)malloc(sizeof(double) * (size_t)c->nc * c->nc);
+  memcpy(L0->A, c->Ac, sizeof(double) * (size_t)c->nc * c->nc);
+  int l = 0;
+  for (; l < levels; ++l) {
+    struct or_level *F = &c->lev[l], *C = &c->lev[l + 1];
+    if (F->n[0] % 2 || F->n[1] % 2 || F->n[2] % 2 || F->n[0] < 4 || F->n[1] < 4 || F->n[2] < 4) break;
+    for (int a = 0; a < 3; ++a) {
+      C->n[a] = F->n[a] / 2;
+      C->x[a] = (double *)malloc(sizeof(double) * (C->n[a] + 1));
+      for (int i = 0; i <= C->n[a]; ++i) C->x[a][i] = F->x[a][2 * i];
+    }
+    C->nf = (C->n[0] - 1) * (C->n[1] - 1) * (C->n[2] - 1);
+    /* P (F->nf x C->nf): tensor product of the 1D linear interpolation weights */
+    F->P = (double *)calloc((size_t)F->nf * C->nf, sizeof(double));
+    for (int vz = 1; vz < F->n[2]; ++vz)
+      for (int vy = 1; vy < F->n[1]; ++vy)
+        for (int vx = 1; vx < F->n[0]; ++vx) {
+          const int i = lev_index(F, vx, vy, vz);
+          for (int Vz = 1; Vz < C->n[2]; ++Vz)
+            for (int Vy = 1; Vy < C->n[1]; ++Vy)
+              for (int Vx = 1; Vx < C->n[0]; ++Vx) {
+                const double w = interp1(F->x[0], vx, Vx) * interp1(F->x[1], vy, Vy) * interp1(F->x[2], vz, Vz);
+                if (w != 0.0) F->P[(size_t)i * C->nf + lev_index(C, Vx, Vy, Vz)] = w;
+              }
+        }
+    /* A_c = P^T A P */
+    double *AP = (double *)calloc((size_t)F->nf * C->nf, sizeof(double));
+    for (int i = 0; i < F->nf; ++i)
+      for (int k = 0; k < F->nf; ++k) {
+        const double a = F->A[(size_t)i * F->nf + k];
+        if (a == 0.0) continue;
+        for (int J = 0; J < C->nf; ++J) AP[(size_t)i * C->nf + J] += a * F->P[(size_t)k * C->nf + J];
+      }
+    C->A = (double *)calloc((size_t)C->nf * C->nf, sizeof(double));
+    for (int i = 0; i < F->nf; ++i)
+      for (int I = 0; I < C->nf; ++I) {
+        const double pi = F->P[(size_t)i * C->nf + I];
+        if (pi == 0.0) continue;
+        for (int J = 0; J < C->nf; ++J) C->A[(size_t)I * C->nf + J] += pi * AP[(size_t)i * C->nf + J];
+      }
+    free(AP);
+  }
+  c->gmg_levels = l;
+  c->gmg_nu = nu;
+  c->gmg_omega = omega;
+  struct or_level *B = &c->lev[l];
+  B->L = (double *)malloc(sizeof(double) * (size_t)B->nf * B->nf);
+  memcpy(B->L, B->A, sizeof(double) * (size_t)B->nf * B->nf);
+  return or_cholesky(B->nf, B->L) ? -1 : l;
+}
+
+/* x = V-cycle on level l applied to b (x starts at zero) */
+static void gmg_vcycle(const or_ctx *c, int l, const double *b, double *x) {
+  const struct or_level *F = &c->lev[l];
+  const int n = F->nf;
+  if (l == c->gmg_levels) {
+    memcpy(x, b, sizeof(double) * n);
+    chol_solve(n, F->L, x);
+    return;
+  }
+  const struct or_level *C = &c->lev[l + 1];
+  double *r = (double *)malloc(sizeof(double) * n), *bc = (double *)calloc(C->nf, sizeof(double));
+  double *xc = (double *)calloc(C->nf, sizeof(double));
+  memset(x, 0, sizeof(double) * n);
+  for (int sweep = 0; sweep < 2 * c->gmg_nu + 1; ++sweep) {
+    if (sweep == c->gmg_nu) { /* coarse-grid correction between the pre- and post-sweeps */
+      for (int i = 0; i < n; ++i) {
+        double s = b[i];
+        for (int k = 0; k < n; ++k) s -= F->A[(size_t)i * n + k] * x[k];
+        r[i] = s;
+      }
+      for (int I = 0; I < C->nf; ++I) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += F->P[(size_t)i * C->nf + I] * r[i];
+        bc[I] = s;
+      }
+      gmg_vcycle(c, l + 1, bc, xc);
+      for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int I = 0; I < C->nf; ++I) s += F->P[(size_t)i * C->nf + I] * xc[I];
+        x[i] += s;
+      }
+      continue;
+    }
+    /* damped point-Jacobi: x += omega D^{-1} (b - A x) */
+    for (int i = 0; i < n; ++i) {
+      double s = b[i];
+      for (int k = 0; k < n; ++k) s -= F->A[(size_t)i * n + k] * x[k];
+      r[i] = s;
+    }
+    for (int i = 0; i < n; ++i) x[i] += c->gmg_omega * r[i] / F->A[(size_t)i * n + i];
+  }
+  free(r); free(bc); free(xc);
+}
+
+int or_gmg_level(const or_ctx *c, int l, int *nf, double *A) {
+  if (!c->lev || l < 0 || l > c->gmg_levels) { set_err("gmg: no such level"); return -1; }
+  *nf = c->lev[l].nf;
+  if (A) memcpy(A, c->lev[l].A, sizeof(double) * (size_t)c->lev[l].nf * c->lev[l].nf);
+  return 0;
+}
+
+int or_gmg_vcycle(const or_ctx *c, const double *b, double *x) {
+  if (!c->lev) { set_err("gmg not set up"); return -1; }
+  gmg_vcycle(c, 0, b, x);
+  return 0;
 }
 
 int or_coarse_matrix(const or_ctx *c, int *nc, double *Ac) {
@@ -1078,7 +1252,16 @@ int or_coarse_apply(const or_ctx *c, const double *r, double *z) {
             }
         rc[f] = s;
       }
-  if (c->nc > 0) chol_solve(c->nc, c->Lc, rc);
+  if (c->nc > 0) {
+    if (c->gmg_levels > 0) { /* one geometric multigrid V-cycle on the Q1 problem */
+      double *xc = (double *)calloc(c->nc, sizeof(double));
+      gmg_vcycle(c, 0, rc, xc);
+      memcpy(rc, xc, sizeof(double) * c->nc);
+      free(xc);
+    } else {
+      chol_solve(c->nc, c->Lc, rc);
+    }
+  }
   /* z = P x_c */
   for (int gz = 0; gz < c->N[2]; ++gz)
     for (int gy = 0; gy < c->N[1]; ++gy)

@@ -121,6 +121,21 @@ int or_setup_coarse(or_ctx *c);
 int or_coarse_apply(const or_ctx *c, const double *r, double *z);
 int or_coarse_matrix(const or_ctx *c, int *nc, double *Ac);
 
+/* Geometric multigrid for the Q1 problem (the paper's solver for the
+ * p-coarse problem, Section 3 solver diagram): `levels` nested coarsenings
+ * (every other vertex per axis, while all cell counts are even and >= 4), P
+ * linear interpolation in the level's vertex coordinates, A_{l+1} = P^T A_l P,
+ * `nu` damped point-Jacobi sweeps (damping omega) before and after the
+ * coarse-grid correction, Cholesky on the coarsest level.  After this call the
+ * coarse correction of or_coarse_apply / or_pc_apply is one V-cycle instead of
+ * the exact solve.  Returns the number of levels built (0: exact solve kept),
+ * negative on error.  Requires or_setup_coarse. */
+int or_setup_coarse_gmg(or_ctx *c, int levels, int nu, double omega);
+/* level l's dense operator (nf x nf; A may be NULL to query nf) */
+int or_gmg_level(const or_ctx *c, int l, int *nf, double *A);
+/* x = one V-cycle on the Q1 problem applied to b (free coarse dofs) */
+int or_gmg_vcycle(const or_ctx *c, const double *b, double *x);
+
 /* Hybrid multiplicative V(1,1): z = P^{-1} r (Section 2.5). */
 int or_pc_apply(const or_ctx *c, const double *r, double *z);
 

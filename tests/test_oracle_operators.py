@@ -315,3 +315,67 @@ def test_iterations_flat_in_p(oracle_lib):
         assert conv
         its.append(it)
     assert max(its) - min(its) <= 3 and max(its) <= 16, its
+
+
+# ---------------------------------------------------------------- geometric multigrid on the Q1 problem
+def _coarsened(v):
+    return v[::2].copy()
+
+
+def test_gmg_galerkin_level_equals_rediscretised_q1(oracle_lib):
+    """Nested Q1 spaces: P^T A_0 P on the graded 8^3 mesh equals the Q1
+    stiffness of the mesh with every other vertex (pins the interpolation
+    weights in the graded coordinates and the triple product)."""
+    xv, yv, zv = inputs.graded_vertices(8, 17)
+    P = oracle_lib.Problem(3, xv, yv, zv)
+    P.setup_coarse()
+    assert P.setup_coarse_gmg(2) == 2
+    A1 = P.gmg_level(1)
+    Q = oracle_lib.Problem(1, _coarsened(xv), _coarsened(yv), _coarsened(zv))
+    Q.setup_coarse()
+    ref = Q.coarse_matrix()
+    assert A1.shape == ref.shape == (27, 27)
+    assert np.abs(A1 - ref).max() <= 1e-12 * np.abs(ref).max()
+    A2 = P.gmg_level(2)
+    assert A2.shape == (1, 1)
+
+
+def test_gmg_vcycle_converges_as_iteration(oracle_lib):
+    """One V-cycle (2 + 2 damped Jacobi sweeps, omega = 2/3) used as a
+    stationary iteration on the Q1 problem reduces the residual by a factor
+    well below one per cycle, on a graded mesh."""
+    xv, yv, zv = inputs.graded_vertices(12, 18)
+    P = oracle_lib.Problem(1, xv, yv, zv)
+    P.setup_coarse()
+    assert P.setup_coarse_gmg(5) == 2                 # 12 -> 6 -> 3 cells per axis
+    A = P.coarse_matrix()
+    b = np.random.default_rng(3).standard_normal(A.shape[0])
+    x = np.zeros_like(b)
+    r0 = np.linalg.norm(b)
+    rates = []
+    for _ in range(6):
+        r = b - A @ x
+        x = x + P.gmg_vcycle(r)
+        rn = np.linalg.norm(b - A @ x)
+        rates.append(rn / np.linalg.norm(r))
+    assert max(rates[1:]) < 0.35, rates
+    assert np.linalg.norm(b - A @ x) < 1e-3 * r0
+
+
+def test_pcg_with_gmg_coarse_solve(oracle_lib):
+    """The hybrid V(1,1) with one multigrid V-cycle on the Q1 problem as its
+    coarse correction: PCG converges in at most two more iterations than with
+    the exact coarse solve."""
+    xv, yv, zv = inputs.graded_vertices(8, 19)
+    P = oracle_lib.Problem(3, xv, yv, zv)
+    P.setup_patches()
+    P.setup_coarse()
+    P.lanczos_omega(inputs.lanczos_start(P.ndof))
+    free = bf.free_mask(3, 8, 8, 8)
+    b = np.where(free, P.mass_apply(inputs.normal_rhs(P.ndof, 5)), 0.0)
+    x0, it0, _, conv0 = P.pcg(b, 1e-8, 200)
+    assert P.setup_coarse_gmg(2) == 2
+    x1, it1, _, conv1 = P.pcg(b, 1e-8, 200)
+    assert conv0 and conv1
+    assert it0 <= it1 <= it0 + 2, (it0, it1)
+    assert np.abs(x1 - x0).max() <= 1e-6 * np.abs(x0).max()
