@@ -123,6 +123,16 @@ typedef struct {
   int patch_rows_per_warp; /* rows a warp keeps in flight in the forward products of the
                               one-CTA-per-patch solve: 4 or 8 (0 = 8 for 256 threads and L21
                               rows of 200 or more, else 4) */
+  int coarse_levels;  /* solve of the Q1 coarse problem (Section 3): 0 = exact (dense inverse
+                         from a banded Cholesky factor); k > 0 = one geometric multigrid V-cycle
+                         with at most k coarsenings (every other vertex per axis while all cell
+                         counts are even and >= 4; linear interpolation in the vertex coordinates;
+                         Galerkin operators P^T A P; gmg_nu damped point-Jacobi sweeps before and
+                         after each coarse-grid correction; the exact solve on the coarsest level);
+                         -1 (default) = exact up to 4096 Q1 unknowns, else multigrid on every level
+                         the mesh allows */
+  int gmg_nu;         /* Jacobi sweeps before and after the coarse-grid correction (<= 0: 2) */
+  double gmg_omega;   /* Jacobi damping (<= 0: 2/3) */
 } fdm_options;
 
 /* Fills the defaults listed above. */
@@ -285,6 +295,12 @@ int fdm_surrogate_apply(fdm_ctx *ctx, const float *w, int judge, int *nfallback,
 #define FDM_Q_TUNING 24        /* double[8]: autotuner choice: patch kernel (1 classic, 3 resident),
                                   threads, eight rows per warp (0/1), sweep time (us), candidates
                                   timed; zeros without autotune */
+#define FDM_Q_GMG_LEVELS 25    /* int32[1 + 4 (L+1)]: coarsenings L of the Q1 multigrid (0 = exact
+                                  coarse solve), then per level cells nx, ny, nz and unknowns nf */
+#define FDM_Q_GMG_STENCIL 26   /* double[sum of 27 nf]: each level's 27-point operator, level by
+                                  level, coefficient-major [27][nf] with offset
+                                  k = (dx+1) + 3 (dy+1) + 9 (dz+1) (unknowns lexicographic in
+                                  the free vertices, x fastest) */
 /* timers of FDM_Q_KERNEL_TIMES */
 #define FDM_T_RESTRICT 0  /* basis change to the FDM basis */
 #define FDM_T_PATCH 1     /* patch gather + condense + triangular solves + back-substitution */

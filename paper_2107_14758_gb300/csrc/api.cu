@@ -74,6 +74,20 @@ struct fdm_ctx {
   size_t rsmem64 = 0, rsmem32 = 0;
   // coarse
   int nc = 0;
+  int nc_dense = 0;  // order of the dense inverse: the Q1 problem, or the coarsest multigrid level
+  // geometric multigrid on the Q1 problem: gmg_L coarsenings (0 = exact solve)
+  int gmg_L = 0, gmg_nu = 2;
+  double gmg_omega = 2.0 / 3.0;
+  std::vector<GmgHostLevel> gmg_host;
+  template <typename T>
+  struct GmgVecs {
+    std::vector<GmgDev<T>> lev;
+    std::vector<T *> b, out, xa, xb, r;  // per level: right-hand side, result, two iterates, residual
+  };
+  GmgVecs<double> gmg64;
+  GmgVecs<float> gmg32;
+  template <typename T> GmgVecs<T> &gmg();
+  std::vector<double> vert[3];  // mesh vertex coordinates per axis
   int *cfree = nullptr;
   double *Acinv64 = nullptr, *rc64 = nullptr, *xc64 = nullptr, *cb64 = nullptr;
   float *Acinv32 = nullptr, *rc32 = nullptr, *xc32 = nullptr, *cb32 = nullptr;
@@ -145,6 +159,10 @@ struct fdm_ctx {
   template <typename T> T *X() const;
   template <typename T> const T *L() const;
   template <typename T> size_t smem() const;
+  template <typename T> T *rc() const;
+  template <typename T> T *xc() const;
+  template <typename T> T *cb() const;
+  template <typename T> const T *Acinv() const;
   OpArgs op_args(bool fp32) const {
     OpArgs a;
     a.g = g;
@@ -156,6 +174,8 @@ struct fdm_ctx {
     return a;
   }
 };
+template <> fdm_ctx::GmgVecs<double> &fdm_ctx::gmg<double>() { return gmg64; }
+template <> fdm_ctx::GmgVecs<float> &fdm_ctx::gmg<float>() { return gmg32; }
 template <> const double *fdm_ctx::tab<double>() const { return tab64; }
 template <> const float *fdm_ctx::tab<float>() const { return tab32; }
 template <> double *fdm_ctx::E<double>() const { return E64; }
@@ -169,6 +189,14 @@ template <typename T> ClusterArgs<T> cluster_args(const fdm_ctx *c);
 template <> ClusterArgs<float> cluster_args<float>(const fdm_ctx *c) { return c->cla32; }
 template <> ClusterArgs<double> cluster_args<double>(const fdm_ctx *c) { return c->cla64; }
 template <> size_t fdm_ctx::smem<float>() const { return smem32; }
+template <> double *fdm_ctx::rc<double>() const { return rc64; }
+template <> float *fdm_ctx::rc<float>() const { return rc32; }
+template <> double *fdm_ctx::xc<double>() const { return xc64; }
+template <> float *fdm_ctx::xc<float>() const { return xc32; }
+template <> double *fdm_ctx::cb<double>() const { return cb64; }
+template <> float *fdm_ctx::cb<float>() const { return cb32; }
+template <> const double *fdm_ctx::Acinv<double>() const { return Acinv64; }
+template <> const float *fdm_ctx::Acinv<float>() const { return Acinv32; }
 
 struct fdm_batch {
   std::vector<fdm_ctx *> ctxs;
@@ -286,25 +314,52 @@ void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st, c
   c->launches += 3;
 }
 
+// one V-cycle of the geometric multigrid on level l: out = V(b) from a zero
+// start (min(nu, 2) Jacobi sweeps in one kernel, the rest one kernel each)
 template <typename T>
-void coarse_correct(fdm_ctx *c, const T *r1, T *x, cudaStream_t st);
-template <>
-void coarse_correct<double>(fdm_ctx *c, const double *r1, double *x, cudaStream_t st) {
-  c->tmark(FDM_T_COARSE, true, st);
-  launch_coarse_restrict<double, double>(c->g, r1, c->tab64, c->cfree, c->rc64, c->cb64, st);
-  launch_dense_symv<double>(c->nc, c->Acinv64, c->rc64, c->xc64, st);
-  launch_coarse_prolong<double, double>(c->g, c->xc64, c->tab64, c->cfree, x, true, st);
-  c->tmark(FDM_T_COARSE, false, st);
-  c->launches += c->nc > 0 ? 4 : 3;
+void gmg_level(fdm_ctx *c, int l, const T *b, T *out, cudaStream_t st) {
+  auto &G = c->gmg<T>();
+  if (l == c->gmg_L) {
+    launch_dense_symv<T>(c->nc_dense, c->Acinv<T>(), b, out, st);
+    c->launches += 1;
+    return;
+  }
+  const GmgDev<T> &F = G.lev[l], &C = G.lev[l + 1];
+  const int nu = c->gmg_nu;
+  T *cur = G.xa[l], *oth = G.xb[l];
+  launch_gmg_pre<T>(F, nu, b, cur, st);
+  for (int s = 2; s < nu; ++s) {
+    launch_gmg_sweep<T>(F, b, cur, oth, st);
+    std::swap(cur, oth);
+  }
+  launch_gmg_resid<T>(F, b, cur, G.r[l], st);
+  launch_gmg_restrict<T>(F, C, G.r[l], G.b[l + 1], st);
+  gmg_level<T>(c, l + 1, G.b[l + 1], G.out[l + 1], st);
+  launch_gmg_prolong<T>(F, C, G.out[l + 1], cur, st);
+  for (int s = 0; s < nu; ++s) {
+    T *dst = s == nu - 1 ? out : oth;
+    launch_gmg_sweep<T>(F, b, cur, dst, st);
+    std::swap(cur, oth);
+  }
+  c->launches += (nu >= 2 ? nu - 1 : 1) + 3 + nu;
 }
-template <>
-void coarse_correct<float>(fdm_ctx *c, const float *r1, float *x, cudaStream_t st) {
+
+// restriction to the Q1 vertices, the Q1 solve (exact, or one multigrid
+// V-cycle), prolongation added to x
+template <typename T>
+void coarse_correct(fdm_ctx *c, const T *r1, T *x, cudaStream_t st) {
   c->tmark(FDM_T_COARSE, true, st);
-  launch_coarse_restrict<float, float>(c->g, r1, c->tab32, c->cfree, c->rc32, c->cb32, st);
-  launch_dense_symv<float>(c->nc, c->Acinv32, c->rc32, c->xc32, st);
-  launch_coarse_prolong<float, float>(c->g, c->xc32, c->tab32, c->cfree, x, true, st);
+  launch_coarse_restrict<T, T>(c->g, r1, c->tab<T>(), c->cfree, c->rc<T>(), c->cb<T>(), st);
+  if (c->nc > 0) {
+    if (c->gmg_L > 0) gmg_level<T>(c, 0, c->rc<T>(), c->xc<T>(), st);
+    else {
+      launch_dense_symv<T>(c->nc, c->Acinv<T>(), c->rc<T>(), c->xc<T>(), st);
+      c->launches += 1;
+    }
+  }
+  launch_coarse_prolong<T, T>(c->g, c->xc<T>(), c->tab<T>(), c->cfree, x, true, st);
   c->tmark(FDM_T_COARSE, false, st);
-  c->launches += c->nc > 0 ? 4 : 3;
+  c->launches += 3;
 }
 
 // y = A u with the FP64 operator (PCG residual) or the FP32 one (inside the preconditioner)
@@ -384,6 +439,9 @@ void setup_geometry(fdm_ctx *c, const fdm_mesh *mesh, const fdm_coeff *coeff) {
   for (auto *v : {&xv, &yv, &zv})
     for (size_t i = 0; i + 1 < v->size(); ++i)
       if (!((*v)[i + 1] > (*v)[i])) fail(FDM_EINVAL, "vertex coordinates must be strictly increasing");
+  c->vert[0] = xv;
+  c->vert[1] = yv;
+  c->vert[2] = zv;
   std::vector<double> mub(3 * ncell);
   for (int cz = 0; cz < c->g.nz; ++cz)
     for (int cy = 0; cy < c->g.ny; ++cy)
@@ -705,6 +763,49 @@ void factor_all(fdm_ctx *c, cudaStream_t st) {
   if (hs) fail(FDM_ENOTSPD, "a patch Schur complement has a nonpositive pivot");
 }
 
+// device copies of one multigrid level in precision T
+template <typename T>
+GmgDev<T> upload_level(fdm_ctx *c, const GmgHostLevel &H, double omega) {
+  GmgDev<T> d;
+  for (int a = 0; a < 3; ++a) d.m[a] = H.m[a];
+  d.nf = H.nf;
+  std::vector<T> A(H.A.begin(), H.A.end()), dw(H.nf);
+  for (int i = 0; i < H.nf; ++i) dw[i] = (T)(omega / H.A[(size_t)13 * H.nf + i]);
+  d.A = c->upload(A);
+  d.dw = c->upload(dw);
+  for (int a = 0; a < 3; ++a)
+    if (!H.t[a].empty()) d.t[a] = c->upload(std::vector<T>(H.t[a].begin(), H.t[a].end()));
+  return d;
+}
+
+template <typename T>
+void alloc_gmg_vectors(fdm_ctx *c, T *rc, T *xc) {
+  auto &G = c->gmg<T>();
+  const int L = c->gmg_L;
+  G.lev.clear();
+  for (int l = 0; l <= L; ++l) G.lev.push_back(upload_level<T>(c, c->gmg_host[l], c->gmg_omega));
+  G.b.assign(L + 1, nullptr);
+  G.out.assign(L + 1, nullptr);
+  G.xa.assign(L + 1, nullptr);
+  G.xb.assign(L + 1, nullptr);
+  G.r.assign(L + 1, nullptr);
+  for (int l = 0; l <= L; ++l) {
+    const int nf = c->gmg_host[l].nf;
+    G.b[l] = l == 0 ? rc : c->alloc<T>(nf);
+    G.out[l] = l == 0 ? xc : c->alloc<T>(nf);
+    if (l < L) {
+      G.xa[l] = c->alloc<T>(nf);
+      G.xb[l] = c->alloc<T>(nf);
+      G.r[l] = c->alloc<T>(nf);
+    }
+  }
+}
+
+// The Q1 coarse space (Section 3): the Galerkin operator of the p-coarse
+// problem, assembled from the cells' 8 x 8 matrices as a 27-point stencil over
+// the free vertices, then either inverted densely (from a banded Cholesky
+// factor) or handed to the geometric multigrid, whose coarsest level is
+// inverted the same way.
 void setup_coarse(fdm_ctx *c, cudaStream_t st) {
   const int nvx = c->g.nx + 1, nvy = c->g.ny + 1, nvz = c->g.nz + 1, nv = nvx * nvy * nvz;
   std::vector<int> cfree(nv, -1);
@@ -722,6 +823,8 @@ void setup_coarse(fdm_ctx *c, cudaStream_t st) {
   c->xc64 = c->alloc<double>(nc);
   c->rc32 = c->alloc<float>(nc);
   c->xc32 = c->alloc<float>(nc);
+  c->gmg_L = 0;
+  c->gmg_host.clear();
   if (nc == 0) return;
   double *Ac = c->alloc<double>((size_t)64 * c->g.ncell);
   launch_coarse_cell_matrices(c->op_args(false), Ac, st);
@@ -729,22 +832,57 @@ void setup_coarse(fdm_ctx *c, cudaStream_t st) {
   std::vector<double> hAc((size_t)64 * c->g.ncell);
   FDM_CUDA(cudaMemcpyAsync(hAc.data(), Ac, hAc.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   FDM_CUDA(cudaStreamSynchronize(st));
-  // banded lower storage Lb[i][k] = A[i][i-k]
-  const int bw = 1 + (c->g.nx - 1) + (c->g.nx - 1) * (c->g.ny - 1);
-  std::vector<double> Lb((size_t)nc * (bw + 1), 0.0);
-  for (int cz = 0; cz < c->g.nz; ++cz)
-    for (int cy = 0; cy < c->g.ny; ++cy)
-      for (int cx = 0; cx < c->g.nx; ++cx) {
-        int e = cx + c->g.nx * (cy + c->g.ny * cz);
-        int f[8];
-        for (int s = 0; s < 8; ++s)
-          f[s] = cfree[(cx + (s & 1)) + nvx * ((cy + ((s >> 1) & 1)) + nvy * (cz + (s >> 2)))];
-        for (int t = 0; t < 8; ++t)
+  // level 0: the Q1 operator as a 27-point stencil (cell contributions in cell order)
+  std::vector<GmgHostLevel> &lev = c->gmg_host;
+  lev.emplace_back();
+  {
+    GmgHostLevel &L0 = lev[0];
+    const int ncell[3] = {c->g.nx, c->g.ny, c->g.nz};
+    for (int a = 0; a < 3; ++a) {
+      L0.n[a] = ncell[a];
+      L0.m[a] = ncell[a] - 1;
+      L0.x[a] = c->vert[a];
+    }
+    L0.nf = nc;
+    L0.A.assign((size_t)27 * nc, 0.0);
+    for (int cz = 0; cz < c->g.nz; ++cz)
+      for (int cy = 0; cy < c->g.ny; ++cy)
+        for (int cx = 0; cx < c->g.nx; ++cx) {
+          const int e = cx + c->g.nx * (cy + c->g.ny * cz);
+          int f[8];
           for (int s = 0; s < 8; ++s)
-            if (f[t] >= 0 && f[s] >= 0 && f[t] >= f[s]) Lb[(size_t)f[t] * (bw + 1) + (f[t] - f[s])] += hAc[(size_t)e * 64 + t * 8 + s];
-      }
+            f[s] = cfree[(cx + (s & 1)) + nvx * ((cy + ((s >> 1) & 1)) + nvy * (cz + (s >> 2)))];
+          for (int t = 0; t < 8; ++t)
+            for (int s = 0; s < 8; ++s)
+              if (f[t] >= 0 && f[s] >= 0) {
+                const int k = ((s & 1) - (t & 1) + 1) + 3 * (((s >> 1) & 1) - ((t >> 1) & 1) + 1) + 9 * ((s >> 2) - (t >> 2) + 1);
+                L0.A[(size_t)k * nc + f[t]] += hAc[(size_t)e * 64 + t * 8 + s];
+              }
+        }
+  }
+  int want = c->opt.coarse_levels;
+  if (want < 0) want = nc > 4096 ? 64 : 0;
+  c->gmg_nu = c->opt.gmg_nu > 0 ? c->opt.gmg_nu : 2;
+  c->gmg_omega = c->opt.gmg_omega > 0.0 ? c->opt.gmg_omega : 2.0 / 3.0;
+  gmg_coarsen(lev, want);
+  c->gmg_L = (int)lev.size() - 1;
+  // the dense inverse of the coarsest level, from its banded Cholesky factor
+  // (lexicographic order: the band reaches the (+1, +1, +1) neighbour)
+  const GmgHostLevel &B = lev.back();
+  const int m = B.nf;
+  const int bw = 1 + B.m[0] + B.m[0] * B.m[1];
+  std::vector<double> Lb((size_t)m * (bw + 1), 0.0);
+  for (int i = 0; i < m; ++i) {
+    const int ix = i % B.m[0], iy = (i / B.m[0]) % B.m[1], iz = i / (B.m[0] * B.m[1]);
+    for (int k = 0; k < 27; ++k) {
+      const int jx = ix + k % 3 - 1, jy = iy + (k / 3) % 3 - 1, jz = iz + k / 9 - 1;
+      if (jx < 0 || jy < 0 || jz < 0 || jx >= B.m[0] || jy >= B.m[1] || jz >= B.m[2]) continue;
+      const int j = jx + B.m[0] * (jy + B.m[1] * jz);
+      if (j <= i) Lb[(size_t)i * (bw + 1) + (i - j)] = B.A[(size_t)k * m + i];
+    }
+  }
   // banded Cholesky
-  for (int i = 0; i < nc; ++i)
+  for (int i = 0; i < m; ++i)
     for (int k = std::max(0, i - bw); k <= i; ++k) {
       double s = Lb[(size_t)i * (bw + 1) + (i - k)];
       for (int j = std::max(0, std::max(i - bw, k - bw)); j < k; ++j)
@@ -757,10 +895,15 @@ void setup_coarse(fdm_ctx *c, cudaStream_t st) {
       }
     }
   double *dLb = c->upload(Lb);
-  c->Acinv64 = c->alloc<double>((size_t)nc * nc);
-  c->Acinv32 = c->alloc<float>((size_t)nc * nc);
-  launch_banded_inverse(nc, bw, dLb, c->Acinv64, st);
-  launch_convert<double, float>((int64_t)nc * nc, c->Acinv64, c->Acinv32, st);
+  c->nc_dense = m;
+  c->Acinv64 = c->alloc<double>((size_t)m * m);
+  c->Acinv32 = c->alloc<float>((size_t)m * m);
+  launch_banded_inverse(m, bw, dLb, c->Acinv64, st);
+  launch_convert<double, float>((int64_t)m * m, c->Acinv64, c->Acinv32, st);
+  if (c->gmg_L > 0) {
+    alloc_gmg_vectors<double>(c, c->rc64, c->xc64);
+    alloc_gmg_vectors<float>(c, c->rc32, c->xc32);
+  }
   FDM_CUDA(cudaStreamSynchronize(st));
   FDM_CUDA(cudaGetLastError());
 }
@@ -1232,6 +1375,9 @@ int fdm_default_options(fdm_options *opt) {
   opt->patch_l2_hints = 0;
   opt->autotune = 0;
   opt->patch_rows_per_warp = 0;
+  opt->coarse_levels = -1;
+  opt->gmg_nu = 2;
+  opt->gmg_omega = 2.0 / 3.0;
   return FDM_OK;
 }
 
@@ -1743,6 +1889,18 @@ int fdm_query(fdm_ctx *c, int what, void *out, size_t *len) {
         break;
       }
       case FDM_Q_TUNING: put(c->tuning, sizeof c->tuning); break;
+      case FDM_Q_GMG_LEVELS: {
+        std::vector<int> v{c->gmg_L};
+        for (const GmgHostLevel &H : c->gmg_host) v.insert(v.end(), {H.n[0], H.n[1], H.n[2], H.nf});
+        put(v.data(), v.size() * sizeof(int));
+        break;
+      }
+      case FDM_Q_GMG_STENCIL: {
+        std::vector<double> v;
+        for (const GmgHostLevel &H : c->gmg_host) v.insert(v.end(), H.A.begin(), H.A.end());
+        put(v.data(), v.size() * sizeof(double));
+        break;
+      }
       case FDM_Q_STATUS: {
         int v = 0;
         FDM_CUDA(cudaMemcpy(&v, c->status, sizeof(int), cudaMemcpyDeviceToHost));

@@ -39,6 +39,20 @@ struct Basis1D {
 };
 Basis1D make_basis(int p);  // throws via fail() on error
 
+// ---------------------------------------------------------------- geometric multigrid (Q1 problem)
+// A level on the host: n cells and m = n - 1 free vertices per axis, vertex
+// coordinates x[n+1], the 27-point stencil A[27][nf] (offset k = (dx+1) +
+// 3 (dy+1) + 9 (dz+1), zero towards Dirichlet vertices) and, once the level has
+// been coarsened, the interpolation parameter t[v] of its odd vertices.
+struct GmgHostLevel {
+  int n[3] = {0, 0, 0}, m[3] = {0, 0, 0}, nf = 0;
+  std::vector<double> x[3], t[3], A;
+};
+// Appends up to max_levels coarser levels to lev (lev[0] given): every other
+// vertex per axis while all cell counts are even and >= 4, linear interpolation
+// in the vertex coordinates, Galerkin operators P^T A P.
+void gmg_coarsen(std::vector<GmgHostLevel> &lev, int max_levels);
+
 // one bulk copy of the streamed patch solve: kind | first << 8 | last << 9,
 // item range [a0, a1) (rows, lines or ELL slices), byte count, element offset
 enum { CK_DINV = 0, CK_ELL_F = 1, CK_LINES_F = 2, CK_L21_F = 3, CK_Z_F = 4, CK_Z_B = 5, CK_L21_B = 6,

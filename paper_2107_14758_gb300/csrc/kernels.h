@@ -157,6 +157,29 @@ int ctx_fail(fdm_ctx *c, int code, const std::string &msg);
 template <typename T, typename Tin>
 void launch_coarse_restrict(const Grid &g, const Tin *r, const T *tab, const int *cfree, T *rc, T *cellbuf,
                             cudaStream_t st);
+// one level of the geometric multigrid on the Q1 problem: m free vertices per
+// axis (lexicographic, x fastest), 27-point stencil A[k][nf] with offset
+// k = (dx+1) + 3 (dy+1) + 9 (dz+1), dw = omega / A[13], and per axis the
+// interpolation parameter t[v] = (x_v - x_{v-1}) / (x_{v+1} - x_{v-1}) at the odd
+// vertices v of this level (used when this level is the fine side of a transfer)
+template <typename T>
+struct GmgDev {
+  int m[3] = {0, 0, 0};
+  int nf = 0;
+  const T *A = nullptr;
+  const T *dw = nullptr;
+  const T *t[3] = {nullptr, nullptr, nullptr};
+};
+template <typename T>
+void launch_gmg_pre(const GmgDev<T> &L, int nu, const T *b, T *x, cudaStream_t st);  // min(nu, 2) sweeps from 0
+template <typename T>
+void launch_gmg_sweep(const GmgDev<T> &L, const T *b, const T *x, T *out, cudaStream_t st);
+template <typename T>
+void launch_gmg_resid(const GmgDev<T> &L, const T *b, const T *x, T *r, cudaStream_t st);
+template <typename T>
+void launch_gmg_restrict(const GmgDev<T> &F, const GmgDev<T> &C, const T *r, T *bc, cudaStream_t st);
+template <typename T>
+void launch_gmg_prolong(const GmgDev<T> &F, const GmgDev<T> &C, const T *xc, T *x, cudaStream_t st);  // x += P xc
 template <typename T>
 void launch_dense_symv(int m, const T *Ainv, const T *x, T *y, cudaStream_t st);
 template <typename T, typename Tout>

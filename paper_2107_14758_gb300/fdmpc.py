@@ -22,7 +22,8 @@ FDM_SURR_AVERAGED, FDM_SURR_EXTERNAL = 0, 1
 (FDM_Q_NDOF, FDM_Q_OMEGA, FDM_Q_LAMBDA, FDM_Q_MU, FDM_Q_NPATCH, FDM_Q_PATCH_CLASS, FDM_Q_CLASS_INFO,
  FDM_Q_GAMMA_ORDER, FDM_Q_FACTOR_NNZ, FDM_Q_PATTERN, FDM_Q_FACTOR, FDM_Q_BASIS, FDM_Q_FACTOR_BYTES,
  FDM_Q_SETUP_SECONDS, FDM_Q_KERNEL_TIMES, FDM_Q_LAUNCHES, FDM_Q_ALGO_BYTES, FDM_Q_STATUS,
- FDM_Q_SURR_FEATURES, FDM_Q_SURR_LABELS, FDM_Q_SURR_BOUNDS, FDM_Q_MUBAR, FDM_Q_SURR_OUTPUT, FDM_Q_TUNING) = range(1, 25)
+ FDM_Q_SURR_FEATURES, FDM_Q_SURR_LABELS, FDM_Q_SURR_BOUNDS, FDM_Q_MUBAR, FDM_Q_SURR_OUTPUT, FDM_Q_TUNING,
+ FDM_Q_GMG_LEVELS, FDM_Q_GMG_STENCIL) = range(1, 27)
 FDM_MLP_NPARAM = 16515
 TIMERS = ("restrict", "patch", "interp", "op64", "op32", "coarse", "vec")
 
@@ -44,7 +45,8 @@ class fdm_options(C.Structure):
                 ("kernel_timing", C.c_int), ("patch_ctas_per_sm", C.c_int), ("patch_threads", C.c_int),
                 ("patch_kernel", C.c_int), ("stream_buffers", C.c_int), ("stream_buffer_kb", C.c_int),
                 ("inject_stall", C.c_int), ("patch_prefetch", C.c_int), ("pcg_graph", C.c_int),
-                ("patch_l2_hints", C.c_int), ("autotune", C.c_int), ("patch_rows_per_warp", C.c_int)]
+                ("patch_l2_hints", C.c_int), ("autotune", C.c_int), ("patch_rows_per_warp", C.c_int),
+                ("coarse_levels", C.c_int), ("gmg_nu", C.c_int), ("gmg_omega", C.c_double)]
 
 
 class fdm_solve_info(C.Structure):
@@ -259,7 +261,7 @@ class Context:
                  omega=0.0, lanczos_start=None, lanczos_steps=20, flexible_beta=-1, kernel_timing=0,
                  patch_ctas_per_sm=0, patch_threads=0, patch_kernel=0, stream_buffers=0, stream_buffer_kb=0,
                  inject_stall=0, wait_timeout_s=1.0, patch_prefetch=0, pcg_graph=1, patch_l2_hints=0, autotune=0, patch_rows_per_warp=0,
-                 stream=None):
+                 coarse_levels=-1, gmg_nu=2, gmg_omega=2.0 / 3.0, stream=None):
         self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (xv, yv, zv)]
         mesh = fdm_mesh()
         mesh.nx, mesh.ny, mesh.nz = len(xv) - 1, len(yv) - 1, len(zv) - 1
@@ -292,6 +294,7 @@ class Context:
         opt.patch_l2_hints = patch_l2_hints
         opt.autotune = autotune
         opt.patch_rows_per_warp = patch_rows_per_warp
+        opt.coarse_levels, opt.gmg_nu, opt.gmg_omega = coarse_levels, gmg_nu, gmg_omega
         opt.wait_timeout_s = wait_timeout_s
         if lanczos_start is not None:
             s = np.ascontiguousarray(lanczos_start, dtype=np.float64)
@@ -376,6 +379,23 @@ class Context:
         """(kernel, threads, rows8, sweep us, candidates) chosen by the autotuner."""
         t = self.query(FDM_Q_TUNING, np.float64, 8)
         return int(t[0]), int(t[1]), int(t[2]), float(t[3]), int(t[4])
+
+    def gmg_levels(self):
+        """[(nx, ny, nz, nf)] of the Q1 multigrid levels (one entry: exact coarse solve)."""
+        v = self.query(FDM_Q_GMG_LEVELS, np.int32, 1 + 4 * 32)
+        L = int(v[0])
+        v = v[1:1 + 4 * (L + 1)].reshape(L + 1, 4)
+        return [tuple(int(a) for a in r) for r in v]
+
+    def gmg_stencils(self):
+        """Each level's 27-point operator as an array [27, nf]."""
+        lev = self.gmg_levels()
+        v = self.query(FDM_Q_GMG_STENCIL, np.float64, 27 * sum(r[3] for r in lev))
+        out, o = [], 0
+        for r in lev:
+            out.append(v[o:o + 27 * r[3]].reshape(27, r[3]))
+            o += 27 * r[3]
+        return out
 
     def lanczos_extremes(self):
         return tuple(self.query(FDM_Q_LAMBDA, np.float64, 2))

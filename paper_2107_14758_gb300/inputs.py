@@ -180,6 +180,9 @@ def workload(name, seed=None):
     if name == "q7_graded16":       # 16^3 graded tensor mesh, Q7, N(0,1) nodal f
         xv, yv, zv = graded_vertices(16, 2 if seed is None else seed)
         return dict(name=name, p=7, xv=xv, yv=yv, zv=zv, jac=None, kappa=None, rhs="nodal_normal", seed=2)
+    if name == "q7_graded32":       # 32^3 graded tensor mesh, Q7, N(0,1) nodal f (multigrid coarse solve)
+        xv, yv, zv = graded_vertices(32, 6 if seed is None else seed)
+        return dict(name=name, p=7, xv=xv, yv=yv, zv=zv, jac=None, kappa=None, rhs="nodal_normal", seed=6)
     if name == "q15_uniform8":      # 8^3 uniform, Q15, manufactured sine
         xv, yv, zv = uniform_vertices(8)
         return dict(name=name, p=15, xv=xv, yv=yv, zv=zv, jac=None, kappa=None, rhs="manufactured", seed=3)

@@ -63,3 +63,14 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert L.fdm_surrogate_grad(None, wp, wp, None, None) == fdmpc.FDM_EINVAL
     o = fdmpc.fdm_default_options()
     assert o.precision == fdmpc.FDM_PREC_FP32 and o.pc == fdmpc.FDM_PC_VCYCLE and o.lanczos_steps == 20
+
+
+def test_default_options_match_header(lib):
+    """The Python struct mirrors the C layout: the defaults written by the
+    library land in the fields of the same names."""
+    from paper_2107_14758_gb300 import fdmpc
+    o = fdmpc.fdm_default_options()
+    assert o.precision == fdmpc.FDM_PREC_FP32 and o.pc == fdmpc.FDM_PC_VCYCLE
+    assert o.lanczos_steps == 20 and o.lanczos_seed == 12345 and o.wait_timeout_s == 1.0
+    assert o.pcg_graph == 1 and o.autotune == 0 and o.patch_rows_per_warp == 0
+    assert o.coarse_levels == -1 and o.gmg_nu == 2 and o.gmg_omega == pytest.approx(2.0 / 3.0, rel=1e-15)
