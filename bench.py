@@ -251,7 +251,8 @@ def bench_gpu(args):
 
     w = inputs.workload(WORKLOAD)
     # the timed solves: the device-driven PCG loop (captured graph), no per-kernel events
-    ctx = fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP32, autotune=1)
+    ctx = fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP32, autotune=1,
+                        pcg_graph=0 if args.pcg_host_loop else 1)
     setup_s = list(ctx.setup_seconds())
     tuning = ctx.tuning()
     free = _free_dofs(ctx.N)
@@ -275,10 +276,12 @@ def bench_gpu(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    torch.cuda.nvtx.range_push("timed_solves")
     iters = []
     for _ in range(args.steps):
         info = step()
         iters.append(info.iterations)
+    torch.cuda.nvtx.range_pop()
     e1.record(stream)
     torch.cuda.synchronize()
     if ws > 1:
@@ -324,8 +327,10 @@ def bench_gpu(args):
     e8 = torch.cuda.Event(enable_timing=True)
     e9 = torch.cuda.Event(enable_timing=True)
     e8.record(stream)
+    torch.cuda.nvtx.range_push("roofline_solves")
     for _ in range(args.steps):
         ctx_kt.pcg_solve(b, x, rtol=RTOL, maxit=MAXIT)
+    torch.cuda.nvtx.range_pop()
     e9.record(stream)
     torch.cuda.synchronize()
     kt = ctx_kt.kernel_times()
@@ -398,6 +403,7 @@ def bench_gpu(args):
                                  (ab["patch32"] / 1e6),
                            "iterations": int(np.median(iters)), "true_rel_residual": rel,
                            "setup_seconds": sum(setup_s),
+                           "pcg_loop": "host" if args.pcg_host_loop else "device (CUDA graph)",
                            "autotuned_patch_solve": {"kernel": "resident" if tuning[0] == 3 else "one CTA per patch",
                                                      "threads": tuning[1], "rows_per_warp": 8 if tuning[2] else 4,
                                                      "sweep_us": tuning[3], "candidates": tuning[4]}},
@@ -613,6 +619,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-preconditioner comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--pcg-host-loop", action="store_true",
+                    help="timed solves through the host PCG loop instead of the captured CUDA graph "
+                         "(for kernel profilers that replay launches one at a time)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the p = 15, deformed (learned surrogate) and 64-problem batched workloads")
     args = ap.parse_args()

@@ -156,3 +156,50 @@ def asm_gll(p, xv, yv, zv, A_full, r):
 def q1_dense(xv, yv, zv):
     """Trilinear (Q1) stiffness on the vertex grid by 2-point Gauss per axis."""
     return dense_matrix(1, xv, yv, zv)
+
+
+def dense_elasticity(p, xv, yv, zv, mu, lam, q=None):
+    """Dense linear-elasticity matrix on the full grid, component-major
+    [3 N, 3 N] (Neumann; restrict with free_mask per component).
+
+    Cell matrices from 3D basis gradients at a tensor Gauss rule: for
+    v = phi_i e_a, u = phi_j e_b, 2 eps(v):eps(u) = delta_ab grad phi_i . grad
+    phi_j + d_b phi_i d_a phi_j and div v div u = d_a phi_i d_b phi_j.
+    """
+    nx, ny, nz = len(xv) - 1, len(yv) - 1, len(zv) - 1
+    n = p + 1
+    q = q or n + 1
+    xg, wg = leg.leggauss(q)
+    V, D = _basis_at(p, xg)
+    Nx, Ny, Nz = grid_shape(p, nx, ny, nz)
+    N = Nx * Ny * Nz
+    M = np.zeros((3 * N, 3 * N))
+    gx = np.einsum("ck,bj,ai->cbakji", V, V, D).reshape(q ** 3, n ** 3)
+    gy = np.einsum("ck,bj,ai->cbakji", V, D, V).reshape(q ** 3, n ** 3)
+    gz = np.einsum("ck,bj,ai->cbakji", D, V, V).reshape(q ** 3, n ** 3)
+    w3 = np.einsum("c,b,a->cba", wg, wg, wg).ravel()
+    for cz in range(nz):
+        for cy in range(ny):
+            for cx in range(nx):
+                h = np.array([xv[cx + 1] - xv[cx], yv[cy + 1] - yv[cy], zv[cz + 1] - zv[cz]])
+                det = np.prod(h / 2)
+                G = np.stack([gx * 2 / h[0], gy * 2 / h[1], gz * 2 / h[2]], axis=-1)   # q, i, 3 (physical)
+                w = w3 * det
+                lap = np.einsum("q,qia,qja->ij", w, G, G)
+                K = np.zeros((3, n ** 3, 3, n ** 3))
+                for a in range(3):
+                    for b in range(3):
+                        blk = mu * np.einsum("q,qi,qj->ij", w, G[:, :, b], G[:, :, a]) + \
+                            lam * np.einsum("q,qi,qj->ij", w, G[:, :, a], G[:, :, b])
+                        if a == b:
+                            blk = blk + mu * lap
+                        K[a, :, b, :] = blk
+                idx = []
+                for k in range(n):
+                    for j in range(n):
+                        for i in range(n):
+                            idx.append((cx * p + i) + Nx * ((cy * p + j) + Ny * (cz * p + k)))
+                idx = np.array(idx)
+                full = np.concatenate([idx + a * N for a in range(3)])
+                M[np.ix_(full, full)] += K.reshape(3 * n ** 3, 3 * n ** 3)
+    return M

@@ -1,0 +1,156 @@
+"""Pins of the elasticity oracle (Section 4.1: primal formulation, SDC
+relaxation): closed forms of the 1D derivative-mass matrix, rigid-body modes
+and a closed-form energy of the independent brute-force assembly, the
+Kronecker operator against that assembly, the SDC blocks against dense
+GLL-basis block-Jacobi Schwarz, PCG against a dense direct solve, and the
+Poisson-ratio dependence that Section 4.1 predicts."""
+import numpy as np
+import pytest
+
+from paper_2107_14758_gb300 import inputs
+from tests import bruteforce as bf
+
+
+@pytest.fixture(scope="module")
+def el(oracle_lib):
+    from oracle import elasticity
+    return elasticity
+
+
+def test_c_hat_closed_forms(el):
+    C1 = el.c_hat(1)
+    assert np.allclose(C1, [[-0.5, -0.5], [0.5, 0.5]], atol=1e-15)
+    for p in (2, 4, 7):
+        C = el.c_hat(p)
+        E = np.zeros((p + 1, p + 1))
+        E[0, 0], E[p, p] = -1.0, 1.0
+        assert np.abs(C + C.T - E).max() <= 1e-13          # integration by parts
+        assert np.abs(C.sum(axis=0)).max() <= 1e-13        # derivative of the constant
+    # exact polynomial integration
+    p = 4
+    L = bf.lagrange_polys(bf.gll_nodes(p))
+    ref = np.array([[((L[k].deriv() * L[l]).integ())(1) - ((L[k].deriv() * L[l]).integ())(-1)
+                     for l in range(p + 1)] for k in range(p + 1)])
+    assert np.abs(el.c_hat(p) - ref).max() <= 1e-13
+
+
+def _grid_coords(p, xv, yv, zv, xi):
+    def nodes(v):
+        out = [v[0]]
+        for c in range(len(v) - 1):
+            out += list(v[c] + 0.5 * (v[c + 1] - v[c]) * (1 + xi[1:]))
+        return np.array(out)
+    X, Y, Z = np.meshgrid(nodes(xv), nodes(yv), nodes(zv), indexing="ij")
+    return [np.transpose(a, (2, 1, 0)).ravel() for a in (X, Y, Z)]
+
+
+def test_bruteforce_rigid_modes_and_dilation(oracle_lib):
+    p = 2
+    xv, yv, zv = np.array([0, 0.4, 1.0]), np.array([0, 0.7]), np.array([0, 0.3, 0.9])
+    mu, lam = 1.3, 2.1
+    K = bf.dense_elasticity(p, xv, yv, zv, mu, lam)
+    x, y, z = _grid_coords(p, xv, yv, zv, bf.gll_nodes(p))
+    one, zero = np.ones_like(x), np.zeros_like(x)
+    modes = [np.concatenate(m) for m in ([one, zero, zero], [zero, one, zero], [zero, zero, one],
+                                         [-y, x, zero], [zero, -z, y], [z, zero, -x])]
+    for u in modes:
+        assert np.abs(K @ u).max() <= 1e-12 * np.abs(K).max()
+    u = np.concatenate([x, y, z])                       # eps = I, div = 3
+    vol = 1.0 * 0.7 * 0.9
+    assert u @ K @ u == pytest.approx((6 * mu + 9 * lam) * vol, rel=1e-12)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_apply_vs_bruteforce(el, p):
+    xv, yv, zv = np.array([0, 0.3, 1.0]), np.array([0, 0.45, 0.8]), np.array([0, 0.2, 0.7, 1.1])
+    mu, lam = 0.8, 3.7
+    E = el.Elasticity(p, xv, yv, zv, mu, lam)
+    K = bf.dense_elasticity(p, xv, yv, zv, mu, lam)
+    free = np.tile(E.free, 3)
+    u = np.where(free, np.random.default_rng(p).standard_normal(3 * E.N), 0.0)
+    ref = np.where(free, K @ u, 0.0)
+    got = E.apply(u).ravel()
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_sdc_blocks_are_block_jacobi_schwarz(el):
+    """The scalar FDM/sparse relaxation with the SDC surrogate of component j is
+    additive Schwarz over the vertex stars of the diagonal block A_jj itself
+    (dense GLL-basis patches of the brute-force matrix)."""
+    p = 2
+    xv, yv, zv = np.array([0, 0.3, 1.0]), np.array([0, 0.45, 0.8]), np.array([0, 0.2, 0.7])
+    E = el.Elasticity(p, xv, yv, zv, 1.1, 4.0)
+    E.setup_sdc()
+    K = bf.dense_elasticity(p, xv, yv, zv, 1.1, 4.0)
+    N = E.N
+    r = np.where(np.tile(E.free, 3), np.random.default_rng(4).standard_normal(3 * N), 0.0).reshape(3, N)
+    z = E.sdc(r)
+    for j in range(3):
+        Kjj = K[j * N:(j + 1) * N, j * N:(j + 1) * N]
+        ref = bf.asm_gll(p, xv, yv, zv, Kjj, r[j])
+        assert np.abs(z[j] - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_coarse_is_galerkin_and_exact_on_q1(el):
+    """P^T A P is symmetric positive definite, and the coarse correction
+    reproduces a Q1 displacement: x = P A_c^{-1} P^T A (P v) = P v."""
+    p = 3
+    xv, yv, zv = inputs.graded_vertices(3, 61)
+    E = el.Elasticity(p, xv, yv, zv, 1.0, 10.0)
+    E.setup_coarse()
+    assert np.allclose(E.Ac, E.Ac.T, atol=1e-12 * np.abs(E.Ac).max())
+    assert np.linalg.eigvalsh(E.Ac).min() > 0
+    v = np.random.default_rng(5).standard_normal((3, E.nq))
+    u = E.prolong(v)
+    assert np.abs(E.coarse_apply(E.apply(u)) - u).max() <= 1e-10 * np.abs(u).max()
+
+
+def test_pcg_matches_direct_solve(el):
+    p = 2
+    xv, yv, zv = inputs.graded_vertices(3, 62)
+    E = el.Elasticity(p, xv, yv, zv, 1.0, 5.0)
+    E.setup_sdc()
+    E.setup_coarse()
+    E.lanczos_omega(inputs.lanczos_start(3 * E.N))
+    K = bf.dense_elasticity(p, xv, yv, zv, 1.0, 5.0)
+    free = np.tile(E.free, 3)
+    b = np.where(free, np.random.default_rng(6).standard_normal(3 * E.N), 0.0)
+    xd = np.zeros(3 * E.N)
+    xd[free] = np.linalg.solve(K[np.ix_(free, free)], b[free])
+    for pc in (1, 2):
+        x, it, conv = E.pcg(b, rtol=1e-10, maxit=400, pc=pc)
+        assert conv
+        assert np.linalg.norm(x.ravel() - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+def test_vcycle_symmetric_positive(el):
+    xv, yv, zv = inputs.graded_vertices(3, 63)
+    E = el.Elasticity(2, xv, yv, zv, 1.0, 20.0)
+    E.setup_sdc()
+    E.setup_coarse()
+    E.lanczos_omega(inputs.lanczos_start(3 * E.N))
+    rng = np.random.default_rng(7)
+    free = np.tile(E.free, 3)
+    r1, r2 = (np.where(free, rng.standard_normal(3 * E.N), 0.0) for _ in range(2))
+    z1, z2 = E.pc_apply(r1).ravel(), E.pc_apply(r2).ravel()
+    assert abs(z1 @ r2 - z2 @ r1) <= 1e-11 * abs(z1 @ r1)
+    assert z1 @ r1 > 0 and z2 @ r2 > 0
+
+
+def test_iterations_grow_with_lambda(el):
+    """Section 4.1: the SDC bound grows like (1 - nu) / (1 - 2 nu); the PCG
+    iteration counts grow with lambda at fixed mu = 1 (uniform 4^3 mesh, p = 3,
+    body force -0.02 e_2)."""
+    xv = np.linspace(0, 1, 5)
+    its = []
+    for lam in (0.0, 1.0, 10.0, 100.0):
+        E = el.Elasticity(3, xv, xv, xv, 1.0, lam)
+        E.setup_sdc()
+        E.setup_coarse()
+        E.lanczos_omega(inputs.lanczos_start(3 * E.N))
+        b = E.body_force([0.0, -0.02, 0.0])
+        _, it, conv = E.pcg(b, rtol=1e-8, maxit=500)
+        assert conv
+        its.append(it)
+    assert all(a <= b for a, b in zip(its, its[1:])), its
+    assert its[-1] >= 2 * its[0], its
