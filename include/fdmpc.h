@@ -73,10 +73,15 @@ typedef struct {
  * samples27 (HOST, optional, copied): inputs of the learned surrogate,
  * kappa and J (row-major) at the 3x3x3 Gauss-Legendre points of every cell
  * (points x fastest, cells x fastest): 270 nx ny nz doubles, kappa > 0;
- * curved cells only. */
+ * curved cells only.
+ * mu (HOST, optional, copied): the per-cell separable coefficients of the
+ * relaxation (3 per cell: x, y, z scalings, cells x fastest, > 0), used
+ * instead of the box-cell values or the averaged surrogate; the same as a
+ * later fdm_surrogate_load without refactoring. */
 typedef struct {
   const double *kappa_q;
   const double *samples27;
+  const double *mu;
 } fdm_coeff;
 
 typedef struct {
@@ -263,6 +268,40 @@ int fdm_surrogate_train(int k, fdm_ctx *const *ctxs, const float *w_init, int st
  * Synchronises `stream`. */
 int fdm_surrogate_apply(fdm_ctx *ctx, const float *w, int judge, int *nfallback, int *kept,
                         void *stream);
+
+/* ---- primal linear elasticity (Section 4.1) ----
+ * a(v, u) = int 2 mu eps(v):eps(u) + lambda div v div u on box cells
+ * (mesh->jac must be NULL), Q_p per displacement component on the GLL grid of
+ * the scalar problem, clamped (homogeneous Dirichlet) on the whole boundary.
+ * Vectors are DEVICE FP64 arrays of 3 ndof doubles, component-major
+ * ([component][node], nodes x fastest); Dirichlet entries are ignored on input
+ * and 0 on output.
+ * The preconditioner (opt->pc): FDM_PC_ASM = omega times the separate
+ * displacement components (SDC) relaxation, i.e. block-Jacobi over the
+ * components, each block A_jj (per-axis coefficients mu + (mu + lambda)
+ * delta_aj: separable on box cells) relaxed by the vertex-star FDM/sparse
+ * additive Schwarz of the scalar problem; FDM_PC_VCYCLE (default) = the hybrid
+ * V(1,1) with that relaxation, the elasticity residual and the vector Q1
+ * Galerkin coarse problem solved exactly.  omega from opt->lanczos_steps
+ * CG-Lanczos steps on A_SDC^{-1} A (opt->lanczos_start: 3 ndof HOST doubles,
+ * or N(0,1) from opt->lanczos_seed), unless opt->omega > 0.  opt->precision
+ * selects the FP32 or FP64 preconditioner; PCG is FP64 (flexible beta with
+ * FP32).  The patch-solve options apply to the three scalar relaxations.
+ * Degrees 1..15.  Errors as for the scalar problem; fdm_elast_last_error. */
+typedef struct fdm_elast fdm_elast;
+int fdm_elast_setup(const fdm_mesh *mesh, int p, double mu, double lambda, const fdm_options *opt,
+                    fdm_elast **out, void *stream);
+/* y = A u */
+int elast_apply(fdm_elast *e, const double *u_dev, double *y_dev, void *stream);
+/* z = P^{-1} r (the preconditioner selected by opt->pc) */
+int elast_pc_apply(fdm_elast *e, const double *r_dev, double *z_dev, void *stream);
+/* PCG from x = 0 to ||r||_2 <= rtol ||b||_2 (as pcg_solve, host-driven loop) */
+int elast_pcg_solve(fdm_elast *e, const double *b_dev, double *x_dev, double rtol, int maxit,
+                    fdm_solve_info *info, void *stream);
+/* FDM_Q_NDOF (int64, nodes per component), FDM_Q_OMEGA, FDM_Q_LAMBDA, FDM_Q_LAUNCHES */
+int fdm_elast_query(fdm_elast *e, int what, void *out, size_t *len);
+const char *fdm_elast_last_error(const fdm_elast *e);
+void fdm_elast_destroy(fdm_elast *e);
 
 /* ---- introspection ---- */
 #define FDM_Q_NDOF 1         /* int64: number of grid nodes */

@@ -354,6 +354,18 @@ bool launch_box_op_fast(const OpArgs &a, const Tin *u, Tout *y, T *E, cudaStream
   }
 }
 
+template <typename T, typename Tout>
+void launch_gather_cells(const Grid &g, const T *E, const double *rsub, Tout *y, cudaStream_t st) {
+  if (!dispatch_n(g.n, [&](auto NC) {
+        constexpr int N = decltype(NC)::value;
+        k_gather_t<T, Tout, N><<<dim3((g.N[0] + 127) / 128, g.N[1], g.N[2]), 128, 0, st>>>(g, E, rsub, y);
+      }))
+    fail(FDM_EINVAL, "node gather: unsupported degree");
+}
+template void launch_gather_cells<double, double>(const Grid &, const double *, const double *, double *,
+                                                  cudaStream_t);
+template void launch_gather_cells<float, float>(const Grid &, const float *, const double *, float *, cudaStream_t);
+
 template bool launch_box_op_fast<double, double, double>(const OpArgs &, const double *, double *, double *,
                                                          cudaStream_t, const double *);
 template bool launch_box_op_fast<float, float, float>(const OpArgs &, const float *, float *, float *, cudaStream_t,

@@ -162,6 +162,18 @@ void launch_coarse_restrict(const Grid &g, const Tin *r, const T *tab, const int
 // k = (dx+1) + 3 (dy+1) + 9 (dz+1), dw = omega / A[13], and per axis the
 // interpolation parameter t[v] = (x_v - x_{v-1}) / (x_{v+1} - x_{v-1}) at the odd
 // vertices v of this level (used when this level is the fine side of a transfer)
+// sums cell-local values E [cell][n^3] over the cells of each grid node: y = sum
+// (or rsub - sum), Dirichlet nodes 0
+template <typename T, typename Tout>
+void launch_gather_cells(const Grid &g, const T *E, const double *rsub, Tout *y, cudaStream_t st);
+// linear elasticity on box cells: cell-local y^K = K^K u^K for the three
+// components (u [3][ndof], G scratch [9][ncell][n^3], E [3][ncell][n^3]);
+// Lc = half-widths [cell][3]; tab = the 1D tables (Gauss V, D), wq = Gauss weights
+template <typename T>
+size_t elast_smem(int n);
+template <typename T, typename Tin>
+void launch_elast_cells(const Grid &g, const Tin *u, const T *tab, const T *wq, const double *Lc, double mu, double lam,
+                        T *G, T *E, cudaStream_t st);
 template <typename T>
 struct GmgDev {
   int m[3] = {0, 0, 0};

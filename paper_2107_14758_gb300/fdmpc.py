@@ -35,7 +35,8 @@ class fdm_mesh(C.Structure):
 
 
 class fdm_coeff(C.Structure):
-    _fields_ = [("kappa_q", C.POINTER(C.c_double)), ("samples27", C.POINTER(C.c_double))]
+    _fields_ = [("kappa_q", C.POINTER(C.c_double)), ("samples27", C.POINTER(C.c_double)),
+                ("mu", C.POINTER(C.c_double))]
 
 
 class fdm_options(C.Structure):
@@ -93,6 +94,16 @@ def load():
     L.fdm_last_error.restype = C.c_char_p
     L.fdm_destroy.argtypes = [vp]
     L.fdm_destroy.restype = None
+    L.fdm_elast_setup.argtypes = [C.POINTER(fdm_mesh), C.c_int, C.c_double, C.c_double, C.POINTER(fdm_options),
+                                  C.POINTER(vp), vp]
+    for f in ("elast_apply", "elast_pc_apply"):
+        getattr(L, f).argtypes = [vp, vp, vp, vp]
+    L.elast_pcg_solve.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.POINTER(fdm_solve_info), vp]
+    L.fdm_elast_query.argtypes = [vp, C.c_int, vp, C.POINTER(C.c_size_t)]
+    L.fdm_elast_last_error.argtypes = [vp]
+    L.fdm_elast_last_error.restype = C.c_char_p
+    L.fdm_elast_destroy.argtypes = [vp]
+    L.fdm_elast_destroy.restype = None
     _lib = L
     return L
 
@@ -162,6 +173,45 @@ def pcg_solve(ctx, b, x, rtol, maxit, stream=None, raise_on_noconv=True):
         return info
     _check(rc, ctx)
     return info
+
+
+def _check_elast(rc, e=None):
+    if rc < 0:
+        raise FdmError(rc, load().fdm_elast_last_error(e).decode())
+    return rc
+
+
+def fdm_elast_setup(mesh, p, mu, lam, opt, stream=None):
+    h = C.c_void_p()
+    _check_elast(load().fdm_elast_setup(C.byref(mesh), p, mu, lam, C.byref(opt), C.byref(h), _stream(stream)))
+    return h
+
+
+def elast_apply(e, u, y, stream=None):
+    _check_elast(load().elast_apply(e, _tptr(u), _tptr(y), _stream(stream)), e)
+
+
+def elast_pc_apply(e, r, z, stream=None):
+    _check_elast(load().elast_pc_apply(e, _tptr(r), _tptr(z), _stream(stream)), e)
+
+
+def elast_pcg_solve(e, b, x, rtol, maxit, stream=None, raise_on_noconv=True):
+    info = fdm_solve_info()
+    rc = load().elast_pcg_solve(e, _tptr(b), _tptr(x), rtol, maxit, C.byref(info), _stream(stream))
+    if rc == FDM_ENOCONV and not raise_on_noconv:
+        return info
+    _check_elast(rc, e)
+    return info
+
+
+def fdm_elast_query(e, what, out):
+    n = C.c_size_t(out.nbytes)
+    _check_elast(load().fdm_elast_query(e, what, out.ctypes.data_as(C.c_void_p), C.byref(n)), e)
+    return n.value
+
+
+def fdm_elast_destroy(e):
+    load().fdm_elast_destroy(e)
 
 
 def fdm_batch_setup(ctxs):
@@ -456,3 +506,72 @@ class Context:
     @property
     def npatch(self):
         return int(self.query(FDM_Q_NPATCH, np.int32, 1)[0])
+
+
+class Elasticity:
+    """Owns one primal linear-elasticity problem (fdm_elast): box cells,
+    clamped boundary, vectors [3 * ndof] component-major on the device."""
+
+    def __init__(self, p, xv, yv, zv, mu, lam, precision=FDM_PREC_FP32, pc=FDM_PC_VCYCLE, omega=0.0,
+                 lanczos_start=None, lanczos_steps=20, flexible_beta=-1, patch_threads=0, stream=None):
+        self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (xv, yv, zv)]
+        mesh = fdm_mesh()
+        mesh.nx, mesh.ny, mesh.nz = len(xv) - 1, len(yv) - 1, len(zv) - 1
+        mesh.xv, mesh.yv, mesh.zv = [_dptr(a) for a in self._keep]
+        opt = fdm_default_options()
+        opt.precision, opt.pc, opt.omega, opt.lanczos_steps = precision, pc, omega, lanczos_steps
+        opt.flexible_beta = flexible_beta
+        opt.patch_threads = patch_threads
+        if lanczos_start is not None:
+            s = np.ascontiguousarray(lanczos_start, dtype=np.float64)
+            self._keep.append(s)
+            opt.lanczos_start = _dptr(s)
+        self.p = p
+        self.N = (mesh.nx * p + 1, mesh.ny * p + 1, mesh.nz * p + 1)
+        self.ndof = self.N[0] * self.N[1] * self.N[2]
+        self.h = fdm_elast_setup(mesh, p, mu, lam, opt, stream)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            fdm_elast_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _out(self, like):
+        import torch
+        return torch.empty(3 * self.ndof, dtype=torch.float64, device=like.device)
+
+    def apply(self, u, y=None):
+        y = self._out(u) if y is None else y
+        elast_apply(self.h, u, y)
+        return y
+
+    def pc_apply(self, r, z=None):
+        z = self._out(r) if z is None else z
+        elast_pc_apply(self.h, r, z)
+        return z
+
+    def pcg_solve(self, b, x=None, rtol=1e-8, maxit=500, raise_on_noconv=True):
+        x = self._out(b) if x is None else x
+        return x, elast_pcg_solve(self.h, b, x, rtol, maxit, raise_on_noconv=raise_on_noconv)
+
+    @property
+    def omega(self):
+        out = np.zeros(1)
+        fdm_elast_query(self.h, FDM_Q_OMEGA, out)
+        return float(out[0])
+
+    def lanczos_extremes(self):
+        out = np.zeros(2)
+        fdm_elast_query(self.h, FDM_Q_LAMBDA, out)
+        return float(out[0]), float(out[1])
+
+    def launches(self):
+        out = np.zeros(1, dtype=np.int64)
+        fdm_elast_query(self.h, FDM_Q_LAUNCHES, out)
+        return int(out[0])

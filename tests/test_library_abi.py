@@ -33,7 +33,9 @@ def test_header_declares_the_boundary():
     names = _declared_functions()
     for required in ("fdm_setup", "stiffness_apply", "pc_apply", "asm_apply", "pcg_solve", "fdm_query",
                      "fdm_destroy", "fdm_last_error", "fdm_batch_setup", "pcg_solve_batched",
-                     "fdm_surrogate_load", "fdm_surrogate_train", "fdm_surrogate_grad", "fdm_surrogate_apply"):
+                     "fdm_surrogate_load", "fdm_surrogate_train", "fdm_surrogate_grad", "fdm_surrogate_apply",
+                     "fdm_elast_setup", "elast_apply", "elast_pc_apply", "elast_pcg_solve", "fdm_elast_query",
+                     "fdm_elast_destroy"):
         assert required in names
 
 
@@ -63,6 +65,16 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert L.fdm_surrogate_grad(None, wp, wp, None, None) == fdmpc.FDM_EINVAL
     o = fdmpc.fdm_default_options()
     assert o.precision == fdmpc.FDM_PREC_FP32 and o.pc == fdmpc.FDM_PC_VCYCLE and o.lanczos_steps == 20
+    # elasticity: Lame parameters, degree and curved cells are checked on the host
+    for mu, lam, p in ((0.0, 1.0, 3), (1.0, -1.0, 3), (1.0, 1.0, 16), (float("nan"), 1.0, 3)):
+        assert L.fdm_elast_setup(ctypes.byref(mesh), p, mu, lam, ctypes.byref(o), ctypes.byref(h), None) == \
+            fdmpc.FDM_EINVAL
+    jac = np.zeros(9 * 8 * 4 ** 3)
+    mesh.jac = jac.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert L.fdm_elast_setup(ctypes.byref(mesh), 3, 1.0, 1.0, ctypes.byref(o), ctypes.byref(h), None) == \
+        fdmpc.FDM_EINVAL
+    assert "box cells" in L.fdm_elast_last_error(None).decode()
+    assert L.elast_apply(None, None, None, None) == fdmpc.FDM_EINVAL
 
 
 def test_default_options_match_header(lib):
