@@ -384,6 +384,7 @@ def bench_gpu(args):
         secondary["deformed"] = bench_deformed(dev, fdmpc, inputs)
         secondary["batched"] = bench_batched(dev, fdmpc, inputs)
         secondary["gmg"] = bench_gmg(dev, fdmpc, inputs)
+        secondary["elasticity"] = bench_elasticity(dev, fdmpc, inputs)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -507,6 +508,53 @@ def bench_gmg(dev, fdmpc, inputs):
            "mixed_true_rel_residual": info.true_rnorm / info.rnorm0,
            "setup_seconds": {"symbolic": setup[0], "factor": setup[1], "coarse": setup[2], "lanczos": setup[3]}}
     ctx.close()
+    return out
+
+
+ELAST_LAMBDAS = (0.0, 1.0, 10.0, 100.0, 1000.0)
+
+
+def bench_elasticity(dev, fdmpc, inputs):
+    """Primal linear elasticity (Section 4.1) on the 8^3 uniform mesh of the
+    unit cube, mu = 1, body force -0.02 e_2, clamped boundary: PCG iterations
+    with the SDC/FDM/sparse relaxation in the hybrid V(1,1) for p = 3, 7, 15 and
+    lambda = 0 .. 1000 (mixed precision), and the solve throughput at p = 7."""
+    import torch
+    xv = [i / 8.0 for i in range(9)]
+    table = {}
+    out = {"workload": "elasticity 8^3 uniform unit cube, mu = 1, body force -0.02 e_2, clamped boundary, "
+                       "SDC relaxation, mixed precision"}
+    for p in (3, 7, 15):
+        its = []
+        for lam in ELAST_LAMBDAS:
+            e = fdmpc.Elasticity(p, xv, xv, xv, 1.0, lam, precision=fdmpc.FDM_PREC_FP32)
+            n = e.ndof
+            # load vector: b_y = -0.02 * int phi (the mass of the constant), from the scalar mass apply
+            ctx = fdmpc.Context(p, xv, xv, xv, precision=fdmpc.FDM_PREC_FP64, omega=1.0, pc=fdmpc.FDM_PC_ASM)
+            m = ctx.mass_apply(torch.ones(n, dtype=torch.float64, device=dev))
+            ctx.close()
+            b = torch.zeros(3 * n, dtype=torch.float64, device=dev)
+            b[n:2 * n] = -0.02 * m
+            x = torch.empty_like(b)
+            info = e.pcg_solve(b, x, rtol=RTOL, maxit=3000)[1]
+            its.append(info.iterations)
+            if p == 7 and lam == 1.0:
+                free = 3 * (8 * p - 1) ** 3
+                torch.cuda.synchronize()
+                s0 = torch.cuda.Event(enable_timing=True)
+                s1 = torch.cuda.Event(enable_timing=True)
+                s0.record(torch.cuda.current_stream())
+                for _ in range(3):
+                    info = e.pcg_solve(b, x, rtol=RTOL, maxit=3000)[1]
+                s1.record(torch.cuda.current_stream())
+                torch.cuda.synchronize()
+                ms = s0.elapsed_time(s1) / 3
+                out["q7_lambda1"] = {"free_dofs": free, "ms_per_solve": ms, "solve_dofs_per_s": free / (ms * 1e-3),
+                                     "iterations": info.iterations,
+                                     "true_rel_residual": info.true_rnorm / info.rnorm0}
+            e.close()
+        table["p=%d" % p] = its
+    out["iterations"] = {"lambda": list(ELAST_LAMBDAS), **table}
     return out
 
 
