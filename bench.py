@@ -405,14 +405,16 @@ def bench_gpu(args):
                            "iterations": int(np.median(iters)), "true_rel_residual": rel,
                            "setup_seconds": sum(setup_s),
                            "pcg_loop": "host" if args.pcg_host_loop else "device (CUDA graph)",
-                           "autotuned_patch_solve": {"kernel": "resident" if tuning[0] == 3 else "one CTA per patch",
+                           "autotuned_patch_solve": {"kernel": {3: "resident", 5: "one CTA per patch, Schur-coupling form"}.get(
+                                                         tuning[0], "one CTA per patch"),
                                                      "threads": tuning[1], "rows_per_warp": 8 if tuning[2] else 4,
                                                      "sweep_us": tuning[3], "candidates": tuning[4]}},
                 "clocks": clocks,
                 "e2e": {"value": e2e_value, "unit": "DoF/s", "h2d_bytes_per_step": 8 * ctx.ndof,
                         "d2h_bytes_per_step": 8 * ctx.ndof},
                 "gpu_launches": int(launches),
-                "roofline": {"kernel": "k_patch_resident<float>" if tuning[0] == 3 else "k_patch_solve<float>",
+                "roofline": {"kernel": {3: "k_patch_resident<float>", 5: "k_patch_solve_sc<float>"}.get(
+                                 tuning[0], "k_patch_solve<float>"),
                              "bound": "hbm", "achieved": achieved, "peak": peak,
                              "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                              "algorithmic_bytes_per_launch": ab["patch32"], "avg_launch_ms": patch_ms,

@@ -128,6 +128,13 @@ typedef struct {
   int patch_rows_per_warp; /* rows a warp keeps in flight in the forward products of the
                               one-CTA-per-patch solve: 4 or 8 (0 = 8 for 256 threads and L21
                               rows of 200 or more, else 4) */
+  int patch_form;     /* layout of the patch factors: 1 = L form (the Cholesky factor L_G:
+                         diagonal level 0, sparse L10/L20, line blocks, dense L21, Z = L_TT^{-1});
+                         2 = Schur-coupling form (y_B = S_BB^{-1} g_B, x_T = W (g_T - S_TB y_B),
+                         x_B = y_B - S_BB^{-1} S_BT x_T with B = levels 0 and 1, T = the top
+                         level, S_TB in S_G's own sparsity and W = (L_TT L_TT^T)^{-1}: no dense
+                         L21, W read once), one CTA per patch only; 0 (default) = 2 for
+                         patch_kernel 0 or 1, else 1 */
   int coarse_levels;  /* solve of the Q1 coarse problem (Section 3): 0 = exact (dense inverse
                          from a banded Cholesky factor); k > 0 = one geometric multigrid V-cycle
                          with at most k coarsenings (every other vertex per axis while all cell

@@ -65,6 +65,8 @@ struct fdm_ctx {
   bool res64 = false, res32 = false;
   int fcap = 0, res_threads = 512, res_tmp = 0;
   int rows8 = 0;  // forward products of the classic patch solve: eight rows per warp
+  bool scform = false;  // Schur-coupling form of the patch factors and solve
+  int headcap32 = 0, headcap64 = 0;  // its staged values before W, per precision (elements)
   // cluster patch solve for the classes with a dense top level (a prefix of the order)
   int n_heavy = 0, cl_threads = 256;
   bool cl32 = false, cl64 = false;
@@ -278,7 +280,14 @@ void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st, c
   c->tmark(FDM_T_RESTRICT, false, st);
   c->tmark(FDM_T_PATCH, true, st);
   const bool resident = sizeof(T) == 4 ? c->res32 : c->res64;
-  if (c->stream) {
+  if (c->scform) {
+    PatchSolveArgs<T> a{c->g, c->d_cls, c->d_patches, c->d_order, c->E<T>(), c->mu, c->tab<T>(), c->L<T>(),
+                        c->X<T>(), patch_sc_tmp(c->maxN1, c->maxN2, c->patch_threads), 0,
+                        (uint64_t)(std::max(c->opt.wait_timeout_s, 0.0) * 1e9), c->status, 0, 0, 0};
+    a.headcap = sizeof(T) == 4 ? c->headcap32 : c->headcap64;
+    launch_patch_sc<T>(a, c->nsolve, patch_sc_smem<T>(c->maxG, c->maxN1, c->maxN2, c->patch_threads, a.headcap),
+                       c->patch_threads, st);
+  } else if (c->stream) {
     if (launch_patch_stream<T>(stream_args<T>(c), c->patch_threads, st) != 0)
       fail(FDM_ECUDA, "streamed patch solve: launch configuration rejected");
   } else if (resident) {
@@ -590,7 +599,12 @@ void setup_cluster(fdm_ctx *c) {
 
 void setup_patches(fdm_ctx *c) {
   const int p = c->p;
-  c->classes = build_classes(p);
+  // factor form: the Schur-coupling form serves the one-CTA-per-patch solve;
+  // the streamed, resident and cluster kernels read the L form
+  const bool l_kernel = c->opt.patch_kernel >= 2;
+  if (c->opt.patch_form == 2 && l_kernel) fail(FDM_EINVAL, "patch_form 2 needs patch_kernel 0 or 1");
+  c->scform = c->opt.patch_form == 2 || (c->opt.patch_form == 0 && !l_kernel);
+  c->classes = build_classes(p, c->scform);
   c->nbuf = c->opt.stream_buffers > 0 ? c->opt.stream_buffers : 4;
   c->buf_bytes = 1024 * (c->opt.stream_buffer_kb > 0 ? c->opt.stream_buffer_kb : 16);
   // default: one CTA per patch reading the factor directly (measured fastest on
@@ -620,6 +634,15 @@ void setup_patches(fdm_ctx *c) {
     D.ginv = c->upload(C.ginv);
     D.line_of = c->upload(C.line_of);
     D.gsrc = c->upload(C.gsrc);
+    D.sc = C.sc ? 1 : 0;
+    D.KT = C.KT;
+    D.ldT = C.ldT;
+    D.off_st = C.off_st;
+    D.st_col = c->upload(C.st_col);
+    D.ct_ptr = c->upload(C.ct_ptr);
+    D.ct_pos = c->upload(C.ct_pos);
+    D.cB_ptr = c->upload(C.cB_ptr);
+    D.cB_pos = c->upload(C.cB_pos);
     {
       std::vector<ChunkDev> s32 = build_schedule(C, 4, c->buf_bytes), s64 = build_schedule(C, 8, c->buf_bytes);
       D.sched32 = c->upload(s32);
@@ -705,6 +728,16 @@ void setup_patches(fdm_ctx *c) {
   c->smem64 = patch_smem_bytes<double>(c->g.n, c->maxG, c->maxN1, c->maxN2);
   c->smem32 = patch_smem_bytes<float>(c->g.n, c->maxG, c->maxN1, c->maxN2);
   c->patch_threads = c->opt.patch_threads > 0 ? c->opt.patch_threads : (c->maxG > 1000 ? 1024 : 256);
+  if (c->scform) {  // 256 or 512 threads
+    c->patch_threads = c->opt.patch_threads > 0 ? (c->opt.patch_threads >= 512 ? 512 : 256) : (c->maxG > 1000 ? 512 : 256);
+    if (patch_sc_smem<double>(c->maxG, c->maxN1, c->maxN2, 512, 0) > 224 * 1024)
+      fail(FDM_EINVAL, "patch interface too large for shared memory (Schur-coupling form)");
+    // stage the values before W in shared memory where the largest class's fit in 48 KB
+    int64_t head = 0;
+    for (const PatchClass &C : c->classes) head = std::max<int64_t>(head, C.off_z);
+    c->headcap32 = head * 4 <= 48 * 1024 ? (int)head : 0;
+    c->headcap64 = head * 8 <= 48 * 1024 ? (int)head : 0;
+  }
   // eight rows per warp in flight pay off for long L21 rows with 256 threads (measured:
   // 10 % at Q8, neutral at Q7, slower with 1024 threads at Q15)
   {
@@ -1025,7 +1058,8 @@ void autotune_patch(fdm_ctx *c, cudaStream_t st) {
   std::vector<Cand> cands = {{1, 256, 0}, {1, 256, 1}, {1, 512, 0}, {1, 1024, 0}};
   const bool fp32 = c->opt.precision == FDM_PREC_FP32;
   const size_t rs = fp32 ? c->rsmem32 : c->rsmem64;
-  if (rs <= 225 * 1024) cands.push_back({3, 512, 0});
+  if (c->scform) cands = {{5, 256, 0}, {5, 512, 0}};  // the factor layout fixes the kernel
+  else if (rs <= 225 * 1024) cands.push_back({3, 512, 0});
   const int64_t n = c->g.ndof;
   fill(n, 1.0, c->r, st);
   mask_dirichlet(c->g, c->r, st);
@@ -2215,13 +2249,16 @@ int fdm_query(fdm_ctx *c, int what, void *out, size_t *len) {
         break;
       }
       case FDM_Q_ALGO_BYTES: {
-        // one patch-solve launch reads every structurally nonzero entry of every
-        // L_Gamma once, reads the cell-local FDM residual once and writes every
-        // star solution once; one asm_apply adds the FP64 input and output vectors
-        // and the 3 surrogate coefficients per cell.
+        // one patch-solve launch reads every stored nonzero of every patch's
+        // solve operator once (L form: the structurally nonzero entries of
+        // L_Gamma; Schur-coupling form: level-0 pivots, L10, the line blocks,
+        // S_TB and the lower triangle of W), reads the cell-local FDM residual
+        // once and writes every star solution once; one asm_apply adds the FP64
+        // input and output vectors and the 3 surrogate coefficients per cell.
         double nnz = 0.0, nd = 0.0;
         for (int i = 0; i < c->npatch; ++i) {
-          nnz += (double)c->classes[c->h_patches[i].cls].nnzL;
+          const PatchClass &K = c->classes[c->h_patches[i].cls];
+          nnz += (double)(c->scform ? K.nnzSC : K.nnzL);
           nd += (double)c->classes[c->h_patches[i].cls].nd;
         }
         double ne = (double)c->g.ncell * c->g.n * c->g.n * c->g.n;

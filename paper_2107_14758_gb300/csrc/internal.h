@@ -83,6 +83,14 @@ struct PatchClass {
   std::vector<int> c0_ptr, c0_pos;  // per level-0 column: positions e*ldr0 + r in the ELL block
   std::vector<int> r0_ptr, r0_idx;  // per level-0 column: rows (>= n0, ascending) of L
   int ld21 = 0;                 // row stride of L21 (n1 rounded up to 4)
+  // Schur-coupling form: S_TB (top rows x levels 0 and 1, S's own pattern) in
+  // ELL by top rows, and the positions of each lower column for S_BT x
+  bool sc = false;
+  int KT = 0, ldT = 0;          // entries per top row, slice stride (n2 rounded up to 4)
+  int64_t off_st = 0, nnzST = 0, nnzSC = 0;
+  std::vector<int> st_col;      // [KT * ldT] lower column or -1
+  std::vector<int> ct_ptr, ct_pos;  // per lower column (n0 + n1): positions e*ldT + t
+  std::vector<int> cB_ptr, cB_pos;  // per level-0 column: ELL positions of level-1 rows only
   // value layout of one patch (in elements)
   int64_t off_dinv0 = 0, off_ell = 0, off_lines = 0, off_l21 = 0, off_z = 0, nval = 0;
   std::vector<int> line_off;    // [nlines] offsets of the inverse line blocks
@@ -94,7 +102,7 @@ struct PatchClass {
   std::vector<int> gsrc;        // [8*nG] cells containing each interface dof (slot << 16 | local)
 };
 
-std::vector<PatchClass> build_classes(int p);
+std::vector<PatchClass> build_classes(int p, bool sc);
 
 // ---------------------------------------------------------------- device views
 // Per-class tables on the device (concatenated over classes).
@@ -118,6 +126,14 @@ struct ClassDev {
   const int *gsrc;       // [8*nG] (star cell slot << 16 | cell-local index), -1 terminated
   const ChunkDev *sched32, *sched64;  // streamed-solve schedules (FP32 / FP64 values)
   int nsched32, nsched64;
+  // Schur-coupling form
+  int sc, KT, ldT;
+  int64_t off_st;
+  const int *st_col;     // [KT*ldT]
+  const int *ct_ptr;     // [n0+n1+1]
+  const int *ct_pos;
+  const int *cB_ptr;     // [n0+1]
+  const int *cB_pos;
 };
 std::vector<ChunkDev> build_schedule(const struct PatchClass &C, int elem_bytes, int cap_bytes);
 

@@ -609,6 +609,221 @@ void launch_interp_fdm(const InterpArgs<T> &a, double omega, Tout *z, cudaStream
   k_interp_fdm<T, Tout><<<a.g.ncell, 256, sm, st>>>(a, omega, z);
 }
 
+// ------------------------------------------------------------------ Schur-coupling form
+// The same exact patch solve, organised around the 2 x 2 block form of the
+// interface Schur complement with B = levels 0 and 1, T = the top level:
+//   y_B = S_BB^{-1} g_B,  x_T = W (g_T - S_TB y_B),  x_B = y_B - S_BB^{-1} S_BT x_T,
+// where S_BB = L_BB L_BB^T (diagonal level 0, sparse L10, line blocks of L11:
+// the leading block of L_G) and W = (L_TT L_TT^T)^{-1} is the inverse of the
+// top block's Schur complement.  S_TB keeps S_G's own sparsity (no fill), so
+// the dense L21 block of the factor is not stored, and W is read once where
+// Z = L_TT^{-1} is read twice (forward and backward).
+
+// out = S_BB^{-1} in over the lower block (n0 + n1 entries); t1, z1: n1 each
+template <typename T, int NT>
+__device__ __forceinline__ void bb_solve(const ClassDev &C, const T *Lv, const T *in, T *out, T *t1, T *z1) {
+  const int tid = threadIdx.x, n0 = C.n0, n1 = C.n1;
+  const T *dinv0 = Lv + C.off_dinv0, *ell = Lv + C.off_ell;
+  for (int j = tid; j < n0; j += NT) out[j] = in[j] * dinv0[j];  // y_0 = L_00^{-1} g_0
+  __syncthreads();
+  for (int r = tid; r < n1; r += NT) {  // t_1 = g_1 - L_10 y_0
+    T acc = 0;
+#pragma unroll 4
+    for (int e = 0; e < C.K0; ++e) {
+      const int col = C.ell_col[e * C.ldr0 + r];
+      if (col >= 0) acc += ell[e * C.ldr0 + r] * out[col];
+    }
+    t1[r] = in[n0 + r] - acc;
+  }
+  __syncthreads();
+  for (int i = tid; i < n1; i += NT) {  // z_1 = L_11^{-1} t_1, line by line
+    const int b = C.line_of[i], s0 = C.line_start[b], w = C.line_len[b];
+    const T *Li = Lv + C.off_lines + C.line_off[b] + (int64_t)(i - s0) * w;
+    T acc = 0;
+    for (int cc = 0; cc <= i - s0; ++cc) acc += Li[cc] * t1[s0 + cc];
+    z1[i] = acc;
+  }
+  __syncthreads();
+  for (int i = tid; i < n1; i += NT) {  // x_1 = L_11^{-T} z_1
+    const int b = C.line_of[i], s0 = C.line_start[b], w = C.line_len[b];
+    const T *Lb = Lv + C.off_lines + C.line_off[b];
+    T s = 0;
+    for (int cc = i - s0; cc < w; ++cc) s += Lb[cc * w + (i - s0)] * z1[s0 + cc];
+    out[n0 + i] = s;
+  }
+  __syncthreads();
+  for (int j = tid; j < n0; j += NT) {  // x_0 = L_00^{-T} (y_0 - L_10^T x_1)
+    T s = out[j];
+    const int q1 = C.cB_ptr[j + 1];
+    for (int q = C.cB_ptr[j]; q < q1; ++q) {
+      const int pos = C.cB_pos[q];
+      s -= ell[pos] * out[n0 + pos % C.ldr0];
+    }
+    out[j] = s * dinv0[j];
+  }
+  __syncthreads();
+}
+
+// x = W v for the symmetric W given by its lower triangle in rows (row r holds
+// W[r][0..r], zero-padded to a multiple of 4).  A warp takes four rows at a
+// time; each lane reads the same column groups of the four rows, adds the row
+// dots (the lower triangle with the diagonal, butterfly-reduced) and
+// accumulates the strictly lower entries times v_r into its warp's column
+// accumulator (acc, NW rows of ld, zero on entry): the lower triangle is read
+// once and every entry used twice.  The warp accumulators are summed in fixed
+// order, so the result does not depend on timing.
+template <typename T, int NT>
+__device__ __forceinline__ void sym_apply(const ClassDev &C, const T *Wv, const T *v, T *x, T *acc, int ld) {
+  constexpr int NW = NT / 32, RB = 4;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, n2 = C.n2;
+  T *aw = acc + warp * ld;
+  for (int r0 = warp * RB; r0 < n2; r0 += NW * RB) {
+    T rs[RB], vr[RB];
+    int ngu[RB];
+    const T *row[RB];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int r = r0 + u < n2 ? r0 + u : n2 - 1;
+      row[u] = Wv + C.zoff[r];
+      ngu[u] = r0 + u < n2 ? (C.zoff[r + 1] - C.zoff[r]) / 4 : 0;
+      rs[u] = 0;
+      vr[u] = r0 + u < n2 ? v[r0 + u] : T(0);
+    }
+    int ngmax = 0;
+#pragma unroll
+    for (int u = 0; u < RB; ++u) ngmax = ngu[u] > ngmax ? ngu[u] : ngmax;
+    for (int q4 = lane; q4 < ngmax; q4 += 32) {
+      V4<T> w[RB];
+#pragma unroll
+      for (int u = 0; u < RB; ++u) w[u] = q4 < ngu[u] ? load4(row[u] + 4 * q4) : V4<T>{0, 0, 0, 0};
+      const T *vv = v + 4 * q4;  // padding entries of W are zero, v is finite there
+      const int cb = 4 * q4;
+      T c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+#pragma unroll
+      for (int u = 0; u < RB; ++u) {
+        rs[u] += w[u].x * vv[0] + w[u].y * vv[1] + w[u].z * vv[2] + w[u].w * vv[3];
+        const int r = r0 + u;
+        c0 += (cb < r ? w[u].x : T(0)) * vr[u];
+        c1 += (cb + 1 < r ? w[u].y : T(0)) * vr[u];
+        c2 += (cb + 2 < r ? w[u].z : T(0)) * vr[u];
+        c3 += (cb + 3 < r ? w[u].w : T(0)) * vr[u];
+      }
+      aw[cb] += c0;
+      aw[cb + 1] += c1;
+      aw[cb + 2] += c2;
+      aw[cb + 3] += c3;
+    }
+    multi_warp_sum<T, RB>(rs, lane);
+    if ((lane & (32 / RB - 1)) == 0) {
+      const int u = rb_slot<RB>(lane);
+      if (r0 + u < n2) x[r0 + u] = rs[0];
+    }
+  }
+  __syncthreads();
+  for (int cc = tid; cc < n2; cc += NT) {
+    T s = x[cc];
+    for (int q = 0; q < NW; ++q) s += acc[q * ld + cc];
+    x[cc] = s;
+  }
+  __syncthreads();
+}
+
+// The values before W (level-0 pivots, L10, the line blocks, S_TB: the small,
+// latency-bound phases) are staged in shared memory by one bulk copy
+// (cp.async.bulk) issued before the gather when they fit in a.headcap
+// elements; the mbarrier wait is bounded by a.timeout_ns (status word on
+// expiry).  W streams from global memory.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_patch_solve_sc(PatchSolveArgs<T> a) {
+  extern __shared__ __align__(128) unsigned char smem_[];
+  const int tid = threadIdx.x;
+  const PatchDev P = a.patches[a.order[blockIdx.x]];
+  const ClassDev &C = a.cls[P.cls];
+  __shared__ int sCell[8];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int sFail;
+  T *H = reinterpret_cast<T *>(smem_);  // a.headcap elements (a multiple of 4)
+  T *gv = H + a.headcap;
+  const T *Lv = a.L + P.voff;
+  const bool stage = C.off_z > 0 && C.off_z <= a.headcap;
+  if (stage && tid == 0) {
+    sFail = 0;
+    bulk::mbar_init(&bar, 1);
+    bulk::fence_mbar_init();
+    const uint32_t bytes = (uint32_t)(C.off_z * (int64_t)sizeof(T));  // a multiple of 16
+    bulk::mbar_arrive_expect_tx(&bar, bytes);
+    for (uint32_t off = 0; off < bytes; off += 32768)
+      bulk::bulk_g2s(reinterpret_cast<char *>(H) + off, reinterpret_cast<const char *>(Lv) + off,
+                     bytes - off < 32768 ? bytes - off : 32768, &bar);
+  }
+  patch_gather<T, NT>(a, P, C, gv, sCell);  // also zeroes y, x and tmp (barriers inside)
+  const T *Lh = Lv;
+  if (stage) {
+    if (!bulk::mbar_wait_bounded(&bar, 0, a.timeout_ns)) sFail = 1;
+    __syncthreads();
+    if (sFail) {
+      bulk::mbar_wait_bounded(&bar, 0, a.timeout_ns);  // a second bounded wait for the copy in flight
+      if (tid == 0) atomicExch(a.status, 1);
+      return;
+    }
+    Lh = H;
+  }
+  const int nG = C.nG, nb = C.n0 + C.n1, n2 = C.n2, ld = C.ldT;
+  T *yv = gv + nG, *xv = yv + nG, *tmp = xv + nG;
+  const int l1 = (C.n1 + 3) & ~3;
+  T *t1 = tmp, *z1 = tmp + l1, *acc = tmp + 2 * l1;
+  bb_solve<T, NT>(C, Lh, gv, yv, t1, z1);  // y_B = S_BB^{-1} g_B
+  const T *st = Lh + C.off_st;
+  for (int t = tid; t < n2; t += NT) {  // v_T = g_T - S_TB y_B, in place
+    T s = 0;
+    for (int e = 0; e < C.KT; ++e) {
+      const int col = C.st_col[e * ld + t];
+      if (col >= 0) s += st[e * ld + t] * yv[col];
+    }
+    gv[nb + t] -= s;
+  }
+  __syncthreads();
+  sym_apply<T, NT>(C, Lv + C.off_z, gv + nb, xv + nb, acc, ld);  // x_T = W v_T
+  for (int cc = tid; cc < nb; cc += NT) {  // r_B = S_BT x_T (g_B is no longer needed)
+    T s = 0;
+    const int q1 = C.ct_ptr[cc + 1];
+    for (int q = C.ct_ptr[cc]; q < q1; ++q) {
+      const int pos = C.ct_pos[q];
+      s += st[pos] * xv[nb + pos % ld];
+    }
+    gv[cc] = s;
+  }
+  __syncthreads();
+  bb_solve<T, NT>(C, Lh, gv, xv, t1, z1);  // u_B = S_BB^{-1} r_B
+  for (int k = tid; k < nb; k += NT) xv[k] = yv[k] - xv[k];  // x_B = y_B - u_B
+  __syncthreads();
+  T *X = a.X + P.xoff;
+  for (int k = tid; k < nG; k += NT) X[k] = xv[k];
+}
+
+int patch_sc_tmp(int maxN1, int maxN2, int threads) {
+  const int l1 = (maxN1 + 3) & ~3, l2 = (maxN2 + 3) & ~3;
+  return 2 * l1 + (threads / 32) * l2;
+}
+
+template <typename T>
+size_t patch_sc_smem(int maxG, int maxN1, int maxN2, int threads, int headcap) {
+  return sizeof(T) * ((size_t)headcap + 3 * (size_t)maxG + patch_sc_tmp(maxN1, maxN2, threads));
+}
+
+template <typename T>
+void launch_patch_sc(const PatchSolveArgs<T> &a, int npatch, size_t smem, int threads, cudaStream_t st) {
+  if (npatch <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    FDM_CUDA(cudaFuncSetAttribute(k_patch_solve_sc<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024));
+    FDM_CUDA(cudaFuncSetAttribute(k_patch_solve_sc<T, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024));
+    attr = true;
+  }
+  if (threads >= 512) k_patch_solve_sc<T, 512><<<npatch, 512, smem, st>>>(a);
+  else k_patch_solve_sc<T, 256><<<npatch, 256, smem, st>>>(a);
+}
+
 int patch_tmp_elems(int maxN1, int maxN2) {
   // tmp holds a level-1 vector (n1) or the sliced partial sums of L21^T x_2
   // and Z^T y_2 (slices * row length, slices clamped to fit)
@@ -704,7 +919,9 @@ void launch_patch_solve(const PatchSolveArgs<T> &a, int npatch, size_t smem, int
   template void launch_patch_solve<T>(const PatchSolveArgs<T> &, int, size_t, int, cudaStream_t);        \
   template size_t patch_resident_smem<T>(int, int, int);                                                    \
   template void launch_patch_resident<T>(const PatchSolveArgs<T> &, int, int, size_t, int, cudaStream_t);  \
-  template size_t patch_smem_for_occupancy<T>(size_t, int);
+  template size_t patch_smem_for_occupancy<T>(size_t, int);                                                 \
+  template size_t patch_sc_smem<T>(int, int, int, int, int);                                                \
+  template void launch_patch_sc<T>(const PatchSolveArgs<T> &, int, size_t, int, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

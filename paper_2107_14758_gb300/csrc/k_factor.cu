@@ -311,10 +311,11 @@ __global__ void __launch_bounds__(256) k_pack(FactorArgs a) {
     int64_t off = C.off_lines + C.line_off[b];
     tri_inverse(S + (int64_t)s0 * nG + s0, nG, w, V + off, w, W != nullptr, W ? W + off : nullptr);
   }
-  for (int64_t q = threadIdx.x; q < (int64_t)n2 * C.ld21; q += blockDim.x) {
-    int r = (int)(q / C.ld21), cc = (int)(q % C.ld21);
-    put(C.off_l21 + q, cc < n1 ? S[(int64_t)(n0 + n1 + r) * nG + n0 + cc] : 0.0);
-  }
+  if (!C.sc)
+    for (int64_t q = threadIdx.x; q < (int64_t)n2 * C.ld21; q += blockDim.x) {
+      int r = (int)(q / C.ld21), cc = (int)(q % C.ld21);
+      put(C.off_l21 + q, cc < n1 ? S[(int64_t)(n0 + n1 + r) * nG + n0 + cc] : 0.0);
+    }
   // top level: Z = L_top^{-1} by forward substitution, one column per thread;
   // column c of Z (below the diagonal) is kept in row c of the strict upper
   // triangle of the workspace, which the factorisation no longer uses.
@@ -331,15 +332,82 @@ __global__ void __launch_bounds__(256) k_pack(FactorArgs a) {
     }
   }
   __syncthreads();
-  for (int r = 0; r < n2; ++r) {
-    const int len = C.zoff[r + 1] - C.zoff[r];
-    const int64_t off = C.off_z + C.zoff[r];
-    for (int cc = threadIdx.x; cc < len; cc += blockDim.x) {
-      double v = 0.0;
-      if (cc == r) v = 1.0 / S[(int64_t)(base + r) * nG + base + r];
-      else if (cc < r) v = S[(int64_t)(base + cc) * nG + base + r];
-      put(off + cc, v);
+  if (!C.sc) {
+    for (int r = 0; r < n2; ++r) {
+      const int len = C.zoff[r + 1] - C.zoff[r];
+      const int64_t off = C.off_z + C.zoff[r];
+      for (int cc = threadIdx.x; cc < len; cc += blockDim.x) {
+        double v = 0.0;
+        if (cc == r) v = 1.0 / S[(int64_t)(base + r) * nG + base + r];
+        else if (cc < r) v = S[(int64_t)(base + cc) * nG + base + r];
+        put(off + cc, v);
+      }
     }
+    return;
+  }
+  // Schur-coupling form: W = Z^T Z = (L_top L_top^T)^{-1}, its lower triangle by
+  // rows.  With Zt[x][k] = Z[k][x] (row x of Zt is column x of Z, stored in row
+  // base + x of the workspace above the diagonal, 1 / L_xx on it, zero before
+  // it), W[r][c] = sum_k Zt[r][k] Zt[c][k]: a symmetric rank-n2 product by
+  // 32 x 32 tiles, each thread owning four entries of a tile.
+  __shared__ double Ta[PANEL][PANEL + 1], Tb[PANEL][PANEL + 1];
+  auto zt = [&](int x, int k) -> double {
+    if (x >= n2 || k >= n2 || k < x) return 0.0;
+    if (k == x) return 1.0 / S[(int64_t)(base + x) * nG + base + x];
+    return Sw[(int64_t)(base + x) * nG + base + k];
+  };
+  const int nt = (n2 + PANEL - 1) / PANEL;
+  for (int tile = 0; tile < nt * (nt + 1) / 2; ++tile) {
+    int ti = 0;
+    while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+    const int tj = tile - ti * (ti + 1) / 2;
+    const int r0 = ti * PANEL, c0 = tj * PANEL;
+    double acc[PANEL * PANEL / 256];
+#pragma unroll
+    for (int m = 0; m < PANEL * PANEL / 256; ++m) acc[m] = 0.0;
+    for (int k0 = r0; k0 < n2; k0 += PANEL) {  // Zt[r][k] = 0 for k < r0 <= r
+      for (int q = threadIdx.x; q < PANEL * PANEL; q += blockDim.x) {
+        const int i = q / PANEL, k = q % PANEL;
+        Ta[i][k] = zt(r0 + i, k0 + k);
+        Tb[i][k] = zt(c0 + i, k0 + k);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < PANEL * PANEL / 256; ++m) {
+        const int q = threadIdx.x + 256 * m, i = q / PANEL, j = q % PANEL;
+        double s = 0.0;
+#pragma unroll 8
+        for (int k = 0; k < PANEL; ++k) s += Ta[i][k] * Tb[j][k];
+        acc[m] += s;
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int m = 0; m < PANEL * PANEL / 256; ++m) {
+      const int q = threadIdx.x + 256 * m, r = r0 + q / PANEL, cc = c0 + q % PANEL;
+      if (r < n2 && cc <= r) put(C.off_z + C.zoff[r] + cc, acc[m]);
+    }
+  }
+  for (int r = threadIdx.x; r < n2; r += blockDim.x)  // zero padding of each row
+    for (int cc = r + 1; cc < C.zoff[r + 1] - C.zoff[r]; ++cc) put(C.off_z + C.zoff[r] + cc, 0.0);
+}
+
+// Schur-coupling form: the values of S_TB (top rows of S_G in the lower
+// columns, S's own pattern) before the factorisation overwrites S
+__global__ void __launch_bounds__(256) k_extract_st(FactorArgs a) {
+  const int slot = blockIdx.x;
+  const PatchDev P = a.patches[a.plist[slot]];
+  const ClassDev &C = a.cls[P.cls];
+  if (!C.sc || C.KT == 0) return;
+  const int nG = C.nG, base = C.n0 + C.n1;
+  const double *S = a.S + (int64_t)slot * a.ldS;
+  double *V = a.L64 + P.voff;
+  float *W = a.L32 ? a.L32 + P.voff : nullptr;
+  for (int q = threadIdx.x; q < C.KT * C.ldT; q += blockDim.x) {
+    const int col = C.st_col[q], t = q % C.ldT;
+    const double v = (col >= 0 && t < C.n2) ? S[(int64_t)(base + t) * nG + col] : 0.0;
+    V[C.off_st + q] = v;
+    if (W) W[C.off_st + q] = (float)v;
   }
 }
 
@@ -353,6 +421,7 @@ void launch_factor_batch(const FactorArgs &a, int count, cudaStream_t st) {
   size_t sm = assemble_smem_bytes(a.g.n);
   cudaFuncSetAttribute(k_assemble_schur, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   k_assemble_schur<<<count, 256, sm, st>>>(a);
+  k_extract_st<<<count, 256, 0, st>>>(a);
   k_factor<<<count, 256, 0, st>>>(a);
   k_pack<<<count, 256, 0, st>>>(a);
 }

@@ -29,8 +29,16 @@ struct PatchSolveArgs {
   int inject_stall;
   int l2hint;  // L2 eviction priorities: forward reads evict-last, backward reads evict-first
   int rows8;   // eight rows per warp in the forward products (else four)
+  int headcap = 0;  // Schur-coupling form: elements of shared memory for the patch's values
+                    // before W (staged by one bulk copy where they fit), 0 = none
 };
 int patch_tmp_elems(int maxN1, int maxN2);
+// Schur-coupling form of the patch solve (one CTA per patch, 256 or 512 threads)
+int patch_sc_tmp(int maxN1, int maxN2, int threads);
+template <typename T>
+size_t patch_sc_smem(int maxG, int maxN1, int maxN2, int threads, int headcap);
+template <typename T>
+void launch_patch_sc(const PatchSolveArgs<T> &a, int npatch, size_t smem, int threads, cudaStream_t st);
 // the resident variant: fcap factor elements per CTA in shared memory (one
 // patch's values), tmp sized for `threads`
 int patch_resident_tmp(int maxN1, int maxN2, int threads);

@@ -50,7 +50,7 @@ inline bool af_nz(int i, int j, int p) { return i == j || isv(i, p) || isv(j, p)
 
 }  // namespace
 
-std::vector<PatchClass> build_classes(int p) {
+std::vector<PatchClass> build_classes(int p, bool sc) {
   std::vector<PatchClass> out(8);
   for (int id = 0; id < 8; ++id) {
     PatchClass &C = out[id];
@@ -209,6 +209,7 @@ std::vector<PatchClass> build_classes(int p) {
                   for (int v = 0; v < u; ++v) add(fc[u], fc[v]);
               }
         }
+    const std::vector<Bits> col0 = col;  // the pattern of S_G itself (before fill)
     // --- symbolic Cholesky via the elimination tree ---
     for (int j = 0; j < m; ++j) {
       int par = col[j].first_from(j + 1);
@@ -249,6 +250,12 @@ std::vector<PatchClass> build_classes(int p) {
       }
       C.r0_ptr[j + 1] = (int)C.r0_idx.size();
     }
+    // the Schur-coupling form keeps only the level-1 rows (L10); the top rows'
+    // level-0 couplings live in S_TB there
+    if (sc) {
+      C.nrow0 = C.n1;
+      rowcols.resize(C.n1);
+    }
     C.K0 = 0;
     for (auto &v : rowcols) C.K0 = std::max(C.K0, (int)v.size());
     C.ldr0 = (C.nrow0 + 3) & ~3;
@@ -265,8 +272,45 @@ std::vector<PatchClass> build_classes(int p) {
       for (int q : colpos[j]) C.c0_pos.push_back(q);
       C.c0_ptr[j + 1] = (int)C.c0_pos.size();
     }
-    // --- value layout of one patch (elements), 16-byte aligned sections ---
+    // level-0 columns restricted to the level-1 rows (the lower block B of
+    // the Schur-coupling form)
+    C.cB_ptr.assign(C.n0 + 1, 0);
+    for (int j = 0; j < C.n0; ++j) {
+      for (int q = C.c0_ptr[j]; q < C.c0_ptr[j + 1]; ++q)
+        if (C.c0_pos[q] % C.ldr0 < C.n1) C.cB_pos.push_back(C.c0_pos[q]);
+      C.cB_ptr[j + 1] = (int)C.cB_pos.size();
+    }
+    // --- Schur-coupling form: the top rows of S_G in the columns of levels 0
+    // and 1, S_TB, with S's own pattern (no fill): ELL by top rows and, for
+    // S_BT = S_TB^T, the positions of each lower column in ascending order ---
     auto up4 = [](int64_t x) { return (x + 3) & ~int64_t(3); };
+    const int nb = C.n0 + C.n1;
+    C.ldT = (int)up4(C.n2);
+    std::vector<std::vector<int>> trow(C.n2);
+    for (int cc = 0; cc < nb; ++cc)
+      for (int r = col0[cc].first_from(nb); r >= 0; r = col0[cc].first_from(r + 1)) trow[r - nb].push_back(cc);
+    C.KT = 0;
+    for (auto &v : trow) C.KT = std::max(C.KT, (int)v.size());
+    C.st_col.assign((size_t)C.KT * C.ldT, -1);
+    std::vector<std::vector<int>> tpos(nb);
+    for (int t = 0; t < C.n2; ++t)
+      for (size_t e = 0; e < trow[t].size(); ++e) {
+        C.st_col[e * C.ldT + t] = trow[t][e];
+        tpos[trow[t][e]].push_back((int)(e * C.ldT + t));
+      }
+    C.ct_ptr.assign(nb + 1, 0);
+    for (int cc = 0; cc < nb; ++cc) {
+      std::sort(tpos[cc].begin(), tpos[cc].end());
+      for (int q : tpos[cc]) C.ct_pos.push_back(q);
+      C.ct_ptr[cc + 1] = (int)C.ct_pos.size();
+    }
+    C.nnzST = (int64_t)C.ct_pos.size();
+    // stored nonzeros of the Schur-coupling form: level-0 pivots, L10, the line
+    // blocks of L11 (lower triangles), S_TB, the lower triangle of W
+    C.nnzSC = C.n0 + (int64_t)C.cB_pos.size() + C.nnzST + (int64_t)C.n2 * (C.n2 + 1) / 2;
+    for (int b = 0; b < C.nlines; ++b) C.nnzSC += (int64_t)C.line_len[b] * (C.line_len[b] + 1) / 2;
+    // --- value layout of one patch (elements), 16-byte aligned sections ---
+    C.sc = sc;
     C.ld21 = (int)up4(C.n1);
     int64_t off = 0;
     C.off_dinv0 = off;
@@ -278,9 +322,13 @@ std::vector<PatchClass> build_classes(int p) {
       C.line_off.push_back((int)(off - C.off_lines));
       off = up4(off + (int64_t)C.line_len[b] * C.line_len[b]);
     }
+    // L form: the dense L21 block; Schur-coupling form: the values of S_TB
     C.off_l21 = off;
-    off = up4(off + (int64_t)C.n2 * C.ld21);
-    // top level: Z = L_top^{-1} (lower triangular) by rows, each padded to 4
+    C.off_st = off;
+    off = sc ? up4(off + (int64_t)C.KT * C.ldT) : up4(off + (int64_t)C.n2 * C.ld21);
+    // top level by rows, each padded to 4: Z = L_top^{-1} (lower triangular; L
+    // form) or the lower triangle of W = Z^T Z = (L_top L_top^T)^{-1} (Schur-
+    // coupling form)
     C.off_z = off;
     C.zoff.assign(C.n2 + 1, 0);
     for (int r = 0; r < C.n2; ++r) C.zoff[r + 1] = C.zoff[r] + (int)up4(r + 1);

@@ -374,7 +374,7 @@ def test_resident_matches_classic_bitwise(p, precision):
     out = []
     for kernel in (1, 3):
         ctx = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7, patch_kernel=kernel,
-                            patch_threads=512)
+                            patch_threads=512, patch_form=1)
         out.append(N(ctx.asm_apply(r)))
         assert ctx.status() == 0
         ctx.close()
@@ -406,10 +406,14 @@ def test_autotuned_context_matches(p, precision):
     a = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7)
     b = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7, autotune=1)
     kernel, threads, rows8, us, ncand = b.tuning()
+    assert kernel == 5 and threads in (256, 512) and us > 0 and ncand == 2   # Schur-coupling form (default)
+    c = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7, autotune=1, patch_form=1)
+    kernel, threads, rows8, us, ncand = c.tuning()
     assert kernel in (1, 3) and threads in (256, 512, 1024) and rows8 in (0, 1) and us > 0 and ncand >= 4
     assert a.tuning()[4] == 0
     tol = 1e-12 if precision == FP64 else 1e-5
     assert relerr(N(b.asm_apply(r)), N(a.asm_apply(r))) <= tol
+    assert relerr(N(c.asm_apply(r)), N(a.asm_apply(r))) <= tol
     assert b.status() == 0
 
 
@@ -443,3 +447,32 @@ def test_bounded_wait_reports_timeout():
     y = ctx.stiffness_apply(b)  # the CUDA context is still healthy
     torch.cuda.synchronize()
     assert torch.isfinite(y).all()
+
+
+@pytest.mark.parametrize("p,precision", [(1, FP64), (2, FP64), (3, FP64), (7, FP64), (11, FP64), (4, FP32), (7, FP32),
+                                         (15, FP32)])
+def test_patch_forms_agree(p, precision):
+    """The Schur-coupling form (x_T = W (g_T - S_TB y_B), x_B = y_B - S_BB^{-1}
+    S_BT x_T) and the L form (forward and backward solves with L_G) are the same
+    exact patch solve: the relaxations agree to rounding, and the Schur-coupling
+    form stores fewer values (no dense L21, W in place of Z)."""
+    xv, yv, zv = inputs.graded_vertices(2 if p >= 11 else 3, 12)
+    r = T(np.random.default_rng(61).standard_normal(((len(xv) - 1) * p + 1) ** 3))
+    out, ab = [], []
+    for form in (1, 2):
+        ctx = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7, patch_form=form)
+        out.append(N(ctx.asm_apply(r)))
+        ab.append(ctx.algo_bytes()["patch64"])
+        assert ctx.status() == 0
+        ctx.close()
+    assert relerr(out[1], out[0]) <= (1e-12 if precision == FP64 else 2e-5)
+    if p >= 7:
+        assert ab[1] < 0.6 * ab[0]
+    elif p >= 3:
+        assert ab[1] < ab[0]
+
+
+def test_patch_form_rejects_l_kernels():
+    xv = np.linspace(0, 1, 3)
+    with pytest.raises(fdmpc.FdmError):
+        fdmpc.Context(3, xv, xv, xv, precision=FP32, omega=1.0, patch_kernel=3, patch_form=2)
