@@ -127,7 +127,8 @@ typedef struct {
                          tuned differently agree to rounding, not bit for bit */
   int patch_rows_per_warp; /* rows a warp keeps in flight in the forward products of the
                               one-CTA-per-patch solve: 4 or 8 (0 = 8 for 256 threads and L21
-                              rows of 200 or more, else 4) */
+                              rows of 200 or more, else 4); in the Schur-coupling form, the
+                              rows of W per warp: 4 (64 registers) or otherwise 2 (48) */
   int patch_form;     /* layout of the patch factors: 1 = L form (the Cholesky factor L_G:
                          diagonal level 0, sparse L10/L20, line blocks, dense L21, Z = L_TT^{-1});
                          2 = Schur-coupling form (y_B = S_BB^{-1} g_B, x_T = W (g_T - S_TB y_B),

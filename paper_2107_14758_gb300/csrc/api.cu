@@ -67,6 +67,7 @@ struct fdm_ctx {
   int rows8 = 0;  // forward products of the classic patch solve: eight rows per warp
   bool scform = false;  // Schur-coupling form of the patch factors and solve
   int headcap32 = 0, headcap64 = 0;  // its staged values before W, per precision (elements)
+  int bcap32 = 0, bcap64 = 0;        // the same before S_TB (lower block only)
   // cluster patch solve for the classes with a dense top level (a prefix of the order)
   int n_heavy = 0, cl_threads = 256;
   bool cl32 = false, cl64 = false;
@@ -284,7 +285,10 @@ void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st, c
     PatchSolveArgs<T> a{c->g, c->d_cls, c->d_patches, c->d_order, c->E<T>(), c->mu, c->tab<T>(), c->L<T>(),
                         c->X<T>(), patch_sc_tmp(c->maxN1, c->maxN2, c->patch_threads), 0,
                         (uint64_t)(std::max(c->opt.wait_timeout_s, 0.0) * 1e9), c->status, 0, 0, 0};
-    a.headcap = sizeof(T) == 4 ? c->headcap32 : c->headcap64;
+    // 128 threads: only the lower block's values are staged (eight CTAs per SM)
+    a.stage_st = c->patch_threads <= 128 ? 0 : 1;
+    a.headcap = a.stage_st ? (sizeof(T) == 4 ? c->headcap32 : c->headcap64) : (sizeof(T) == 4 ? c->bcap32 : c->bcap64);
+    a.rows8 = c->rows8;  // Schur-coupling form: four rows per warp in the W product (else two)
     launch_patch_sc<T>(a, c->nsolve, patch_sc_smem<T>(c->maxG, c->maxN1, c->maxN2, c->patch_threads, a.headcap),
                        c->patch_threads, st);
   } else if (c->stream) {
@@ -729,14 +733,22 @@ void setup_patches(fdm_ctx *c) {
   c->smem32 = patch_smem_bytes<float>(c->g.n, c->maxG, c->maxN1, c->maxN2);
   c->patch_threads = c->opt.patch_threads > 0 ? c->opt.patch_threads : (c->maxG > 1000 ? 1024 : 256);
   if (c->scform) {  // 256 or 512 threads
-    c->patch_threads = c->opt.patch_threads > 0 ? (c->opt.patch_threads >= 512 ? 512 : 256) : (c->maxG > 1000 ? 512 : 256);
+    c->patch_threads = c->opt.patch_threads > 0 ? (c->opt.patch_threads >= 512 ? 512 : c->opt.patch_threads <= 128 ? 128 : 256)
+                                                : (c->maxG > 1000 ? 512 : 256);
     if (patch_sc_smem<double>(c->maxG, c->maxN1, c->maxN2, 512, 0) > 224 * 1024)
       fail(FDM_EINVAL, "patch interface too large for shared memory (Schur-coupling form)");
+    // two rows per warp in the W product (48 registers: five CTAs per SM), four on request
+    c->rows8 = c->opt.patch_rows_per_warp == 4 ? 1 : 0;
     // stage the values before W in shared memory where the largest class's fit in 48 KB
-    int64_t head = 0;
-    for (const PatchClass &C : c->classes) head = std::max<int64_t>(head, C.off_z);
+    int64_t head = 0, bhead = 0;
+    for (const PatchClass &C : c->classes) {
+      head = std::max<int64_t>(head, C.off_z);
+      bhead = std::max<int64_t>(bhead, C.off_st);
+    }
     c->headcap32 = head * 4 <= 48 * 1024 ? (int)head : 0;
     c->headcap64 = head * 8 <= 48 * 1024 ? (int)head : 0;
+    c->bcap32 = bhead * 4 <= 24 * 1024 ? (int)bhead : 0;
+    c->bcap64 = bhead * 8 <= 24 * 1024 ? (int)bhead : 0;
   }
   // eight rows per warp in flight pay off for long L21 rows with 256 threads (measured:
   // 10 % at Q8, neutral at Q7, slower with 1024 threads at Q15)
@@ -1058,7 +1070,7 @@ void autotune_patch(fdm_ctx *c, cudaStream_t st) {
   std::vector<Cand> cands = {{1, 256, 0}, {1, 256, 1}, {1, 512, 0}, {1, 1024, 0}};
   const bool fp32 = c->opt.precision == FDM_PREC_FP32;
   const size_t rs = fp32 ? c->rsmem32 : c->rsmem64;
-  if (c->scform) cands = {{5, 256, 0}, {5, 512, 0}};  // the factor layout fixes the kernel
+  if (c->scform) cands = {{5, 128, 0}, {5, 256, 0}, {5, 256, 1}, {5, 512, 0}};  // the layout fixes the kernel
   else if (rs <= 225 * 1024) cands.push_back({3, 512, 0});
   const int64_t n = c->g.ndof;
   fill(n, 1.0, c->r, st);

@@ -156,14 +156,14 @@ __device__ __forceinline__ V4<double> load4h(const double *p, uint64_t pol) {
 // zero g, y, x and tmp (zero-padded factor columns then multiply finite values
 // only), find the star's cells and gather the condensed FDM residual on the
 // interface (fixed cell order)
-template <typename T, int NT>
+template <typename T, int NT, int NV = 3>
 __device__ __forceinline__ void patch_gather(const PatchSolveArgs<T> &a, const PatchDev &P, const ClassDev &C, T *gv,
                                              int *sCell) {
   const int tid = threadIdx.x;
   const Grid &g = a.g;
   const int n = g.n, n3 = n * n * n;
   const int nG = C.nG;
-  for (int i = tid; i < 3 * nG + a.tmpcap; i += NT) gv[i] = T(0);
+  for (int i = tid; i < NV * nG + a.tmpcap; i += NT) gv[i] = T(0);
   if (tid < 8) {
     int s[3] = {tid & 1, (tid >> 1) & 1, tid >> 2};
     int ncl[3] = {g.nx, g.ny, g.nz};
@@ -196,7 +196,7 @@ __device__ __forceinline__ void patch_gather(const PatchSolveArgs<T> &a, const P
 // forward and backward solves with the factor values Lv of this patch (global
 // or shared memory), then the interface solution in factor order
 
-// Sums over the 32 lanes of RB values per lane (RB = 4 or 8) with a butterfly
+// Sums over the 32 lanes of RB values per lane (RB = 2, 4 or 8) with a butterfly
 // that halves the number of values per lane at each of the first log2(RB)
 // stages: 2 + 1 + 3 shuffles for RB = 4 (4 + 2 + 1 + 2 for RB = 8) instead of
 // 5 per value.  On return lane l holds the total of value index
@@ -204,7 +204,7 @@ __device__ __forceinline__ void patch_gather(const PatchSolveArgs<T> &a, const P
 // RB totals.
 template <int RB>
 __device__ __forceinline__ int rb_slot(int lane) {
-  return RB == 4 ? (lane >> 3) : (lane >> 2);
+  return lane / (32 / RB);  // RB = 2, 4 or 8
 }
 template <typename T, int RB>
 __device__ __forceinline__ void multi_warp_sum(T (&acc)[RB], int lane) {
@@ -619,47 +619,55 @@ void launch_interp_fdm(const InterpArgs<T> &a, double omega, Tout *z, cudaStream
 // the dense L21 block of the factor is not stored, and W is read once where
 // Z = L_TT^{-1} is read twice (forward and backward).
 
-// out = S_BB^{-1} in over the lower block (n0 + n1 entries); t1, z1: n1 each
+// u = S_BB^{-1} in over the lower block (n0 + n1 entries) in three phases:
+//   t_1 = g_1 - L_10 (D_0^{-1} g_0)            (y_0 = L_00^{-1} g_0 formed where used)
+//   u_1 = L_11^{-T} L_11^{-1} t_1              (a warp per line: both line solves)
+//   u_0 = L_00^{-T} (y_0 - L_10^T u_1)
+// out may alias in (each phase reads in only at indices it or an earlier phase
+// owns).  fin, when given, also receives y - u (the final lower values).
 template <typename T, int NT>
-__device__ __forceinline__ void bb_solve(const ClassDev &C, const T *Lv, const T *in, T *out, T *t1, T *z1) {
-  const int tid = threadIdx.x, n0 = C.n0, n1 = C.n1;
+__device__ __forceinline__ void bb_solve(const ClassDev &C, const T *Lv, const T *in, T *out, T *t1, T *z1,
+                                         const T *y = nullptr, T *fin = nullptr) {
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, n0 = C.n0, n1 = C.n1;
   const T *dinv0 = Lv + C.off_dinv0, *ell = Lv + C.off_ell;
-  for (int j = tid; j < n0; j += NT) out[j] = in[j] * dinv0[j];  // y_0 = L_00^{-1} g_0
-  __syncthreads();
-  for (int r = tid; r < n1; r += NT) {  // t_1 = g_1 - L_10 y_0
+  for (int r = tid; r < n1; r += NT) {
     T acc = 0;
 #pragma unroll 4
     for (int e = 0; e < C.K0; ++e) {
       const int col = C.ell_col[e * C.ldr0 + r];
-      if (col >= 0) acc += ell[e * C.ldr0 + r] * out[col];
+      if (col >= 0) acc += ell[e * C.ldr0 + r] * (in[col] * dinv0[col]);
     }
     t1[r] = in[n0 + r] - acc;
   }
   __syncthreads();
-  for (int i = tid; i < n1; i += NT) {  // z_1 = L_11^{-1} t_1, line by line
-    const int b = C.line_of[i], s0 = C.line_start[b], w = C.line_len[b];
-    const T *Li = Lv + C.off_lines + C.line_off[b] + (int64_t)(i - s0) * w;
-    T acc = 0;
-    for (int cc = 0; cc <= i - s0; ++cc) acc += Li[cc] * t1[s0 + cc];
-    z1[i] = acc;
+  for (int b = warp; b < C.nlines; b += NW) {
+    const int s0 = C.line_start[b], w = C.line_len[b];
+    const T *Lb = Lv + C.off_lines + C.line_off[b];  // w x w inverse of the line block, lower
+    for (int i = lane; i < w; i += 32) {
+      T acc = 0;
+      for (int cc = 0; cc <= i; ++cc) acc += Lb[i * w + cc] * t1[s0 + cc];
+      z1[s0 + i] = acc;
+    }
+    __syncwarp();
+    for (int i = lane; i < w; i += 32) {
+      T acc = 0;
+      for (int cc = i; cc < w; ++cc) acc += Lb[cc * w + i] * z1[s0 + cc];
+      out[n0 + s0 + i] = acc;
+      if (fin) fin[n0 + s0 + i] = y[n0 + s0 + i] - acc;
+    }
   }
   __syncthreads();
-  for (int i = tid; i < n1; i += NT) {  // x_1 = L_11^{-T} z_1
-    const int b = C.line_of[i], s0 = C.line_start[b], w = C.line_len[b];
-    const T *Lb = Lv + C.off_lines + C.line_off[b];
-    T s = 0;
-    for (int cc = i - s0; cc < w; ++cc) s += Lb[cc * w + (i - s0)] * z1[s0 + cc];
-    out[n0 + i] = s;
-  }
-  __syncthreads();
-  for (int j = tid; j < n0; j += NT) {  // x_0 = L_00^{-T} (y_0 - L_10^T x_1)
-    T s = out[j];
+  for (int j = tid; j < n0; j += NT) {
+    T s = in[j] * dinv0[j];
     const int q1 = C.cB_ptr[j + 1];
     for (int q = C.cB_ptr[j]; q < q1; ++q) {
       const int pos = C.cB_pos[q];
       s -= ell[pos] * out[n0 + pos % C.ldr0];
     }
-    out[j] = s * dinv0[j];
+    s *= dinv0[j];
+    out[j] = s;
+    if (fin) fin[j] = y[j] - s;
   }
   __syncthreads();
 }
@@ -672,9 +680,9 @@ __device__ __forceinline__ void bb_solve(const ClassDev &C, const T *Lv, const T
 // accumulator (acc, NW rows of ld, zero on entry): the lower triangle is read
 // once and every entry used twice.  The warp accumulators are summed in fixed
 // order, so the result does not depend on timing.
-template <typename T, int NT>
+template <typename T, int NT, int RB>
 __device__ __forceinline__ void sym_apply(const ClassDev &C, const T *Wv, const T *v, T *x, T *acc, int ld) {
-  constexpr int NW = NT / 32, RB = 4;
+  constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, n2 = C.n2;
   T *aw = acc + warp * ld;
   for (int r0 = warp * RB; r0 < n2; r0 += NW * RB) {
@@ -733,8 +741,8 @@ __device__ __forceinline__ void sym_apply(const ClassDev &C, const T *Wv, const 
 // (cp.async.bulk) issued before the gather when they fit in a.headcap
 // elements; the mbarrier wait is bounded by a.timeout_ns (status word on
 // expiry).  W streams from global memory.
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT) k_patch_solve_sc(PatchSolveArgs<T> a) {
+template <typename T, int NT, int SRB, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_patch_solve_sc(PatchSolveArgs<T> a) {
   extern __shared__ __align__(128) unsigned char smem_[];
   const int tid = threadIdx.x;
   const PatchDev P = a.patches[a.order[blockIdx.x]];
@@ -745,18 +753,25 @@ __global__ void __launch_bounds__(NT) k_patch_solve_sc(PatchSolveArgs<T> a) {
   T *H = reinterpret_cast<T *>(smem_);  // a.headcap elements (a multiple of 4)
   T *gv = H + a.headcap;
   const T *Lv = a.L + P.voff;
-  const bool stage = C.off_z > 0 && C.off_z <= a.headcap;
-  if (stage && tid == 0) {
-    sFail = 0;
-    bulk::mbar_init(&bar, 1);
-    bulk::fence_mbar_init();
-    const uint32_t bytes = (uint32_t)(C.off_z * (int64_t)sizeof(T));  // a multiple of 16
-    bulk::mbar_arrive_expect_tx(&bar, bytes);
-    for (uint32_t off = 0; off < bytes; off += 32768)
-      bulk::bulk_g2s(reinterpret_cast<char *>(H) + off, reinterpret_cast<const char *>(Lv) + off,
-                     bytes - off < 32768 ? bytes - off : 32768, &bar);
+  const int64_t hend = a.stage_st ? C.off_z : C.off_st;  // staged prefix (a multiple of 4 elements)
+  const bool stage = hend > 0 && hend <= a.headcap;
+  if (tid == 0) {
+    if (stage) {
+      sFail = 0;
+      bulk::mbar_init(&bar, 1);
+      bulk::fence_mbar_init();
+      const uint32_t bytes = (uint32_t)(hend * (int64_t)sizeof(T));  // a multiple of 16
+      bulk::mbar_arrive_expect_tx(&bar, bytes);
+      for (uint32_t off = 0; off < bytes; off += 32768)
+        bulk::bulk_g2s(reinterpret_cast<char *>(H) + off, reinterpret_cast<const char *>(Lv) + off,
+                       bytes - off < 32768 ? bytes - off : 32768, &bar);
+    }
+    // W into L2 while the gather and the lower solve run
+    const uint32_t wb = (uint32_t)((C.nval - C.off_z) * (int64_t)sizeof(T));
+    const char *ws = reinterpret_cast<const char *>(Lv + C.off_z);
+    for (uint32_t off = 0; off < wb; off += 32768) bulk::prefetch_l2(ws + off, wb - off < 32768 ? wb - off : 32768);
   }
-  patch_gather<T, NT>(a, P, C, gv, sCell);  // also zeroes y, x and tmp (barriers inside)
+  patch_gather<T, NT, 2>(a, P, C, gv, sCell);  // also zeroes y and tmp (barriers inside)
   const T *Lh = Lv;
   if (stage) {
     if (!bulk::mbar_wait_bounded(&bar, 0, a.timeout_ns)) sFail = 1;
@@ -769,11 +784,13 @@ __global__ void __launch_bounds__(NT) k_patch_solve_sc(PatchSolveArgs<T> a) {
     Lh = H;
   }
   const int nG = C.nG, nb = C.n0 + C.n1, n2 = C.n2, ld = C.ldT;
-  T *yv = gv + nG, *xv = yv + nG, *tmp = xv + nG;
+  // gv: g, later r_B and u_B; yv: y_B, then x_T in its top part
+  T *yv = gv + nG, *tmp = yv + nG;
   const int l1 = (C.n1 + 3) & ~3;
   T *t1 = tmp, *z1 = tmp + l1, *acc = tmp + 2 * l1;
+  T *X = a.X + P.xoff;
   bb_solve<T, NT>(C, Lh, gv, yv, t1, z1);  // y_B = S_BB^{-1} g_B
-  const T *st = Lh + C.off_st;
+  const T *st = (a.stage_st ? Lh : Lv) + C.off_st;
   for (int t = tid; t < n2; t += NT) {  // v_T = g_T - S_TB y_B, in place
     T s = 0;
     for (int e = 0; e < C.KT; ++e) {
@@ -783,22 +800,19 @@ __global__ void __launch_bounds__(NT) k_patch_solve_sc(PatchSolveArgs<T> a) {
     gv[nb + t] -= s;
   }
   __syncthreads();
-  sym_apply<T, NT>(C, Lv + C.off_z, gv + nb, xv + nb, acc, ld);  // x_T = W v_T
+  sym_apply<T, NT, SRB>(C, Lv + C.off_z, gv + nb, yv + nb, acc, ld);  // x_T = W v_T
+  for (int k = tid; k < n2; k += NT) X[nb + k] = yv[nb + k];
   for (int cc = tid; cc < nb; cc += NT) {  // r_B = S_BT x_T (g_B is no longer needed)
     T s = 0;
     const int q1 = C.ct_ptr[cc + 1];
     for (int q = C.ct_ptr[cc]; q < q1; ++q) {
       const int pos = C.ct_pos[q];
-      s += st[pos] * xv[nb + pos % ld];
+      s += st[pos] * yv[nb + pos % ld];
     }
     gv[cc] = s;
   }
   __syncthreads();
-  bb_solve<T, NT>(C, Lh, gv, xv, t1, z1);  // u_B = S_BB^{-1} r_B
-  for (int k = tid; k < nb; k += NT) xv[k] = yv[k] - xv[k];  // x_B = y_B - u_B
-  __syncthreads();
-  T *X = a.X + P.xoff;
-  for (int k = tid; k < nG; k += NT) X[k] = xv[k];
+  bb_solve<T, NT>(C, Lh, gv, gv, t1, z1, yv, X);  // u_B = S_BB^{-1} r_B in place, X_B = y_B - u_B
 }
 
 int patch_sc_tmp(int maxN1, int maxN2, int threads) {
@@ -808,7 +822,7 @@ int patch_sc_tmp(int maxN1, int maxN2, int threads) {
 
 template <typename T>
 size_t patch_sc_smem(int maxG, int maxN1, int maxN2, int threads, int headcap) {
-  return sizeof(T) * ((size_t)headcap + 3 * (size_t)maxG + patch_sc_tmp(maxN1, maxN2, threads));
+  return sizeof(T) * ((size_t)headcap + 2 * (size_t)maxG + patch_sc_tmp(maxN1, maxN2, threads));
 }
 
 template <typename T>
@@ -816,12 +830,16 @@ void launch_patch_sc(const PatchSolveArgs<T> &a, int npatch, size_t smem, int th
   if (npatch <= 0) return;
   static bool attr = false;
   if (!attr) {
-    FDM_CUDA(cudaFuncSetAttribute(k_patch_solve_sc<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024));
-    FDM_CUDA(cudaFuncSetAttribute(k_patch_solve_sc<T, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024));
+    FDM_CUDA(cudaFuncSetAttribute(k_patch_solve_sc<T, 256, 2, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024));
+    FDM_CUDA(cudaFuncSetAttribute(k_patch_solve_sc<T, 256, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024));
+    FDM_CUDA(cudaFuncSetAttribute(k_patch_solve_sc<T, 512, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024));
+    FDM_CUDA(cudaFuncSetAttribute(k_patch_solve_sc<T, 128, 2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024));
     attr = true;
   }
-  if (threads >= 512) k_patch_solve_sc<T, 512><<<npatch, 512, smem, st>>>(a);
-  else k_patch_solve_sc<T, 256><<<npatch, 256, smem, st>>>(a);
+  if (threads <= 128) k_patch_solve_sc<T, 128, 2, 8><<<npatch, 128, smem, st>>>(a);
+  else if (threads >= 512) k_patch_solve_sc<T, 512, 4, 2><<<npatch, 512, smem, st>>>(a);
+  else if (a.rows8) k_patch_solve_sc<T, 256, 4, 4><<<npatch, 256, smem, st>>>(a);
+  else k_patch_solve_sc<T, 256, 2, 5><<<npatch, 256, smem, st>>>(a);
 }
 
 int patch_tmp_elems(int maxN1, int maxN2) {

@@ -30,7 +30,9 @@ struct PatchSolveArgs {
   int l2hint;  // L2 eviction priorities: forward reads evict-last, backward reads evict-first
   int rows8;   // eight rows per warp in the forward products (else four)
   int headcap = 0;  // Schur-coupling form: elements of shared memory for the patch's values
-                    // before W (staged by one bulk copy where they fit), 0 = none
+                    // before S_TB (stage_st = 0) or before W (stage_st = 1), staged by one
+                    // bulk copy where they fit; 0 = none
+  int stage_st = 1;
 };
 int patch_tmp_elems(int maxN1, int maxN2);
 // Schur-coupling form of the patch solve (one CTA per patch, 256 or 512 threads)
