@@ -318,7 +318,7 @@ def bench_gpu(args):
     # ---- roofline of the dominant kernel (patch solve), FP32 factors: the same
     # solves through the host loop with CUDA events around every kernel group
     ctx_kt = fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP32, kernel_timing=1,
-                           patch_kernel=3 if tuning[0] == 3 else 1, patch_threads=tuning[1],
+                           patch_kernel={3: 3, 6: 5}.get(tuning[0], 1), patch_threads=tuning[1],
                            patch_rows_per_warp=8 if tuning[2] else 4)
     for _ in range(args.warmup):
         ctx_kt.pcg_solve(b, x, rtol=RTOL, maxit=MAXIT)
@@ -405,7 +405,8 @@ def bench_gpu(args):
                            "iterations": int(np.median(iters)), "true_rel_residual": rel,
                            "setup_seconds": sum(setup_s),
                            "pcg_loop": "host" if args.pcg_host_loop else "device (CUDA graph)",
-                           "autotuned_patch_solve": {"kernel": {3: "resident", 5: "one CTA per patch, Schur-coupling form"}.get(
+                           "autotuned_patch_solve": {"kernel": {3: "resident", 5: "one CTA per patch, Schur-coupling form",
+                                                                6: "persistent, Schur-coupling form"}.get(
                                                          tuning[0], "one CTA per patch"),
                                                      "threads": tuning[1], "rows_per_warp": 8 if tuning[2] else 4,
                                                      "sweep_us": tuning[3], "candidates": tuning[4]}},
@@ -413,7 +414,8 @@ def bench_gpu(args):
                 "e2e": {"value": e2e_value, "unit": "DoF/s", "h2d_bytes_per_step": 8 * ctx.ndof,
                         "d2h_bytes_per_step": 8 * ctx.ndof},
                 "gpu_launches": int(launches),
-                "roofline": {"kernel": {3: "k_patch_resident<float>", 5: "k_patch_solve_sc<float>"}.get(
+                "roofline": {"kernel": {3: "k_patch_resident<float>", 5: "k_patch_solve_sc<float>",
+                                        6: "k_patch_solve_scp<float>"}.get(
                                  tuning[0], "k_patch_solve<float>"),
                              "bound": "hbm", "achieved": achieved, "peak": peak,
                              "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,

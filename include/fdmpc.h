@@ -105,7 +105,9 @@ typedef struct {
                          3 = resident: persistent CTAs that bulk-copy each patch's whole factor
                          into shared memory (falls back to 1 where it does not fit), 4 = cluster:
                          the interior stars on thread-block clusters that hold L21 in shared
-                         memory across both solves, the other stars as 1 */
+                         memory across both solves, the other stars as 1; 5 = persistent CTAs in
+                         the Schur-coupling form that stage the next patch's lower-block values in
+                         shared memory and its S_TB and W in L2 while solving the current one */
   int stream_buffers; /* ring buffers of the streamed solve (0 = 4) */
   int stream_buffer_kb; /* size of each ring buffer in KiB (0 = 16) */
   int inject_stall;   /* test hook: the streamed solve waits on a barrier that is never
@@ -134,8 +136,8 @@ typedef struct {
                          2 = Schur-coupling form (y_B = S_BB^{-1} g_B, x_T = W (g_T - S_TB y_B),
                          x_B = y_B - S_BB^{-1} S_BT x_T with B = levels 0 and 1, T = the top
                          level, S_TB in S_G's own sparsity and W = (L_TT L_TT^T)^{-1}: no dense
-                         L21, W read once), one CTA per patch only; 0 (default) = 2 for
-                         patch_kernel 0 or 1, else 1 */
+                         L21, W read once), patch_kernel 0, 1 or 5 only; 0 (default) = 2 for
+                         patch_kernel 0, 1 or 5, else 1 */
   int coarse_levels;  /* solve of the Q1 coarse problem (Section 3): 0 = exact (dense inverse
                          from a banded Cholesky factor); k > 0 = one geometric multigrid V-cycle
                          with at most k coarsenings (every other vertex per axis while all cell

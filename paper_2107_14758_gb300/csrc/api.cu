@@ -68,6 +68,7 @@ struct fdm_ctx {
   bool scform = false;  // Schur-coupling form of the patch factors and solve
   int headcap32 = 0, headcap64 = 0;  // its staged values before W, per precision (elements)
   int bcap32 = 0, bcap64 = 0;        // the same before S_TB (lower block only)
+  bool sc_persist = false;           // persistent Schur-coupling kernel (patch_kernel = 5)
   // cluster patch solve for the classes with a dense top level (a prefix of the order)
   int n_heavy = 0, cl_threads = 256;
   bool cl32 = false, cl64 = false;
@@ -285,12 +286,19 @@ void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st, c
     PatchSolveArgs<T> a{c->g, c->d_cls, c->d_patches, c->d_order, c->E<T>(), c->mu, c->tab<T>(), c->L<T>(),
                         c->X<T>(), patch_sc_tmp(c->maxN1, c->maxN2, c->patch_threads), 0,
                         (uint64_t)(std::max(c->opt.wait_timeout_s, 0.0) * 1e9), c->status, 0, 0, 0};
-    // 128 threads: only the lower block's values are staged (eight CTAs per SM)
-    a.stage_st = c->patch_threads <= 128 ? 0 : 1;
-    a.headcap = a.stage_st ? (sizeof(T) == 4 ? c->headcap32 : c->headcap64) : (sizeof(T) == 4 ? c->bcap32 : c->bcap64);
     a.rows8 = c->rows8;  // Schur-coupling form: four rows per warp in the W product (else two)
-    launch_patch_sc<T>(a, c->nsolve, patch_sc_smem<T>(c->maxG, c->maxN1, c->maxN2, c->patch_threads, a.headcap),
-                       c->patch_threads, st);
+    if (c->sc_persist) {  // persistent (256 threads): two buffers for the lower block's values, S_TB and W via L2
+      a.stage_st = 0;
+      a.tmpcap = patch_sc_tmp(c->maxN1, c->maxN2, 256);  // the scratch the kernel zeroes, sized for its threads
+      a.headcap = sizeof(T) == 4 ? c->bcap32 : c->bcap64;
+      launch_patch_scp<T>(a, c->nsolve, patch_sc_smem<T>(c->maxG, c->maxN1, c->maxN2, 256, 2 * a.headcap), st);
+    } else {
+      // 128 threads: only the lower block's values are staged (eight CTAs per SM)
+      a.stage_st = c->patch_threads <= 128 ? 0 : 1;
+      a.headcap = a.stage_st ? (sizeof(T) == 4 ? c->headcap32 : c->headcap64) : (sizeof(T) == 4 ? c->bcap32 : c->bcap64);
+      launch_patch_sc<T>(a, c->nsolve, patch_sc_smem<T>(c->maxG, c->maxN1, c->maxN2, c->patch_threads, a.headcap),
+                         c->patch_threads, st);
+    }
   } else if (c->stream) {
     if (launch_patch_stream<T>(stream_args<T>(c), c->patch_threads, st) != 0)
       fail(FDM_ECUDA, "streamed patch solve: launch configuration rejected");
@@ -605,9 +613,12 @@ void setup_patches(fdm_ctx *c) {
   const int p = c->p;
   // factor form: the Schur-coupling form serves the one-CTA-per-patch solve;
   // the streamed, resident and cluster kernels read the L form
-  const bool l_kernel = c->opt.patch_kernel >= 2;
-  if (c->opt.patch_form == 2 && l_kernel) fail(FDM_EINVAL, "patch_form 2 needs patch_kernel 0 or 1");
+  const bool l_kernel = c->opt.patch_kernel >= 2 && c->opt.patch_kernel <= 4;
+  if (c->opt.patch_form == 2 && l_kernel) fail(FDM_EINVAL, "patch_form 2 needs patch_kernel 0, 1 or 5");
+  if (c->opt.patch_form == 1 && c->opt.patch_kernel == 5) fail(FDM_EINVAL, "patch_kernel 5 needs the Schur-coupling form");
+  if (c->opt.patch_kernel < 0 || c->opt.patch_kernel > 5) fail(FDM_EINVAL, "patch_kernel out of range");
   c->scform = c->opt.patch_form == 2 || (c->opt.patch_form == 0 && !l_kernel);
+  c->sc_persist = c->scform && c->opt.patch_kernel == 5;
   c->classes = build_classes(p, c->scform);
   c->nbuf = c->opt.stream_buffers > 0 ? c->opt.stream_buffers : 4;
   c->buf_bytes = 1024 * (c->opt.stream_buffer_kb > 0 ? c->opt.stream_buffer_kb : 16);
@@ -1070,7 +1081,7 @@ void autotune_patch(fdm_ctx *c, cudaStream_t st) {
   std::vector<Cand> cands = {{1, 256, 0}, {1, 256, 1}, {1, 512, 0}, {1, 1024, 0}};
   const bool fp32 = c->opt.precision == FDM_PREC_FP32;
   const size_t rs = fp32 ? c->rsmem32 : c->rsmem64;
-  if (c->scform) cands = {{5, 128, 0}, {5, 256, 0}, {5, 256, 1}, {5, 512, 0}};  // the layout fixes the kernel
+  if (c->scform) cands = {{5, 128, 0}, {5, 256, 0}, {5, 256, 1}, {5, 512, 0}, {6, 256, 0}};  // layout fixes the kernel
   else if (rs <= 225 * 1024) cands.push_back({3, 512, 0});
   const int64_t n = c->g.ndof;
   fill(n, 1.0, c->r, st);
@@ -1088,6 +1099,7 @@ void autotune_patch(fdm_ctx *c, cudaStream_t st) {
     c->res32 = fp32 && k.kernel == 3;
     c->res64 = !fp32 && k.kernel == 3;
     c->res_threads = k.threads;
+    c->sc_persist = k.kernel == 6;
     auto sweep = [&]() {
       if (fp32) run_asm<float, double, double>(c, c->r, c->z, c->omega, st);
       else run_asm<double, double, double>(c, c->r, c->z, c->omega, st);
@@ -1113,6 +1125,7 @@ void autotune_patch(fdm_ctx *c, cudaStream_t st) {
   c->res32 = fp32 && pick.kernel == 3;
   c->res64 = !fp32 && pick.kernel == 3;
   c->res_threads = pick.kernel == 3 ? pick.threads : rthreads;
+  c->sc_persist = pick.kernel == 6;
   c->tuning[0] = pick.kernel;
   c->tuning[1] = pick.threads;
   c->tuning[2] = pick.rows8;

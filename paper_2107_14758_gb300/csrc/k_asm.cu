@@ -741,6 +741,44 @@ __device__ __forceinline__ void sym_apply(const ClassDev &C, const T *Wv, const 
 // (cp.async.bulk) issued before the gather when they fit in a.headcap
 // elements; the mbarrier wait is bounded by a.timeout_ns (status word on
 // expiry).  W streams from global memory.
+// everything after the gather: Lh holds the values before S_TB (staged or
+// global), S_TB from Lh when stage_st else from global, W from global
+template <typename T, int NT, int SRB>
+__device__ __forceinline__ void sc_patch_compute(const PatchSolveArgs<T> &a, const PatchDev &P, const ClassDev &C,
+                                                 const T *Lh, const T *Lv, T *gv, bool stage_st) {
+  const int tid = threadIdx.x;
+  const int nG = C.nG, nb = C.n0 + C.n1, n2 = C.n2, ld = C.ldT;
+  // gv: g, later r_B and u_B; yv: y_B, then x_T in its top part
+  T *yv = gv + nG, *tmp = yv + nG;
+  const int l1 = (C.n1 + 3) & ~3;
+  T *t1 = tmp, *z1 = tmp + l1, *acc = tmp + 2 * l1;
+  T *X = a.X + P.xoff;
+  bb_solve<T, NT>(C, Lh, gv, yv, t1, z1);  // y_B = S_BB^{-1} g_B
+  const T *st = (stage_st ? Lh : Lv) + C.off_st;
+  for (int t = tid; t < n2; t += NT) {  // v_T = g_T - S_TB y_B, in place
+    T s = 0;
+    for (int e = 0; e < C.KT; ++e) {
+      const int col = C.st_col[e * ld + t];
+      if (col >= 0) s += st[e * ld + t] * yv[col];
+    }
+    gv[nb + t] -= s;
+  }
+  __syncthreads();
+  sym_apply<T, NT, SRB>(C, Lv + C.off_z, gv + nb, yv + nb, acc, ld);  // x_T = W v_T
+  for (int k = tid; k < n2; k += NT) X[nb + k] = yv[nb + k];
+  for (int cc = tid; cc < nb; cc += NT) {  // r_B = S_BT x_T (g_B is no longer needed)
+    T s = 0;
+    const int q1 = C.ct_ptr[cc + 1];
+    for (int q = C.ct_ptr[cc]; q < q1; ++q) {
+      const int pos = C.ct_pos[q];
+      s += st[pos] * yv[nb + pos % ld];
+    }
+    gv[cc] = s;
+  }
+  __syncthreads();
+  bb_solve<T, NT>(C, Lh, gv, gv, t1, z1, yv, X);  // u_B = S_BB^{-1} r_B in place, X_B = y_B - u_B
+}
+
 template <typename T, int NT, int SRB, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_patch_solve_sc(PatchSolveArgs<T> a) {
   extern __shared__ __align__(128) unsigned char smem_[];
@@ -783,36 +821,78 @@ __global__ void __launch_bounds__(NT, MINB) k_patch_solve_sc(PatchSolveArgs<T> a
     }
     Lh = H;
   }
-  const int nG = C.nG, nb = C.n0 + C.n1, n2 = C.n2, ld = C.ldT;
-  // gv: g, later r_B and u_B; yv: y_B, then x_T in its top part
-  T *yv = gv + nG, *tmp = yv + nG;
-  const int l1 = (C.n1 + 3) & ~3;
-  T *t1 = tmp, *z1 = tmp + l1, *acc = tmp + 2 * l1;
-  T *X = a.X + P.xoff;
-  bb_solve<T, NT>(C, Lh, gv, yv, t1, z1);  // y_B = S_BB^{-1} g_B
-  const T *st = (a.stage_st ? Lh : Lv) + C.off_st;
-  for (int t = tid; t < n2; t += NT) {  // v_T = g_T - S_TB y_B, in place
-    T s = 0;
-    for (int e = 0; e < C.KT; ++e) {
-      const int col = C.st_col[e * ld + t];
-      if (col >= 0) s += st[e * ld + t] * yv[col];
+  sc_patch_compute<T, NT, SRB>(a, P, C, Lh, Lv, gv, a.stage_st != 0);
+}
+
+// Persistent variant: each CTA walks the patch order with a stride of the
+// grid.  While it solves one patch, the next one's lower-block values (before
+// S_TB) are bulk-copied into the other of two shared-memory buffers and its
+// S_TB and W are prefetched into L2, so that every phase of the next solve
+// reads on-chip memory or L2.  Each buffer has its own mbarrier (one phase per
+// copy); every wait is bounded by a.timeout_ns, after which the CTA waits once
+// more (bounded) for its copies in flight, sets the status word and returns.
+template <typename T, int NT, int SRB, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_patch_solve_scp(PatchSolveArgs<T> a, int npatch) {
+  extern __shared__ __align__(128) unsigned char smem_[];
+  const int tid = threadIdx.x;
+  __shared__ int sCell[8];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int sFail, sPend[2];
+  T *const H0 = reinterpret_cast<T *>(smem_);  // two buffers of a.headcap elements (multiples of 4)
+  T *const H1 = H0 + a.headcap;
+  T *gv = H1 + a.headcap;
+  auto issue = [&](int it, int b) {  // thread 0: stage patch `it` into buffer b, S_TB and W into L2
+    const PatchDev Q = a.patches[a.order[it]];
+    const ClassDev &D = a.cls[Q.cls];
+    const T *Lq = a.L + Q.voff;
+    sPend[b] = 0;
+    if (D.off_st > 0 && D.off_st <= a.headcap) {
+      bulk::fence_proxy_async();  // the buffer's previous contents were read by every thread
+      const uint32_t bytes = (uint32_t)(D.off_st * (int64_t)sizeof(T));  // a multiple of 16
+      char *dst = reinterpret_cast<char *>(b ? H1 : H0);
+      bulk::mbar_arrive_expect_tx(&bar[b], bytes);
+      for (uint32_t off = 0; off < bytes; off += 32768)
+        bulk::bulk_g2s(dst + off, reinterpret_cast<const char *>(Lq) + off, bytes - off < 32768 ? bytes - off : 32768,
+                       &bar[b]);
+      sPend[b] = 1;
     }
-    gv[nb + t] -= s;
+    const uint32_t wb = (uint32_t)((D.nval - D.off_st) * (int64_t)sizeof(T));
+    const char *ws = reinterpret_cast<const char *>(Lq + D.off_st);
+    for (uint32_t off = 0; off < wb; off += 32768) bulk::prefetch_l2(ws + off, wb - off < 32768 ? wb - off : 32768);
+  };
+  if (tid == 0) {
+    bulk::mbar_init(&bar[0], 1);
+    bulk::mbar_init(&bar[1], 1);
+    bulk::fence_mbar_init();
+    sFail = 0;
+    sPend[0] = sPend[1] = 0;
+    if ((int)blockIdx.x < npatch) issue(blockIdx.x, 0);
   }
   __syncthreads();
-  sym_apply<T, NT, SRB>(C, Lv + C.off_z, gv + nb, yv + nb, acc, ld);  // x_T = W v_T
-  for (int k = tid; k < n2; k += NT) X[nb + k] = yv[nb + k];
-  for (int cc = tid; cc < nb; cc += NT) {  // r_B = S_BT x_T (g_B is no longer needed)
-    T s = 0;
-    const int q1 = C.ct_ptr[cc + 1];
-    for (int q = C.ct_ptr[cc]; q < q1; ++q) {
-      const int pos = C.ct_pos[q];
-      s += st[pos] * yv[nb + pos % ld];
+  uint32_t par[2] = {0, 0};
+  int b = 0;
+  for (int it = blockIdx.x; it < npatch; it += gridDim.x, b ^= 1) {
+    const PatchDev P = a.patches[a.order[it]];
+    const ClassDev &C = a.cls[P.cls];
+    if (tid == 0 && it + (int)gridDim.x < npatch) issue(it + gridDim.x, b ^ 1);
+    patch_gather<T, NT, 2>(a, P, C, gv, sCell);  // also zeroes y and tmp (barriers inside)
+    const T *Lv = a.L + P.voff;
+    const T *Lh = Lv;
+    if (sPend[b]) {
+      if (!bulk::mbar_wait_bounded(&bar[b], par[b], a.timeout_ns)) sFail = 1;
+      __syncthreads();
+      if (sFail) {
+        for (int q = 0; q < 2; ++q)  // a second bounded wait for every copy in flight
+          if (sPend[q]) bulk::mbar_wait_bounded(&bar[q], par[q], a.timeout_ns);
+        if (tid == 0) atomicExch(a.status, 1);
+        return;
+      }
+      par[b] ^= 1u;
+      Lh = b ? H1 : H0;
     }
-    gv[cc] = s;
+    sc_patch_compute<T, NT, SRB>(a, P, C, Lh, Lv, gv, false);
+    __syncthreads();  // buffer b and gv are free for the next patch
   }
-  __syncthreads();
-  bb_solve<T, NT>(C, Lh, gv, gv, t1, z1, yv, X);  // u_B = S_BB^{-1} r_B in place, X_B = y_B - u_B
 }
 
 int patch_sc_tmp(int maxN1, int maxN2, int threads) {
@@ -823,6 +903,24 @@ int patch_sc_tmp(int maxN1, int maxN2, int threads) {
 template <typename T>
 size_t patch_sc_smem(int maxG, int maxN1, int maxN2, int threads, int headcap) {
   return sizeof(T) * ((size_t)headcap + 2 * (size_t)maxG + patch_sc_tmp(maxN1, maxN2, threads));
+}
+
+template <typename T>
+void launch_patch_scp(const PatchSolveArgs<T> &a, int npatch, size_t smem, cudaStream_t st) {
+  if (npatch <= 0) return;
+  static size_t attr = 0;
+  static int per_sm = 0, nsm = 0;
+  if (attr < smem) {
+    FDM_CUDA(cudaFuncSetAttribute(k_patch_solve_scp<T, 256, 2, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    FDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_patch_solve_scp<T, 256, 2, 5>, 256, smem));
+    int dev = 0;
+    FDM_CUDA(cudaGetDevice(&dev));
+    FDM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    attr = smem;
+  }
+  const int grid = std::max(1, std::min(npatch, std::max(per_sm, 1) * nsm));
+  k_patch_solve_scp<T, 256, 2, 5><<<grid, 256, smem, st>>>(a, npatch);
 }
 
 template <typename T>
@@ -939,7 +1037,8 @@ void launch_patch_solve(const PatchSolveArgs<T> &a, int npatch, size_t smem, int
   template void launch_patch_resident<T>(const PatchSolveArgs<T> &, int, int, size_t, int, cudaStream_t);  \
   template size_t patch_smem_for_occupancy<T>(size_t, int);                                                 \
   template size_t patch_sc_smem<T>(int, int, int, int, int);                                                \
-  template void launch_patch_sc<T>(const PatchSolveArgs<T> &, int, size_t, int, cudaStream_t);
+  template void launch_patch_sc<T>(const PatchSolveArgs<T> &, int, size_t, int, cudaStream_t);             \
+  template void launch_patch_scp<T>(const PatchSolveArgs<T> &, int, size_t, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -41,6 +41,9 @@ template <typename T>
 size_t patch_sc_smem(int maxG, int maxN1, int maxN2, int threads, int headcap);
 template <typename T>
 void launch_patch_sc(const PatchSolveArgs<T> &a, int npatch, size_t smem, int threads, cudaStream_t st);
+// persistent variant (256 threads): headcap = elements of each of its two staging buffers
+template <typename T>
+void launch_patch_scp(const PatchSolveArgs<T> &a, int npatch, size_t smem, cudaStream_t st);
 // the resident variant: fcap factor elements per CTA in shared memory (one
 // patch's values), tmp sized for `threads`
 int patch_resident_tmp(int maxN1, int maxN2, int threads);

@@ -335,7 +335,7 @@ def test_full_size_sampled(name):
 
 
 # ---------------------------------------------------------------- kernels and failure detection
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5])
 def test_both_patch_kernels_agree(kernel):
     """The classic (one CTA per patch), streamed (bulk copies into a
     shared-memory ring) and resident (whole factor in shared memory) patch
@@ -406,7 +406,7 @@ def test_autotuned_context_matches(p, precision):
     a = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7)
     b = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7, autotune=1)
     kernel, threads, rows8, us, ncand = b.tuning()
-    assert kernel == 5 and threads in (128, 256, 512) and us > 0 and ncand == 4   # Schur-coupling form (default)
+    assert kernel in (5, 6) and threads in (128, 256, 512) and us > 0 and ncand == 5   # Schur-coupling form (default)
     c = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7, autotune=1, patch_form=1)
     kernel, threads, rows8, us, ncand = c.tuning()
     assert kernel in (1, 3) and threads in (256, 512, 1024) and rows8 in (0, 1) and us > 0 and ncand >= 4
@@ -494,3 +494,19 @@ def test_sc_variants_agree(rows):
             assert relerr(N(ctx.asm_apply(T(r))), ref.asm_apply(r)) <= 1e-11
             assert ctx.status() == 0
             ctx.close()
+
+
+@pytest.mark.parametrize("p,precision", [(3, FP64), (7, FP64), (7, FP32), (15, FP32)])
+def test_persistent_sc_matches(p, precision):
+    """The persistent Schur-coupling kernel (double-buffered staging, a CTA
+    walking many patches) gives the one-CTA-per-patch kernel's relaxation to
+    rounding, and reports no expired wait."""
+    xv, yv, zv = inputs.graded_vertices(2 if p >= 11 else 3, 14)
+    r = T(np.random.default_rng(63).standard_normal(((len(xv) - 1) * p + 1) ** 3))
+    out = []
+    for kernel in (1, 5):
+        ctx = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7, patch_kernel=kernel)
+        out.append(N(ctx.asm_apply(r)))
+        assert ctx.status() == 0
+        ctx.close()
+    assert relerr(out[1], out[0]) <= (1e-12 if precision == FP64 else 1e-5)
