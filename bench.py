@@ -420,6 +420,10 @@ def bench_gpu(args):
                              "bound": "hbm", "achieved": achieved, "peak": peak,
                              "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                              "algorithmic_bytes_per_launch": ab["patch32"], "avg_launch_ms": patch_ms,
+                             # the same launch time against the bytes the L form of the patch solve
+                             # would have to move (the dense L21 block and Z): what the form change bought
+                             "l_form_bytes_per_launch": ab["lform32"],
+                             "l_form_equivalent_frac": ab["lform32"] / (patch_ms * 1e-3) / 1e9 / peak,
                              "launches": pcount},
                 "kernel_ms_per_step": {k: v[1] / args.steps for k, v in kt.items()},
                 "kernel_timed_solve_ms": ms_kt,

@@ -350,6 +350,8 @@ void fdm_elast_destroy(fdm_elast *e);
                                   level, coefficient-major [27][nf] with offset
                                   k = (dx+1) + 3 (dy+1) + 9 (dz+1) (unknowns lexicographic in
                                   the free vertices, x fastest) */
+#define FDM_Q_ALGO_BYTES_LFORM 27 /* double[2]: FDM_Q_ALGO_BYTES' patch-solve bytes (FP64, FP32) of the L
+                                     form, whichever form the context uses */
 /* timers of FDM_Q_KERNEL_TIMES */
 #define FDM_T_RESTRICT 0  /* basis change to the FDM basis */
 #define FDM_T_PATCH 1     /* patch gather + condense + triangular solves + back-substitution */

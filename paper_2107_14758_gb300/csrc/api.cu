@@ -2296,6 +2296,17 @@ int fdm_query(fdm_ctx *c, int what, void *out, size_t *len) {
         put(v, sizeof v);
         break;
       }
+      case FDM_Q_ALGO_BYTES_LFORM: {  // the same count for the L form (whichever form is in use)
+        double nnz = 0.0, nd = 0.0;
+        for (int i = 0; i < c->npatch; ++i) {
+          nnz += (double)c->classes[c->h_patches[i].cls].nnzL;
+          nd += (double)c->classes[c->h_patches[i].cls].nd;
+        }
+        const double ne = (double)c->g.ncell * c->g.n * c->g.n * c->g.n;
+        double v[2] = {8.0 * (nnz + ne + nd), 4.0 * (nnz + ne + nd)};
+        put(v, sizeof v);
+        break;
+      }
       default: fail(FDM_EINVAL, "fdm_query: unknown quantity");
     }
   } catch (const Error &e) { return handle(c, e); }

@@ -23,7 +23,7 @@ FDM_SURR_AVERAGED, FDM_SURR_EXTERNAL = 0, 1
  FDM_Q_GAMMA_ORDER, FDM_Q_FACTOR_NNZ, FDM_Q_PATTERN, FDM_Q_FACTOR, FDM_Q_BASIS, FDM_Q_FACTOR_BYTES,
  FDM_Q_SETUP_SECONDS, FDM_Q_KERNEL_TIMES, FDM_Q_LAUNCHES, FDM_Q_ALGO_BYTES, FDM_Q_STATUS,
  FDM_Q_SURR_FEATURES, FDM_Q_SURR_LABELS, FDM_Q_SURR_BOUNDS, FDM_Q_MUBAR, FDM_Q_SURR_OUTPUT, FDM_Q_TUNING,
- FDM_Q_GMG_LEVELS, FDM_Q_GMG_STENCIL) = range(1, 27)
+ FDM_Q_GMG_LEVELS, FDM_Q_GMG_STENCIL, FDM_Q_ALGO_BYTES_LFORM) = range(1, 28)
 FDM_MLP_NPARAM = 16515
 TIMERS = ("restrict", "patch", "interp", "op64", "op32", "coarse", "vec")
 
@@ -500,7 +500,8 @@ class Context:
 
     def algo_bytes(self):
         v = self.query(FDM_Q_ALGO_BYTES, np.float64, 4)
-        return dict(patch64=v[0], patch32=v[1], asm64=v[2], asm32=v[3])
+        lf = self.query(FDM_Q_ALGO_BYTES_LFORM, np.float64, 2)
+        return dict(patch64=v[0], patch32=v[1], asm64=v[2], asm32=v[3], lform64=lf[0], lform32=lf[1])
 
     def setup_seconds(self):
         return self.query(FDM_Q_SETUP_SECONDS, np.float64, 4)

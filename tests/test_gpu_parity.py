@@ -458,14 +458,16 @@ def test_patch_forms_agree(p, precision):
     form stores fewer values (no dense L21, W in place of Z)."""
     xv, yv, zv = inputs.graded_vertices(2 if p >= 11 else 3, 12)
     r = T(np.random.default_rng(61).standard_normal(((len(xv) - 1) * p + 1) ** 3))
-    out, ab = [], []
+    out, ab, lf = [], [], []
     for form in (1, 2):
         ctx = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7, patch_form=form)
         out.append(N(ctx.asm_apply(r)))
         ab.append(ctx.algo_bytes()["patch64"])
+        lf.append(ctx.algo_bytes()["lform64"])
         assert ctx.status() == 0
         ctx.close()
     assert relerr(out[1], out[0]) <= (1e-12 if precision == FP64 else 2e-5)
+    assert lf[0] == lf[1] == ab[0]   # the L-form count does not depend on the form in use
     if p >= 7:
         assert ab[1] < 0.6 * ab[0]
     elif p >= 3:
