@@ -319,7 +319,7 @@ def bench_gpu(args):
     # solves through the host loop with CUDA events around every kernel group
     ctx_kt = fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP32, kernel_timing=1,
                            patch_kernel={3: 3, 6: 5}.get(tuning[0], 1), patch_threads=tuning[1],
-                           patch_rows_per_warp=8 if tuning[2] else 4)
+                           patch_rows_per_warp=8 if tuning[2] else 4, sc_variant=tuning[2] + 1)
     for _ in range(args.warmup):
         ctx_kt.pcg_solve(b, x, rtol=RTOL, maxit=MAXIT)
     ctx_kt.kernel_times()
@@ -408,7 +408,7 @@ def bench_gpu(args):
                            "autotuned_patch_solve": {"kernel": {3: "resident", 5: "one CTA per patch, Schur-coupling form",
                                                                 6: "persistent, Schur-coupling form"}.get(
                                                          tuning[0], "one CTA per patch"),
-                                                     "threads": tuning[1], "rows_per_warp": 8 if tuning[2] else 4,
+                                                     "threads": tuning[1], "variant": tuning[2],
                                                      "sweep_us": tuning[3], "candidates": tuning[4]}},
                 "clocks": clocks,
                 "e2e": {"value": e2e_value, "unit": "DoF/s", "h2d_bytes_per_step": 8 * ctx.ndof,

@@ -129,8 +129,7 @@ typedef struct {
                          tuned differently agree to rounding, not bit for bit */
   int patch_rows_per_warp; /* rows a warp keeps in flight in the forward products of the
                               one-CTA-per-patch solve: 4 or 8 (0 = 8 for 256 threads and L21
-                              rows of 200 or more, else 4); in the Schur-coupling form, the
-                              rows of W per warp: 4 (64 registers) or otherwise 2 (48) */
+                              rows of 200 or more, else 4); L form only */
   int patch_form;     /* layout of the patch factors: 1 = L form (the Cholesky factor L_G:
                          diagonal level 0, sparse L10/L20, line blocks, dense L21, Z = L_TT^{-1});
                          2 = Schur-coupling form (y_B = S_BB^{-1} g_B, x_T = W (g_T - S_TB y_B),
@@ -148,6 +147,10 @@ typedef struct {
                          the mesh allows */
   int gmg_nu;         /* Jacobi sweeps before and after the coarse-grid correction (<= 0: 2) */
   double gmg_omega;   /* Jacobi damping (<= 0: 2/3) */
+  int sc_variant;     /* Schur-coupling one-CTA-per-patch solve with 256 threads: 1 (0 = default) =
+                         two rows of W per warp, lower-block values and S_TB staged in shared
+                         memory (five CTAs per SM); 2 = four rows of W per warp (four CTAs per SM);
+                         3 = two rows, only the lower-block values staged (six CTAs per SM) */
 } fdm_options;
 
 /* Fills the defaults listed above. */

@@ -293,8 +293,9 @@ void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st, c
       a.headcap = sizeof(T) == 4 ? c->bcap32 : c->bcap64;
       launch_patch_scp<T>(a, c->nsolve, patch_sc_smem<T>(c->maxG, c->maxN1, c->maxN2, 256, 2 * a.headcap), st);
     } else {
-      // 128 threads: only the lower block's values are staged (eight CTAs per SM)
-      a.stage_st = c->patch_threads <= 128 ? 0 : 1;
+      // 128 threads, or 256 with rows8 = 2: only the lower block's values are staged (eight or
+      // six CTAs per SM)
+      a.stage_st = (c->patch_threads <= 128 || c->rows8 == 2) ? 0 : 1;
       a.headcap = a.stage_st ? (sizeof(T) == 4 ? c->headcap32 : c->headcap64) : (sizeof(T) == 4 ? c->bcap32 : c->bcap64);
       launch_patch_sc<T>(a, c->nsolve, patch_sc_smem<T>(c->maxG, c->maxN1, c->maxN2, c->patch_threads, a.headcap),
                          c->patch_threads, st);
@@ -748,8 +749,10 @@ void setup_patches(fdm_ctx *c) {
                                                 : (c->maxG > 1000 ? 512 : 256);
     if (patch_sc_smem<double>(c->maxG, c->maxN1, c->maxN2, 512, 0) > 224 * 1024)
       fail(FDM_EINVAL, "patch interface too large for shared memory (Schur-coupling form)");
-    // two rows per warp in the W product (48 registers: five CTAs per SM), four on request
-    c->rows8 = c->opt.patch_rows_per_warp == 4 ? 1 : 0;
+    // the variant of the 256-thread kernel (rows8 holds its code): 0 = two rows of W per warp,
+    // all values before W staged; 1 = four rows; 2 = two rows, lower block staged only
+    if (c->opt.sc_variant < 0 || c->opt.sc_variant > 3) fail(FDM_EINVAL, "sc_variant out of range");
+    c->rows8 = c->opt.sc_variant > 0 ? c->opt.sc_variant - 1 : 0;
     // stage the values before W in shared memory where the largest class's fit in 48 KB
     int64_t head = 0, bhead = 0;
     for (const PatchClass &C : c->classes) {
@@ -1081,7 +1084,8 @@ void autotune_patch(fdm_ctx *c, cudaStream_t st) {
   std::vector<Cand> cands = {{1, 256, 0}, {1, 256, 1}, {1, 512, 0}, {1, 1024, 0}};
   const bool fp32 = c->opt.precision == FDM_PREC_FP32;
   const size_t rs = fp32 ? c->rsmem32 : c->rsmem64;
-  if (c->scform) cands = {{5, 128, 0}, {5, 256, 0}, {5, 256, 1}, {5, 512, 0}, {6, 256, 0}};  // layout fixes the kernel
+  if (c->scform)  // the layout fixes the kernel
+    cands = {{5, 128, 0}, {5, 256, 0}, {5, 256, 1}, {5, 256, 2}, {5, 512, 0}, {6, 256, 0}};
   else if (rs <= 225 * 1024) cands.push_back({3, 512, 0});
   const int64_t n = c->g.ndof;
   fill(n, 1.0, c->r, st);

@@ -932,9 +932,11 @@ void launch_patch_sc(const PatchSolveArgs<T> &a, int npatch, size_t smem, int th
     FDM_CUDA(cudaFuncSetAttribute(k_patch_solve_sc<T, 256, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024));
     FDM_CUDA(cudaFuncSetAttribute(k_patch_solve_sc<T, 512, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024));
     FDM_CUDA(cudaFuncSetAttribute(k_patch_solve_sc<T, 128, 2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024));
+    FDM_CUDA(cudaFuncSetAttribute(k_patch_solve_sc<T, 256, 2, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024));
     attr = true;
   }
   if (threads <= 128) k_patch_solve_sc<T, 128, 2, 8><<<npatch, 128, smem, st>>>(a);
+  else if (threads == 256 && !a.stage_st) k_patch_solve_sc<T, 256, 2, 6><<<npatch, 256, smem, st>>>(a);
   else if (threads >= 512) k_patch_solve_sc<T, 512, 4, 2><<<npatch, 512, smem, st>>>(a);
   else if (a.rows8) k_patch_solve_sc<T, 256, 4, 4><<<npatch, 256, smem, st>>>(a);
   else k_patch_solve_sc<T, 256, 2, 5><<<npatch, 256, smem, st>>>(a);

@@ -48,7 +48,7 @@ class fdm_options(C.Structure):
                 ("inject_stall", C.c_int), ("patch_prefetch", C.c_int), ("pcg_graph", C.c_int),
                 ("patch_l2_hints", C.c_int), ("autotune", C.c_int), ("patch_rows_per_warp", C.c_int),
                 ("patch_form", C.c_int), ("coarse_levels", C.c_int), ("gmg_nu", C.c_int),
-                ("gmg_omega", C.c_double)]
+                ("gmg_omega", C.c_double), ("sc_variant", C.c_int)]
 
 
 class fdm_solve_info(C.Structure):
@@ -312,7 +312,7 @@ class Context:
                  omega=0.0, lanczos_start=None, lanczos_steps=20, flexible_beta=-1, kernel_timing=0,
                  patch_ctas_per_sm=0, patch_threads=0, patch_kernel=0, stream_buffers=0, stream_buffer_kb=0,
                  inject_stall=0, wait_timeout_s=1.0, patch_prefetch=0, pcg_graph=1, patch_l2_hints=0, autotune=0, patch_rows_per_warp=0,
-                 coarse_levels=-1, gmg_nu=2, gmg_omega=2.0 / 3.0, patch_form=0, stream=None):
+                 coarse_levels=-1, gmg_nu=2, gmg_omega=2.0 / 3.0, patch_form=0, sc_variant=0, stream=None):
         self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (xv, yv, zv)]
         mesh = fdm_mesh()
         mesh.nx, mesh.ny, mesh.nz = len(xv) - 1, len(yv) - 1, len(zv) - 1
@@ -347,6 +347,7 @@ class Context:
         opt.patch_rows_per_warp = patch_rows_per_warp
         opt.coarse_levels, opt.gmg_nu, opt.gmg_omega = coarse_levels, gmg_nu, gmg_omega
         opt.patch_form = patch_form
+        opt.sc_variant = sc_variant
         opt.wait_timeout_s = wait_timeout_s
         if lanczos_start is not None:
             s = np.ascontiguousarray(lanczos_start, dtype=np.float64)
