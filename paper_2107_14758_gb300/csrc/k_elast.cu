@@ -22,46 +22,50 @@ namespace {
 
 constexpr int EL_THREADS = 256;
 
-// out[z][y][r] = sum_c M[r][c] in[z][y][c]  (trans: M[c][r])
-template <typename T, bool TR>
-__device__ void pass_x(int n, const T *M, const T *in, T *out, bool acc) {
-  const int n3 = n * n * n;
-  for (int o = threadIdx.x; o < n3; o += blockDim.x) {
-    const int r = o % n, zy = o / n;
-    const T *src = in + zy * n;
+// out[z][y][r] = sum_c M[r][c] in[z][y][c]  (trans: M[c][r]); n = N at compile time
+template <typename T, int N, bool TR>
+__device__ __forceinline__ void pass_x(const T *M, const T *in, T *out, bool acc) {
+  constexpr int N3 = N * N * N;
+  for (int o = threadIdx.x; o < N3; o += blockDim.x) {
+    const int r = o % N, zy = o / N;
+    const T *src = in + zy * N;
     T s = 0;
-    for (int c = 0; c < n; ++c) s = fma(TR ? M[c * n + r] : M[r * n + c], src[c], s);
+#pragma unroll
+    for (int c = 0; c < N; ++c) s = fma(TR ? M[c * N + r] : M[r * N + c], src[c], s);
     out[o] = acc ? out[o] + s : s;
   }
 }
-template <typename T, bool TR>
-__device__ void pass_y(int n, const T *M, const T *in, T *out, bool acc) {
-  const int n3 = n * n * n;
-  for (int o = threadIdx.x; o < n3; o += blockDim.x) {
-    const int x = o % n, r = (o / n) % n, z = o / (n * n);
-    const T *src = in + z * n * n + x;
+template <typename T, int N, bool TR>
+__device__ __forceinline__ void pass_y(const T *M, const T *in, T *out, bool acc) {
+  constexpr int N3 = N * N * N;
+  for (int o = threadIdx.x; o < N3; o += blockDim.x) {
+    const int x = o % N, r = (o / N) % N, z = o / (N * N);
+    const T *src = in + z * N * N + x;
     T s = 0;
-    for (int c = 0; c < n; ++c) s = fma(TR ? M[c * n + r] : M[r * n + c], src[c * n], s);
+#pragma unroll
+    for (int c = 0; c < N; ++c) s = fma(TR ? M[c * N + r] : M[r * N + c], src[c * N], s);
     out[o] = acc ? out[o] + s : s;
   }
 }
-template <typename T, bool TR>
-__device__ void pass_z(int n, const T *M, const T *in, T *out, bool acc) {
-  const int n2 = n * n, n3 = n2 * n;
-  for (int o = threadIdx.x; o < n3; o += blockDim.x) {
-    const int xy = o % n2, r = o / n2;
+template <typename T, int N, bool TR>
+__device__ __forceinline__ void pass_z(const T *M, const T *in, T *out, bool acc) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  for (int o = threadIdx.x; o < N3; o += blockDim.x) {
+    const int xy = o % N2, r = o / N2;
     const T *src = in + xy;
     T s = 0;
-    for (int c = 0; c < n; ++c) s = fma(TR ? M[c * n + r] : M[r * n + c], src[c * n2], s);
+#pragma unroll
+    for (int c = 0; c < N; ++c) s = fma(TR ? M[c * N + r] : M[r * N + c], src[c * N2], s);
     out[o] = acc ? out[o] + s : s;
   }
 }
 
-template <typename T, typename Tin>
+template <typename T, typename Tin, int N>
 __global__ void __launch_bounds__(EL_THREADS) k_elast_grad(Grid g, const Tin *__restrict__ u,
                                                            const T *__restrict__ tab, T *__restrict__ G) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = g.n, p = g.p, n3 = n * n * n;
+  constexpr int n = N, n3 = N * N * N;
+  const int p = g.p;
   T *M = reinterpret_cast<T *>(smem_raw);  // V, D (2 n^2)
   T *U = M + 2 * n * n, *S1 = U + n3, *S2 = S1 + n3, *S3 = S2 + n3;
   const int cell = blockIdx.x, b = blockIdx.y;
@@ -81,26 +85,26 @@ __global__ void __launch_bounds__(EL_THREADS) k_elast_grad(Grid g, const Tin *__
   const T *V = M, *D = M + n * n;
   T *Gb = G + (int64_t)(3 * b) * g.ncell * n3 + (int64_t)cell * n3;  // G[b][d][cell][q^3]
   const int64_t dstride = (int64_t)g.ncell * n3;
-  pass_z<T, false>(n, V, U, S1, false);   // V_z u
+  pass_z<T, N, false>(V, U, S1, false);   // V_z u
   __syncthreads();
-  pass_y<T, false>(n, V, S1, S2, false);  // V_y V_z u
-  pass_y<T, false>(n, D, S1, S3, false);  // D_y V_z u
+  pass_y<T, N, false>(V, S1, S2, false);  // V_y V_z u
+  pass_y<T, N, false>(D, S1, S3, false);  // D_y V_z u
   __syncthreads();
-  pass_x<T, false>(n, D, S2, Gb, false);               // d/dxi_x
-  pass_x<T, false>(n, V, S3, Gb + dstride, false);     // d/dxi_y
-  pass_z<T, false>(n, D, U, S1, false);                // D_z u
+  pass_x<T, N, false>(D, S2, Gb, false);               // d/dxi_x
+  pass_x<T, N, false>(V, S3, Gb + dstride, false);     // d/dxi_y
+  pass_z<T, N, false>(D, U, S1, false);                // D_z u
   __syncthreads();
-  pass_y<T, false>(n, V, S1, S2, false);
+  pass_y<T, N, false>(V, S1, S2, false);
   __syncthreads();
-  pass_x<T, false>(n, V, S2, Gb + 2 * dstride, false);  // d/dxi_z
+  pass_x<T, N, false>(V, S2, Gb + 2 * dstride, false);  // d/dxi_z
 }
 
-template <typename T>
+template <typename T, int N>
 __global__ void __launch_bounds__(EL_THREADS) k_elast_flux(Grid g, const T *__restrict__ G, const T *__restrict__ tab,
                                                            const T *__restrict__ wq, const double *__restrict__ Lc,
                                                            double mu, double lam, T *__restrict__ E) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n = g.n, n3 = n * n * n;
+  constexpr int n = N, n3 = N * N * N;
   T *M = reinterpret_cast<T *>(smem_raw);
   T *S0 = M + 2 * n * n, *S1 = S0 + n3, *S2 = S1 + n3, *S3 = S2 + n3;
   const int cell = blockIdx.x, a = blockIdx.y;
@@ -108,40 +112,44 @@ __global__ void __launch_bounds__(EL_THREADS) k_elast_flux(Grid g, const T *__re
     M[i] = tab[tab_off(TAB_VQ, n) + i];
     M[n * n + i] = tab[tab_off(TAB_DQ, n) + i];
   }
-  const double L[3] = {Lc[3 * cell], Lc[3 * cell + 1], Lc[3 * cell + 2]};
-  const double vol = L[0] * L[1] * L[2];
+  // the pointwise stress in the kernel's precision (FP32 inside the FP32 preconditioner)
+  const T L[3] = {T(Lc[3 * cell]), T(Lc[3 * cell + 1]), T(Lc[3 * cell + 2])};
+  const T vol = L[0] * L[1] * L[2];
+  const T iL[3] = {T(1) / L[0], T(1) / L[1], T(1) / L[2]};  // no divisions per point
+  const T tmu = T(mu), tlam = T(lam);
   const int64_t dstride = (int64_t)g.ncell * n3;
   const T *Gc = G + (int64_t)cell * n3;
   // physical derivative d_d u_b at point o
-  auto grad = [&](int b, int d, int o) { return double(Gc[(3 * b + d) * dstride + o]) / L[d]; };
+  auto grad = [&](int b, int d, int o) { return Gc[(3 * b + d) * dstride + o] * iL[d]; };
   T *F[3] = {S0, S1, S2};
   for (int o = threadIdx.x; o < n3; o += blockDim.x) {
     const int i = o % n, j = (o / n) % n, k = o / (n * n);
-    const double w = double(wq[i]) * double(wq[j]) * double(wq[k]) * vol;
-    const double div = grad(0, 0, o) + grad(1, 1, o) + grad(2, 2, o);
+    const T w = wq[i] * wq[j] * wq[k] * vol;
+    const T div = grad(0, 0, o) + grad(1, 1, o) + grad(2, 2, o);
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
-      double s = mu * (grad(a, d, o) + grad(d, a, o));
-      if (d == a) s += lam * div;
-      F[d][o] = T(w * s / L[d]);
+      T s = tmu * (grad(a, d, o) + grad(d, a, o));
+      if (d == a) s += tlam * div;
+      F[d][o] = w * s * iL[d];
     }
   }
   __syncthreads();
   const T *V = M, *D = M + n * n;
   // y = V_z^T [V_y^T D_x^T F_x + D_y^T V_x^T F_y] + D_z^T V_y^T V_x^T F_z, four buffers
-  pass_x<T, true>(n, D, S0, S3, false);  // S3 = D_x^T F_x
+  pass_x<T, N, true>(D, S0, S3, false);  // S3 = D_x^T F_x
   __syncthreads();
-  pass_x<T, true>(n, V, S1, S0, false);  // S0 = V_x^T F_y
+  pass_x<T, N, true>(V, S1, S0, false);  // S0 = V_x^T F_y
   __syncthreads();
-  pass_y<T, true>(n, V, S3, S1, false);  // S1 = V_y^T S3
+  pass_y<T, N, true>(V, S3, S1, false);  // S1 = V_y^T S3
   __syncthreads();
-  pass_y<T, true>(n, D, S0, S1, true);   // S1 += D_y^T S0
-  pass_x<T, true>(n, V, S2, S3, false);  // S3 = V_x^T F_z
+  pass_y<T, N, true>(D, S0, S1, true);   // S1 += D_y^T S0
+  pass_x<T, N, true>(V, S2, S3, false);  // S3 = V_x^T F_z
   __syncthreads();
-  pass_y<T, true>(n, V, S3, S0, false);  // S0 = V_y^T S3
+  pass_y<T, N, true>(V, S3, S0, false);  // S0 = V_y^T S3
   __syncthreads();
-  pass_z<T, true>(n, V, S1, S2, false);  // S2 = V_z^T S1
+  pass_z<T, N, true>(V, S1, S2, false);  // S2 = V_z^T S1
   __syncthreads();
-  pass_z<T, true>(n, D, S0, S2, true);   // S2 += D_z^T S0
+  pass_z<T, N, true>(D, S0, S2, true);   // S2 += D_z^T S0
   __syncthreads();
   T *Ea = E + (int64_t)a * g.ncell * n3 + (int64_t)cell * n3;
   for (int o = threadIdx.x; o < n3; o += blockDim.x) Ea[o] = S2[o];
@@ -158,10 +166,14 @@ template <typename T, typename Tin>
 void launch_elast_cells(const Grid &g, const Tin *u, const T *tab, const T *wq, const double *Lc, double mu, double lam,
                         T *G, T *E, cudaStream_t st) {
   const size_t sm = elast_smem<T>(g.n);
-  set_smem(k_elast_grad<T, Tin>, sm);
-  set_smem(k_elast_flux<T>, sm);
-  k_elast_grad<T, Tin><<<dim3(g.ncell, 3), EL_THREADS, sm, st>>>(g, u, tab, G);
-  k_elast_flux<T><<<dim3(g.ncell, 3), EL_THREADS, sm, st>>>(g, G, tab, wq, Lc, mu, lam, E);
+  if (!dispatch_n(g.n, [&](auto NC) {
+        constexpr int N = decltype(NC)::value;
+        set_smem(k_elast_grad<T, Tin, N>, sm);
+        set_smem(k_elast_flux<T, N>, sm);
+        k_elast_grad<T, Tin, N><<<dim3(g.ncell, 3), EL_THREADS, sm, st>>>(g, u, tab, G);
+        k_elast_flux<T, N><<<dim3(g.ncell, 3), EL_THREADS, sm, st>>>(g, G, tab, wq, Lc, mu, lam, E);
+      }))
+    fail(FDM_EINVAL, "elasticity operator: unsupported degree");
 }
 
 template size_t elast_smem<double>(int);
