@@ -49,7 +49,8 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_restrict_t(Grid 
       const int mult = ((i == 0 && cx > 0) || (i == P && cx < g.nx - 1) ? 2 : 1) *
                        ((j == 0 && cy > 0) || (j == P && cy < g.ny - 1) ? 2 : 1) *
                        ((k == 0 && cz > 0) || (k == P && cz < g.nz - 1) ? 2 : 1);
-      U[pid<N>(i, j, k)] = dir ? T(0) : T(r[gidx(g, gx, gy, gz)]) / T(mult);
+      const T wm = mult == 1 ? T(1) : (mult == 2 ? T(0.5) : (mult == 4 ? T(0.25) : T(0.125)));  // exact 1/mult
+      U[pid<N>(i, j, k)] = dir ? T(0) : T(r[gidx(g, gx, gy, gz)]) * wm;
     }
   }
   __syncthreads();
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_coarse_restrict_
         const int gy = cy * P + j;
         if (gy == 0 || gy == g.N[1] - 1) continue;
         const int m = mxz * ((j == 0 && cy > 0) || (j == P && cy < g.ny - 1) ? 2 : 1);
-        const T v = T(r[gidx(g, gx, gy, gz)]) / T(m);
+        const T v = T(r[gidx(g, gx, gy, gz)]) * (m == 1 ? T(1) : (m == 2 ? T(0.5) : (m == 4 ? T(0.25) : T(0.125))));
         s0 += T(0.5) * (T(1) - xi[j]) * v;
         s1 += T(0.5) * (T(1) + xi[j]) * v;
       }
