@@ -103,3 +103,43 @@ def test_batched_edge_cases():
         assert infos[0].rnorm <= 1e-6 * infos[0].rnorm0
     finally:
         fdmpc.fdm_batch_destroy(batch)
+
+
+def test_full_batch_workload():
+    """The 64-problem workload as the benchmark runs it (n in 2..10, p in
+    3..15, mixed precision, autotuned patch solves, one graph): every solve
+    reaches the FP64 true residual 1e-8, and the smallest problems match the
+    FP64 oracle's solution to the solver tolerance."""
+    probs = inputs.batch_problems(64, 1000)
+    ctxs, bs = [], []
+    for w in probs:
+        n, p = len(w["xv"]) - 1, w["p"]
+        nd = (n * p + 1) ** 3
+        ctxs.append(fdmpc.Context(p, w["xv"], w["yv"], w["zv"], precision=FP32, lanczos_start=inputs.lanczos_start(nd),
+                                  autotune=1))
+        bs.append(torch.tensor(inputs.normal_rhs(nd, w["seed"]), device=DEV))
+    batch = fdmpc.fdm_batch_setup([c.h for c in ctxs])
+    try:
+        xs = [torch.empty_like(b) for b in bs]
+        infos = fdmpc.pcg_solve_batched(batch, bs, xs, 1e-8, 300)
+        for info in infos:
+            assert info.converged and info.true_rnorm <= 1.5e-8 * info.rnorm0
+        small = sorted(range(64), key=lambda i: (len(probs[i]["xv"]) - 1) ** 3 * probs[i]["p"] ** 3)[:4]
+        for i in small:
+            w = probs[i]
+            ref = oracle.Problem(w["p"], w["xv"], w["yv"], w["zv"])
+            ref.setup_patches()
+            ref.setup_coarse()
+            ref.set_omega(ctxs[i].omega)
+            b = bs[i].cpu().numpy()
+            from tests import bruteforce as bf
+            n = len(w["xv"]) - 1
+            b = np.where(bf.free_mask(w["p"], n, n, n), b, 0.0)
+            x_ref, _, _, conv = ref.pcg(b, 1e-10, 400)
+            assert conv
+            x = xs[i].cpu().numpy()
+            assert np.abs(x - x_ref).max() <= 1e-6 * np.abs(x_ref).max()
+    finally:
+        fdmpc.fdm_batch_destroy(batch)
+        for c in ctxs:
+            c.close()

@@ -306,16 +306,19 @@ def _node_in_cell_interior(ref, cell, seed):
     return (cx * p + i) + ref.N[0] * ((cy * p + j) + ref.N[1] * (cz * p + k)), (cx, cy, cz)
 
 
-@pytest.mark.parametrize("name", ["q7_graded16", "q15_uniform8"])
+@pytest.mark.parametrize("name", ["q7_graded16", "q15_uniform8", "q8_deformed12"])
 def test_full_size_sampled(name):
     """At the benchmark sizes: the full stiffness apply, and the relaxation
     applied to a unit vector at a sampled cell-interior node, which only
-    involves the 8 vertex stars of that cell (set up alone in the oracle)."""
+    involves the 8 vertex stars of that cell (set up alone in the oracle).
+    The deformed workload runs with its curved cells, kappa and averaged
+    surrogate."""
     w = inputs.workload(name)
     p = w["p"]
     for precision in (FP64, FP32):
-        ctx = fdmpc.Context(p, w["xv"], w["yv"], w["zv"], precision=precision, pc=fdmpc.FDM_PC_ASM, omega=1.0)
-        ref = oracle.Problem(p, w["xv"], w["yv"], w["zv"])
+        ctx = fdmpc.Context(p, w["xv"], w["yv"], w["zv"], jac=w["jac"], kappa=w["kappa"], precision=precision,
+                            pc=fdmpc.FDM_PC_ASM, omega=1.0)
+        ref = oracle.Problem(p, w["xv"], w["yv"], w["zv"], jac=w["jac"], kappa=w["kappa"])
         if precision == FP64:
             u = np.random.default_rng(12).standard_normal(ref.ndof)
             assert relerr(N(ctx.stiffness_apply(T(u))), ref.stiffness_apply(u)) <= 1e-12
