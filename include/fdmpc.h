@@ -110,8 +110,9 @@ typedef struct {
                          shared memory and its S_TB and W in L2 while solving the current one */
   int stream_buffers; /* ring buffers of the streamed solve (0 = 4) */
   int stream_buffer_kb; /* size of each ring buffer in KiB (0 = 16) */
-  int inject_stall;   /* test hook: the streamed solve waits on a barrier that is never
-                         completed, gives up after wait_timeout_s and reports FDM_ETIMEOUT */
+  int inject_stall;   /* test hook: the streamed, resident, cluster and (where it stages values in
+                         shared memory) Schur-coupling solves wait on a barrier that is never
+                         completed, give up after wait_timeout_s and report FDM_ETIMEOUT */
   int patch_prefetch; /* one-CTA-per-patch solve: L2 bulk prefetch of the factor, 1 = all at
                          the start, 2 = one section ahead of use, 3 = none (0 = 3) */
   int pcg_graph;      /* 1 (default): pcg_solve runs its loop on the device in a captured CUDA

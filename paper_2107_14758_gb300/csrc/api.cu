@@ -287,6 +287,7 @@ void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st, c
                         c->X<T>(), patch_sc_tmp(c->maxN1, c->maxN2, c->patch_threads), 0,
                         (uint64_t)(std::max(c->opt.wait_timeout_s, 0.0) * 1e9), c->status, 0, 0, 0};
     a.rows8 = c->rows8;  // Schur-coupling form: four rows per warp in the W product (else two)
+    a.inject_stall = c->opt.inject_stall;
     if (c->sc_persist) {  // persistent (256 threads): two buffers for the lower block's values, S_TB and W via L2
       a.stage_st = 0;
       a.tmpcap = patch_sc_tmp(c->maxN1, c->maxN2, 256);  // the scratch the kernel zeroes, sized for its threads

@@ -458,6 +458,7 @@ __global__ void __launch_bounds__(NT, 1) k_patch_resident(PatchSolveArgs<T> a, i
   if (tid == 0) {
     bulk::mbar_init(&bar[0], 1);
     bulk::mbar_init(&bar[1], 1);
+    bulk::mbar_init(&bar[2], 1);
     bulk::fence_mbar_init();
     sFail = 0;
   }
@@ -786,7 +787,7 @@ __global__ void __launch_bounds__(NT, MINB) k_patch_solve_sc(PatchSolveArgs<T> a
   const PatchDev P = a.patches[a.order[blockIdx.x]];
   const ClassDev &C = a.cls[P.cls];
   __shared__ int sCell[8];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar, stall;  // stall: test hook, never completed
   __shared__ int sFail;
   T *H = reinterpret_cast<T *>(smem_);  // a.headcap elements (a multiple of 4)
   T *gv = H + a.headcap;
@@ -797,6 +798,7 @@ __global__ void __launch_bounds__(NT, MINB) k_patch_solve_sc(PatchSolveArgs<T> a
     if (stage) {
       sFail = 0;
       bulk::mbar_init(&bar, 1);
+      bulk::mbar_init(&stall, 1);
       bulk::fence_mbar_init();
       const uint32_t bytes = (uint32_t)(hend * (int64_t)sizeof(T));  // a multiple of 16
       bulk::mbar_arrive_expect_tx(&bar, bytes);
@@ -812,7 +814,9 @@ __global__ void __launch_bounds__(NT, MINB) k_patch_solve_sc(PatchSolveArgs<T> a
   patch_gather<T, NT, 2>(a, P, C, gv, sCell);  // also zeroes y and tmp (barriers inside)
   const T *Lh = Lv;
   if (stage) {
-    if (!bulk::mbar_wait_bounded(&bar, 0, a.timeout_ns)) sFail = 1;
+    bool ok = !a.inject_stall || bulk::mbar_wait_bounded(&stall, 0, a.timeout_ns);  // never completes
+    ok = ok && bulk::mbar_wait_bounded(&bar, 0, a.timeout_ns);
+    if (!ok) sFail = 1;
     __syncthreads();
     if (sFail) {
       bulk::mbar_wait_bounded(&bar, 0, a.timeout_ns);  // a second bounded wait for the copy in flight
@@ -836,7 +840,7 @@ __global__ void __launch_bounds__(NT, MINB) k_patch_solve_scp(PatchSolveArgs<T> 
   extern __shared__ __align__(128) unsigned char smem_[];
   const int tid = threadIdx.x;
   __shared__ int sCell[8];
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t bar[3];  // [2]: test hook, never completed
   __shared__ int sFail, sPend[2];
   T *const H0 = reinterpret_cast<T *>(smem_);  // two buffers of a.headcap elements (multiples of 4)
   T *const H1 = H0 + a.headcap;
@@ -879,7 +883,9 @@ __global__ void __launch_bounds__(NT, MINB) k_patch_solve_scp(PatchSolveArgs<T> 
     const T *Lv = a.L + P.voff;
     const T *Lh = Lv;
     if (sPend[b]) {
-      if (!bulk::mbar_wait_bounded(&bar[b], par[b], a.timeout_ns)) sFail = 1;
+      bool ok = !a.inject_stall || bulk::mbar_wait_bounded(&bar[2], 0, a.timeout_ns);  // never completes
+      ok = ok && bulk::mbar_wait_bounded(&bar[b], par[b], a.timeout_ns);
+      if (!ok) sFail = 1;
       __syncthreads();
       if (sFail) {
         for (int q = 0; q < 2; ++q)  // a second bounded wait for every copy in flight

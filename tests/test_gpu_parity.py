@@ -384,9 +384,11 @@ def test_resident_matches_classic_bitwise(p, precision):
     assert np.array_equal(out[0], out[1])
 
 
-@pytest.mark.parametrize("kernel", [2, 3, 4])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5])
 def test_bounded_wait_reports_timeout_kernels(kernel):
-    """As below, for the streamed and the resident patch solves."""
+    """As below, for every patch solve with a bounded device-side wait: the
+    Schur-coupling kernels (its staging copy), the streamed, resident and
+    cluster kernels."""
     xv, yv, zv = inputs.graded_vertices(2, 3)
     ctx = fdmpc.Context(3, xv, yv, zv, precision=FP32, omega=0.2, inject_stall=1, wait_timeout_s=0.02,
                         patch_kernel=kernel)
