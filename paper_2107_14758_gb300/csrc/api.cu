@@ -9,6 +9,7 @@
 #include "factor.h"
 #include "internal.h"
 #include "kernels.h"
+#include "ctx.h"
 
 namespace fdm {
 [[noreturn]] void fail(int code, const std::string &msg) { throw Error{code, msg}; }
@@ -23,184 +24,6 @@ double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 }  // namespace
-
-struct fdm_ctx {
-  Grid g{};
-  int p = 0;
-  fdm_options opt{};
-  Basis1D basis;
-  std::vector<PatchClass> classes;
-  int general = 0;
-  std::vector<void *> allocs;
-  std::string err;
-
-  // device data
-  double *tab64 = nullptr;
-  float *tab32 = nullptr;
-  double *mu_box = nullptr, *mu = nullptr;
-  double *Gw64 = nullptr, *detw64 = nullptr;
-  float *Gw32 = nullptr, *detw32 = nullptr;
-  ClassDev *d_cls = nullptr;
-  int *cmap = nullptr;  // cell node -> star interface index per (class, corner)
-  std::vector<ClassDev> h_cls;
-  std::vector<PatchDev> h_patches;
-  PatchDev *d_patches = nullptr;
-  int *d_order = nullptr;
-  int npatch = 0, nsolve = 0;
-  int maxG = 0, maxN0 = 0, maxN1 = 0, maxN2 = 0;
-  int patch_threads = 256;
-  // streamed patch solve
-  bool stream = true;
-  int nbuf = 4, buf_bytes = 16384;
-  int *status = nullptr;
-  int *d_order_nz = nullptr;  // patches with an interface, heaviest first
-  int nsolve_nz = 0;
-  int64_t nval_total = 0, nstar_total = 0;
-  double *L64 = nullptr;
-  float *L32 = nullptr;
-  double *X64 = nullptr, *E64 = nullptr;
-  float *X32 = nullptr, *E32 = nullptr;
-  size_t smem64 = 0, smem32 = 0;
-  // resident patch solve (whole factor of a patch in shared memory), per precision
-  bool res64 = false, res32 = false;
-  int fcap = 0, res_threads = 512, res_tmp = 0;
-  int rows8 = 0;  // forward products of the classic patch solve: eight rows per warp
-  bool scform = false;  // Schur-coupling form of the patch factors and solve
-  int headcap32 = 0, headcap64 = 0;  // its staged values before W, per precision (elements)
-  int bcap32 = 0, bcap64 = 0;        // the same before S_TB (lower block only)
-  bool sc_persist = false;           // persistent Schur-coupling kernel (patch_kernel = 5)
-  // cluster patch solve for the classes with a dense top level (a prefix of the order)
-  int n_heavy = 0, cl_threads = 256;
-  bool cl32 = false, cl64 = false;
-  ClusterArgs<float> cla32{};
-  ClusterArgs<double> cla64{};
-  double tuning[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // autotuner: kernel, threads, rows8, best us, candidates tried
-  size_t rsmem64 = 0, rsmem32 = 0;
-  // coarse
-  int nc = 0;
-  int nc_dense = 0;  // order of the dense inverse: the Q1 problem, or the coarsest multigrid level
-  // geometric multigrid on the Q1 problem: gmg_L coarsenings (0 = exact solve)
-  int gmg_L = 0, gmg_nu = 2;
-  double gmg_omega = 2.0 / 3.0;
-  std::vector<GmgHostLevel> gmg_host;
-  template <typename T>
-  struct GmgVecs {
-    std::vector<GmgDev<T>> lev;
-    std::vector<T *> b, out, xa, xb, r;  // per level: right-hand side, result, two iterates, residual
-  };
-  GmgVecs<double> gmg64;
-  GmgVecs<float> gmg32;
-  template <typename T> GmgVecs<T> &gmg();
-  std::vector<double> vert[3];  // mesh vertex coordinates per axis
-  int *cfree = nullptr;
-  double *Acinv64 = nullptr, *rc64 = nullptr, *xc64 = nullptr, *cb64 = nullptr;
-  float *Acinv32 = nullptr, *rc32 = nullptr, *xc32 = nullptr, *cb32 = nullptr;
-  // work vectors
-  double *r = nullptr, *z = nullptr, *zold = nullptr, *d = nullptr, *q = nullptr;
-  double *v1 = nullptr, *v2 = nullptr, *v3 = nullptr;
-  float *f_in = nullptr, *f_out = nullptr, *f1 = nullptr, *f2 = nullptr, *f3 = nullptr;
-  double *partial = nullptr, *dots = nullptr, *sc = nullptr;
-  double omega = 1.0, lmin = 0.0, lmax = 0.0;
-  double t_setup[4] = {0, 0, 0, 0};
-  // learned surrogate (curved cells)
-  double *mubar = nullptr;      // averaged surrogate of Section 2.7, [ncell][3]
-  double *wq64 = nullptr;       // Gauss weights (n)
-  float *feat = nullptr;        // network inputs [ncell][189] (with samples27)
-  double *cstar = nullptr, *F0 = nullptr, *F1 = nullptr;  // labels and bound ratios (on first use)
-  float *label32 = nullptr;
-  float *surr_c = nullptr;      // network outputs of the last fdm_surrogate_apply
-  int *d_count = nullptr;
-  double *Fcur = nullptr;       // bound ratios at the current mu (queries)
-  double kappa_avg = 0.0;       // Lanczos lmax / lmin with the averaged surrogate (0: not run)
-  // instrumentation: launch counter and optional per-group CUDA-event timers
-  int64_t launches = 0;
-  std::vector<cudaEvent_t> ev_pool;
-  std::vector<int> ev_tag;  // tag of each recorded (begin, end) pair
-  size_t ev_used = 0;
-  bool capturing = false;  // building a CUDA graph: no event timers
-  struct fdm_batch *solo = nullptr;  // one-problem batch of the graph-driven pcg_solve
-  void tmark(int tag, bool begin, cudaStream_t st) {
-    if (!opt.kernel_timing || capturing) return;
-    if (begin) {
-      if (ev_used + 2 > ev_pool.size()) {
-        for (int i = 0; i < 256; ++i) {
-          cudaEvent_t e;
-          FDM_CUDA(cudaEventCreate(&e));
-          ev_pool.push_back(e);
-        }
-      }
-      ev_tag.push_back(tag);
-      FDM_CUDA(cudaEventRecord(ev_pool[ev_used], st));
-    } else {
-      FDM_CUDA(cudaEventRecord(ev_pool[ev_used + 1], st));
-      ev_used += 2;
-    }
-  }
-
-  template <typename T>
-  T *alloc(size_t n) {
-    void *ptr = nullptr;
-    if (cudaMalloc(&ptr, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
-      cudaGetLastError();
-      fail(FDM_ENOMEM, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed");
-    }
-    allocs.push_back(ptr);
-    return static_cast<T *>(ptr);
-  }
-  template <typename T>
-  T *upload(const std::vector<T> &h) {
-    T *ptr = alloc<T>(h.size());
-    if (!h.empty()) FDM_CUDA(cudaMemcpy(ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
-    return ptr;
-  }
-  ~fdm_ctx() {
-    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
-    for (void *ptr : allocs) cudaFree(ptr);
-  }
-
-  template <typename T> const T *tab() const;
-  template <typename T> T *E() const;
-  template <typename T> T *X() const;
-  template <typename T> const T *L() const;
-  template <typename T> size_t smem() const;
-  template <typename T> T *rc() const;
-  template <typename T> T *xc() const;
-  template <typename T> T *cb() const;
-  template <typename T> const T *Acinv() const;
-  OpArgs op_args(bool fp32) const {
-    OpArgs a;
-    a.g = g;
-    a.general = general;
-    a.mu_box = mu_box;
-    a.Gw = fp32 ? (const void *)Gw32 : (const void *)Gw64;
-    a.detw = fp32 ? (const void *)detw32 : (const void *)detw64;
-    a.tab = fp32 ? (const void *)tab32 : (const void *)tab64;
-    return a;
-  }
-};
-template <> fdm_ctx::GmgVecs<double> &fdm_ctx::gmg<double>() { return gmg64; }
-template <> fdm_ctx::GmgVecs<float> &fdm_ctx::gmg<float>() { return gmg32; }
-template <> const double *fdm_ctx::tab<double>() const { return tab64; }
-template <> const float *fdm_ctx::tab<float>() const { return tab32; }
-template <> double *fdm_ctx::E<double>() const { return E64; }
-template <> float *fdm_ctx::E<float>() const { return E32; }
-template <> double *fdm_ctx::X<double>() const { return X64; }
-template <> float *fdm_ctx::X<float>() const { return X32; }
-template <> const double *fdm_ctx::L<double>() const { return L64; }
-template <> const float *fdm_ctx::L<float>() const { return L32; }
-template <> size_t fdm_ctx::smem<double>() const { return smem64; }
-template <typename T> ClusterArgs<T> cluster_args(const fdm_ctx *c);
-template <> ClusterArgs<float> cluster_args<float>(const fdm_ctx *c) { return c->cla32; }
-template <> ClusterArgs<double> cluster_args<double>(const fdm_ctx *c) { return c->cla64; }
-template <> size_t fdm_ctx::smem<float>() const { return smem32; }
-template <> double *fdm_ctx::rc<double>() const { return rc64; }
-template <> float *fdm_ctx::rc<float>() const { return rc32; }
-template <> double *fdm_ctx::xc<double>() const { return xc64; }
-template <> float *fdm_ctx::xc<float>() const { return xc32; }
-template <> double *fdm_ctx::cb<double>() const { return cb64; }
-template <> float *fdm_ctx::cb<float>() const { return cb32; }
-template <> const double *fdm_ctx::Acinv<double>() const { return Acinv64; }
-template <> const float *fdm_ctx::Acinv<float>() const { return Acinv32; }
 
 struct fdm_batch {
   std::vector<fdm_ctx *> ctxs;
@@ -1420,284 +1243,26 @@ namespace fdm {
 OpArgs ctx_op_args64(const fdm_ctx *c) { return c->op_args(false); }
 void ctx_count_launches(fdm_ctx *c, int k) { c->launches += k; }
 int ctx_fail(fdm_ctx *c, int code, const std::string &msg) { return handle(c, Error{code, msg}); }
-}  // namespace fdm
-
-// ====================================================================== linear elasticity (Section 4.1)
-// Primal formulation on box cells, clamped on the whole boundary; vectors are
-// component-major [3][ndof].  The SDC relaxation is block-Jacobi over the
-// displacement components: block j is the scalar operator with per-axis
-// coefficients mu + (mu + lam) delta_aj, separable on box cells, so each block
-// is a scalar context whose vertex-star FDM/sparse relaxation uses the exact
-// surrogate mu_a^(j) = (mu + (mu + lam) delta_aj) vol / L_a^2.  The V(1,1)
-// cycle uses the elasticity residual and the vector Q1 Galerkin coarse
-// problem, which on box cells is the Q1 elasticity stiffness (exactly
-// integrated by 2 Gauss points per axis), solved through its dense inverse.
-struct fdm_elast {
-  fdm_ctx *comp[3] = {nullptr, nullptr, nullptr};
-  fdm_options opt;
-  double mu = 1.0, lam = 0.0, omega = 1.0, lmin = 0.0, lmax = 0.0;
-  Grid g{};
-  int64_t n = 0;  // grid nodes per component
-  std::string err;
-  std::vector<void *> allocs;
-  double *Lc = nullptr;
-  double *wq64 = nullptr;
-  float *wq32 = nullptr;
-  double *G64 = nullptr, *E64 = nullptr;
-  float *G32 = nullptr, *E32 = nullptr;
-  int nq = 0, m = 0;  // free Q1 vertices, coarse unknowns 3 nq
-  double *Ainv64 = nullptr, *rc64 = nullptr, *xc64 = nullptr;
-  float *Ainv32 = nullptr, *rc32 = nullptr, *xc32 = nullptr;
-  double *r = nullptr, *z = nullptr, *zold = nullptr, *d = nullptr, *q = nullptr, *v1 = nullptr, *v3 = nullptr;
-  float *f1 = nullptr, *f3 = nullptr;
-  double *partial = nullptr, *dots = nullptr, *sc = nullptr;
-  int64_t launches = 0;
-  template <typename T>
-  T *alloc(size_t k) {
-    void *ptr = nullptr;
-    if (cudaMalloc(&ptr, std::max<size_t>(k, 1) * sizeof(T)) != cudaSuccess) {
-      cudaGetLastError();
-      fail(FDM_ENOMEM, "cudaMalloc of " + std::to_string(k * sizeof(T)) + " bytes failed");
-    }
-    allocs.push_back(ptr);
-    return static_cast<T *>(ptr);
-  }
-  template <typename T>
-  T *upload(const std::vector<T> &h) {
-    T *ptr = alloc<T>(h.size());
-    if (!h.empty()) FDM_CUDA(cudaMemcpy(ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
-    return ptr;
-  }
-  template <typename T> T *G() const;
-  template <typename T> T *E() const;
-  template <typename T> const T *wq() const;
-  template <typename T> const T *Ainv() const;
-  template <typename T> T *rc() const;
-  template <typename T> T *xc() const;
-  ~fdm_elast() {
-    for (fdm_ctx *c : comp)
-      if (c) {
-        delete c->solo;
-        delete c;
-      }
-    for (void *ptr : allocs) cudaFree(ptr);
-  }
-};
-template <> double *fdm_elast::G<double>() const { return G64; }
-template <> float *fdm_elast::G<float>() const { return G32; }
-template <> double *fdm_elast::E<double>() const { return E64; }
-template <> float *fdm_elast::E<float>() const { return E32; }
-template <> const double *fdm_elast::wq<double>() const { return wq64; }
-template <> const float *fdm_elast::wq<float>() const { return wq32; }
-template <> const double *fdm_elast::Ainv<double>() const { return Ainv64; }
-template <> const float *fdm_elast::Ainv<float>() const { return Ainv32; }
-template <> double *fdm_elast::rc<double>() const { return rc64; }
-template <> float *fdm_elast::rc<float>() const { return rc32; }
-template <> double *fdm_elast::xc<double>() const { return xc64; }
-template <> float *fdm_elast::xc<float>() const { return xc32; }
-
-namespace {
-
-int handle_elast(fdm_elast *e, const Error &err) {
-  if (e) e->err = err.msg;
-  g_last_error = err.msg;
-  return err.code;
+void ctx_mask_dirichlet(const Grid &g, double *v, cudaStream_t st) { mask_dirichlet(g, v, st); }
+void ctx_copy(int64_t n, const double *a, double *b, cudaStream_t st) { copy(n, a, b, st); }
+int ctx_vec_blocks(int64_t n) { return vec_blocks(n); }
+void ctx_banded_cholesky(int m, int bw, std::vector<double> &Lb) { banded_cholesky(m, bw, Lb); }
+void ctx_tridiag_extremes(const std::vector<double> &d, const std::vector<double> &e, double &lo, double &hi) {
+  tridiag_extremes(d, e, lo, hi);
 }
-
-void mask3(const fdm_elast *e, double *v, cudaStream_t st) {
-  for (int a = 0; a < 3; ++a) mask_dirichlet(e->g, v + a * e->n, st);
-}
-
-// y = A u (rsub == nullptr) or y = rsub - A u, in precision T
-template <typename T, typename Tin>
-void elast_op(fdm_elast *e, const Tin *u, T *y, const double *rsub, cudaStream_t st) {
-  launch_elast_cells<T, Tin>(e->g, u, e->comp[0]->tab<T>(), e->wq<T>(), e->Lc, e->mu, e->lam, e->G<T>(), e->E<T>(), st);
-  const int64_t cn = (int64_t)e->g.ncell * e->g.n * e->g.n * e->g.n;
-  for (int a = 0; a < 3; ++a)
-    launch_gather_cells<T, T>(e->g, e->E<T>() + a * cn, rsub ? rsub + a * e->n : nullptr, y + a * e->n, st);
-  e->launches += 5;
-}
-
-// z = omega S(r): the three scalar relaxations (precision T inside)
+void ctx_normal_vector(uint64_t seed, int64_t n, std::vector<double> &out) { normal_vector(seed, n, out); }
+std::string &ctx_last_error() { return g_last_error; }
 template <typename T, typename Tin, typename Tout>
-void elast_sdc(fdm_elast *e, const Tin *r, Tout *z, double omega, cudaStream_t st, const T *addv = nullptr) {
-  for (int a = 0; a < 3; ++a) {
-    fdm_ctx *c = e->comp[a];
-    c->launches = 0;
-    run_asm<T, Tin, Tout>(c, r + a * e->n, z + a * e->n, omega, st, addv ? addv + a * e->n : nullptr);
-    e->launches += c->launches;
-  }
+void ctx_run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st, const T *addv) {
+  run_asm<T, Tin, Tout>(c, r, z, omega, st, addv);
 }
-
-template <typename T>
-void elast_coarse(fdm_elast *e, const T *r1, T *x1, cudaStream_t st) {
-  for (int a = 0; a < 3; ++a) {
-    fdm_ctx *c = e->comp[a];
-    launch_coarse_restrict<T, T>(c->g, r1 + a * e->n, c->tab<T>(), c->cfree, e->rc<T>() + a * e->nq, c->cb<T>(), st);
-  }
-  launch_dense_symv<T>(e->m, e->Ainv<T>(), e->rc<T>(), e->xc<T>(), st);
-  for (int a = 0; a < 3; ++a) {
-    fdm_ctx *c = e->comp[a];
-    launch_coarse_prolong<T, T>(c->g, e->xc<T>() + a * e->nq, c->tab<T>(), c->cfree, x1 + a * e->n, true, st);
-  }
-  e->launches += 10;
-}
-
-// the hybrid V(1,1) with the SDC relaxation, FP64 r to FP64 z, computed in T
-template <typename T>
-void elast_vcycle(fdm_elast *e, const double *r, double *z, T *x1, T *r1, cudaStream_t st) {
-  elast_sdc<T, double, T>(e, r, x1, e->omega, st);
-  elast_op<T, T>(e, x1, r1, r, st);
-  if (e->m > 0) elast_coarse<T>(e, r1, x1, st);
-  elast_op<T, T>(e, x1, r1, r, st);
-  elast_sdc<T, T, double>(e, r1, z, e->omega, st, x1);
-}
-
-void elast_pc(fdm_elast *e, const double *r, double *z, cudaStream_t st) {
-  const bool fp64 = e->opt.precision == FDM_PREC_FP64;
-  if (e->opt.pc == FDM_PC_NONE) {
-    copy(3 * e->n, r, z, st);
-    mask3(e, z, st);
-    e->launches += 4;
-  } else if (e->opt.pc == FDM_PC_ASM) {
-    if (fp64) elast_sdc<double, double, double>(e, r, z, e->omega, st);
-    else elast_sdc<float, double, double>(e, r, z, e->omega, st);
-  } else {
-    if (fp64) elast_vcycle<double>(e, r, z, e->v1, e->v3, st);
-    else elast_vcycle<float>(e, r, z, e->f1, e->f3, st);
-  }
-}
-
-__global__ void k_permute_sym(int m, int nq, const double *__restrict__ in, double *__restrict__ out) {
-  // out is component-major (a nq + v), in interleaved (3 v + a)
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)m * m;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(t / m), j = (int)(t % m);
-    const int pi = 3 * (i % nq) + i / nq, pj = 3 * (j % nq) + j / nq;
-    out[t] = in[(int64_t)pi * m + pj];
-  }
-}
-
-// vector Q1 coarse problem: cell stiffness of Q1 elasticity by 2-point Gauss
-// (exact on box cells), banded Cholesky in vertex-interleaved order, dense
-// inverse on the device, permuted to component-major order
-void elast_setup_coarse(fdm_elast *e, cudaStream_t st) {
-  const fdm_ctx *c0 = e->comp[0];
-  const int nx = e->g.nx, ny = e->g.ny, nz = e->g.nz, nvx = nx + 1, nvy = ny + 1;
-  const int mx = nx - 1, my = ny - 1;
-  e->nq = c0->nc;
-  e->m = 3 * e->nq;
-  e->rc64 = e->alloc<double>(e->m);
-  e->xc64 = e->alloc<double>(e->m);
-  e->rc32 = e->alloc<float>(e->m);
-  e->xc32 = e->alloc<float>(e->m);
-  if (e->m == 0) return;
-  const int m = e->m, bw = 3 * (1 + mx + mx * my) + 2;
-  std::vector<double> Lb((size_t)m * (bw + 1), 0.0);
-  const double gp = 1.0 / std::sqrt(3.0);
-  for (int cz = 0; cz < nz; ++cz)
-    for (int cy = 0; cy < ny; ++cy)
-      for (int cx = 0; cx < nx; ++cx) {
-        const double L[3] = {0.5 * (c0->vert[0][cx + 1] - c0->vert[0][cx]), 0.5 * (c0->vert[1][cy + 1] - c0->vert[1][cy]),
-                             0.5 * (c0->vert[2][cz + 1] - c0->vert[2][cz])};
-        const double vol = L[0] * L[1] * L[2];
-        int f[8];
-        for (int s = 0; s < 8; ++s) {
-          const int vx = cx + (s & 1), vy = cy + ((s >> 1) & 1), vz = cz + (s >> 2);
-          const bool inner = vx > 0 && vy > 0 && vz > 0 && vx < nx && vy < ny && vz < nz;
-          f[s] = inner ? (vx - 1) + mx * ((vy - 1) + my * (vz - 1)) : -1;
-        }
-        (void)nvx;
-        (void)nvy;
-        double K[24][24] = {};
-        for (int qp = 0; qp < 8; ++qp) {
-          const double xi[3] = {(qp & 1) ? gp : -gp, ((qp >> 1) & 1) ? gp : -gp, (qp >> 2) ? gp : -gp};
-          double dphi[8][3];
-          for (int s = 0; s < 8; ++s) {
-            const double sg[3] = {(s & 1) ? 1.0 : -1.0, ((s >> 1) & 1) ? 1.0 : -1.0, (s >> 2) ? 1.0 : -1.0};
-            const double h[3] = {0.5 * (1 + sg[0] * xi[0]), 0.5 * (1 + sg[1] * xi[1]), 0.5 * (1 + sg[2] * xi[2])};
-            dphi[s][0] = 0.5 * sg[0] * h[1] * h[2] / L[0];
-            dphi[s][1] = 0.5 * sg[1] * h[0] * h[2] / L[1];
-            dphi[s][2] = 0.5 * sg[2] * h[0] * h[1] / L[2];
-          }
-          for (int s = 0; s < 8; ++s)
-            for (int a = 0; a < 3; ++a)
-              for (int t = 0; t < 8; ++t)
-                for (int b = 0; b < 3; ++b) {
-                  double v = e->mu * dphi[s][b] * dphi[t][a] + e->lam * dphi[s][a] * dphi[t][b];
-                  if (a == b) v += e->mu * (dphi[s][0] * dphi[t][0] + dphi[s][1] * dphi[t][1] + dphi[s][2] * dphi[t][2]);
-                  K[3 * s + a][3 * t + b] += vol * v;
-                }
-        }
-        for (int s = 0; s < 8; ++s)
-          for (int t = 0; t < 8; ++t) {
-            if (f[s] < 0 || f[t] < 0) continue;
-            for (int a = 0; a < 3; ++a)
-              for (int b = 0; b < 3; ++b) {
-                const int i = 3 * f[s] + a, j = 3 * f[t] + b;
-                if (j <= i) Lb[(size_t)i * (bw + 1) + (i - j)] += K[3 * s + a][3 * t + b];
-              }
-          }
-      }
-  banded_cholesky(m, bw, Lb);
-  double *dLb = e->upload(Lb);
-  double *inv_il = e->alloc<double>((size_t)m * m);
-  e->Ainv64 = e->alloc<double>((size_t)m * m);
-  e->Ainv32 = e->alloc<float>((size_t)m * m);
-  launch_banded_inverse(m, bw, dLb, inv_il, st);
-  k_permute_sym<<<vec_blocks((int64_t)m * m), 256, 0, st>>>(m, e->nq, inv_il, e->Ainv64);
-  launch_convert<double, float>((int64_t)m * m, e->Ainv64, e->Ainv32, st);
-  FDM_CUDA(cudaStreamSynchronize(st));
-  FDM_CUDA(cudaGetLastError());
-}
-
-// omega from k CG-Lanczos steps on A_SDC^{-1} A (undamped SDC relaxation), FP64
-void elast_lanczos(fdm_elast *e, const double *start_host, cudaStream_t st) {
-  const int64_t n3 = 3 * e->n;
-  std::vector<double> b0;
-  if (start_host) b0.assign(start_host, start_host + n3);
-  else normal_vector(e->opt.lanczos_seed, n3, b0);
-  FDM_CUDA(cudaMemcpyAsync(e->r, b0.data(), n3 * sizeof(double), cudaMemcpyHostToDevice, st));
-  mask3(e, e->r, st);
-  elast_sdc<double, double, double>(e, e->r, e->z, 1.0, st);
-  FDM_CUDA(cudaMemcpyAsync(e->d, e->z, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  double h[2];
-  launch_dot(n3, e->r, e->z, e->partial, e->dots, st);
-  FDM_CUDA(cudaMemcpyAsync(h, e->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
-  FDM_CUDA(cudaStreamSynchronize(st));
-  double rz = h[0];
-  std::vector<double> al, be;
-  for (int k = 0; k < e->opt.lanczos_steps; ++k) {
-    if (!(rz > 0.0)) break;
-    elast_op<double, double>(e, e->d, e->q, nullptr, st);
-    launch_dot(n3, e->d, e->q, e->partial, e->dots, st);
-    FDM_CUDA(cudaMemcpyAsync(h, e->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
-    FDM_CUDA(cudaStreamSynchronize(st));
-    if (!(h[0] > 0.0)) break;
-    const double alpha = rz / h[0];
-    al.push_back(alpha);
-    launch_axpby<double>(n3, -alpha, e->q, 1.0, e->r, e->r, st);
-    elast_sdc<double, double, double>(e, e->r, e->z, 1.0, st);
-    launch_dot(n3, e->r, e->z, e->partial, e->dots, st);
-    FDM_CUDA(cudaMemcpyAsync(h, e->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
-    FDM_CUDA(cudaStreamSynchronize(st));
-    const double beta = h[0] / rz;
-    be.push_back(beta);
-    rz = h[0];
-    launch_axpby<double>(n3, 1.0, e->z, beta, e->d, e->d, st);
-  }
-  const int m = (int)al.size();
-  if (m < 1) fail(FDM_EINVAL, "Lanczos: no steps could be taken");
-  std::vector<double> dd(m), ee(std::max(m - 1, 1), 0.0);
-  for (int j = 0; j < m; ++j) {
-    dd[j] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
-    if (j + 1 < m) ee[j] = std::sqrt(be[j]) / al[j];
-  }
-  tridiag_extremes(dd, ee, e->lmin, e->lmax);
-  e->omega = 2.0 / (1.25 * e->lmax + 0.75 * e->lmin);
-}
-
-}  // namespace
+template void ctx_run_asm<double, double, double>(fdm_ctx *, const double *, double *, double, cudaStream_t,
+                                                  const double *);
+template void ctx_run_asm<float, double, float>(fdm_ctx *, const double *, float *, double, cudaStream_t, const float *);
+template void ctx_run_asm<float, float, double>(fdm_ctx *, const float *, double *, double, cudaStream_t, const float *);
+template void ctx_run_asm<float, double, double>(fdm_ctx *, const double *, double *, double, cudaStream_t,
+                                                 const float *);
+}  // namespace fdm
 
 // ====================================================================== C-ABI
 extern "C" {
@@ -2325,218 +1890,5 @@ void fdm_destroy(fdm_ctx *c) {
   delete c->solo;
   delete c;
 }
-
-// ---------------------------------------------------------------- linear elasticity (Section 4.1)
-int fdm_elast_setup(const fdm_mesh *mesh, int p, double mu, double lam, const fdm_options *opt, fdm_elast **out,
-                    void *stream) {
-  if (!out) return FDM_EINVAL;
-  *out = nullptr;
-  if (!mesh || !mesh->xv || !mesh->yv || !mesh->zv || mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || p < 1 ||
-      p > 15 || !(mu > 0.0) || !(lam >= 0.0) || !std::isfinite(mu) || !std::isfinite(lam)) {
-    g_last_error = "fdm_elast_setup: invalid mesh, degree (1..15) or Lame parameters (mu > 0, lambda >= 0)";
-    return FDM_EINVAL;
-  }
-  if (mesh->jac) {
-    g_last_error = "fdm_elast_setup: box cells only (mesh->jac must be NULL)";
-    return FDM_EINVAL;
-  }
-  fdm_elast *e = new fdm_elast();
-  try {
-    cudaStream_t st = (cudaStream_t)stream;
-    if (opt) e->opt = *opt;
-    else fdm_default_options(&e->opt);
-    if (e->opt.lanczos_steps <= 0) e->opt.lanczos_steps = 20;
-    if (e->opt.flexible_beta < 0) e->opt.flexible_beta = e->opt.precision == FDM_PREC_FP32 ? 1 : 0;
-    e->mu = mu;
-    e->lam = lam;
-    const int nx = mesh->nx, ny = mesh->ny, nz = mesh->nz, ncell = nx * ny * nz;
-    std::vector<double> L(3 * (size_t)ncell);
-    for (int cz = 0; cz < nz; ++cz)
-      for (int cy = 0; cy < ny; ++cy)
-        for (int cx = 0; cx < nx; ++cx) {
-          const int c = cx + nx * (cy + ny * cz);
-          L[3 * c] = 0.5 * (mesh->xv[cx + 1] - mesh->xv[cx]);
-          L[3 * c + 1] = 0.5 * (mesh->yv[cy + 1] - mesh->yv[cy]);
-          L[3 * c + 2] = 0.5 * (mesh->zv[cz + 1] - mesh->zv[cz]);
-        }
-    // the scalar contexts of the SDC blocks: exact separable coefficients
-    fdm_options copt = e->opt;
-    copt.pc = FDM_PC_ASM;
-    copt.omega = 1.0;
-    copt.lanczos_start = nullptr;
-    copt.pcg_graph = 0;
-    copt.kernel_timing = 0;
-    for (int a = 0; a < 3; ++a) {
-      std::vector<double> mua(3 * (size_t)ncell);
-      for (int c = 0; c < ncell; ++c) {
-        const double vol = L[3 * c] * L[3 * c + 1] * L[3 * c + 2];
-        for (int d = 0; d < 3; ++d)
-          mua[3 * c + d] = (mu + (d == a ? mu + lam : 0.0)) * vol / (L[3 * c + d] * L[3 * c + d]);
-      }
-      fdm_coeff cf{nullptr, nullptr, mua.data()};
-      const int rc = fdm_setup(mesh, p, &cf, &copt, &e->comp[a], stream);
-      if (rc != FDM_OK) fail(rc, "SDC block " + std::to_string(a) + ": " + g_last_error);
-    }
-    e->g = e->comp[0]->g;
-    e->n = e->g.ndof;
-    e->Lc = e->upload(L);
-    e->wq64 = e->upload(e->comp[0]->basis.wq);
-    e->wq32 = e->upload(std::vector<float>(e->comp[0]->basis.wq.begin(), e->comp[0]->basis.wq.end()));
-    const size_t cn = (size_t)ncell * e->g.n * e->g.n * e->g.n;
-    e->G64 = e->alloc<double>(9 * cn);
-    e->E64 = e->alloc<double>(3 * cn);
-    if (e->opt.precision == FDM_PREC_FP32) {
-      e->G32 = e->alloc<float>(9 * cn);
-      e->E32 = e->alloc<float>(3 * cn);
-      e->f1 = e->alloc<float>(3 * e->n);
-      e->f3 = e->alloc<float>(3 * e->n);
-    }
-    for (double **v : {&e->r, &e->z, &e->zold, &e->d, &e->q, &e->v1, &e->v3}) *v = e->alloc<double>(3 * e->n);
-    e->partial = e->alloc<double>(2 * DOT_BLOCKS);
-    e->dots = e->alloc<double>(4);
-    e->sc = e->alloc<double>(16);
-    elast_setup_coarse(e, st);
-    if (e->opt.omega > 0.0) e->omega = e->opt.omega;
-    else elast_lanczos(e, e->opt.lanczos_start, st);
-    FDM_CUDA(cudaStreamSynchronize(st));
-    FDM_CUDA(cudaGetLastError());
-  } catch (const Error &err) {
-    g_last_error = err.msg;
-    delete e;
-    return err.code;
-  }
-  *out = e;
-  return FDM_OK;
-}
-
-int elast_apply(fdm_elast *e, const double *u, double *y, void *stream) {
-  if (!e || !u || !y) return FDM_EINVAL;
-  try {
-    elast_op<double, double>(e, u, y, nullptr, (cudaStream_t)stream);
-    FDM_CUDA(cudaGetLastError());
-  } catch (const Error &err) { return handle_elast(e, err); }
-  return FDM_OK;
-}
-
-int elast_pc_apply(fdm_elast *e, const double *r, double *z, void *stream) {
-  if (!e || !r || !z) return FDM_EINVAL;
-  try {
-    elast_pc(e, r, z, (cudaStream_t)stream);
-    FDM_CUDA(cudaGetLastError());
-  } catch (const Error &err) { return handle_elast(e, err); }
-  return FDM_OK;
-}
-
-int elast_pcg_solve(fdm_elast *e, const double *b, double *x, double rtol, int maxit, fdm_solve_info *info,
-                    void *stream) {
-  if (!e || !b || !x || maxit < 0 || !(rtol >= 0.0)) return FDM_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
-  const int64_t n3 = 3 * e->n;
-  try {
-    cudaEvent_t e0, e1;
-    FDM_CUDA(cudaEventCreate(&e0));
-    FDM_CUDA(cudaEventCreate(&e1));
-    FDM_CUDA(cudaEventRecord(e0, st));
-    double hsc[16] = {0};
-    hsc[7] = e->opt.flexible_beta ? 1.0 : 0.0;
-    FDM_CUDA(cudaMemcpyAsync(e->sc, hsc, sizeof hsc, cudaMemcpyHostToDevice, st));
-    FDM_CUDA(cudaMemsetAsync(x, 0, n3 * sizeof(double), st));
-    FDM_CUDA(cudaMemcpyAsync(e->r, b, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    mask3(e, e->r, st);
-    double h[2];
-    launch_dot(n3, e->r, e->r, e->partial, e->dots, st);
-    e->launches += 5;
-    FDM_CUDA(cudaMemcpyAsync(h, e->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
-    FDM_CUDA(cudaStreamSynchronize(st));
-    const double nb = std::sqrt(h[0]);
-    double nr = nb;
-    int it = 0, conv = nb == 0.0, bad = 0;
-    double *z = e->z, *zold = e->zold;
-    if (!conv) {
-      elast_pc(e, e->r, z, st);
-      launch_dot(n3, e->r, z, e->partial, e->dots, st);
-      launch_pcg_scalars(2, e->sc, e->dots, st);
-      FDM_CUDA(cudaMemcpyAsync(e->d, z, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      e->launches += 3;
-      while (it < maxit) {
-        elast_op<double, double>(e, e->d, e->q, nullptr, st);
-        launch_dot(n3, e->d, e->q, e->partial, e->dots, st);
-        launch_pcg_scalars(0, e->sc, e->dots, st);
-        launch_pcg_update_xr(n3, e->sc, e->d, e->q, x, e->r, st);
-        ++it;
-        launch_dot(n3, e->r, e->r, e->partial, e->dots + 2, st);
-        e->launches += 6;
-        FDM_CUDA(cudaMemcpyAsync(h, e->dots + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
-        FDM_CUDA(cudaStreamSynchronize(st));
-        nr = std::sqrt(h[0]);
-        if (!std::isfinite(nr)) { bad = 1; break; }
-        if (nr <= rtol * nb) { conv = 1; break; }
-        std::swap(z, zold);
-        elast_pc(e, e->r, z, st);
-        launch_dot2(n3, e->r, z, zold, e->partial, e->dots, st);
-        launch_pcg_scalars(1, e->sc, e->dots, st);
-        launch_pcg_update_d(n3, e->sc, z, e->d, st);
-        e->launches += 4;
-      }
-    }
-    FDM_CUDA(cudaEventRecord(e1, st));
-    FDM_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    FDM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    FDM_CUDA(cudaMemcpy(hsc, e->sc, sizeof hsc, cudaMemcpyDeviceToHost));
-    if (hsc[8] != 0.0) bad = 1;
-    for (fdm_ctx *c : e->comp) {
-      int hstat = 0;
-      FDM_CUDA(cudaMemcpy(&hstat, c->status, sizeof(int), cudaMemcpyDeviceToHost));
-      if (hstat) {
-        FDM_CUDA(cudaMemset(c->status, 0, sizeof(int)));
-        fail(FDM_ETIMEOUT, "a bounded device-side wait of the patch solve ran out");
-      }
-    }
-    if (info) {
-      info->iterations = it;
-      info->converged = conv;
-      info->rnorm0 = nb;
-      info->rnorm = nr;
-      info->seconds = ms * 1e-3;
-      elast_op<double, double>(e, x, e->v1, b, st);  // b - A x
-      mask3(e, e->v1, st);
-      launch_dot(n3, e->v1, e->v1, e->partial, e->dots, st);
-      e->launches += 4;
-      FDM_CUDA(cudaMemcpyAsync(h, e->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
-      FDM_CUDA(cudaStreamSynchronize(st));
-      info->true_rnorm = std::sqrt(h[0]);
-    }
-    FDM_CUDA(cudaGetLastError());
-    if (bad) { e->err = "non-finite scalar in PCG"; return FDM_ENAN; }
-    if (!conv) { e->err = "PCG reached maxit"; return FDM_ENOCONV; }
-  } catch (const Error &err) { return handle_elast(e, err); }
-  return FDM_OK;
-}
-
-int fdm_elast_query(fdm_elast *e, int what, void *out, size_t *len) {
-  if (!e || !out || !len) return FDM_EINVAL;
-  try {
-    auto put = [&](const void *src, size_t bytes) {
-      if (*len < bytes) fail(FDM_EINVAL, "fdm_elast_query: buffer too small (" + std::to_string(bytes) + " bytes needed)");
-      std::memcpy(out, src, bytes);
-      *len = bytes;
-    };
-    switch (what) {
-      case FDM_Q_NDOF: { int64_t v = e->n; put(&v, sizeof v); break; }
-      case FDM_Q_OMEGA: put(&e->omega, sizeof(double)); break;
-      case FDM_Q_LAMBDA: { double v[2] = {e->lmin, e->lmax}; put(v, sizeof v); break; }
-      case FDM_Q_LAUNCHES: { int64_t v = e->launches; e->launches = 0; put(&v, sizeof v); break; }
-      default: fail(FDM_EINVAL, "fdm_elast_query: unknown quantity");
-    }
-  } catch (const Error &err) { return handle_elast(e, err); }
-  return FDM_OK;
-}
-
-const char *fdm_elast_last_error(const fdm_elast *e) { return e ? e->err.c_str() : g_last_error.c_str(); }
-
-void fdm_elast_destroy(fdm_elast *e) { delete e; }
 
 }  // extern "C"
