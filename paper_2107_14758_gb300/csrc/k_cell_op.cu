@@ -78,7 +78,10 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_box_op(Grid g, c
   constexpr int ES = EO<T, N>::S;
   T *tA = reinterpret_cast<T *>(smem_), *tB = tA + ES;
   const int c = threadIdx.x / L, l = threadIdx.x % L;
-  T *U = tB + ES + c * 4 * PS, *B1 = U + PS, *B2 = B1 + PS, *B3 = B2 + PS;
+  // two buffers per cell: every pass reads a thread's whole line into registers
+  // before writing the same line's positions, so results overwrite their inputs
+  T *U = tB + ES + c * 2 * PS, *V = U + PS;
+  T *B1 = U, *B2 = V, *B3 = V;
   const int cell = blockIdx.x * CPB + c;
   const bool valid = cell < g.ncell;
   EO<T, N>::build(tab + tab_off(TAB_A, N), tA, threadIdx.x, blockDim.x);
@@ -345,7 +348,7 @@ bool launch_box_op_fast(const OpArgs &a, const Tin *u, Tout *y, T *E, cudaStream
         k_gen_op<T, Tin, N><<<(a.g.ncell + CPB - 1) / CPB, CPB * N * N, sm, st>>>(
             a.g, tab, reinterpret_cast<const T *>(a.Gw), u, E);
       } else {
-        const size_t sm = sizeof(T) * (2 * EO<T, N>::S + (size_t)CPB * 4 * psize<N>());
+        const size_t sm = sizeof(T) * (2 * EO<T, N>::S + (size_t)CPB * 2 * psize<N>());
         set_smem(k_box_op<T, Tin, N>, sm);
         k_box_op<T, Tin, N><<<(a.g.ncell + CPB - 1) / CPB, CPB * N * N, sm, st>>>(a.g, a.mu_box, tab, u, E);
       }
