@@ -620,17 +620,17 @@ void launch_interp_fdm(const InterpArgs<T> &a, double omega, Tout *z, cudaStream
 // the dense L21 block of the factor is not stored, and W is read once where
 // Z = L_TT^{-1} is read twice (forward and backward).
 
-// u = S_BB^{-1} in over the lower block (n0 + n1 entries) in three phases:
+// u = S_BB^{-1} in over the lower block (n0 + n1 entries; t1: n1 scratch) in three phases:
 //   t_1 = g_1 - L_10 (D_0^{-1} g_0)            (y_0 = L_00^{-1} g_0 formed where used)
-//   u_1 = L_11^{-T} L_11^{-1} t_1              (a warp per line: both line solves)
+//   u_1 = (L_11 L_11^T)^{-1} t_1               (the symmetric inverse of each line block,
+//                                               stored in place of the line inverse)
 //   u_0 = L_00^{-T} (y_0 - L_10^T u_1)
 // out may alias in (each phase reads in only at indices it or an earlier phase
 // owns).  fin, when given, also receives y - u (the final lower values).
 template <typename T, int NT>
-__device__ __forceinline__ void bb_solve(const ClassDev &C, const T *Lv, const T *in, T *out, T *t1, T *z1,
+__device__ __forceinline__ void bb_solve(const ClassDev &C, const T *Lv, const T *in, T *out, T *t1,
                                          const T *y = nullptr, T *fin = nullptr) {
-  constexpr int NW = NT / 32;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, n0 = C.n0, n1 = C.n1;
+  const int tid = threadIdx.x, n0 = C.n0, n1 = C.n1;
   const T *dinv0 = Lv + C.off_dinv0, *ell = Lv + C.off_ell;
   for (int r = tid; r < n1; r += NT) {
     T acc = 0;
@@ -642,21 +642,13 @@ __device__ __forceinline__ void bb_solve(const ClassDev &C, const T *Lv, const T
     t1[r] = in[n0 + r] - acc;
   }
   __syncthreads();
-  for (int b = warp; b < C.nlines; b += NW) {
-    const int s0 = C.line_start[b], w = C.line_len[b];
-    const T *Lb = Lv + C.off_lines + C.line_off[b];  // w x w inverse of the line block, lower
-    for (int i = lane; i < w; i += 32) {
-      T acc = 0;
-      for (int cc = 0; cc <= i; ++cc) acc += Lb[i * w + cc] * t1[s0 + cc];
-      z1[s0 + i] = acc;
-    }
-    __syncwarp();
-    for (int i = lane; i < w; i += 32) {
-      T acc = 0;
-      for (int cc = i; cc < w; ++cc) acc += Lb[cc * w + i] * z1[s0 + cc];
-      out[n0 + s0 + i] = acc;
-      if (fin) fin[n0 + s0 + i] = y[n0 + s0 + i] - acc;
-    }
+  for (int r = tid; r < n1; r += NT) {  // one row of one line's symmetric block per thread
+    const int b = C.line_of[r], s0 = C.line_start[b], w = C.line_len[b], i = r - s0;
+    const T *Mb = Lv + C.off_lines + C.line_off[b];
+    T acc = 0;
+    for (int cc = 0; cc < w; ++cc) acc += Mb[cc * w + i] * t1[s0 + cc];
+    out[n0 + r] = acc;
+    if (fin) fin[n0 + r] = y[n0 + r] - acc;
   }
   __syncthreads();
   for (int j = tid; j < n0; j += NT) {
@@ -752,9 +744,9 @@ __device__ __forceinline__ void sc_patch_compute(const PatchSolveArgs<T> &a, con
   // gv: g, later r_B and u_B; yv: y_B, then x_T in its top part
   T *yv = gv + nG, *tmp = yv + nG;
   const int l1 = (C.n1 + 3) & ~3;
-  T *t1 = tmp, *z1 = tmp + l1, *acc = tmp + 2 * l1;
+  T *t1 = tmp, *acc = tmp + 2 * l1;  // tmp + l1: unused
   T *X = a.X + P.xoff;
-  bb_solve<T, NT>(C, Lh, gv, yv, t1, z1);  // y_B = S_BB^{-1} g_B
+  bb_solve<T, NT>(C, Lh, gv, yv, t1);  // y_B = S_BB^{-1} g_B
   const T *st = (stage_st ? Lh : Lv) + C.off_st;
   for (int t = tid; t < n2; t += NT) {  // v_T = g_T - S_TB y_B, in place
     T s = 0;
@@ -777,7 +769,7 @@ __device__ __forceinline__ void sc_patch_compute(const PatchSolveArgs<T> &a, con
     gv[cc] = s;
   }
   __syncthreads();
-  bb_solve<T, NT>(C, Lh, gv, gv, t1, z1, yv, X);  // u_B = S_BB^{-1} r_B in place, X_B = y_B - u_B
+  bb_solve<T, NT>(C, Lh, gv, gv, t1, yv, X);  // u_B = S_BB^{-1} r_B in place, X_B = y_B - u_B
 }
 
 template <typename T, int NT, int SRB, int MINB>

@@ -311,6 +311,29 @@ __global__ void __launch_bounds__(256) k_pack(FactorArgs a) {
     int64_t off = C.off_lines + C.line_off[b];
     tri_inverse(S + (int64_t)s0 * nG + s0, nG, w, V + off, w, W != nullptr, W ? W + off : nullptr);
   }
+  if (C.sc) {
+    // Schur-coupling form: both line solves at once, (L_b L_b^T)^{-1} = L_b^{-T} L_b^{-1}
+    // (symmetric, w x w) per line; formed in the line's block of the workspace, whose
+    // factor values are no longer needed, then written over the line inverse
+    __syncthreads();
+    double *Sw0 = a.S + (int64_t)slot * a.ldS;
+    for (int b = 0; b < C.nlines; ++b) {
+      const int s0 = n0 + C.line_start[b], w = C.line_len[b];
+      const int64_t off = C.off_lines + C.line_off[b];
+      for (int q = threadIdx.x; q < w * w; q += blockDim.x) {
+        const int i = q / w, j = q % w, k0 = i > j ? i : j;
+        double m = 0.0;
+        for (int k = k0; k < w; ++k) m += V[off + (int64_t)k * w + i] * V[off + (int64_t)k * w + j];
+        Sw0[(int64_t)(s0 + i) * nG + s0 + j] = m;
+      }
+    }
+    __syncthreads();
+    for (int b = 0; b < C.nlines; ++b) {
+      const int s0 = n0 + C.line_start[b], w = C.line_len[b];
+      const int64_t off = C.off_lines + C.line_off[b];
+      for (int q = threadIdx.x; q < w * w; q += blockDim.x) put(off + q, Sw0[(int64_t)(s0 + q / w) * nG + s0 + q % w]);
+    }
+  }
   if (!C.sc)
     for (int64_t q = threadIdx.x; q < (int64_t)n2 * C.ld21; q += blockDim.x) {
       int r = (int)(q / C.ld21), cc = (int)(q % C.ld21);
