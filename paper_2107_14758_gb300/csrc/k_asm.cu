@@ -734,6 +734,35 @@ __device__ __forceinline__ void sym_apply(const ClassDev &C, const T *Wv, const 
 // (cp.async.bulk) issued before the gather when they fit in a.headcap
 // elements; the mbarrier wait is bounded by a.timeout_ns (status word on
 // expiry).  W streams from global memory.
+// The gather of the Schur-coupling kernels: the star's cells in closed form
+// (slot s = x side + 2 y side + 4 z side: the lowest cell of the star plus
+// the sides' strides), so no shared table and no barrier; zeroes y and the
+// scratch (the range after g, which the gather fills completely).  The caller
+// ends the phase with a barrier.
+template <typename T, int NT>
+__device__ __forceinline__ void sc_gather(const PatchSolveArgs<T> &a, const PatchDev &P, const ClassDev &C, T *gv) {
+  const int tid = threadIdx.x;
+  const Grid &g = a.g;
+  const int n3 = g.n * g.n * g.n, nG = C.nG;
+  for (int i = nG + tid; i < 2 * nG + a.tmpcap; i += NT) gv[i] = T(0);
+  const int lo = star_cell_along(C.full[0], P.v[0], g.nx, 0) +
+                 g.nx * (star_cell_along(C.full[1], P.v[1], g.ny, 0) + g.ny * star_cell_along(C.full[2], P.v[2], g.nz, 0));
+  const int sy = g.nx, sz = g.nx * g.ny;
+  const T *E = a.E;
+  for (int k = tid; k < nG; k += NT) {
+    const int *src = C.gsrc + 8 * k;
+    T r = 0;
+    for (int e = 0; e < 8; ++e) {
+      const int code = src[e];
+      if (code < 0) break;
+      const int slot = code >> 16;
+      const int cell = lo + (slot & 1) + ((slot >> 1) & 1) * sy + (slot >> 2) * sz;
+      r += E[(int64_t)cell * n3 + (code & 0xffff)];
+    }
+    gv[k] = r;
+  }
+}
+
 // everything after the gather: Lh holds the values before S_TB (staged or
 // global), S_TB from Lh when stage_st else from global, W from global
 template <typename T, int NT, int SRB>
@@ -778,7 +807,6 @@ __global__ void __launch_bounds__(NT, MINB) k_patch_solve_sc(PatchSolveArgs<T> a
   const int tid = threadIdx.x;
   const PatchDev P = a.patches[a.order[blockIdx.x]];
   const ClassDev &C = a.cls[P.cls];
-  __shared__ int sCell[8];
   __shared__ __align__(8) uint64_t bar, stall;  // stall: test hook, never completed
   __shared__ int sFail;
   T *H = reinterpret_cast<T *>(smem_);  // a.headcap elements (a multiple of 4)
@@ -803,13 +831,16 @@ __global__ void __launch_bounds__(NT, MINB) k_patch_solve_sc(PatchSolveArgs<T> a
     const char *ws = reinterpret_cast<const char *>(Lv + C.off_z);
     for (uint32_t off = 0; off < wb; off += 32768) bulk::prefetch_l2(ws + off, wb - off < 32768 ? wb - off : 32768);
   }
-  patch_gather<T, NT, 2>(a, P, C, gv, sCell);  // also zeroes y and tmp (barriers inside)
+  __syncthreads();  // the barriers' initialisation and sFail are visible
+  sc_gather<T, NT>(a, P, C, gv);  // also zeroes y and tmp
   const T *Lh = Lv;
-  if (stage) {
+  if (stage) {  // the staging wait shares the gather's barrier
     bool ok = !a.inject_stall || bulk::mbar_wait_bounded(&stall, 0, a.timeout_ns);  // never completes
     ok = ok && bulk::mbar_wait_bounded(&bar, 0, a.timeout_ns);
     if (!ok) sFail = 1;
-    __syncthreads();
+  }
+  __syncthreads();
+  if (stage) {
     if (sFail) {
       bulk::mbar_wait_bounded(&bar, 0, a.timeout_ns);  // a second bounded wait for the copy in flight
       if (tid == 0) atomicExch(a.status, 1);
