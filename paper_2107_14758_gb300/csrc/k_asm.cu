@@ -118,6 +118,13 @@ __device__ __forceinline__ V4<double> load4(const double *p) {
   double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
   return {a.x, a.y, b.x, b.y};
 }
+__device__ __forceinline__ void store4(float *p, const V4<float> &v) {
+  *reinterpret_cast<float4 *>(p) = make_float4(v.x, v.y, v.z, v.w);
+}
+__device__ __forceinline__ void store4(double *p, const V4<double> &v) {
+  reinterpret_cast<double2 *>(p)[0] = make_double2(v.x, v.y);
+  reinterpret_cast<double2 *>(p)[1] = make_double2(v.z, v.w);
+}
 
 // L2 eviction-priority policies: the forward solve reads the factor's large
 // sections (L21, Z) as evict-last so that they survive until the backward
@@ -678,6 +685,9 @@ __device__ __forceinline__ void sym_apply(const ClassDev &C, const T *Wv, const 
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, n2 = C.n2;
   T *aw = acc + warp * ld;
+  // 128-bit shared accesses where v and the accumulators are 16-byte aligned
+  // (acc always is; v = g_T is when the lower block has a multiple of 4 rows)
+  const bool vec = ((reinterpret_cast<uintptr_t>(v) | reinterpret_cast<uintptr_t>(acc)) & 15) == 0;
   for (int r0 = warp * RB; r0 < n2; r0 += NW * RB) {
     T rs[RB], vr[RB];
     int ngu[RB];
@@ -697,22 +707,31 @@ __device__ __forceinline__ void sym_apply(const ClassDev &C, const T *Wv, const 
       V4<T> w[RB];
 #pragma unroll
       for (int u = 0; u < RB; ++u) w[u] = q4 < ngu[u] ? load4(row[u] + 4 * q4) : V4<T>{0, 0, 0, 0};
-      const T *vv = v + 4 * q4;  // padding entries of W are zero, v is finite there
       const int cb = 4 * q4;
+      const V4<T> vv = vec ? load4(v + cb) : V4<T>{v[cb], v[cb + 1], v[cb + 2], v[cb + 3]};  // padding of W is zero
       T c0 = 0, c1 = 0, c2 = 0, c3 = 0;
 #pragma unroll
       for (int u = 0; u < RB; ++u) {
-        rs[u] += w[u].x * vv[0] + w[u].y * vv[1] + w[u].z * vv[2] + w[u].w * vv[3];
+        rs[u] += w[u].x * vv.x + w[u].y * vv.y + w[u].z * vv.z + w[u].w * vv.w;
         const int r = r0 + u;
         c0 += (cb < r ? w[u].x : T(0)) * vr[u];
         c1 += (cb + 1 < r ? w[u].y : T(0)) * vr[u];
         c2 += (cb + 2 < r ? w[u].z : T(0)) * vr[u];
         c3 += (cb + 3 < r ? w[u].w : T(0)) * vr[u];
       }
-      aw[cb] += c0;
-      aw[cb + 1] += c1;
-      aw[cb + 2] += c2;
-      aw[cb + 3] += c3;
+      if (vec) {
+        V4<T> a4 = load4(aw + cb);
+        a4.x += c0;
+        a4.y += c1;
+        a4.z += c2;
+        a4.w += c3;
+        store4(aw + cb, a4);
+      } else {
+        aw[cb] += c0;
+        aw[cb + 1] += c1;
+        aw[cb + 2] += c2;
+        aw[cb + 3] += c3;
+      }
     }
     multi_warp_sum<T, RB>(rs, lane);
     if ((lane & (32 / RB - 1)) == 0) {
@@ -773,7 +792,8 @@ __device__ __forceinline__ void sc_patch_compute(const PatchSolveArgs<T> &a, con
   // gv: g, later r_B and u_B; yv: y_B, then x_T in its top part
   T *yv = gv + nG, *tmp = yv + nG;
   const int l1 = (C.n1 + 3) & ~3;
-  T *t1 = tmp, *acc = tmp + 2 * l1;  // tmp + l1: unused
+  // acc at a 16-byte aligned offset from gv (gv itself is aligned): tmp has 4 elements of slack
+  T *t1 = tmp, *acc = gv + ((2 * nG + 2 * l1 + 3) & ~3);
   T *X = a.X + P.xoff;
   bb_solve<T, NT>(C, Lh, gv, yv, t1);  // y_B = S_BB^{-1} g_B
   const T *st = (stage_st ? Lh : Lv) + C.off_st;
@@ -926,7 +946,7 @@ __global__ void __launch_bounds__(NT, MINB) k_patch_solve_scp(PatchSolveArgs<T> 
 
 int patch_sc_tmp(int maxN1, int maxN2, int threads) {
   const int l1 = (maxN1 + 3) & ~3, l2 = (maxN2 + 3) & ~3;
-  return 2 * l1 + (threads / 32) * l2;
+  return 2 * l1 + (threads / 32) * l2 + 4;  // + 4: the accumulators' 16-byte alignment
 }
 
 template <typename T>
