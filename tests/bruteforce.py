@@ -203,3 +203,94 @@ def dense_elasticity(p, xv, yv, zv, mu, lam, q=None):
                 full = np.concatenate([idx + a * N for a in range(3)])
                 M[np.ix_(full, full)] += K.reshape(3 * n ** 3, 3 * n ** 3)
     return M
+
+
+def dense_sipg(p, xv, yv, zv, eta, q=None):
+    """Dense SIPG matrix of the DQ_p Poisson problem (cell-major values, cells x
+    fastest, (z, y, x) inside a cell), weak Dirichlet condition on the whole
+    boundary, from explicit quadrature of the weak form in physical
+    coordinates: cell integrals of grad v . grad u; on every facet the
+    penalty eta |e| mean(1/|K|) [v].[u] and the two consistency terms
+    -[v].{grad u} - {grad v}.[u], with [w] = sum over the sides of w n_side
+    and {.} the mean of the sides (one side on the boundary)."""
+    nc = [len(xv) - 1, len(yv) - 1, len(zv) - 1]
+    verts = [np.asarray(a, dtype=float) for a in (xv, yv, zv)]
+    n = p + 1
+    q = q or n + 1
+    xg, wg = leg.leggauss(q)
+    polys = lagrange_polys(gll_nodes(p))
+    dpolys = [P.deriv() for P in polys]
+    ncell = nc[0] * nc[1] * nc[2]
+    N = ncell * n ** 3
+    M = np.zeros((N, N))
+
+    def cell_id(c):
+        return c[0] + nc[0] * (c[1] + nc[1] * c[2])
+
+    def geom(c):
+        lo = np.array([verts[a][c[a]] for a in range(3)])
+        w = np.array([verts[a][c[a] + 1] - verts[a][c[a]] for a in range(3)])
+        return lo, w
+
+    def eval_cell(c, pts):
+        """Values [npts, n^3] and physical gradients [npts, n^3, 3] of cell c's basis."""
+        lo, w = geom(c)
+        ref = 2.0 * (pts - lo) / w - 1.0
+        val1 = [np.array([[P(t) for P in polys] for t in ref[:, a]]) for a in range(3)]
+        der1 = [np.array([[P(t) for P in dpolys] for t in ref[:, a]]) * (2.0 / w[a]) for a in range(3)]
+        phi = np.einsum("qk,qj,qi->qkji", val1[2], val1[1], val1[0]).reshape(len(pts), -1)
+        g = np.stack([np.einsum("qk,qj,qi->qkji", val1[2], val1[1], der1[0]).reshape(len(pts), -1),
+                      np.einsum("qk,qj,qi->qkji", val1[2], der1[1], val1[0]).reshape(len(pts), -1),
+                      np.einsum("qk,qj,qi->qkji", der1[2], val1[1], val1[0]).reshape(len(pts), -1)], axis=-1)
+        return phi, g
+
+    cells = [(cx, cy, cz) for cz in range(nc[2]) for cy in range(nc[1]) for cx in range(nc[0])]
+    for c in cells:
+        lo, w = geom(c)
+        g1 = [lo[a] + 0.5 * w[a] * (xg + 1.0) for a in range(3)]
+        pts = np.stack(np.meshgrid(g1[0], g1[1], g1[2], indexing="ij"), axis=-1).reshape(-1, 3)
+        wt = np.einsum("i,j,k->ijk", wg, wg, wg).ravel() * np.prod(w / 2.0)
+        _, g = eval_cell(c, pts)
+        K = np.einsum("q,qia,qja->ij", wt, g, g)
+        s = cell_id(c) * n ** 3
+        M[s:s + n ** 3, s:s + n ** 3] += K
+    for c in cells:
+        lo, w = geom(c)
+        volK = np.prod(w)
+        for a in range(3):
+            for side in (0, 1):                      # the low (0) or high (1) face of c normal to axis a
+                nb = list(c)
+                nb[a] += 1 if side else -1
+                inside = 0 <= nb[a] < nc[a]
+                if inside and side == 0:
+                    continue                         # each interior facet once, from its low cell
+                t = [b for b in range(3) if b != a]
+                area = w[t[0]] * w[t[1]]
+                ft = [lo[b] + 0.5 * w[b] * (xg + 1.0) for b in t]
+                P1, P2 = np.meshgrid(ft[0], ft[1], indexing="ij")
+                pts = np.zeros((q * q, 3))
+                pts[:, t[0]], pts[:, t[1]] = P1.ravel(), P2.ravel()
+                pts[:, a] = lo[a] + (w[a] if side else 0.0)
+                ws = np.einsum("i,j->ij", wg, wg).ravel() * area / 4.0
+                normal = np.zeros(3)
+                normal[a] = 1.0 if side else -1.0    # outward normal of c
+                phi, g = eval_cell(c, pts)
+                if inside:
+                    nbt = tuple(nb)
+                    phin, gn = eval_cell(nbt, pts)
+                    volN = np.prod(geom(nbt)[1])
+                    hinv = area * 0.5 * (1.0 / volK + 1.0 / volN)
+                    # jumps along the normal of c: v_c n_c + v_nb (-n_c)
+                    J = np.concatenate([phi, -phin], axis=1)
+                    G = 0.5 * np.concatenate([g @ normal, gn @ normal], axis=1)
+                    idx = np.concatenate([cell_id(c) * n ** 3 + np.arange(n ** 3),
+                                          cell_id(nbt) * n ** 3 + np.arange(n ** 3)])
+                else:
+                    hinv = area / volK
+                    J = phi
+                    G = g @ normal
+                    idx = cell_id(c) * n ** 3 + np.arange(n ** 3)
+                F = (eta * hinv * np.einsum("q,qi,qj->ij", ws, J, J)
+                     - np.einsum("q,qi,qj->ij", ws, J, G) - np.einsum("q,qi,qj->ij", ws, G, J))
+                M[np.ix_(idx, idx)] += F
+    return M
