@@ -385,6 +385,7 @@ def bench_gpu(args):
         secondary["batched"] = bench_batched(dev, fdmpc, inputs)
         secondary["gmg"] = bench_gmg(dev, fdmpc, inputs)
         secondary["elasticity"] = bench_elasticity(dev, fdmpc, inputs)
+        secondary["sipg"] = bench_sipg(dev, fdmpc, inputs)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -516,6 +517,53 @@ def bench_gmg(dev, fdmpc, inputs):
            "mixed_true_rel_residual": info.true_rnorm / info.rnorm0,
            "setup_seconds": {"symbolic": setup[0], "factor": setup[1], "coarse": setup[2], "lanczos": setup[3]}}
     ctx.close()
+    return out
+
+
+def bench_sipg(dev, fdmpc, inputs):
+    """SIPG on DQ_7 (Section 5), 16^3 graded cells, 2.1 M values, eta = p(p+1):
+    PCG to 1e-8 with the hybrid V(1,1) (vertex-star Schwarz with exact star
+    solves, Q1 coarse space) in mixed precision and in FP64, and the FP32
+    relaxation sweep (3375 stars of 16^3 values, 8 launches) with its FLOP
+    rate: 6 line passes of 16^4 multiply-adds per star."""
+    import torch
+    p = 7
+    xv, yv, zv = inputs.graded_vertices(16, 7)
+    ndof = 16 ** 3 * (p + 1) ** 3
+    m = 2 * (p + 1)
+    stars = 15 ** 3
+    out = {"workload": "SIPG DQ_7, 16^3 graded cells (widths U(0.5, 1.5), seed 7), %d values, b ~ N(0,1)" % ndof}
+    b = torch.randn(ndof, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(7))
+    for name, prec in (("mixed", fdmpc.FDM_PREC_FP32), ("fp64", fdmpc.FDM_PREC_FP64)):
+        s = fdmpc.Sipg(p, xv, yv, zv, precision=prec, lanczos_start=inputs.lanczos_start(ndof))
+        x = torch.empty_like(b)
+        info = s.pcg_solve(b, x, rtol=RTOL, maxit=1000)[1]
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(torch.cuda.current_stream())
+        for _ in range(3):
+            info = s.pcg_solve(b, x, rtol=RTOL, maxit=1000)[1]
+        e1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        out[name] = {"ms_per_solve": ms, "solve_dofs_per_s": ndof / (ms * 1e-3), "iterations": info.iterations,
+                     "true_rel_residual": info.true_rnorm / info.rnorm0, "omega": s.omega}
+        if name == "mixed":
+            z = torch.empty_like(b)
+            for _ in range(3):
+                s.asm_apply(b, z)
+            torch.cuda.synchronize()
+            e0.record(torch.cuda.current_stream())
+            for _ in range(20):
+                s.asm_apply(b, z)
+            e1.record(torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            ms_sweep = e0.elapsed_time(e1) / 20
+            flops = 2.0 * 6 * m ** 4 * stars
+            out["fp32_sweep"] = {"ms": ms_sweep, "gflop": flops * 1e-9, "tflops": flops / (ms_sweep * 1e-3) * 1e-12}
+        s.close()
+    out["mixed_over_fp64"] = out["mixed"]["solve_dofs_per_s"] / out["fp64"]["solve_dofs_per_s"]
     return out
 
 

@@ -317,6 +317,48 @@ int fdm_elast_query(fdm_elast *e, int what, void *out, size_t *len);
 const char *fdm_elast_last_error(const fdm_elast *e);
 void fdm_elast_destroy(fdm_elast *e);
 
+/* ---- symmetric interior penalty DG, DQ_p (Section 5) ----
+ * The Poisson equation -div grad u = f discretised by SIPG on the DQ_p space
+ * of GLL Lagrange nodal functions: box cells only (mesh->jac NULL), at least
+ * 2 cells per axis, 1 <= p <= 10, homogeneous Dirichlet condition imposed
+ * weakly on the whole boundary.  Vectors are cell-major: value (i, j, k) of
+ * cell (cx, cy, cz) at ((cx + nx (cy + ny cz)) (p+1) + k) (p+1)^2 + j (p+1) + i,
+ * ndof = nx ny nz (p+1)^3 doubles (DEVICE).  The operator is
+ *   a(v, u) = sum_K int_K grad v.grad u + sum_e int_e eta h_e^{-1} [v].[u]
+ *             - [v].{grad u} - {grad v}.[u]   (interior facets and boundary),
+ * h_e^{-1} = |e| {|K|^{-1}}, eta > 0 (eta <= 0 selects the default p (p+1)).
+ * Relaxation: additive Schwarz over the vertex stars of the interior vertices
+ * ((2p+2)^3 values each, exact solves: on a Cartesian star the star matrix is
+ * a Kronecker sum of 1D two-cell pencils and is inverted by their
+ * eigendecompositions); coarse space: the conforming Q1 functions vanishing
+ * on the boundary (Galerkin operator: the Q1 stiffness, solved as for the
+ * conforming problem: opt->coarse_levels); preconditioner selected by
+ * opt->pc (FDM_PC_ASM: omega ASM; FDM_PC_VCYCLE: the hybrid V(1,1)) in
+ * opt->precision; omega from opt->lanczos_steps CG-Lanczos steps on
+ * ASM^{-1} A unless opt->omega > 0.  Errors as for the scalar problem
+ * (FDM_ENOTSPD if a star pencil is not positive definite: eta too small);
+ * fdm_sipg_last_error. */
+typedef struct fdm_sipg fdm_sipg;
+int fdm_sipg_setup(const fdm_mesh *mesh, int p, double eta, const fdm_options *opt, fdm_sipg **out, void *stream);
+/* y = A u */
+int sipg_apply(fdm_sipg *s, const double *u_dev, double *y_dev, void *stream);
+/* z = omega sum_v R_v^T A_v^{-1} R_v r (the 8 vertex parity classes, each one launch, in a fixed order) */
+int sipg_asm_apply(fdm_sipg *s, const double *r_dev, double *z_dev, void *stream);
+/* z = P^{-1} r (the preconditioner selected by opt->pc) */
+int sipg_pc_apply(fdm_sipg *s, const double *r_dev, double *z_dev, void *stream);
+/* for nv interior vertices (HOST list, index vx + (nx+1) (vy + (ny+1) vz)),
+ * out[k][(2p+2)^3] = A_v^{-1} R_v r in star order [Z][Y][X], X = a (p+1) + i
+ * for the cell at x offset a (0, 1) around the vertex (the same for Y, Z);
+ * FDM_EINVAL for a vertex that is not interior; synchronises the stream */
+int sipg_patch_solve(fdm_sipg *s, const double *r_dev, int nv, const int *vertices, double *out_dev, void *stream);
+/* PCG from x = 0 to ||r||_2 <= rtol ||b||_2 (host-driven loop) */
+int sipg_pcg_solve(fdm_sipg *s, const double *b_dev, double *x_dev, double rtol, int maxit, fdm_solve_info *info,
+                   void *stream);
+/* FDM_Q_NDOF (int64), FDM_Q_OMEGA, FDM_Q_LAMBDA, FDM_Q_LAUNCHES, FDM_Q_NPATCH (int32: stars) */
+int fdm_sipg_query(fdm_sipg *s, int what, void *out, size_t *len);
+const char *fdm_sipg_last_error(const fdm_sipg *s);
+void fdm_sipg_destroy(fdm_sipg *s);
+
 /* ---- introspection ---- */
 #define FDM_Q_NDOF 1         /* int64: number of grid nodes */
 #define FDM_Q_OMEGA 2        /* double: damping */

@@ -1262,6 +1262,17 @@ template void ctx_run_asm<float, double, float>(fdm_ctx *, const double *, float
 template void ctx_run_asm<float, float, double>(fdm_ctx *, const float *, double *, double, cudaStream_t, const float *);
 template void ctx_run_asm<float, double, double>(fdm_ctx *, const double *, double *, double, cudaStream_t,
                                                  const float *);
+template <typename T>
+void ctx_coarse_solve(fdm_ctx *c, cudaStream_t st) {
+  if (c->nc == 0) return;
+  if (c->gmg_L > 0) gmg_level<T>(c, 0, c->rc<T>(), c->xc<T>(), st);
+  else {
+    launch_dense_symv<T>(c->nc, c->Acinv<T>(), c->rc<T>(), c->xc<T>(), st);
+    c->launches += 1;
+  }
+}
+template void ctx_coarse_solve<double>(fdm_ctx *, cudaStream_t);
+template void ctx_coarse_solve<float>(fdm_ctx *, cudaStream_t);
 }  // namespace fdm
 
 // ====================================================================== C-ABI

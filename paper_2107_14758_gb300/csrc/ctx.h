@@ -202,4 +202,7 @@ std::string &ctx_last_error();
 // one relaxation sweep z = omega ASM(r) (+ addv) in precision T
 template <typename T, typename Tin, typename Tout>
 void ctx_run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st, const T *addv);
+// xc = A_c^{-1} rc on the context's Q1 vectors (exact, or one multigrid V-cycle), precision T
+template <typename T>
+void ctx_coarse_solve(fdm_ctx *c, cudaStream_t st);
 }  // namespace fdm

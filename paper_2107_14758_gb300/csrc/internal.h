@@ -53,6 +53,18 @@ struct GmgHostLevel {
 // in the vertex coordinates, Galerkin operators P^T A P.
 void gmg_coarsen(std::vector<GmgHostLevel> &lev, int max_levels);
 
+// ---------------------------------------------------------------- SIPG star pencils (Section 5)
+// l_i'(-1) and l_i'(+1) of the Lagrange basis on the nodes xi (first and last at -1, +1)
+void sipg_end_derivatives(const std::vector<double> &xi, std::vector<double> &dm, std::vector<double> &dp);
+// the 2n x 2n stiffness A and mass M (row-major, cell c0's values first) of a
+// star's 1D two-cell pencil: half-widths h0, h1 of the star's cells and hl, hr
+// of the cells beyond (<= 0: the domain boundary), penalty eta
+void sipg_star_pencil(int n, const double *A1, const double *B1, const double *dm, const double *dp, double eta,
+                      double h0, double h1, double hl, double hr, double *A, double *M);
+// A S = M S diag(lam), S^T M S = I (S row-major, column i = eigenvector i);
+// fails with FDM_ENOTSPD unless M and A are positive definite
+void sym_gen_eig(int m, const double *A, const double *M, double *S, double *lam);
+
 // one bulk copy of the streamed patch solve: kind | first << 8 | last << 9,
 // item range [a0, a1) (rows, lines or ELL slices), byte count, element offset
 enum { CK_DINV = 0, CK_ELL_F = 1, CK_LINES_F = 2, CK_L21_F = 3, CK_Z_F = 4, CK_Z_B = 5, CK_L21_B = 6,

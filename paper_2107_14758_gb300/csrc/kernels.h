@@ -187,6 +187,38 @@ size_t elast_smem(int n);
 template <typename T, typename Tin>
 void launch_elast_cells(const Grid &g, const Tin *u, const T *tab, const T *wq, const double *Lc, double mu, double lam,
                         T *G, T *E, cudaStream_t st);
+// SIPG on DQ_p box cells (Section 5): cell-major vectors, (p+1)^3 values per cell
+constexpr int SIPG_MAX_N = 11;  // p <= 10
+template <typename T>
+struct SipgDev {
+  int p = 0, n = 0, nx = 0, ny = 0, nz = 0, ncell = 0;
+  double eta = 0.0;
+  const double *hx = nullptr, *hy = nullptr, *hz = nullptr;  // half-widths per axis
+  const T *tab = nullptr;  // A_hat, B_hat (n x n), l_i'(-1), l_i'(+1), GLL nodes (n each)
+  // per axis a and interior vertex v (1..nc_a - 1): the 1D star pencil's
+  // eigenvectors S[soff[a] + (v - 1) (2n)^2] (row-major, column i = vector i)
+  // and eigenvalues lam[loff[a] + (v - 1) 2n]
+  const T *S = nullptr, *lam = nullptr;
+  int64_t soff[3] = {0, 0, 0}, loff[3] = {0, 0, 0};
+};
+template <typename T>
+size_t sipg_cell_smem(int n);
+template <typename T>
+size_t sipg_patch_smem(int n);
+// y = A u, or y = rsub - A u (rsub != nullptr); F: face data [ncell][12][n^2]
+template <typename T, typename Tin>
+void launch_sipg_op(const SipgDev<T> &d, const Tin *u, T *F, const double *rsub, T *y, cudaStream_t st);
+// the stars of one vertex parity class (color = px | py << 1 | pz << 2, nblocks
+// of them), or of the listed vertices (vlist): z += omega A_v^{-1} R_v r on
+// their cells, or (zpatch != nullptr) A_v^{-1} R_v r into zpatch[block][(2n)^3]
+template <typename T, typename Tin, typename Tout>
+void launch_sipg_patch(const SipgDev<T> &d, int color, int nblocks, const int *vlist, const Tin *r, Tout *z,
+                       T *zpatch, double omega, cudaStream_t st);
+template <typename T, typename Tin>
+void launch_sipg_restrict(const SipgDev<T> &d, const Tin *r, const int *cfree, T *cellbuf, T *rc, cudaStream_t st);
+template <typename T>
+void launch_sipg_prolong(const SipgDev<T> &d, const int *cfree, const T *xc, T *x, cudaStream_t st);  // x += P xc
+
 template <typename T>
 struct GmgDev {
   int m[3] = {0, 0, 0};

@@ -105,6 +105,16 @@ def load():
     L.fdm_elast_last_error.restype = C.c_char_p
     L.fdm_elast_destroy.argtypes = [vp]
     L.fdm_elast_destroy.restype = None
+    L.fdm_sipg_setup.argtypes = [C.POINTER(fdm_mesh), C.c_int, C.c_double, C.POINTER(fdm_options), C.POINTER(vp), vp]
+    for f in ("sipg_apply", "sipg_asm_apply", "sipg_pc_apply"):
+        getattr(L, f).argtypes = [vp, vp, vp, vp]
+    L.sipg_patch_solve.argtypes = [vp, vp, C.c_int, ip, vp, vp]
+    L.sipg_pcg_solve.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.POINTER(fdm_solve_info), vp]
+    L.fdm_sipg_query.argtypes = [vp, C.c_int, vp, C.POINTER(C.c_size_t)]
+    L.fdm_sipg_last_error.argtypes = [vp]
+    L.fdm_sipg_last_error.restype = C.c_char_p
+    L.fdm_sipg_destroy.argtypes = [vp]
+    L.fdm_sipg_destroy.restype = None
     _lib = L
     return L
 
@@ -213,6 +223,55 @@ def fdm_elast_query(e, what, out):
 
 def fdm_elast_destroy(e):
     load().fdm_elast_destroy(e)
+
+
+def _check_sipg(rc, s=None):
+    if rc < 0:
+        raise FdmError(rc, load().fdm_sipg_last_error(s).decode())
+    return rc
+
+
+def fdm_sipg_setup(mesh, p, eta, opt, stream=None):
+    h = C.c_void_p()
+    _check_sipg(load().fdm_sipg_setup(C.byref(mesh), p, eta, C.byref(opt), C.byref(h), _stream(stream)))
+    return h
+
+
+def sipg_apply(s, u, y, stream=None):
+    _check_sipg(load().sipg_apply(s, _tptr(u), _tptr(y), _stream(stream)), s)
+
+
+def sipg_asm_apply(s, r, z, stream=None):
+    _check_sipg(load().sipg_asm_apply(s, _tptr(r), _tptr(z), _stream(stream)), s)
+
+
+def sipg_pc_apply(s, r, z, stream=None):
+    _check_sipg(load().sipg_pc_apply(s, _tptr(r), _tptr(z), _stream(stream)), s)
+
+
+def sipg_patch_solve(s, r, vertices, out, stream=None):
+    v = np.ascontiguousarray(vertices, dtype=np.int32)
+    _check_sipg(load().sipg_patch_solve(s, _tptr(r), len(v), v.ctypes.data_as(C.POINTER(C.c_int)), _tptr(out),
+                                        _stream(stream)), s)
+
+
+def sipg_pcg_solve(s, b, x, rtol, maxit, stream=None, raise_on_noconv=True):
+    info = fdm_solve_info()
+    rc = load().sipg_pcg_solve(s, _tptr(b), _tptr(x), rtol, maxit, C.byref(info), _stream(stream))
+    if rc == FDM_ENOCONV and not raise_on_noconv:
+        return info
+    _check_sipg(rc, s)
+    return info
+
+
+def fdm_sipg_query(s, what, out):
+    n = C.c_size_t(out.nbytes)
+    _check_sipg(load().fdm_sipg_query(s, what, out.ctypes.data_as(C.c_void_p), C.byref(n)), s)
+    return n.value
+
+
+def fdm_sipg_destroy(s):
+    load().fdm_sipg_destroy(s)
 
 
 def fdm_batch_setup(ctxs):
@@ -578,4 +637,90 @@ class Elasticity:
     def launches(self):
         out = np.zeros(1, dtype=np.int64)
         fdm_elast_query(self.h, FDM_Q_LAUNCHES, out)
+        return int(out[0])
+
+
+class Sipg:
+    """Owns one SIPG DQ_p Poisson problem (fdm_sipg): box cells, weak
+    Dirichlet condition on the boundary, cell-major vectors [ndof] on the
+    device (ndof = cells * (p+1)^3)."""
+
+    def __init__(self, p, xv, yv, zv, eta=0.0, precision=FDM_PREC_FP32, pc=FDM_PC_VCYCLE, omega=0.0,
+                 lanczos_start=None, lanczos_steps=20, flexible_beta=-1, coarse_levels=-1, stream=None):
+        self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (xv, yv, zv)]
+        mesh = fdm_mesh()
+        mesh.nx, mesh.ny, mesh.nz = len(xv) - 1, len(yv) - 1, len(zv) - 1
+        mesh.xv, mesh.yv, mesh.zv = [_dptr(a) for a in self._keep]
+        opt = fdm_default_options()
+        opt.precision, opt.pc, opt.omega, opt.lanczos_steps = precision, pc, omega, lanczos_steps
+        opt.flexible_beta = flexible_beta
+        opt.coarse_levels = coarse_levels
+        if lanczos_start is not None:
+            s = np.ascontiguousarray(lanczos_start, dtype=np.float64)
+            self._keep.append(s)
+            opt.lanczos_start = _dptr(s)
+        self.p = p
+        self.nc = (mesh.nx, mesh.ny, mesh.nz)
+        self.ndof = mesh.nx * mesh.ny * mesh.nz * (p + 1) ** 3
+        self.h = fdm_sipg_setup(mesh, p, eta, opt, stream)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            fdm_sipg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _out(self, like, n=None):
+        import torch
+        return torch.empty(self.ndof if n is None else n, dtype=torch.float64, device=like.device)
+
+    def apply(self, u, y=None):
+        y = self._out(u) if y is None else y
+        sipg_apply(self.h, u, y)
+        return y
+
+    def asm_apply(self, r, z=None):
+        z = self._out(r) if z is None else z
+        sipg_asm_apply(self.h, r, z)
+        return z
+
+    def pc_apply(self, r, z=None):
+        z = self._out(r) if z is None else z
+        sipg_pc_apply(self.h, r, z)
+        return z
+
+    def vertex_index(self, vx, vy, vz):
+        return vx + (self.nc[0] + 1) * (vy + (self.nc[1] + 1) * vz)
+
+    def patch_solve(self, r, vertices):
+        """A_v^{-1} R_v r for (vx, vy, vz) interior vertices: [len, (2p+2)^3] in star order."""
+        idx = [self.vertex_index(*v) for v in vertices]
+        m3 = (2 * self.p + 2) ** 3
+        out = self._out(r, len(idx) * m3)
+        sipg_patch_solve(self.h, r, idx, out)
+        return out.view(len(idx), m3)
+
+    def pcg_solve(self, b, x=None, rtol=1e-8, maxit=500, raise_on_noconv=True):
+        x = self._out(b) if x is None else x
+        return x, sipg_pcg_solve(self.h, b, x, rtol, maxit, raise_on_noconv=raise_on_noconv)
+
+    @property
+    def omega(self):
+        out = np.zeros(1)
+        fdm_sipg_query(self.h, FDM_Q_OMEGA, out)
+        return float(out[0])
+
+    def lanczos_extremes(self):
+        out = np.zeros(2)
+        fdm_sipg_query(self.h, FDM_Q_LAMBDA, out)
+        return float(out[0]), float(out[1])
+
+    def launches(self):
+        out = np.zeros(1, dtype=np.int64)
+        fdm_sipg_query(self.h, FDM_Q_LAUNCHES, out)
         return int(out[0])

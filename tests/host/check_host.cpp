@@ -131,8 +131,35 @@ static int gmg() {
   return bad + (lev.size() == 3 ? 0 : 1);  // 8x12x8 -> 4x6x4 -> 2x3x2 (3 is odd: stop)
 }
 
+// prints the end derivatives, the 1D star pencil (A, M) and its generalized
+// eigendecomposition (S, lam) for p, eta and the half-widths h0 h1 hl hr
+static int sipg(int argc, char **argv) {
+  if (argc < 8) return 1;
+  const int p = std::atoi(argv[2]), n = p + 1, m = 2 * n;
+  const double eta = std::atof(argv[3]), h0 = std::atof(argv[4]), h1 = std::atof(argv[5]), hl = std::atof(argv[6]),
+               hr = std::atof(argv[7]);
+  const Basis1D b = make_basis(p);
+  std::vector<double> dm, dp, A(m * m), M(m * m), S(m * m), lam(m);
+  sipg_end_derivatives(b.xi, dm, dp);
+  sipg_star_pencil(n, b.A.data(), b.B.data(), dm.data(), dp.data(), eta, h0, h1, hl, hr, A.data(), M.data());
+  sym_gen_eig(m, A.data(), M.data(), S.data(), lam.data());
+  auto put = [](const char *name, const std::vector<double> &v) {
+    std::printf("%s", name);
+    for (double x : v) std::printf(" %.17g", x);
+    std::printf("\n");
+  };
+  put("dm", dm);
+  put("dp", dp);
+  put("A", A);
+  put("M", M);
+  put("S", S);
+  put("lam", lam);
+  return 0;
+}
+
 int main(int argc, char **argv) {
   const std::string what = argc > 1 ? argv[1] : "all";
+  if (what == "sipg") return sipg(argc, argv);
   int bad = 0;
   if (what == "topology" || what == "all") bad += topology();
   if (what == "gmg" || what == "all") bad += gmg();

@@ -2,7 +2,9 @@
 the package's own host sources): the patch-class tables of the L and the
 Schur-coupling factor forms for p = 1..15, and the multigrid Galerkin
 coarsening against the Q1 stiffness assembled directly on each coarsened
-graded mesh (nested Q1 spaces make them equal)."""
+graded mesh (nested Q1 spaces make them equal), and the SIPG star pencils
+(Section 5): their generalized eigendecompositions, and the Kronecker sum of
+the three pencils of a star against the oracle's star matrix."""
 import os
 import shutil
 import subprocess
@@ -22,7 +24,8 @@ def checker(tmp_path_factory):
     out = str(tmp_path_factory.mktemp("host") / "check_host")
     cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
     subprocess.run([gxx, "-O1", "-std=c++17", "-I", cuda_inc, "-o", out, os.path.join(HERE, "host", "check_host.cpp"),
-                    os.path.join(CSRC, "topology.cpp"), os.path.join(CSRC, "gmg.cpp")], check=True)
+                    os.path.join(CSRC, "topology.cpp"), os.path.join(CSRC, "gmg.cpp"),
+                    os.path.join(CSRC, "basis1d.cpp"), os.path.join(CSRC, "sipg_host.cpp")], check=True)
     return out
 
 
@@ -49,3 +52,58 @@ def test_gmg_galerkin_levels(checker):
     rc, lines = run(checker, "gmg")
     assert rc == 0, "\n".join(lines)
     assert any("levels=2" in l for l in lines)
+
+
+def sipg_pencil(checker, p, eta, h0, h1, hl, hr):
+    r = subprocess.run([checker, "sipg", str(p)] + ["%.17g" % float(x) for x in (eta, h0, h1, hl, hr)],
+                       capture_output=True, text=True, check=True)
+    import numpy as np
+    out = {}
+    for line in r.stdout.splitlines():
+        k, *v = line.split()
+        out[k] = np.array([float(x) for x in v])
+    m = 2 * (p + 1)
+    for k in ("A", "M", "S"):
+        out[k] = out[k].reshape(m, m)
+    return out
+
+
+@pytest.mark.parametrize("p", [1, 3, 7, 10])
+def test_sipg_pencil_eigendecomposition(checker, p):
+    import numpy as np
+    from tests import bruteforce as bf
+    P = sipg_pencil(checker, p, p * (p + 1.0), 0.3, 0.07, 0.2, -1.0)
+    L = bf.lagrange_polys(bf.gll_nodes(p))
+    assert np.allclose(P["dm"], [q.deriv()(-1.0) for q in L], rtol=1e-11, atol=1e-11 * p * p)
+    assert np.allclose(P["dp"], [q.deriv()(1.0) for q in L], rtol=1e-11, atol=1e-11 * p * p)
+    S, A, M, lam = P["S"], P["A"], P["M"], P["lam"]
+    assert np.all(lam > 0)
+    assert np.abs(S.T @ M @ S - np.eye(len(lam))).max() <= 1e-11
+    assert np.abs(S.T @ A @ S - np.diag(lam)).max() <= 1e-11 * lam.max()
+
+
+def test_sipg_star_is_kronecker_sum_of_pencils(checker):
+    """The star matrix of every vertex of a graded 4 x 3 x 3 mesh (the oracle's
+    principal submatrix of A) is Ax (x) My (x) Mz + Mx (x) Ay (x) Mz + Mx (x) My
+    (x) Az of the host's pencils, and the fast-diagonalisation inverse built
+    from their eigendecompositions inverts it."""
+    import numpy as np
+    from oracle.sipg import Sipg
+    p = 2
+    S = Sipg(p, [0, .3, .5, 1, 1.2], [0, .2, .6, 1.0], [0, .4, .7, 1])
+    for v in S.vertices():
+        pen = []
+        for a in range(3):
+            k, h = v[a], S.h[a]
+            hl = h[k - 2] if k >= 2 else -1.0
+            hr = h[k + 1] if k + 1 < S.nc[a] else -1.0
+            pen.append(sipg_pencil(checker, p, S.eta, h[k - 1], h[k], hl, hr))
+        X, Y, Z = pen
+        K = (np.kron(Z["A"], np.kron(Y["M"], X["M"])) + np.kron(Z["M"], np.kron(Y["A"], X["M"])) +
+             np.kron(Z["M"], np.kron(Y["M"], X["A"])))
+        Av = S.patch_matrix(v)
+        assert np.abs(K - Av).max() <= 1e-13 * np.abs(Av).max()
+        Sk = np.kron(Z["S"], np.kron(Y["S"], X["S"]))
+        D = (Z["lam"][:, None, None] + Y["lam"][None, :, None] + X["lam"][None, None, :]).ravel()
+        inv = Sk @ np.diag(1.0 / D) @ Sk.T
+        assert np.abs(inv @ Av - np.eye(len(D))).max() <= 1e-10
