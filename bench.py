@@ -526,6 +526,10 @@ def bench_gmg(dev, fdmpc, inputs):
     return out
 
 
+# FP32 CUDA-core FMA peak from the unit counts and the maximum SM clock
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 * 1e-12
+
+
 def bench_sipg(dev, fdmpc, inputs):
     """SIPG on DQ_7 (Section 5), 16^3 graded cells, 2.1 M values, eta = p(p+1):
     PCG to 1e-8 with the hybrid V(1,1) (vertex-star Schwarz with exact star
@@ -567,7 +571,11 @@ def bench_sipg(dev, fdmpc, inputs):
             torch.cuda.synchronize()
             ms_sweep = e0.elapsed_time(e1) / 20
             flops = 2.0 * 6 * m ** 4 * stars
-            out["fp32_sweep"] = {"ms": ms_sweep, "gflop": flops * 1e-9, "tflops": flops / (ms_sweep * 1e-3) * 1e-12}
+            tflops = flops / (ms_sweep * 1e-3) * 1e-12
+            out["fp32_sweep"] = {"ms": ms_sweep, "gflop": flops * 1e-9, "tflops": tflops,
+                                 "roofline": {"bound": "alu", "achieved": tflops, "peak": FP32_ALU_TFLOPS,
+                                              "unit": "TFLOP/s", "frac": tflops / FP32_ALU_TFLOPS,
+                                              "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}}
         s.close()
     out["mixed_over_fp64"] = out["mixed"]["solve_dofs_per_s"] / out["fp64"]["solve_dofs_per_s"]
     return out

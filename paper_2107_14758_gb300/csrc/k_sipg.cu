@@ -18,7 +18,7 @@
 //                  two-cell operators (cell and facet terms) and masses, so
 //                  with S^T A S = Lambda, S^T M S = I per axis its inverse is
 //                  (S (x) S (x) S) (Lambda_x + Lambda_y + Lambda_z)^{-1}
-//                  (S (x) S (x) S)^T: five line passes over the star tensor
+//                  (S (x) S (x) S)^T: six line passes over the star tensor
 //                  in shared memory, one line per thread.  The stars of the
 //                  vertices of one parity class (vx, vy, vz mod 2) share no
 //                  cell, so each of the 8 classes is one launch that adds its
@@ -220,22 +220,54 @@ __device__ __forceinline__ int line_index(int l, int m) {
   return AXIS == 0 ? m + MP * (a + M * b) : (AXIS == 1 ? a + MP * (m + M * b) : a + MP * (b + M * m));
 }
 
-// in place: line <- S^T line (TR) or S line, S row-major [m][i] (column i =
-// eigenvector i).  The thread holds its input line in registers and writes
-// each output as soon as it is formed.
-template <typename T, int M, int MP, int AXIS, bool TR>
-__device__ __forceinline__ void star_pass(T *U, const T *S, int nthr) {
+// sum over m = 0..M-1 of row[m] x[m], accumulated in that order, the row (in
+// shared memory, 16-byte aligned where M allows) read by vector loads: with the
+// row shared by the whole warp each load is a broadcast, and one vector load
+// replaces two or four scalar ones
+template <typename T, int M>
+__device__ __forceinline__ T row_dot(const T *row, const T (&x)[M]) {
+  T s = 0;
+  if constexpr (sizeof(T) == 4 && M % 4 == 0) {
+    const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+    for (int q = 0; q < M / 4; ++q) {
+      const float4 v = r4[q];
+      s = fma(v.x, x[4 * q], s);
+      s = fma(v.y, x[4 * q + 1], s);
+      s = fma(v.z, x[4 * q + 2], s);
+      s = fma(v.w, x[4 * q + 3], s);
+    }
+  } else if constexpr (sizeof(T) == 4) {
+    const float2 *r2 = reinterpret_cast<const float2 *>(row);
+#pragma unroll
+    for (int q = 0; q < M / 2; ++q) {
+      const float2 v = r2[q];
+      s = fma(v.x, x[2 * q], s);
+      s = fma(v.y, x[2 * q + 1], s);
+    }
+  } else {
+    const double2 *r2 = reinterpret_cast<const double2 *>(row);
+#pragma unroll
+    for (int q = 0; q < M / 2; ++q) {
+      const double2 v = r2[q];
+      s = fma(v.x, x[2 * q], s);
+      s = fma(v.y, x[2 * q + 1], s);
+    }
+  }
+  return s;
+}
+
+// in place: line <- R line, R row-major [i][m] (R = S^T for the transform to
+// the eigenbasis, S for the way back).  The thread holds its input line in
+// registers and writes each output as soon as it is formed.
+template <typename T, int M, int MP, int AXIS>
+__device__ __forceinline__ void star_pass(T *U, const T *R, int nthr) {
   for (int l = threadIdx.x; l < M * M; l += nthr) {
     T x[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) x[m] = U[line_index<M, MP, AXIS>(l, m)];
 #pragma unroll 2
-    for (int i = 0; i < M; ++i) {
-      T s = 0;
-#pragma unroll
-      for (int m = 0; m < M; ++m) s = fma(TR ? S[m * M + i] : S[i * M + m], x[m], s);
-      U[line_index<M, MP, AXIS>(l, i)] = s;
-    }
+    for (int i = 0; i < M; ++i) U[line_index<M, MP, AXIS>(l, i)] = row_dot<T, M>(R + i * M, x);
   }
 }
 
@@ -245,8 +277,9 @@ __global__ void __launch_bounds__(SIPG_THREADS) k_sipg_patch(SipgDev<T> d, int c
                                                              T *__restrict__ zpatch, double omega) {
   constexpr int M = 2 * N, MP = M + 1, M2 = M * M, N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *S = reinterpret_cast<T *>(smem_raw);  // [3][M][M]
-  T *lam = S + 3 * M2;                     // [3][M]
+  T *S = reinterpret_cast<T *>(smem_raw);  // [3][M][M]: S per axis, row-major
+  T *ST = S + 3 * M2;                      // [3][M][M]: S^T per axis, row-major
+  T *lam = ST + 3 * M2;                    // [3][M]
   T *U = lam + 3 * M;                      // [M][M][MP]
   const int nvx = d.nx + 1, nvy = d.ny + 1;
   int v[3];
@@ -272,11 +305,16 @@ __global__ void __launch_bounds__(SIPG_THREADS) k_sipg_patch(SipgDev<T> d, int c
   for (int a = 0; a < 3; ++a) {
     const T *Sa = d.S + d.soff[a] + (int64_t)(v[a] - 1) * M2;
     const T *la = d.lam + d.loff[a] + (int64_t)(v[a] - 1) * M;
-    for (int t = threadIdx.x; t < M2; t += nthr) S[a * M2 + t] = Sa[t];
+    for (int t = threadIdx.x; t < M2; t += nthr) {
+      const T v = Sa[t];
+      S[a * M2 + t] = v;
+      ST[a * M2 + (t % M) * M + t / M] = v;
+    }
     for (int t = threadIdx.x; t < M; t += nthr) lam[a * M + t] = la[t];
   }
   __syncthreads();
   const T *Sx = S, *Sy = S + M2, *Sz = S + 2 * M2;
+  const T *STx = ST, *STy = ST + M2, *STz = ST + 2 * M2;
   // gather fused with the x pass: the thread of line (Y, Z) reads two cell rows
   for (int l = threadIdx.x; l < M2; l += nthr) {
     const int Y = l % M, Z = l / M;
@@ -290,15 +328,10 @@ __global__ void __launch_bounds__(SIPG_THREADS) k_sipg_patch(SipgDev<T> d, int c
       for (int i = 0; i < N; ++i) x[ca * N + i] = T(row[i]);
     }
 #pragma unroll 2
-    for (int i = 0; i < M; ++i) {
-      T s = 0;
-#pragma unroll
-      for (int m = 0; m < M; ++m) s = fma(Sx[m * M + i], x[m], s);
-      U[i + MP * (Y + M * Z)] = s;
-    }
+    for (int i = 0; i < M; ++i) U[i + MP * (Y + M * Z)] = row_dot<T, M>(STx + i * M, x);
   }
   __syncthreads();
-  star_pass<T, M, MP, 1, true>(U, Sy, nthr);
+  star_pass<T, M, MP, 1>(U, STy, nthr);
   __syncthreads();
   // z pass forward with the division by the eigenvalue sums, then back; the
   // line stays with its thread, so no barrier between the two
@@ -310,24 +343,14 @@ __global__ void __launch_bounds__(SIPG_THREADS) k_sipg_patch(SipgDev<T> d, int c
     for (int m = 0; m < M; ++m) x[m] = line[MP * M * m];
     const T lxy = lam[X] + lam[M + Y];
 #pragma unroll 2
-    for (int i = 0; i < M; ++i) {
-      T s = 0;
-#pragma unroll
-      for (int m = 0; m < M; ++m) s = fma(Sz[m * M + i], x[m], s);
-      line[MP * M * i] = s / (lxy + lam[2 * M + i]);
-    }
+    for (int i = 0; i < M; ++i) line[MP * M * i] = row_dot<T, M>(STz + i * M, x) / (lxy + lam[2 * M + i]);
 #pragma unroll
     for (int m = 0; m < M; ++m) x[m] = line[MP * M * m];
 #pragma unroll 2
-    for (int m = 0; m < M; ++m) {
-      T s = 0;
-#pragma unroll
-      for (int i = 0; i < M; ++i) s = fma(Sz[m * M + i], x[i], s);
-      line[MP * M * m] = s;
-    }
+    for (int m = 0; m < M; ++m) line[MP * M * m] = row_dot<T, M>(Sz + m * M, x);
   }
   __syncthreads();
-  star_pass<T, M, MP, 1, false>(U, Sy, nthr);
+  star_pass<T, M, MP, 1>(U, Sy, nthr);
   __syncthreads();
   // x pass back fused with the scatter (z += omega result) or the patch output
   const T w = T(omega);
@@ -345,9 +368,7 @@ __global__ void __launch_bounds__(SIPG_THREADS) k_sipg_patch(SipgDev<T> d, int c
                 N * (j + N * k);
 #pragma unroll 2
     for (int m = 0; m < M; ++m) {
-      T s = 0;
-#pragma unroll
-      for (int i = 0; i < M; ++i) s = fma(Sx[m * M + i], x[i], s);
+      const T s = row_dot<T, M>(Sx + m * M, x);
       if (zp) zp[m] = s;
       else {
         Tout *o = row[m / N] + m % N;
@@ -467,7 +488,7 @@ size_t sipg_cell_smem(int n) {
 template <typename T>
 size_t sipg_patch_smem(int n) {
   const size_t m = 2 * (size_t)n;
-  return sizeof(T) * (3 * m * m + 3 * m + m * m * (m + 1));
+  return sizeof(T) * (6 * m * m + 3 * m + m * m * (m + 1));
 }
 
 template <typename T, typename Tin>
