@@ -35,7 +35,9 @@ def test_header_declares_the_boundary():
                      "fdm_destroy", "fdm_last_error", "fdm_batch_setup", "pcg_solve_batched",
                      "fdm_surrogate_load", "fdm_surrogate_train", "fdm_surrogate_grad", "fdm_surrogate_apply",
                      "fdm_elast_setup", "elast_apply", "elast_pc_apply", "elast_pcg_solve", "fdm_elast_query",
-                     "fdm_elast_destroy"):
+                     "fdm_elast_destroy", "fdm_sipg_setup", "sipg_apply", "sipg_asm_apply", "sipg_pc_apply",
+                     "sipg_patch_solve", "sipg_pcg_solve", "fdm_sipg_query", "fdm_sipg_last_error",
+                     "fdm_sipg_destroy", "stiffness_apply_noalloc"):
         assert required in names
 
 
@@ -75,6 +77,53 @@ def test_invalid_arguments_rejected_without_gpu(lib):
         fdmpc.FDM_EINVAL
     assert "box cells" in L.fdm_elast_last_error(None).decode()
     assert L.elast_apply(None, None, None, None) == fdmpc.FDM_EINVAL
+
+
+def test_sipg_and_noalloc_arguments_rejected_without_gpu(lib):
+    """SIPG set-up checks the mesh (at least 2 cells per axis, strictly
+    increasing vertices, box cells), the degree (1..10) and the penalty on the
+    host; every SIPG entry point and the fixed-scratch stiffness apply reject
+    a null context or null vectors before any CUDA call."""
+    import numpy as np
+    from paper_2107_14758_gb300 import fdmpc
+    L = fdmpc.load()
+    h = ctypes.c_void_p()
+    o = fdmpc.fdm_default_options()
+    dbl = ctypes.POINTER(ctypes.c_double)
+
+    def mesh_of(xv, yv, zv):
+        m = fdmpc.fdm_mesh()
+        m.nx, m.ny, m.nz = len(xv) - 1, len(yv) - 1, len(zv) - 1
+        m.xv, m.yv, m.zv = (a.ctypes.data_as(dbl) for a in (xv, yv, zv))
+        return m
+
+    v3 = np.array([0.0, 0.4, 1.0])
+    ok = mesh_of(v3, v3, v3)
+    for p, eta in ((0, -1.0), (11, -1.0), (3, float("nan")), (3, float("inf"))):
+        assert L.fdm_sipg_setup(ctypes.byref(ok), p, eta, ctypes.byref(o), ctypes.byref(h), None) == \
+            fdmpc.FDM_EINVAL
+    assert "degree (1..10)" in L.fdm_sipg_last_error(None).decode()
+    one = np.array([0.0, 1.0])
+    thin = mesh_of(v3, one, v3)  # one cell along y: no interior vertex line
+    assert L.fdm_sipg_setup(ctypes.byref(thin), 3, -1.0, ctypes.byref(o), ctypes.byref(h), None) == fdmpc.FDM_EINVAL
+    bad = np.array([0.0, 0.6, 0.5])
+    dec = mesh_of(v3, bad, v3)
+    assert L.fdm_sipg_setup(ctypes.byref(dec), 3, -1.0, ctypes.byref(o), ctypes.byref(h), None) == fdmpc.FDM_EINVAL
+    assert "increase strictly" in L.fdm_sipg_last_error(None).decode()
+    jac = np.zeros(9 * 8 * 4 ** 3)
+    ok.jac = jac.ctypes.data_as(dbl)
+    assert L.fdm_sipg_setup(ctypes.byref(ok), 3, -1.0, ctypes.byref(o), ctypes.byref(h), None) == fdmpc.FDM_EINVAL
+    assert "box cells" in L.fdm_sipg_last_error(None).decode()
+    assert L.fdm_sipg_setup(ctypes.byref(ok), 3, -1.0, ctypes.byref(o), None, None) == fdmpc.FDM_EINVAL
+    assert L.sipg_apply(None, None, None, None) == fdmpc.FDM_EINVAL
+    assert L.sipg_asm_apply(None, None, None, None) == fdmpc.FDM_EINVAL
+    assert L.sipg_pc_apply(None, None, None, None) == fdmpc.FDM_EINVAL
+    assert L.sipg_patch_solve(None, None, 0, None, None, None) == fdmpc.FDM_EINVAL
+    assert L.sipg_pcg_solve(None, None, None, ctypes.c_double(1e-8), 10, None, None) == fdmpc.FDM_EINVAL
+    n = ctypes.c_size_t(8)
+    assert L.fdm_sipg_query(None, fdmpc.FDM_Q_NDOF, ctypes.byref(ctypes.c_int64()), ctypes.byref(n)) == \
+        fdmpc.FDM_EINVAL
+    assert L.stiffness_apply_noalloc(None, None, None, None) == fdmpc.FDM_EINVAL
 
 
 def test_default_options_match_header(lib):
