@@ -185,20 +185,29 @@ def run_oracle_solve(P, b):
 
 
 def oracle_problem():
+    """The CPU sample problem set up by the oracle; returns (problem, b, set-up seconds)."""
     import oracle
     from paper_2107_14758_gb300 import inputs
     oracle.build()
     p, xv, yv, zv = cpu_sample_problem()
+    t0 = time.perf_counter()
     P = oracle.Problem(p, xv, yv, zv)
     P.setup_patches()
     P.setup_coarse()
     P.lanczos_omega(inputs.lanczos_start(P.ndof))
+    setup_s = time.perf_counter() - t0
     b = P.mass_apply(inputs.normal_rhs(P.ndof, 2))
-    return P, b
+    return P, b, setup_s
 
 
 def cpu_cores():
-    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    """Threads the oracle's OpenMP loops use: OMP_NUM_THREADS, else the CPUs this process may run on."""
+    if os.environ.get("OMP_NUM_THREADS", "").strip().isdigit():
+        return int(os.environ["OMP_NUM_THREADS"])
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 SAMPLE_TEXT = ("the same problem family (graded tensor mesh, Q7, N(0,1) nodal f, PCG + V(1,1), rtol 1e-8) "
@@ -209,7 +218,7 @@ def bench_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    P, b = oracle_problem()
+    P, b, setup_s = oracle_problem()
     free = _free_dofs(P.N)
     for _ in range(args.warmup):
         run_oracle_solve(P, b)
@@ -226,7 +235,7 @@ def bench_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT, "sample": SAMPLE_TEXT, "iterations": int(np.median(its))},
             "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": cpu_cores(), "kind": "oracle",
-                             "sample": SAMPLE_TEXT},
+                             "sample": SAMPLE_TEXT, "setup_s": setup_s},
             "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -396,10 +405,10 @@ def bench_gpu(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        P, bc = oracle_problem()
+        P, bc, setup_cpu = oracle_problem()
         t, it, conv = run_oracle_solve(P, bc)
         cpu = {"value": _free_dofs(P.N) / t, "unit": "DoF/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": SAMPLE_TEXT}
+               "sample": SAMPLE_TEXT, "setup_s": setup_cpu, "iterations": it}
 
     if rank == 0:
         line = {"metric": "pcg_solve_dofs_per_s", "value": value, "unit": "DoF/s", "n_gpus": ws,
