@@ -18,6 +18,14 @@ Workload families (stand-ins for the paper's Cartesian Poisson runs, Section
              (unit variance in the mode average).
 * rhs:       i.i.d. N(0,1) nodal values, or the manufactured
              f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z) sampled at the GLL nodes.
+* unstructured hexahedra: a 2D quad mesh of the unit square with vertices of
+             valence 3, 4, 6 and 8 (an m x m grid of squares cut into two
+             triangles along a random diagonal, each triangle cut into three
+             quads through its centroid and edge midpoints, interior grid
+             points jittered), extruded through graded layers in z; every
+             cell's reference axes reoriented by a random symmetry of the
+             cube.  A stand-in for the paper's unstructured meshes (2D base
+             meshes extruded with six layers), which are not available.
 """
 import numpy as np
 from numpy.polynomial import legendre as _leg
@@ -239,3 +247,118 @@ def rhs_for(w, ndof):
     if w["rhs"] == "nodal_normal":
         return "nodal", normal_rhs(ndof, w["seed"])
     return "load", normal_rhs(ndof, w["seed"])
+
+
+# ---- general hexahedral meshes (vertex coordinates + cell-to-vertex lists) ----
+#
+# A cell lists its 8 vertices in the order of the reference cube's corners
+# (a, b, c) in {0, 1}^3 at index a + 2 b + 4 c (reference coordinate -1 -> 0,
+# +1 -> 1); the geometry is the trilinear map through them.
+
+def tensor_hex_mesh(xv, yv, zv):
+    """The tensor mesh of the vertex vectors as vertices X[nv, 3] (x fastest)
+    and cells[nc, 8] (cells x fastest, reference axes along x, y, z)."""
+    xv, yv, zv = (np.asarray(a, dtype=np.float64) for a in (xv, yv, zv))
+    nx, ny, nz = len(xv) - 1, len(yv) - 1, len(zv) - 1
+    Z, Y, X = np.meshgrid(zv, yv, xv, indexing="ij")
+    verts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    cells = []
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                cells.append([(i + a) + (nx + 1) * ((j + b) + (ny + 1) * (k + c))
+                              for c in (0, 1) for b in (0, 1) for a in (0, 1)])
+    return verts, np.array(cells, dtype=np.int64)
+
+
+def reorient_cells(cells, seed):
+    """Lists every cell's vertices in the frame of a random symmetry of the
+    reference cube (one of the 48 axis permutations with reflections), so that
+    neighbouring cells see their shared faces and edges in different
+    orientations.  The cells themselves are unchanged."""
+    rng = np.random.default_rng(seed)
+    cells = np.asarray(cells, dtype=np.int64)
+    out = np.empty_like(cells)
+    for e in range(cells.shape[0]):
+        perm = rng.permutation(3)
+        flip = rng.integers(0, 2, size=3)
+        for a in (0, 1):
+            for b in (0, 1):
+                for c in (0, 1):
+                    r = (a, b, c)
+                    old = [0, 0, 0]
+                    for d in range(3):
+                        old[perm[d]] = 1 - r[d] if flip[d] else r[d]
+                    out[e, a + 2 * b + 4 * c] = cells[e, old[0] + 2 * old[1] + 4 * old[2]]
+    return out
+
+
+def unstructured_quad_mesh(m, seed, jitter=0.2):
+    """2D quad mesh of the unit square: returns vertices V[nv, 2] and quads
+    [nq, 4] listed counter-clockwise.  An m x m grid of squares, each cut into
+    two triangles along a diagonal drawn at random, each triangle cut into
+    three quads (corner, edge midpoint, centroid, edge midpoint).  Interior
+    grid points move by up to jitter * h per coordinate (h = 1/m) before the
+    midpoints and centroids are placed, which keeps every quad convex.
+    Valences: centroids 3, edge midpoints 4 (2 on the boundary), grid points
+    the number of triangles around them (4, 6 or 8 inside)."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / m
+    g = np.array([[i * h, j * h] for j in range(m + 1) for i in range(m + 1)])
+    for j in range(1, m):
+        for i in range(1, m):
+            g[i + (m + 1) * j] += rng.uniform(-jitter * h, jitter * h, size=2)
+    verts = [tuple(v) for v in g]
+    mid = {}
+
+    def midpoint(a, b):
+        key = (min(a, b), max(a, b))
+        if key not in mid:
+            mid[key] = len(verts)
+            verts.append(tuple(0.5 * (g[a] + g[b])))
+        return mid[key]
+
+    quads = []
+    for j in range(m):
+        for i in range(m):
+            c00, c10 = i + (m + 1) * j, i + 1 + (m + 1) * j
+            c01, c11 = i + (m + 1) * (j + 1), i + 1 + (m + 1) * (j + 1)
+            if rng.integers(0, 2):
+                tris = [(c00, c10, c11), (c00, c11, c01)]
+            else:
+                tris = [(c00, c10, c01), (c10, c11, c01)]
+            for (a, b, c) in tris:  # counter-clockwise
+                cen = len(verts)
+                verts.append(tuple((g[a] + g[b] + g[c]) / 3.0))
+                mab, mbc, mca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
+                quads += [[a, mab, cen, mca], [b, mbc, cen, mab], [c, mca, cen, mbc]]
+    return np.array(verts), np.array(quads, dtype=np.int64)
+
+
+def extruded_hex_mesh(V2, quads, zv):
+    """Extrudes a counter-clockwise 2D quad mesh through the layers of zv:
+    vertices X[nv2 * len(zv), 3] (layer-major) and cells[nq * (len(zv)-1), 8]
+    with reference axes (quad edge a->b, quad edge a->d, z)."""
+    V2 = np.asarray(V2, dtype=np.float64)
+    zv = np.asarray(zv, dtype=np.float64)
+    nv2 = V2.shape[0]
+    X = np.concatenate([np.column_stack([V2, np.full(nv2, z)]) for z in zv])
+    cells = []
+    for layer in range(len(zv) - 1):
+        for (a, b, c, d) in quads:
+            lo = [a, b, d, c]
+            cells.append([v + nv2 * layer for v in lo] + [v + nv2 * (layer + 1) for v in lo])
+    return X, np.array(cells, dtype=np.int64)
+
+
+def unstructured_hex_mesh(m, nz, seed, jitter=0.2):
+    """The unstructured workload mesh: unstructured_quad_mesh(m) extruded
+    through nz graded layers (widths U(0.5, 1.5), normalised), cells
+    reoriented at random.  Returns X, cells."""
+    V2, quads = unstructured_quad_mesh(m, seed, jitter)
+    rng = np.random.default_rng(seed + 1)
+    w = rng.uniform(0.5, 1.5, size=nz)
+    zv = np.concatenate([[0.0], np.cumsum(w / w.sum())])
+    zv[-1] = 1.0
+    X, cells = extruded_hex_mesh(V2, quads, zv)
+    return X, reorient_cells(cells, seed + 2)

@@ -294,3 +294,36 @@ def dense_sipg(p, xv, yv, zv, eta, q=None):
                      - np.einsum("q,qi,qj->ij", ws, J, G) - np.einsum("q,qi,qj->ij", ws, G, J))
                 M[np.ix_(idx, idx)] += F
     return M
+
+
+def q1_stiffness_hex(X, cells, q):
+    """Stiffness matrix of the conforming Q1 space on a general hexahedral
+    mesh (trilinear cells, corners at index a + 2b + 4c), indexed by mesh
+    vertex: each entry summed over cells of the q^3-point Gauss rule of
+    grad N_u . grad N_v |det J| with the physical gradients J^{-T} grad_xi."""
+    X = np.asarray(X, dtype=np.float64)
+    nv = X.shape[0]
+    A = np.zeros((nv, nv))
+    t, w = leg.leggauss(q)
+    corners = [(a, b, c) for c in (0, 1) for b in (0, 1) for a in (0, 1)]
+
+    def hat(s, k):
+        return 0.5 * (1.0 + s) if k else 0.5 * (1.0 - s)
+
+    def dhat(k):
+        return 0.5 if k else -0.5
+
+    for cell in np.asarray(cells):
+        P = X[cell]
+        for i, xi in enumerate(t):
+            for j, eta in enumerate(t):
+                for k, zeta in enumerate(t):
+                    # reference gradients of the 8 trilinear functions, [8, 3]
+                    g = np.array([[dhat(a) * hat(eta, b) * hat(zeta, c),
+                                   hat(xi, a) * dhat(b) * hat(zeta, c),
+                                   hat(xi, a) * hat(eta, b) * dhat(c)] for (a, b, c) in corners])
+                    J = P.T @ g                      # J[i, d] = d x_i / d xi_d
+                    phys = np.linalg.solve(J.T, g.T).T  # rows: physical gradients
+                    wt = w[i] * w[j] * w[k] * abs(np.linalg.det(J))
+                    A[np.ix_(cell, cell)] += wt * phys @ phys.T
+    return A

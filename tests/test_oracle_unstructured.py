@@ -1,0 +1,200 @@
+"""Pins of the unstructured-hexahedra oracle (oracle/unstructured.py): the
+vertex-star FDM/sparse relaxation on general conforming hexahedral meshes
+(Sections 2.1-2.7; the unstructured meshes of the Section 3 experiments),
+against what the mathematics and the structured oracle fix:
+
+* a tensor mesh listed as general hexahedra with every cell reoriented by a
+  random symmetry of the cube gives the structured C oracle's stiffness,
+  mass, surrogate coefficients (as a set per cell), relaxation, V(1,1),
+  Lanczos estimates and PCG iterates (node orders matched by position);
+* on an unstructured extruded mesh with vertices of valence 3 to 16: the
+  energy of a linear function is |a|^2 |Omega| exactly, the patch test
+  (A applied to a linear function vanishes at the free nodes) and its second
+  order form (A x^2 = -2 M 1 at the free nodes for p >= 2, integration by
+  parts) hold to rounding, the mass of 1 is the volume, A is symmetric
+  positive definite on the free nodes;
+* the star of an interior vertex with k cells per layer (2k cells) holds
+  1 + (k+2)(p-1) + 3k(p-1)^2 + 2k(p-1)^3 nodes (the vertex, its k+2 edges,
+  3k faces and 2k cells);
+* in the FDM basis glued across the star's cells (Section 2.4) the
+  surrogate star matrix has a diagonal interior block and d + 1 = 4
+  nonzeros in each interior row (Section 2.6), on unstructured stars too;
+* on a mesh whose only interior vertex belongs to every cell, that vertex's
+  star covers every free node, so its star solve with the exact star matrix
+  is the global direct solve;
+* the Galerkin coarse operator P^T A P is the Q1 stiffness of the same mesh
+  (nested spaces), assembled independently (tests/bruteforce.py);
+* PCG with the hybrid V(1,1) converges with slowly growing iteration counts
+  in p (the trend of the unstructured column of Table 1).
+"""
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+import oracle
+from oracle.unstructured import HexProblem
+from paper_2107_14758_gb300 import inputs
+from tests import bruteforce as bf
+
+
+def _structured_pair(p, n=3, seed=5):
+    xv, yv, zv = inputs.graded_vertices(n, seed)
+    X, cells = inputs.tensor_hex_mesh(xv, yv, zv)
+    H = HexProblem(p, X, inputs.reorient_cells(cells, seed + 4))
+    S = oracle.Problem(p, xv, yv, zv)
+    g = [inputs.node_coords(v, p) for v in (xv, yv, zv)]
+    Z, Y, Xg = np.meshgrid(g[2], g[1], g[0], indexing="ij")
+    dist, perm = cKDTree(H.nodes).query(np.stack([Xg.ravel(), Y.ravel(), Z.ravel()], axis=1))
+    assert dist.max() < 1e-12 and len(set(perm.tolist())) == H.ndof == S.ndof
+    return H, S, perm
+
+
+def relerr(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_reoriented_tensor_mesh_is_the_structured_problem(p):
+    H, S, perm = _structured_pair(p)
+    rng = np.random.default_rng(p)
+    u = rng.standard_normal(H.ndof)
+    assert relerr(H.apply(u)[perm], S.stiffness_apply(u[perm])) <= 1e-13
+    assert relerr(H.mass_apply(u)[perm], S.mass_apply(u[perm])) <= 1e-13
+    assert np.allclose(np.sort(H.mu, axis=1), np.sort(S.get_mu().reshape(-1, 3), axis=1), rtol=1e-13, atol=0)
+    S.setup_patches()
+    S.set_omega(1.0)
+    assert relerr(H.asm(u)[perm], S.asm_apply(u[perm])) <= 1e-12
+    S.setup_coarse()
+    b0 = inputs.lanczos_start(H.ndof)
+    lo, hi, om = H.lanczos_omega(b0)
+    slo, shi, som = S.lanczos_omega(b0[perm])
+    assert abs(lo - slo) <= 1e-7 * slo and abs(hi - shi) <= 1e-7 * shi
+    S.set_omega(om)
+    assert relerr(H.pc_apply(u)[perm], S.pc_apply(u[perm])) <= 1e-12
+    b = H.mass_apply(inputs.normal_rhs(H.ndof, 3))
+    xs, its, _, _ = S.pcg(b[perm], rtol=1e-8, maxit=100)
+    xh, ith, conv = H.pcg(b, rtol=1e-8)
+    assert conv and abs(ith - its) <= 1 and (ith != its or relerr(xh[perm], xs) <= 1e-10)
+
+
+def test_dirichlet_nodes_are_the_boundary():
+    H, S, perm = _structured_pair(2)
+    on_bnd = np.any((np.abs(H.nodes) < 1e-12) | (np.abs(H.nodes - 1.0) < 1e-12), axis=1)
+    assert np.array_equal(H.dirichlet, on_bnd)
+
+
+@pytest.fixture(scope="module")
+def mesh():
+    return inputs.unstructured_hex_mesh(2, 2, 5)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_linear_functions(mesh, p):
+    """Energy |a|^2 |Omega| and the patch test, exact for any trilinear mesh
+    and q = p + 1 Gauss points (the integrands are polynomials of degree at
+    most p + 2 per axis)."""
+    U = HexProblem(p, *mesh)
+    a = np.array([0.3, -1.1, 0.7])
+    ul = U.nodes @ a + 0.25
+    assert abs(ul @ (U.A @ ul) - a @ a) <= 1e-13
+    assert np.abs((U.A @ ul)[U.free]).max() <= 1e-13
+    assert abs(U.M.sum() - 1.0) <= 1e-13
+    assert abs(U.A - U.A.T).max() <= 1e-15
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_quadratic_function_integration_by_parts(mesh, p):
+    """u = x^2 lies in Q_p of every trilinear cell for p >= 2, and
+    int grad v . grad u = -int 2 v for v vanishing on the boundary."""
+    U = HexProblem(p, *mesh)
+    u = U.nodes[:, 0] ** 2
+    lhs = (U.A @ u)[U.free]
+    rhs = -2.0 * (U.M @ np.ones(U.ndof))[U.free]
+    assert np.abs(lhs - rhs).max() <= 1e-12 * np.abs(rhs).max()
+
+
+def test_spd_on_free_nodes(mesh):
+    U = HexProblem(2, *mesh)
+    Aff = U.A[U.free][:, U.free].toarray()
+    assert np.linalg.eigvalsh(Aff).min() > 0
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_star_sizes_and_fdm_sparsity(mesh, p):
+    U = HexProblem(p, *mesh)
+    seen = set()
+    for v in range(U.X.shape[0]):
+        x = U.X[v]
+        if not (0 < x[2] < 1) or np.any(np.abs(x[:2]) < 1e-12) or np.any(np.abs(x[:2] - 1) < 1e-12):
+            continue  # boundary vertex
+        k = len(U.vertex_cells[v]) // 2
+        want = 1 + (k + 2) * (p - 1) + 3 * k * (p - 1) ** 2 + 2 * k * (p - 1) ** 3
+        assert len(U.star_dofs(v)) == want
+        if k in seen:
+            continue
+        seen.add(k)
+        dofs, Tv, kind = U.star_fdm(v)
+        assert np.array_equal(np.bincount(kind, minlength=4),
+                              [2 * k * (p - 1) ** 3, 3 * k * (p - 1) ** 2, (k + 2) * (p - 1), 1])
+        Af = Tv.T @ U.As[dofs][:, dofs].toarray() @ Tv
+        sc = np.abs(Af).max()
+        I = kind == 0
+        AII = Af[np.ix_(I, I)]
+        assert np.abs(AII - np.diag(np.diag(AII))).max() <= 1e-13 * sc
+        assert (np.abs(Af[I]) > 1e-12 * sc).sum(axis=1).max() == 4
+        # the star solve in the FDM basis is the star solve
+        r = np.random.default_rng(k).standard_normal(len(dofs))
+        A_v = U.As[dofs][:, dofs].toarray()
+        assert relerr(Tv @ np.linalg.solve(Af, Tv.T @ r), np.linalg.solve(A_v, r)) <= 1e-11
+    assert {3, 4} <= seen
+
+
+def _single_star_mesh():
+    V2 = np.array([[0.0, 0.0], [1.0, 0.0], [0.2, 0.9]])
+    a, b, c = 0, 1, 2
+    pts = list(V2)
+    mab, mbc, mca, cen = 3, 4, 5, 6
+    pts += [0.5 * (V2[a] + V2[b]), 0.5 * (V2[b] + V2[c]), 0.5 * (V2[c] + V2[a]), V2.mean(axis=0)]
+    quads = [[a, mab, cen, mca], [b, mbc, cen, mab], [c, mca, cen, mbc]]
+    X, cells = inputs.extruded_hex_mesh(np.array(pts), quads, [0.0, 0.45, 1.0])
+    return X, inputs.reorient_cells(cells, 3), cen + len(pts)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_single_star_is_the_direct_solve(p):
+    X, cells, v = _single_star_mesh()
+    for exact in (True, False):
+        U = HexProblem(p, X, cells, exact_patches=exact)
+        assert np.array_equal(U.star_dofs(v), np.flatnonzero(U.free))
+        r = U._mask(np.random.default_rng(p).standard_normal(U.ndof))
+        M = (U.A if exact else U.As)[U.free][:, U.free].toarray()
+        dofs, zv = U.patch_solve(v, r)
+        assert relerr(zv, np.linalg.solve(M, r[U.free])) <= 1e-11
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_galerkin_coarse_is_q1_stiffness(mesh, p):
+    U = HexProblem(p, *mesh)
+    U.setup_coarse()
+    Aq1 = bf.q1_stiffness_hex(U.X, U.cells, p + 1)
+    bnd = np.zeros(U.X.shape[0], dtype=bool)
+    for v in range(U.X.shape[0]):
+        x = U.X[v]
+        bnd[v] = np.any(np.abs(x) < 1e-12) or np.any(np.abs(x - 1.0) < 1e-12)
+    inner = np.flatnonzero(~bnd)
+    assert U.Ac.shape == (len(inner), len(inner))
+    assert relerr(U.Ac, Aq1[np.ix_(inner, inner)]) <= 1e-12
+
+
+def test_pcg_iterations_grow_slowly_in_p(mesh):
+    its = []
+    for p in (2, 3, 4):
+        U = HexProblem(p, *mesh)
+        U.setup_patches()
+        U.setup_coarse()
+        U.lanczos_omega(inputs.lanczos_start(U.ndof))
+        b = U.mass_apply(np.ones(U.ndof))
+        x, it, conv = U.pcg(b, rtol=1e-8)
+        assert conv and np.linalg.norm(b - U.apply(x)) <= 1.5e-8 * np.linalg.norm(b)
+        its.append(it)
+    assert max(its) <= 30 and its[-1] - its[0] <= 6, its
