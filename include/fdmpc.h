@@ -359,6 +359,47 @@ int fdm_sipg_query(fdm_sipg *s, int what, void *out, size_t *len);
 const char *fdm_sipg_last_error(const fdm_sipg *s);
 void fdm_sipg_destroy(fdm_sipg *s);
 
+/* ---- general hexahedral meshes: host topology (no CUDA call) ----
+ * The vertex-star relaxation on an unstructured conforming hexahedral mesh
+ * (Sections 2.4 and 2.6 on the general meshes of the Section 3 experiments)
+ * needs, besides the cell kernels, a node numbering that neighbouring cells of
+ * any orientation share, the vertex stars in FDM order, the signed map from
+ * each cell's tensor-product FDM functions to the global ones, and each star's
+ * sparsity pattern.  fdm_hexmesh_create builds them on the host from
+ * cells[nc][8] (HOST; vertex ids in [0, nv) at the corners (a, b, c) of the
+ * reference cube, index a + 2 b + 4 c) for degree 1 <= p <= 15.  Numbering:
+ * one node per used vertex (by vertex id), then (p-1) per edge (from its
+ * lower-id vertex), (p-1)^2 per face (frame at its lowest-id corner, first
+ * axis towards the lower-id neighbouring corner), (p-1)^3 per cell (cell-local
+ * lexicographic); the FDM functions use the same slots (eigen-index m - 1 on
+ * an edge or face axis), with a sign -1 where a cell sees an odd interior
+ * function reversed.  Dirichlet nodes: the closure of the faces of one cell.
+ * Stars: every used vertex with at least one free node; its free nodes
+ * ordered cell interiors (by cell), faces, edges, the vertex; the pattern of
+ * its separable surrogate matrix in the FDM basis as CSR over star positions.
+ * FDM_EINVAL for a vertex id out of range, a degenerate cell, a face of more
+ * than two cells or more than 2^31 - 1 nodes; fdm_hexmesh_last_error. */
+typedef struct fdm_hexmesh fdm_hexmesh;
+int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_hexmesh **out);
+#define FDM_HQ_NNODE 1          /* int64: number of nodes */
+#define FDM_HQ_CELL_NODES 2     /* int32[nc][(p+1)^3]: node of each cell-local GLL node (i + n (j + n k)) */
+#define FDM_HQ_CELL_FDM 3       /* int32[nc][(p+1)^3]: global FDM function of each cell-local FDM function */
+#define FDM_HQ_CELL_SIGN 4      /* int8[nc][(p+1)^3]: its sign (+1 or -1) */
+#define FDM_HQ_DIRICHLET 5      /* uint8[nnode]: 1 on Dirichlet nodes */
+#define FDM_HQ_NSTAR 6          /* int32: number of stars */
+#define FDM_HQ_STAR_VERTEX 7    /* int32[nstar]: the vertex of each star */
+#define FDM_HQ_STAR_PTR 8       /* int64[nstar + 1]: offsets into FDM_HQ_STAR_NODES */
+#define FDM_HQ_STAR_NODES 9     /* int32[...]: each star's nodes in FDM order */
+#define FDM_HQ_PATTERN_PTR 10   /* int64[nstar + 1]: offsets into FDM_HQ_PATTERN_ROWPTR (star size + 1 each) */
+#define FDM_HQ_PATTERN_ROWPTR 11 /* int64[...]: per star, CSR row pointers starting at 0 */
+#define FDM_HQ_PATTERN_COLPTR 12 /* int64[nstar + 1]: offsets into FDM_HQ_PATTERN_COLS */
+#define FDM_HQ_PATTERN_COLS 13  /* int32[...]: per star, CSR column positions (sorted per row) */
+/* Copies `what` into out (HOST); *len is the capacity in bytes on input and
+ * the size written on output (out NULL: the size only). */
+int fdm_hexmesh_query(fdm_hexmesh *h, int what, void *out, size_t *len);
+const char *fdm_hexmesh_last_error(const fdm_hexmesh *h);
+void fdm_hexmesh_destroy(fdm_hexmesh *h);
+
 /* ---- introspection ---- */
 #define FDM_Q_NDOF 1         /* int64: number of grid nodes */
 #define FDM_Q_OMEGA 2        /* double: damping */

@@ -1,0 +1,405 @@
+// Host topology of a conforming hexahedral mesh for the vertex-star
+// relaxation on unstructured meshes (Sections 2.4 and 2.6 applied to general
+// meshes): the Q_p node numbering shared by neighbouring cells of any
+// orientation, the Dirichlet nodes, the vertex stars in FDM order, the signed
+// map from each cell's tensor-product FDM functions to the global FDM
+// functions, and the sparsity pattern of every star's separable surrogate
+// matrix in the FDM basis.  Host memory only: no CUDA call.
+//
+// Numbering.  Entities: the mesh vertices used by cells, the edges (vertex
+// pairs) and faces (vertex quadruples) of the cells, and the cells.  Nodes
+// (and, slot for slot, FDM functions) are numbered vertex nodes first (one per
+// used vertex, by vertex id), then edges ((p-1) each, by first appearance),
+// faces ((p-1)^2 each) and cell interiors ((p-1)^3 each, cell-local
+// lexicographic order).  An edge's nodes run from its lower-id vertex to the
+// higher; a face's nodes are indexed (s, t) in its canonical frame: origin at
+// its lowest-id corner, s towards the lower-id of the two neighbouring corners,
+// t towards the other.  The GLL points are symmetric, so a reversed axis maps
+// node index i to p - i.  The 1D interior FDM functions s_m are even or odd
+// under reflection (the pencil is centrosymmetric): a reversed axis keeps the
+// eigen-index m and multiplies by the parity of s_m.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+struct fdm_hexmesh {
+  int p = 0, n = 0, nv = 0, nc = 0;
+  int64_t nnode = 0;
+  std::vector<int32_t> cell_nodes;   // [nc][n^3] global node of each cell-local GLL node
+  std::vector<int32_t> cell_fdm;     // [nc][n^3] global FDM function of each cell-local FDM function
+  std::vector<int8_t> cell_sign;     // [nc][n^3] its sign
+  std::vector<uint8_t> dirichlet;    // [nnode]
+  std::vector<int32_t> star_vertex;  // [nstar]
+  std::vector<int64_t> star_ptr;     // [nstar + 1] into star_nodes
+  std::vector<int32_t> star_nodes;   // per star: cell interiors, faces, edges, vertex
+  std::vector<int64_t> pat_ptr;      // [nstar + 1] into pat_rowptr (each star: its size + 1 entries)
+  std::vector<int64_t> pat_rowptr;   // per star: CSR row pointers (star-local, from 0)
+  std::vector<int64_t> pat_colptr;   // [nstar + 1] into pat_cols
+  std::vector<int32_t> pat_cols;     // per star: CSR column indices (star-local positions)
+  std::string err;
+};
+
+namespace {
+
+std::string &hex_last_error() {
+  static std::string e;
+  return e;
+}
+
+int handle_hex(fdm_hexmesh *h, const fdm::Error &e) {
+  if (h) h->err = e.msg;
+  hex_last_error() = e.msg;
+  return e.code;
+}
+
+struct Builder {
+  int p, n, nv, nc;
+  const int *cells;
+  std::vector<int> parity;                          // parity of s_m, m = 1..p-1 (index m - 1)
+  std::vector<double> Af, Bf;                       // 1D FDM stiffness and mass (n x n)
+  std::vector<int64_t> vbase;                       // node of each vertex, -1 unused
+  std::map<std::pair<int, int>, int64_t> ebase;     // first node of each edge
+  std::map<std::array<int, 4>, int64_t> fbase;      // first node of each face
+  std::map<std::array<int, 4>, int> fcount;         // cells per face
+  std::vector<int64_t> cbase;
+  int64_t nnode = 0;
+
+  int corner(int e, int a, int b, int c) const { return cells[8 * e + a + 2 * b + 4 * c]; }
+
+  static std::array<int, 4> face_key(std::array<int, 4> v) {
+    std::sort(v.begin(), v.end());
+    return v;
+  }
+
+  // the corners of the face of cell e normal to axis d at side s, indexed by
+  // the two tangential axes (d1 < d2) as t1 + 2 t2
+  std::array<int, 4> face_corners(int e, int d, int s) const {
+    std::array<int, 4> out{};
+    const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+    for (int t2 = 0; t2 < 2; ++t2)
+      for (int t1 = 0; t1 < 2; ++t1) {
+        int r[3];
+        r[d] = s;
+        r[d1] = t1;
+        r[d2] = t2;
+        out[t1 + 2 * t2] = corner(e, r[0], r[1], r[2]);
+      }
+    return out;
+  }
+
+  void number() {
+    vbase.assign(nv, -1);
+    for (int e = 0; e < nc; ++e)
+      for (int k = 0; k < 8; ++k) {
+        const int v = cells[8 * e + k];
+        if (v < 0 || v >= nv) fdm::fail(FDM_EINVAL, "fdm_hexmesh_create: vertex index out of range");
+      }
+    std::vector<char> used(nv, 0);
+    for (int e = 0; e < nc; ++e)
+      for (int k = 0; k < 8; ++k) used[cells[8 * e + k]] = 1;
+    for (int v = 0; v < nv; ++v)
+      if (used[v]) vbase[v] = nnode++;
+    const int64_t m = p - 1;
+    for (int e = 0; e < nc; ++e)
+      for (int d = 0; d < 3; ++d)
+        for (int a = 0; a < 2; ++a)
+          for (int b = 0; b < 2; ++b) {
+            int r0[3], r1[3];
+            const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+            r0[d] = 0; r1[d] = 1;
+            r0[d1] = r1[d1] = a;
+            r0[d2] = r1[d2] = b;
+            int u = corner(e, r0[0], r0[1], r0[2]), w = corner(e, r1[0], r1[1], r1[2]);
+            if (u == w) fdm::fail(FDM_EINVAL, "fdm_hexmesh_create: degenerate cell edge");
+            auto key = std::make_pair(std::min(u, w), std::max(u, w));
+            if (!ebase.count(key)) {
+              ebase[key] = nnode;
+              nnode += m;
+            }
+          }
+    for (int e = 0; e < nc; ++e)
+      for (int d = 0; d < 3; ++d)
+        for (int s = 0; s < 2; ++s) {
+          auto key = face_key(face_corners(e, d, s));
+          if (key[0] == key[1] || key[1] == key[2] || key[2] == key[3])
+            fdm::fail(FDM_EINVAL, "fdm_hexmesh_create: degenerate cell face");
+          if (!fbase.count(key)) {
+            fbase[key] = nnode;
+            nnode += m * m;
+          }
+          ++fcount[key];
+        }
+    for (auto &kv : fcount)
+      if (kv.second > 2) fdm::fail(FDM_EINVAL, "fdm_hexmesh_create: a face belongs to more than two cells");
+    cbase.resize(nc);
+    for (int e = 0; e < nc; ++e) {
+      cbase[e] = nnode;
+      nnode += m * m * m;
+    }
+    if (nnode > INT32_MAX) fdm::fail(FDM_EINVAL, "fdm_hexmesh_create: more than 2^31 - 1 nodes");
+  }
+
+  // global node and FDM function of cell-local index (i, j, k) (node indices
+  // for the GLL map, eigen-indices on the interior axes for the FDM map)
+  void map_local(int e, const int idx[3], int64_t &node, int64_t &fdm_fn, int &sign) const {
+    const int m = p - 1;
+    int ends = 0;
+    for (int d = 0; d < 3; ++d) ends += (idx[d] == 0 || idx[d] == p);
+    sign = 1;
+    if (ends == 3) {
+      node = fdm_fn = vbase[corner(e, idx[0] / p, idx[1] / p, idx[2] / p)];
+      return;
+    }
+    if (ends == 0) {
+      node = fdm_fn = cbase[e] + (idx[0] - 1) + (int64_t)m * ((idx[1] - 1) + (int64_t)m * (idx[2] - 1));
+      return;
+    }
+    if (ends == 2) {
+      int d = 0;  // the edge's axis: the one interior index
+      for (int a = 0; a < 3; ++a)
+        if (idx[a] != 0 && idx[a] != p) d = a;
+      int r0[3], r1[3];
+      for (int a = 0; a < 3; ++a) r0[a] = r1[a] = idx[a] / p;
+      r0[d] = 0;
+      r1[d] = 1;
+      const int u = corner(e, r0[0], r0[1], r0[2]), w = corner(e, r1[0], r1[1], r1[2]);
+      const int64_t base = ebase.at(std::make_pair(std::min(u, w), std::max(u, w)));
+      const bool rev = u > w;
+      node = base + (rev ? p - idx[d] : idx[d]) - 1;
+      fdm_fn = base + idx[d] - 1;
+      if (rev) sign = parity[idx[d] - 1];
+      return;
+    }
+    // a face: normal axis d (the end index), tangential d1 < d2
+    int d = 0;
+    for (int a = 0; a < 3; ++a)
+      if (idx[a] == 0 || idx[a] == p) d = a;
+    const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+    const auto fc = face_corners(e, d, idx[d] / p);
+    int o = 0;  // corner (t1 + 2 t2) with the lowest vertex id
+    for (int k = 1; k < 4; ++k)
+      if (fc[k] < fc[o]) o = k;
+    const int a0 = o & 1, b0 = o >> 1;
+    const int n1 = fc[(1 - a0) + 2 * b0], n2 = fc[a0 + 2 * (1 - b0)];  // neighbours along d1, d2
+    const bool s_along_d1 = n1 < n2;
+    const int i1 = idx[d1], i2 = idx[d2];
+    const int pos1 = a0 ? p - i1 : i1, pos2 = b0 ? p - i2 : i2;  // node positions from the origin
+    const int64_t base = fbase.at(face_key(fc));
+    int s_node, t_node, s_fn, t_fn;
+    if (s_along_d1) {
+      s_node = pos1; t_node = pos2; s_fn = i1; t_fn = i2;
+    } else {
+      s_node = pos2; t_node = pos1; s_fn = i2; t_fn = i1;
+    }
+    node = base + (s_node - 1) + (int64_t)m * (t_node - 1);
+    fdm_fn = base + (s_fn - 1) + (int64_t)m * (t_fn - 1);
+    if (a0) sign *= parity[i1 - 1];
+    if (b0) sign *= parity[i2 - 1];
+  }
+};
+
+}  // namespace
+
+extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_hexmesh **out) {
+  if (!out) return FDM_EINVAL;
+  *out = nullptr;
+  if (nv < 8 || nc < 1 || !cells || p < 1 || p > 15) {
+    hex_last_error() = "fdm_hexmesh_create: need at least 8 vertices, 1 cell and 1 <= p <= 15";
+    return FDM_EINVAL;
+  }
+  fdm_hexmesh *h = new fdm_hexmesh();
+  try {
+    const int n = p + 1, n3 = n * n * n, m = p - 1;
+    h->p = p;
+    h->n = n;
+    h->nv = nv;
+    h->nc = nc;
+    Builder B{p, n, nv, nc, cells, {}, {}, {}, {}, {}, {}, {}, {}, 0};
+    const fdm::Basis1D basis = fdm::make_basis(p);
+    B.Af = basis.Af;
+    B.Bf = basis.Bf;
+    B.parity.resize(std::max(m, 0));
+    for (int j = 0; j < m; ++j) {
+      double even = 0.0, odd = 0.0, scale = 0.0;
+      for (int i = 0; i < m; ++i) {
+        const double a = basis.S[i * m + j], b = basis.S[(m - 1 - i) * m + j];
+        even = std::max(even, std::fabs(a - b));
+        odd = std::max(odd, std::fabs(a + b));
+        scale = std::max(scale, std::fabs(a));
+      }
+      if (even <= 1e-10 * scale) B.parity[j] = 1;
+      else if (odd <= 1e-10 * scale) B.parity[j] = -1;
+      else fdm::fail(FDM_EINVAL, "fdm_hexmesh_create: an interior FDM function is neither even nor odd");
+    }
+    B.number();
+    h->nnode = B.nnode;
+    h->cell_nodes.resize((size_t)nc * n3);
+    h->cell_fdm.resize((size_t)nc * n3);
+    h->cell_sign.resize((size_t)nc * n3);
+    for (int e = 0; e < nc; ++e)
+      for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j)
+          for (int i = 0; i < n; ++i) {
+            const int idx[3] = {i, j, k};
+            int64_t node, fn;
+            int sign;
+            B.map_local(e, idx, node, fn, sign);
+            const size_t l = (size_t)e * n3 + i + n * (j + n * k);
+            h->cell_nodes[l] = (int32_t)node;
+            h->cell_fdm[l] = (int32_t)fn;
+            h->cell_sign[l] = (int8_t)sign;
+          }
+    // Dirichlet: the closure of every face that belongs to one cell
+    h->dirichlet.assign(B.nnode, 0);
+    for (int e = 0; e < nc; ++e)
+      for (int d = 0; d < 3; ++d)
+        for (int s = 0; s < 2; ++s) {
+          if (B.fcount.at(Builder::face_key(B.face_corners(e, d, s))) != 1) continue;
+          for (int k = 0; k < n; ++k)
+            for (int j = 0; j < n; ++j)
+              for (int i = 0; i < n; ++i) {
+                const int idx[3] = {i, j, k};
+                if (idx[d] == (s ? p : 0)) h->dirichlet[h->cell_nodes[(size_t)e * n3 + i + n * (j + n * k)]] = 1;
+              }
+        }
+    // stars: per used vertex, the free nodes of the entities that contain it,
+    // ordered cell interiors (by cell), faces, edges, the vertex
+    std::vector<std::vector<int>> vcells(nv);
+    for (int e = 0; e < nc; ++e)
+      for (int k = 0; k < 8; ++k) vcells[cells[8 * e + k]].push_back(e);
+    h->star_ptr.push_back(0);
+    h->pat_ptr.push_back(0);
+    h->pat_colptr.push_back(0);
+    for (int v = 0; v < nv; ++v) {
+      if (vcells[v].empty()) continue;
+      std::vector<int64_t> lists[4];  // by number of end axes: 0 interior, 1 face, 2 edge, 3 vertex
+      std::vector<char> seen;
+      std::map<int64_t, int> in_star;
+      for (int e : vcells[v]) {
+        int cv = 0;
+        while (cells[8 * e + cv] != v) ++cv;
+        const int cr[3] = {cv & 1, (cv >> 1) & 1, cv >> 2};
+        for (int k = 0; k < n; ++k)
+          for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+              const int idx[3] = {i, j, k};
+              // the node's entity contains the vertex iff every end index is at the vertex's side
+              int ends = 0;
+              bool at_v = true;
+              for (int d = 0; d < 3; ++d)
+                if (idx[d] == 0 || idx[d] == p) {
+                  ++ends;
+                  if (idx[d] != cr[d] * p) at_v = false;
+                }
+              if (!at_v) continue;
+              const int64_t g = h->cell_nodes[(size_t)e * n3 + i + n * (j + n * k)];
+              if (h->dirichlet[g] || in_star.count(g)) continue;
+              in_star[g] = 0;
+              lists[ends].push_back(g);
+            }
+      }
+      std::vector<int64_t> order;
+      for (int t = 0; t < 4; ++t) {
+        if (t > 0) std::sort(lists[t].begin(), lists[t].end());
+        order.insert(order.end(), lists[t].begin(), lists[t].end());
+      }
+      if (order.empty()) continue;
+      for (size_t k = 0; k < order.size(); ++k) in_star[order[k]] = (int)k;
+      h->star_vertex.push_back(v);
+      for (int64_t g : order) h->star_nodes.push_back((int32_t)g);
+      h->star_ptr.push_back((int64_t)h->star_nodes.size());
+      // the surrogate pattern: FDM functions c1, c2 of a star cell couple iff for
+      // some axis a, Af couples them along a and Bf along the other two axes
+      const int ns = (int)order.size();
+      std::vector<std::vector<int>> rows(ns);
+      for (int e : vcells[v]) {
+        // (cell-local FDM index, star position): an entity's FDM functions use the
+        // slots of its nodes, so the star's functions are those whose slot is a star node
+        std::vector<std::pair<int, int>> loc;
+        for (int c = 0; c < n3; ++c) {
+          auto it = in_star.find(h->cell_fdm[(size_t)e * n3 + c]);
+          if (it != in_star.end()) loc.push_back({c, it->second});
+        }
+        for (auto &x : loc)
+          for (auto &y : loc) {
+            const int a[3] = {x.first % n, (x.first / n) % n, x.first / (n * n)};
+            const int b[3] = {y.first % n, (y.first / n) % n, y.first / (n * n)};
+            bool nz = false;
+            for (int d = 0; d < 3 && !nz; ++d) {
+              bool term = B.Af[a[d] * n + b[d]] != 0.0;
+              for (int o = 0; o < 3 && term; ++o)
+                if (o != d) term = B.Bf[a[o] * n + b[o]] != 0.0;
+              nz = term;
+            }
+            if (nz) rows[x.second].push_back(y.second);
+          }
+      }
+      h->pat_rowptr.push_back(0);
+      int64_t cnt = 0;
+      for (auto &r : rows) {
+        std::sort(r.begin(), r.end());
+        r.erase(std::unique(r.begin(), r.end()), r.end());
+        for (int c : r) h->pat_cols.push_back(c);
+        cnt += (int64_t)r.size();
+        h->pat_rowptr.push_back(cnt);
+      }
+      h->pat_ptr.push_back((int64_t)h->pat_rowptr.size());
+      h->pat_colptr.push_back((int64_t)h->pat_cols.size());
+    }
+  } catch (const fdm::Error &e) {
+    int rc = handle_hex(h, e);
+    delete h;
+    return rc;
+  } catch (const std::exception &e) {
+    hex_last_error() = std::string("fdm_hexmesh_create: ") + e.what();
+    delete h;
+    return FDM_EINVAL;
+  }
+  *out = h;
+  return FDM_OK;
+}
+
+extern "C" int fdm_hexmesh_query(fdm_hexmesh *h, int what, void *out, size_t *len) {
+  if (!h || !len) return FDM_EINVAL;
+  auto put = [&](const void *src, size_t bytes) {
+    if (out) {
+      if (*len < bytes) {
+        h->err = "fdm_hexmesh_query: buffer too small";
+        return FDM_EINVAL;
+      }
+      if (bytes) std::copy((const char *)src, (const char *)src + bytes, (char *)out);
+    }
+    *len = bytes;
+    return FDM_OK;
+  };
+  const int32_t nstar = (int32_t)h->star_vertex.size();
+  switch (what) {
+    case FDM_HQ_NNODE: return put(&h->nnode, sizeof(int64_t));
+    case FDM_HQ_CELL_NODES: return put(h->cell_nodes.data(), h->cell_nodes.size() * sizeof(int32_t));
+    case FDM_HQ_CELL_FDM: return put(h->cell_fdm.data(), h->cell_fdm.size() * sizeof(int32_t));
+    case FDM_HQ_CELL_SIGN: return put(h->cell_sign.data(), h->cell_sign.size() * sizeof(int8_t));
+    case FDM_HQ_DIRICHLET: return put(h->dirichlet.data(), h->dirichlet.size());
+    case FDM_HQ_NSTAR: return put(&nstar, sizeof(int32_t));
+    case FDM_HQ_STAR_VERTEX: return put(h->star_vertex.data(), h->star_vertex.size() * sizeof(int32_t));
+    case FDM_HQ_STAR_PTR: return put(h->star_ptr.data(), h->star_ptr.size() * sizeof(int64_t));
+    case FDM_HQ_STAR_NODES: return put(h->star_nodes.data(), h->star_nodes.size() * sizeof(int32_t));
+    case FDM_HQ_PATTERN_PTR: return put(h->pat_ptr.data(), h->pat_ptr.size() * sizeof(int64_t));
+    case FDM_HQ_PATTERN_ROWPTR: return put(h->pat_rowptr.data(), h->pat_rowptr.size() * sizeof(int64_t));
+    case FDM_HQ_PATTERN_COLPTR: return put(h->pat_colptr.data(), h->pat_colptr.size() * sizeof(int64_t));
+    case FDM_HQ_PATTERN_COLS: return put(h->pat_cols.data(), h->pat_cols.size() * sizeof(int32_t));
+    default:
+      h->err = "fdm_hexmesh_query: unknown query";
+      return FDM_EINVAL;
+  }
+}
+
+extern "C" const char *fdm_hexmesh_last_error(const fdm_hexmesh *h) {
+  return h ? h->err.c_str() : hex_last_error().c_str();
+}
+
+extern "C" void fdm_hexmesh_destroy(fdm_hexmesh *h) { delete h; }

@@ -24,6 +24,9 @@ FDM_SURR_AVERAGED, FDM_SURR_EXTERNAL = 0, 1
  FDM_Q_SETUP_SECONDS, FDM_Q_KERNEL_TIMES, FDM_Q_LAUNCHES, FDM_Q_ALGO_BYTES, FDM_Q_STATUS,
  FDM_Q_SURR_FEATURES, FDM_Q_SURR_LABELS, FDM_Q_SURR_BOUNDS, FDM_Q_MUBAR, FDM_Q_SURR_OUTPUT, FDM_Q_TUNING,
  FDM_Q_GMG_LEVELS, FDM_Q_GMG_STENCIL, FDM_Q_ALGO_BYTES_LFORM) = range(1, 28)
+(FDM_HQ_NNODE, FDM_HQ_CELL_NODES, FDM_HQ_CELL_FDM, FDM_HQ_CELL_SIGN, FDM_HQ_DIRICHLET, FDM_HQ_NSTAR,
+ FDM_HQ_STAR_VERTEX, FDM_HQ_STAR_PTR, FDM_HQ_STAR_NODES, FDM_HQ_PATTERN_PTR, FDM_HQ_PATTERN_ROWPTR,
+ FDM_HQ_PATTERN_COLPTR, FDM_HQ_PATTERN_COLS) = range(1, 14)
 FDM_MLP_NPARAM = 16515
 TIMERS = ("restrict", "patch", "interp", "op64", "op32", "coarse", "vec")
 
@@ -115,6 +118,12 @@ def load():
     L.fdm_sipg_last_error.restype = C.c_char_p
     L.fdm_sipg_destroy.argtypes = [vp]
     L.fdm_sipg_destroy.restype = None
+    L.fdm_hexmesh_create.argtypes = [C.c_int, C.c_int, ip, C.c_int, C.POINTER(vp)]
+    L.fdm_hexmesh_query.argtypes = [vp, C.c_int, vp, C.POINTER(C.c_size_t)]
+    L.fdm_hexmesh_last_error.argtypes = [vp]
+    L.fdm_hexmesh_last_error.restype = C.c_char_p
+    L.fdm_hexmesh_destroy.argtypes = [vp]
+    L.fdm_hexmesh_destroy.restype = None
     _lib = L
     return L
 
@@ -724,3 +733,72 @@ class Sipg:
         out = np.zeros(1, dtype=np.int64)
         fdm_sipg_query(self.h, FDM_Q_LAUNCHES, out)
         return int(out[0])
+
+
+class HexMesh:
+    """Host topology of a conforming hexahedral mesh (fdm_hexmesh_create):
+    node numbering, Dirichlet nodes, vertex stars in FDM order, the signed
+    cell-to-global FDM map and the stars' surrogate patterns.  Host arrays
+    only; needs no GPU."""
+
+    def __init__(self, nv, cells, p):
+        L = load()
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        self.p, self.n, self.nc = p, p + 1, cells.shape[0]
+        h = C.c_void_p()
+        rc = L.fdm_hexmesh_create(int(nv), self.nc, cells.ctypes.data_as(C.POINTER(C.c_int)), p, C.byref(h))
+        if rc < 0:
+            raise FdmError(rc, L.fdm_hexmesh_last_error(None).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().fdm_hexmesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def query(self, what, dtype):
+        L = load()
+        n = C.c_size_t(0)
+        rc = L.fdm_hexmesh_query(self.h, what, None, C.byref(n))
+        if rc < 0:
+            raise FdmError(rc, L.fdm_hexmesh_last_error(self.h).decode())
+        out = np.zeros(n.value // np.dtype(dtype).itemsize, dtype=dtype)
+        rc = L.fdm_hexmesh_query(self.h, what, out.ctypes.data_as(C.c_void_p), C.byref(n))
+        if rc < 0:
+            raise FdmError(rc, L.fdm_hexmesh_last_error(self.h).decode())
+        return out
+
+    @property
+    def nnode(self):
+        return int(self.query(FDM_HQ_NNODE, np.int64)[0])
+
+    def cell_nodes(self):
+        return self.query(FDM_HQ_CELL_NODES, np.int32).reshape(self.nc, self.n ** 3)
+
+    def cell_fdm(self):
+        return (self.query(FDM_HQ_CELL_FDM, np.int32).reshape(self.nc, self.n ** 3),
+                self.query(FDM_HQ_CELL_SIGN, np.int8).reshape(self.nc, self.n ** 3))
+
+    def dirichlet(self):
+        return self.query(FDM_HQ_DIRICHLET, np.uint8).astype(bool)
+
+    def stars(self):
+        """[(vertex, nodes in FDM order)] for every star."""
+        vert = self.query(FDM_HQ_STAR_VERTEX, np.int32)
+        ptr = self.query(FDM_HQ_STAR_PTR, np.int64)
+        nodes = self.query(FDM_HQ_STAR_NODES, np.int32)
+        return [(int(vert[k]), nodes[ptr[k]:ptr[k + 1]]) for k in range(len(vert))]
+
+    def patterns(self):
+        """Per star, (rowptr, cols) of its surrogate pattern over star positions."""
+        pp = self.query(FDM_HQ_PATTERN_PTR, np.int64)
+        rp = self.query(FDM_HQ_PATTERN_ROWPTR, np.int64)
+        cp = self.query(FDM_HQ_PATTERN_COLPTR, np.int64)
+        cols = self.query(FDM_HQ_PATTERN_COLS, np.int32)
+        return [(rp[pp[k]:pp[k + 1]], cols[cp[k]:cp[k + 1]]) for k in range(len(pp) - 1)]

@@ -1,0 +1,123 @@
+"""CPU tests of the library's host topology for general hexahedral meshes
+(fdm_hexmesh_*, through the C-ABI; no GPU) against the unstructured oracle
+(oracle/unstructured.py), which numbers nodes independently by merging the
+cells' GLL nodes by position and glues its star FDM bases by matching traces:
+
+* the library's node numbering is a consistent bijection onto the oracle's
+  (every cell-local node maps through it to the oracle's node);
+* Dirichlet nodes and every star's node set agree;
+* the star FDM functions built from the library's signed cell-to-global map
+  agree on every node shared by two cells (the parity signs are right), and
+  the library's structural star pattern equals the numerical pattern of the
+  oracle's surrogate star matrix in that basis;
+* interior rows of every star pattern have d + 1 = 4 entries and no
+  interior-interior coupling (Section 2.6);
+* invalid meshes are rejected.
+"""
+import numpy as np
+import pytest
+
+from oracle.unstructured import HexProblem, _kron3
+from paper_2107_14758_gb300 import inputs
+
+
+@pytest.fixture(scope="module")
+def fdmpc():
+    from paper_2107_14758_gb300 import build
+    build.build()
+    from paper_2107_14758_gb300 import fdmpc as f
+    return f
+
+
+MESHES = {
+    "unstructured": lambda: inputs.unstructured_hex_mesh(2, 2, 5),
+    "reoriented_tensor": lambda: (lambda X, c: (X, inputs.reorient_cells(c, 11)))(
+        *inputs.tensor_hex_mesh(*inputs.graded_vertices(3, 4))),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MESHES))
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_topology_matches_the_oracle(fdmpc, name, p):
+    X, cells = MESHES[name]()
+    H = fdmpc.HexMesh(X.shape[0], cells, p)
+    U = HexProblem(p, X, cells)
+    n = p + 1
+    cn = H.cell_nodes()
+    assert H.nnode == U.ndof
+    pi = -np.ones(H.nnode, dtype=np.int64)
+    pi[cn.ravel()] = U.gid.ravel()
+    assert np.array_equal(pi[cn], U.gid)                      # consistent
+    assert np.array_equal(np.sort(pi), np.arange(U.ndof))     # bijective
+    assert np.array_equal(H.dirichlet(), U.dirichlet[pi])
+    stars = H.stars()
+    assert len(stars) == sum(1 for v in range(X.shape[0]) if len(U.star_dofs(v)))
+    cf, cs = H.cell_fdm()
+    T3 = _kron3(U.T1, U.T1, U.T1)
+    for (v, nodes), (rp, cols) in zip(stars, H.patterns()):
+        assert np.array_equal(np.sort(pi[nodes]), U.star_dofs(v))
+        pos = {int(g): i for i, g in enumerate(nodes)}
+        ns = len(nodes)
+        Tv = np.zeros((ns, ns))
+        setm = np.zeros((ns, ns), dtype=bool)
+        for e in U.vertex_cells[v]:
+            rows = np.array([pos.get(int(g), -1) for g in cn[e]])
+            inside = rows >= 0
+            for c in range(n ** 3):
+                col = pos.get(int(cf[e, c]))
+                if col is None:
+                    continue
+                vals = cs[e, c] * T3[:, c]
+                assert np.abs(vals[~inside]).max(initial=0.0) <= 1e-13
+                r = rows[inside]
+                prev = setm[r, col]
+                assert np.abs(Tv[r[prev], col] - vals[inside][prev]).max(initial=0.0) <= 1e-12
+                Tv[r, col] = vals[inside]
+                setm[r, col] = True
+        dofs = pi[nodes]
+        Af = Tv.T @ U.As[dofs][:, dofs].toarray() @ Tv
+        P = np.zeros((ns, ns), dtype=bool)
+        for r in range(ns):
+            P[r, cols[rp[r]:rp[r + 1]]] = True
+        assert np.array_equal(np.abs(Af) > 1e-12 * np.abs(Af).max(), P)
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_interior_rows_of_star_patterns(fdmpc, p):
+    X, cells = inputs.unstructured_hex_mesh(2, 2, 5)
+    H = fdmpc.HexMesh(X.shape[0], cells, p)
+    cn = H.cell_nodes()
+    interior = np.zeros(H.nnode, dtype=bool)
+    n = p + 1
+    idx = np.arange(n)
+    I3 = np.stack(np.meshgrid(idx, idx, idx, indexing="ij"), axis=-1).reshape(-1, 3)
+    cell_int = np.all((I3 > 0) & (I3 < p), axis=1)
+    interior[cn[:, cell_int].ravel()] = True
+    for (v, nodes), (rp, cols) in zip(H.stars(), H.patterns()):
+        ni = int(interior[nodes].sum())
+        assert interior[nodes[:ni]].all() and not interior[nodes[ni:]].any()  # interiors first
+        for r in range(ni):
+            row = cols[rp[r]:rp[r + 1]]
+            assert r in row and not np.any((row < ni) & (row != r))
+            # itself plus the faces of its cell that contain v (3, fewer at the boundary)
+            assert len(row) <= 4
+
+
+def test_invalid_meshes(fdmpc):
+    X, cells = inputs.tensor_hex_mesh(*inputs.uniform_vertices(2))
+    nv = X.shape[0]
+    with pytest.raises(fdmpc.FdmError):
+        fdmpc.HexMesh(nv, cells, 0)
+    with pytest.raises(fdmpc.FdmError):
+        fdmpc.HexMesh(nv, cells, 16)
+    bad = cells.copy()
+    bad[0, 0] = nv
+    with pytest.raises(fdmpc.FdmError, match="out of range"):
+        fdmpc.HexMesh(nv, bad, 2)
+    bad = cells.copy()
+    bad[0, 1] = bad[0, 0]
+    with pytest.raises(fdmpc.FdmError, match="degenerate"):
+        fdmpc.HexMesh(nv, bad, 2)
+    three = np.concatenate([cells[:1], cells[:1], cells[:1]])
+    with pytest.raises(fdmpc.FdmError, match="more than two cells"):
+        fdmpc.HexMesh(nv, three, 2)

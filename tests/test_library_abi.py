@@ -37,7 +37,8 @@ def test_header_declares_the_boundary():
                      "fdm_elast_setup", "elast_apply", "elast_pc_apply", "elast_pcg_solve", "fdm_elast_query",
                      "fdm_elast_destroy", "fdm_sipg_setup", "sipg_apply", "sipg_asm_apply", "sipg_pc_apply",
                      "sipg_patch_solve", "sipg_pcg_solve", "fdm_sipg_query", "fdm_sipg_last_error",
-                     "fdm_sipg_destroy", "stiffness_apply_noalloc"):
+                     "fdm_sipg_destroy", "stiffness_apply_noalloc", "fdm_hexmesh_create", "fdm_hexmesh_query",
+                     "fdm_hexmesh_last_error", "fdm_hexmesh_destroy"):
         assert required in names
 
 
