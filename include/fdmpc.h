@@ -376,7 +376,10 @@ void fdm_sipg_destroy(fdm_sipg *s);
  * function reversed.  Dirichlet nodes: the closure of the faces of one cell.
  * Stars: every used vertex with at least one free node; its free nodes
  * ordered cell interiors (by cell), faces, edges, the vertex; the pattern of
- * its separable surrogate matrix in the FDM basis as CSR over star positions.
+ * its separable surrogate matrix in the FDM basis as CSR over star positions
+ * (its interior block is diagonal, Section 2.6).  Stars with equal patterns
+ * form a class, which shares the symbolic Cholesky factorisation (elimination
+ * tree and fill) of the interface Schur complement (Section 2.6, eq. LDLT).
  * FDM_EINVAL for a vertex id out of range, a degenerate cell, a face of more
  * than two cells or more than 2^31 - 1 nodes; fdm_hexmesh_last_error. */
 typedef struct fdm_hexmesh fdm_hexmesh;
@@ -394,6 +397,20 @@ int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_hexmesh **ou
 #define FDM_HQ_PATTERN_ROWPTR 11 /* int64[...]: per star, CSR row pointers starting at 0 */
 #define FDM_HQ_PATTERN_COLPTR 12 /* int64[nstar + 1]: offsets into FDM_HQ_PATTERN_COLS */
 #define FDM_HQ_PATTERN_COLS 13  /* int32[...]: per star, CSR column positions (sorted per row) */
+#define FDM_HQ_STAR_NINT 14     /* int32[nstar]: cell-interior functions of each star (its first positions) */
+#define FDM_HQ_STAR_CLASS 15    /* int32[nstar]: sparsity class (equal pattern and interior count) */
+#define FDM_HQ_NCLASS 16        /* int32: number of classes */
+#define FDM_HQ_CLASS_STAR 17    /* int32[nclass]: the first star of each class */
+#define FDM_HQ_CLASS_NNZL 18    /* int64[nclass]: nonzeros of the Cholesky factor L of the class's
+                                 * interface Schur complement S_G = A_GG - A_GI D^{-1} A_IG
+                                 * (interface positions in star order, diagonal included) */
+#define FDM_HQ_FILL_PTR 19      /* int64[nclass + 1]: offsets into FDM_HQ_FILL_ROWPTR (interface size + 1 each) */
+#define FDM_HQ_FILL_ROWPTR 20   /* int64[...]: per class, CSR row pointers of L starting at 0 */
+#define FDM_HQ_FILL_COLPTR 21   /* int64[nclass + 1]: offsets into FDM_HQ_FILL_COLS */
+#define FDM_HQ_FILL_COLS 22     /* int32[...]: per class, the columns of each row of L (sorted) */
+#define FDM_HQ_ETREE_PTR 23     /* int64[nclass + 1]: offsets into FDM_HQ_ETREE */
+#define FDM_HQ_ETREE 24         /* int32[...]: per class, the elimination-tree parent of each
+                                 * interface column (-1 for a root) */
 /* Copies `what` into out (HOST); *len is the capacity in bytes on input and
  * the size written on output (out NULL: the size only). */
 int fdm_hexmesh_query(fdm_hexmesh *h, int what, void *out, size_t *len);

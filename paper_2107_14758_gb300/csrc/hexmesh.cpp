@@ -41,10 +41,53 @@ struct fdm_hexmesh {
   std::vector<int64_t> pat_rowptr;   // per star: CSR row pointers (star-local, from 0)
   std::vector<int64_t> pat_colptr;   // [nstar + 1] into pat_cols
   std::vector<int32_t> pat_cols;     // per star: CSR column indices (star-local positions)
+  std::vector<int32_t> star_nint;    // [nstar] cell-interior functions (the first positions)
+  std::vector<int32_t> star_class;   // [nstar] sparsity class
+  // per class: its interface Schur complement S_G = A_GG - A_GI D^{-1} A_IG factored
+  // symbolically: elimination tree and the rows of L (lower, diagonal included)
+  std::vector<int32_t> class_star;   // [nclass] first star of the class
+  std::vector<int64_t> class_nnzl;   // [nclass] nonzeros of L
+  std::vector<int64_t> fill_ptr;     // [nclass + 1] into fill_rowptr (interface size + 1 each)
+  std::vector<int64_t> fill_rowptr;  // per class: CSR row pointers of L from 0
+  std::vector<int64_t> fill_colptr;  // [nclass + 1] into fill_cols
+  std::vector<int32_t> fill_cols;    // per class: columns of each row of L (interface positions, sorted)
+  std::vector<int64_t> etree_ptr;    // [nclass + 1] into etree
+  std::vector<int32_t> etree;        // per class: parent of each interface column (-1: root)
   std::string err;
 };
 
 namespace {
+
+// Symbolic Cholesky of a symmetric pattern given by its rows (diagonal
+// included): column j of L holds the later rows of column j of S and of the
+// columns of L whose elimination-tree parent is j.  Returns the rows of L
+// (lower, diagonal included) and the parents.
+void symbolic_cholesky(const std::vector<std::vector<int>> &S, std::vector<std::vector<int>> &Lrows,
+                       std::vector<int> &parent) {
+  const int m = (int)S.size();
+  std::vector<std::vector<int>> cols(m), children(m);
+  parent.assign(m, -1);
+  Lrows.assign(m, {});
+  for (int j = 0; j < m; ++j) {
+    std::vector<int> c;
+    for (int i : S[j])
+      if (i > j) c.push_back(i);
+    for (int ch : children[j]) {
+      for (int i : cols[ch])
+        if (i > j) c.push_back(i);
+      std::vector<int>().swap(cols[ch]);  // a column merges into its parent only
+    }
+    std::sort(c.begin(), c.end());
+    c.erase(std::unique(c.begin(), c.end()), c.end());
+    if (!c.empty()) {
+      parent[j] = c[0];
+      children[c[0]].push_back(j);
+    }
+    Lrows[j].push_back(j);
+    for (int i : c) Lrows[i].push_back(j);
+    cols[j] = std::move(c);
+  }
+}
 
 std::string &hex_last_error() {
   static std::string e;
@@ -272,6 +315,7 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
     std::vector<std::vector<int>> vcells(nv);
     for (int e = 0; e < nc; ++e)
       for (int k = 0; k < 8; ++k) vcells[cells[8 * e + k]].push_back(e);
+    std::map<std::vector<int>, int> classes;
     h->star_ptr.push_back(0);
     h->pat_ptr.push_back(0);
     h->pat_colptr.push_back(0);
@@ -303,6 +347,7 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
               lists[ends].push_back(g);
             }
       }
+      const int nint = (int)lists[0].size();
       std::vector<int64_t> order;
       for (int t = 0; t < 4; ++t) {
         if (t > 0) std::sort(lists[t].begin(), lists[t].end());
@@ -350,6 +395,63 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
       }
       h->pat_ptr.push_back((int64_t)h->pat_rowptr.size());
       h->pat_colptr.push_back((int64_t)h->pat_cols.size());
+      h->star_nint.push_back(nint);
+      // the class: stars with equal patterns and interior counts share the
+      // symbolic factorisation of their interface Schur complement
+      std::vector<int> key;
+      key.push_back(ns);
+      key.push_back(nint);
+      for (auto &r : rows) {
+        key.push_back((int)r.size());
+        key.insert(key.end(), r.begin(), r.end());
+      }
+      auto found = classes.find(key);
+      if (found != classes.end()) {
+        h->star_class.push_back(found->second);
+        continue;
+      }
+      const int cls = (int)h->class_star.size();
+      classes.emplace(std::move(key), cls);
+      h->star_class.push_back(cls);
+      h->class_star.push_back((int32_t)h->star_vertex.size() - 1);
+      // pattern of S_G: A_GG plus, through every interior function, the
+      // interface functions it couples to (the interior block is diagonal)
+      const int nG = ns - nint;
+      std::vector<std::vector<int>> Sg(nG);
+      for (int r = nint; r < ns; ++r) {
+        std::vector<int> &out = Sg[r - nint];
+        for (int c : rows[r]) {
+          if (c >= nint) out.push_back(c - nint);
+          else
+            for (int c2 : rows[c])
+              if (c2 >= nint) out.push_back(c2 - nint);
+        }
+        std::sort(out.begin(), out.end());
+        out.erase(std::unique(out.begin(), out.end()), out.end());
+      }
+      for (int r = 0; r < nint; ++r)
+        for (int c : rows[r])
+          if (c < nint && c != r) fdm::fail(FDM_EINVAL, "fdm_hexmesh_create: interior block of a star is not diagonal");
+      std::vector<std::vector<int>> Lrows;
+      std::vector<int> parent;
+      symbolic_cholesky(Sg, Lrows, parent);
+      if (h->fill_ptr.empty()) {
+        h->fill_ptr.push_back(0);
+        h->fill_colptr.push_back(0);
+        h->etree_ptr.push_back(0);
+      }
+      int64_t nnzl = 0;
+      h->fill_rowptr.push_back(0);
+      for (auto &r : Lrows) {
+        h->fill_cols.insert(h->fill_cols.end(), r.begin(), r.end());
+        nnzl += (int64_t)r.size();
+        h->fill_rowptr.push_back(nnzl);
+      }
+      h->fill_ptr.push_back((int64_t)h->fill_rowptr.size());
+      h->fill_colptr.push_back((int64_t)h->fill_cols.size());
+      h->etree.insert(h->etree.end(), parent.begin(), parent.end());
+      h->etree_ptr.push_back((int64_t)h->etree.size());
+      h->class_nnzl.push_back(nnzl);
     }
   } catch (const fdm::Error &e) {
     int rc = handle_hex(h, e);
@@ -392,6 +494,20 @@ extern "C" int fdm_hexmesh_query(fdm_hexmesh *h, int what, void *out, size_t *le
     case FDM_HQ_PATTERN_ROWPTR: return put(h->pat_rowptr.data(), h->pat_rowptr.size() * sizeof(int64_t));
     case FDM_HQ_PATTERN_COLPTR: return put(h->pat_colptr.data(), h->pat_colptr.size() * sizeof(int64_t));
     case FDM_HQ_PATTERN_COLS: return put(h->pat_cols.data(), h->pat_cols.size() * sizeof(int32_t));
+    case FDM_HQ_STAR_NINT: return put(h->star_nint.data(), h->star_nint.size() * sizeof(int32_t));
+    case FDM_HQ_STAR_CLASS: return put(h->star_class.data(), h->star_class.size() * sizeof(int32_t));
+    case FDM_HQ_NCLASS: {
+      const int32_t nclass = (int32_t)h->class_star.size();
+      return put(&nclass, sizeof(int32_t));
+    }
+    case FDM_HQ_CLASS_STAR: return put(h->class_star.data(), h->class_star.size() * sizeof(int32_t));
+    case FDM_HQ_CLASS_NNZL: return put(h->class_nnzl.data(), h->class_nnzl.size() * sizeof(int64_t));
+    case FDM_HQ_FILL_PTR: return put(h->fill_ptr.data(), h->fill_ptr.size() * sizeof(int64_t));
+    case FDM_HQ_FILL_ROWPTR: return put(h->fill_rowptr.data(), h->fill_rowptr.size() * sizeof(int64_t));
+    case FDM_HQ_FILL_COLPTR: return put(h->fill_colptr.data(), h->fill_colptr.size() * sizeof(int64_t));
+    case FDM_HQ_FILL_COLS: return put(h->fill_cols.data(), h->fill_cols.size() * sizeof(int32_t));
+    case FDM_HQ_ETREE_PTR: return put(h->etree_ptr.data(), h->etree_ptr.size() * sizeof(int64_t));
+    case FDM_HQ_ETREE: return put(h->etree.data(), h->etree.size() * sizeof(int32_t));
     default:
       h->err = "fdm_hexmesh_query: unknown query";
       return FDM_EINVAL;

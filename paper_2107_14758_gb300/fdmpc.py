@@ -26,7 +26,9 @@ FDM_SURR_AVERAGED, FDM_SURR_EXTERNAL = 0, 1
  FDM_Q_GMG_LEVELS, FDM_Q_GMG_STENCIL, FDM_Q_ALGO_BYTES_LFORM) = range(1, 28)
 (FDM_HQ_NNODE, FDM_HQ_CELL_NODES, FDM_HQ_CELL_FDM, FDM_HQ_CELL_SIGN, FDM_HQ_DIRICHLET, FDM_HQ_NSTAR,
  FDM_HQ_STAR_VERTEX, FDM_HQ_STAR_PTR, FDM_HQ_STAR_NODES, FDM_HQ_PATTERN_PTR, FDM_HQ_PATTERN_ROWPTR,
- FDM_HQ_PATTERN_COLPTR, FDM_HQ_PATTERN_COLS) = range(1, 14)
+ FDM_HQ_PATTERN_COLPTR, FDM_HQ_PATTERN_COLS, FDM_HQ_STAR_NINT, FDM_HQ_STAR_CLASS, FDM_HQ_NCLASS,
+ FDM_HQ_CLASS_STAR, FDM_HQ_CLASS_NNZL, FDM_HQ_FILL_PTR, FDM_HQ_FILL_ROWPTR, FDM_HQ_FILL_COLPTR, FDM_HQ_FILL_COLS,
+ FDM_HQ_ETREE_PTR, FDM_HQ_ETREE) = range(1, 25)
 FDM_MLP_NPARAM = 16515
 TIMERS = ("restrict", "patch", "interp", "op64", "op32", "coarse", "vec")
 
@@ -802,3 +804,20 @@ class HexMesh:
         cp = self.query(FDM_HQ_PATTERN_COLPTR, np.int64)
         cols = self.query(FDM_HQ_PATTERN_COLS, np.int32)
         return [(rp[pp[k]:pp[k + 1]], cols[cp[k]:cp[k + 1]]) for k in range(len(pp) - 1)]
+
+    def classes(self):
+        """Per star its class and interior count; per class (first star,
+        nnz(L), rows of L as (rowptr, cols), elimination-tree parents)."""
+        cls = self.query(FDM_HQ_STAR_CLASS, np.int32)
+        nint = self.query(FDM_HQ_STAR_NINT, np.int32)
+        first = self.query(FDM_HQ_CLASS_STAR, np.int32)
+        nnzl = self.query(FDM_HQ_CLASS_NNZL, np.int64)
+        fp = self.query(FDM_HQ_FILL_PTR, np.int64)
+        fr = self.query(FDM_HQ_FILL_ROWPTR, np.int64)
+        fc = self.query(FDM_HQ_FILL_COLPTR, np.int64)
+        cols = self.query(FDM_HQ_FILL_COLS, np.int32)
+        ep = self.query(FDM_HQ_ETREE_PTR, np.int64)
+        et = self.query(FDM_HQ_ETREE, np.int32)
+        per = [(int(first[k]), int(nnzl[k]), (fr[fp[k]:fp[k + 1]], cols[fc[k]:fc[k + 1]]), et[ep[k]:ep[k + 1]])
+               for k in range(len(first))]
+        return cls, nint, per

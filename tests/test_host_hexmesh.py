@@ -12,6 +12,11 @@ cells' GLL nodes by position and glues its star FDM bases by matching traces:
   oracle's surrogate star matrix in that basis;
 * interior rows of every star pattern have d + 1 = 4 entries and no
   interior-interior coupling (Section 2.6);
+* every class's symbolic factorisation of the interface Schur complement
+  (fill and elimination tree) equals the oracle's symbolic fill of the
+  numerically formed Schur complement, the numeric Cholesky factor stays
+  inside it, and a tensor mesh in lexicographic orientation has the 8 star
+  classes of the structured path;
 * invalid meshes are rejected.
 """
 import numpy as np
@@ -121,3 +126,68 @@ def test_invalid_meshes(fdmpc):
     three = np.concatenate([cells[:1], cells[:1], cells[:1]])
     with pytest.raises(fdmpc.FdmError, match="more than two cells"):
         fdmpc.HexMesh(nv, three, 2)
+
+
+@pytest.mark.parametrize("name", sorted(MESHES))
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_class_symbolic_factorisation(fdmpc, oracle_lib, name, p):
+    """Each class's fill and elimination tree equal the oracle's symbolic
+    fill of the numerically formed interface Schur complement of its first
+    star (in the basis of the library's signed FDM map), the numeric Cholesky
+    factor stays inside the fill, and every star of a class has its pattern."""
+    X, cells = MESHES[name]()
+    H = fdmpc.HexMesh(X.shape[0], cells, p)
+    U = HexProblem(p, X, cells)
+    n = p + 1
+    cn = H.cell_nodes()
+    cf, cs = H.cell_fdm()
+    pi = np.zeros(H.nnode, dtype=np.int64)
+    pi[cn.ravel()] = U.gid.ravel()
+    T3 = _kron3(U.T1, U.T1, U.T1)
+    stars, pats = H.stars(), H.patterns()
+    cls, nint, per = H.classes()
+    assert len(cls) == len(stars) and cls.max() + 1 == len(per)
+    for k in range(len(stars)):
+        first = per[cls[k]][0]
+        assert nint[k] == nint[first]
+        assert all(np.array_equal(a, b) for a, b in zip(pats[k], pats[first]))
+    for first, nnzl, (rp, cols), parent in per:
+        v, nodes = stars[first]
+        pos = {int(g): i for i, g in enumerate(nodes)}
+        ns, ni = len(nodes), int(nint[first])
+        Tv = np.zeros((ns, ns))
+        for e in U.vertex_cells[v]:
+            rows = np.array([pos.get(int(g), -1) for g in cn[e]])
+            inside = rows >= 0
+            for c in range(n ** 3):
+                col = pos.get(int(cf[e, c]))
+                if col is not None:
+                    Tv[rows[inside], col] = cs[e, c] * T3[inside, c]
+        Af = Tv.T @ U.As[pi[nodes]][:, pi[nodes]].toarray() @ Tv
+        S = Af[ni:, ni:] - Af[ni:, :ni] @ (Af[:ni, ni:] / np.diag(Af)[:ni, None])
+        nG = ns - ni
+        if nG == 0:
+            assert nnzl == 0
+            continue
+        Lp = np.zeros((nG, nG), dtype=bool)
+        for r in range(nG):
+            Lp[r, cols[rp[r]:rp[r + 1]]] = True
+        assert Lp.sum() == nnzl
+        assert np.array_equal(oracle_lib.symbolic_fill(np.abs(S) > 1e-12 * np.abs(S).max()), Lp)
+        L = np.linalg.cholesky(S)
+        assert not np.any((np.abs(L) > 1e-12 * np.abs(L).max()) & ~Lp)
+        for j in range(nG):
+            below = np.flatnonzero(Lp[j + 1:, j])
+            assert parent[j] == (j + 1 + below[0] if len(below) else -1)
+
+
+def test_tensor_mesh_has_the_eight_structured_classes(fdmpc):
+    """On a tensor mesh listed in lexicographic orientation the stars fall into
+    the 8 classes of the structured path (interior, 3 face, 3 edge and corner
+    stars) for p >= 3."""
+    X, cells = inputs.tensor_hex_mesh(*inputs.graded_vertices(4, 4))
+    for p in (3, 4):
+        cls, nint, per = fdmpc.HexMesh(X.shape[0], cells, p).classes()
+        assert len(per) == 8
+        sizes = sorted({(int(nint[f]), int(nnzl)) for f, nnzl, _, _ in per})
+        assert sizes[-1][0] == 8 * (p - 1) ** 3  # the interior star's 8 cell interiors
