@@ -375,7 +375,9 @@ void fdm_sipg_destroy(fdm_sipg *s);
  * an edge or face axis), with a sign -1 where a cell sees an odd interior
  * function reversed.  Dirichlet nodes: the closure of the faces of one cell.
  * Stars: every used vertex with at least one free node; its free nodes
- * ordered cell interiors (by cell), faces, edges, the vertex; the pattern of
+ * ordered cell interiors (by cell), then the interface (faces, edges, the
+ * vertex) entity by entity in minimum-degree order of the interface Schur
+ * complement's pattern (each entity's functions by node number); the pattern of
  * its separable surrogate matrix in the FDM basis as CSR over star positions
  * (its interior block is diagonal, Section 2.6).  Stars with equal patterns
  * form a class, which shares the symbolic Cholesky factorisation (elimination
@@ -392,7 +394,7 @@ int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_hexmesh **ou
 #define FDM_HQ_NSTAR 6          /* int32: number of stars */
 #define FDM_HQ_STAR_VERTEX 7    /* int32[nstar]: the vertex of each star */
 #define FDM_HQ_STAR_PTR 8       /* int64[nstar + 1]: offsets into FDM_HQ_STAR_NODES */
-#define FDM_HQ_STAR_NODES 9     /* int32[...]: each star's nodes in FDM order */
+#define FDM_HQ_STAR_NODES 9     /* int32[...]: each star's nodes in star order */
 #define FDM_HQ_PATTERN_PTR 10   /* int64[nstar + 1]: offsets into FDM_HQ_PATTERN_ROWPTR (star size + 1 each) */
 #define FDM_HQ_PATTERN_ROWPTR 11 /* int64[...]: per star, CSR row pointers starting at 0 */
 #define FDM_HQ_PATTERN_COLPTR 12 /* int64[nstar + 1]: offsets into FDM_HQ_PATTERN_COLS */

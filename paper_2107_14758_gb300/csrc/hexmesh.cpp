@@ -1,7 +1,8 @@
 // Host topology of a conforming hexahedral mesh for the vertex-star
 // relaxation on unstructured meshes (Sections 2.4 and 2.6 applied to general
 // meshes): the Q_p node numbering shared by neighbouring cells of any
-// orientation, the Dirichlet nodes, the vertex stars in FDM order, the signed
+// orientation, the Dirichlet nodes, the vertex stars (cell interiors first, then
+// the interface entities in minimum-degree order), the signed
 // map from each cell's tensor-product FDM functions to the global FDM
 // functions, and the sparsity pattern of every star's separable surrogate
 // matrix in the FDM basis.  Host memory only: no CUDA call.
@@ -89,6 +90,45 @@ void symbolic_cholesky(const std::vector<std::vector<int>> &S, std::vector<std::
   }
 }
 
+// Minimum-degree order of the groups (entities) of a symmetric pattern S:
+// repeatedly eliminates the group whose neighbours hold the fewest functions
+// (ties: the lower group), joining its neighbours into a clique.  Returns the
+// positions of S in elimination order, each group's positions together.
+std::vector<int> entity_minimum_degree(const std::vector<std::vector<int>> &S, const std::vector<int> &group_of,
+                                       int ngroup) {
+  std::vector<std::vector<int>> members(ngroup);
+  for (int i = 0; i < (int)S.size(); ++i) members[group_of[i]].push_back(i);
+  std::vector<std::vector<char>> adj(ngroup, std::vector<char>(ngroup, 0));
+  for (int i = 0; i < (int)S.size(); ++i)
+    for (int j : S[i])
+      if (group_of[i] != group_of[j]) adj[group_of[i]][group_of[j]] = adj[group_of[j]][group_of[i]] = 1;
+  std::vector<char> alive(ngroup, 1);
+  std::vector<int> out;
+  for (int step = 0; step < ngroup; ++step) {
+    int best = -1;
+    int64_t best_deg = 0;
+    for (int g = 0; g < ngroup; ++g) {
+      if (!alive[g]) continue;
+      int64_t deg = 0;
+      for (int h = 0; h < ngroup; ++h)
+        if (alive[h] && adj[g][h]) deg += (int64_t)members[h].size();
+      if (best < 0 || deg < best_deg) {
+        best = g;
+        best_deg = deg;
+      }
+    }
+    alive[best] = 0;
+    std::vector<int> nb;
+    for (int h = 0; h < ngroup; ++h)
+      if (alive[h] && adj[best][h]) nb.push_back(h);
+    for (int a : nb)
+      for (int b : nb)
+        if (a != b) adj[a][b] = 1;
+    out.insert(out.end(), members[best].begin(), members[best].end());
+  }
+  return out;
+}
+
 std::string &hex_last_error() {
   static std::string e;
   return e;
@@ -110,6 +150,7 @@ struct Builder {
   std::map<std::array<int, 4>, int64_t> fbase;      // first node of each face
   std::map<std::array<int, 4>, int> fcount;         // cells per face
   std::vector<int64_t> cbase;
+  std::vector<int64_t> entity;                      // first slot of each node's entity
   int64_t nnode = 0;
 
   int corner(int e, int a, int b, int c) const { return cells[8 * e + a + 2 * b + 4 * c]; }
@@ -185,6 +226,16 @@ struct Builder {
       nnode += m * m * m;
     }
     if (nnode > INT32_MAX) fdm::fail(FDM_EINVAL, "fdm_hexmesh_create: more than 2^31 - 1 nodes");
+    // the first slot of each node's entity
+    entity.assign(nnode, -1);
+    for (int v = 0; v < nv; ++v)
+      if (vbase[v] >= 0) entity[vbase[v]] = vbase[v];
+    for (auto &kv : ebase)
+      for (int64_t k = 0; k < m; ++k) entity[kv.second + k] = kv.second;
+    for (auto &kv : fbase)
+      for (int64_t k = 0; k < m * m; ++k) entity[kv.second + k] = kv.second;
+    for (int e = 0; e < nc; ++e)
+      for (int64_t k = 0; k < m * m * m; ++k) entity[cbase[e] + k] = cbase[e];
   }
 
   // global node and FDM function of cell-local index (i, j, k) (node indices
@@ -262,7 +313,7 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
     h->n = n;
     h->nv = nv;
     h->nc = nc;
-    Builder B{p, n, nv, nc, cells, {}, {}, {}, {}, {}, {}, {}, {}, 0};
+    Builder B{p, n, nv, nc, cells, {}, {}, {}, {}, {}, {}, {}, {}, {}, 0};
     const fdm::Basis1D basis = fdm::make_basis(p);
     B.Af = basis.Af;
     B.Bf = basis.Bf;
@@ -355,9 +406,6 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
       }
       if (order.empty()) continue;
       for (size_t k = 0; k < order.size(); ++k) in_star[order[k]] = (int)k;
-      h->star_vertex.push_back(v);
-      for (int64_t g : order) h->star_nodes.push_back((int32_t)g);
-      h->star_ptr.push_back((int64_t)h->star_nodes.size());
       // the surrogate pattern: FDM functions c1, c2 of a star cell couple iff for
       // some axis a, Af couples them along a and Bf along the other two axes
       const int ns = (int)order.size();
@@ -384,11 +432,61 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
             if (nz) rows[x.second].push_back(y.second);
           }
       }
-      h->pat_rowptr.push_back(0);
-      int64_t cnt = 0;
       for (auto &r : rows) {
         std::sort(r.begin(), r.end());
         r.erase(std::unique(r.begin(), r.end()), r.end());
+      }
+      for (int r = 0; r < nint; ++r)
+        for (int c : rows[r])
+          if (c < nint && c != r) fdm::fail(FDM_EINVAL, "fdm_hexmesh_create: interior block of a star is not diagonal");
+      // the interface order: minimum degree over the star's entities in the
+      // pattern of the interface Schur complement S_G = A_GG - A_GI D^{-1} A_IG
+      auto schur_pattern = [&](const std::vector<std::vector<int>> &R) {
+        std::vector<std::vector<int>> Sg(ns - nint);
+        for (int r = nint; r < ns; ++r) {
+          std::vector<int> &o = Sg[r - nint];
+          for (int c : R[r]) {
+            if (c >= nint) o.push_back(c - nint);
+            else
+              for (int c2 : R[c])
+                if (c2 >= nint) o.push_back(c2 - nint);
+          }
+          std::sort(o.begin(), o.end());
+          o.erase(std::unique(o.begin(), o.end()), o.end());
+        }
+        return Sg;
+      };
+      {
+        const std::vector<std::vector<int>> S0 = schur_pattern(rows);
+        std::map<int64_t, int> gid_of;
+        std::vector<int> group_of(ns - nint);
+        for (int r = nint; r < ns; ++r) {
+          const int64_t ent = B.entity[order[r]];
+          auto it = gid_of.find(ent);
+          if (it == gid_of.end()) it = gid_of.emplace(ent, (int)gid_of.size()).first;
+          group_of[r - nint] = it->second;
+        }
+        // groups numbered in the default order (faces, edges, vertex by node number)
+        const std::vector<int> elim = entity_minimum_degree(S0, group_of, (int)gid_of.size());
+        std::vector<int> newpos(ns);
+        for (int r = 0; r < nint; ++r) newpos[r] = r;
+        for (int k = 0; k < (int)elim.size(); ++k) newpos[nint + elim[k]] = nint + k;
+        std::vector<int64_t> order2(ns);
+        std::vector<std::vector<int>> rows2(ns);
+        for (int r = 0; r < ns; ++r) {
+          order2[newpos[r]] = order[r];
+          for (int c : rows[r]) rows2[newpos[r]].push_back(newpos[c]);
+        }
+        for (auto &r : rows2) std::sort(r.begin(), r.end());
+        order.swap(order2);
+        rows.swap(rows2);
+      }
+      h->star_vertex.push_back(v);
+      for (int64_t g : order) h->star_nodes.push_back((int32_t)g);
+      h->star_ptr.push_back((int64_t)h->star_nodes.size());
+      h->pat_rowptr.push_back(0);
+      int64_t cnt = 0;
+      for (auto &r : rows) {
         for (int c : r) h->pat_cols.push_back(c);
         cnt += (int64_t)r.size();
         h->pat_rowptr.push_back(cnt);
@@ -416,22 +514,7 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
       h->class_star.push_back((int32_t)h->star_vertex.size() - 1);
       // pattern of S_G: A_GG plus, through every interior function, the
       // interface functions it couples to (the interior block is diagonal)
-      const int nG = ns - nint;
-      std::vector<std::vector<int>> Sg(nG);
-      for (int r = nint; r < ns; ++r) {
-        std::vector<int> &out = Sg[r - nint];
-        for (int c : rows[r]) {
-          if (c >= nint) out.push_back(c - nint);
-          else
-            for (int c2 : rows[c])
-              if (c2 >= nint) out.push_back(c2 - nint);
-        }
-        std::sort(out.begin(), out.end());
-        out.erase(std::unique(out.begin(), out.end()), out.end());
-      }
-      for (int r = 0; r < nint; ++r)
-        for (int c : rows[r])
-          if (c < nint && c != r) fdm::fail(FDM_EINVAL, "fdm_hexmesh_create: interior block of a star is not diagonal");
+      const std::vector<std::vector<int>> Sg = schur_pattern(rows);
       std::vector<std::vector<int>> Lrows;
       std::vector<int> parent;
       symbolic_cholesky(Sg, Lrows, parent);
