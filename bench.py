@@ -210,6 +210,35 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def oracle_single_core(n=6):
+    """The oracle's PCG solve of the same family on an n^3 mesh with one
+    OpenMP thread, in a fresh interpreter (the thread count is fixed when the
+    OpenMP runtime starts).  Returns {"value": DoF/s, ...} or None."""
+    code = ("import json, sys, time; sys.path.insert(0, %r)\n"
+            "import oracle\n"
+            "from paper_2107_14758_gb300 import inputs\n"
+            "xv, yv, zv = inputs.graded_vertices(%d, 2)\n"
+            "t0 = time.perf_counter()\n"
+            "P = oracle.Problem(7, xv, yv, zv); P.setup_patches(); P.setup_coarse()\n"
+            "P.lanczos_omega(inputs.lanczos_start(P.ndof))\n"
+            "t1 = time.perf_counter()\n"
+            "b = P.mass_apply(inputs.normal_rhs(P.ndof, 2))\n"
+            "t2 = time.perf_counter()\n"
+            "x, it, _, conv = P.pcg(b, rtol=%r, maxit=%d)\n"
+            "t3 = time.perf_counter()\n"
+            "print(json.dumps({'free': (%d * 7 - 1) ** 3, 'setup_s': t1 - t0, 'solve_s': t3 - t2, 'iterations': it}))\n"
+            % (ROOT, n, RTOL, MAXIT, n))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=300)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+    return {"value": d["free"] / d["solve_s"], "unit": "DoF/s", "cores": 1, "setup_s": d["setup_s"],
+            "iterations": d["iterations"],
+            "sample": "the same family on a %d^3 mesh (Q7, %d free dofs), one OpenMP thread" % (n, d["free"])}
+
+
 SAMPLE_TEXT = ("the same problem family (graded tensor mesh, Q7, N(0,1) nodal f, PCG + V(1,1), rtol 1e-8) "
                "on a %d^3 mesh instead of 16^3; DoF/s = free dofs / solve wall time, set-up excluded" % CPU_SAMPLE_N)
 
@@ -235,7 +264,7 @@ def bench_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT, "sample": SAMPLE_TEXT, "iterations": int(np.median(its))},
             "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": cpu_cores(), "kind": "oracle",
-                             "sample": SAMPLE_TEXT, "setup_s": setup_s},
+                             "sample": SAMPLE_TEXT, "setup_s": setup_s, "single_core": oracle_single_core()},
             "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -408,7 +437,8 @@ def bench_gpu(args):
         P, bc, setup_cpu = oracle_problem()
         t, it, conv = run_oracle_solve(P, bc)
         cpu = {"value": _free_dofs(P.N) / t, "unit": "DoF/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": SAMPLE_TEXT, "setup_s": setup_cpu, "iterations": it}
+               "sample": SAMPLE_TEXT, "setup_s": setup_cpu, "iterations": it,
+               "single_core": oracle_single_core()}
 
     if rank == 0:
         line = {"metric": "pcg_solve_dofs_per_s", "value": value, "unit": "DoF/s", "n_gpus": ws,
