@@ -413,6 +413,22 @@ int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_hexmesh **ou
 #define FDM_HQ_ETREE_PTR 23     /* int64[nclass + 1]: offsets into FDM_HQ_ETREE */
 #define FDM_HQ_ETREE 24         /* int32[...]: per class, the elimination-tree parent of each
                                  * interface column (-1 for a root) */
+#define FDM_HQ_MU 25            /* double[nc][3]: averaged surrogate coefficients (after fdm_hexmesh_factor) */
+#define FDM_HQ_DIAG_PTR 26      /* int64[nstar + 1]: offsets into FDM_HQ_DIAG */
+#define FDM_HQ_DIAG 27          /* double[...]: per star, the diagonal interior block D of its surrogate matrix */
+#define FDM_HQ_FACTOR_PTR 28    /* int64[nstar + 1]: offsets into FDM_HQ_FACTOR */
+#define FDM_HQ_FACTOR 29        /* double[...]: per star, L of S_G (S_G = L L^T) in its class's fill
+                                 * pattern, row by row (FDM_HQ_FILL_*) */
+/* Numeric set-up on the host, FP64 (Sections 2.6-2.7): X[nv][3] (HOST) the
+ * vertex coordinates, kappa_q NULL or the coefficient at the (p+1)^3 Gauss
+ * points of every cell (x fastest).  Per cell the averaged surrogate mu_d =
+ * (1/8) sum_q w_q G_dd, G = kappa |det J| J^{-1} J^{-T} of the trilinear map;
+ * per star its surrogate matrix in the FDM basis (sum over its cells of
+ * sum_d mu_d (A_f along axis d, B_f along the others), with the map's
+ * signs), the interior pivots D and the Cholesky factor of the interface
+ * Schur complement in the class's fill.  FDM_ENOTSPD for a pivot <= 0,
+ * FDM_EINVAL for degenerate geometry or nv other than at creation. */
+int fdm_hexmesh_factor(fdm_hexmesh *h, int nv, const double *X, const double *kappa_q);
 /* Copies `what` into out (HOST); *len is the capacity in bytes on input and
  * the size written on output (out NULL: the size only). */
 int fdm_hexmesh_query(fdm_hexmesh *h, int what, void *out, size_t *len);

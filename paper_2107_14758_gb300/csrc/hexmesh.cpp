@@ -54,6 +54,15 @@ struct fdm_hexmesh {
   std::vector<int32_t> fill_cols;    // per class: columns of each row of L (interface positions, sorted)
   std::vector<int64_t> etree_ptr;    // [nclass + 1] into etree
   std::vector<int32_t> etree;        // per class: parent of each interface column (-1: root)
+  // kept for the numeric set-up
+  std::vector<int> cells;            // [nc][8]
+  std::vector<double> Af, Bf, xq, wq;
+  // numeric set-up (fdm_hexmesh_factor)
+  std::vector<double> mu;            // [nc][3] averaged surrogate coefficients
+  std::vector<int64_t> diag_ptr;     // [nstar + 1] into diag
+  std::vector<double> diag;          // per star: the diagonal interior block D
+  std::vector<int64_t> factor_ptr;   // [nstar + 1] into factor
+  std::vector<double> factor;        // per star: L of S_G in its class's fill pattern (row by row)
   std::string err;
 };
 
@@ -332,6 +341,11 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
     }
     B.number();
     h->nnode = B.nnode;
+    h->cells.assign(cells, cells + 8 * (size_t)nc);
+    h->Af = basis.Af;
+    h->Bf = basis.Bf;
+    h->xq = basis.xq;
+    h->wq = basis.wq;
     h->cell_nodes.resize((size_t)nc * n3);
     h->cell_fdm.resize((size_t)nc * n3);
     h->cell_sign.resize((size_t)nc * n3);
@@ -549,6 +563,158 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
   return FDM_OK;
 }
 
+extern "C" int fdm_hexmesh_factor(fdm_hexmesh *h, int nv, const double *X, const double *kappa_q) {
+  if (!h || !X || nv != h->nv) {
+    if (h) h->err = "fdm_hexmesh_factor: need the mesh's nv vertex coordinates";
+    return FDM_EINVAL;
+  }
+  try {
+    const int p = h->p, n = h->n, n3 = n * n * n, nc = h->nc, q = n, q3 = q * q * q;
+    // ---- averaged surrogate per cell (Section 2.7): mu_d = (1/8) sum_q w_q G_dd,
+    // G = kappa |det J| J^{-1} J^{-T} of the trilinear map at the Gauss points
+    h->mu.assign((size_t)nc * 3, 0.0);
+    for (int e = 0; e < nc; ++e)
+      for (int qz = 0; qz < q; ++qz)
+        for (int qy = 0; qy < q; ++qy)
+          for (int qx = 0; qx < q; ++qx) {
+            const double t[3] = {h->xq[qx], h->xq[qy], h->xq[qz]};
+            double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+            for (int c = 0; c < 8; ++c) {
+              const int a[3] = {c & 1, (c >> 1) & 1, c >> 2};
+              double N[3], dN[3];
+              for (int d = 0; d < 3; ++d) {
+                N[d] = a[d] ? 0.5 * (1.0 + t[d]) : 0.5 * (1.0 - t[d]);
+                dN[d] = a[d] ? 0.5 : -0.5;
+              }
+              const double g[3] = {dN[0] * N[1] * N[2], N[0] * dN[1] * N[2], N[0] * N[1] * dN[2]};
+              const double *xv = X + 3 * (size_t)h->cells[8 * (size_t)e + c];
+              for (int i = 0; i < 3; ++i)
+                for (int d = 0; d < 3; ++d) J[i][d] += xv[i] * g[d];
+            }
+            const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                               J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+            if (!(std::fabs(det) > 0.0)) fdm::fail(FDM_EINVAL, "fdm_hexmesh_factor: degenerate cell geometry");
+            // rows of J^{-1} = columns of the cofactor matrix / det
+            double C[3][3];
+            for (int i = 0; i < 3; ++i)
+              for (int j = 0; j < 3; ++j) {
+                const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+                C[i][j] = J[i1][j1] * J[i2][j2] - J[i1][j2] * J[i2][j1];
+              }
+            const int qi = qx + q * (qy + q * qz);
+            const double kap = kappa_q ? kappa_q[(size_t)e * q3 + qi] : 1.0;
+            const double w = h->wq[qx] * h->wq[qy] * h->wq[qz];
+            for (int d = 0; d < 3; ++d) {
+              // (J^{-1})[d][i] = C[i][d] / det
+              double gdd = 0.0;
+              for (int i = 0; i < 3; ++i) gdd += C[i][d] * C[i][d];
+              h->mu[3 * (size_t)e + d] += w * kap * gdd / std::fabs(det) / 8.0;
+            }
+          }
+    // ---- per star: the surrogate matrix in the FDM basis on the star's pattern,
+    // its interior pivots D and the Cholesky factor of S_G in the class's fill
+    std::vector<std::vector<int>> vcells(h->nv);
+    for (int e = 0; e < nc; ++e)
+      for (int k = 0; k < 8; ++k) vcells[h->cells[8 * (size_t)e + k]].push_back(e);
+    const int nstar = (int)h->star_vertex.size();
+    h->diag_ptr.assign(1, 0);
+    h->factor_ptr.assign(1, 0);
+    h->diag.clear();
+    h->factor.clear();
+    for (int k = 0; k < nstar; ++k) {
+      const int64_t s0 = h->star_ptr[k], ns = h->star_ptr[k + 1] - s0;
+      const int nint = h->star_nint[k], nG = (int)ns - nint;
+      std::map<int32_t, int> pos;
+      for (int64_t i = 0; i < ns; ++i) pos[h->star_nodes[s0 + i]] = (int)i;
+      const int64_t *rp = h->pat_rowptr.data() + h->pat_ptr[k];
+      const int32_t *cols = h->pat_cols.data() + h->pat_colptr[k];
+      std::vector<double> A(rp[ns], 0.0);
+      for (int e : vcells[h->star_vertex[k]]) {
+        std::vector<std::array<int, 3>> loc;  // (local FDM index, star position, sign)
+        for (int c = 0; c < n3; ++c) {
+          auto it = pos.find(h->cell_fdm[(size_t)e * n3 + c]);
+          if (it != pos.end()) loc.push_back({c, it->second, h->cell_sign[(size_t)e * n3 + c]});
+        }
+        const double *me = &h->mu[3 * (size_t)e];
+        for (auto &x : loc)
+          for (auto &y : loc) {
+            const int a[3] = {x[0] % n, (x[0] / n) % n, x[0] / (n * n)};
+            const int b[3] = {y[0] % n, (y[0] / n) % n, y[0] / (n * n)};
+            double v = 0.0;
+            for (int d = 0; d < 3; ++d) {
+              double t = me[d] * h->Af[a[d] * n + b[d]];
+              for (int o = 0; o < 3; ++o)
+                if (o != d) t *= h->Bf[a[o] * n + b[o]];
+              v += t;
+            }
+            if (v == 0.0) continue;
+            const int32_t *r0 = cols + rp[x[1]], *r1 = cols + rp[x[1] + 1];
+            const int32_t *f = std::lower_bound(r0, r1, y[1]);
+            if (f == r1 || *f != y[1]) fdm::fail(FDM_EINVAL, "fdm_hexmesh_factor: entry outside the star pattern");
+            A[f - cols] += x[2] * y[2] * v;
+          }
+      }
+      auto entry = [&](int r, int c) {
+        const int32_t *r0 = cols + rp[r], *r1 = cols + rp[r + 1];
+        const int32_t *f = std::lower_bound(r0, r1, c);
+        return (f != r1 && *f == c) ? A[f - cols] : 0.0;
+      };
+      for (int i = 0; i < nint; ++i) {
+        const double d = entry(i, i);
+        if (!(d > 0.0)) fdm::fail(FDM_ENOTSPD, "fdm_hexmesh_factor: interior pivot <= 0");
+        h->diag.push_back(d);
+      }
+      h->diag_ptr.push_back((int64_t)h->diag.size());
+      // S_G = A_GG - A_GI D^{-1} A_IG (dense, lower triangle used)
+      std::vector<double> S((size_t)nG * nG, 0.0);
+      for (int r = nint; r < ns; ++r)
+        for (int64_t t = rp[r]; t < rp[r + 1]; ++t)
+          if (cols[t] >= nint) S[(size_t)(r - nint) * nG + (cols[t] - nint)] = A[t];
+      for (int i = 0; i < nint; ++i) {
+        std::vector<std::pair<int, double>> nb;
+        for (int64_t t = rp[i]; t < rp[i + 1]; ++t)
+          if (cols[t] >= nint) nb.push_back({cols[t] - nint, A[t]});
+        const double d = h->diag[h->diag_ptr[k] + i];
+        for (auto &a : nb)
+          for (auto &b : nb) S[(size_t)a.first * nG + b.first] -= a.second * b.second / d;
+      }
+      // Cholesky (right-looking), then the values in the class's fill pattern;
+      // an entry outside the fill would mean a wrong symbolic factorisation
+      double smax = 0.0;
+      for (double v : S) smax = std::max(smax, std::fabs(v));
+      for (int j = 0; j < nG; ++j) {
+        double &djj = S[(size_t)j * nG + j];
+        if (!(djj > 0.0)) fdm::fail(FDM_ENOTSPD, "fdm_hexmesh_factor: interface pivot <= 0");
+        djj = std::sqrt(djj);
+        for (int i = j + 1; i < nG; ++i) S[(size_t)i * nG + j] /= djj;
+        for (int c = j + 1; c < nG; ++c) {
+          const double lcj = S[(size_t)c * nG + j];
+          if (lcj == 0.0) continue;
+          for (int i = c; i < nG; ++i) S[(size_t)i * nG + c] -= S[(size_t)i * nG + j] * lcj;
+        }
+      }
+      const int cls = h->star_class[k];
+      const int64_t *frp = h->fill_rowptr.data() + h->fill_ptr[cls];
+      const int32_t *fcols = h->fill_cols.data() + h->fill_colptr[cls];
+      std::vector<char> in_fill((size_t)nG * nG, 0);
+      for (int r = 0; r < nG; ++r)
+        for (int64_t t = frp[r]; t < frp[r + 1]; ++t) {
+          in_fill[(size_t)r * nG + fcols[t]] = 1;
+          h->factor.push_back(S[(size_t)r * nG + fcols[t]]);
+        }
+      for (int r = 0; r < nG; ++r)
+        for (int c = 0; c < r; ++c)
+          if (!in_fill[(size_t)r * nG + c] && std::fabs(S[(size_t)r * nG + c]) > 1e-10 * std::sqrt(smax))
+            fdm::fail(FDM_EINVAL, "fdm_hexmesh_factor: factor entry outside the symbolic fill");
+      h->factor_ptr.push_back((int64_t)h->factor.size());
+    }
+  } catch (const fdm::Error &e) {
+    return handle_hex(h, e);
+  }
+  return FDM_OK;
+}
+
 extern "C" int fdm_hexmesh_query(fdm_hexmesh *h, int what, void *out, size_t *len) {
   if (!h || !len) return FDM_EINVAL;
   auto put = [&](const void *src, size_t bytes) {
@@ -591,6 +757,11 @@ extern "C" int fdm_hexmesh_query(fdm_hexmesh *h, int what, void *out, size_t *le
     case FDM_HQ_FILL_COLS: return put(h->fill_cols.data(), h->fill_cols.size() * sizeof(int32_t));
     case FDM_HQ_ETREE_PTR: return put(h->etree_ptr.data(), h->etree_ptr.size() * sizeof(int64_t));
     case FDM_HQ_ETREE: return put(h->etree.data(), h->etree.size() * sizeof(int32_t));
+    case FDM_HQ_MU: return put(h->mu.data(), h->mu.size() * sizeof(double));
+    case FDM_HQ_DIAG_PTR: return put(h->diag_ptr.data(), h->diag_ptr.size() * sizeof(int64_t));
+    case FDM_HQ_DIAG: return put(h->diag.data(), h->diag.size() * sizeof(double));
+    case FDM_HQ_FACTOR_PTR: return put(h->factor_ptr.data(), h->factor_ptr.size() * sizeof(int64_t));
+    case FDM_HQ_FACTOR: return put(h->factor.data(), h->factor.size() * sizeof(double));
     default:
       h->err = "fdm_hexmesh_query: unknown query";
       return FDM_EINVAL;

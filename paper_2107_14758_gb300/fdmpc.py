@@ -28,7 +28,8 @@ FDM_SURR_AVERAGED, FDM_SURR_EXTERNAL = 0, 1
  FDM_HQ_STAR_VERTEX, FDM_HQ_STAR_PTR, FDM_HQ_STAR_NODES, FDM_HQ_PATTERN_PTR, FDM_HQ_PATTERN_ROWPTR,
  FDM_HQ_PATTERN_COLPTR, FDM_HQ_PATTERN_COLS, FDM_HQ_STAR_NINT, FDM_HQ_STAR_CLASS, FDM_HQ_NCLASS,
  FDM_HQ_CLASS_STAR, FDM_HQ_CLASS_NNZL, FDM_HQ_FILL_PTR, FDM_HQ_FILL_ROWPTR, FDM_HQ_FILL_COLPTR, FDM_HQ_FILL_COLS,
- FDM_HQ_ETREE_PTR, FDM_HQ_ETREE) = range(1, 25)
+ FDM_HQ_ETREE_PTR, FDM_HQ_ETREE, FDM_HQ_MU, FDM_HQ_DIAG_PTR, FDM_HQ_DIAG, FDM_HQ_FACTOR_PTR,
+ FDM_HQ_FACTOR) = range(1, 30)
 FDM_MLP_NPARAM = 16515
 TIMERS = ("restrict", "patch", "interp", "op64", "op32", "coarse", "vec")
 
@@ -122,6 +123,7 @@ def load():
     L.fdm_sipg_destroy.restype = None
     L.fdm_hexmesh_create.argtypes = [C.c_int, C.c_int, ip, C.c_int, C.POINTER(vp)]
     L.fdm_hexmesh_query.argtypes = [vp, C.c_int, vp, C.POINTER(C.c_size_t)]
+    L.fdm_hexmesh_factor.argtypes = [vp, C.c_int, dp, dp]
     L.fdm_hexmesh_last_error.argtypes = [vp]
     L.fdm_hexmesh_last_error.restype = C.c_char_p
     L.fdm_hexmesh_destroy.argtypes = [vp]
@@ -821,3 +823,17 @@ class HexMesh:
         per = [(int(first[k]), int(nnzl[k]), (fr[fp[k]:fp[k + 1]], cols[fc[k]:fc[k + 1]]), et[ep[k]:ep[k + 1]])
                for k in range(len(first))]
         return cls, nint, per
+
+    def factor(self, X, kappa_q=None):
+        """Numeric set-up (fdm_hexmesh_factor); returns (mu[nc,3], per star
+        (D, L values in its class's fill pattern))."""
+        L = load()
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        kq = None if kappa_q is None else np.ascontiguousarray(kappa_q, dtype=np.float64)
+        rc = L.fdm_hexmesh_factor(self.h, X.shape[0], _dptr(X), None if kq is None else _dptr(kq))
+        if rc < 0:
+            raise FdmError(rc, L.fdm_hexmesh_last_error(self.h).decode())
+        mu = self.query(FDM_HQ_MU, np.float64).reshape(self.nc, 3)
+        dp_, d = self.query(FDM_HQ_DIAG_PTR, np.int64), self.query(FDM_HQ_DIAG, np.float64)
+        fp_, f = self.query(FDM_HQ_FACTOR_PTR, np.int64), self.query(FDM_HQ_FACTOR, np.float64)
+        return mu, [(d[dp_[k]:dp_[k + 1]], f[fp_[k]:fp_[k + 1]]) for k in range(len(dp_) - 1)]

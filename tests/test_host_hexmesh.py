@@ -17,7 +17,11 @@ cells' GLL nodes by position and glues its star FDM bases by matching traces:
   numerically formed Schur complement, the numeric Cholesky factor stays
   inside it, and a tensor mesh in lexicographic orientation has the 8 star
   classes of the structured path;
-* invalid meshes are rejected.
+* the numeric set-up (fdm_hexmesh_factor) gives the oracle's surrogate
+  coefficients (also with a coefficient at the Gauss points), interior pivots
+  and interface Schur complement (L L^T), and the star solve from D and L in
+  the FDM basis is the oracle's star solve;
+* invalid meshes and geometry are rejected.
 """
 import numpy as np
 import pytest
@@ -191,3 +195,78 @@ def test_tensor_mesh_has_the_eight_structured_classes(fdmpc):
         assert len(per) == 8
         sizes = sorted({(int(nint[f]), int(nnzl)) for f, nnzl, _, _ in per})
         assert sizes[-1][0] == 8 * (p - 1) ** 3  # the interior star's 8 cell interiors
+
+
+def _star_fdm_matrix(U, H, k, pi):
+    """The oracle's surrogate star matrix of star k in the basis of the
+    library's signed FDM map, and the star's GLL-basis nodes (oracle order)."""
+    p, n = U.p, U.n
+    cn = H.cell_nodes()
+    cf, cs = H.cell_fdm()
+    T3 = _kron3(U.T1, U.T1, U.T1)
+    v, nodes = H.stars()[k]
+    pos = {int(g): i for i, g in enumerate(nodes)}
+    ns = len(nodes)
+    Tv = np.zeros((ns, ns))
+    for e in U.vertex_cells[v]:
+        rows = np.array([pos.get(int(g), -1) for g in cn[e]])
+        inside = rows >= 0
+        for c in range(n ** 3):
+            col = pos.get(int(cf[e, c]))
+            if col is not None:
+                Tv[rows[inside], col] = cs[e, c] * T3[inside, c]
+    dofs = pi[nodes]
+    return Tv, Tv.T @ U.As[dofs][:, dofs].toarray() @ Tv, v, dofs
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_numeric_factorisation(fdmpc, p):
+    """fdm_hexmesh_factor: the surrogate coefficients equal the oracle's, the
+    interior pivots and L L^T equal the oracle's star matrix and its interface
+    Schur complement, and the star solve from D and L (in the FDM basis) is
+    the oracle's star solve; with a coefficient kappa at the Gauss points too."""
+    X, cells = inputs.unstructured_hex_mesh(2, 2, 5)
+    rng = np.random.default_rng(p)
+    for kappa in (None, np.exp(rng.uniform(-1, 1, size=(cells.shape[0], (p + 1) ** 3)))):
+        H = fdmpc.HexMesh(X.shape[0], cells, p)
+        U = HexProblem(p, X, cells, kappa=kappa)
+        mu, fac = H.factor(X, kappa)
+        assert np.allclose(mu, U.mu, rtol=1e-13, atol=0)
+        cn = H.cell_nodes()
+        pi = np.zeros(H.nnode, dtype=np.int64)
+        pi[cn.ravel()] = U.gid.ravel()
+        cls, nint, per = H.classes()
+        for k in range(0, len(cls), 7):
+            Tv, Af, v, dofs = _star_fdm_matrix(U, H, k, pi)
+            ni = int(nint[k])
+            D, Lv = fac[k]
+            assert np.allclose(D, np.diag(Af)[:ni], rtol=1e-13, atol=0)
+            nG = len(dofs) - ni
+            rp, fcols = per[cls[k]][2]
+            L = np.zeros((nG, nG))
+            for r in range(nG):
+                L[r, fcols[rp[r]:rp[r + 1]]] = Lv[rp[r]:rp[r + 1]]
+            S = Af[ni:, ni:] - Af[ni:, :ni] @ (Af[:ni, ni:] / D[:, None])
+            if nG:
+                assert np.abs(L @ L.T - S).max() <= 1e-12 * np.abs(S).max()
+            # the star solve: y = A_v^{-1} g in the FDM basis by block elimination
+            r = rng.standard_normal(U.ndof)
+            g = Tv.T @ r[dofs]
+            gI, gG = g[:ni], g[ni:]
+            xG = np.linalg.solve(L.T, np.linalg.solve(L, gG - Af[ni:, :ni] @ (gI / D))) if nG else gG
+            xI = (gI - Af[:ni, ni:] @ xG) / D
+            want = U.patch_solve(v, r)[1]
+            got = Tv @ np.concatenate([xI, xG])
+            order = np.argsort(dofs)
+            assert np.abs(got[order] - want).max() <= 1e-11 * np.abs(want).max()
+
+
+def test_factor_rejects_bad_geometry(fdmpc):
+    X, cells = inputs.tensor_hex_mesh(*inputs.uniform_vertices(2))
+    H = fdmpc.HexMesh(X.shape[0], cells, 2)
+    with pytest.raises(fdmpc.FdmError):
+        H.factor(X[:-1])
+    flat = X.copy()
+    flat[:, 2] = 0.0
+    with pytest.raises(fdmpc.FdmError, match="degenerate"):
+        H.factor(flat)
