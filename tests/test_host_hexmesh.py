@@ -270,3 +270,15 @@ def test_factor_rejects_bad_geometry(fdmpc):
     flat[:, 2] = 0.0
     with pytest.raises(fdmpc.FdmError, match="degenerate"):
         H.factor(flat)
+
+
+def test_factor_reports_not_spd(fdmpc):
+    """A negative coefficient makes the surrogate's pivots negative: the set-up
+    returns FDM_ENOTSPD (a status code, nothing aborts)."""
+    X, cells = inputs.unstructured_hex_mesh(2, 2, 5)
+    H = fdmpc.HexMesh(X.shape[0], cells, 2)
+    with pytest.raises(fdmpc.FdmError) as err:
+        H.factor(X, -np.ones((cells.shape[0], 27)))
+    assert err.value.code == fdmpc.FDM_ENOTSPD and "pivot" in str(err.value)
+    mu, fac = H.factor(X)  # the same object sets up again afterwards
+    assert np.all(mu > 0) and len(fac) == len(H.stars())
