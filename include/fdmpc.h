@@ -374,10 +374,13 @@ void fdm_sipg_destroy(fdm_sipg *s);
  * lexicographic); the FDM functions use the same slots (eigen-index m - 1 on
  * an edge or face axis), with a sign -1 where a cell sees an odd interior
  * function reversed.  Dirichlet nodes: the closure of the faces of one cell.
- * Stars: every used vertex with at least one free node; its free nodes
- * ordered cell interiors (by cell), then the interface (faces, edges, the
- * vertex) entity by entity in minimum-degree order of the interface Schur
- * complement's pattern (each entity's functions by node number); the pattern of
+ * Stars: every used vertex with at least one free node; its FDM functions
+ * in canonical order (the star's cells walked from the start cell and edge
+ * labelling with the smallest encoding of their shared faces and edges, so
+ * that equal configurations get equal orders in any cell orientation): cell
+ * interiors first, then the interface (faces, edges, the vertex) entity by
+ * entity in minimum-degree order of the interface Schur complement's
+ * pattern; the pattern of
  * its separable surrogate matrix in the FDM basis as CSR over star positions
  * (its interior block is diagonal, Section 2.6).  Stars with equal patterns
  * form a class, which shares the symbolic Cholesky factorisation (elimination

@@ -247,6 +247,169 @@ struct Builder {
       for (int64_t k = 0; k < m * m * m; ++k) entity[cbase[e] + k] = cbase[e];
   }
 
+  // The star of vertex v in canonical order: its FDM slots, cell interiors
+  // first (nint of them), then faces, edges and the vertex.  The cells around
+  // v are walked from every start cell and every assignment of labels 0, 1, 2
+  // to its three edges at v; a neighbour across the face normal to label a
+  // keeps the labels of the two shared edges and gives a to its third.  Each
+  // walk encodes, cell by cell, its three faces and three edges at v by
+  // first-seen entity number and Dirichlet flag; the smallest encoding fixes
+  // the cell order and the labels.  Stars with equal encodings are the same
+  // configuration, so their orders (and patterns) coincide.
+  std::vector<int64_t> canonical_star(int v, const std::vector<int> &vc, const std::vector<int32_t> &cell_fdm,
+                                      const std::vector<uint8_t> &dirichlet, int &nint) const {
+    const int nvc = (int)vc.size(), n3 = n * n * n;
+    struct AtV {
+      int e, cv;
+      int w[3];                     // the vertex at the other end of the edge along each cell axis
+      std::array<int, 4> face[3];   // the face normal to each cell axis that contains v
+    };
+    std::vector<AtV> C(nvc);
+    std::map<std::array<int, 4>, std::vector<int>> fcells;
+    for (int k = 0; k < nvc; ++k) {
+      AtV &a = C[k];
+      a.e = vc[k];
+      a.cv = 0;
+      while (cells[8 * a.e + a.cv] != v) ++a.cv;
+      for (int d = 0; d < 3; ++d) {
+        const int o = a.cv ^ (1 << d);
+        a.w[d] = cells[8 * a.e + o];
+        a.face[d] = face_key(face_corners(a.e, d, (a.cv >> d) & 1));
+        fcells[a.face[d]].push_back(k);
+      }
+    }
+    static const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    auto free_slot = [&](int e, const int idx[3]) {
+      const int64_t g = cell_fdm[(size_t)e * n3 + idx[0] + n * (idx[1] + n * idx[2])];
+      return !dirichlet[g];
+    };
+    // is the entity of cell k with the given end axes free?  (probe one of its functions)
+    auto entity_free = [&](int k, int ends_mask) {
+      if (p < 2 && ends_mask != 7) return false;
+      int idx[3];
+      for (int d = 0; d < 3; ++d) idx[d] = (ends_mask >> d & 1) ? ((C[k].cv >> d) & 1) * p : 1;
+      return free_slot(C[k].e, idx);
+    };
+    std::vector<int> best_enc, best_seq;
+    std::vector<std::array<int, 3>> best_frame;
+    for (int s0 = 0; s0 < nvc; ++s0)
+      for (const auto &pm : perms) {
+        std::vector<std::array<int, 3>> frame(nvc);
+        std::vector<char> seen(nvc, 0);
+        std::vector<int> seq;
+        frame[s0] = {pm[0], pm[1], pm[2]};
+        seen[s0] = 1;
+        seq.push_back(s0);
+        for (size_t h = 0; h < seq.size(); ++h) {
+          const int k = seq[h];
+          for (int a = 0; a < 3; ++a) {
+            for (int k2 : fcells[C[k].face[frame[k][a]]]) {
+              if (seen[k2]) continue;
+              std::array<int, 3> f2{-1, -1, -1};
+              bool used[3] = {false, false, false};
+              bool ok = true;
+              for (int b = 0; b < 3 && ok; ++b) {
+                if (b == a) continue;
+                const int wb = C[k].w[frame[k][b]];
+                int d2 = -1;
+                for (int d = 0; d < 3; ++d)
+                  if (C[k2].w[d] == wb) d2 = d;
+                if (d2 < 0 || used[d2]) ok = false;
+                else {
+                  f2[b] = d2;
+                  used[d2] = true;
+                }
+              }
+              if (!ok) continue;
+              for (int d = 0; d < 3; ++d)
+                if (!used[d]) f2[a] = d;
+              frame[k2] = f2;
+              seen[k2] = 1;
+              seq.push_back(k2);
+            }
+          }
+        }
+        for (int k = 0; k < nvc; ++k)  // cells not reached through faces (not expected)
+          if (!seen[k]) {
+            frame[k] = {0, 1, 2};
+            seq.push_back(k);
+          }
+        std::map<std::vector<int>, int> ids;
+        std::vector<int> enc;
+        for (int k : seq) {
+          for (int a = 0; a < 3; ++a) {
+            const std::array<int, 4> &fk = C[k].face[frame[k][a]];
+            auto it = ids.emplace(std::vector<int>{0, fk[0], fk[1], fk[2], fk[3]}, (int)ids.size()).first;
+            enc.push_back(2 * it->second + (entity_free(k, 1 << frame[k][a]) ? 1 : 0));
+          }
+          for (int a = 0; a < 3; ++a) {
+            const int w = C[k].w[frame[k][a]];
+            auto it = ids.emplace(std::vector<int>{1, std::min(v, w), std::max(v, w)}, (int)ids.size()).first;
+            enc.push_back(2 * it->second + (entity_free(k, 7 ^ (1 << frame[k][a])) ? 1 : 0));
+          }
+        }
+        if (best_seq.empty() || enc < best_enc) {
+          best_enc.swap(enc);
+          best_seq = seq;
+          best_frame = frame;
+        }
+      }
+    // the order: interiors cell by cell, then faces, edges (first seen in the
+    // canonical walk, functions in the first cell's labels), the vertex
+    std::vector<int64_t> out;
+    std::map<int64_t, char> done;
+    const int m = p - 1;
+    auto emit = [&](int k, const int idx[3]) {
+      const int64_t g = cell_fdm[(size_t)C[k].e * n3 + idx[0] + n * (idx[1] + n * idx[2])];
+      if (dirichlet[g] || done.count(g)) return;
+      done[g] = 1;
+      out.push_back(g);
+    };
+    for (int k : best_seq) {
+      const auto &f = best_frame[k];
+      for (int m3 = 1; m3 <= m; ++m3)
+        for (int m2 = 1; m2 <= m; ++m2)
+          for (int m1 = 1; m1 <= m; ++m1) {
+            int idx[3];
+            idx[f[0]] = m1;
+            idx[f[1]] = m2;
+            idx[f[2]] = m3;
+            emit(k, idx);
+          }
+    }
+    nint = (int)out.size();
+    for (int k : best_seq) {
+      const auto &f = best_frame[k];
+      for (int a = 0; a < 3; ++a) {
+        const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+        for (int mc = 1; mc <= m; ++mc)
+          for (int mb = 1; mb <= m; ++mb) {
+            int idx[3];
+            idx[f[a]] = ((C[k].cv >> f[a]) & 1) * p;
+            idx[f[b]] = mb;
+            idx[f[c]] = mc;
+            emit(k, idx);
+          }
+      }
+    }
+    for (int k : best_seq) {
+      const auto &f = best_frame[k];
+      for (int a = 0; a < 3; ++a)
+        for (int ma = 1; ma <= m; ++ma) {
+          int idx[3];
+          for (int d = 0; d < 3; ++d) idx[d] = ((C[k].cv >> d) & 1) * p;
+          idx[f[a]] = ma;
+          emit(k, idx);
+        }
+    }
+    {
+      int idx[3];
+      for (int d = 0; d < 3; ++d) idx[d] = ((C[best_seq[0]].cv >> d) & 1) * p;
+      emit(best_seq[0], idx);
+    }
+    return out;
+  }
+
   // global node and FDM function of cell-local index (i, j, k) (node indices
   // for the GLL map, eigen-indices on the interior axes for the FDM map)
   void map_local(int e, const int idx[3], int64_t &node, int64_t &fdm_fn, int &sign) const {
@@ -375,8 +538,8 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
                 if (idx[d] == (s ? p : 0)) h->dirichlet[h->cell_nodes[(size_t)e * n3 + i + n * (j + n * k)]] = 1;
               }
         }
-    // stars: per used vertex, the free nodes of the entities that contain it,
-    // ordered cell interiors (by cell), faces, edges, the vertex
+    // stars: per used vertex, the free FDM functions of the entities that
+    // contain it, in the star's canonical order (cell interiors first)
     std::vector<std::vector<int>> vcells(nv);
     for (int e = 0; e < nc; ++e)
       for (int k = 0; k < 8; ++k) vcells[cells[8 * e + k]].push_back(e);
@@ -386,38 +549,9 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
     h->pat_colptr.push_back(0);
     for (int v = 0; v < nv; ++v) {
       if (vcells[v].empty()) continue;
-      std::vector<int64_t> lists[4];  // by number of end axes: 0 interior, 1 face, 2 edge, 3 vertex
-      std::vector<char> seen;
+      int nint = 0;
+      std::vector<int64_t> order = B.canonical_star(v, vcells[v], h->cell_fdm, h->dirichlet, nint);
       std::map<int64_t, int> in_star;
-      for (int e : vcells[v]) {
-        int cv = 0;
-        while (cells[8 * e + cv] != v) ++cv;
-        const int cr[3] = {cv & 1, (cv >> 1) & 1, cv >> 2};
-        for (int k = 0; k < n; ++k)
-          for (int j = 0; j < n; ++j)
-            for (int i = 0; i < n; ++i) {
-              const int idx[3] = {i, j, k};
-              // the node's entity contains the vertex iff every end index is at the vertex's side
-              int ends = 0;
-              bool at_v = true;
-              for (int d = 0; d < 3; ++d)
-                if (idx[d] == 0 || idx[d] == p) {
-                  ++ends;
-                  if (idx[d] != cr[d] * p) at_v = false;
-                }
-              if (!at_v) continue;
-              const int64_t g = h->cell_nodes[(size_t)e * n3 + i + n * (j + n * k)];
-              if (h->dirichlet[g] || in_star.count(g)) continue;
-              in_star[g] = 0;
-              lists[ends].push_back(g);
-            }
-      }
-      const int nint = (int)lists[0].size();
-      std::vector<int64_t> order;
-      for (int t = 0; t < 4; ++t) {
-        if (t > 0) std::sort(lists[t].begin(), lists[t].end());
-        order.insert(order.end(), lists[t].begin(), lists[t].end());
-      }
       if (order.empty()) continue;
       for (size_t k = 0; k < order.size(); ++k) in_star[order[k]] = (int)k;
       // the surrogate pattern: FDM functions c1, c2 of a star cell couple iff for

@@ -14,9 +14,9 @@ cells' GLL nodes by position and glues its star FDM bases by matching traces:
   interior-interior coupling (Section 2.6);
 * every class's symbolic factorisation of the interface Schur complement
   (fill and elimination tree) equals the oracle's symbolic fill of the
-  numerically formed Schur complement, the numeric Cholesky factor stays
-  inside it, and a tensor mesh in lexicographic orientation has the 8 star
-  classes of the structured path;
+  numerically formed Schur complement, and the numeric Cholesky factor stays
+  inside it; stars are ordered canonically, so a tensor mesh has 4 classes in
+  any cell orientation;
 * the numeric set-up (fdm_hexmesh_factor) gives the oracle's surrogate
   coefficients (also with a coefficient at the Gauss points), interior pivots
   and interface Schur complement (L L^T), and the star solve from D and L in
@@ -185,16 +185,26 @@ def test_class_symbolic_factorisation(fdmpc, oracle_lib, name, p):
             assert parent[j] == (j + 1 + below[0] if len(below) else -1)
 
 
-def test_tensor_mesh_has_the_eight_structured_classes(fdmpc):
-    """On a tensor mesh listed in lexicographic orientation the stars fall into
-    the 8 classes of the structured path (interior, 3 face, 3 edge and corner
-    stars) for p >= 3."""
+def test_canonical_star_classes(fdmpc):
+    """Stars are ordered canonically (a walk over their cells from the
+    smallest encoding), so equal configurations share a class whatever the
+    cells' orientation: a tensor mesh has 4 classes (interior, face, edge and
+    corner stars; the three face and edge kinds are the same up to axis
+    labels) in lexicographic and in random orientation, with the same fill;
+    the unstructured mesh has far fewer classes than stars."""
     X, cells = inputs.tensor_hex_mesh(*inputs.graded_vertices(4, 4))
     for p in (3, 4):
-        cls, nint, per = fdmpc.HexMesh(X.shape[0], cells, p).classes()
-        assert len(per) == 8
-        sizes = sorted({(int(nint[f]), int(nnzl)) for f, nnzl, _, _ in per})
-        assert sizes[-1][0] == 8 * (p - 1) ** 3  # the interior star's 8 cell interiors
+        ref = None
+        for c in (cells, inputs.reorient_cells(cells, 3)):
+            cls, nint, per = fdmpc.HexMesh(X.shape[0], c, p).classes()
+            assert len(per) == 4
+            got = sorted((int(nint[f]), int(nnzl)) for f, nnzl, _, _ in per)
+            assert got[-1][0] == 8 * (p - 1) ** 3  # the interior star's 8 cell interiors
+            assert ref is None or got == ref
+            ref = got
+    Xu, cu = inputs.unstructured_hex_mesh(3, 3, 7)
+    cls, nint, per = fdmpc.HexMesh(Xu.shape[0], cu, 3).classes()
+    assert len(per) <= 20 and len(cls) > 250
 
 
 def _star_fdm_matrix(U, H, k, pi):
