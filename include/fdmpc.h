@@ -422,6 +422,14 @@ int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_hexmesh **ou
 #define FDM_HQ_FACTOR_PTR 28    /* int64[nstar + 1]: offsets into FDM_HQ_FACTOR */
 #define FDM_HQ_FACTOR 29        /* double[...]: per star, L of S_G (S_G = L L^T) in its class's fill
                                  * pattern, row by row (FDM_HQ_FILL_*) */
+#define FDM_HQ_SLOT_CELLS_PTR 30 /* int64[nnode + 1]: offsets into FDM_HQ_SLOT_CELLS */
+#define FDM_HQ_SLOT_CELLS 31    /* int32[nc (p+1)^3]: per FDM slot, e (p+1)^3 + c of every cell-local
+                                 * FDM function mapped to it (by cell): the assembly of the global FDM
+                                 * residual from the cells' ones */
+#define FDM_HQ_SLOT_STARS_PTR 32 /* int64[nnode + 1]: offsets (in pairs) into FDM_HQ_SLOT_STARS */
+#define FDM_HQ_SLOT_STARS 33    /* int32[2 ...]: per FDM slot, the (star, position) pairs holding it (by star):
+                                 * the sum of the star solutions */
+#define FDM_HQ_NODE_OWNER 34    /* int32[nnode]: e (p+1)^3 + l of the lowest cell holding each node */
 /* Numeric set-up on the host, FP64 (Sections 2.6-2.7): X[nv][3] (HOST) the
  * vertex coordinates, kappa_q NULL or the coefficient at the (p+1)^3 Gauss
  * points of every cell (x fastest).  Per cell the averaged surrogate mu_d =

@@ -54,6 +54,13 @@ struct fdm_hexmesh {
   std::vector<int32_t> fill_cols;    // per class: columns of each row of L (interface positions, sorted)
   std::vector<int64_t> etree_ptr;    // [nclass + 1] into etree
   std::vector<int32_t> etree;        // per class: parent of each interface column (-1: root)
+  // inverse maps for the apply: per FDM slot its (cell, local index) pairs and
+  // its (star, position) pairs, per node its owner (lowest cell, local index)
+  std::vector<int64_t> slot_cells_ptr;  // [nnode + 1]
+  std::vector<int32_t> slot_cells;      // e * (p+1)^3 + c, by cell
+  std::vector<int64_t> slot_stars_ptr;  // [nnode + 1]
+  std::vector<int32_t> slot_stars;      // (star, position) pairs, by star
+  std::vector<int32_t> node_owner;      // [nnode] e * (p+1)^3 + l
   // kept for the numeric set-up
   std::vector<int> cells;            // [nc][8]
   std::vector<double> Af, Bf, xq, wq;
@@ -684,6 +691,32 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
       h->etree_ptr.push_back((int64_t)h->etree.size());
       h->class_nnzl.push_back(nnzl);
     }
+    // inverse maps (counting sort by slot keeps the cell / star order)
+    {
+      const int64_t N = B.nnode;
+      h->slot_cells_ptr.assign(N + 1, 0);
+      for (size_t l = 0; l < h->cell_fdm.size(); ++l) ++h->slot_cells_ptr[h->cell_fdm[l] + 1];
+      for (int64_t g = 0; g < N; ++g) h->slot_cells_ptr[g + 1] += h->slot_cells_ptr[g];
+      h->slot_cells.resize(h->cell_fdm.size());
+      std::vector<int64_t> fillp(h->slot_cells_ptr.begin(), h->slot_cells_ptr.end() - 1);
+      for (size_t l = 0; l < h->cell_fdm.size(); ++l) h->slot_cells[fillp[h->cell_fdm[l]]++] = (int32_t)l;
+      const int nstar = (int)h->star_vertex.size();
+      h->slot_stars_ptr.assign(N + 1, 0);
+      for (int k = 0; k < nstar; ++k)
+        for (int64_t t = h->star_ptr[k]; t < h->star_ptr[k + 1]; ++t) ++h->slot_stars_ptr[h->star_nodes[t] + 1];
+      for (int64_t g = 0; g < N; ++g) h->slot_stars_ptr[g + 1] += h->slot_stars_ptr[g];
+      h->slot_stars.resize(2 * (size_t)h->slot_stars_ptr[N]);
+      std::vector<int64_t> sp(h->slot_stars_ptr.begin(), h->slot_stars_ptr.end() - 1);
+      for (int k = 0; k < nstar; ++k)
+        for (int64_t t = h->star_ptr[k]; t < h->star_ptr[k + 1]; ++t) {
+          const int64_t at = sp[h->star_nodes[t]]++;
+          h->slot_stars[2 * at] = k;
+          h->slot_stars[2 * at + 1] = (int32_t)(t - h->star_ptr[k]);
+        }
+      h->node_owner.assign(N, -1);
+      for (size_t l = 0; l < h->cell_nodes.size(); ++l)
+        if (h->node_owner[h->cell_nodes[l]] < 0) h->node_owner[h->cell_nodes[l]] = (int32_t)l;
+    }
   } catch (const fdm::Error &e) {
     int rc = handle_hex(h, e);
     delete h;
@@ -892,6 +925,11 @@ extern "C" int fdm_hexmesh_query(fdm_hexmesh *h, int what, void *out, size_t *le
     case FDM_HQ_ETREE_PTR: return put(h->etree_ptr.data(), h->etree_ptr.size() * sizeof(int64_t));
     case FDM_HQ_ETREE: return put(h->etree.data(), h->etree.size() * sizeof(int32_t));
     case FDM_HQ_MU: return put(h->mu.data(), h->mu.size() * sizeof(double));
+    case FDM_HQ_SLOT_CELLS_PTR: return put(h->slot_cells_ptr.data(), h->slot_cells_ptr.size() * sizeof(int64_t));
+    case FDM_HQ_SLOT_CELLS: return put(h->slot_cells.data(), h->slot_cells.size() * sizeof(int32_t));
+    case FDM_HQ_SLOT_STARS_PTR: return put(h->slot_stars_ptr.data(), h->slot_stars_ptr.size() * sizeof(int64_t));
+    case FDM_HQ_SLOT_STARS: return put(h->slot_stars.data(), h->slot_stars.size() * sizeof(int32_t));
+    case FDM_HQ_NODE_OWNER: return put(h->node_owner.data(), h->node_owner.size() * sizeof(int32_t));
     case FDM_HQ_DIAG_PTR: return put(h->diag_ptr.data(), h->diag_ptr.size() * sizeof(int64_t));
     case FDM_HQ_DIAG: return put(h->diag.data(), h->diag.size() * sizeof(double));
     case FDM_HQ_FACTOR_PTR: return put(h->factor_ptr.data(), h->factor_ptr.size() * sizeof(int64_t));

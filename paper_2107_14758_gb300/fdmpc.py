@@ -29,7 +29,8 @@ FDM_SURR_AVERAGED, FDM_SURR_EXTERNAL = 0, 1
  FDM_HQ_PATTERN_COLPTR, FDM_HQ_PATTERN_COLS, FDM_HQ_STAR_NINT, FDM_HQ_STAR_CLASS, FDM_HQ_NCLASS,
  FDM_HQ_CLASS_STAR, FDM_HQ_CLASS_NNZL, FDM_HQ_FILL_PTR, FDM_HQ_FILL_ROWPTR, FDM_HQ_FILL_COLPTR, FDM_HQ_FILL_COLS,
  FDM_HQ_ETREE_PTR, FDM_HQ_ETREE, FDM_HQ_MU, FDM_HQ_DIAG_PTR, FDM_HQ_DIAG, FDM_HQ_FACTOR_PTR,
- FDM_HQ_FACTOR) = range(1, 30)
+ FDM_HQ_FACTOR, FDM_HQ_SLOT_CELLS_PTR, FDM_HQ_SLOT_CELLS, FDM_HQ_SLOT_STARS_PTR, FDM_HQ_SLOT_STARS,
+ FDM_HQ_NODE_OWNER) = range(1, 35)
 FDM_MLP_NPARAM = 16515
 TIMERS = ("restrict", "patch", "interp", "op64", "op32", "coarse", "vec")
 
@@ -837,3 +838,9 @@ class HexMesh:
         dp_, d = self.query(FDM_HQ_DIAG_PTR, np.int64), self.query(FDM_HQ_DIAG, np.float64)
         fp_, f = self.query(FDM_HQ_FACTOR_PTR, np.int64), self.query(FDM_HQ_FACTOR, np.float64)
         return mu, [(d[dp_[k]:dp_[k + 1]], f[fp_[k]:fp_[k + 1]]) for k in range(len(dp_) - 1)]
+
+    def inverse_maps(self):
+        """(slot_cells_ptr, slot_cells, slot_stars_ptr, slot_stars[:, 2], node_owner)."""
+        return (self.query(FDM_HQ_SLOT_CELLS_PTR, np.int64), self.query(FDM_HQ_SLOT_CELLS, np.int32),
+                self.query(FDM_HQ_SLOT_STARS_PTR, np.int64), self.query(FDM_HQ_SLOT_STARS, np.int32).reshape(-1, 2),
+                self.query(FDM_HQ_NODE_OWNER, np.int32))

@@ -17,6 +17,10 @@ cells' GLL nodes by position and glues its star FDM bases by matching traces:
   numerically formed Schur complement, and the numeric Cholesky factor stays
   inside it; stars are ordered canonically, so a tensor mesh has 4 classes in
   any cell orientation;
+* one additive Schwarz sweep assembled from the library's tables and factors
+  alone, in the steps of a GPU apply (cell-local FDM residuals, assembly per
+  FDM slot, star block eliminations, sum per slot, basis change back per
+  cell), equals the oracle's sweep;
 * the numeric set-up (fdm_hexmesh_factor) gives the oracle's surrogate
   coefficients (also with a coefficient at the Gauss points), interior pivots
   and interface Schur complement (L L^T), and the star solve from D and L in
@@ -292,3 +296,96 @@ def test_factor_reports_not_spd(fdmpc):
     assert err.value.code == fdmpc.FDM_ENOTSPD and "pivot" in str(err.value)
     mu, fac = H.factor(X)  # the same object sets up again afterwards
     assert np.all(mu > 0) and len(fac) == len(H.stars())
+
+
+def _emulated_asm(H, X, r, basis):
+    """One additive Schwarz sweep (undamped) computed from the library's
+    tables and factors only, in the steps a GPU apply takes: cell-local FDM
+    residuals E_e = (T^T)^{x3} (W r)_e (W = 1/multiplicity), their assembly per
+    FDM slot through FDM_HQ_SLOT_CELLS with the map's signs, per star the
+    block elimination with D, A_GI (from mu and the 1D A_f, B_f) and L, the
+    sum of the star solutions per slot through FDM_HQ_SLOT_STARS, and the basis
+    change back T^{x3} per cell with the node taken from its owner cell.
+    Returns (z in library node order, largest mismatch of a node's value
+    between the cells that hold it)."""
+    p, n = H.p, H.n
+    n3 = n ** 3
+    T3 = _kron3(basis["T"], basis["T"], basis["T"])
+    Af, Bf = basis["Af"], basis["Bf"]
+    cn = H.cell_nodes()
+    cf, cs = H.cell_fdm()
+    scp, sc, ssp, ss, owner = H.inverse_maps()
+    mu, fac = H.factor(X)
+    cls, nint, per = H.classes()
+    dirichlet = H.dirichlet()
+    mult = np.bincount(cn.ravel(), minlength=H.nnode)
+    rW = np.where(dirichlet, 0.0, r) / mult
+    E = rW[cn] @ T3                                   # [cell, c]
+    rf = np.zeros(H.nnode)
+    for g in range(H.nnode):
+        for t in range(scp[g], scp[g + 1]):
+            e, c = divmod(int(sc[t]), n3)
+            rf[g] += cs[e, c] * E[e, c]
+
+    def coupling(e, c1, c2):
+        a = (c1 % n, (c1 // n) % n, c1 // (n * n))
+        b = (c2 % n, (c2 // n) % n, c2 // (n * n))
+        val = 0.0
+        for d in range(3):
+            t = mu[e, d] * Af[a[d], b[d]]
+            for o in range(3):
+                if o != d:
+                    t *= Bf[a[o], b[o]]
+            val += t
+        return cs[e, c1] * cs[e, c2] * val
+
+    xs = []
+    for k, (v, nodes) in enumerate(H.stars()):
+        ni = int(nint[k])
+        nG = len(nodes) - ni
+        pos = {int(g): i for i, g in enumerate(nodes)}
+        D, Lv = fac[k]
+        AGI = np.zeros((nG, ni))
+        for i in range(ni):
+            e, ci = divmod(int(sc[scp[nodes[i]]]), n3)  # an interior slot has one cell
+            for c in range(n3):
+                j = pos.get(int(cf[e, c]), -1)
+                if j >= ni:
+                    AGI[j - ni, i] = coupling(e, c, ci)
+        rp, fcols = per[cls[k]][2]
+        L = np.zeros((nG, nG))
+        for rr in range(nG):
+            L[rr, fcols[rp[rr]:rp[rr + 1]]] = Lv[rp[rr]:rp[rr + 1]]
+        g = rf[nodes]
+        gI, gG = g[:ni], g[ni:]
+        xG = np.linalg.solve(L.T, np.linalg.solve(L, gG - AGI @ (gI / D))) if nG else gG
+        xI = (gI - AGI.T @ xG) / D
+        xs.append(np.concatenate([xI, xG]))
+    zf = np.zeros(H.nnode)
+    for g in range(H.nnode):
+        for t in range(ssp[g], ssp[g + 1]):
+            zf[g] += xs[ss[t, 0]][ss[t, 1]]
+    Z = (cs * zf[cf]) @ T3.T                          # [cell, local node]
+    z = Z.ravel()[owner]
+    z[dirichlet] = 0.0
+    return z, np.abs(Z - z[cn]).max()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_emulated_gpu_sweep_is_the_oracle_asm(fdmpc, p):
+    """The relaxation assembled from the library's tables and factors (the
+    blueprint of the GPU apply for general meshes) equals the oracle's
+    additive Schwarz sweep, and the glued FDM functions give every node one
+    value from all its cells."""
+    import oracle
+    X, cells = inputs.unstructured_hex_mesh(2, 2, 5)
+    H = fdmpc.HexMesh(X.shape[0], cells, p)
+    U = HexProblem(p, X, cells)
+    cn = H.cell_nodes()
+    pi = np.zeros(H.nnode, dtype=np.int64)
+    pi[cn.ravel()] = U.gid.ravel()
+    r = np.random.default_rng(p).standard_normal(U.ndof)
+    z, mismatch = _emulated_asm(H, X, r[pi], oracle.basis1d(p))
+    want = U.asm(r)[pi]
+    assert np.abs(z - want).max() <= 1e-11 * np.abs(want).max()
+    assert mismatch <= 1e-11 * np.abs(want).max()
