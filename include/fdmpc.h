@@ -430,10 +430,22 @@ int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_hexmesh **ou
 #define FDM_HQ_SLOT_STARS 33    /* int32[2 ...]: per FDM slot, the (star, position) pairs holding it (by star):
                                  * the sum of the star solutions */
 #define FDM_HQ_NODE_OWNER 34    /* int32[nnode]: e (p+1)^3 + l of the lowest cell holding each node */
+#define FDM_HQ_NODE_CELLS_PTR 35 /* int64[nnode + 1]: offsets into FDM_HQ_NODE_CELLS */
+#define FDM_HQ_NODE_CELLS 36    /* int32[nc (p+1)^3]: per node, e (p+1)^3 + l of every cell-local copy (by cell):
+                                 * the deterministic sum of the cells' operator results */
+#define FDM_HQ_GEOM 37          /* double[nc][(p+1)^3][6] (after fdm_hexmesh_factor): w_q kappa |det J| J^{-1} J^{-T}
+                                 * at the Gauss points (x fastest), entries xx, yy, zz, xy, xz, yz: the
+                                 * stiffness a(v, u) = sum_K sum_q grad_xi v^T G grad_xi u */
+#define FDM_HQ_COARSE_OF 38     /* int32[nv]: coarse unknown of each vertex, -1 on boundary faces or unused */
+#define FDM_HQ_COARSE 39        /* double[nco][nco] (after fdm_hexmesh_factor): the Q1 Galerkin operator
+                                 * P^T A P, P the Q1 functions of the coarse vertices in Q_p */
 /* Numeric set-up on the host, FP64 (Sections 2.6-2.7): X[nv][3] (HOST) the
  * vertex coordinates, kappa_q NULL or the coefficient at the (p+1)^3 Gauss
  * points of every cell (x fastest).  Per cell the averaged surrogate mu_d =
  * (1/8) sum_q w_q G_dd, G = kappa |det J| J^{-1} J^{-T} of the trilinear map;
+ * the geometry factors of the stiffness at the Gauss points (FDM_HQ_GEOM);
+ * the Q1 coarse operator (FDM_HQ_COARSE, the Q1 stiffness of the same
+ * quadrature, which is P^T A P since the trilinear functions lie in Q_p);
  * per star its surrogate matrix in the FDM basis (sum over its cells of
  * sum_d mu_d (A_f along axis d, B_f along the others), with the map's
  * signs), the interior pivots D and the Cholesky factor of the interface

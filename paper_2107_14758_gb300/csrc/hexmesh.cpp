@@ -61,11 +61,16 @@ struct fdm_hexmesh {
   std::vector<int64_t> slot_stars_ptr;  // [nnode + 1]
   std::vector<int32_t> slot_stars;      // (star, position) pairs, by star
   std::vector<int32_t> node_owner;      // [nnode] e * (p+1)^3 + l
+  std::vector<int64_t> node_cells_ptr;  // [nnode + 1]
+  std::vector<int32_t> node_cells;      // e * (p+1)^3 + l of every cell-local node of each node, by cell
   // kept for the numeric set-up
   std::vector<int> cells;            // [nc][8]
   std::vector<double> Af, Bf, xq, wq;
   // numeric set-up (fdm_hexmesh_factor)
   std::vector<double> mu;            // [nc][3] averaged surrogate coefficients
+  std::vector<double> geom;          // [nc][q^3][6] w_q kappa |det J| J^{-1} J^{-T}: xx, yy, zz, xy, xz, yz
+  std::vector<int32_t> coarse_of;    // [nv] coarse unknown of each vertex (-1: none)
+  std::vector<double> coarse;        // [nco][nco] Q1 Galerkin operator P^T A P
   std::vector<int64_t> diag_ptr;     // [nstar + 1] into diag
   std::vector<double> diag;          // per star: the diagonal interior block D
   std::vector<int64_t> factor_ptr;   // [nstar + 1] into factor
@@ -716,6 +721,12 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
       h->node_owner.assign(N, -1);
       for (size_t l = 0; l < h->cell_nodes.size(); ++l)
         if (h->node_owner[h->cell_nodes[l]] < 0) h->node_owner[h->cell_nodes[l]] = (int32_t)l;
+      h->node_cells_ptr.assign(N + 1, 0);
+      for (size_t l = 0; l < h->cell_nodes.size(); ++l) ++h->node_cells_ptr[h->cell_nodes[l] + 1];
+      for (int64_t g = 0; g < N; ++g) h->node_cells_ptr[g + 1] += h->node_cells_ptr[g];
+      h->node_cells.resize(h->cell_nodes.size());
+      std::vector<int64_t> np_(h->node_cells_ptr.begin(), h->node_cells_ptr.end() - 1);
+      for (size_t l = 0; l < h->cell_nodes.size(); ++l) h->node_cells[np_[h->cell_nodes[l]]++] = (int32_t)l;
     }
   } catch (const fdm::Error &e) {
     int rc = handle_hex(h, e);
@@ -740,6 +751,32 @@ extern "C" int fdm_hexmesh_factor(fdm_hexmesh *h, int nv, const double *X, const
     // ---- averaged surrogate per cell (Section 2.7): mu_d = (1/8) sum_q w_q G_dd,
     // G = kappa |det J| J^{-1} J^{-T} of the trilinear map at the Gauss points
     h->mu.assign((size_t)nc * 3, 0.0);
+    h->geom.assign((size_t)nc * q3 * 6, 0.0);
+    // coarse space: the Q1 functions of the vertices not on a boundary face
+    h->coarse_of.assign(h->nv, -1);
+    {
+      std::vector<char> bnd(h->nv, 0), used(h->nv, 0);
+      std::map<std::array<int, 4>, int> fc;
+      for (int e = 0; e < nc; ++e)
+        for (int d = 0; d < 3; ++d)
+          for (int sd = 0; sd < 2; ++sd) {
+            std::array<int, 4> f{};
+            int t = 0;
+            for (int c = 0; c < 8; ++c)
+              if (((c >> d) & 1) == sd) f[t++] = h->cells[8 * (size_t)e + c];
+            std::sort(f.begin(), f.end());
+            ++fc[f];
+          }
+      for (auto &kv : fc)
+        if (kv.second == 1)
+          for (int v : kv.first) bnd[v] = 1;
+      for (int c : h->cells) used[c] = 1;
+      int nco = 0;
+      for (int v = 0; v < h->nv; ++v)
+        if (used[v] && !bnd[v]) h->coarse_of[v] = nco++;
+      h->coarse.assign((size_t)nco * nco, 0.0);
+    }
+    const int nco = (int)std::lround(std::sqrt((double)h->coarse.size()));
     for (int e = 0; e < nc; ++e)
       for (int qz = 0; qz < q; ++qz)
         for (int qy = 0; qy < q; ++qy)
@@ -772,11 +809,47 @@ extern "C" int fdm_hexmesh_factor(fdm_hexmesh *h, int nv, const double *X, const
             const int qi = qx + q * (qy + q * qz);
             const double kap = kappa_q ? kappa_q[(size_t)e * q3 + qi] : 1.0;
             const double w = h->wq[qx] * h->wq[qy] * h->wq[qz];
-            for (int d = 0; d < 3; ++d) {
-              // (J^{-1})[d][i] = C[i][d] / det
-              double gdd = 0.0;
-              for (int i = 0; i < 3; ++i) gdd += C[i][d] * C[i][d];
-              h->mu[3 * (size_t)e + d] += w * kap * gdd / std::fabs(det) / 8.0;
+            // G[d][f] = kappa |det J| sum_i (J^{-1})[d][i] (J^{-1})[f][i], (J^{-1})[d][i] = C[i][d] / det
+            double G[3][3];
+            for (int d = 0; d < 3; ++d)
+              for (int f = 0; f < 3; ++f) {
+                double s = 0.0;
+                for (int i = 0; i < 3; ++i) s += C[i][d] * C[i][f];
+                G[d][f] = kap * s / std::fabs(det);
+              }
+            for (int d = 0; d < 3; ++d) h->mu[3 * (size_t)e + d] += w * G[d][d] / 8.0;
+            double *gq = &h->geom[((size_t)e * q3 + qi) * 6];
+            gq[0] = w * G[0][0];
+            gq[1] = w * G[1][1];
+            gq[2] = w * G[2][2];
+            gq[3] = w * G[0][1];
+            gq[4] = w * G[0][2];
+            gq[5] = w * G[1][2];
+            // the Q1 Galerkin operator: P^T A P cell by cell is the Q1 stiffness
+            // of the same quadrature (the trilinear functions lie in Q_p)
+            double gN[8][3];
+            for (int c = 0; c < 8; ++c) {
+              const int a[3] = {c & 1, (c >> 1) & 1, c >> 2};
+              double N[3], dN[3];
+              for (int d = 0; d < 3; ++d) {
+                N[d] = a[d] ? 0.5 * (1.0 + t[d]) : 0.5 * (1.0 - t[d]);
+                dN[d] = a[d] ? 0.5 : -0.5;
+              }
+              gN[c][0] = dN[0] * N[1] * N[2];
+              gN[c][1] = N[0] * dN[1] * N[2];
+              gN[c][2] = N[0] * N[1] * dN[2];
+            }
+            for (int c1 = 0; c1 < 8; ++c1) {
+              const int i1 = h->coarse_of[h->cells[8 * (size_t)e + c1]];
+              if (i1 < 0) continue;
+              for (int c2 = 0; c2 < 8; ++c2) {
+                const int i2 = h->coarse_of[h->cells[8 * (size_t)e + c2]];
+                if (i2 < 0) continue;
+                double s = 0.0;
+                for (int d = 0; d < 3; ++d)
+                  for (int f = 0; f < 3; ++f) s += gN[c1][d] * G[d][f] * gN[c2][f];
+                h->coarse[(size_t)i1 * nco + i2] += w * s;
+              }
             }
           }
     // ---- per star: the surrogate matrix in the FDM basis on the star's pattern,
@@ -930,6 +1003,11 @@ extern "C" int fdm_hexmesh_query(fdm_hexmesh *h, int what, void *out, size_t *le
     case FDM_HQ_SLOT_STARS_PTR: return put(h->slot_stars_ptr.data(), h->slot_stars_ptr.size() * sizeof(int64_t));
     case FDM_HQ_SLOT_STARS: return put(h->slot_stars.data(), h->slot_stars.size() * sizeof(int32_t));
     case FDM_HQ_NODE_OWNER: return put(h->node_owner.data(), h->node_owner.size() * sizeof(int32_t));
+    case FDM_HQ_NODE_CELLS_PTR: return put(h->node_cells_ptr.data(), h->node_cells_ptr.size() * sizeof(int64_t));
+    case FDM_HQ_NODE_CELLS: return put(h->node_cells.data(), h->node_cells.size() * sizeof(int32_t));
+    case FDM_HQ_GEOM: return put(h->geom.data(), h->geom.size() * sizeof(double));
+    case FDM_HQ_COARSE_OF: return put(h->coarse_of.data(), h->coarse_of.size() * sizeof(int32_t));
+    case FDM_HQ_COARSE: return put(h->coarse.data(), h->coarse.size() * sizeof(double));
     case FDM_HQ_DIAG_PTR: return put(h->diag_ptr.data(), h->diag_ptr.size() * sizeof(int64_t));
     case FDM_HQ_DIAG: return put(h->diag.data(), h->diag.size() * sizeof(double));
     case FDM_HQ_FACTOR_PTR: return put(h->factor_ptr.data(), h->factor_ptr.size() * sizeof(int64_t));

@@ -30,7 +30,8 @@ FDM_SURR_AVERAGED, FDM_SURR_EXTERNAL = 0, 1
  FDM_HQ_CLASS_STAR, FDM_HQ_CLASS_NNZL, FDM_HQ_FILL_PTR, FDM_HQ_FILL_ROWPTR, FDM_HQ_FILL_COLPTR, FDM_HQ_FILL_COLS,
  FDM_HQ_ETREE_PTR, FDM_HQ_ETREE, FDM_HQ_MU, FDM_HQ_DIAG_PTR, FDM_HQ_DIAG, FDM_HQ_FACTOR_PTR,
  FDM_HQ_FACTOR, FDM_HQ_SLOT_CELLS_PTR, FDM_HQ_SLOT_CELLS, FDM_HQ_SLOT_STARS_PTR, FDM_HQ_SLOT_STARS,
- FDM_HQ_NODE_OWNER) = range(1, 35)
+ FDM_HQ_NODE_OWNER, FDM_HQ_NODE_CELLS_PTR, FDM_HQ_NODE_CELLS, FDM_HQ_GEOM, FDM_HQ_COARSE_OF,
+ FDM_HQ_COARSE) = range(1, 40)
 FDM_MLP_NPARAM = 16515
 TIMERS = ("restrict", "patch", "interp", "op64", "op32", "coarse", "vec")
 
@@ -844,3 +845,14 @@ class HexMesh:
         return (self.query(FDM_HQ_SLOT_CELLS_PTR, np.int64), self.query(FDM_HQ_SLOT_CELLS, np.int32),
                 self.query(FDM_HQ_SLOT_STARS_PTR, np.int64), self.query(FDM_HQ_SLOT_STARS, np.int32).reshape(-1, 2),
                 self.query(FDM_HQ_NODE_OWNER, np.int32))
+
+    def operator_tables(self):
+        """(node_cells_ptr, node_cells, geom[nc, q^3, 6], coarse_of[nv], coarse[nco, nco]);
+        geom and coarse after factor()."""
+        ptr = self.query(FDM_HQ_NODE_CELLS_PTR, np.int64)
+        nodec = self.query(FDM_HQ_NODE_CELLS, np.int32)
+        geom = self.query(FDM_HQ_GEOM, np.float64).reshape(self.nc, self.n ** 3, 6)
+        cof = self.query(FDM_HQ_COARSE_OF, np.int32)
+        co = self.query(FDM_HQ_COARSE, np.float64)
+        m = int(round(np.sqrt(co.size)))
+        return ptr, nodec, geom, cof, co.reshape(m, m)

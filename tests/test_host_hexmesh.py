@@ -20,7 +20,9 @@ cells' GLL nodes by position and glues its star FDM bases by matching traces:
 * one additive Schwarz sweep assembled from the library's tables and factors
   alone, in the steps of a GPU apply (cell-local FDM residuals, assembly per
   FDM slot, star block eliminations, sum per slot, basis change back per
-  cell), equals the oracle's sweep;
+  cell), equals the oracle's sweep; so do the stiffness apply from the
+  library's geometry factors and node-to-cell map, the library's Q1 coarse
+  operator and the hybrid V(1,1) built from them (with a coefficient kappa);
 * the numeric set-up (fdm_hexmesh_factor) gives the oracle's surrogate
   coefficients (also with a coefficient at the Gauss points), interior pivots
   and interface Schur complement (L L^T), and the star solve from D and L in
@@ -298,7 +300,7 @@ def test_factor_reports_not_spd(fdmpc):
     assert np.all(mu > 0) and len(fac) == len(H.stars())
 
 
-def _emulated_asm(H, X, r, basis):
+def _emulated_asm(H, r, basis, mu, fac):
     """One additive Schwarz sweep (undamped) computed from the library's
     tables and factors only, in the steps a GPU apply takes: cell-local FDM
     residuals E_e = (T^T)^{x3} (W r)_e (W = 1/multiplicity), their assembly per
@@ -315,7 +317,6 @@ def _emulated_asm(H, X, r, basis):
     cn = H.cell_nodes()
     cf, cs = H.cell_fdm()
     scp, sc, ssp, ss, owner = H.inverse_maps()
-    mu, fac = H.factor(X)
     cls, nint, per = H.classes()
     dirichlet = H.dirichlet()
     mult = np.bincount(cn.ravel(), minlength=H.nnode)
@@ -385,7 +386,82 @@ def test_emulated_gpu_sweep_is_the_oracle_asm(fdmpc, p):
     pi = np.zeros(H.nnode, dtype=np.int64)
     pi[cn.ravel()] = U.gid.ravel()
     r = np.random.default_rng(p).standard_normal(U.ndof)
-    z, mismatch = _emulated_asm(H, X, r[pi], oracle.basis1d(p))
+    mu, fac = H.factor(X)
+    z, mismatch = _emulated_asm(H, r[pi], oracle.basis1d(p), mu, fac)
     want = U.asm(r)[pi]
     assert np.abs(z - want).max() <= 1e-11 * np.abs(want).max()
     assert mismatch <= 1e-11 * np.abs(want).max()
+
+
+def _emulated_operator(H, u, geom, ptr, nodec, p):
+    """y = A u from the library's geometry factors and node-to-cell map: per
+    cell sum_{d,f} D_d^T (G_df o D_f u_e) (D_d: the GLL Lagrange basis
+    differentiated along axis d at the Gauss points), summed per node in the
+    map's order; 0 on Dirichlet nodes."""
+    import oracle
+    n = p + 1
+    xi = oracle.basis1d(p)["xi"]
+    xq, _ = oracle.gauss(n)
+    V, Dq = oracle.lagrange(p, xi, xq)
+    Dm = [_kron3(V, V, Dq), _kron3(V, Dq, V), _kron3(Dq, V, V)]
+    cn = H.cell_nodes()
+    dirichlet = H.dirichlet()
+    ue = np.where(dirichlet, 0.0, u)[cn]                       # [cell, node]
+    grads = [ue @ D.T for D in Dm]                           # [cell, q]
+    comp = {(0, 0): 0, (1, 1): 1, (2, 2): 2, (0, 1): 3, (1, 0): 3, (0, 2): 4, (2, 0): 4, (1, 2): 5, (2, 1): 5}
+    ye = np.zeros_like(ue)
+    for d in range(3):
+        flux = sum(geom[:, :, comp[d, f]] * grads[f] for f in range(3))
+        ye += flux @ Dm[d]
+    flat = ye.ravel()
+    y = np.array([flat[nodec[ptr[g]:ptr[g + 1]]].sum() for g in range(H.nnode)])
+    y[dirichlet] = 0.0
+    return y
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_emulated_operator_and_vcycle(fdmpc, p):
+    """The stiffness apply from the library's geometry factors and the hybrid
+    V(1,1) from the library's tables, factors and Q1 operator (the steps of
+    the GPU apply) equal the oracle's, on the unstructured mesh with a
+    coefficient at the Gauss points."""
+    import oracle
+    X, cells = inputs.unstructured_hex_mesh(2, 2, 5)
+    kappa = np.exp(np.random.default_rng(p).uniform(-0.5, 0.5, size=(cells.shape[0], (p + 1) ** 3)))
+    H = fdmpc.HexMesh(X.shape[0], cells, p)
+    U = HexProblem(p, X, cells, kappa=kappa)
+    mu, fac = H.factor(X, kappa)
+    ptr, nodec, geom, cof, Ac = H.operator_tables()
+    cn = H.cell_nodes()
+    pi = np.zeros(H.nnode, dtype=np.int64)
+    pi[cn.ravel()] = U.gid.ravel()
+    rng = np.random.default_rng(10 + p)
+    u = rng.standard_normal(U.ndof)
+    y = _emulated_operator(H, u[pi], geom, ptr, nodec, p)
+    want = U.apply(u)[pi]
+    assert np.abs(y - want).max() <= 1e-12 * np.abs(want).max()
+    # coarse space: P from the vertices' Q1 functions at each cell's GLL nodes
+    U.setup_coarse()
+    xi = oracle.basis1d(p)["xi"]
+    hat = np.stack([0.5 * (1 - xi), 0.5 * (1 + xi)], axis=1)
+    P = np.zeros((H.nnode, Ac.shape[0]))
+    for e in range(cells.shape[0]):
+        for c in range(8):
+            k = cof[cells[e, c]]
+            if k >= 0:
+                P[cn[e], k] = _kron3(hat[:, c >> 2], hat[:, (c >> 1) & 1], hat[:, c & 1])
+    P[H.dirichlet()] = 0.0
+    assert np.abs(Ac - U.Ac).max() <= 1e-12 * np.abs(U.Ac).max()
+    # V(1,1) with the oracle's omega
+    U.setup_patches()
+    lo, hi, om = U.lanczos_omega(inputs.lanczos_start(U.ndof))
+    basis = oracle.basis1d(p)
+    A = lambda x: _emulated_operator(H, x, geom, ptr, nodec, p)  # noqa: E731
+    S = lambda x: _emulated_asm(H, x, basis, mu, fac)[0]  # noqa: E731
+    r = rng.standard_normal(U.ndof)[pi]
+    r[H.dirichlet()] = 0.0
+    x1 = om * S(r)
+    x1 = x1 + P @ np.linalg.solve(Ac, P.T @ (r - A(x1)))
+    z = x1 + om * S(r - A(x1))
+    want = U.pc_apply(r[np.argsort(pi)])[pi]
+    assert np.abs(z - want).max() <= 1e-11 * np.abs(want).max()
