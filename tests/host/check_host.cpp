@@ -157,9 +157,31 @@ static int sipg(int argc, char **argv) {
   return 0;
 }
 
+// prints the library's 1D basis for degree p (Sections 2.1-2.4)
+static int basis(int argc, char **argv) {
+  if (argc < 3) return 1;
+  const Basis1D b = make_basis(std::atoi(argv[2]));
+  auto put = [](const char *name, const std::vector<double> &v) {
+    std::printf("%s", name);
+    for (double x : v) std::printf(" %.17g", x);
+    std::printf("\n");
+  };
+  put("xi", b.xi);
+  put("wgll", b.wgll);
+  put("A", b.A);
+  put("B", b.B);
+  put("S", b.S);
+  put("lam", b.lam);
+  put("T", b.T);
+  put("Af", b.Af);
+  put("Bf", b.Bf);
+  return 0;
+}
+
 int main(int argc, char **argv) {
   const std::string what = argc > 1 ? argv[1] : "all";
   if (what == "sipg") return sipg(argc, argv);
+  if (what == "basis") return basis(argc, argv);
   int bad = 0;
   if (what == "topology" || what == "all") bad += topology();
   if (what == "gmg" || what == "all") bad += gmg();

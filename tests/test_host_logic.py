@@ -107,3 +107,26 @@ def test_sipg_star_is_kronecker_sum_of_pencils(checker):
         D = (Z["lam"][:, None, None] + Y["lam"][None, :, None] + X["lam"][None, None, :]).ravel()
         inv = Sk @ np.diag(1.0 / D) @ Sk.T
         assert np.abs(inv @ Av - np.eye(len(D))).max() <= 1e-10
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 7, 10, 15])
+def test_library_basis_matches_the_oracle(checker, oracle_lib, p):
+    """The library's 1D basis (host code, make_basis) against the oracle's:
+    GLL rule, exact A_hat and B_hat, the interior eigenbasis (same order and
+    sign convention), T, and A_f, B_f with the same exact structural zeros."""
+    import numpy as np
+    r = subprocess.run([checker, "basis", str(p)], capture_output=True, text=True, check=True)
+    lib = {}
+    for line in r.stdout.splitlines():
+        k, *v = line.split()
+        lib[k] = np.array([float(x) for x in v])
+    ref = oracle_lib.basis1d(p)
+    n, m = p + 1, p - 1
+    assert np.abs(lib["xi"] - ref["xi"]).max() <= 1e-14
+    for k in ("A", "B", "T", "Af", "Bf"):
+        a, b = lib[k].reshape(n, n), ref[k]
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), k
+        assert np.array_equal(a == 0.0, b == 0.0), k  # identical exact zeros
+    if m > 0:
+        assert np.abs(lib["S"].reshape(m, m) - ref["S"]).max() <= 1e-11
+        assert np.abs(lib["lam"] - ref["lam"]).max() <= 1e-11 * ref["lam"].max()
