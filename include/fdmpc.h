@@ -34,7 +34,9 @@ extern "C" {
 /* ---- error codes ---- */
 #define FDM_OK 0
 #define FDM_EINVAL (-1)   /* bad argument */
-#define FDM_ENOMEM (-2)   /* device or host allocation failed */
+#define FDM_ENOMEM (-2)   /* device or host allocation failed, or a context's device allocations would
+                           * exceed the byte limit in the environment variable FDM_ALLOC_LIMIT_BYTES
+                           * (unset, empty or not a number: no limit) */
 #define FDM_ENOTSPD (-3)  /* a patch or coarse Cholesky pivot was <= 0 */
 #define FDM_ENOCONV (-4)  /* PCG reached maxit before rtol */
 #define FDM_ENAN (-5)     /* a non-finite scalar appeared in PCG */

@@ -2,6 +2,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -13,6 +15,26 @@
 
 namespace fdm {
 [[noreturn]] void fail(int code, const std::string &msg) { throw Error{code, msg}; }
+
+void *device_alloc(size_t bytes, size_t &used) {
+  bytes = std::max<size_t>(bytes, 1);
+  size_t limit = SIZE_MAX;
+  if (const char *s = std::getenv("FDM_ALLOC_LIMIT_BYTES")) {
+    char *end = nullptr;
+    const unsigned long long v = std::strtoull(s, &end, 10);
+    if (end != s && *end == '\0' && s[0] != '-') limit = (size_t)v;
+  }
+  if (bytes > limit || used > limit - bytes)
+    fail(FDM_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes would exceed FDM_ALLOC_LIMIT_BYTES = " +
+                         std::to_string(limit) + " (" + std::to_string(used) + " bytes allocated)");
+  void *ptr = nullptr;
+  if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    fail(FDM_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  used += bytes;
+  return ptr;
+}
 static_assert(MLP_NPARAM == FDM_MLP_NPARAM, "network size of the public header");
 }  // namespace fdm
 
@@ -1215,13 +1237,10 @@ void ensure_labels(fdm_ctx *c, cudaStream_t st) {
 // device buffers of one training run, released on every exit path
 struct DevScratch {
   std::vector<void *> p;
+  size_t bytes = 0;
   template <typename T>
   T *get(size_t n) {
-    void *ptr = nullptr;
-    if (cudaMalloc(&ptr, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
-      cudaGetLastError();
-      fail(FDM_ENOMEM, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed");
-    }
+    void *ptr = device_alloc(n * sizeof(T), bytes);
     p.push_back(ptr);
     return static_cast<T *>(ptr);
   }

@@ -125,13 +125,10 @@ struct fdm_ctx {
     }
   }
 
+  size_t alloc_bytes = 0;  // device bytes allocated through alloc()
   template <typename T>
   T *alloc(size_t n) {
-    void *ptr = nullptr;
-    if (cudaMalloc(&ptr, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
-      cudaGetLastError();
-      fail(FDM_ENOMEM, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed");
-    }
+    void *ptr = device_alloc(n * sizeof(T), alloc_bytes);
     allocs.push_back(ptr);
     return static_cast<T *>(ptr);
   }

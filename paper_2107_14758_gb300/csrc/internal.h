@@ -19,6 +19,13 @@ struct Error {
   std::string msg;
 };
 [[noreturn]] void fail(int code, const std::string &msg);
+// Device allocation on behalf of a context that has `used` bytes allocated so
+// far (updated): fails with FDM_ENOMEM when cudaMalloc fails or when the
+// context would exceed the byte limit in the environment variable
+// FDM_ALLOC_LIMIT_BYTES (unset, empty or not a number: no limit).  The limit
+// caps a context's device memory and lets a caller reach the FDM_ENOMEM
+// paths without exhausting a GPU.
+void *device_alloc(size_t bytes, size_t &used);
 #define FDM_CUDA(call)                                                              \
   do {                                                                              \
     cudaError_t e_ = (call);                                                        \

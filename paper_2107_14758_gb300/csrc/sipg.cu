@@ -41,13 +41,10 @@ struct fdm_sipg {
   int vcap = 0;
   int64_t zcap = 0;
   int64_t launches = 0;
+  size_t alloc_bytes = 0;  // device bytes allocated through alloc()
   template <typename T>
   T *alloc(size_t k) {
-    void *ptr = nullptr;
-    if (cudaMalloc(&ptr, std::max<size_t>(k, 1) * sizeof(T)) != cudaSuccess) {
-      cudaGetLastError();
-      fail(FDM_ENOMEM, "cudaMalloc of " + std::to_string(k * sizeof(T)) + " bytes failed");
-    }
+    void *ptr = device_alloc(k * sizeof(T), alloc_bytes);
     allocs.push_back(ptr);
     return static_cast<T *>(ptr);
   }

@@ -136,3 +136,40 @@ def test_default_options_match_header(lib):
     assert o.lanczos_steps == 20 and o.lanczos_seed == 12345 and o.wait_timeout_s == 1.0
     assert o.pcg_graph == 1 and o.autotune == 0 and o.patch_rows_per_warp == 0
     assert o.coarse_levels == -1 and o.gmg_nu == 2 and o.gmg_omega == pytest.approx(2.0 / 3.0, rel=1e-15)
+
+
+def test_allocation_limit_reports_enomem_without_gpu(lib, monkeypatch):
+    """FDM_ALLOC_LIMIT_BYTES caps a context's device memory: a set-up that
+    would exceed it returns FDM_ENOMEM before any device call (so the error
+    path runs without a GPU), for the scalar, elasticity and SIPG contexts;
+    unset, empty, negative or non-numeric values set no limit (the set-up then
+    reaches cudaMalloc, which fails here only because there is no GPU)."""
+    import numpy as np
+    from paper_2107_14758_gb300 import fdmpc
+    L = fdmpc.load()
+    mesh = fdmpc.fdm_mesh()
+    v = np.linspace(0, 1, 3)
+    mesh.nx = mesh.ny = mesh.nz = 2
+    mesh.xv = mesh.yv = mesh.zv = v.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    h = ctypes.c_void_p()
+    o = fdmpc.fdm_default_options()
+    for limit in ("0", "100"):
+        monkeypatch.setenv("FDM_ALLOC_LIMIT_BYTES", limit)
+        assert L.fdm_setup(ctypes.byref(mesh), 2, None, ctypes.byref(o), ctypes.byref(h), None) == fdmpc.FDM_ENOMEM
+        assert "FDM_ALLOC_LIMIT_BYTES = %s" % limit in fdmpc.fdm_last_error(None)
+        assert L.fdm_elast_setup(ctypes.byref(mesh), 2, 1.0, 1.0, ctypes.byref(o), ctypes.byref(h),
+                                 None) == fdmpc.FDM_ENOMEM
+        assert "FDM_ALLOC_LIMIT_BYTES" in L.fdm_elast_last_error(None).decode()
+        assert L.fdm_sipg_setup(ctypes.byref(mesh), 2, -1.0, ctypes.byref(o), ctypes.byref(h),
+                                None) == fdmpc.FDM_ENOMEM
+        assert "FDM_ALLOC_LIMIT_BYTES" in L.fdm_sipg_last_error(None).decode()
+    import torch
+    if torch.cuda.is_available():
+        return  # the no-limit case below needs cudaMalloc to fail
+    for value in (None, "", "abc", "-5"):
+        if value is None:
+            monkeypatch.delenv("FDM_ALLOC_LIMIT_BYTES", raising=False)
+        else:
+            monkeypatch.setenv("FDM_ALLOC_LIMIT_BYTES", value)
+        assert L.fdm_setup(ctypes.byref(mesh), 2, None, ctypes.byref(o), ctypes.byref(h), None) == fdmpc.FDM_ENOMEM
+        assert "FDM_ALLOC_LIMIT_BYTES" not in fdmpc.fdm_last_error(None)
