@@ -1240,7 +1240,7 @@ struct DevScratch {
   size_t bytes = 0;
   template <typename T>
   T *get(size_t n) {
-    void *ptr = device_alloc(n * sizeof(T), bytes);
+    void *ptr = device_alloc(std::max<size_t>(n, 1) * sizeof(T), bytes);
     p.push_back(ptr);
     return static_cast<T *>(ptr);
   }

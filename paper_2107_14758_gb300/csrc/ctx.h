@@ -128,7 +128,7 @@ struct fdm_ctx {
   size_t alloc_bytes = 0;  // device bytes allocated through alloc()
   template <typename T>
   T *alloc(size_t n) {
-    void *ptr = device_alloc(n * sizeof(T), alloc_bytes);
+    void *ptr = device_alloc(std::max<size_t>(n, 1) * sizeof(T), alloc_bytes);
     allocs.push_back(ptr);
     return static_cast<T *>(ptr);
   }

@@ -44,7 +44,7 @@ struct fdm_sipg {
   size_t alloc_bytes = 0;  // device bytes allocated through alloc()
   template <typename T>
   T *alloc(size_t k) {
-    void *ptr = device_alloc(k * sizeof(T), alloc_bytes);
+    void *ptr = device_alloc(std::max<size_t>(k, 1) * sizeof(T), alloc_bytes);
     allocs.push_back(ptr);
     return static_cast<T *>(ptr);
   }
