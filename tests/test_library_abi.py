@@ -173,3 +173,18 @@ def test_allocation_limit_reports_enomem_without_gpu(lib, monkeypatch):
             monkeypatch.setenv("FDM_ALLOC_LIMIT_BYTES", value)
         assert L.fdm_setup(ctypes.byref(mesh), 2, None, ctypes.byref(o), ctypes.byref(h), None) == fdmpc.FDM_ENOMEM
         assert "FDM_ALLOC_LIMIT_BYTES" not in fdmpc.fdm_last_error(None)
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/fdmpc.h is a C header: it compiles as pedantic C99 (no torch or
+    C++ types in the boundary)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "fdmpc.h"\nint main(void) { fdm_options o; fdm_default_options(&o); return o.pc; }\n')
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
