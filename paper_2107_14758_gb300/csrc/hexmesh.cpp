@@ -269,7 +269,8 @@ struct Builder {
   // the cell order and the labels.  Stars with equal encodings are the same
   // configuration, so their orders (and patterns) coincide.
   std::vector<int64_t> canonical_star(int v, const std::vector<int> &vc, const std::vector<int32_t> &cell_fdm,
-                                      const std::vector<uint8_t> &dirichlet, int &nint) const {
+                                      const std::vector<uint8_t> &dirichlet, int &nint,
+                                      std::vector<int> &encoding) const {
     const int nvc = (int)vc.size(), n3 = n * n * n;
     struct AtV {
       int e, cv;
@@ -366,6 +367,7 @@ struct Builder {
           best_frame = frame;
         }
       }
+    encoding = best_enc;
     // the order: interiors cell by cell, then faces, edges (first seen in the
     // canonical walk, functions in the first cell's labels), the vertex
     std::vector<int64_t> out;
@@ -556,19 +558,52 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
     for (int e = 0; e < nc; ++e)
       for (int k = 0; k < 8; ++k) vcells[cells[8 * e + k]].push_back(e);
     std::map<std::vector<int>, int> classes;
+    // per canonical configuration: the interface permutation, the interior count and the class
+    struct StarShape {
+      std::vector<int> newpos;
+      int nint = 0, cls = -1;
+    };
+    std::map<std::vector<int>, StarShape> star_cache;
     h->star_ptr.push_back(0);
     h->pat_ptr.push_back(0);
     h->pat_colptr.push_back(0);
     for (int v = 0; v < nv; ++v) {
       if (vcells[v].empty()) continue;
       int nint = 0;
-      std::vector<int64_t> order = B.canonical_star(v, vcells[v], h->cell_fdm, h->dirichlet, nint);
-      std::map<int64_t, int> in_star;
+      std::vector<int> enc;
+      std::vector<int64_t> order = B.canonical_star(v, vcells[v], h->cell_fdm, h->dirichlet, nint, enc);
       if (order.empty()) continue;
+      const int ns = (int)order.size();
+      // a configuration seen before: its pattern, interface order and class
+      auto hit = star_cache.find(enc);
+      if (hit != star_cache.end()) {
+        const StarShape &sh = hit->second;
+        if ((int)sh.newpos.size() != ns || sh.nint != nint)
+          fdm::fail(FDM_EINVAL, "fdm_hexmesh_create: inconsistent star configuration");
+        std::vector<int64_t> order2(ns);
+        for (int r = 0; r < ns; ++r) order2[sh.newpos[r]] = order[r];
+        h->star_vertex.push_back(v);
+        for (int64_t g : order2) h->star_nodes.push_back((int32_t)g);
+        h->star_ptr.push_back((int64_t)h->star_nodes.size());
+        // the pattern of the class's first star (copied out first: the vectors grow)
+        const int k0 = h->class_star[sh.cls];
+        const std::vector<int64_t> rp0(h->pat_rowptr.begin() + h->pat_ptr[k0],
+                                       h->pat_rowptr.begin() + h->pat_ptr[k0] + ns + 1);
+        const std::vector<int32_t> c0(h->pat_cols.begin() + h->pat_colptr[k0],
+                                      h->pat_cols.begin() + h->pat_colptr[k0] + rp0[ns]);
+        h->pat_rowptr.insert(h->pat_rowptr.end(), rp0.begin(), rp0.end());
+        h->pat_cols.insert(h->pat_cols.end(), c0.begin(), c0.end());
+        h->pat_ptr.push_back((int64_t)h->pat_rowptr.size());
+        h->pat_colptr.push_back((int64_t)h->pat_cols.size());
+        h->star_nint.push_back(nint);
+        h->star_class.push_back(sh.cls);
+        continue;
+      }
+      StarShape shape;
+      std::map<int64_t, int> in_star;
       for (size_t k = 0; k < order.size(); ++k) in_star[order[k]] = (int)k;
       // the surrogate pattern: FDM functions c1, c2 of a star cell couple iff for
       // some axis a, Af couples them along a and Bf along the other two axes
-      const int ns = (int)order.size();
       std::vector<std::vector<int>> rows(ns);
       for (int e : vcells[v]) {
         // (cell-local FDM index, star position): an entity's FDM functions use the
@@ -640,6 +675,8 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
         for (auto &r : rows2) std::sort(r.begin(), r.end());
         order.swap(order2);
         rows.swap(rows2);
+        shape.newpos.swap(newpos);
+        shape.nint = nint;
       }
       h->star_vertex.push_back(v);
       for (int64_t g : order) h->star_nodes.push_back((int32_t)g);
@@ -666,10 +703,14 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
       auto found = classes.find(key);
       if (found != classes.end()) {
         h->star_class.push_back(found->second);
+        shape.cls = found->second;
+        star_cache.emplace(std::move(enc), std::move(shape));
         continue;
       }
       const int cls = (int)h->class_star.size();
       classes.emplace(std::move(key), cls);
+      shape.cls = cls;
+      star_cache.emplace(std::move(enc), std::move(shape));
       h->star_class.push_back(cls);
       h->class_star.push_back((int32_t)h->star_vertex.size() - 1);
       // pattern of S_G: A_GG plus, through every interior function, the
