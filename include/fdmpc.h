@@ -441,6 +441,20 @@ int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_hexmesh **ou
 #define FDM_HQ_COARSE_OF 38     /* int32[nv]: coarse unknown of each vertex, -1 on boundary faces or unused */
 #define FDM_HQ_COARSE 39        /* double[nco][nco] (after fdm_hexmesh_factor): the Q1 Galerkin operator
                                  * P^T A P, P the Q1 functions of the coarse vertices in Q_p */
+#define FDM_HQ_SC_SPLIT 40      /* int32[nclass]: size t of the top block T of the Schur-coupling form (the
+                                 * last t interface positions, whole entities, chosen to minimise the stored
+                                 * values nnz(L_BB) + nnz(S_TB) + t (t + 1) / 2) */
+#define FDM_HQ_SC_PTR 41        /* int64[nclass + 1]: offsets into FDM_HQ_SC_ROWPTR */
+#define FDM_HQ_SC_ROWPTR 42     /* int64[...]: per class, the row pointers of L_BB (nB + 1, from 0) and of
+                                 * S_TB (t + 1, from 0); nB = interface size - t */
+#define FDM_HQ_SC_COLPTR 43     /* int64[nclass + 1]: offsets into FDM_HQ_SC_COLS */
+#define FDM_HQ_SC_COLS 44       /* int32[...]: per class, L_BB's columns then S_TB's (B positions) */
+#define FDM_HQ_SC_VALUES_PTR 45 /* int64[nstar + 1]: offsets into FDM_HQ_SC_VALUES */
+#define FDM_HQ_SC_VALUES 46     /* double[...] (after fdm_hexmesh_factor): per star, the values of L_BB
+                                 * (S_BB = L_BB L_BB^T), of S_TB, and the lower triangle of
+                                 * W = (S_TT - S_TB S_BB^{-1} S_BT)^{-1} row by row: the star's interface
+                                 * solve is y_B = S_BB^{-1} g_B, x_T = W (g_T - S_TB y_B),
+                                 * x_B = y_B - S_BB^{-1} S_BT x_T */
 /* Numeric set-up on the host, FP64 (Sections 2.6-2.7): X[nv][3] (HOST) the
  * vertex coordinates, kappa_q NULL or the coefficient at the (p+1)^3 Gauss
  * points of every cell (x fastest).  Per cell the averaged surrogate mu_d =

@@ -54,6 +54,15 @@ struct fdm_hexmesh {
   std::vector<int32_t> fill_cols;    // per class: columns of each row of L (interface positions, sorted)
   std::vector<int64_t> etree_ptr;    // [nclass + 1] into etree
   std::vector<int32_t> etree;        // per class: parent of each interface column (-1: root)
+  // Schur-coupling form per class: the top block T = the last t interface
+  // positions; the rows of L_BB (fill of S_BB) and of S_TB (S_G's pattern)
+  std::vector<int32_t> sc_t;         // [nclass]
+  std::vector<int64_t> sc_ptr;       // [nclass + 1] into sc_rowptr (nB + 1 + t + 1 entries each)
+  std::vector<int64_t> sc_rowptr;    // per class: L_BB row pointers from 0, then S_TB row pointers from 0
+  std::vector<int64_t> sc_colptr;    // [nclass + 1] into sc_cols
+  std::vector<int32_t> sc_cols;      // per class: L_BB columns, then S_TB columns (B positions)
+  std::vector<int64_t> sc_values_ptr;  // [nstar + 1] into sc_values
+  std::vector<double> sc_values;     // per star: L_BB, S_TB, then the lower triangle of W = S_T^{-1} by rows
   // inverse maps for the apply: per FDM slot its (cell, local index) pairs and
   // its (star, position) pairs, per node its owner (lowest cell, local index)
   std::vector<int64_t> slot_cells_ptr;  // [nnode + 1]
@@ -736,6 +745,61 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
       h->etree.insert(h->etree.end(), parent.begin(), parent.end());
       h->etree_ptr.push_back((int64_t)h->etree.size());
       h->class_nnzl.push_back(nnzl);
+      // Schur-coupling split: the top block T is a suffix of the interface
+      // order made of whole entities, chosen to minimise the stored values
+      // nnz(L_BB) + nnz(S_TB) + t (t + 1) / 2
+      {
+        const int nG = ns - nint;
+        std::vector<int> cand{0};
+        for (int i = nG - 1; i >= 1; --i)
+          if (B.entity[order[nint + i]] != B.entity[order[nint + i - 1]]) cand.push_back(nG - i);
+        if (nG > 0) cand.push_back(nG);
+        int64_t best = -1;
+        int best_t = 0;
+        std::vector<std::vector<int>> best_L, best_TB;
+        for (int t : cand) {
+          const int nB = nG - t;
+          std::vector<std::vector<int>> SB(nB), TB(t);
+          int64_t ntb = 0;
+          for (int r = 0; r < nG; ++r)
+            for (int c : Sg[r]) {
+              if (c >= nB) continue;
+              if (r < nB) SB[r].push_back(c);
+              else {
+                TB[r - nB].push_back(c);
+                ++ntb;
+              }
+            }
+          std::vector<std::vector<int>> Lb;
+          std::vector<int> pb;
+          symbolic_cholesky(SB, Lb, pb);
+          int64_t nl = 0;
+          for (auto &x : Lb) nl += (int64_t)x.size();
+          const int64_t cost = nl + ntb + (int64_t)t * (t + 1) / 2;
+          if (best < 0 || cost < best) {
+            best = cost;
+            best_t = t;
+            best_L.swap(Lb);
+            best_TB.swap(TB);
+          }
+        }
+        if (h->sc_ptr.empty()) {
+          h->sc_ptr.push_back(0);
+          h->sc_colptr.push_back(0);
+        }
+        h->sc_t.push_back(best_t);
+        for (auto *part : {&best_L, &best_TB}) {
+          int64_t cnt2 = 0;
+          h->sc_rowptr.push_back(0);
+          for (auto &r : *part) {
+            h->sc_cols.insert(h->sc_cols.end(), r.begin(), r.end());
+            cnt2 += (int64_t)r.size();
+            h->sc_rowptr.push_back(cnt2);
+          }
+        }
+        h->sc_ptr.push_back((int64_t)h->sc_rowptr.size());
+        h->sc_colptr.push_back((int64_t)h->sc_cols.size());
+      }
     }
     // inverse maps (counting sort by slot keeps the cell / star order)
     {
@@ -903,6 +967,8 @@ extern "C" int fdm_hexmesh_factor(fdm_hexmesh *h, int nv, const double *X, const
     h->factor_ptr.assign(1, 0);
     h->diag.clear();
     h->factor.clear();
+    h->sc_values_ptr.assign(1, 0);
+    h->sc_values.clear();
     for (int k = 0; k < nstar; ++k) {
       const int64_t s0 = h->star_ptr[k], ns = h->star_ptr[k + 1] - s0;
       const int nint = h->star_nint[k], nG = (int)ns - nint;
@@ -960,6 +1026,7 @@ extern "C" int fdm_hexmesh_factor(fdm_hexmesh *h, int nv, const double *X, const
         for (auto &a : nb)
           for (auto &b : nb) S[(size_t)a.first * nG + b.first] -= a.second * b.second / d;
       }
+      const std::vector<double> S0 = S;  // S_G before the factorisation (full, symmetric)
       // Cholesky (right-looking), then the values in the class's fill pattern;
       // an entry outside the fill would mean a wrong symbolic factorisation
       double smax = 0.0;
@@ -989,6 +1056,82 @@ extern "C" int fdm_hexmesh_factor(fdm_hexmesh *h, int nv, const double *X, const
           if (!in_fill[(size_t)r * nG + c] && std::fabs(S[(size_t)r * nG + c]) > 1e-10 * std::sqrt(smax))
             fdm::fail(FDM_EINVAL, "fdm_hexmesh_factor: factor entry outside the symbolic fill");
       h->factor_ptr.push_back((int64_t)h->factor.size());
+      // the Schur-coupling form: L_BB, S_TB and W = (S_TT - S_TB S_BB^{-1} S_BT)^{-1}
+      {
+        const int t = h->sc_t[cls], nB = nG - t;
+        const int64_t *rpb = h->sc_rowptr.data() + h->sc_ptr[cls];
+        const int64_t *rpt = rpb + nB + 1;
+        const int32_t *cb = h->sc_cols.data() + h->sc_colptr[cls];
+        const int32_t *ct = cb + rpb[nB];
+        std::vector<double> LB((size_t)nB * nB, 0.0);
+        for (int r = 0; r < nB; ++r)
+          for (int c = 0; c <= r; ++c) LB[(size_t)r * nB + c] = S0[(size_t)r * nG + c];
+        for (int j = 0; j < nB; ++j) {
+          double &djj = LB[(size_t)j * nB + j];
+          if (!(djj > 0.0)) fdm::fail(FDM_ENOTSPD, "fdm_hexmesh_factor: lower-block pivot <= 0");
+          djj = std::sqrt(djj);
+          for (int i = j + 1; i < nB; ++i) LB[(size_t)i * nB + j] /= djj;
+          for (int c = j + 1; c < nB; ++c) {
+            const double lcj = LB[(size_t)c * nB + j];
+            if (lcj == 0.0) continue;
+            for (int i = c; i < nB; ++i) LB[(size_t)i * nB + c] -= LB[(size_t)i * nB + j] * lcj;
+          }
+        }
+        std::vector<char> in_b((size_t)nB * nB, 0);
+        for (int r = 0; r < nB; ++r)
+          for (int64_t q2 = rpb[r]; q2 < rpb[r + 1]; ++q2) {
+            in_b[(size_t)r * nB + cb[q2]] = 1;
+            h->sc_values.push_back(LB[(size_t)r * nB + cb[q2]]);
+          }
+        for (int r = 0; r < nB; ++r)
+          for (int c = 0; c < r; ++c)
+            if (!in_b[(size_t)r * nB + c] && std::fabs(LB[(size_t)r * nB + c]) > 1e-10 * std::sqrt(smax))
+              fdm::fail(FDM_EINVAL, "fdm_hexmesh_factor: lower-block entry outside its symbolic fill");
+        for (int r = 0; r < t; ++r)
+          for (int64_t q2 = rpt[r]; q2 < rpt[r + 1]; ++q2) h->sc_values.push_back(S0[(size_t)(nB + r) * nG + ct[q2]]);
+        // Y = L_BB^{-1} S_BT (nB x t), C = S_TT - Y^T Y, W = C^{-1}
+        std::vector<double> Y((size_t)nB * t);
+        for (int j = 0; j < t; ++j)
+          for (int i = 0; i < nB; ++i) {
+            double v = S0[(size_t)i * nG + nB + j];
+            for (int l = 0; l < i; ++l) v -= LB[(size_t)i * nB + l] * Y[(size_t)l * t + j];
+            Y[(size_t)i * t + j] = v / LB[(size_t)i * nB + i];
+          }
+        std::vector<double> Cm((size_t)t * t);
+        for (int a = 0; a < t; ++a)
+          for (int b2 = 0; b2 < t; ++b2) {
+            double v = S0[(size_t)(nB + a) * nG + nB + b2];
+            for (int i = 0; i < nB; ++i) v -= Y[(size_t)i * t + a] * Y[(size_t)i * t + b2];
+            Cm[(size_t)a * t + b2] = v;
+          }
+        // Cholesky of C, then W = C^{-1} column by column
+        for (int j = 0; j < t; ++j) {
+          double &djj = Cm[(size_t)j * t + j];
+          if (!(djj > 0.0)) fdm::fail(FDM_ENOTSPD, "fdm_hexmesh_factor: top-block pivot <= 0");
+          djj = std::sqrt(djj);
+          for (int i = j + 1; i < t; ++i) Cm[(size_t)i * t + j] /= djj;
+          for (int c = j + 1; c < t; ++c) {
+            const double lcj = Cm[(size_t)c * t + j];
+            for (int i = c; i < t; ++i) Cm[(size_t)i * t + c] -= Cm[(size_t)i * t + j] * lcj;
+          }
+        }
+        std::vector<double> Wm((size_t)t * t), col(t);
+        for (int j = 0; j < t; ++j) {
+          for (int i = 0; i < t; ++i) {  // forward: L y = e_j
+            double v = (i == j) ? 1.0 : 0.0;
+            for (int l = 0; l < i; ++l) v -= Cm[(size_t)i * t + l] * col[l];
+            col[i] = v / Cm[(size_t)i * t + i];
+          }
+          for (int i = t - 1; i >= 0; --i) {  // backward: L^T x = y
+            double v = col[i];
+            for (int l = i + 1; l < t; ++l) v -= Cm[(size_t)l * t + i] * Wm[(size_t)l * t + j];
+            Wm[(size_t)i * t + j] = v / Cm[(size_t)i * t + i];
+          }
+        }
+        for (int r = 0; r < t; ++r)
+          for (int c = 0; c <= r; ++c) h->sc_values.push_back(0.5 * (Wm[(size_t)r * t + c] + Wm[(size_t)c * t + r]));
+        h->sc_values_ptr.push_back((int64_t)h->sc_values.size());
+      }
     }
   } catch (const fdm::Error &e) {
     return handle_hex(h, e);
@@ -1053,6 +1196,13 @@ extern "C" int fdm_hexmesh_query(fdm_hexmesh *h, int what, void *out, size_t *le
     case FDM_HQ_DIAG: return put(h->diag.data(), h->diag.size() * sizeof(double));
     case FDM_HQ_FACTOR_PTR: return put(h->factor_ptr.data(), h->factor_ptr.size() * sizeof(int64_t));
     case FDM_HQ_FACTOR: return put(h->factor.data(), h->factor.size() * sizeof(double));
+    case FDM_HQ_SC_SPLIT: return put(h->sc_t.data(), h->sc_t.size() * sizeof(int32_t));
+    case FDM_HQ_SC_PTR: return put(h->sc_ptr.data(), h->sc_ptr.size() * sizeof(int64_t));
+    case FDM_HQ_SC_ROWPTR: return put(h->sc_rowptr.data(), h->sc_rowptr.size() * sizeof(int64_t));
+    case FDM_HQ_SC_COLPTR: return put(h->sc_colptr.data(), h->sc_colptr.size() * sizeof(int64_t));
+    case FDM_HQ_SC_COLS: return put(h->sc_cols.data(), h->sc_cols.size() * sizeof(int32_t));
+    case FDM_HQ_SC_VALUES_PTR: return put(h->sc_values_ptr.data(), h->sc_values_ptr.size() * sizeof(int64_t));
+    case FDM_HQ_SC_VALUES: return put(h->sc_values.data(), h->sc_values.size() * sizeof(double));
     default:
       h->err = "fdm_hexmesh_query: unknown query";
       return FDM_EINVAL;

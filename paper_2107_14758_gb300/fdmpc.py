@@ -31,7 +31,8 @@ FDM_SURR_AVERAGED, FDM_SURR_EXTERNAL = 0, 1
  FDM_HQ_ETREE_PTR, FDM_HQ_ETREE, FDM_HQ_MU, FDM_HQ_DIAG_PTR, FDM_HQ_DIAG, FDM_HQ_FACTOR_PTR,
  FDM_HQ_FACTOR, FDM_HQ_SLOT_CELLS_PTR, FDM_HQ_SLOT_CELLS, FDM_HQ_SLOT_STARS_PTR, FDM_HQ_SLOT_STARS,
  FDM_HQ_NODE_OWNER, FDM_HQ_NODE_CELLS_PTR, FDM_HQ_NODE_CELLS, FDM_HQ_GEOM, FDM_HQ_COARSE_OF,
- FDM_HQ_COARSE) = range(1, 40)
+ FDM_HQ_COARSE, FDM_HQ_SC_SPLIT, FDM_HQ_SC_PTR, FDM_HQ_SC_ROWPTR, FDM_HQ_SC_COLPTR, FDM_HQ_SC_COLS,
+ FDM_HQ_SC_VALUES_PTR, FDM_HQ_SC_VALUES) = range(1, 47)
 FDM_MLP_NPARAM = 16515
 TIMERS = ("restrict", "patch", "interp", "op64", "op32", "coarse", "vec")
 
@@ -856,3 +857,22 @@ class HexMesh:
         co = self.query(FDM_HQ_COARSE, np.float64)
         m = int(round(np.sqrt(co.size)))
         return ptr, nodec, geom, cof, co.reshape(m, m)
+
+    def schur_coupling(self):
+        """Per class (t, (L_BB rowptr, cols), (S_TB rowptr, cols)); per star its
+        values (L_BB, S_TB, lower triangle of W) after factor()."""
+        t = self.query(FDM_HQ_SC_SPLIT, np.int32)
+        sp = self.query(FDM_HQ_SC_PTR, np.int64)
+        rp = self.query(FDM_HQ_SC_ROWPTR, np.int64)
+        cp = self.query(FDM_HQ_SC_COLPTR, np.int64)
+        cols = self.query(FDM_HQ_SC_COLS, np.int32)
+        per = []
+        for k in range(len(t)):
+            r = rp[sp[k]:sp[k + 1]]
+            nB = len(r) - int(t[k]) - 2
+            rb, rt = r[:nB + 1], r[nB + 1:]
+            c = cols[cp[k]:cp[k + 1]]
+            per.append((int(t[k]), (rb, c[:rb[-1]]), (rt, c[rb[-1]:])))
+        vp = self.query(FDM_HQ_SC_VALUES_PTR, np.int64)
+        v = self.query(FDM_HQ_SC_VALUES, np.float64)
+        return per, [v[vp[k]:vp[k + 1]] for k in range(len(vp) - 1)]

@@ -23,6 +23,8 @@ cells' GLL nodes by position and glues its star FDM bases by matching traces:
   cell), equals the oracle's sweep; so do the stiffness apply from the
   library's geometry factors and node-to-cell map, the library's Q1 coarse
   operator and the hybrid V(1,1) built from them (with a coefficient kappa);
+* the Schur-coupling form of every star (L_BB, S_TB, W) solves the oracle's
+  interface Schur complement and stores fewer values on the large stars;
 * the numeric set-up (fdm_hexmesh_factor) gives the oracle's surrogate
   coefficients (also with a coefficient at the Gauss points), interior pivots
   and interface Schur complement (L L^T), and the star solve from D and L in
@@ -465,3 +467,55 @@ def test_emulated_operator_and_vcycle(fdmpc, p):
     z = x1 + om * S(r - A(x1))
     want = U.pc_apply(r[np.argsort(pi)])[pi]
     assert np.abs(z - want).max() <= 1e-11 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_schur_coupling_form(fdmpc, p):
+    """The Schur-coupling form of every star's interface solve (y_B = S_BB^{-1}
+    g_B, x_T = W (g_T - S_TB y_B), x_B = y_B - S_BB^{-1} S_BT x_T, from the
+    library's L_BB, S_TB and W) solves the oracle's interface Schur
+    complement, and it stores fewer values than the L form on the large stars."""
+    X, cells = inputs.unstructured_hex_mesh(2, 2, 5)
+    H = fdmpc.HexMesh(X.shape[0], cells, p)
+    U = HexProblem(p, X, cells)
+    mu, fac = H.factor(X)
+    per_sc, vals = H.schur_coupling()
+    cls, nint, per = H.classes()
+    cn = H.cell_nodes()
+    pi = np.zeros(H.nnode, dtype=np.int64)
+    pi[cn.ravel()] = U.gid.ravel()
+    rng = np.random.default_rng(p)
+    for k in range(len(cls)):
+        t, (rb, cb), (rt, ct) = per_sc[cls[k]]
+        Tv, Af, v, dofs = _star_fdm_matrix(U, H, k, pi)
+        ni = int(nint[k])
+        nG = len(dofs) - ni
+        nB = nG - t
+        if nG == 0:
+            assert t == 0 and len(vals[k]) == 0
+            continue
+        D = np.diag(Af)[:ni]
+        S = Af[ni:, ni:] - Af[ni:, :ni] @ (Af[:ni, ni:] / D[:, None])
+        val = vals[k]
+        LB = np.zeros((nB, nB))
+        for r in range(nB):
+            LB[r, cb[rb[r]:rb[r + 1]]] = val[rb[r]:rb[r + 1]]
+        o = rb[-1]
+        STB = np.zeros((t, nB))
+        for r in range(t):
+            STB[r, ct[rt[r]:rt[r + 1]]] = val[o + rt[r]:o + rt[r + 1]]
+        o += rt[-1]
+        W = np.zeros((t, t))
+        W[np.tril_indices(t)] = val[o:]
+        W = W + np.tril(W, -1).T
+        assert len(val) == o + t * (t + 1) // 2
+        g = rng.standard_normal(nG)
+        solve_B = lambda y: np.linalg.solve(LB.T, np.linalg.solve(LB, y)) if nB else y  # noqa: E731
+        yB = solve_B(g[:nB])
+        xT = W @ (g[nB:] - STB @ yB)
+        xB = yB - solve_B(STB.T @ xT)
+        x = np.concatenate([xB, xT])
+        want = np.linalg.solve(S, g)
+        assert np.abs(x - want).max() <= 1e-10 * np.abs(want).max()
+        if nG > 100:
+            assert len(val) < per[cls[k]][1]
