@@ -399,6 +399,20 @@ def bench_gpu(args):
     ctx.kernel_times()
     ctx.launches()
     secondary = {"pc_apply_gdofs": free / (pc_ms * 1e-3) / 1e9, "pc_apply_ms": pc_ms}
+    try:  # one damped additive Schwarz sweep (asm_apply), the relaxation alone
+        for _ in range(3):
+            ctx.asm_apply(r, z)
+        torch.cuda.synchronize()
+        e4.record(stream)
+        for _ in range(20):
+            ctx.asm_apply(r, z)
+        e5.record(stream)
+        torch.cuda.synchronize()
+        asm_ms = e4.elapsed_time(e5) / 20
+        secondary["asm_apply_gdofs"] = free / (asm_ms * 1e-3) / 1e9
+        secondary["asm_apply_ms"] = asm_ms
+    except Exception as exc:  # noqa: BLE001
+        secondary["asm_apply_error"] = "%s: %s" % (type(exc).__name__, exc)
     if not args.no_fp64:
         ctx64 = fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP64)
         for _ in range(2):
