@@ -492,6 +492,343 @@ struct Builder {
   }
 };
 
+// the parity (+1 even, -1 odd under reflection) of each interior 1D FDM
+// function s_m, m = 1..p-1, read off the computed eigenvectors
+std::vector<int> interior_parities(const fdm::Basis1D &basis, int p) {
+  const int m = p - 1;
+  std::vector<int> parity(std::max(m, 0));
+  for (int j = 0; j < m; ++j) {
+    double even = 0.0, odd = 0.0, scale = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double a = basis.S[i * m + j], b = basis.S[(m - 1 - i) * m + j];
+      even = std::max(even, std::fabs(a - b));
+      odd = std::max(odd, std::fabs(a + b));
+      scale = std::max(scale, std::fabs(a));
+    }
+    if (even <= 1e-10 * scale) parity[j] = 1;
+    else if (odd <= 1e-10 * scale) parity[j] = -1;
+    else fdm::fail(FDM_EINVAL, "fdm_hexmesh_create: an interior FDM function is neither even nor odd");
+  }
+  return parity;
+}
+
+// appends rows as one CSR block: row pointers from 0 to rowptr, columns to cols
+template <typename Rows>
+int64_t append_csr(const Rows &rows, std::vector<int64_t> &rowptr, std::vector<int32_t> &cols) {
+  int64_t cnt = 0;
+  rowptr.push_back(0);
+  for (auto &r : rows) {
+    cols.insert(cols.end(), r.begin(), r.end());
+    cnt += (int64_t)r.size();
+    rowptr.push_back(cnt);
+  }
+  return cnt;
+}
+
+// per cell and local index: the node, the FDM slot and its sign
+void build_cell_maps(fdm_hexmesh *h, const Builder &B) {
+  const int n = h->n, n3 = n * n * n;
+  h->cell_nodes.resize((size_t)h->nc * n3);
+  h->cell_fdm.resize((size_t)h->nc * n3);
+  h->cell_sign.resize((size_t)h->nc * n3);
+  for (int e = 0; e < h->nc; ++e)
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          const int idx[3] = {i, j, k};
+          int64_t node, fn;
+          int sign;
+          B.map_local(e, idx, node, fn, sign);
+          const size_t l = (size_t)e * n3 + i + n * (j + n * k);
+          h->cell_nodes[l] = (int32_t)node;
+          h->cell_fdm[l] = (int32_t)fn;
+          h->cell_sign[l] = (int8_t)sign;
+        }
+}
+
+// Dirichlet nodes: the closure of every face that belongs to one cell
+void mark_dirichlet(fdm_hexmesh *h, const Builder &B) {
+  const int n = h->n, n3 = n * n * n, p = h->p;
+  h->dirichlet.assign(B.nnode, 0);
+  for (int e = 0; e < h->nc; ++e)
+    for (int d = 0; d < 3; ++d)
+      for (int s = 0; s < 2; ++s) {
+        if (B.fcount.at(Builder::face_key(B.face_corners(e, d, s))) != 1) continue;
+        for (int k = 0; k < n; ++k)
+          for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+              const int idx[3] = {i, j, k};
+              if (idx[d] == (s ? p : 0)) h->dirichlet[h->cell_nodes[(size_t)e * n3 + i + n * (j + n * k)]] = 1;
+            }
+      }
+}
+
+// pattern of S_G = A_GG - A_GI D^{-1} A_IG over interface positions: A_GG plus,
+// through every interior function, the interface functions it couples to
+// (the interior block is diagonal)
+std::vector<std::vector<int>> schur_pattern(const std::vector<std::vector<int>> &rows, int nint) {
+  const int ns = (int)rows.size();
+  std::vector<std::vector<int>> Sg(ns - nint);
+  for (int r = nint; r < ns; ++r) {
+    std::vector<int> &o = Sg[r - nint];
+    for (int c : rows[r]) {
+      if (c >= nint) o.push_back(c - nint);
+      else
+        for (int c2 : rows[c])
+          if (c2 >= nint) o.push_back(c2 - nint);
+    }
+    std::sort(o.begin(), o.end());
+    o.erase(std::unique(o.begin(), o.end()), o.end());
+  }
+  return Sg;
+}
+
+// The vertex stars: their canonical order, surrogate patterns, interface
+// order, sparsity classes and each class's symbolic factorisations.
+struct StarBuilder {
+  fdm_hexmesh *h;
+  const Builder &B;
+  std::vector<std::vector<int>> vcells;  // cells of each vertex
+  std::map<std::vector<int>, int> classes;  // pattern -> class
+  // per canonical configuration: the interface permutation, the interior count and the class
+  struct StarShape {
+    std::vector<int> newpos;
+    int nint = 0, cls = -1;
+  };
+  std::map<std::vector<int>, StarShape> cache;
+
+  StarBuilder(fdm_hexmesh *h_, const Builder &B_) : h(h_), B(B_), vcells(h_->nv) {
+    for (int e = 0; e < h->nc; ++e)
+      for (int k = 0; k < 8; ++k) vcells[h->cells[8 * (size_t)e + k]].push_back(e);
+    h->star_ptr.push_back(0);
+    h->pat_ptr.push_back(0);
+    h->pat_colptr.push_back(0);
+  }
+
+  void push_star(int v, const std::vector<int64_t> &order, int nint) {
+    h->star_vertex.push_back(v);
+    for (int64_t g : order) h->star_nodes.push_back((int32_t)g);
+    h->star_ptr.push_back((int64_t)h->star_nodes.size());
+    h->star_nint.push_back(nint);
+  }
+
+  // the surrogate pattern of the star in the given order: FDM functions c1, c2
+  // of a star cell couple iff for some axis a, Af couples them along a and Bf
+  // along the other two axes.  An entity's FDM functions use the slots of its
+  // nodes, so the star's functions are those whose slot is a star node.
+  std::vector<std::vector<int>> surrogate_pattern(int v, const std::vector<int64_t> &order) const {
+    const int n = h->n, n3 = n * n * n;
+    std::map<int64_t, int> in_star;
+    for (size_t k = 0; k < order.size(); ++k) in_star[order[k]] = (int)k;
+    std::vector<std::vector<int>> rows(order.size());
+    for (int e : vcells[v]) {
+      std::vector<std::pair<int, int>> loc;  // (cell-local FDM index, star position)
+      for (int c = 0; c < n3; ++c) {
+        auto it = in_star.find(h->cell_fdm[(size_t)e * n3 + c]);
+        if (it != in_star.end()) loc.push_back({c, it->second});
+      }
+      for (auto &x : loc)
+        for (auto &y : loc) {
+          const int a[3] = {x.first % n, (x.first / n) % n, x.first / (n * n)};
+          const int b[3] = {y.first % n, (y.first / n) % n, y.first / (n * n)};
+          bool nz = false;
+          for (int d = 0; d < 3 && !nz; ++d) {
+            bool term = B.Af[a[d] * n + b[d]] != 0.0;
+            for (int o = 0; o < 3 && term; ++o)
+              if (o != d) term = B.Bf[a[o] * n + b[o]] != 0.0;
+            nz = term;
+          }
+          if (nz) rows[x.second].push_back(y.second);
+        }
+    }
+    for (auto &r : rows) {
+      std::sort(r.begin(), r.end());
+      r.erase(std::unique(r.begin(), r.end()), r.end());
+    }
+    return rows;
+  }
+
+  // reorders the interface by minimum degree over the star's entities in the
+  // pattern of S_G; returns the new position of every old position
+  std::vector<int> interface_order(const std::vector<int64_t> &order, const std::vector<std::vector<int>> &rows,
+                                   int nint) const {
+    const int ns = (int)order.size();
+    std::map<int64_t, int> gid_of;
+    std::vector<int> group_of(ns - nint);
+    for (int r = nint; r < ns; ++r) {
+      const int64_t ent = B.entity[order[r]];
+      auto it = gid_of.find(ent);
+      if (it == gid_of.end()) it = gid_of.emplace(ent, (int)gid_of.size()).first;
+      group_of[r - nint] = it->second;  // groups numbered in the canonical order
+    }
+    const std::vector<int> elim = entity_minimum_degree(schur_pattern(rows, nint), group_of, (int)gid_of.size());
+    std::vector<int> newpos(ns);
+    for (int r = 0; r < nint; ++r) newpos[r] = r;
+    for (int k = 0; k < (int)elim.size(); ++k) newpos[nint + elim[k]] = nint + k;
+    return newpos;
+  }
+
+  // a new class: the symbolic factorisation of S_G (L form) and the
+  // Schur-coupling split (the top block T a suffix of whole entities of the
+  // interface order, chosen to minimise nnz(L_BB) + nnz(S_TB) + t (t + 1) / 2)
+  void add_class(const std::vector<int64_t> &order, const std::vector<std::vector<int>> &rows, int nint) {
+    const int ns = (int)order.size(), nG = ns - nint;
+    h->class_star.push_back((int32_t)h->star_vertex.size() - 1);
+    const std::vector<std::vector<int>> Sg = schur_pattern(rows, nint);
+    std::vector<std::vector<int>> Lrows;
+    std::vector<int> parent;
+    symbolic_cholesky(Sg, Lrows, parent);
+    if (h->fill_ptr.empty()) {
+      h->fill_ptr.push_back(0);
+      h->fill_colptr.push_back(0);
+      h->etree_ptr.push_back(0);
+      h->sc_ptr.push_back(0);
+      h->sc_colptr.push_back(0);
+    }
+    h->class_nnzl.push_back(append_csr(Lrows, h->fill_rowptr, h->fill_cols));
+    h->fill_ptr.push_back((int64_t)h->fill_rowptr.size());
+    h->fill_colptr.push_back((int64_t)h->fill_cols.size());
+    h->etree.insert(h->etree.end(), parent.begin(), parent.end());
+    h->etree_ptr.push_back((int64_t)h->etree.size());
+    std::vector<int> cand{0};
+    for (int i = nG - 1; i >= 1; --i)
+      if (B.entity[order[nint + i]] != B.entity[order[nint + i - 1]]) cand.push_back(nG - i);
+    if (nG > 0) cand.push_back(nG);
+    int64_t best = -1;
+    int best_t = 0;
+    std::vector<std::vector<int>> best_L, best_TB;
+    for (int t : cand) {
+      const int nB = nG - t;
+      std::vector<std::vector<int>> SB(nB), TB(t);
+      int64_t ntb = 0;
+      for (int r = 0; r < nG; ++r)
+        for (int c : Sg[r]) {
+          if (c >= nB) continue;
+          if (r < nB) SB[r].push_back(c);
+          else {
+            TB[r - nB].push_back(c);
+            ++ntb;
+          }
+        }
+      std::vector<std::vector<int>> Lb;
+      std::vector<int> pb;
+      symbolic_cholesky(SB, Lb, pb);
+      int64_t nl = 0;
+      for (auto &x : Lb) nl += (int64_t)x.size();
+      const int64_t cost = nl + ntb + (int64_t)t * (t + 1) / 2;
+      if (best < 0 || cost < best) {
+        best = cost;
+        best_t = t;
+        best_L.swap(Lb);
+        best_TB.swap(TB);
+      }
+    }
+    h->sc_t.push_back(best_t);
+    append_csr(best_L, h->sc_rowptr, h->sc_cols);
+    append_csr(best_TB, h->sc_rowptr, h->sc_cols);
+    h->sc_ptr.push_back((int64_t)h->sc_rowptr.size());
+    h->sc_colptr.push_back((int64_t)h->sc_cols.size());
+  }
+
+  void add_star(int v) {
+    if (vcells[v].empty()) return;
+    int nint = 0;
+    std::vector<int> enc;
+    std::vector<int64_t> order = B.canonical_star(v, vcells[v], h->cell_fdm, h->dirichlet, nint, enc);
+    if (order.empty()) return;
+    const int ns = (int)order.size();
+    auto hit = cache.find(enc);
+    if (hit != cache.end()) {  // a configuration seen before: its pattern, interface order and class
+      const StarShape &sh = hit->second;
+      if ((int)sh.newpos.size() != ns || sh.nint != nint)
+        fdm::fail(FDM_EINVAL, "fdm_hexmesh_create: inconsistent star configuration");
+      std::vector<int64_t> order2(ns);
+      for (int r = 0; r < ns; ++r) order2[sh.newpos[r]] = order[r];
+      push_star(v, order2, nint);
+      // the pattern of the class's first star (copied out first: the vectors grow)
+      const int k0 = h->class_star[sh.cls];
+      const std::vector<int64_t> rp0(h->pat_rowptr.begin() + h->pat_ptr[k0],
+                                     h->pat_rowptr.begin() + h->pat_ptr[k0] + ns + 1);
+      const std::vector<int32_t> c0(h->pat_cols.begin() + h->pat_colptr[k0],
+                                    h->pat_cols.begin() + h->pat_colptr[k0] + rp0[ns]);
+      h->pat_rowptr.insert(h->pat_rowptr.end(), rp0.begin(), rp0.end());
+      h->pat_cols.insert(h->pat_cols.end(), c0.begin(), c0.end());
+      h->pat_ptr.push_back((int64_t)h->pat_rowptr.size());
+      h->pat_colptr.push_back((int64_t)h->pat_cols.size());
+      h->star_class.push_back(sh.cls);
+      return;
+    }
+    const std::vector<std::vector<int>> rows0 = surrogate_pattern(v, order);
+    for (int r = 0; r < nint; ++r)
+      for (int c : rows0[r])
+        if (c < nint && c != r) fdm::fail(FDM_EINVAL, "fdm_hexmesh_create: interior block of a star is not diagonal");
+    StarShape shape;
+    shape.nint = nint;
+    shape.newpos = interface_order(order, rows0, nint);
+    std::vector<int64_t> order2(ns);
+    std::vector<std::vector<int>> rows(ns);
+    for (int r = 0; r < ns; ++r) {
+      order2[shape.newpos[r]] = order[r];
+      for (int c : rows0[r]) rows[shape.newpos[r]].push_back(shape.newpos[c]);
+    }
+    for (auto &r : rows) std::sort(r.begin(), r.end());
+    push_star(v, order2, nint);
+    append_csr(rows, h->pat_rowptr, h->pat_cols);
+    h->pat_ptr.push_back((int64_t)h->pat_rowptr.size());
+    h->pat_colptr.push_back((int64_t)h->pat_cols.size());
+    // the class: stars with equal patterns and interior counts share the
+    // symbolic factorisation of their interface Schur complement
+    std::vector<int> key{ns, nint};
+    for (auto &r : rows) {
+      key.push_back((int)r.size());
+      key.insert(key.end(), r.begin(), r.end());
+    }
+    auto found = classes.find(key);
+    if (found != classes.end()) shape.cls = found->second;
+    else {
+      shape.cls = (int)h->class_star.size();
+      classes.emplace(std::move(key), shape.cls);
+    }
+    h->star_class.push_back(shape.cls);
+    if (found == classes.end()) add_class(order2, rows, nint);
+    cache.emplace(std::move(enc), std::move(shape));
+  }
+};
+
+// CSR of the inverse of a map l -> target[l] (targets in [0, N)), sources by l
+void invert_map(const std::vector<int32_t> &target, int64_t N, std::vector<int64_t> &ptr, std::vector<int32_t> &src) {
+  ptr.assign(N + 1, 0);
+  for (int32_t g : target) ++ptr[g + 1];
+  for (int64_t g = 0; g < N; ++g) ptr[g + 1] += ptr[g];
+  src.resize(target.size());
+  std::vector<int64_t> at(ptr.begin(), ptr.end() - 1);
+  for (size_t l = 0; l < target.size(); ++l) src[at[target[l]]++] = (int32_t)l;
+}
+
+// the inverse maps of the apply: FDM slot -> cell copies, FDM slot -> (star,
+// position), node -> cell copies and its owner (the lowest cell)
+void build_inverse_maps(fdm_hexmesh *h) {
+  const int64_t N = h->nnode;
+  invert_map(h->cell_fdm, N, h->slot_cells_ptr, h->slot_cells);
+  invert_map(h->cell_nodes, N, h->node_cells_ptr, h->node_cells);
+  h->node_owner.assign(N, -1);
+  for (int64_t g = 0; g < N; ++g)
+    if (h->node_cells_ptr[g + 1] > h->node_cells_ptr[g]) h->node_owner[g] = h->node_cells[h->node_cells_ptr[g]];
+  const int nstar = (int)h->star_vertex.size();
+  h->slot_stars_ptr.assign(N + 1, 0);
+  for (int k = 0; k < nstar; ++k)
+    for (int64_t t = h->star_ptr[k]; t < h->star_ptr[k + 1]; ++t) ++h->slot_stars_ptr[h->star_nodes[t] + 1];
+  for (int64_t g = 0; g < N; ++g) h->slot_stars_ptr[g + 1] += h->slot_stars_ptr[g];
+  h->slot_stars.resize(2 * (size_t)h->slot_stars_ptr[N]);
+  std::vector<int64_t> sp(h->slot_stars_ptr.begin(), h->slot_stars_ptr.end() - 1);
+  for (int k = 0; k < nstar; ++k)
+    for (int64_t t = h->star_ptr[k]; t < h->star_ptr[k + 1]; ++t) {
+      const int64_t at = sp[h->star_nodes[t]]++;
+      h->slot_stars[2 * at] = k;
+      h->slot_stars[2 * at + 1] = (int32_t)(t - h->star_ptr[k]);
+    }
+}
+
 }  // namespace
 
 extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_hexmesh **out) {
@@ -503,336 +840,24 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
   }
   fdm_hexmesh *h = new fdm_hexmesh();
   try {
-    const int n = p + 1, n3 = n * n * n, m = p - 1;
     h->p = p;
-    h->n = n;
+    h->n = p + 1;
     h->nv = nv;
     h->nc = nc;
-    Builder B{p, n, nv, nc, cells, {}, {}, {}, {}, {}, {}, {}, {}, {}, 0};
-    const fdm::Basis1D basis = fdm::make_basis(p);
-    B.Af = basis.Af;
-    B.Bf = basis.Bf;
-    B.parity.resize(std::max(m, 0));
-    for (int j = 0; j < m; ++j) {
-      double even = 0.0, odd = 0.0, scale = 0.0;
-      for (int i = 0; i < m; ++i) {
-        const double a = basis.S[i * m + j], b = basis.S[(m - 1 - i) * m + j];
-        even = std::max(even, std::fabs(a - b));
-        odd = std::max(odd, std::fabs(a + b));
-        scale = std::max(scale, std::fabs(a));
-      }
-      if (even <= 1e-10 * scale) B.parity[j] = 1;
-      else if (odd <= 1e-10 * scale) B.parity[j] = -1;
-      else fdm::fail(FDM_EINVAL, "fdm_hexmesh_create: an interior FDM function is neither even nor odd");
-    }
-    B.number();
-    h->nnode = B.nnode;
     h->cells.assign(cells, cells + 8 * (size_t)nc);
+    const fdm::Basis1D basis = fdm::make_basis(p);
     h->Af = basis.Af;
     h->Bf = basis.Bf;
     h->xq = basis.xq;
     h->wq = basis.wq;
-    h->cell_nodes.resize((size_t)nc * n3);
-    h->cell_fdm.resize((size_t)nc * n3);
-    h->cell_sign.resize((size_t)nc * n3);
-    for (int e = 0; e < nc; ++e)
-      for (int k = 0; k < n; ++k)
-        for (int j = 0; j < n; ++j)
-          for (int i = 0; i < n; ++i) {
-            const int idx[3] = {i, j, k};
-            int64_t node, fn;
-            int sign;
-            B.map_local(e, idx, node, fn, sign);
-            const size_t l = (size_t)e * n3 + i + n * (j + n * k);
-            h->cell_nodes[l] = (int32_t)node;
-            h->cell_fdm[l] = (int32_t)fn;
-            h->cell_sign[l] = (int8_t)sign;
-          }
-    // Dirichlet: the closure of every face that belongs to one cell
-    h->dirichlet.assign(B.nnode, 0);
-    for (int e = 0; e < nc; ++e)
-      for (int d = 0; d < 3; ++d)
-        for (int s = 0; s < 2; ++s) {
-          if (B.fcount.at(Builder::face_key(B.face_corners(e, d, s))) != 1) continue;
-          for (int k = 0; k < n; ++k)
-            for (int j = 0; j < n; ++j)
-              for (int i = 0; i < n; ++i) {
-                const int idx[3] = {i, j, k};
-                if (idx[d] == (s ? p : 0)) h->dirichlet[h->cell_nodes[(size_t)e * n3 + i + n * (j + n * k)]] = 1;
-              }
-        }
-    // stars: per used vertex, the free FDM functions of the entities that
-    // contain it, in the star's canonical order (cell interiors first)
-    std::vector<std::vector<int>> vcells(nv);
-    for (int e = 0; e < nc; ++e)
-      for (int k = 0; k < 8; ++k) vcells[cells[8 * e + k]].push_back(e);
-    std::map<std::vector<int>, int> classes;
-    // per canonical configuration: the interface permutation, the interior count and the class
-    struct StarShape {
-      std::vector<int> newpos;
-      int nint = 0, cls = -1;
-    };
-    std::map<std::vector<int>, StarShape> star_cache;
-    h->star_ptr.push_back(0);
-    h->pat_ptr.push_back(0);
-    h->pat_colptr.push_back(0);
-    for (int v = 0; v < nv; ++v) {
-      if (vcells[v].empty()) continue;
-      int nint = 0;
-      std::vector<int> enc;
-      std::vector<int64_t> order = B.canonical_star(v, vcells[v], h->cell_fdm, h->dirichlet, nint, enc);
-      if (order.empty()) continue;
-      const int ns = (int)order.size();
-      // a configuration seen before: its pattern, interface order and class
-      auto hit = star_cache.find(enc);
-      if (hit != star_cache.end()) {
-        const StarShape &sh = hit->second;
-        if ((int)sh.newpos.size() != ns || sh.nint != nint)
-          fdm::fail(FDM_EINVAL, "fdm_hexmesh_create: inconsistent star configuration");
-        std::vector<int64_t> order2(ns);
-        for (int r = 0; r < ns; ++r) order2[sh.newpos[r]] = order[r];
-        h->star_vertex.push_back(v);
-        for (int64_t g : order2) h->star_nodes.push_back((int32_t)g);
-        h->star_ptr.push_back((int64_t)h->star_nodes.size());
-        // the pattern of the class's first star (copied out first: the vectors grow)
-        const int k0 = h->class_star[sh.cls];
-        const std::vector<int64_t> rp0(h->pat_rowptr.begin() + h->pat_ptr[k0],
-                                       h->pat_rowptr.begin() + h->pat_ptr[k0] + ns + 1);
-        const std::vector<int32_t> c0(h->pat_cols.begin() + h->pat_colptr[k0],
-                                      h->pat_cols.begin() + h->pat_colptr[k0] + rp0[ns]);
-        h->pat_rowptr.insert(h->pat_rowptr.end(), rp0.begin(), rp0.end());
-        h->pat_cols.insert(h->pat_cols.end(), c0.begin(), c0.end());
-        h->pat_ptr.push_back((int64_t)h->pat_rowptr.size());
-        h->pat_colptr.push_back((int64_t)h->pat_cols.size());
-        h->star_nint.push_back(nint);
-        h->star_class.push_back(sh.cls);
-        continue;
-      }
-      StarShape shape;
-      std::map<int64_t, int> in_star;
-      for (size_t k = 0; k < order.size(); ++k) in_star[order[k]] = (int)k;
-      // the surrogate pattern: FDM functions c1, c2 of a star cell couple iff for
-      // some axis a, Af couples them along a and Bf along the other two axes
-      std::vector<std::vector<int>> rows(ns);
-      for (int e : vcells[v]) {
-        // (cell-local FDM index, star position): an entity's FDM functions use the
-        // slots of its nodes, so the star's functions are those whose slot is a star node
-        std::vector<std::pair<int, int>> loc;
-        for (int c = 0; c < n3; ++c) {
-          auto it = in_star.find(h->cell_fdm[(size_t)e * n3 + c]);
-          if (it != in_star.end()) loc.push_back({c, it->second});
-        }
-        for (auto &x : loc)
-          for (auto &y : loc) {
-            const int a[3] = {x.first % n, (x.first / n) % n, x.first / (n * n)};
-            const int b[3] = {y.first % n, (y.first / n) % n, y.first / (n * n)};
-            bool nz = false;
-            for (int d = 0; d < 3 && !nz; ++d) {
-              bool term = B.Af[a[d] * n + b[d]] != 0.0;
-              for (int o = 0; o < 3 && term; ++o)
-                if (o != d) term = B.Bf[a[o] * n + b[o]] != 0.0;
-              nz = term;
-            }
-            if (nz) rows[x.second].push_back(y.second);
-          }
-      }
-      for (auto &r : rows) {
-        std::sort(r.begin(), r.end());
-        r.erase(std::unique(r.begin(), r.end()), r.end());
-      }
-      for (int r = 0; r < nint; ++r)
-        for (int c : rows[r])
-          if (c < nint && c != r) fdm::fail(FDM_EINVAL, "fdm_hexmesh_create: interior block of a star is not diagonal");
-      // the interface order: minimum degree over the star's entities in the
-      // pattern of the interface Schur complement S_G = A_GG - A_GI D^{-1} A_IG
-      auto schur_pattern = [&](const std::vector<std::vector<int>> &R) {
-        std::vector<std::vector<int>> Sg(ns - nint);
-        for (int r = nint; r < ns; ++r) {
-          std::vector<int> &o = Sg[r - nint];
-          for (int c : R[r]) {
-            if (c >= nint) o.push_back(c - nint);
-            else
-              for (int c2 : R[c])
-                if (c2 >= nint) o.push_back(c2 - nint);
-          }
-          std::sort(o.begin(), o.end());
-          o.erase(std::unique(o.begin(), o.end()), o.end());
-        }
-        return Sg;
-      };
-      {
-        const std::vector<std::vector<int>> S0 = schur_pattern(rows);
-        std::map<int64_t, int> gid_of;
-        std::vector<int> group_of(ns - nint);
-        for (int r = nint; r < ns; ++r) {
-          const int64_t ent = B.entity[order[r]];
-          auto it = gid_of.find(ent);
-          if (it == gid_of.end()) it = gid_of.emplace(ent, (int)gid_of.size()).first;
-          group_of[r - nint] = it->second;
-        }
-        // groups numbered in the default order (faces, edges, vertex by node number)
-        const std::vector<int> elim = entity_minimum_degree(S0, group_of, (int)gid_of.size());
-        std::vector<int> newpos(ns);
-        for (int r = 0; r < nint; ++r) newpos[r] = r;
-        for (int k = 0; k < (int)elim.size(); ++k) newpos[nint + elim[k]] = nint + k;
-        std::vector<int64_t> order2(ns);
-        std::vector<std::vector<int>> rows2(ns);
-        for (int r = 0; r < ns; ++r) {
-          order2[newpos[r]] = order[r];
-          for (int c : rows[r]) rows2[newpos[r]].push_back(newpos[c]);
-        }
-        for (auto &r : rows2) std::sort(r.begin(), r.end());
-        order.swap(order2);
-        rows.swap(rows2);
-        shape.newpos.swap(newpos);
-        shape.nint = nint;
-      }
-      h->star_vertex.push_back(v);
-      for (int64_t g : order) h->star_nodes.push_back((int32_t)g);
-      h->star_ptr.push_back((int64_t)h->star_nodes.size());
-      h->pat_rowptr.push_back(0);
-      int64_t cnt = 0;
-      for (auto &r : rows) {
-        for (int c : r) h->pat_cols.push_back(c);
-        cnt += (int64_t)r.size();
-        h->pat_rowptr.push_back(cnt);
-      }
-      h->pat_ptr.push_back((int64_t)h->pat_rowptr.size());
-      h->pat_colptr.push_back((int64_t)h->pat_cols.size());
-      h->star_nint.push_back(nint);
-      // the class: stars with equal patterns and interior counts share the
-      // symbolic factorisation of their interface Schur complement
-      std::vector<int> key;
-      key.push_back(ns);
-      key.push_back(nint);
-      for (auto &r : rows) {
-        key.push_back((int)r.size());
-        key.insert(key.end(), r.begin(), r.end());
-      }
-      auto found = classes.find(key);
-      if (found != classes.end()) {
-        h->star_class.push_back(found->second);
-        shape.cls = found->second;
-        star_cache.emplace(std::move(enc), std::move(shape));
-        continue;
-      }
-      const int cls = (int)h->class_star.size();
-      classes.emplace(std::move(key), cls);
-      shape.cls = cls;
-      star_cache.emplace(std::move(enc), std::move(shape));
-      h->star_class.push_back(cls);
-      h->class_star.push_back((int32_t)h->star_vertex.size() - 1);
-      // pattern of S_G: A_GG plus, through every interior function, the
-      // interface functions it couples to (the interior block is diagonal)
-      const std::vector<std::vector<int>> Sg = schur_pattern(rows);
-      std::vector<std::vector<int>> Lrows;
-      std::vector<int> parent;
-      symbolic_cholesky(Sg, Lrows, parent);
-      if (h->fill_ptr.empty()) {
-        h->fill_ptr.push_back(0);
-        h->fill_colptr.push_back(0);
-        h->etree_ptr.push_back(0);
-      }
-      int64_t nnzl = 0;
-      h->fill_rowptr.push_back(0);
-      for (auto &r : Lrows) {
-        h->fill_cols.insert(h->fill_cols.end(), r.begin(), r.end());
-        nnzl += (int64_t)r.size();
-        h->fill_rowptr.push_back(nnzl);
-      }
-      h->fill_ptr.push_back((int64_t)h->fill_rowptr.size());
-      h->fill_colptr.push_back((int64_t)h->fill_cols.size());
-      h->etree.insert(h->etree.end(), parent.begin(), parent.end());
-      h->etree_ptr.push_back((int64_t)h->etree.size());
-      h->class_nnzl.push_back(nnzl);
-      // Schur-coupling split: the top block T is a suffix of the interface
-      // order made of whole entities, chosen to minimise the stored values
-      // nnz(L_BB) + nnz(S_TB) + t (t + 1) / 2
-      {
-        const int nG = ns - nint;
-        std::vector<int> cand{0};
-        for (int i = nG - 1; i >= 1; --i)
-          if (B.entity[order[nint + i]] != B.entity[order[nint + i - 1]]) cand.push_back(nG - i);
-        if (nG > 0) cand.push_back(nG);
-        int64_t best = -1;
-        int best_t = 0;
-        std::vector<std::vector<int>> best_L, best_TB;
-        for (int t : cand) {
-          const int nB = nG - t;
-          std::vector<std::vector<int>> SB(nB), TB(t);
-          int64_t ntb = 0;
-          for (int r = 0; r < nG; ++r)
-            for (int c : Sg[r]) {
-              if (c >= nB) continue;
-              if (r < nB) SB[r].push_back(c);
-              else {
-                TB[r - nB].push_back(c);
-                ++ntb;
-              }
-            }
-          std::vector<std::vector<int>> Lb;
-          std::vector<int> pb;
-          symbolic_cholesky(SB, Lb, pb);
-          int64_t nl = 0;
-          for (auto &x : Lb) nl += (int64_t)x.size();
-          const int64_t cost = nl + ntb + (int64_t)t * (t + 1) / 2;
-          if (best < 0 || cost < best) {
-            best = cost;
-            best_t = t;
-            best_L.swap(Lb);
-            best_TB.swap(TB);
-          }
-        }
-        if (h->sc_ptr.empty()) {
-          h->sc_ptr.push_back(0);
-          h->sc_colptr.push_back(0);
-        }
-        h->sc_t.push_back(best_t);
-        for (auto *part : {&best_L, &best_TB}) {
-          int64_t cnt2 = 0;
-          h->sc_rowptr.push_back(0);
-          for (auto &r : *part) {
-            h->sc_cols.insert(h->sc_cols.end(), r.begin(), r.end());
-            cnt2 += (int64_t)r.size();
-            h->sc_rowptr.push_back(cnt2);
-          }
-        }
-        h->sc_ptr.push_back((int64_t)h->sc_rowptr.size());
-        h->sc_colptr.push_back((int64_t)h->sc_cols.size());
-      }
-    }
-    // inverse maps (counting sort by slot keeps the cell / star order)
-    {
-      const int64_t N = B.nnode;
-      h->slot_cells_ptr.assign(N + 1, 0);
-      for (size_t l = 0; l < h->cell_fdm.size(); ++l) ++h->slot_cells_ptr[h->cell_fdm[l] + 1];
-      for (int64_t g = 0; g < N; ++g) h->slot_cells_ptr[g + 1] += h->slot_cells_ptr[g];
-      h->slot_cells.resize(h->cell_fdm.size());
-      std::vector<int64_t> fillp(h->slot_cells_ptr.begin(), h->slot_cells_ptr.end() - 1);
-      for (size_t l = 0; l < h->cell_fdm.size(); ++l) h->slot_cells[fillp[h->cell_fdm[l]]++] = (int32_t)l;
-      const int nstar = (int)h->star_vertex.size();
-      h->slot_stars_ptr.assign(N + 1, 0);
-      for (int k = 0; k < nstar; ++k)
-        for (int64_t t = h->star_ptr[k]; t < h->star_ptr[k + 1]; ++t) ++h->slot_stars_ptr[h->star_nodes[t] + 1];
-      for (int64_t g = 0; g < N; ++g) h->slot_stars_ptr[g + 1] += h->slot_stars_ptr[g];
-      h->slot_stars.resize(2 * (size_t)h->slot_stars_ptr[N]);
-      std::vector<int64_t> sp(h->slot_stars_ptr.begin(), h->slot_stars_ptr.end() - 1);
-      for (int k = 0; k < nstar; ++k)
-        for (int64_t t = h->star_ptr[k]; t < h->star_ptr[k + 1]; ++t) {
-          const int64_t at = sp[h->star_nodes[t]]++;
-          h->slot_stars[2 * at] = k;
-          h->slot_stars[2 * at + 1] = (int32_t)(t - h->star_ptr[k]);
-        }
-      h->node_owner.assign(N, -1);
-      for (size_t l = 0; l < h->cell_nodes.size(); ++l)
-        if (h->node_owner[h->cell_nodes[l]] < 0) h->node_owner[h->cell_nodes[l]] = (int32_t)l;
-      h->node_cells_ptr.assign(N + 1, 0);
-      for (size_t l = 0; l < h->cell_nodes.size(); ++l) ++h->node_cells_ptr[h->cell_nodes[l] + 1];
-      for (int64_t g = 0; g < N; ++g) h->node_cells_ptr[g + 1] += h->node_cells_ptr[g];
-      h->node_cells.resize(h->cell_nodes.size());
-      std::vector<int64_t> np_(h->node_cells_ptr.begin(), h->node_cells_ptr.end() - 1);
-      for (size_t l = 0; l < h->cell_nodes.size(); ++l) h->node_cells[np_[h->cell_nodes[l]]++] = (int32_t)l;
-    }
+    Builder B{p, p + 1, nv, nc, cells, interior_parities(basis, p), basis.Af, basis.Bf, {}, {}, {}, {}, {}, {}, 0};
+    B.number();
+    h->nnode = B.nnode;
+    build_cell_maps(h, B);
+    mark_dirichlet(h, B);
+    StarBuilder stars(h, B);
+    for (int v = 0; v < nv; ++v) stars.add_star(v);
+    build_inverse_maps(h);
   } catch (const fdm::Error &e) {
     int rc = handle_hex(h, e);
     delete h;
@@ -846,293 +871,291 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
   return FDM_OK;
 }
 
+namespace {
+
+// value and reference gradient of the 8 trilinear corner functions at t
+void trilinear_gradients(const double t[3], double gN[8][3]) {
+  for (int c = 0; c < 8; ++c) {
+    const int a[3] = {c & 1, (c >> 1) & 1, c >> 2};
+    double N[3], dN[3];
+    for (int d = 0; d < 3; ++d) {
+      N[d] = a[d] ? 0.5 * (1.0 + t[d]) : 0.5 * (1.0 - t[d]);
+      dN[d] = a[d] ? 0.5 : -0.5;
+    }
+    gN[c][0] = dN[0] * N[1] * N[2];
+    gN[c][1] = N[0] * dN[1] * N[2];
+    gN[c][2] = N[0] * N[1] * dN[2];
+  }
+}
+
+// in place, the lower triangle of the m x m row-major matrix M becomes its
+// Cholesky factor (right-looking); FDM_ENOTSPD naming `what` for a pivot <= 0
+void dense_cholesky(std::vector<double> &M, int m, const char *what) {
+  for (int j = 0; j < m; ++j) {
+    double &djj = M[(size_t)j * m + j];
+    if (!(djj > 0.0)) fdm::fail(FDM_ENOTSPD, std::string("fdm_hexmesh_factor: ") + what + " pivot <= 0");
+    djj = std::sqrt(djj);
+    for (int i = j + 1; i < m; ++i) M[(size_t)i * m + j] /= djj;
+    for (int c = j + 1; c < m; ++c) {
+      const double lcj = M[(size_t)c * m + j];
+      if (lcj == 0.0) continue;
+      for (int i = c; i < m; ++i) M[(size_t)i * m + c] -= M[(size_t)i * m + j] * lcj;
+    }
+  }
+}
+
+// appends the entries of the factor L (m x m, row-major) in the rows of its
+// symbolic fill; an entry outside the fill above `tol` is an error
+void extract_fill(const std::vector<double> &L, int m, const int64_t *rp, const int32_t *cols, double tol,
+                  std::vector<double> &out, const char *what) {
+  std::vector<char> in_fill((size_t)m * m, 0);
+  for (int r = 0; r < m; ++r)
+    for (int64_t t = rp[r]; t < rp[r + 1]; ++t) {
+      in_fill[(size_t)r * m + cols[t]] = 1;
+      out.push_back(L[(size_t)r * m + cols[t]]);
+    }
+  for (int r = 0; r < m; ++r)
+    for (int c = 0; c < r; ++c)
+      if (!in_fill[(size_t)r * m + c] && std::fabs(L[(size_t)r * m + c]) > tol)
+        fdm::fail(FDM_EINVAL, std::string("fdm_hexmesh_factor: ") + what + " entry outside its symbolic fill");
+}
+
+// the coarse unknowns: the vertices not on a boundary face
+void coarse_vertices(fdm_hexmesh *h) {
+  std::vector<char> bnd(h->nv, 0), used(h->nv, 0);
+  std::map<std::array<int, 4>, int> fc;
+  for (int e = 0; e < h->nc; ++e)
+    for (int d = 0; d < 3; ++d)
+      for (int sd = 0; sd < 2; ++sd) {
+        std::array<int, 4> f{};
+        int t = 0;
+        for (int c = 0; c < 8; ++c)
+          if (((c >> d) & 1) == sd) f[t++] = h->cells[8 * (size_t)e + c];
+        std::sort(f.begin(), f.end());
+        ++fc[f];
+      }
+  for (auto &kv : fc)
+    if (kv.second == 1)
+      for (int v : kv.first) bnd[v] = 1;
+  for (int c : h->cells) used[c] = 1;
+  h->coarse_of.assign(h->nv, -1);
+  int nco = 0;
+  for (int v = 0; v < h->nv; ++v)
+    if (used[v] && !bnd[v]) h->coarse_of[v] = nco++;
+  h->coarse.assign((size_t)nco * nco, 0.0);
+}
+
+// per cell and Gauss point G = kappa |det J| J^{-1} J^{-T} of the trilinear map:
+// the averaged surrogate mu_d = (1/8) sum_q w_q G_dd (Section 2.7), the
+// stiffness factors w_q G, and the Q1 Galerkin operator (P^T A P cell by cell
+// is the Q1 stiffness of the same quadrature: the trilinear functions lie in Q_p)
+void cell_geometry(fdm_hexmesh *h, const double *X, const double *kappa_q) {
+  const int q = h->n, q3 = q * q * q, nc = h->nc;
+  const int nco = (int)std::lround(std::sqrt((double)h->coarse.size()));
+  h->mu.assign((size_t)nc * 3, 0.0);
+  h->geom.assign((size_t)nc * q3 * 6, 0.0);
+  for (int e = 0; e < nc; ++e)
+    for (int qz = 0; qz < q; ++qz)
+      for (int qy = 0; qy < q; ++qy)
+        for (int qx = 0; qx < q; ++qx) {
+          const double t[3] = {h->xq[qx], h->xq[qy], h->xq[qz]};
+          double gN[8][3];
+          trilinear_gradients(t, gN);
+          double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+          for (int c = 0; c < 8; ++c) {
+            const double *xv = X + 3 * (size_t)h->cells[8 * (size_t)e + c];
+            for (int i = 0; i < 3; ++i)
+              for (int d = 0; d < 3; ++d) J[i][d] += xv[i] * gN[c][d];
+          }
+          const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                             J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                             J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+          if (!(std::fabs(det) > 0.0)) fdm::fail(FDM_EINVAL, "fdm_hexmesh_factor: degenerate cell geometry");
+          // cofactors: (J^{-1})[d][i] = C[i][d] / det
+          double C[3][3];
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+              const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+              C[i][j] = J[i1][j1] * J[i2][j2] - J[i1][j2] * J[i2][j1];
+            }
+          const int qi = qx + q * (qy + q * qz);
+          const double kap = kappa_q ? kappa_q[(size_t)e * q3 + qi] : 1.0;
+          const double w = h->wq[qx] * h->wq[qy] * h->wq[qz];
+          double G[3][3];
+          for (int d = 0; d < 3; ++d)
+            for (int f = 0; f < 3; ++f) {
+              double s = 0.0;
+              for (int i = 0; i < 3; ++i) s += C[i][d] * C[i][f];
+              G[d][f] = kap * s / std::fabs(det);
+            }
+          for (int d = 0; d < 3; ++d) h->mu[3 * (size_t)e + d] += w * G[d][d] / 8.0;
+          double *gq = &h->geom[((size_t)e * q3 + qi) * 6];
+          gq[0] = w * G[0][0];
+          gq[1] = w * G[1][1];
+          gq[2] = w * G[2][2];
+          gq[3] = w * G[0][1];
+          gq[4] = w * G[0][2];
+          gq[5] = w * G[1][2];
+          for (int c1 = 0; c1 < 8; ++c1) {
+            const int i1 = h->coarse_of[h->cells[8 * (size_t)e + c1]];
+            if (i1 < 0) continue;
+            for (int c2 = 0; c2 < 8; ++c2) {
+              const int i2 = h->coarse_of[h->cells[8 * (size_t)e + c2]];
+              if (i2 < 0) continue;
+              double s = 0.0;
+              for (int d = 0; d < 3; ++d)
+                for (int f = 0; f < 3; ++f) s += gN[c1][d] * G[d][f] * gN[c2][f];
+              h->coarse[(size_t)i1 * nco + i2] += w * s;
+            }
+          }
+        }
+}
+
+// the surrogate matrix of star k in the FDM basis on the star's pattern (the
+// sum over its cells of sum_d mu_d (A_f along axis d, B_f along the others),
+// with the map's signs): values aligned with the pattern's columns
+std::vector<double> star_matrix(const fdm_hexmesh *h, int k, const std::vector<int> &star_cells) {
+  const int n = h->n, n3 = n * n * n;
+  const int64_t s0 = h->star_ptr[k], ns = h->star_ptr[k + 1] - s0;
+  std::map<int32_t, int> pos;
+  for (int64_t i = 0; i < ns; ++i) pos[h->star_nodes[s0 + i]] = (int)i;
+  const int64_t *rp = h->pat_rowptr.data() + h->pat_ptr[k];
+  const int32_t *cols = h->pat_cols.data() + h->pat_colptr[k];
+  std::vector<double> A(rp[ns], 0.0);
+  for (int e : star_cells) {
+    std::vector<std::array<int, 3>> loc;  // (local FDM index, star position, sign)
+    for (int c = 0; c < n3; ++c) {
+      auto it = pos.find(h->cell_fdm[(size_t)e * n3 + c]);
+      if (it != pos.end()) loc.push_back({c, it->second, h->cell_sign[(size_t)e * n3 + c]});
+    }
+    const double *me = &h->mu[3 * (size_t)e];
+    for (auto &x : loc)
+      for (auto &y : loc) {
+        const int a[3] = {x[0] % n, (x[0] / n) % n, x[0] / (n * n)};
+        const int b[3] = {y[0] % n, (y[0] / n) % n, y[0] / (n * n)};
+        double v = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          double t = me[d] * h->Af[a[d] * n + b[d]];
+          for (int o = 0; o < 3; ++o)
+            if (o != d) t *= h->Bf[a[o] * n + b[o]];
+          v += t;
+        }
+        if (v == 0.0) continue;
+        const int32_t *r0 = cols + rp[x[1]], *r1 = cols + rp[x[1] + 1];
+        const int32_t *f = std::lower_bound(r0, r1, y[1]);
+        if (f == r1 || *f != y[1]) fdm::fail(FDM_EINVAL, "fdm_hexmesh_factor: entry outside the star pattern");
+        A[f - cols] += x[2] * y[2] * v;
+      }
+  }
+  return A;
+}
+
+// star k: interior pivots D, the Cholesky factor of S_G = A_GG - A_GI D^{-1}
+// A_IG in its class's fill (L form), and the Schur-coupling form L_BB, S_TB,
+// W = (S_TT - S_TB S_BB^{-1} S_BT)^{-1}
+void factor_star(fdm_hexmesh *h, int k, const std::vector<int> &star_cells) {
+  const int64_t ns = h->star_ptr[k + 1] - h->star_ptr[k];
+  const int nint = h->star_nint[k], nG = (int)ns - nint;
+  const int64_t *rp = h->pat_rowptr.data() + h->pat_ptr[k];
+  const int32_t *cols = h->pat_cols.data() + h->pat_colptr[k];
+  const std::vector<double> A = star_matrix(h, k, star_cells);
+  for (int i = 0; i < nint; ++i) {
+    const int32_t *f = std::lower_bound(cols + rp[i], cols + rp[i + 1], i);
+    const double d = (f != cols + rp[i + 1] && *f == i) ? A[f - cols] : 0.0;
+    if (!(d > 0.0)) fdm::fail(FDM_ENOTSPD, "fdm_hexmesh_factor: interior pivot <= 0");
+    h->diag.push_back(d);
+  }
+  h->diag_ptr.push_back((int64_t)h->diag.size());
+  // S_G, dense and symmetric
+  std::vector<double> S((size_t)nG * nG, 0.0);
+  for (int r = nint; r < ns; ++r)
+    for (int64_t t = rp[r]; t < rp[r + 1]; ++t)
+      if (cols[t] >= nint) S[(size_t)(r - nint) * nG + (cols[t] - nint)] = A[t];
+  for (int i = 0; i < nint; ++i) {
+    std::vector<std::pair<int, double>> nb;
+    for (int64_t t = rp[i]; t < rp[i + 1]; ++t)
+      if (cols[t] >= nint) nb.push_back({cols[t] - nint, A[t]});
+    const double d = h->diag[h->diag_ptr[k] + i];
+    for (auto &a : nb)
+      for (auto &b : nb) S[(size_t)a.first * nG + b.first] -= a.second * b.second / d;
+  }
+  double smax = 0.0;
+  for (double v : S) smax = std::max(smax, std::fabs(v));
+  const double tol = 1e-10 * std::sqrt(smax);
+  const int cls = h->star_class[k];
+  // the L form
+  std::vector<double> L = S;
+  dense_cholesky(L, nG, "interface");
+  extract_fill(L, nG, h->fill_rowptr.data() + h->fill_ptr[cls], h->fill_cols.data() + h->fill_colptr[cls], tol,
+               h->factor, "factor");
+  h->factor_ptr.push_back((int64_t)h->factor.size());
+  // the Schur-coupling form
+  const int t = h->sc_t[cls], nB = nG - t;
+  const int64_t *rpb = h->sc_rowptr.data() + h->sc_ptr[cls];
+  const int64_t *rpt = rpb + nB + 1;
+  const int32_t *cb = h->sc_cols.data() + h->sc_colptr[cls];
+  const int32_t *ct = cb + rpb[nB];
+  std::vector<double> LB((size_t)nB * nB, 0.0);
+  for (int r = 0; r < nB; ++r)
+    for (int c = 0; c <= r; ++c) LB[(size_t)r * nB + c] = S[(size_t)r * nG + c];
+  dense_cholesky(LB, nB, "lower-block");
+  extract_fill(LB, nB, rpb, cb, tol, h->sc_values, "lower-block");
+  for (int r = 0; r < t; ++r)
+    for (int64_t q2 = rpt[r]; q2 < rpt[r + 1]; ++q2) h->sc_values.push_back(S[(size_t)(nB + r) * nG + ct[q2]]);
+  // Y = L_BB^{-1} S_BT (nB x t), C = S_TT - Y^T Y, W = C^{-1}
+  std::vector<double> Y((size_t)nB * t);
+  for (int j = 0; j < t; ++j)
+    for (int i = 0; i < nB; ++i) {
+      double v = S[(size_t)i * nG + nB + j];
+      for (int l = 0; l < i; ++l) v -= LB[(size_t)i * nB + l] * Y[(size_t)l * t + j];
+      Y[(size_t)i * t + j] = v / LB[(size_t)i * nB + i];
+    }
+  std::vector<double> Cm((size_t)t * t);
+  for (int a = 0; a < t; ++a)
+    for (int b = 0; b < t; ++b) {
+      double v = S[(size_t)(nB + a) * nG + nB + b];
+      for (int i = 0; i < nB; ++i) v -= Y[(size_t)i * t + a] * Y[(size_t)i * t + b];
+      Cm[(size_t)a * t + b] = v;
+    }
+  dense_cholesky(Cm, t, "top-block");
+  std::vector<double> Wm((size_t)t * t), col(t);
+  for (int j = 0; j < t; ++j) {  // W e_j: forward L y = e_j, backward L^T x = y
+    for (int i = 0; i < t; ++i) {
+      double v = (i == j) ? 1.0 : 0.0;
+      for (int l = 0; l < i; ++l) v -= Cm[(size_t)i * t + l] * col[l];
+      col[i] = v / Cm[(size_t)i * t + i];
+    }
+    for (int i = t - 1; i >= 0; --i) {
+      double v = col[i];
+      for (int l = i + 1; l < t; ++l) v -= Cm[(size_t)l * t + i] * Wm[(size_t)l * t + j];
+      Wm[(size_t)i * t + j] = v / Cm[(size_t)i * t + i];
+    }
+  }
+  for (int r = 0; r < t; ++r)
+    for (int c = 0; c <= r; ++c) h->sc_values.push_back(0.5 * (Wm[(size_t)r * t + c] + Wm[(size_t)c * t + r]));
+  h->sc_values_ptr.push_back((int64_t)h->sc_values.size());
+}
+
+}  // namespace
+
 extern "C" int fdm_hexmesh_factor(fdm_hexmesh *h, int nv, const double *X, const double *kappa_q) {
   if (!h || !X || nv != h->nv) {
     if (h) h->err = "fdm_hexmesh_factor: need the mesh's nv vertex coordinates";
     return FDM_EINVAL;
   }
   try {
-    const int p = h->p, n = h->n, n3 = n * n * n, nc = h->nc, q = n, q3 = q * q * q;
-    // ---- averaged surrogate per cell (Section 2.7): mu_d = (1/8) sum_q w_q G_dd,
-    // G = kappa |det J| J^{-1} J^{-T} of the trilinear map at the Gauss points
-    h->mu.assign((size_t)nc * 3, 0.0);
-    h->geom.assign((size_t)nc * q3 * 6, 0.0);
-    // coarse space: the Q1 functions of the vertices not on a boundary face
-    h->coarse_of.assign(h->nv, -1);
-    {
-      std::vector<char> bnd(h->nv, 0), used(h->nv, 0);
-      std::map<std::array<int, 4>, int> fc;
-      for (int e = 0; e < nc; ++e)
-        for (int d = 0; d < 3; ++d)
-          for (int sd = 0; sd < 2; ++sd) {
-            std::array<int, 4> f{};
-            int t = 0;
-            for (int c = 0; c < 8; ++c)
-              if (((c >> d) & 1) == sd) f[t++] = h->cells[8 * (size_t)e + c];
-            std::sort(f.begin(), f.end());
-            ++fc[f];
-          }
-      for (auto &kv : fc)
-        if (kv.second == 1)
-          for (int v : kv.first) bnd[v] = 1;
-      for (int c : h->cells) used[c] = 1;
-      int nco = 0;
-      for (int v = 0; v < h->nv; ++v)
-        if (used[v] && !bnd[v]) h->coarse_of[v] = nco++;
-      h->coarse.assign((size_t)nco * nco, 0.0);
-    }
-    const int nco = (int)std::lround(std::sqrt((double)h->coarse.size()));
-    for (int e = 0; e < nc; ++e)
-      for (int qz = 0; qz < q; ++qz)
-        for (int qy = 0; qy < q; ++qy)
-          for (int qx = 0; qx < q; ++qx) {
-            const double t[3] = {h->xq[qx], h->xq[qy], h->xq[qz]};
-            double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-            for (int c = 0; c < 8; ++c) {
-              const int a[3] = {c & 1, (c >> 1) & 1, c >> 2};
-              double N[3], dN[3];
-              for (int d = 0; d < 3; ++d) {
-                N[d] = a[d] ? 0.5 * (1.0 + t[d]) : 0.5 * (1.0 - t[d]);
-                dN[d] = a[d] ? 0.5 : -0.5;
-              }
-              const double g[3] = {dN[0] * N[1] * N[2], N[0] * dN[1] * N[2], N[0] * N[1] * dN[2]};
-              const double *xv = X + 3 * (size_t)h->cells[8 * (size_t)e + c];
-              for (int i = 0; i < 3; ++i)
-                for (int d = 0; d < 3; ++d) J[i][d] += xv[i] * g[d];
-            }
-            const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
-                               J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
-                               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-            if (!(std::fabs(det) > 0.0)) fdm::fail(FDM_EINVAL, "fdm_hexmesh_factor: degenerate cell geometry");
-            // rows of J^{-1} = columns of the cofactor matrix / det
-            double C[3][3];
-            for (int i = 0; i < 3; ++i)
-              for (int j = 0; j < 3; ++j) {
-                const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
-                C[i][j] = J[i1][j1] * J[i2][j2] - J[i1][j2] * J[i2][j1];
-              }
-            const int qi = qx + q * (qy + q * qz);
-            const double kap = kappa_q ? kappa_q[(size_t)e * q3 + qi] : 1.0;
-            const double w = h->wq[qx] * h->wq[qy] * h->wq[qz];
-            // G[d][f] = kappa |det J| sum_i (J^{-1})[d][i] (J^{-1})[f][i], (J^{-1})[d][i] = C[i][d] / det
-            double G[3][3];
-            for (int d = 0; d < 3; ++d)
-              for (int f = 0; f < 3; ++f) {
-                double s = 0.0;
-                for (int i = 0; i < 3; ++i) s += C[i][d] * C[i][f];
-                G[d][f] = kap * s / std::fabs(det);
-              }
-            for (int d = 0; d < 3; ++d) h->mu[3 * (size_t)e + d] += w * G[d][d] / 8.0;
-            double *gq = &h->geom[((size_t)e * q3 + qi) * 6];
-            gq[0] = w * G[0][0];
-            gq[1] = w * G[1][1];
-            gq[2] = w * G[2][2];
-            gq[3] = w * G[0][1];
-            gq[4] = w * G[0][2];
-            gq[5] = w * G[1][2];
-            // the Q1 Galerkin operator: P^T A P cell by cell is the Q1 stiffness
-            // of the same quadrature (the trilinear functions lie in Q_p)
-            double gN[8][3];
-            for (int c = 0; c < 8; ++c) {
-              const int a[3] = {c & 1, (c >> 1) & 1, c >> 2};
-              double N[3], dN[3];
-              for (int d = 0; d < 3; ++d) {
-                N[d] = a[d] ? 0.5 * (1.0 + t[d]) : 0.5 * (1.0 - t[d]);
-                dN[d] = a[d] ? 0.5 : -0.5;
-              }
-              gN[c][0] = dN[0] * N[1] * N[2];
-              gN[c][1] = N[0] * dN[1] * N[2];
-              gN[c][2] = N[0] * N[1] * dN[2];
-            }
-            for (int c1 = 0; c1 < 8; ++c1) {
-              const int i1 = h->coarse_of[h->cells[8 * (size_t)e + c1]];
-              if (i1 < 0) continue;
-              for (int c2 = 0; c2 < 8; ++c2) {
-                const int i2 = h->coarse_of[h->cells[8 * (size_t)e + c2]];
-                if (i2 < 0) continue;
-                double s = 0.0;
-                for (int d = 0; d < 3; ++d)
-                  for (int f = 0; f < 3; ++f) s += gN[c1][d] * G[d][f] * gN[c2][f];
-                h->coarse[(size_t)i1 * nco + i2] += w * s;
-              }
-            }
-          }
-    // ---- per star: the surrogate matrix in the FDM basis on the star's pattern,
-    // its interior pivots D and the Cholesky factor of S_G in the class's fill
+    coarse_vertices(h);
+    cell_geometry(h, X, kappa_q);
     std::vector<std::vector<int>> vcells(h->nv);
-    for (int e = 0; e < nc; ++e)
+    for (int e = 0; e < h->nc; ++e)
       for (int k = 0; k < 8; ++k) vcells[h->cells[8 * (size_t)e + k]].push_back(e);
-    const int nstar = (int)h->star_vertex.size();
     h->diag_ptr.assign(1, 0);
     h->factor_ptr.assign(1, 0);
+    h->sc_values_ptr.assign(1, 0);
     h->diag.clear();
     h->factor.clear();
-    h->sc_values_ptr.assign(1, 0);
     h->sc_values.clear();
-    for (int k = 0; k < nstar; ++k) {
-      const int64_t s0 = h->star_ptr[k], ns = h->star_ptr[k + 1] - s0;
-      const int nint = h->star_nint[k], nG = (int)ns - nint;
-      std::map<int32_t, int> pos;
-      for (int64_t i = 0; i < ns; ++i) pos[h->star_nodes[s0 + i]] = (int)i;
-      const int64_t *rp = h->pat_rowptr.data() + h->pat_ptr[k];
-      const int32_t *cols = h->pat_cols.data() + h->pat_colptr[k];
-      std::vector<double> A(rp[ns], 0.0);
-      for (int e : vcells[h->star_vertex[k]]) {
-        std::vector<std::array<int, 3>> loc;  // (local FDM index, star position, sign)
-        for (int c = 0; c < n3; ++c) {
-          auto it = pos.find(h->cell_fdm[(size_t)e * n3 + c]);
-          if (it != pos.end()) loc.push_back({c, it->second, h->cell_sign[(size_t)e * n3 + c]});
-        }
-        const double *me = &h->mu[3 * (size_t)e];
-        for (auto &x : loc)
-          for (auto &y : loc) {
-            const int a[3] = {x[0] % n, (x[0] / n) % n, x[0] / (n * n)};
-            const int b[3] = {y[0] % n, (y[0] / n) % n, y[0] / (n * n)};
-            double v = 0.0;
-            for (int d = 0; d < 3; ++d) {
-              double t = me[d] * h->Af[a[d] * n + b[d]];
-              for (int o = 0; o < 3; ++o)
-                if (o != d) t *= h->Bf[a[o] * n + b[o]];
-              v += t;
-            }
-            if (v == 0.0) continue;
-            const int32_t *r0 = cols + rp[x[1]], *r1 = cols + rp[x[1] + 1];
-            const int32_t *f = std::lower_bound(r0, r1, y[1]);
-            if (f == r1 || *f != y[1]) fdm::fail(FDM_EINVAL, "fdm_hexmesh_factor: entry outside the star pattern");
-            A[f - cols] += x[2] * y[2] * v;
-          }
-      }
-      auto entry = [&](int r, int c) {
-        const int32_t *r0 = cols + rp[r], *r1 = cols + rp[r + 1];
-        const int32_t *f = std::lower_bound(r0, r1, c);
-        return (f != r1 && *f == c) ? A[f - cols] : 0.0;
-      };
-      for (int i = 0; i < nint; ++i) {
-        const double d = entry(i, i);
-        if (!(d > 0.0)) fdm::fail(FDM_ENOTSPD, "fdm_hexmesh_factor: interior pivot <= 0");
-        h->diag.push_back(d);
-      }
-      h->diag_ptr.push_back((int64_t)h->diag.size());
-      // S_G = A_GG - A_GI D^{-1} A_IG (dense, lower triangle used)
-      std::vector<double> S((size_t)nG * nG, 0.0);
-      for (int r = nint; r < ns; ++r)
-        for (int64_t t = rp[r]; t < rp[r + 1]; ++t)
-          if (cols[t] >= nint) S[(size_t)(r - nint) * nG + (cols[t] - nint)] = A[t];
-      for (int i = 0; i < nint; ++i) {
-        std::vector<std::pair<int, double>> nb;
-        for (int64_t t = rp[i]; t < rp[i + 1]; ++t)
-          if (cols[t] >= nint) nb.push_back({cols[t] - nint, A[t]});
-        const double d = h->diag[h->diag_ptr[k] + i];
-        for (auto &a : nb)
-          for (auto &b : nb) S[(size_t)a.first * nG + b.first] -= a.second * b.second / d;
-      }
-      const std::vector<double> S0 = S;  // S_G before the factorisation (full, symmetric)
-      // Cholesky (right-looking), then the values in the class's fill pattern;
-      // an entry outside the fill would mean a wrong symbolic factorisation
-      double smax = 0.0;
-      for (double v : S) smax = std::max(smax, std::fabs(v));
-      for (int j = 0; j < nG; ++j) {
-        double &djj = S[(size_t)j * nG + j];
-        if (!(djj > 0.0)) fdm::fail(FDM_ENOTSPD, "fdm_hexmesh_factor: interface pivot <= 0");
-        djj = std::sqrt(djj);
-        for (int i = j + 1; i < nG; ++i) S[(size_t)i * nG + j] /= djj;
-        for (int c = j + 1; c < nG; ++c) {
-          const double lcj = S[(size_t)c * nG + j];
-          if (lcj == 0.0) continue;
-          for (int i = c; i < nG; ++i) S[(size_t)i * nG + c] -= S[(size_t)i * nG + j] * lcj;
-        }
-      }
-      const int cls = h->star_class[k];
-      const int64_t *frp = h->fill_rowptr.data() + h->fill_ptr[cls];
-      const int32_t *fcols = h->fill_cols.data() + h->fill_colptr[cls];
-      std::vector<char> in_fill((size_t)nG * nG, 0);
-      for (int r = 0; r < nG; ++r)
-        for (int64_t t = frp[r]; t < frp[r + 1]; ++t) {
-          in_fill[(size_t)r * nG + fcols[t]] = 1;
-          h->factor.push_back(S[(size_t)r * nG + fcols[t]]);
-        }
-      for (int r = 0; r < nG; ++r)
-        for (int c = 0; c < r; ++c)
-          if (!in_fill[(size_t)r * nG + c] && std::fabs(S[(size_t)r * nG + c]) > 1e-10 * std::sqrt(smax))
-            fdm::fail(FDM_EINVAL, "fdm_hexmesh_factor: factor entry outside the symbolic fill");
-      h->factor_ptr.push_back((int64_t)h->factor.size());
-      // the Schur-coupling form: L_BB, S_TB and W = (S_TT - S_TB S_BB^{-1} S_BT)^{-1}
-      {
-        const int t = h->sc_t[cls], nB = nG - t;
-        const int64_t *rpb = h->sc_rowptr.data() + h->sc_ptr[cls];
-        const int64_t *rpt = rpb + nB + 1;
-        const int32_t *cb = h->sc_cols.data() + h->sc_colptr[cls];
-        const int32_t *ct = cb + rpb[nB];
-        std::vector<double> LB((size_t)nB * nB, 0.0);
-        for (int r = 0; r < nB; ++r)
-          for (int c = 0; c <= r; ++c) LB[(size_t)r * nB + c] = S0[(size_t)r * nG + c];
-        for (int j = 0; j < nB; ++j) {
-          double &djj = LB[(size_t)j * nB + j];
-          if (!(djj > 0.0)) fdm::fail(FDM_ENOTSPD, "fdm_hexmesh_factor: lower-block pivot <= 0");
-          djj = std::sqrt(djj);
-          for (int i = j + 1; i < nB; ++i) LB[(size_t)i * nB + j] /= djj;
-          for (int c = j + 1; c < nB; ++c) {
-            const double lcj = LB[(size_t)c * nB + j];
-            if (lcj == 0.0) continue;
-            for (int i = c; i < nB; ++i) LB[(size_t)i * nB + c] -= LB[(size_t)i * nB + j] * lcj;
-          }
-        }
-        std::vector<char> in_b((size_t)nB * nB, 0);
-        for (int r = 0; r < nB; ++r)
-          for (int64_t q2 = rpb[r]; q2 < rpb[r + 1]; ++q2) {
-            in_b[(size_t)r * nB + cb[q2]] = 1;
-            h->sc_values.push_back(LB[(size_t)r * nB + cb[q2]]);
-          }
-        for (int r = 0; r < nB; ++r)
-          for (int c = 0; c < r; ++c)
-            if (!in_b[(size_t)r * nB + c] && std::fabs(LB[(size_t)r * nB + c]) > 1e-10 * std::sqrt(smax))
-              fdm::fail(FDM_EINVAL, "fdm_hexmesh_factor: lower-block entry outside its symbolic fill");
-        for (int r = 0; r < t; ++r)
-          for (int64_t q2 = rpt[r]; q2 < rpt[r + 1]; ++q2) h->sc_values.push_back(S0[(size_t)(nB + r) * nG + ct[q2]]);
-        // Y = L_BB^{-1} S_BT (nB x t), C = S_TT - Y^T Y, W = C^{-1}
-        std::vector<double> Y((size_t)nB * t);
-        for (int j = 0; j < t; ++j)
-          for (int i = 0; i < nB; ++i) {
-            double v = S0[(size_t)i * nG + nB + j];
-            for (int l = 0; l < i; ++l) v -= LB[(size_t)i * nB + l] * Y[(size_t)l * t + j];
-            Y[(size_t)i * t + j] = v / LB[(size_t)i * nB + i];
-          }
-        std::vector<double> Cm((size_t)t * t);
-        for (int a = 0; a < t; ++a)
-          for (int b2 = 0; b2 < t; ++b2) {
-            double v = S0[(size_t)(nB + a) * nG + nB + b2];
-            for (int i = 0; i < nB; ++i) v -= Y[(size_t)i * t + a] * Y[(size_t)i * t + b2];
-            Cm[(size_t)a * t + b2] = v;
-          }
-        // Cholesky of C, then W = C^{-1} column by column
-        for (int j = 0; j < t; ++j) {
-          double &djj = Cm[(size_t)j * t + j];
-          if (!(djj > 0.0)) fdm::fail(FDM_ENOTSPD, "fdm_hexmesh_factor: top-block pivot <= 0");
-          djj = std::sqrt(djj);
-          for (int i = j + 1; i < t; ++i) Cm[(size_t)i * t + j] /= djj;
-          for (int c = j + 1; c < t; ++c) {
-            const double lcj = Cm[(size_t)c * t + j];
-            for (int i = c; i < t; ++i) Cm[(size_t)i * t + c] -= Cm[(size_t)i * t + j] * lcj;
-          }
-        }
-        std::vector<double> Wm((size_t)t * t), col(t);
-        for (int j = 0; j < t; ++j) {
-          for (int i = 0; i < t; ++i) {  // forward: L y = e_j
-            double v = (i == j) ? 1.0 : 0.0;
-            for (int l = 0; l < i; ++l) v -= Cm[(size_t)i * t + l] * col[l];
-            col[i] = v / Cm[(size_t)i * t + i];
-          }
-          for (int i = t - 1; i >= 0; --i) {  // backward: L^T x = y
-            double v = col[i];
-            for (int l = i + 1; l < t; ++l) v -= Cm[(size_t)l * t + i] * Wm[(size_t)l * t + j];
-            Wm[(size_t)i * t + j] = v / Cm[(size_t)i * t + i];
-          }
-        }
-        for (int r = 0; r < t; ++r)
-          for (int c = 0; c <= r; ++c) h->sc_values.push_back(0.5 * (Wm[(size_t)r * t + c] + Wm[(size_t)c * t + r]));
-        h->sc_values_ptr.push_back((int64_t)h->sc_values.size());
-      }
-    }
+    for (int k = 0; k < (int)h->star_vertex.size(); ++k) factor_star(h, k, vcells[h->star_vertex[k]]);
   } catch (const fdm::Error &e) {
     return handle_hex(h, e);
   }
