@@ -1,11 +1,15 @@
-// Host topology of a conforming hexahedral mesh for the vertex-star
-// relaxation on unstructured meshes (Sections 2.4 and 2.6 applied to general
-// meshes): the Q_p node numbering shared by neighbouring cells of any
-// orientation, the Dirichlet nodes, the vertex stars (cell interiors first, then
-// the interface entities in minimum-degree order), the signed
-// map from each cell's tensor-product FDM functions to the global FDM
-// functions, and the sparsity pattern of every star's separable surrogate
-// matrix in the FDM basis.  Host memory only: no CUDA call.
+// Host set-up of the vertex-star relaxation on a conforming hexahedral mesh
+// of any structure (Sections 2.4-2.7 applied to general meshes).  Topology
+// (fdm_hexmesh_create): the Q_p node numbering shared by neighbouring cells of
+// any orientation, the Dirichlet nodes, the signed map from each cell's
+// tensor-product FDM functions to the global FDM functions, the vertex stars
+// in canonical order (cell interiors first, then the interface entities in
+// minimum-degree order), their separable surrogate patterns, sparsity classes
+// with the symbolic factorisations of the interface Schur complement (L form
+// and Schur-coupling form), and the inverse maps of the apply.  Numeric set-up
+// (fdm_hexmesh_factor): the averaged surrogate and stiffness factors from the
+// trilinear geometry, the Q1 coarse operator, and every star's interior pivots
+// and interface factors.  Host memory only: no CUDA call.
 //
 // Numbering.  Entities: the mesh vertices used by cells, the edges (vertex
 // pairs) and faces (vertex quadruples) of the cells, and the cells.  Nodes
