@@ -1,7 +1,8 @@
 """The N > 1 path of bench.py on the CPU: two ranks over gloo.  Each rank
 reports its own time; both must take the maximum (the slowest rank is the
 job's time) and compute the same whole-job throughput; every rank solves its
-own right-hand side; the reference arm runs on rank 0 only."""
+own right-hand side; the reference arm runs on rank 0 only, and its JSON line
+carries the contract's keys."""
 import os
 import socket
 
@@ -70,3 +71,25 @@ def test_single_process_identity():
     import bench
     assert bench.reduce_max(3.5) == 3.5
     assert bench.job_throughput(1, 10, 2, 1000.0) == pytest.approx(20.0)
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference` prints one JSON line with the contract's
+    keys: the oracle's DoF/s on the host cores, its sample, a one-thread
+    measurement, and an e2e block without host-device copies."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "pcg_solve_dofs_per_s" and d["unit"] == "DoF/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert cb["single_core"]["cores"] == 1 and cb["single_core"]["value"] > 0
+    assert d["e2e"] == {"value": d["value"], "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["iterations"] <= 20
