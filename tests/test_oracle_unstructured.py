@@ -27,6 +27,8 @@ against what the mathematics and the structured oracle fix:
 * PCG with the hybrid V(1,1) converges with slowly growing iteration counts
   in p (the trend of the unstructured column of Table 1).
 """
+import os
+
 import numpy as np
 import pytest
 from scipy.spatial import cKDTree
@@ -187,6 +189,13 @@ def test_galerkin_coarse_is_q1_stiffness(mesh, p):
 
 
 def test_pcg_iterations_grow_slowly_in_p(mesh):
+    """Slow growth in p on the unstructured mesh, as the unstructured column of
+    Table 1 shows (tests/golden/table1_unstructured_3d.txt: 17, 22, 25 at
+    p = 3, 7, 15 on the paper's own mesh): the counts stay within the span of
+    the paper's (minus five: the mesh here is smaller) and grow by at most six
+    from p = 2 to p = 4."""
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table1_unstructured_3d.txt")
+    paper = {int(l.split()[0]): int(l.split()[1]) for l in open(golden) if l.strip() and not l.startswith("#")}
     its = []
     for p in (2, 3, 4):
         U = HexProblem(p, *mesh)
@@ -197,4 +206,4 @@ def test_pcg_iterations_grow_slowly_in_p(mesh):
         x, it, conv = U.pcg(b, rtol=1e-8)
         assert conv and np.linalg.norm(b - U.apply(x)) <= 1.5e-8 * np.linalg.norm(b)
         its.append(it)
-    assert max(its) <= 30 and its[-1] - its[0] <= 6, its
+    assert paper[3] - 5 <= min(its) and max(its) <= paper[15] + 5 and its[-1] - its[0] <= 6, its
