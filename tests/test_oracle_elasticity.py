@@ -4,6 +4,8 @@ and a closed-form energy of the independent brute-force assembly, the
 Kronecker operator against that assembly, the SDC blocks against dense
 GLL-basis block-Jacobi Schwarz, PCG against a dense direct solve, and the
 Poisson-ratio dependence that Section 4.1 predicts."""
+import os
+
 import numpy as np
 import pytest
 
@@ -140,7 +142,7 @@ def test_vcycle_symmetric_positive(el):
 def test_iterations_grow_with_lambda(el):
     """Section 4.1: the SDC bound grows like (1 - nu) / (1 - 2 nu); the PCG
     iteration counts grow with lambda at fixed mu = 1 (uniform 4^3 mesh, p = 3,
-    body force -0.02 e_2)."""
+    body force -0.02 e_2), as in Table 3 (tests/golden/table3_elasticity_3d.txt)."""
     xv = np.linspace(0, 1, 5)
     its = []
     for lam in (0.0, 1.0, 10.0, 100.0):
@@ -154,3 +156,9 @@ def test_iterations_grow_with_lambda(el):
         its.append(it)
     assert all(a <= b for a, b in zip(its, its[1:])), its
     assert its[-1] >= 2 * its[0], its
+    # the growth relative to lambda = 0 is that of Table 3 (d = 3, p = 3) within a factor 2
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table3_elasticity_3d.txt")
+    paper = [[int(v) for v in l.split()[1:]] for l in open(golden) if l.strip() and not l.startswith("#")][0]
+    for k in range(1, 4):
+        ratio = (its[k] / its[0]) / (paper[k] / paper[0])
+        assert 0.5 <= ratio <= 2.0, (its, paper)
