@@ -26,6 +26,10 @@ Workload families (stand-ins for the paper's Cartesian Poisson runs, Section
              cell's reference axes reoriented by a random symmetry of the
              cube.  A stand-in for the paper's unstructured meshes (2D base
              meshes extruded with six layers), which are not available.
+* Kershaw-type: the tensor mesh with its y and z grid lines squeezed towards
+             alternating sides in slabs along x (aspect ratios ~0.3 near the
+             corners): an own stand-in for the paper's Kershaw meshes, whose
+             coordinate field is not given.
 """
 import numpy as np
 from numpy.polynomial import legendre as _leg
@@ -362,3 +366,46 @@ def unstructured_hex_mesh(m, nz, seed, jitter=0.2):
     zv[-1] = 1.0
     X, cells = extruded_hex_mesh(V2, quads, zv)
     return X, reorient_cells(cells, seed + 2)
+
+
+def kershaw_like_mesh(n, eps=0.3):
+    """A structured but strongly distorted hexahedral mesh of the unit cube in
+    the spirit of the paper's Kershaw meshes (Section 3): n^3 cells (n a
+    multiple of 2), the grid lines in y and z squeezed towards one side or the
+    other of the cube in alternating slabs along x, so that cells near the
+    corners have aspect ratios of about eps, with a linear blend between
+    neighbouring slabs (the vertices move, the topology stays that of the
+    tensor mesh).  Own construction: the paper's coordinate field is not
+    given.  Returns X, cells."""
+    if n % 2:
+        raise ValueError("n must be even")
+
+    def squeeze(t, left):
+        # piecewise-linear map of [0, 1] onto itself sending 1/2 to eps/(1+eps)
+        # (left) or 1/(1+eps) (right): the cells of one half shrink by eps
+        m = eps / (1.0 + eps) if left else 1.0 / (1.0 + eps)
+        return np.where(t <= 0.5, 2.0 * t * m, m + (2.0 * t - 1.0) * (1.0 - m))
+
+    u = np.linspace(0.0, 1.0, n + 1)
+    X3 = np.zeros((n + 1, n + 1, n + 1, 3))
+    for i, x in enumerate(u):
+        # slab index along x: 3 slabs with alternating squeeze, blended
+        s = min(2.999999, 3.0 * x)
+        k = int(s)
+        w = s - k
+        side = (k % 2 == 0)
+        for j, y in enumerate(u):
+            for l, z in enumerate(u):
+                y0, z0 = squeeze(y, side), squeeze(z, not side)
+                y1, z1 = squeeze(y, not side), squeeze(z, side)
+                blend = 0.5 - 0.5 * np.cos(np.pi * w)
+                X3[l, j, i] = (x, (1 - blend) * y0 + blend * y1 if k < 2 else y0,
+                               (1 - blend) * z0 + blend * z1 if k < 2 else z0)
+    X = X3.reshape(-1, 3)
+    cells = []
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                cells.append([(i + a) + (n + 1) * ((j + b) + (n + 1) * (k + c))
+                              for c in (0, 1) for b in (0, 1) for a in (0, 1)])
+    return X, np.array(cells, dtype=np.int64)

@@ -207,3 +207,45 @@ def test_pcg_iterations_grow_slowly_in_p(mesh):
         assert conv and np.linalg.norm(b - U.apply(x)) <= 1.5e-8 * np.linalg.norm(b)
         its.append(it)
     assert paper[3] - 5 <= min(its) and max(its) <= paper[15] + 5 and its[-1] - its[0] <= 6, its
+
+
+def _corner_jacobians(X, cells):
+    """det J of the trilinear map at the 8 corners of every cell."""
+    out = []
+    for cell in cells:
+        P = X[cell]
+        for c in range(8):
+            a, b, cc = c & 1, (c >> 1) & 1, c >> 2
+            ex = P[(1 - a) + 2 * b + 4 * cc] - P[a + 2 * b + 4 * cc]
+            ey = P[a + 2 * (1 - b) + 4 * cc] - P[a + 2 * b + 4 * cc]
+            ez = P[a + 2 * b + 4 * (1 - cc)] - P[a + 2 * b + 4 * cc]
+            sgn = (1 - 2 * a) * (1 - 2 * b) * (1 - 2 * cc)
+            out.append(sgn * np.linalg.det(np.stack([ex, ey, ez], axis=1)))
+    return np.array(out)
+
+
+def test_kershaw_like_mesh_is_harder():
+    """On a Kershaw-type distorted mesh (a valid mesh: every corner Jacobian
+    positive) the iteration counts grow with p, while on the Cartesian mesh of
+    the same size they stay flat: the trend of Table 1's Kershaw column
+    (tests/golden/table1_kershaw_3d.txt: 54, 98, 131 at p = 3, 7, 15), whose
+    text says the method is not p-robust there."""
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table1_kershaw_3d.txt")
+    paper = {int(l.split()[0]): int(l.split()[1]) for l in open(golden) if l.strip() and not l.startswith("#")}
+    assert paper[3] < paper[7] < paper[15]
+    its = {}
+    for name, (X, cells) in (("cartesian", inputs.tensor_hex_mesh(*inputs.uniform_vertices(6))),
+                             ("kershaw", inputs.kershaw_like_mesh(6, 0.3))):
+        assert _corner_jacobians(X, cells).min() > 0
+        for p in (2, 3):
+            U = HexProblem(p, X, cells)
+            U.setup_patches()
+            U.setup_coarse()
+            U.lanczos_omega(inputs.lanczos_start(U.ndof))
+            b = U.mass_apply(np.ones(U.ndof))
+            x, it, conv = U.pcg(b, maxit=500)
+            assert conv
+            its[name, p] = it
+    assert abs(its["cartesian", 3] - its["cartesian", 2]) <= 1
+    assert its["kershaw", 3] > its["kershaw", 2] >= its["cartesian", 2]
+    assert its["kershaw", 3] >= 1.5 * its["cartesian", 3]
