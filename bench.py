@@ -17,7 +17,6 @@ import argparse
 import hashlib
 import json
 import os
-import re
 import subprocess
 import sys
 import tempfile
@@ -33,8 +32,14 @@ WORKLOAD_TEXT = ("q7_graded16: 16^3 graded hex mesh, Q7, 1,367,631 free dofs, N(
                  "FP32 V(1,1) preconditioner in FP64 PCG, rtol 1e-8")
 RTOL = 1e-8
 MAXIT = 200
-CPU_SAMPLE_N = 10  # CPU-baseline sample: the same family on a 10^3 graded mesh
+CPU_SAMPLE_N = 16  # CPU baseline: the oracle on the benchmark workload itself (16^3 graded, Q7)
 FALLBACK_HBM_GBS = 6800.0
+# DRAM traffic of one launch of the FP32 Schur-coupling patch solve at 16^3
+# graded Q7 (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture,
+# summarised in profiles/patch_solve_q7_graded16.md), valid while the kernel
+# source k_asm.cu has the recorded sha256; null otherwise.
+PROFILED_TRAFFIC = {"kernel_source_sha256": "", "dram_bytes_per_launch": None,
+                    "source": "profiles/patch_solve_q7_graded16.md (one ncu capture, same kernel source)"}
 
 
 def _dist():
@@ -77,18 +82,12 @@ def _peak_hbm():
 
 
 def _traffic_from_profile(kernel_src):
-    """Per-launch DRAM bytes of the patch-solve kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "patch_solve_q7_graded16.md")
-    if not os.path.exists(path):
-        return None
-    txt = open(path).read()
-    m_sha = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
-    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not (m_sha and m_b):
+    """Per-launch DRAM bytes of the patch-solve kernel from the recorded ncu
+    capture, if it was taken on the current kernel source (else None)."""
+    if PROFILED_TRAFFIC["dram_bytes_per_launch"] is None:
         return None
     sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
-    return float(m_b.group(1)) if m_sha.group(1) == sha else None
+    return PROFILED_TRAFFIC["dram_bytes_per_launch"] if sha == PROFILED_TRAFFIC["kernel_source_sha256"] else None
 
 
 class ClockSampler:
@@ -239,8 +238,9 @@ def oracle_single_core(n=6):
             "sample": "the same family on a %d^3 mesh (Q7, %d free dofs), one OpenMP thread" % (n, d["free"])}
 
 
-SAMPLE_TEXT = ("the same problem family (graded tensor mesh, Q7, N(0,1) nodal f, PCG + V(1,1), rtol 1e-8) "
-               "on a %d^3 mesh instead of 16^3; DoF/s = free dofs / solve wall time, set-up excluded" % CPU_SAMPLE_N)
+SAMPLE_TEXT = ("the benchmark workload itself (16^3 graded mesh, Q7, 1,367,631 free dofs, the same b, PCG + "
+               "V(1,1), rtol 1e-8) in the FP64 oracle on all host cores; one step = one full PCG solve; "
+               "DoF/s = free dofs / solve wall time, set-up excluded (reported as setup_s)")
 
 
 def bench_reference(args):
@@ -262,9 +262,11 @@ def bench_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_TEXT, "sample": SAMPLE_TEXT, "iterations": int(np.median(its))},
+            "config": {"workload": WORKLOAD_TEXT, "sample": SAMPLE_TEXT, "same_config": True,
+                       "iterations": int(np.median(its))},
             "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": cpu_cores(), "kind": "oracle",
-                             "sample": SAMPLE_TEXT, "setup_s": setup_s, "single_core": oracle_single_core()},
+                             "sample": SAMPLE_TEXT, "same_config": True, "setup_s": setup_s,
+                             "single_core": oracle_single_core()},
             "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -451,8 +453,9 @@ def bench_gpu(args):
         P, bc, setup_cpu = oracle_problem()
         t, it, conv = run_oracle_solve(P, bc)
         cpu = {"value": _free_dofs(P.N) / t, "unit": "DoF/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": SAMPLE_TEXT, "setup_s": setup_cpu, "iterations": it,
-               "single_core": oracle_single_core()}
+               "sample": SAMPLE_TEXT, "same_config": True, "solve_s": t, "setup_s": setup_cpu,
+               "iterations": it, "single_core": oracle_single_core()}
+        del P
 
     if rank == 0:
         line = {"metric": "pcg_solve_dofs_per_s", "value": value, "unit": "DoF/s", "n_gpus": ws,
@@ -480,6 +483,8 @@ def bench_gpu(args):
                                  tuning[0], "k_patch_solve<float>"),
                              "bound": "hbm", "achieved": achieved, "peak": peak,
                              "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                             "traffic_source": PROFILED_TRAFFIC["source"] if traffic is not None else
+                                               "none: no ncu capture of the current kernel source",
                              "algorithmic_bytes_per_launch": ab["patch32"], "avg_launch_ms": patch_ms,
                              # the same launch time against the bytes the L form of the patch solve
                              # would have to move (the dense L21 block and Z): what the form change bought
@@ -490,6 +495,18 @@ def bench_gpu(args):
                 "kernel_timed_solve_ms": ms_kt,
                 "secondary": secondary,
                 "cpu_baseline": cpu}
+        # the figures the targets rest on, last in the line (kept by a tail of the output)
+        p15 = secondary.get("p15", {})
+        line["targets"] = {
+            "q7": {"mixed_dofs_per_s": value, "fp64_pc_dofs_per_s": secondary.get("fp64_pc_solve_dofs_per_s"),
+                   "mixed_over_fp64": secondary.get("mixed_over_fp64"), "true_rel_residual": rel,
+                   "pc_apply_ms": secondary.get("pc_apply_ms"), "asm_apply_ms": secondary.get("asm_apply_ms"),
+                   "patch_solve_ms": patch_ms, "patch_solve_hbm_frac": achieved / peak},
+            "p15": {k: p15.get(k) for k in ("mixed_solve_dofs_per_s", "fp64_solve_dofs_per_s", "mixed_over_fp64",
+                                              "mixed_true_rel_residual", "pc_apply_ms", "sweep_ms",
+                                              "sweep_hbm_frac_of_measured", "sweep_lform_equivalent_frac")},
+            "p15_sweep_target": "<= 450 us per FP32 sweep, >= 0.5 of measured HBM",
+            "cpu_oracle_same_config_dofs_per_s": cpu["value"] if cpu else None}
         print(json.dumps(line), flush=True)
     ctx.close()
     if ws > 1:
@@ -537,8 +554,22 @@ def bench_p15(dev, fdmpc, inputs, peak):
     e1.record(torch.cuda.current_stream())
     torch.cuda.synchronize()
     pc_ms = e0.elapsed_time(e1) / 10
+    for _ in range(3):
+        ctx.asm_apply(r, z)
+    torch.cuda.synchronize()
+    e0.record(torch.cuda.current_stream())
+    for _ in range(10):
+        ctx.asm_apply(r, z)
+    e1.record(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    sweep_ms = e0.elapsed_time(e1) / 10
     ab = ctx.algo_bytes()
+    # the L form's bytes of one sweep: sum nnz(L_Gamma) plus the same vector and cell terms
+    lform_sweep = ab["lform32"] + (ab["asm32"] - ab["patch32"])
     out = {"workload": "q15_uniform8: 8^3 uniform hex mesh, Q15, %d free dofs, manufactured sine" % free,
+           "sweep_ms": sweep_ms, "sweep_bytes": ab["asm32"], "sweep_lform_bytes": lform_sweep,
+           "sweep_hbm_frac_of_measured": ab["asm32"] / (sweep_ms * 1e-3) / 1e9 / peak,
+           "sweep_lform_equivalent_frac": lform_sweep / (sweep_ms * 1e-3) / 1e9 / peak,
            "mixed_solve_dofs_per_s": free / (ms * 1e-3), "mixed_iterations": info.iterations,
            "mixed_true_rel_residual": info.true_rnorm / info.rnorm0,
            "pc_apply_ms": pc_ms, "pc_apply_gdofs": free / (pc_ms * 1e-3) / 1e9,

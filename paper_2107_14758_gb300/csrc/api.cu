@@ -56,7 +56,8 @@ struct fdm_batch {
   unsigned long long *d_times = nullptr;  // [1 + k] global timer: start, end of each solve
   std::vector<const double *> key_b;
   std::vector<double *> key_x;
-  std::vector<size_t> init_kernels, body_kernels;  // kernel nodes per problem: set-up, one iteration
+  std::vector<size_t> init_kernels, body_kernels, verify_kernels;  // kernel nodes per problem: set-up, one
+                                                                   // iteration, one true-residual check
   double key_rtol = -1.0;
   int key_maxit = -1;
   void release_graph() {
@@ -984,9 +985,12 @@ void autotune_patch(fdm_ctx *c, cudaStream_t st) {
 }
 
 // ---- batched solves: one CUDA graph, a device-driven PCG loop per problem
-// Scalars of a problem in c->sc: [0] r.z, [1] alpha, [2] beta, [3] d.q, [7] flexible beta,
-// [8] non-finite flag, [9] first iteration, [10] rtol^2, [11] maxit, [12] ||b||^2,
+// Scalars of a problem in c->sc: [0] r.z, [1] alpha, [2] beta, [3] d.q, [4] true-residual checks,
+// [7] flexible beta, [8] non-finite flag, [9] first iteration, [10] rtol^2, [11] maxit, [12] ||b||^2,
 // [13] iterations, [14] ||r||^2, [15] converged.  c->dots: [0] r.z, [1] r.z_prev, [2] r.r, [3] d.q.
+// Convergence is declared on the true residual: when the recursive residual
+// meets the test, r is replaced by b - A x (FP64) and the test is repeated on
+// it; if that fails the iteration continues from the replaced residual.
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -1031,23 +1035,41 @@ __global__ void k_bbeta(double *sc, const double *dots) {
   sc[2] = b;
   sc[0] = rz;
 }
-// end of an iteration: stop at ||r||^2 <= rtol^2 ||b||^2, at maxit or on a non-finite value
-__global__ void k_bcheck(double *sc, const double *dots, cudaGraphConditionalHandle h, unsigned long long *tend) {
+// end of an iteration: when the recursive residual meets ||r||^2 <= rtol^2 ||b||^2
+// the true-residual check runs (hv = 1) and decides; otherwise stop at maxit or
+// on a non-finite value
+__global__ void k_bcheck(double *sc, const double *dots, cudaGraphConditionalHandle h,
+                         cudaGraphConditionalHandle hv, unsigned long long *tend) {
   if (threadIdx.x != 0) return;
   const double rr = dots[2];
   const double it = sc[13] + 1.0;
   sc[13] = it;
   sc[14] = rr;
   if (!isfinite(rr)) sc[8] = 1.0;
-  const bool conv = rr <= sc[10] * sc[12];
+  const bool conv = rr <= sc[10] * sc[12] && sc[8] == 0.0;
+  sc[15] = 0.0;
+  const bool stop = it >= sc[11] || sc[8] != 0.0;
+  if (!conv && stop) *tend = global_ns();
+  cudaGraphSetConditional(hv, conv ? 1u : 0u);
+  cudaGraphSetConditional(h, (conv || stop) ? 0u : 1u);
+}
+// after r = b - A x: converged if the true residual meets the test, else
+// continue from it (within maxit)
+__global__ void k_bverify(double *sc, const double *dots, cudaGraphConditionalHandle h, unsigned long long *tend) {
+  if (threadIdx.x != 0) return;
+  const double rr = dots[2];
+  sc[4] += 1.0;
+  sc[14] = rr;
+  if (!isfinite(rr)) sc[8] = 1.0;
+  const bool conv = rr <= sc[10] * sc[12] && sc[8] == 0.0;
   sc[15] = conv ? 1.0 : 0.0;
-  const bool done = conv || it >= sc[11] || sc[8] != 0.0;
+  const bool done = conv || sc[13] >= sc[11] || sc[8] != 0.0;
   if (done) *tend = global_ns();
   cudaGraphSetConditional(h, done ? 0u : 1u);
 }
 
-void capture_iteration(fdm_ctx *c, double *x, cudaGraphConditionalHandle h, unsigned long long *tend,
-                       cudaStream_t st) {
+void capture_iteration(fdm_ctx *c, double *x, cudaGraphConditionalHandle h, cudaGraphConditionalHandle hv,
+                       unsigned long long *tend, cudaStream_t st) {
   const int64_t n = c->g.ndof;
   launch_dot(n, c->r, c->z, c->partial, c->dots + 1, st);  // r . z_prev (flexible beta)
   pc_apply_impl(c, c->r, c->z, st);
@@ -1059,14 +1081,47 @@ void capture_iteration(fdm_ctx *c, double *x, cudaGraphConditionalHandle h, unsi
   launch_pcg_scalars(0, c->sc, c->dots + 3, st);
   launch_pcg_update_xr(n, c->sc, c->d, c->q, x, c->r, st);
   launch_dot(n, c->r, c->r, c->partial, c->dots + 2, st);
-  k_bcheck<<<1, 32, 0, st>>>(c->sc, c->dots, h, tend);
+  k_bcheck<<<1, 32, 0, st>>>(c->sc, c->dots, h, hv, tend);
   FDM_CUDA(cudaGetLastError());
+}
+
+// the true-residual check: r = b - A x (FP64, Dirichlet entries 0), ||r||^2, decide
+void capture_verify(fdm_ctx *c, const double *b, const double *x, cudaGraphConditionalHandle h,
+                    unsigned long long *tend, cudaStream_t st) {
+  const int64_t n = c->g.ndof;
+  apply_op<double>(c, x, c->q, st);
+  launch_sub<double>(n, b, c->q, c->r, st);
+  mask_dirichlet(c->g, c->r, st);
+  launch_dot(n, c->r, c->r, c->partial, c->dots + 2, st);
+  k_bverify<<<1, 32, 0, st>>>(c->sc, c->dots, h, tend);
+  FDM_CUDA(cudaGetLastError());
+}
+
+// the single node of a captured (linear) graph that no other node depends on
+cudaGraphNode_t graph_leaf(cudaGraph_t g) {
+  size_t nn = 0;
+  FDM_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  FDM_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+  cudaGraphNode_t leaf = nullptr;
+  int leaves = 0;
+  for (cudaGraphNode_t v : nodes) {
+    size_t nd = 0;
+    FDM_CUDA(cudaGraphNodeGetDependentNodes(v, nullptr, nullptr, &nd));
+    if (nd == 0) {
+      leaf = v;
+      ++leaves;
+    }
+  }
+  if (leaves != 1) fail(FDM_ECUDA, "captured PCG iteration does not end in a single node");
+  return leaf;
 }
 
 void build_batch_graph(fdm_batch *B, const double *const *bv, double *const *xv, double rtol, int maxit) {
   B->release_graph();
   B->init_kernels.clear();
   B->body_kernels.clear();
+  B->verify_kernels.clear();
   const int k = (int)B->ctxs.size();
   if (!B->cap) FDM_CUDA(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
   if (!B->d_times) FDM_CUDA(cudaMalloc(&B->d_times, sizeof(unsigned long long) * (k + 1)));
@@ -1126,12 +1181,29 @@ void build_batch_graph(fdm_batch *B, const double *const *bv, double *const *xv,
       cp.conditional.size = 1;
       FDM_CUDA(cudaGraphAddNode(&nw, G, &nb, nullptr, 1, &cp));
       cudaGraph_t body = cp.conditional.phGraph_out[0];
+      cudaGraphConditionalHandle hv;
+      FDM_CUDA(cudaGraphConditionalHandleCreate(&hv, body, 0, cudaGraphCondAssignDefault));
       FDM_CUDA(cudaStreamBeginCaptureToGraph(B->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-      capture_iteration(c, xv[i], h, B->d_times + 1 + i, B->cap);
+      capture_iteration(c, xv[i], h, hv, B->d_times + 1 + i, B->cap);
       FDM_CUDA(cudaStreamEndCapture(B->cap, &body));
       size_t nbk = 0;
       FDM_CUDA(cudaGraphGetNodes(body, nullptr, &nbk));
       B->body_kernels.push_back(nbk);
+      // the true-residual check, run when the recursive residual has converged
+      cudaGraphNode_t leaf = graph_leaf(body), nv;
+      cudaGraphNodeParams vp{};
+      vp.type = cudaGraphNodeTypeConditional;
+      vp.conditional.handle = hv;
+      vp.conditional.type = cudaGraphCondTypeIf;
+      vp.conditional.size = 1;
+      FDM_CUDA(cudaGraphAddNode(&nv, body, &leaf, nullptr, 1, &vp));
+      cudaGraph_t vbody = vp.conditional.phGraph_out[0];
+      FDM_CUDA(cudaStreamBeginCaptureToGraph(B->cap, vbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+      capture_verify(c, bv[i], xv[i], h, B->d_times + 1 + i, B->cap);
+      FDM_CUDA(cudaStreamEndCapture(B->cap, &vbody));
+      size_t nvk = 0;
+      FDM_CUDA(cudaGraphGetNodes(vbody, nullptr, &nvk));
+      B->verify_kernels.push_back(nvk);
     } catch (...) {
       c->capturing = false;
       cudaStreamCaptureStatus cs;
@@ -1174,7 +1246,8 @@ int solve_batch(fdm_batch *b, const double *const *bv, double *const *xv, double
       double hsc[16];
       FDM_CUDA(cudaMemcpy(hsc, c->sc, sizeof hsc, cudaMemcpyDeviceToHost));
       // kernels this problem ran inside the graph (the timer kernel counts for the first)
-      c->launches += (int64_t)b->init_kernels[i] + (int64_t)hsc[13] * (int64_t)b->body_kernels[i] + (i == 0);
+      c->launches += (int64_t)b->init_kernels[i] + (int64_t)hsc[13] * (int64_t)b->body_kernels[i] +
+                     (int64_t)hsc[4] * (int64_t)b->verify_kernels[i] + (i == 0);
       int hstat = 0;
       FDM_CUDA(cudaMemcpy(&hstat, c->status, sizeof(int), cudaMemcpyDeviceToHost));
       int rc = FDM_OK;
@@ -1196,15 +1269,19 @@ int solve_batch(fdm_batch *b, const double *const *bv, double *const *xv, double
         f.rnorm0 = std::sqrt(hsc[12]);
         f.rnorm = std::sqrt(hsc[14]);
         f.seconds = hsc[13] > 0 && t[1 + i] > t[0] ? (double)(t[1 + i] - t[0]) * 1e-9 : 0.0;
-        const int64_t n = c->g.ndof;  // true residual ||b - A x||, outside the timed graph
-        launch_operator<double, double, double>(c->op_args(false), false, xv[i], c->q, c->E64, st);
-        launch_sub<double>(n, bv[i], c->q, c->v1, st);
-        mask_dirichlet(c->g, c->v1, st);
-        launch_dot(n, c->v1, c->v1, c->partial, c->dots, st);
-        double h = 0.0;
-        FDM_CUDA(cudaMemcpyAsync(&h, c->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
-        FDM_CUDA(cudaStreamSynchronize(st));
-        f.true_rnorm = std::sqrt(h);
+        if (hsc[15] != 0.0 && hsc[13] > 0) {
+          f.true_rnorm = f.rnorm;  // the converged residual is the true one (checked in the graph)
+        } else {
+          const int64_t n = c->g.ndof;  // true residual ||b - A x||, outside the timed graph
+          launch_operator<double, double, double>(c->op_args(false), false, xv[i], c->q, c->E64, st);
+          launch_sub<double>(n, bv[i], c->q, c->v1, st);
+          mask_dirichlet(c->g, c->v1, st);
+          launch_dot(n, c->v1, c->v1, c->partial, c->dots, st);
+          double h = 0.0;
+          FDM_CUDA(cudaMemcpyAsync(&h, c->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
+          FDM_CUDA(cudaStreamSynchronize(st));
+          f.true_rnorm = std::sqrt(h);
+        }
       }
       if (rc < worst) worst = rc;
     }
@@ -1261,6 +1338,7 @@ namespace fdm {
 // accessors used by other translation units of the library
 OpArgs ctx_op_args64(const fdm_ctx *c) { return c->op_args(false); }
 void ctx_count_launches(fdm_ctx *c, int k) { c->launches += k; }
+int ctx_device(const fdm_ctx *c) { return c->device; }
 int ctx_fail(fdm_ctx *c, int code, const std::string &msg) { return handle(c, Error{code, msg}); }
 void ctx_mask_dirichlet(const Grid &g, double *v, cudaStream_t st) { mask_dirichlet(g, v, st); }
 void ctx_copy(int64_t n, const double *a, double *b, cudaStream_t st) { copy(n, a, b, st); }
@@ -1338,6 +1416,7 @@ int fdm_setup(const fdm_mesh *mesh, int p, const fdm_coeff *coeff, const fdm_opt
   }
   *out = nullptr;
   fdm_ctx *c = new fdm_ctx();
+  cudaGetDevice(&c->device);
   cudaStream_t st = (cudaStream_t)stream;
   try {
     if (opt) c->opt = *opt;
@@ -1492,7 +1571,21 @@ int pcg_solve(fdm_ctx *c, const double *b, double *x, double rtol, int maxit, fd
         FDM_CUDA(cudaStreamSynchronize(st));
         nr = std::sqrt(h[0]);
         if (!std::isfinite(nr)) { bad = 1; break; }
-        if (nr <= rtol * nb) { conv = 1; break; }
+        if (nr <= rtol * nb) {
+          // converged on the recursive residual: replace it by the true one,
+          // r = b - A x, and stop only if that meets the test too
+          apply_op<double>(c, x, c->q, st);
+          launch_sub<double>(n, b, c->q, c->r, st);
+          mask_dirichlet(c->g, c->r, st);
+          launch_dot(n, c->r, c->r, c->partial, c->dots + 2, st);
+          c->launches += 4;
+          FDM_CUDA(cudaMemcpyAsync(h, c->dots + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+          FDM_CUDA(cudaStreamSynchronize(st));
+          nr = std::sqrt(h[0]);
+          if (!std::isfinite(nr)) { bad = 1; break; }
+          if (nr <= rtol * nb) { conv = 1; break; }
+          if (it >= maxit) break;
+        }
         std::swap(z, zold);
         pc_apply_impl(c, c->r, z, st);
         c->tmark(FDM_T_VEC, true, st);

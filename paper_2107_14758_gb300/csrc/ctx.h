@@ -15,6 +15,7 @@ using namespace fdm;
 struct fdm_ctx {
   Grid g{};
   int p = 0;
+  int device = 0;  // the CUDA device current at set-up, which holds all of the context's data
   fdm_options opt{};
   Basis1D basis;
   std::vector<PatchClass> classes;

@@ -429,7 +429,20 @@ int elast_pcg_solve(fdm_elast *e, const double *b, double *x, double rtol, int m
         FDM_CUDA(cudaStreamSynchronize(st));
         nr = std::sqrt(h[0]);
         if (!std::isfinite(nr)) { bad = 1; break; }
-        if (nr <= rtol * nb) { conv = 1; break; }
+        if (nr <= rtol * nb) {
+          // converged on the recursive residual: replace it by the true one,
+          // r = b - A x, and stop only if that meets the test too
+          elast_op<double, double>(e, x, e->r, b, st);
+          mask3(e, e->r, st);
+          launch_dot(n3, e->r, e->r, e->partial, e->dots + 2, st);
+          e->launches += 4;
+          FDM_CUDA(cudaMemcpyAsync(h, e->dots + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+          FDM_CUDA(cudaStreamSynchronize(st));
+          nr = std::sqrt(h[0]);
+          if (!std::isfinite(nr)) { bad = 1; break; }
+          if (nr <= rtol * nb) { conv = 1; break; }
+          if (it >= maxit) break;
+        }
         std::swap(z, zold);
         elast_pc(e, e->r, z, st);
         launch_dot2(n3, e->r, z, zold, e->partial, e->dots, st);

@@ -164,6 +164,7 @@ void launch_coarse_cell_matrices(const OpArgs &a, double *Ac, cudaStream_t st);
 // context accessors (defined with the C-ABI)
 OpArgs ctx_op_args64(const fdm_ctx *c);
 void ctx_count_launches(fdm_ctx *c, int k);
+int ctx_device(const fdm_ctx *c);  // the device that holds the context's data
 int ctx_fail(fdm_ctx *c, int code, const std::string &msg);
 
 // coarse space

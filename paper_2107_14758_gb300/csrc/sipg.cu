@@ -431,7 +431,19 @@ int sipg_pcg_solve(fdm_sipg *s, const double *b, double *x, double rtol, int max
         FDM_CUDA(cudaStreamSynchronize(st));
         nr = std::sqrt(h[0]);
         if (!std::isfinite(nr)) { bad = 1; break; }
-        if (nr <= rtol * nb) { conv = 1; break; }
+        if (nr <= rtol * nb) {
+          // converged on the recursive residual: replace it by the true one,
+          // r = b - A x, and stop only if that meets the test too
+          sipg_op<double, double>(s, x, s->r, b, st);
+          launch_dot(n, s->r, s->r, s->partial, s->dots + 2, st);
+          s->launches += 3;
+          FDM_CUDA(cudaMemcpyAsync(h, s->dots + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+          FDM_CUDA(cudaStreamSynchronize(st));
+          nr = std::sqrt(h[0]);
+          if (!std::isfinite(nr)) { bad = 1; break; }
+          if (nr <= rtol * nb) { conv = 1; break; }
+          if (it >= maxit) break;
+        }
         std::swap(z, zold);
         sipg_pc(s, s->r, z, st);
         launch_dot2(n, s->r, z, zold, s->partial, s->dots, st);

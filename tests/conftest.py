@@ -18,3 +18,4 @@ def oracle_lib():
     import oracle
     oracle.build()
     return oracle
+

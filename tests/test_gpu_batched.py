@@ -5,6 +5,8 @@ and changed calls)."""
 import numpy as np
 import pytest
 
+from tests.record import record  # noqa: E402
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -77,7 +79,8 @@ def test_batched_fp64_matches_oracle():
             xr, it, _, _ = ref.pcg(b.cpu().numpy(), 1e-8, 200)
             assert abs(info.iterations - it) <= 1
             if info.iterations == it:
-                assert np.abs(x.cpu().numpy() - xr).max() <= 1e-10 * np.abs(xr).max()
+                record("batched_fp64", x_relerr=np.abs(x.cpu().numpy() - xr).max() / np.abs(xr).max())
+                assert np.abs(x.cpu().numpy() - xr).max() <= 1e-11 * np.abs(xr).max()
     finally:
         fdmpc.fdm_batch_destroy(batch)
 
@@ -122,8 +125,9 @@ def test_full_batch_workload():
     try:
         xs = [torch.empty_like(b) for b in bs]
         infos = fdmpc.pcg_solve_batched(batch, bs, xs, 1e-8, 300)
+        record("batched_full_worst", true_rel=max(i.true_rnorm / i.rnorm0 for i in infos))
         for info in infos:
-            assert info.converged and info.true_rnorm <= 1.5e-8 * info.rnorm0
+            assert info.converged and info.true_rnorm <= 1e-8 * info.rnorm0
         small = sorted(range(64), key=lambda i: (len(probs[i]["xv"]) - 1) ** 3 * probs[i]["p"] ** 3)[:4]
         for i in small:
             w = probs[i]

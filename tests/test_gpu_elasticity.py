@@ -10,6 +10,8 @@ reaches the FP64 true residual 1e-8.
 import numpy as np
 import pytest
 
+from tests.record import record  # noqa: E402
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -114,7 +116,8 @@ def test_pcg_parity_fp64(el):
     assert abs(info.iterations - it_ref) <= 1
     x2, info2 = gpu.pcg_solve(T(b), rtol=0.0, maxit=it_ref, raise_on_noconv=False)
     assert info2.iterations == it_ref
-    assert relerr(N(x2), x_ref.ravel()) <= 1e-10
+    record("elast_pcg_fp64", x_relerr=relerr(N(x2), x_ref.ravel()), iterations=it_ref)
+    assert relerr(N(x2), x_ref.ravel()) <= 1e-11
 
 
 @pytest.mark.parametrize("lam", [0.0, 1.0, 10.0, 100.0])
@@ -132,7 +135,8 @@ def test_iterations_follow_the_oracle(el, lam):
     mixed = fdmpc.Elasticity(3, xv, xv, xv, 1.0, lam, precision=FP32,
                              lanczos_start=inputs.lanczos_start(3 * ref.N))
     _, im = mixed.pcg_solve(T(b), rtol=1e-8, maxit=500)
-    assert im.converged and im.true_rnorm <= 1.5e-8 * im.rnorm0
+    record("elast_mixed_lam%g" % lam, true_rel=im.true_rnorm / im.rnorm0, iterations=im.iterations)
+    assert im.converged and im.true_rnorm <= 1e-8 * im.rnorm0
     assert im.iterations <= info.iterations + 1
 
 
@@ -146,7 +150,7 @@ def test_mixed_precision_solution(el):
     x_ref, _, conv = ref.pcg(b, rtol=1e-10, maxit=500)
     gpu = fdmpc.Elasticity(4, xv, yv, zv, 1.0, 5.0, precision=FP32)
     x, info = gpu.pcg_solve(T(b), rtol=1e-10, maxit=500)
-    assert info.converged and info.true_rnorm <= 1.5e-10 * info.rnorm0
+    assert info.converged and info.true_rnorm <= 1e-10 * info.rnorm0
     assert relerr(N(x), x_ref.ravel()) <= 1e-7
 
 

@@ -10,6 +10,8 @@ counts; the mixed-precision solve reaches the FP64 true residual 1e-8.
 import numpy as np
 import pytest
 
+from tests.record import record  # noqa: E402
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
@@ -136,7 +138,8 @@ def test_pcg_parity_fp64():
     x, info = ctx.pcg_solve(T(b), rtol=1e-8, maxit=200)
     assert abs(info.iterations - it_ref) <= 1
     x2, info2 = ctx.pcg_solve(T(b), rtol=0.0, maxit=it_ref, raise_on_noconv=False)
-    assert relerr(N(x2), x_ref) <= 1e-10
+    record("gmg_pcg_fp64", x_relerr=relerr(N(x2), x_ref), iterations=it_ref)
+    assert relerr(N(x2), x_ref) <= 1e-11
 
 
 def test_pcg_mixed_precision_and_exact_coarse():
@@ -153,7 +156,7 @@ def test_pcg_mixed_precision_and_exact_coarse():
     _, i0 = exact.pcg_solve(b, rtol=1e-8, maxit=300)
     _, i1 = mg.pcg_solve(b, rtol=1e-8, maxit=300)
     assert i0.converged and i1.converged
-    assert i1.true_rnorm <= 1.5e-8 * i1.rnorm0
+    assert i1.true_rnorm <= 1e-8 * i1.rnorm0
     assert i1.iterations <= i0.iterations + 2
 
 
@@ -179,7 +182,7 @@ def test_mesh_independence_32():
         assert (len(ctx.gmg_levels()) > 1) == (levels != 0)
         b = ctx.mass_apply(T(inputs.normal_rhs(ctx.ndof, 8)))
         _, info = ctx.pcg_solve(b, rtol=1e-8, maxit=300)
-        assert info.converged and info.true_rnorm <= 1.5e-8 * info.rnorm0
+        assert info.converged and info.true_rnorm <= 1e-8 * info.rnorm0
         its.append(info.iterations)
         del ctx
     assert its[1] <= 1.25 * its[0] + 1, its

@@ -1,11 +1,14 @@
 """GPU parity of the CUDA path (through the C-ABI) against the FP64 oracle.
 
 Tolerances: integer/index data (orderings, sparsity patterns) bit-exact;
-FP64 path <= 1e-11 relative (max norm) per operator application; FP32
-preconditioner: <= 1e-4 relative per application (FP32 unit roundoff 6e-8
-times the patch condition growth) and a final PCG residual
-<= 1e-8 relative; PCG iteration counts within +1 of the oracle.
+FP64 path <= 1e-11 relative (max norm) per operator application and for the
+PCG iterates at equal iteration counts; FP32 preconditioner: <= 1e-4 relative
+per application (FP32 unit roundoff 6e-8 times the growth through the patch
+Schur complements, whose condition numbers stay below about 1e2 at p <= 7) and
+a final true residual ||b - A x|| <= 1e-8 ||b|| (PCG declares convergence on
+the true residual); PCG iteration counts within +1 of the oracle.
 """
+from tests.record import record
 import numpy as np
 import pytest
 
@@ -210,11 +213,12 @@ def test_pcg_parity_fp64_manufactured():
     assert conv
     x, info = ctx.pcg_solve(T(b), rtol=1e-8, maxit=100)
     assert abs(info.iterations - it_ref) <= 1
-    assert info.true_rnorm <= 1e-8 * info.rnorm0 * 1.01
+    assert info.true_rnorm <= 1e-8 * info.rnorm0
     # same number of iterations: identical iterates up to rounding
     x2, info2 = ctx.pcg_solve(T(b), rtol=0.0, maxit=it_ref, raise_on_noconv=False)
     assert info2.iterations == it_ref
-    assert relerr(N(x2), x_ref) <= 1e-10
+    record("pcg_fp64_manufactured", x_relerr=relerr(N(x2), x_ref), true_rel=info.true_rnorm / info.rnorm0)
+    assert relerr(N(x2), x_ref) <= 1e-11
     # and the discrete solution approximates the manufactured sine
     u = inputs.manufactured_u(w["xv"], w["yv"], w["zv"], w["p"])
     assert np.abs(N(x) - u).max() < 1e-4
@@ -231,7 +235,8 @@ def test_pcg_parity_fp64_curved():
     x, info = ctx.pcg_solve(T(b), rtol=1e-8, maxit=200)
     assert abs(info.iterations - it_ref) <= 1
     x2, _ = ctx.pcg_solve(T(b), rtol=0.0, maxit=it_ref, raise_on_noconv=False)
-    assert relerr(N(x2), x_ref) <= 1e-10
+    record("pcg_fp64_curved", x_relerr=relerr(N(x2), x_ref), iterations=it_ref)
+    assert relerr(N(x2), x_ref) <= 1e-11
 
 
 @pytest.mark.parametrize("p", [3, 5])
@@ -241,7 +246,9 @@ def test_pcg_mixed_precision(p):
     b = ref.mass_apply(inputs.normal_rhs(ref.ndof, 16))
     x_ref, it_ref, _, _ = ref.pcg(b, rtol=1e-8, maxit=200)
     x, info = ctx.pcg_solve(T(b), rtol=1e-8, maxit=200)
-    assert info.converged and info.true_rnorm <= 1.5e-8 * info.rnorm0
+    record("pcg_mixed_p%d" % p, true_rel=info.true_rnorm / info.rnorm0, x_relerr=relerr(N(x), x_ref),
+           iterations=info.iterations, oracle_iterations=it_ref)
+    assert info.converged and info.true_rnorm <= 1e-8 * info.rnorm0
     assert info.iterations <= it_ref + 1
     # the same discrete solution as the FP64 oracle to the solver tolerance
     assert relerr(N(x), x_ref) <= 1e-6

@@ -151,7 +151,7 @@ def test_learned_surrogate_pcg_parity():
     xr, it, _, _ = ref.pcg(b, 1e-8, 300)
     assert abs(info.iterations - it) <= 1
     if info.iterations == it:
-        assert np.abs(x.cpu().numpy() - xr).max() <= 1e-10 * np.abs(xr).max()
+        assert np.abs(x.cpu().numpy() - xr).max() <= 1e-11 * np.abs(xr).max()
 
 
 def test_trained_network_gain():

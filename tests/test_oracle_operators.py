@@ -379,3 +379,82 @@ def test_pcg_with_gmg_coarse_solve(oracle_lib):
     assert conv0 and conv1
     assert it0 <= it1 <= it0 + 2, (it0, it1)
     assert np.abs(x1 - x0).max() <= 1e-6 * np.abs(x0).max()
+
+
+def _fdm_basis_1d(p):
+    """The 1D FDM basis change T (Sec. 2.4) built independently of the
+    oracle: interior eigenvectors of A_II s = lambda B_II s from scipy's
+    symmetric-definite solver (ascending, B-orthonormal, first interior entry
+    positive), vertex functions B-orthogonal to them."""
+    import scipy.linalg as sla
+    A, B = bf.ref_matrices_exact(p)
+    n = p + 1
+    T = np.eye(n)
+    if p >= 2:
+        I = np.arange(1, p)
+        _, S = sla.eigh(A[np.ix_(I, I)], B[np.ix_(I, I)])
+        S = S * np.where(S[0] < 0, -1.0, 1.0)
+        T[np.ix_(I, I)] = S
+        T[np.ix_(I, [0, p])] = -np.linalg.solve(B[np.ix_(I, I)], B[np.ix_(I, [0, p])])
+    return T
+
+
+def _global_fdm_basis(p, nx, ny, nz):
+    """T_g = T_z (x) T_y (x) T_x over the grid slots: column s is the GLL
+    expansion of the FDM function in slot s (x fastest)."""
+    T = _fdm_basis_1d(p)
+    mats = []
+    for nc in (nx, ny, nz):
+        N = nc * p + 1
+        G = np.zeros((N, N))
+        for c in range(nc):
+            G[c * p + 1:c * p + p, c * p:c * p + p + 1] = T[1:p, :]
+        for v in range(nc + 1):
+            G[v * p, v * p] = 1.0
+        mats.append(G)
+    return np.kron(mats[2], np.kron(mats[1], mats[0]))
+
+
+def _surrogate_jac(mu, q):
+    """Box cells whose Kronecker stiffness has the per-axis coefficients mu
+    (mu_a = L_x L_y L_z / L_a^2 for half-widths L): L = (sqrt(mu_y mu_z),
+    sqrt(mu_x mu_z), sqrt(mu_x mu_y)), one diagonal Jacobian per cell."""
+    mu = np.asarray(mu).reshape(-1, 3)
+    L = np.stack([np.sqrt(mu[:, 1] * mu[:, 2]), np.sqrt(mu[:, 0] * mu[:, 2]), np.sqrt(mu[:, 0] * mu[:, 1])], axis=1)
+    jac = np.zeros((len(mu), q ** 3, 9))
+    jac[:, :, 0], jac[:, :, 4], jac[:, :, 8] = L[:, None, 0], L[:, None, 1], L[:, None, 2]
+    return jac
+
+
+@pytest.mark.parametrize("p,curved", [(2, False), (3, False), (4, False), (2, True), (3, True)])
+def test_patch_matrix_is_basis_transform_of_gll_patch(oracle_lib, p, curved):
+    """Every star's sparse FDM-basis matrix equals T_j^T A_j^GLL T_j, with
+    A_j^GLL the dense GLL-basis matrix of the star's separable surrogate
+    (the operator itself on box cells) assembled from 3D basis gradients and
+    T_j the star's columns of the global FDM basis change (<= 1e-12).  A 3^3
+    mesh has interior, face, edge and corner stars."""
+    n = 3
+    if curved:
+        xv, yv, zv = inputs.uniform_vertices(n)
+        jac, pts = inputs.deformed_jacobians(n, p)
+        P = oracle_lib.Problem(p, xv, yv, zv, jac=jac, kappa=inputs.kappa_field(pts, 3))
+        A = bf.dense_matrix(p, xv, yv, zv, jac=_surrogate_jac(P.get_mu(), p + 1))
+    else:
+        xv, yv, zv = _graded(n, 41)
+        P = oracle_lib.Problem(p, xv, yv, zv)
+        A = bf.dense_matrix(p, xv, yv, zv)
+    free = bf.free_mask(p, n, n, n)
+    A = np.where(np.outer(free, free), A, 0.0)
+    Tg = _global_fdm_basis(p, n, n, n)
+    classes = set()
+    for v in range((n + 1) ** 3):
+        g, _ = P.patch_dofs(v)
+        if len(g) == 0:
+            continue
+        vx, vy, vz = v % (n + 1), (v // (n + 1)) % (n + 1), v // (n + 1) ** 2
+        classes.add(sum(c in (0, n) for c in (vx, vy, vz)))
+        Tj = Tg[:, g]
+        ref = Tj.T @ A @ Tj
+        Aj = P.patch_matrix(v)
+        assert np.abs(Aj - ref).max() <= 1e-12 * np.abs(ref).max(), v
+    assert classes == {0, 1, 2, 3}  # interior, face, edge and corner stars

@@ -4,9 +4,10 @@ device array of the library instead of the context's buffer).
 
 Checked through the C-ABI against stiffness_apply, on two calls in a row (the
 shared array keeps the previous call's contents, which must not leak into the
-next result), and for the rejection of problems beyond the fixed scratch.
-This file is collected last so that a run stopping at its first failure has
-already run every other test.
+next result), on box cells (the Kronecker form) and on curved cells with a
+coefficient (the Gauss-point form), the two cell kernels that write the
+fixed scratch, and for the rejection of problems beyond it.  This file is collected last so that a run stopping
+at its first failure has already run every other test.
 """
 import ctypes
 
@@ -17,20 +18,17 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def _lib_and_ctx(p, xv, yv, zv):
+def _lib_and_ctx(p, xv, yv, zv, **kw):
     import __graft_entry__ as g
     g.build()
     from paper_2107_14758_gb300 import fdmpc
-    ctx = fdmpc.Context(p, xv, yv, zv, precision=fdmpc.FDM_PREC_FP64, omega=1.0)
+    ctx = fdmpc.Context(p, xv, yv, zv, precision=fdmpc.FDM_PREC_FP64, omega=1.0, **kw)
     return fdmpc, fdmpc.load(), ctx
 
 
-def test_noalloc_matches_stiffness_apply_twice():
-    from paper_2107_14758_gb300 import inputs
-    xv, yv, zv = inputs.graded_vertices(4, 31)
-    fdmpc, L, ctx = _lib_and_ctx(5, xv, yv, zv)
+def _twice(fdmpc, L, ctx, seed):
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    gen = torch.Generator(device="cuda:0").manual_seed(7)
+    gen = torch.Generator(device="cuda:0").manual_seed(seed)
     for call in range(2):  # two calls in a row, different inputs
         u = torch.randn(ctx.ndof, dtype=torch.float64, device="cuda:0", generator=gen)
         ref = ctx.stiffness_apply(u)
@@ -41,6 +39,24 @@ def test_noalloc_matches_stiffness_apply_twice():
         a, b = y.cpu().numpy(), ref.cpu().numpy()
         assert np.all(np.isfinite(a))
         assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), call
+
+
+def test_noalloc_matches_stiffness_apply_twice():
+    from paper_2107_14758_gb300 import inputs
+    xv, yv, zv = inputs.graded_vertices(4, 31)
+    fdmpc, L, ctx = _lib_and_ctx(5, xv, yv, zv)
+    _twice(fdmpc, L, ctx, 7)
+    ctx.close()
+
+
+def test_noalloc_curved_cells_with_coefficient():
+    from paper_2107_14758_gb300 import inputs
+    p, n = 3, 3
+    xv, yv, zv = inputs.uniform_vertices(n)
+    jac, pts = inputs.deformed_jacobians(n, p)
+    kap = inputs.kappa_field(pts, 5)
+    fdmpc, L, ctx = _lib_and_ctx(p, xv, yv, zv, jac=jac, kappa=kap)
+    _twice(fdmpc, L, ctx, 8)
     ctx.close()
 
 
