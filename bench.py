@@ -360,7 +360,7 @@ def bench_gpu(args):
     # ---- roofline of the dominant kernel (patch solve), FP32 factors: the same
     # solves through the host loop with CUDA events around every kernel group
     ctx_kt = fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP32, kernel_timing=1,
-                           patch_kernel={3: 3, 6: 5}.get(tuning[0], 1), patch_threads=tuning[1],
+                           patch_kernel={3: 3, 6: 5, 7: 6, 8: 7}.get(tuning[0], 1), patch_threads=tuning[1],
                            patch_rows_per_warp=8 if tuning[2] else 4, sc_variant=tuning[2] + 1)
     for _ in range(args.warmup):
         ctx_kt.pcg_solve(b, x, rtol=RTOL, maxit=MAXIT)
@@ -471,7 +471,9 @@ def bench_gpu(args):
                            "setup_seconds": sum(setup_s),
                            "pcg_loop": "host" if args.pcg_host_loop else "device (CUDA graph)",
                            "autotuned_patch_solve": {"kernel": {3: "resident", 5: "one CTA per patch, Schur-coupling form",
-                                                                6: "persistent, Schur-coupling form"}.get(
+                                                                6: "persistent, Schur-coupling form",
+                                                                7: "persistent, whole patch staged, Schur-coupling form",
+                                                                8: "one warp per patch, Schur-coupling form"}.get(
                                                          tuning[0], "one CTA per patch"),
                                                      "threads": tuning[1], "variant": tuning[2],
                                                      "sweep_us": tuning[3], "candidates": tuning[4]}},
@@ -480,7 +482,8 @@ def bench_gpu(args):
                         "d2h_bytes_per_step": 8 * ctx.ndof},
                 "gpu_launches": int(launches),
                 "roofline": {"kernel": {3: "k_patch_resident<float>", 5: "k_patch_solve_sc<float>",
-                                        6: "k_patch_solve_scp<float>"}.get(
+                                        6: "k_patch_solve_scp<float>", 7: "k_patch_solve_scf<float>",
+                                        8: "k_patch_solve_scw<float>"}.get(
                                  tuning[0], "k_patch_solve<float>"),
                              "bound": "hbm", "achieved": achieved, "peak": peak,
                              "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,

@@ -109,7 +109,11 @@ typedef struct {
                          the interior stars on thread-block clusters that hold L21 in shared
                          memory across both solves, the other stars as 1; 5 = persistent CTAs in
                          the Schur-coupling form that stage the next patch's lower-block values in
-                         shared memory and its S_TB and W in L2 while solving the current one */
+                         shared memory and its S_TB and W in L2 while solving the current one;
+                         6 = persistent CTAs in the Schur-coupling form that bulk-copy each patch's
+                         whole operator (pivots, L10, line blocks, S_TB, W) into one of two
+                         shared-memory buffers while solving the previous patch from the other
+                         (FDM_EINVAL at set-up where two operators do not fit in 227 KB) */
   int stream_buffers; /* ring buffers of the streamed solve (0 = 4) */
   int stream_buffer_kb; /* size of each ring buffer in KiB (0 = 16) */
   int inject_stall;   /* test hook: the streamed, resident, cluster and (where it stages values in
@@ -126,7 +130,9 @@ typedef struct {
                          solve evict-first), 2 = none */
   int autotune;       /* 1: at set-up, time one relaxation sweep with each patch-solve variant
                          (256 threads with four or eight rows per warp in the forward products,
-                         512, 1024 threads, the resident kernel where it fits) and keep the
+                         512, 1024 threads, the resident kernel where it fits; in the
+                         Schur-coupling form its one-CTA-per-patch shapes and the persistent
+                         kernels 5 and 6, the latter where it fits) and keep the
                          fastest (FDM_Q_TUNING); 0 (default): the fixed rule (patch_threads,
                          patch_kernel).  Variants sum in different orders: results of contexts
                          tuned differently agree to rounding, not bit for bit */
@@ -138,8 +144,8 @@ typedef struct {
                          2 = Schur-coupling form (y_B = S_BB^{-1} g_B, x_T = W (g_T - S_TB y_B),
                          x_B = y_B - S_BB^{-1} S_BT x_T with B = levels 0 and 1, T = the top
                          level, S_TB in S_G's own sparsity and W = (L_TT L_TT^T)^{-1}: no dense
-                         L21, W read once), patch_kernel 0, 1 or 5 only; 0 (default) = 2 for
-                         patch_kernel 0, 1 or 5, else 1 */
+                         L21, W read once), patch_kernel 0, 1, 5 or 6 only; 0 (default) = 2 for
+                         patch_kernel 0, 1, 5 or 6, else 1 */
   int coarse_levels;  /* solve of the Q1 coarse problem (Section 3): 0 = exact (dense inverse
                          from a banded Cholesky factor); k > 0 = one geometric multigrid V-cycle
                          with at most k coarsenings (every other vertex per axis while all cell
@@ -153,7 +159,9 @@ typedef struct {
   int sc_variant;     /* Schur-coupling one-CTA-per-patch solve with 256 threads: 1 (0 = default) =
                          two rows of W per warp, lower-block values and S_TB staged in shared
                          memory (five CTAs per SM); 2 = four rows of W per warp (four CTAs per SM);
-                         3 = two rows, only the lower-block values staged (six CTAs per SM) */
+                         3 = two rows, only the lower-block values staged (six CTAs per SM);
+                         4 = two rows, nothing staged, the patch's whole value block prefetched
+                         into L2 when its CTA starts (six CTAs per SM) */
 } fdm_options;
 
 /* Fills the defaults listed above. */

@@ -75,6 +75,17 @@ struct fdm_batch {
 
 namespace {
 
+// dynamic shared memory a CTA may use on sm_103 (227 KB)
+constexpr size_t kScfSmemCap = 227 * 1024;
+
+// whether the warp-per-patch solve takes this context's classes with
+// `threads` / 32 patches per CTA: top blocks within its register column sums,
+// per-warp work space within shared memory
+bool scw_fits(const fdm_ctx *c, bool fp32, int threads) {
+  const size_t ws = (size_t)patch_scw_ws(c->maxG, c->maxN0, c->maxN1) * (fp32 ? 4 : 8) * (threads / 32);
+  return c->maxN2 <= patch_scw_max_n2(4) && ws <= kScfSmemCap;
+}
+
 // ---------------------------------------------------------------- helpers
 __global__ void k_mask_dirichlet(Grid g, double *v) {
   for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < g.ndof; id += (int64_t)gridDim.x * blockDim.x) {
@@ -134,7 +145,15 @@ void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st, c
                         (uint64_t)(std::max(c->opt.wait_timeout_s, 0.0) * 1e9), c->status, 0, 0, 0};
     a.rows8 = c->rows8;  // Schur-coupling form: four rows per warp in the W product (else two)
     a.inject_stall = c->opt.inject_stall;
-    if (c->sc_persist) {  // persistent (256 threads): two buffers for the lower block's values, S_TB and W via L2
+    if (c->sc_warp) {  // one warp per patch, patch_threads / 32 patches per CTA
+      launch_patch_scw<T>(a, c->nsolve, patch_scw_ws(c->maxG, c->maxN0, c->maxN1), c->patch_threads / 32, c->maxN2, st);
+    } else if (c->sc_full) {  // persistent: each patch's whole operator staged, two buffers
+      a.stage_st = 1;
+      a.tmpcap = patch_sc_tmp(c->maxN1, c->maxN2, c->patch_threads);
+      a.headcap = c->fcap_sc;
+      launch_patch_scf<T>(a, c->nsolve, patch_sc_smem<T>(c->maxG, c->maxN1, c->maxN2, c->patch_threads, 2 * a.headcap),
+                          c->patch_threads, st);
+    } else if (c->sc_persist) {  // persistent (256 threads): two buffers for the lower block's values, S_TB and W via L2
       a.stage_st = 0;
       a.tmpcap = patch_sc_tmp(c->maxN1, c->maxN2, 256);  // the scratch the kernel zeroes, sized for its threads
       a.headcap = sizeof(T) == 4 ? c->bcap32 : c->bcap64;
@@ -142,8 +161,12 @@ void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st, c
     } else {
       // 128 threads, or 256 with rows8 = 2: only the lower block's values are staged (eight or
       // six CTAs per SM)
-      a.stage_st = (c->patch_threads <= 128 || c->rows8 == 2) ? 0 : 1;
+      a.stage_st = (c->patch_threads <= 128 || c->rows8 >= 2) ? 0 : 1;
       a.headcap = a.stage_st ? (sizeof(T) == 4 ? c->headcap32 : c->headcap64) : (sizeof(T) == 4 ? c->bcap32 : c->bcap64);
+      if (c->rows8 == 3) {  // nothing staged: the whole value block prefetched into L2 at the start
+        a.headcap = 0;
+        a.prefetch = 1;
+      }
       launch_patch_sc<T>(a, c->nsolve, patch_sc_smem<T>(c->maxG, c->maxN1, c->maxN2, c->patch_threads, a.headcap),
                          c->patch_threads, st);
     }
@@ -463,10 +486,13 @@ void setup_patches(fdm_ctx *c) {
   // the streamed, resident and cluster kernels read the L form
   const bool l_kernel = c->opt.patch_kernel >= 2 && c->opt.patch_kernel <= 4;
   if (c->opt.patch_form == 2 && l_kernel) fail(FDM_EINVAL, "patch_form 2 needs patch_kernel 0, 1 or 5");
-  if (c->opt.patch_form == 1 && c->opt.patch_kernel == 5) fail(FDM_EINVAL, "patch_kernel 5 needs the Schur-coupling form");
-  if (c->opt.patch_kernel < 0 || c->opt.patch_kernel > 5) fail(FDM_EINVAL, "patch_kernel out of range");
+  if (c->opt.patch_form == 1 && c->opt.patch_kernel >= 5)
+    fail(FDM_EINVAL, "patch_kernel 5, 6 and 7 need the Schur-coupling form");
+  if (c->opt.patch_kernel < 0 || c->opt.patch_kernel > 7) fail(FDM_EINVAL, "patch_kernel out of range");
   c->scform = c->opt.patch_form == 2 || (c->opt.patch_form == 0 && !l_kernel);
   c->sc_persist = c->scform && c->opt.patch_kernel == 5;
+  c->sc_full = c->scform && c->opt.patch_kernel == 6;
+  c->sc_warp = c->scform && c->opt.patch_kernel == 7;
   c->classes = build_classes(p, c->scform);
   c->nbuf = c->opt.stream_buffers > 0 ? c->opt.stream_buffers : 4;
   c->buf_bytes = 1024 * (c->opt.stream_buffer_kb > 0 ? c->opt.stream_buffer_kb : 16);
@@ -598,7 +624,7 @@ void setup_patches(fdm_ctx *c) {
       fail(FDM_EINVAL, "patch interface too large for shared memory (Schur-coupling form)");
     // the variant of the 256-thread kernel (rows8 holds its code): 0 = two rows of W per warp,
     // all values before W staged; 1 = four rows; 2 = two rows, lower block staged only
-    if (c->opt.sc_variant < 0 || c->opt.sc_variant > 3) fail(FDM_EINVAL, "sc_variant out of range");
+    if (c->opt.sc_variant < 0 || c->opt.sc_variant > 4) fail(FDM_EINVAL, "sc_variant out of range");
     c->rows8 = c->opt.sc_variant > 0 ? c->opt.sc_variant - 1 : 0;
     // stage the values before W in shared memory where the largest class's fit in 48 KB
     int64_t head = 0, bhead = 0;
@@ -610,6 +636,24 @@ void setup_patches(fdm_ctx *c) {
     c->headcap64 = head * 8 <= 48 * 1024 ? (int)head : 0;
     c->bcap32 = bhead * 4 <= 24 * 1024 ? (int)bhead : 0;
     c->bcap64 = bhead * 8 <= 24 * 1024 ? (int)bhead : 0;
+    int64_t nvmax = 0;  // the fully staged kernel's buffers: the largest class's values
+    for (const PatchClass &C : c->classes) nvmax = std::max<int64_t>(nvmax, C.nval);
+    c->fcap_sc = (int)((nvmax + 3) & ~3);
+    if (c->sc_warp) {
+      if (c->opt.patch_threads > 0 && c->opt.patch_threads != 128 && c->opt.patch_threads != 256)
+        fail(FDM_EINVAL, "patch_kernel 7: patch_threads must be 128 or 256 (4 or 8 patches per CTA)");
+      c->patch_threads = c->opt.patch_threads > 0 ? c->opt.patch_threads : 256;
+      if (!scw_fits(c, c->opt.precision == FDM_PREC_FP32, c->patch_threads))
+        fail(FDM_EINVAL, "patch_kernel 7: the interface is too large for one warp per patch");
+    }
+    if (c->sc_full) {
+      const size_t need = c->opt.precision == FDM_PREC_FP32
+                              ? patch_sc_smem<float>(c->maxG, c->maxN1, c->maxN2, c->patch_threads, 2 * c->fcap_sc)
+                              : patch_sc_smem<double>(c->maxG, c->maxN1, c->maxN2, c->patch_threads, 2 * c->fcap_sc);
+      if (need > kScfSmemCap)
+        fail(FDM_EINVAL, "patch_kernel 6: two patch operators do not fit in shared memory (" + std::to_string(need) +
+                             " bytes)");
+    }
   }
   // eight rows per warp in flight pay off for long L21 rows with 256 threads (measured:
   // 10 % at Q8, neutral at Q7, slower with 1024 threads at Q15)
@@ -931,8 +975,16 @@ void autotune_patch(fdm_ctx *c, cudaStream_t st) {
   std::vector<Cand> cands = {{1, 256, 0}, {1, 256, 1}, {1, 512, 0}, {1, 1024, 0}};
   const bool fp32 = c->opt.precision == FDM_PREC_FP32;
   const size_t rs = fp32 ? c->rsmem32 : c->rsmem64;
-  if (c->scform)  // the layout fixes the kernel
+  if (c->scform) {  // the layout fixes the kernel
     cands = {{5, 128, 0}, {5, 256, 0}, {5, 256, 1}, {5, 256, 2}, {5, 512, 0}, {6, 256, 0}};
+    for (int t : {256, 512, 1024}) {  // fully staged persistent kernel, where two patch operators fit
+      const size_t need = fp32 ? patch_sc_smem<float>(c->maxG, c->maxN1, c->maxN2, t, 2 * c->fcap_sc)
+                               : patch_sc_smem<double>(c->maxG, c->maxN1, c->maxN2, t, 2 * c->fcap_sc);
+      if (need <= kScfSmemCap) cands.push_back({7, t, 0});
+    }
+    for (int t : {128, 256})  // one warp per patch, 4 or 8 patches per CTA
+      if (scw_fits(c, fp32, t)) cands.push_back({8, t, 0});
+  }
   else if (rs <= 225 * 1024) cands.push_back({3, 512, 0});
   const int64_t n = c->g.ndof;
   fill(n, 1.0, c->r, st);
@@ -951,6 +1003,8 @@ void autotune_patch(fdm_ctx *c, cudaStream_t st) {
     c->res64 = !fp32 && k.kernel == 3;
     c->res_threads = k.threads;
     c->sc_persist = k.kernel == 6;
+    c->sc_full = k.kernel == 7;
+    c->sc_warp = k.kernel == 8;
     auto sweep = [&]() {
       if (fp32) run_asm<float, double, double>(c, c->r, c->z, c->omega, st);
       else run_asm<double, double, double>(c, c->r, c->z, c->omega, st);
@@ -977,6 +1031,8 @@ void autotune_patch(fdm_ctx *c, cudaStream_t st) {
   c->res64 = !fp32 && pick.kernel == 3;
   c->res_threads = pick.kernel == 3 ? pick.threads : rthreads;
   c->sc_persist = pick.kernel == 6;
+  c->sc_full = pick.kernel == 7;
+  c->sc_warp = pick.kernel == 8;
   c->tuning[0] = pick.kernel;
   c->tuning[1] = pick.threads;
   c->tuning[2] = pick.rows8;

@@ -58,6 +58,9 @@ struct fdm_ctx {
   int headcap32 = 0, headcap64 = 0;  // its staged values before W, per precision (elements)
   int bcap32 = 0, bcap64 = 0;        // the same before S_TB (lower block only)
   bool sc_persist = false;           // persistent Schur-coupling kernel (patch_kernel = 5)
+  bool sc_full = false;              // persistent, whole patch staged (patch_kernel = 6)
+  bool sc_warp = false;              // one warp per patch (patch_kernel = 7)
+  int fcap_sc = 0;                   // its buffer size: the largest class's value count
   // cluster patch solve for the classes with a dense top level (a prefix of the order)
   int n_heavy = 0, cl_threads = 256;
   bool cl32 = false, cl64 = false;

@@ -846,9 +846,10 @@ __global__ void __launch_bounds__(NT, MINB) k_patch_solve_sc(PatchSolveArgs<T> a
         bulk::bulk_g2s(reinterpret_cast<char *>(H) + off, reinterpret_cast<const char *>(Lv) + off,
                        bytes - off < 32768 ? bytes - off : 32768, &bar);
     }
-    // W into L2 while the gather and the lower solve run
-    const uint32_t wb = (uint32_t)((C.nval - C.off_z) * (int64_t)sizeof(T));
-    const char *ws = reinterpret_cast<const char *>(Lv + C.off_z);
+    // W (a.prefetch: the whole value block) into L2 while the gather and the lower solve run
+    const int64_t pf0 = a.prefetch ? 0 : C.off_z;
+    const uint32_t wb = (uint32_t)((C.nval - pf0) * (int64_t)sizeof(T));
+    const char *ws = reinterpret_cast<const char *>(Lv + pf0);
     for (uint32_t off = 0; off < wb; off += 32768) bulk::prefetch_l2(ws + off, wb - off < 32768 ? wb - off : 32768);
   }
   __syncthreads();  // the barriers' initialisation and sFail are visible
@@ -944,6 +945,76 @@ __global__ void __launch_bounds__(NT, MINB) k_patch_solve_scp(PatchSolveArgs<T> 
   }
 }
 
+// Persistent variant with each patch's whole solve operator staged in shared
+// memory (level-0 pivots, L10, the line blocks, S_TB and W): two buffers of
+// a.headcap elements; while the CTA solves one patch from one buffer, the next
+// patch's values are bulk-copied into the other, so the copies overlap the
+// solves and every phase after the gather (which reads the L2-resident cell
+// residual) runs on chip.  Each stored value leaves DRAM once per sweep.  The
+// launcher guarantees a.headcap >= the largest class's value count.  Each
+// buffer has its own mbarrier (one phase per copy); every wait is bounded by
+// a.timeout_ns, after which the CTA waits once more (bounded) for its copies
+// in flight, sets the status word and returns.
+template <typename T, int NT, int SRB>
+__global__ void __launch_bounds__(NT, 1) k_patch_solve_scf(PatchSolveArgs<T> a, int npatch) {
+  extern __shared__ __align__(128) unsigned char smem_[];
+  const int tid = threadIdx.x;
+  __shared__ __align__(8) uint64_t bar[3];  // [2]: test hook, never completed
+  __shared__ int sFail, sPend[2];
+  T *const H0 = reinterpret_cast<T *>(smem_);
+  T *const H1 = H0 + a.headcap;
+  T *gv = H1 + a.headcap;
+  auto issue = [&](int it, int b) {  // thread 0: copy patch `it`'s values into buffer b
+    const PatchDev Q = a.patches[a.order[it]];
+    const ClassDev &D = a.cls[Q.cls];
+    sPend[b] = 0;
+    if (D.nval > 0) {
+      bulk::fence_proxy_async();  // the buffer's previous contents were read by every thread
+      const uint32_t bytes = (uint32_t)(D.nval * (int64_t)sizeof(T));  // a multiple of 16
+      char *dst = reinterpret_cast<char *>(b ? H1 : H0);
+      const char *src = reinterpret_cast<const char *>(a.L + Q.voff);
+      bulk::mbar_arrive_expect_tx(&bar[b], bytes);
+      for (uint32_t off = 0; off < bytes; off += 32768)
+        bulk::bulk_g2s(dst + off, src + off, bytes - off < 32768 ? bytes - off : 32768, &bar[b]);
+      sPend[b] = 1;
+    }
+  };
+  if (tid == 0) {
+    bulk::mbar_init(&bar[0], 1);
+    bulk::mbar_init(&bar[1], 1);
+    bulk::mbar_init(&bar[2], 1);
+    bulk::fence_mbar_init();
+    sFail = 0;
+    sPend[0] = sPend[1] = 0;
+    if ((int)blockIdx.x < npatch) issue(blockIdx.x, 0);
+  }
+  __syncthreads();
+  uint32_t par[2] = {0, 0};
+  int b = 0;
+  for (int it = blockIdx.x; it < npatch; it += gridDim.x, b ^= 1) {
+    const PatchDev P = a.patches[a.order[it]];
+    const ClassDev &C = a.cls[P.cls];
+    if (tid == 0 && it + (int)gridDim.x < npatch) issue(it + gridDim.x, b ^ 1);
+    sc_gather<T, NT>(a, P, C, gv);  // also zeroes y and the scratch
+    if (sPend[b]) {
+      bool ok = !a.inject_stall || bulk::mbar_wait_bounded(&bar[2], 0, a.timeout_ns);  // never completes
+      ok = ok && bulk::mbar_wait_bounded(&bar[b], par[b], a.timeout_ns);
+      if (!ok) sFail = 1;
+    }
+    __syncthreads();  // the gather is complete and every thread has seen its wait end
+    if (sFail) {
+      for (int q = 0; q < 2; ++q)  // a second bounded wait for every copy in flight
+        if (sPend[q]) bulk::mbar_wait_bounded(&bar[q], par[q], a.timeout_ns);
+      if (tid == 0) atomicExch(a.status, 1);
+      return;
+    }
+    if (sPend[b]) par[b] ^= 1u;
+    const T *Hb = b ? H1 : H0;
+    sc_patch_compute<T, NT, SRB>(a, P, C, Hb, Hb, gv, true);
+    __syncthreads();  // buffer b and gv are free for the next patch
+  }
+}
+
 int patch_sc_tmp(int maxN1, int maxN2, int threads) {
   const int l1 = (maxN1 + 3) & ~3, l2 = (maxN2 + 3) & ~3;
   return 2 * l1 + (threads / 32) * l2 + 4;  // + 4: the accumulators' 16-byte alignment
@@ -970,6 +1041,34 @@ void launch_patch_scp(const PatchSolveArgs<T> &a, int npatch, size_t smem, cudaS
   }
   const int grid = std::max(1, std::min(npatch, std::max(per_sm, 1) * nsm));
   k_patch_solve_scp<T, 256, 2, 5><<<grid, 256, smem, st>>>(a, npatch);
+}
+
+// the fully staged persistent kernel: one CTA per SM (the two buffers take
+// most of its shared memory), threads 256, 512 or 1024
+template <typename T, int NT, int SRB>
+void launch_scf_nt(const PatchSolveArgs<T> &a, int npatch, size_t smem, cudaStream_t st) {
+  static size_t attr = 0;
+  static int per_sm = 0, nsm = 0;
+  if (attr < smem) {
+    FDM_CUDA(cudaFuncSetAttribute(k_patch_solve_scf<T, NT, SRB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+    FDM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_patch_solve_scf<T, NT, SRB>, NT, smem));
+    int dev = 0;
+    FDM_CUDA(cudaGetDevice(&dev));
+    FDM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    attr = smem;
+  }
+  if (per_sm < 1) fail(FDM_EINVAL, "fully staged patch solve: launch configuration does not fit an SM");
+  const int grid = std::max(1, std::min(npatch, per_sm * nsm));
+  k_patch_solve_scf<T, NT, SRB><<<grid, NT, smem, st>>>(a, npatch);
+}
+
+template <typename T>
+void launch_patch_scf(const PatchSolveArgs<T> &a, int npatch, size_t smem, int threads, cudaStream_t st) {
+  if (npatch <= 0) return;
+  if (threads >= 1024) launch_scf_nt<T, 1024, 2>(a, npatch, smem, st);
+  else if (threads >= 512) launch_scf_nt<T, 512, 2>(a, npatch, smem, st);
+  else launch_scf_nt<T, 256, 4>(a, npatch, smem, st);
 }
 
 template <typename T>
@@ -1089,7 +1188,8 @@ void launch_patch_solve(const PatchSolveArgs<T> &a, int npatch, size_t smem, int
   template size_t patch_smem_for_occupancy<T>(size_t, int);                                                 \
   template size_t patch_sc_smem<T>(int, int, int, int, int);                                                \
   template void launch_patch_sc<T>(const PatchSolveArgs<T> &, int, size_t, int, cudaStream_t);             \
-  template void launch_patch_scp<T>(const PatchSolveArgs<T> &, int, size_t, cudaStream_t);
+  template void launch_patch_scp<T>(const PatchSolveArgs<T> &, int, size_t, cudaStream_t);                  \
+  template void launch_patch_scf<T>(const PatchSolveArgs<T> &, int, size_t, int, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -44,6 +44,16 @@ void launch_patch_sc(const PatchSolveArgs<T> &a, int npatch, size_t smem, int th
 // persistent variant (256 threads): headcap = elements of each of its two staging buffers
 template <typename T>
 void launch_patch_scp(const PatchSolveArgs<T> &a, int npatch, size_t smem, cudaStream_t st);
+// persistent, each patch's whole operator staged in one of two shared-memory
+// buffers of a.headcap elements (>= the largest class's value count)
+template <typename T>
+void launch_patch_scf(const PatchSolveArgs<T> &a, int npatch, size_t smem, int threads, cudaStream_t st);
+// one warp per patch: ws = per-warp shared-memory elements (patch_scw_ws),
+// warps = patches per CTA (4 or 8), maxN2 <= patch_scw_max_n2(4)
+int patch_scw_ws(int maxG, int maxN0, int maxN1);
+int patch_scw_max_n2(int nq);
+template <typename T>
+void launch_patch_scw(const PatchSolveArgs<T> &a, int npatch, int ws, int warps, int maxN2, cudaStream_t st);
 // the resident variant: fcap factor elements per CTA in shared memory (one
 // patch's values), tmp sized for `threads`
 int patch_resident_tmp(int maxN1, int maxN2, int threads);

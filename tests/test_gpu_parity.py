@@ -391,7 +391,7 @@ def test_resident_matches_classic_bitwise(p, precision):
     assert np.array_equal(out[0], out[1])
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5, 6])
 def test_bounded_wait_reports_timeout_kernels(kernel):
     """As below, for every patch solve with a bounded device-side wait: the
     Schur-coupling kernels (its staging copy), the streamed, resident and
@@ -418,7 +418,8 @@ def test_autotuned_context_matches(p, precision):
     a = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7)
     b = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7, autotune=1)
     kernel, threads, rows8, us, ncand = b.tuning()
-    assert kernel in (5, 6) and threads in (128, 256, 512) and us > 0 and ncand == 6   # Schur-coupling form (default)
+    # Schur-coupling form (default): six shapes plus the fully staged and warp-per-patch kernels where they fit
+    assert kernel in (5, 6, 7, 8) and threads in (128, 256, 512, 1024) and us > 0 and 6 <= ncand <= 11
     c = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7, autotune=1, patch_form=1)
     kernel, threads, rows8, us, ncand = c.tuning()
     assert kernel in (1, 3) and threads in (256, 512, 1024) and rows8 in (0, 1) and us > 0 and ncand >= 4
@@ -525,3 +526,64 @@ def test_persistent_sc_matches(p, precision):
         assert ctx.status() == 0
         ctx.close()
     assert relerr(out[1], out[0]) <= (1e-12 if precision == FP64 else 1e-5)
+
+
+@pytest.mark.parametrize("p,precision", [(2, FP64), (3, FP64), (5, FP64), (4, FP32), (7, FP32)])
+def test_fully_staged_sc_matches(p, precision):
+    """The persistent kernel that stages each patch's whole operator (pivots,
+    L10, line blocks, S_TB and W) in one of two shared-memory buffers gives the
+    oracle's relaxation with 256, 512 and 1024 threads, and reports no
+    expired wait; the 3^3 graded mesh has every star class."""
+    xv, yv, zv = inputs.graded_vertices(3, 15)
+    ref = oracle.Problem(p, xv, yv, zv)
+    ref.setup_patches()
+    ref.set_omega(0.7)
+    r = np.random.default_rng(64).standard_normal(ref.ndof)
+    zr = ref.asm_apply(r)
+    for threads in (256, 512, 1024):
+        ctx = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7, patch_kernel=6,
+                            patch_threads=threads)
+        z = N(ctx.asm_apply(T(r)))
+        record("scf_p%d_t%d" % (p, threads), relerr=relerr(z, zr))
+        assert relerr(z, zr) <= (1e-11 if precision == FP64 else 1e-4)
+        assert ctx.status() == 0
+        ctx.close()
+
+
+def test_fully_staged_sc_rejects_what_does_not_fit():
+    """Two FP64 patch operators at p = 8 (38,504 values each) exceed shared
+    memory: the set-up refuses the kernel instead of launching it."""
+    xv = np.linspace(0, 1, 3)
+    with pytest.raises(fdmpc.FdmError) as e:
+        fdmpc.Context(8, xv, xv, xv, precision=FP64, omega=1.0, patch_kernel=6)
+    assert e.value.code == fdmpc.FDM_EINVAL
+
+
+@pytest.mark.parametrize("p,precision", [(1, FP64), (2, FP64), (3, FP64), (7, FP64), (4, FP32), (7, FP32), (9, FP32),
+                                         (11, FP32)])
+def test_warp_per_patch_matches(p, precision):
+    """The warp-per-patch Schur-coupling solve (one warp per star, 4 or 8
+    stars per CTA, no CTA barrier) gives the oracle's relaxation on a mesh with
+    every star class; p = 9 and 11 take its wider register column sums."""
+    xv, yv, zv = inputs.graded_vertices(2 if p >= 9 else 3, 16)
+    ref = oracle.Problem(p, xv, yv, zv)
+    ref.setup_patches()
+    ref.set_omega(0.7)
+    r = np.random.default_rng(65).standard_normal(ref.ndof)
+    zr = ref.asm_apply(r)
+    for threads in (128, 256):
+        ctx = fdmpc.Context(p, xv, yv, zv, precision=precision, pc=fdmpc.FDM_PC_ASM, omega=0.7, patch_kernel=7,
+                            patch_threads=threads)
+        z = N(ctx.asm_apply(T(r)))
+        record("scw_p%d_t%d" % (p, threads), relerr=relerr(z, zr))
+        assert relerr(z, zr) <= (1e-11 if precision == FP64 else 1e-4)
+        ctx.close()
+
+
+def test_warp_per_patch_rejects_large_interfaces():
+    """At p = 12 the top block (529 rows) exceeds the warp kernel's register
+    column sums: the set-up refuses it."""
+    xv = np.linspace(0, 1, 3)
+    with pytest.raises(fdmpc.FdmError) as e:
+        fdmpc.Context(12, xv, xv, xv, precision=FP32, omega=1.0, patch_kernel=7)
+    assert e.value.code == fdmpc.FDM_EINVAL
