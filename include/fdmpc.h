@@ -537,6 +537,54 @@ int fdm_query(fdm_ctx *ctx, int what, void *out, size_t *len);
 const char *fdm_last_error(const fdm_ctx *ctx);
 void fdm_destroy(fdm_ctx *ctx);
 
+/* ---------------------------------------------------------------------------
+ * Box partition of the structured mesh over ranks (host only, no GPU): the
+ * layout of a sharded solve.  The path's sums over cells are the direct
+ * stiffness summation of the cell operators (Section 2.2) and the additive
+ * Schwarz sum of the star solutions (Section 2.5); split over ranks, each node
+ * on a box face, edge or corner takes contributions from cells of several
+ * ranks.  Ranks form a px x py x pz grid (rank = rx + px (ry + py rz)); rank r
+ * owns the cells [c0, c1) per axis of a balanced split, c0 = floor(r n / P),
+ * and holds the nodes [c0 p, c1 p] of its cells (its node box, x fastest).
+ * Per-cell contributions of the owned cells are laid out E[local cell][(p+1)^3]
+ * (local cells x fastest within the box, nodes x fastest within a cell).
+ *   send lists: per neighbour (a rank whose node box meets this one, ascending
+ *     rank), the local E indices of this rank's contributions at the shared
+ *     nodes (nodes in ascending global index, then cells in ascending global
+ *     index); the neighbour receives them in that order;
+ *   receive buffer: the neighbours' messages concatenated in neighbour order
+ *     (FDM_PQ_RECV_PTR gives the offsets);
+ *   sum plan: per node of the node box, its contributions in ascending global
+ *     cell index, each >= 0 (local E index) or < 0 (-1 - receive-buffer slot).
+ * Summing the plan in order from 0 gives the single-domain node gather's sum
+ * (ascending global cell index) bit for bit.  Node ownership (FDM_PQ_OWNED):
+ * the box whose half-open cell range holds the node's lower cell along every
+ * axis (the last box for the upper boundary): each node has one owner, which
+ * takes it in dot products.  A vertex star belongs to its vertex's owner
+ * (FDM_PQ_STARS, global vertex indices x fastest); its cells lie in the owner's
+ * cells plus a one-cell halo (FDM_PQ_HALO_BOX).
+ * fdm_partition_create: FDM_EINVAL unless 1 <= p <= 15, 1 <= px <= nx (same for
+ * y, z) and 0 <= rank < px py pz.  The handle owns host memory only. */
+typedef struct fdm_partition fdm_partition;
+int fdm_partition_create(int nx, int ny, int nz, int p, int px, int py, int pz, int rank, fdm_partition **out);
+#define FDM_PQ_CELL_BOX 1   /* int32[6]: owned cells [c0, c1) along x, y, z */
+#define FDM_PQ_NODE_BOX 2   /* int32[6]: node box [g0, g1] (inclusive) along x, y, z */
+#define FDM_PQ_HALO_BOX 3   /* int32[6]: owned cells plus a one-cell halo, [c0, c1) clamped to the mesh */
+#define FDM_PQ_NNEIGH 4     /* int32: number of neighbours */
+#define FDM_PQ_NEIGHBORS 5  /* int32[nneigh]: neighbour ranks, ascending */
+#define FDM_PQ_SEND_PTR 6   /* int64[nneigh + 1]: offsets of the send lists */
+#define FDM_PQ_SEND 7       /* int64[]: local E indices to send, concatenated over neighbours */
+#define FDM_PQ_RECV_PTR 8   /* int64[nneigh + 1]: offsets of each neighbour's message in the receive buffer */
+#define FDM_PQ_SUM_PTR 9    /* int64[nodes + 1]: offsets of each node's sum plan */
+#define FDM_PQ_SUM 10       /* int64[]: sum plans (>= 0 local E index, < 0: -1 - receive slot) */
+#define FDM_PQ_OWNED 11     /* uint8[nodes]: 1 where this rank owns the node */
+#define FDM_PQ_STARS 12     /* int64[]: global indices of the vertices whose stars this rank owns */
+/* Copies the quantity into out (HOST); *len is the capacity in bytes on input
+ * and the size written (or, on FDM_EINVAL for a small buffer, needed) on output. */
+int fdm_partition_query(const fdm_partition *part, int what, void *out, size_t *len);
+const char *fdm_partition_last_error(void);
+void fdm_partition_destroy(fdm_partition *part);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,6 +33,8 @@ FDM_SURR_AVERAGED, FDM_SURR_EXTERNAL = 0, 1
  FDM_HQ_NODE_OWNER, FDM_HQ_NODE_CELLS_PTR, FDM_HQ_NODE_CELLS, FDM_HQ_GEOM, FDM_HQ_COARSE_OF,
  FDM_HQ_COARSE, FDM_HQ_SC_SPLIT, FDM_HQ_SC_PTR, FDM_HQ_SC_ROWPTR, FDM_HQ_SC_COLPTR, FDM_HQ_SC_COLS,
  FDM_HQ_SC_VALUES_PTR, FDM_HQ_SC_VALUES) = range(1, 47)
+(FDM_PQ_CELL_BOX, FDM_PQ_NODE_BOX, FDM_PQ_HALO_BOX, FDM_PQ_NNEIGH, FDM_PQ_NEIGHBORS, FDM_PQ_SEND_PTR, FDM_PQ_SEND,
+ FDM_PQ_RECV_PTR, FDM_PQ_SUM_PTR, FDM_PQ_SUM, FDM_PQ_OWNED, FDM_PQ_STARS) = range(1, 13)
 FDM_MLP_NPARAM = 16515
 TIMERS = ("restrict", "patch", "interp", "op64", "op32", "coarse", "vec")
 
@@ -131,6 +133,12 @@ def load():
     L.fdm_hexmesh_last_error.restype = C.c_char_p
     L.fdm_hexmesh_destroy.argtypes = [vp]
     L.fdm_hexmesh_destroy.restype = None
+    L.fdm_partition_create.argtypes = [C.c_int] * 8 + [C.POINTER(vp)]
+    L.fdm_partition_query.argtypes = [vp, C.c_int, vp, C.POINTER(C.c_size_t)]
+    L.fdm_partition_last_error.argtypes = []
+    L.fdm_partition_last_error.restype = C.c_char_p
+    L.fdm_partition_destroy.argtypes = [vp]
+    L.fdm_partition_destroy.restype = None
     _lib = L
     return L
 
@@ -876,3 +884,75 @@ class HexMesh:
         vp = self.query(FDM_HQ_SC_VALUES_PTR, np.int64)
         v = self.query(FDM_HQ_SC_VALUES, np.float64)
         return per, [v[vp[k]:vp[k + 1]] for k in range(len(vp) - 1)]
+
+
+class Partition:
+    """Box partition of an nx x ny x nz cell mesh at degree p over a
+    px x py x pz rank grid, seen from one rank (fdm_partition_create): host
+    index lists only (cell and node boxes, neighbours, send lists, the
+    per-node sum plans, node ownership, owned stars)."""
+
+    def __init__(self, ncell, p, nrank, rank):
+        L = load()
+        h = C.c_void_p()
+        rc = L.fdm_partition_create(int(ncell[0]), int(ncell[1]), int(ncell[2]), int(p), int(nrank[0]),
+                                    int(nrank[1]), int(nrank[2]), int(rank), C.byref(h))
+        if rc < 0:
+            raise FdmError(rc, L.fdm_partition_last_error().decode())
+        self.h = h
+        self.p, self.rank = p, rank
+
+    def query(self, what, dtype, count=None):
+        """The quantity `what` as a numpy array (size found from the library when count is None)."""
+        L = load()
+        if count is None:
+            n = C.c_size_t(0)
+            probe = np.zeros(1, dtype=np.uint8)
+            L.fdm_partition_query(self.h, what, probe.ctypes.data_as(C.c_void_p), C.byref(n))
+            count = n.value // np.dtype(dtype).itemsize
+        out = np.zeros(max(count, 1), dtype=dtype)
+        n = C.c_size_t(out.nbytes)
+        rc = L.fdm_partition_query(self.h, what, out.ctypes.data_as(C.c_void_p), C.byref(n))
+        if rc < 0:
+            raise FdmError(rc, L.fdm_partition_last_error().decode())
+        return out[:count]
+
+    def cell_box(self):
+        return self.query(FDM_PQ_CELL_BOX, np.int32, 6)
+
+    def node_box(self):
+        return self.query(FDM_PQ_NODE_BOX, np.int32, 6)
+
+    def halo_box(self):
+        return self.query(FDM_PQ_HALO_BOX, np.int32, 6)
+
+    def neighbors(self):
+        k = int(self.query(FDM_PQ_NNEIGH, np.int32, 1)[0])
+        return self.query(FDM_PQ_NEIGHBORS, np.int32, k) if k else np.zeros(0, np.int32)
+
+    def lists(self):
+        """(send_ptr, send, recv_ptr, sum_ptr, sum, owned) as numpy arrays."""
+        k = len(self.neighbors())
+        send_ptr = self.query(FDM_PQ_SEND_PTR, np.int64, k + 1)
+        recv_ptr = self.query(FDM_PQ_RECV_PTR, np.int64, k + 1)
+        nb = self.node_box()
+        nodes = int(np.prod(nb[1::2] - nb[0::2] + 1))
+        sum_ptr = self.query(FDM_PQ_SUM_PTR, np.int64, nodes + 1)
+        send = self.query(FDM_PQ_SEND, np.int64, int(send_ptr[-1]))
+        summ = self.query(FDM_PQ_SUM, np.int64, int(sum_ptr[-1]))
+        owned = self.query(FDM_PQ_OWNED, np.uint8, nodes)
+        return send_ptr, send, recv_ptr, sum_ptr, summ, owned
+
+    def stars(self):
+        return self.query(FDM_PQ_STARS, np.int64)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().fdm_partition_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
