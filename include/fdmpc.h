@@ -482,6 +482,51 @@ int fdm_hexmesh_query(fdm_hexmesh *h, int what, void *out, size_t *len);
 const char *fdm_hexmesh_last_error(const fdm_hexmesh *h);
 void fdm_hexmesh_destroy(fdm_hexmesh *h);
 
+/* ---------------------------------------------------------------------------
+ * General hexahedral meshes on the GPU (Sections 2.4-2.8 on the meshes of the
+ * unstructured experiments, Sec. 3 and Table 1): a device context built from
+ * an fdm_hexmesh after fdm_hexmesh_factor.  Vectors are FP64 DEVICE arrays of
+ * nnode values in the hexmesh's node numbering (FDM_HQ_NNODE), caller-owned;
+ * Dirichlet entries are ignored on input and written as 0 on output.
+ *   hex_stiffness_apply: y = A u, the Gauss-quadrature stiffness with the
+ *     geometry factors FDM_HQ_GEOM, summed per node over its cells in cell order;
+ *   hex_asm_apply: one damped sweep z = omega sum_v R_v^T A~_v^{-1} R_v r of the
+ *     vertex-star relaxation with the averaged surrogate (Sec. 2.7) in the glued
+ *     FDM basis: per-cell basis change and Schur condensation, exact interface
+ *     solves in the Schur-coupling form (FDM_HQ_SC_*), per-cell back-substitution
+ *     and basis change back; in opt.precision;
+ *   hex_pc_apply: the hybrid V(1,1) with the Q1 coarse space (dense inverse of
+ *     FDM_HQ_COARSE), or opt.pc = FDM_PC_ASM / FDM_PC_NONE;
+ *   hex_pcg_solve: PCG from x = 0 to ||b - A x|| <= rtol ||b|| (FP64), as pcg_solve.
+ * omega: opt.omega if > 0, else 2 / (1.25 lmax + 0.75 lmin) from
+ * opt.lanczos_steps CG-Lanczos steps on ASM^{-1} A from opt.lanczos_start (HOST,
+ * nnode values) or a seeded normal vector.  fdm_hex_setup copies what it needs
+ * (the hexmesh may be destroyed afterwards); it returns FDM_EINVAL for a mesh
+ * without its numeric set-up, FDM_ENOTSPD for a coarse operator that is not
+ * positive definite, FDM_ENOMEM when device memory runs out.  The calls are
+ * stream-ordered; hex_pcg_solve synchronises to read its scalars. */
+typedef struct fdm_hexgpu fdm_hexgpu;
+int fdm_hex_setup(const fdm_hexmesh *h, const fdm_options *opt, fdm_hexgpu **out, void *stream);
+int hex_stiffness_apply(fdm_hexgpu *ctx, const double *u_dev, double *y_dev, void *stream);
+int hex_asm_apply(fdm_hexgpu *ctx, const double *r_dev, double *z_dev, void *stream);
+int hex_pc_apply(fdm_hexgpu *ctx, const double *r_dev, double *z_dev, void *stream);
+int hex_pcg_solve(fdm_hexgpu *ctx, const double *b_dev, double *x_dev, double rtol, int maxit,
+                  fdm_solve_info *info, void *stream);
+#define FDM_XQ_NNODE 1       /* int64: nodes */
+#define FDM_XQ_OMEGA 2       /* double: damping */
+#define FDM_XQ_LAMBDA 3      /* double[2]: Lanczos lambda_min, lambda_max (0 with opt.omega given) */
+#define FDM_XQ_LAUNCHES 4    /* int64: kernels launched since the last query */
+#define FDM_XQ_SIZES 5       /* int64[6]: cells, stars, star interface values, stored factor values,
+                                coarse unknowns, largest star interface */
+#define FDM_XQ_ALGO_BYTES 6  /* double[2]: bytes of one relaxation sweep moved once (FP64, FP32 factors):
+                                the stored factor values, twice the cell-local residual, the slot values
+                                and star solutions, the surrogate, the per-cell maps, r in and z out */
+/* Copies `what` into out (HOST); *len is the capacity in bytes on input and
+ * the size written on output. */
+int fdm_hex_query(fdm_hexgpu *ctx, int what, void *out, size_t *len);
+const char *fdm_hex_last_error(const fdm_hexgpu *ctx);
+void fdm_hex_destroy(fdm_hexgpu *ctx);
+
 /* ---- introspection ---- */
 #define FDM_Q_NDOF 1         /* int64: number of grid nodes */
 #define FDM_Q_OMEGA 2        /* double: damping */

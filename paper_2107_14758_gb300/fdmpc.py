@@ -33,6 +33,7 @@ FDM_SURR_AVERAGED, FDM_SURR_EXTERNAL = 0, 1
  FDM_HQ_NODE_OWNER, FDM_HQ_NODE_CELLS_PTR, FDM_HQ_NODE_CELLS, FDM_HQ_GEOM, FDM_HQ_COARSE_OF,
  FDM_HQ_COARSE, FDM_HQ_SC_SPLIT, FDM_HQ_SC_PTR, FDM_HQ_SC_ROWPTR, FDM_HQ_SC_COLPTR, FDM_HQ_SC_COLS,
  FDM_HQ_SC_VALUES_PTR, FDM_HQ_SC_VALUES) = range(1, 47)
+FDM_XQ_NNODE, FDM_XQ_OMEGA, FDM_XQ_LAMBDA, FDM_XQ_LAUNCHES, FDM_XQ_SIZES, FDM_XQ_ALGO_BYTES = range(1, 7)
 (FDM_PQ_CELL_BOX, FDM_PQ_NODE_BOX, FDM_PQ_HALO_BOX, FDM_PQ_NNEIGH, FDM_PQ_NEIGHBORS, FDM_PQ_SEND_PTR, FDM_PQ_SEND,
  FDM_PQ_RECV_PTR, FDM_PQ_SUM_PTR, FDM_PQ_SUM, FDM_PQ_OWNED, FDM_PQ_STARS) = range(1, 13)
 FDM_MLP_NPARAM = 16515
@@ -133,6 +134,15 @@ def load():
     L.fdm_hexmesh_last_error.restype = C.c_char_p
     L.fdm_hexmesh_destroy.argtypes = [vp]
     L.fdm_hexmesh_destroy.restype = None
+    L.fdm_hex_setup.argtypes = [vp, C.POINTER(fdm_options), C.POINTER(vp), vp]
+    for f in ("hex_stiffness_apply", "hex_asm_apply", "hex_pc_apply"):
+        getattr(L, f).argtypes = [vp, vp, vp, vp]
+    L.hex_pcg_solve.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.POINTER(fdm_solve_info), vp]
+    L.fdm_hex_query.argtypes = [vp, C.c_int, vp, C.POINTER(C.c_size_t)]
+    L.fdm_hex_last_error.argtypes = [vp]
+    L.fdm_hex_last_error.restype = C.c_char_p
+    L.fdm_hex_destroy.argtypes = [vp]
+    L.fdm_hex_destroy.restype = None
     L.fdm_partition_create.argtypes = [C.c_int] * 8 + [C.POINTER(vp)]
     L.fdm_partition_query.argtypes = [vp, C.c_int, vp, C.POINTER(C.c_size_t)]
     L.fdm_partition_last_error.argtypes = []
@@ -949,6 +959,98 @@ class Partition:
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
             load().fdm_partition_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HexGpu:
+    """Owns one GPU context on a general hexahedral mesh (fdm_hex_setup) built
+    from a HexMesh after its numeric set-up; vectors are CUDA float64 tensors
+    of HexMesh.nnode values in the mesh's node numbering."""
+
+    def __init__(self, mesh, precision=FDM_PREC_FP64, pc=FDM_PC_VCYCLE, omega=0.0, lanczos_start=None,
+                 lanczos_steps=20, flexible_beta=-1, stream=None):
+        opt = fdm_default_options()
+        opt.precision, opt.pc, opt.omega, opt.lanczos_steps = precision, pc, omega, lanczos_steps
+        opt.flexible_beta = flexible_beta
+        self._keep = []
+        if lanczos_start is not None:
+            st = np.ascontiguousarray(lanczos_start, dtype=np.float64)
+            self._keep.append(st)
+            opt.lanczos_start = _dptr(st)
+        L = load()
+        h = C.c_void_p()
+        rc = L.fdm_hex_setup(mesh.h, C.byref(opt), C.byref(h), _stream(stream))
+        if rc < 0:
+            raise FdmError(rc, L.fdm_hex_last_error(None).decode())
+        self.h = h
+        self.nnode = mesh.nnode
+
+    def _check(self, rc):
+        if rc < 0:
+            raise FdmError(rc, load().fdm_hex_last_error(self.h).decode())
+        return rc
+
+    def _out(self, like):
+        import torch
+        return torch.empty_like(like)
+
+    def stiffness_apply(self, u, y=None, stream=None):
+        y = self._out(u) if y is None else y
+        self._check(load().hex_stiffness_apply(self.h, _tptr(u), _tptr(y), _stream(stream)))
+        return y
+
+    def asm_apply(self, r, z=None, stream=None):
+        z = self._out(r) if z is None else z
+        self._check(load().hex_asm_apply(self.h, _tptr(r), _tptr(z), _stream(stream)))
+        return z
+
+    def pc_apply(self, r, z=None, stream=None):
+        z = self._out(r) if z is None else z
+        self._check(load().hex_pc_apply(self.h, _tptr(r), _tptr(z), _stream(stream)))
+        return z
+
+    def pcg_solve(self, b, x=None, rtol=1e-8, maxit=500, raise_on_noconv=True, stream=None):
+        x = self._out(b) if x is None else x
+        info = fdm_solve_info()
+        rc = load().hex_pcg_solve(self.h, _tptr(b), _tptr(x), rtol, maxit, C.byref(info), _stream(stream))
+        if not (rc == FDM_ENOCONV and not raise_on_noconv):
+            self._check(rc)
+        return x, info
+
+    def query(self, what, dtype, count):
+        out = np.zeros(count, dtype=dtype)
+        n = C.c_size_t(out.nbytes)
+        self._check(load().fdm_hex_query(self.h, what, out.ctypes.data_as(C.c_void_p), C.byref(n)))
+        return out
+
+    @property
+    def omega(self):
+        return float(self.query(FDM_XQ_OMEGA, np.float64, 1)[0])
+
+    def lanczos_extremes(self):
+        v = self.query(FDM_XQ_LAMBDA, np.float64, 2)
+        return float(v[0]), float(v[1])
+
+    def launches(self):
+        return int(self.query(FDM_XQ_LAUNCHES, np.int64, 1)[0])
+
+    def sizes(self):
+        """(cells, stars, star interface values, stored factor values, coarse unknowns, largest interface)."""
+        return tuple(int(v) for v in self.query(FDM_XQ_SIZES, np.int64, 6))
+
+    def algo_bytes(self):
+        v = self.query(FDM_XQ_ALGO_BYTES, np.float64, 2)
+        return dict(sweep64=float(v[0]), sweep32=float(v[1]))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().fdm_hex_destroy(self.h)
             self.h = None
 
     def __del__(self):
