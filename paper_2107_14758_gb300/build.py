@@ -53,7 +53,7 @@ def build(verbose=False, ptxas_info=False):
             sys.stdout.write(o)
     if jobs or not os.path.exists(LIB):
         tmp = LIB + ".tmp%d" % os.getpid()
-        run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
+        run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -10,9 +10,11 @@
 // level's rows are solved in parallel); the Q1 Galerkin operator is inverted
 // densely (host Cholesky); omega comes from CG-Lanczos on the device.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "hexdev.h"
@@ -109,21 +111,30 @@ std::vector<double> spd_inverse(const std::vector<double> &A, int m) {
       L[(size_t)i * m + j] = t / djj;
     }
   }
-  // columns of A^{-1} = L^{-T} L^{-1} e_c
-  std::vector<double> inv((size_t)m * m), y(m);
-  for (int c = 0; c < m; ++c) {
-    for (int i = 0; i < m; ++i) {
-      double s = i == c ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) s -= L[(size_t)i * m + k] * y[k];
-      y[i] = s / L[(size_t)i * m + i];
+  // columns of A^{-1} = L^{-T} L^{-1} e_c, independent: on host threads
+  std::vector<double> inv((size_t)m * m);
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    std::vector<double> y(m);
+    for (int c = next++; c < m; c = next++) {
+      for (int i = 0; i < m; ++i) {
+        double s = i == c ? 1.0 : 0.0;
+        for (int k = 0; k < i; ++k) s -= L[(size_t)i * m + k] * y[k];
+        y[i] = s / L[(size_t)i * m + i];
+      }
+      for (int i = m - 1; i >= 0; --i) {
+        double s = y[i];
+        for (int k = i + 1; k < m; ++k) s -= L[(size_t)k * m + i] * y[k];
+        y[i] = s / L[(size_t)i * m + i];
+      }
+      for (int i = 0; i < m; ++i) inv[(size_t)i * m + c] = y[i];
     }
-    for (int i = m - 1; i >= 0; --i) {
-      double s = y[i];
-      for (int k = i + 1; k < m; ++k) s -= L[(size_t)k * m + i] * y[k];
-      y[i] = s / L[(size_t)i * m + i];
-    }
-    for (int i = 0; i < m; ++i) inv[(size_t)i * m + c] = y[i];
-  }
+  };
+  const int nt = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), 64));
+  std::vector<std::thread> pool;
+  for (int i = 1; i < nt && m > 256; ++i) pool.emplace_back(work);
+  work();
+  for (std::thread &t : pool) t.join();
   return inv;
 }
 

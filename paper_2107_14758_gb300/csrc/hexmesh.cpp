@@ -25,9 +25,12 @@
 // eigen-index m and multiplies by the parity of s_m.
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <map>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -1000,7 +1003,12 @@ std::vector<double> star_matrix(const fdm_hexmesh *h, int k, const std::vector<i
 // star k: interior pivots D, the Cholesky factor of S_G = A_GG - A_GI D^{-1}
 // A_IG in its class's fill (L form), and the Schur-coupling form L_BB, S_TB,
 // W = (S_TT - S_TB S_BB^{-1} S_BT)^{-1}
-void factor_star(fdm_hexmesh *h, int k, const std::vector<int> &star_cells) {
+struct StarOut {
+  std::vector<double> diag, factor, sc;
+  int code = 0;
+  std::string msg;
+};
+void factor_star(const fdm_hexmesh *h, int k, const std::vector<int> &star_cells, StarOut &o) {
   const int64_t ns = h->star_ptr[k + 1] - h->star_ptr[k];
   const int nint = h->star_nint[k], nG = (int)ns - nint;
   const int64_t *rp = h->pat_rowptr.data() + h->pat_ptr[k];
@@ -1010,9 +1018,8 @@ void factor_star(fdm_hexmesh *h, int k, const std::vector<int> &star_cells) {
     const int32_t *f = std::lower_bound(cols + rp[i], cols + rp[i + 1], i);
     const double d = (f != cols + rp[i + 1] && *f == i) ? A[f - cols] : 0.0;
     if (!(d > 0.0)) fdm::fail(FDM_ENOTSPD, "fdm_hexmesh_factor: interior pivot <= 0");
-    h->diag.push_back(d);
+    o.diag.push_back(d);
   }
-  h->diag_ptr.push_back((int64_t)h->diag.size());
   // S_G, dense and symmetric
   std::vector<double> S((size_t)nG * nG, 0.0);
   for (int r = nint; r < ns; ++r)
@@ -1022,7 +1029,7 @@ void factor_star(fdm_hexmesh *h, int k, const std::vector<int> &star_cells) {
     std::vector<std::pair<int, double>> nb;
     for (int64_t t = rp[i]; t < rp[i + 1]; ++t)
       if (cols[t] >= nint) nb.push_back({cols[t] - nint, A[t]});
-    const double d = h->diag[h->diag_ptr[k] + i];
+    const double d = o.diag[i];
     for (auto &a : nb)
       for (auto &b : nb) S[(size_t)a.first * nG + b.first] -= a.second * b.second / d;
   }
@@ -1034,8 +1041,7 @@ void factor_star(fdm_hexmesh *h, int k, const std::vector<int> &star_cells) {
   std::vector<double> L = S;
   dense_cholesky(L, nG, "interface");
   extract_fill(L, nG, h->fill_rowptr.data() + h->fill_ptr[cls], h->fill_cols.data() + h->fill_colptr[cls], tol,
-               h->factor, "factor");
-  h->factor_ptr.push_back((int64_t)h->factor.size());
+               o.factor, "factor");
   // the Schur-coupling form
   const int t = h->sc_t[cls], nB = nG - t;
   const int64_t *rpb = h->sc_rowptr.data() + h->sc_ptr[cls];
@@ -1046,9 +1052,9 @@ void factor_star(fdm_hexmesh *h, int k, const std::vector<int> &star_cells) {
   for (int r = 0; r < nB; ++r)
     for (int c = 0; c <= r; ++c) LB[(size_t)r * nB + c] = S[(size_t)r * nG + c];
   dense_cholesky(LB, nB, "lower-block");
-  extract_fill(LB, nB, rpb, cb, tol, h->sc_values, "lower-block");
+  extract_fill(LB, nB, rpb, cb, tol, o.sc, "lower-block");
   for (int r = 0; r < t; ++r)
-    for (int64_t q2 = rpt[r]; q2 < rpt[r + 1]; ++q2) h->sc_values.push_back(S[(size_t)(nB + r) * nG + ct[q2]]);
+    for (int64_t q2 = rpt[r]; q2 < rpt[r + 1]; ++q2) o.sc.push_back(S[(size_t)(nB + r) * nG + ct[q2]]);
   // Y = L_BB^{-1} S_BT (nB x t), C = S_TT - Y^T Y, W = C^{-1}
   std::vector<double> Y((size_t)nB * t);
   for (int j = 0; j < t; ++j)
@@ -1079,8 +1085,47 @@ void factor_star(fdm_hexmesh *h, int k, const std::vector<int> &star_cells) {
     }
   }
   for (int r = 0; r < t; ++r)
-    for (int c = 0; c <= r; ++c) h->sc_values.push_back(0.5 * (Wm[(size_t)r * t + c] + Wm[(size_t)c * t + r]));
-  h->sc_values_ptr.push_back((int64_t)h->sc_values.size());
+    for (int c = 0; c <= r; ++c) o.sc.push_back(0.5 * (Wm[(size_t)r * t + c] + Wm[(size_t)c * t + r]));
+}
+
+// factor_star over all stars on host threads (FDM_HOST_THREADS, default the
+// hardware's), each into its own buffers, concatenated in star order: the
+// result does not depend on the thread count; the first failing star in star
+// order reports its error
+void factor_stars(fdm_hexmesh *h, const std::vector<std::vector<int>> &vcells) {
+  const int nstar = (int)h->star_vertex.size();
+  std::vector<StarOut> out(nstar);
+  int nt = (int)std::thread::hardware_concurrency();
+  if (const char *s = std::getenv("FDM_HOST_THREADS")) nt = std::atoi(s);
+  nt = std::max(1, std::min({nt, 64, std::max(nstar, 1)}));
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    for (int k = next++; k < nstar; k = next++) {
+      try {
+        factor_star(h, k, vcells[h->star_vertex[k]], out[k]);
+      } catch (const fdm::Error &e) {
+        out[k].code = e.code;
+        out[k].msg = e.msg;
+      } catch (const std::exception &e) {
+        out[k].code = FDM_ENOMEM;
+        out[k].msg = std::string("fdm_hexmesh_factor: ") + e.what();
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int i = 1; i < nt; ++i) pool.emplace_back(work);
+  work();
+  for (std::thread &t : pool) t.join();
+  for (int k = 0; k < nstar; ++k)
+    if (out[k].code) fdm::fail(out[k].code, out[k].msg);
+  for (int k = 0; k < nstar; ++k) {
+    h->diag.insert(h->diag.end(), out[k].diag.begin(), out[k].diag.end());
+    h->diag_ptr.push_back((int64_t)h->diag.size());
+    h->factor.insert(h->factor.end(), out[k].factor.begin(), out[k].factor.end());
+    h->factor_ptr.push_back((int64_t)h->factor.size());
+    h->sc_values.insert(h->sc_values.end(), out[k].sc.begin(), out[k].sc.end());
+    h->sc_values_ptr.push_back((int64_t)h->sc_values.size());
+  }
 }
 
 }  // namespace
@@ -1102,7 +1147,7 @@ extern "C" int fdm_hexmesh_factor(fdm_hexmesh *h, int nv, const double *X, const
     h->diag.clear();
     h->factor.clear();
     h->sc_values.clear();
-    for (int k = 0; k < (int)h->star_vertex.size(); ++k) factor_star(h, k, vcells[h->star_vertex[k]]);
+    factor_stars(h, vcells);
   } catch (const fdm::Error &e) {
     return handle_hex(h, e);
   }
