@@ -493,8 +493,11 @@ void fdm_hexmesh_destroy(fdm_hexmesh *h);
  *   hex_asm_apply: one damped sweep z = omega sum_v R_v^T A~_v^{-1} R_v r of the
  *     vertex-star relaxation with the averaged surrogate (Sec. 2.7) in the glued
  *     FDM basis: per-cell basis change and Schur condensation, exact interface
- *     solves in the Schur-coupling form (FDM_HQ_SC_*), per-cell back-substitution
- *     and basis change back; in opt.precision;
+ *     solves, per-cell back-substitution and basis change back; in opt.precision.
+ *     The interface solve uses the dense inverse of each star's interface Schur
+ *     complement (lower triangle, formed at set-up from its Cholesky factor;
+ *     default) or, with opt.patch_form = 2, the Schur-coupling form (FDM_HQ_SC_*)
+ *     with level-scheduled sparse solves with L_BB;
  *   hex_pc_apply: the hybrid V(1,1) with the Q1 coarse space (dense inverse of
  *     FDM_HQ_COARSE), or opt.pc = FDM_PC_ASM / FDM_PC_NONE;
  *   hex_pcg_solve: PCG from x = 0 to ||b - A x|| <= rtol ||b|| (FP64), as pcg_solve.

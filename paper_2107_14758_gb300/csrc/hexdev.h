@@ -32,6 +32,7 @@ struct HexClassDev {
   int lev_f, rows_f, lptr, lcol, lpos, ldiag, lev_b, rows_b, tptr, trow, tpos, stptr, stcol, sbtptr, sbtrow,
       sbtpos;
   int off_st, off_w;
+  int zoff;  // dense form: int offset of the row offsets [nG + 1] of the lower triangle of S_G^{-1}
 };
 
 template <typename T>
@@ -77,6 +78,10 @@ template <typename T>
 void launch_hex_assemble(const HexDev<T> &d, const T *CE, T *rc, cudaStream_t st);
 template <typename T>
 void launch_hex_star_solve(const HexDev<T> &d, const T *rc, T *X, int maxG, cudaStream_t st);
+// the dense form: x_G = S_G^{-1} g_G with the lower triangle of S_G^{-1} by rows
+// (row r at zoff[r], padded to a multiple of 4 values)
+template <typename T>
+void launch_hex_star_dense(const HexDev<T> &d, const T *rc, T *X, int maxG, cudaStream_t st);
 template <typename T>
 void launch_hex_slot_stars(const HexDev<T> &d, const T *X, T *zf, cudaStream_t st);
 template <typename T, typename Tout>

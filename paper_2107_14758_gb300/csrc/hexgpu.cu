@@ -28,6 +28,7 @@ struct fdm_hexgpu {
   fdm_options opt{};
   int p = 0, n = 0, nc = 0, nv = 0, nstar = 0, nco = 0, maxG = 0;
   int64_t nnode = 0, nxtot = 0, nval = 0;
+  bool dense = true;  // interface solves with the dense S_G^{-1} (else the Schur-coupling form)
   std::vector<void *> allocs;
   size_t alloc_bytes = 0;
   HexDev<double> d64;
@@ -136,6 +137,85 @@ std::vector<double> spd_inverse(const std::vector<double> &A, int m) {
   work();
   for (std::thread &t : pool) t.join();
   return inv;
+}
+
+// the lower triangle of S^{-1} = L^{-T} L^{-1} by rows (row r at zoff[r],
+// padded with zeros to zoff[r + 1]) from the Cholesky factor L (m x m, dense,
+// row-major): Z = L^{-1} by row updates, then S^{-1} = Z^T Z
+void dense_inverse_rows(const std::vector<double> &L, int m, const std::vector<int> &zoff, double *out) {
+  std::vector<double> Z((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) {
+    double *zi = Z.data() + (size_t)i * m;
+    zi[i] = 1.0;
+    for (int k = 0; k < i; ++k) {
+      const double l = L[(size_t)i * m + k];
+      if (l == 0.0) continue;
+      const double *zk = Z.data() + (size_t)k * m;
+      for (int j = 0; j <= k; ++j) zi[j] -= l * zk[j];
+    }
+    const double inv = 1.0 / L[(size_t)i * m + i];
+    for (int j = 0; j <= i; ++j) zi[j] *= inv;
+  }
+  for (int r = 0; r < m; ++r)
+    for (int q = zoff[r]; q < zoff[r + 1]; ++q) out[q] = 0.0;
+  for (int k = 0; k < m; ++k) {  // S^{-1}[i][j] = sum_{k >= i} Z[k][i] Z[k][j], j <= i
+    const double *zk = Z.data() + (size_t)k * m;
+    for (int i = 0; i <= k; ++i) {
+      const double a = zk[i];
+      if (a == 0.0) continue;
+      double *row = out + zoff[i];
+      for (int j = 0; j <= i; ++j) row[j] += a * zk[j];
+    }
+  }
+}
+
+// the dense interface inverses of all stars (host threads), values in star
+// order at voff; per class the row offsets appended to ct
+void build_dense(fdm_hexgpu *c, const fdm_hexmesh *h, std::vector<HexStarDev> &stars, std::vector<HexClassDev> &classes,
+                 const std::vector<int> &cls_nG, std::vector<int> &ct, std::vector<double> &vals) {
+  const int ncls = (int)classes.size();
+  std::vector<std::vector<int>> zoff(ncls);
+  for (int cl = 0; cl < ncls; ++cl) {
+    const int m = std::max(cls_nG[cl], 0);
+    zoff[cl].assign(m + 1, 0);
+    for (int r = 0; r < m; ++r) zoff[cl][r + 1] = zoff[cl][r] + ((r + 1 + 3) & ~3);
+    classes[cl].zoff = (int)ct.size();
+    ct.insert(ct.end(), zoff[cl].begin(), zoff[cl].end());
+  }
+  int64_t off = 0;
+  for (HexStarDev &S : stars) {
+    S.voff = off;
+    off += zoff[S.cls].back();
+  }
+  vals.assign((size_t)std::max<int64_t>(off, 1), 0.0);
+  std::atomic<int> next{0};
+  std::vector<std::string> errs(stars.size());
+  auto work = [&]() {
+    for (int k = next++; k < (int)stars.size(); k = next++) {
+      const HexStarDev &S = stars[k];
+      const int m = S.nG;
+      if (m == 0) continue;
+      const int64_t *rp = h->fill_rowptr.data() + h->fill_ptr[S.cls];
+      const int32_t *cols = h->fill_cols.data() + h->fill_colptr[S.cls];
+      const double *fv = h->factor.data() + h->factor_ptr[k];
+      if (h->factor_ptr[k + 1] - h->factor_ptr[k] != rp[m]) {
+        errs[k] = "fdm_hex_setup: star " + std::to_string(k) + " has a factor of another pattern";
+        continue;
+      }
+      std::vector<double> L((size_t)m * m, 0.0);
+      for (int r = 0; r < m; ++r)
+        for (int64_t q = rp[r]; q < rp[r + 1]; ++q) L[(size_t)r * m + cols[q]] = fv[q];
+      dense_inverse_rows(L, m, zoff[S.cls], vals.data() + S.voff);
+    }
+  };
+  const int nt = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), 64));
+  std::vector<std::thread> pool;
+  for (int i = 1; i < nt; ++i) pool.emplace_back(work);
+  work();
+  for (std::thread &t : pool) t.join();
+  for (const std::string &e : errs)
+    if (!e.empty()) fail(FDM_EINVAL, e);
+  c->nval = off;
 }
 
 // the class tables of the stars' interface solves, concatenated into ct
@@ -262,7 +342,8 @@ void hex_mask(fdm_hexgpu *c, double *v, cudaStream_t st) {
 // the device view in precision T of the host tables (integer maps shared)
 template <typename T>
 void fill_dev(fdm_hexgpu *c, const fdm_hexmesh *h, HexDev<T> &d, const HexDev<double> &base,
-              const std::vector<double> &tab, const std::vector<double> &inv_mult, const std::vector<double> &Ainv) {
+              const std::vector<double> &tab, const std::vector<double> &inv_mult, const std::vector<double> &Ainv,
+              const std::vector<double> &vals) {
   d = HexDev<T>();
   d.p = base.p;
   d.n = base.n;
@@ -295,7 +376,7 @@ void fill_dev(fdm_hexgpu *c, const fdm_hexmesh *h, HexDev<T> &d, const HexDev<do
   d.mu = c->upload(conv<T>(h->mu));
   d.tab = c->upload(conv<T>(tab));
   d.geom = c->upload(conv<T>(h->geom));
-  d.vals = c->upload(conv<T>(h->sc_values));
+  d.vals = c->upload(conv<T>(vals));
   d.Acinv = c->upload(conv<T>(Ainv));
 }
 
@@ -363,6 +444,9 @@ void setup(fdm_hexgpu *c, const fdm_hexmesh *h, cudaStream_t st) {
       fail(FDM_EINVAL, "fdm_hex_setup: star " + std::to_string(k) + " has values of another layout");
   }
   c->nval = (int64_t)h->sc_values.size();
+  c->dense = c->opt.patch_form != 2;
+  std::vector<double> dvals;
+  if (c->dense) build_dense(c, h, stars, classes, cls_nG, ct, dvals);
   // coarse space: unknowns, their vertices and cells, the dense inverse
   int nco = 0;
   for (int v = 0; v < h->nv; ++v) nco = std::max(nco, h->coarse_of[v] + 1);
@@ -409,8 +493,9 @@ void setup(fdm_hexgpu *c, const fdm_hexmesh *h, cudaStream_t st) {
   b.vcell = c->upload(vcell.empty() ? std::vector<int>{0} : vcell);
   b.coarse_vertex = c->upload(coarse_vertex);
   const HexDev<double> base = b;
-  fill_dev<double>(c, h, c->d64, base, tab, inv_mult, Ainv);
-  fill_dev<float>(c, h, c->d32, base, tab, inv_mult, Ainv);
+  const std::vector<double> &vals = c->dense ? dvals : h->sc_values;
+  fill_dev<double>(c, h, c->d64, base, tab, inv_mult, Ainv, vals);
+  fill_dev<float>(c, h, c->d32, base, tab, inv_mult, Ainv, vals);
   // work vectors
   const int64_t ne = (int64_t)nc * n3, nn = h->nnode, nx = std::max<int64_t>(c->nxtot, 1);
   const bool fp32 = c->opt.precision == FDM_PREC_FP32;
@@ -458,7 +543,8 @@ void hex_asm(fdm_hexgpu *c, const T *r, T *z, double omega, cudaStream_t st) {
   const HexDev<T> &d = c->dev<T>();
   launch_hex_restrict<T, T>(d, r, c->E<T>(), st);
   launch_hex_assemble<T>(d, c->E<T>(), c->rc<T>(), st);
-  launch_hex_star_solve<T>(d, c->rc<T>(), c->X<T>(), c->maxG, st);
+  if (c->dense) launch_hex_star_dense<T>(d, c->rc<T>(), c->X<T>(), c->maxG, st);
+  else launch_hex_star_solve<T>(d, c->rc<T>(), c->X<T>(), c->maxG, st);
   launch_hex_slot_stars<T>(d, c->X<T>(), c->zf<T>(), st);
   launch_hex_interp<T, T>(d, c->E<T>(), c->zf<T>(), omega, z, st);
   c->launches += 5;

@@ -459,3 +459,132 @@ FDM_HEX_INST(double)
 FDM_HEX_INST(float)
 
 }  // namespace fdm
+
+namespace fdm {
+namespace {
+
+template <typename T> struct H4 { T x, y, z, w; };
+__device__ __forceinline__ H4<float> ld4g(const float *p) {
+  const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+  return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ H4<double> ld4g(const double *p) {
+  const double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+  return {a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ H4<float> ld4s(const float *p) {
+  const float4 v = *reinterpret_cast<const float4 *>(p);
+  return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ H4<double> ld4s(const double *p) {
+  const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+  return {a.x, a.y, b.x, b.y};
+}
+
+// one CTA of 8 warps per star: x = S^{-1} g with the lower triangle of the
+// symmetric S^{-1} by rows.  Warp w takes the row blocks w, w + 8, ... (RB
+// rows each); lane l owns the column groups q4 = l + 32 q (q < NQ), reads them
+// for each row, adds the row dot (warp sum) and keeps the strictly lower
+// entries times g_r as column sums in registers; the warps' column sums are
+// added in warp order after the row dots (deterministic).
+template <typename T, int NQ, int RB>
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : (NQ >= 8 ? 2 : 3)) k_hex_star_dense(HexDev<T> d, const T *__restrict__ rc,
+                                                                          T *__restrict__ X, int cap) {
+  extern __shared__ __align__(16) unsigned char smem_[];
+  const HexStarDev S = d.stars[blockIdx.x];
+  const int nG = S.nG;
+  if (nG == 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T *g = reinterpret_cast<T *>(smem_), *x = g + cap, *colbuf = x + cap;  // colbuf [8][cap]
+  const int *zoff = d.ct + d.classes[S.cls].zoff;
+  const T *Wv = d.vals + S.voff;
+  const int *nodes = d.star_nodes + S.nodes_off + S.ni;
+  for (int j = threadIdx.x; j < cap; j += blockDim.x) g[j] = j < nG ? rc[nodes[j]] : T(0);
+  __syncthreads();
+  T cacc[NQ][4];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) cacc[q][i] = 0;
+  for (int r0 = warp * RB; r0 < nG; r0 += 8 * RB) {
+    H4<T> wr[RB][NQ];
+    T gr[RB];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int r = r0 + u < nG ? r0 + u : nG - 1;
+      const int z0 = __ldg(zoff + r), ng = r0 + u < nG ? (__ldg(zoff + r + 1) - z0) / 4 : 0;
+      gr[u] = r0 + u < nG ? g[r] : T(0);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int q4 = lane + 32 * q;
+        wr[u][q] = q4 < ng ? ld4g(Wv + z0 + 4 * q4) : H4<T>{0, 0, 0, 0};
+      }
+    }
+    T rs[RB];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int r = r0 + u;
+      T s = 0;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int cb = 4 * (lane + 32 * q);
+        const H4<T> &w = wr[u][q];
+        if (cb < cap) {
+          const H4<T> v = ld4s(g + cb);
+          s += w.x * v.x + w.y * v.y + w.z * v.z + w.w * v.w;
+        }
+        cacc[q][0] += (cb < r ? w.x : T(0)) * gr[u];
+        cacc[q][1] += (cb + 1 < r ? w.y : T(0)) * gr[u];
+        cacc[q][2] += (cb + 2 < r ? w.z : T(0)) * gr[u];
+        cacc[q][3] += (cb + 3 < r ? w.w : T(0)) * gr[u];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      rs[u] = s;
+    }
+    if (lane < RB && r0 + lane < nG) {
+      T s = rs[0];
+#pragma unroll
+      for (int u = 1; u < RB; ++u) s = lane == u ? rs[u] : s;
+      x[r0 + lane] = s;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int cb = 4 * (lane + 32 * q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (cb + i < cap) colbuf[warp * cap + cb + i] = cacc[q][i];
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < nG; c += blockDim.x) {
+    T s = x[c];
+    for (int w = 0; w < 8; ++w) s += colbuf[w * cap + c];
+    X[S.xoff + c] = s;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void launch_hex_star_dense(const HexDev<T> &d, const T *rc, T *X, int maxG, cudaStream_t st) {
+  if (d.nstar <= 0) return;
+  const int cap = (maxG + 3) & ~3;
+  const size_t sm = sizeof(T) * 10 * (size_t)cap;
+  if (maxG <= 256) {
+    hex_set_smem(k_hex_star_dense<T, 2, 4>, sm);
+    k_hex_star_dense<T, 2, 4><<<d.nstar, 256, sm, st>>>(d, rc, X, cap);
+  } else if (maxG <= 512) {
+    hex_set_smem(k_hex_star_dense<T, 4, 2>, sm);
+    k_hex_star_dense<T, 4, 2><<<d.nstar, 256, sm, st>>>(d, rc, X, cap);
+  } else if (maxG <= 1024) {
+    hex_set_smem(k_hex_star_dense<T, 8, 1>, sm);
+    k_hex_star_dense<T, 8, 1><<<d.nstar, 256, sm, st>>>(d, rc, X, cap);
+  } else {
+    fail(FDM_EINVAL, "dense star solve: interface larger than 1024");
+  }
+}
+template void launch_hex_star_dense<double>(const HexDev<double> &, const double *, double *, int, cudaStream_t);
+template void launch_hex_star_dense<float>(const HexDev<float> &, const float *, float *, int, cudaStream_t);
+
+}  // namespace fdm

@@ -974,10 +974,11 @@ class HexGpu:
     of HexMesh.nnode values in the mesh's node numbering."""
 
     def __init__(self, mesh, precision=FDM_PREC_FP64, pc=FDM_PC_VCYCLE, omega=0.0, lanczos_start=None,
-                 lanczos_steps=20, flexible_beta=-1, stream=None):
+                 lanczos_steps=20, flexible_beta=-1, patch_form=0, stream=None):
         opt = fdm_default_options()
         opt.precision, opt.pc, opt.omega, opt.lanczos_steps = precision, pc, omega, lanczos_steps
         opt.flexible_beta = flexible_beta
+        opt.patch_form = patch_form
         self._keep = []
         if lanczos_start is not None:
             st = np.ascontiguousarray(lanczos_start, dtype=np.float64)

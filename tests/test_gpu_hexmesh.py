@@ -85,17 +85,40 @@ def test_stiffness_apply(fdmpc, name, p):
 
 @pytest.mark.parametrize("name", sorted(MESHES))
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
-def test_relaxation_sweep(fdmpc, name, p):
+@pytest.mark.parametrize("form", [0, 2])
+def test_relaxation_sweep(fdmpc, name, p, form):
+    """Both interface-solve forms: the dense inverse of the star's interface
+    Schur complement (form 0) and the Schur-coupling form with level-scheduled
+    sparse solves (form 2)."""
     H, U, pi = _setup(fdmpc, name, p, kappa_seed=20 + p)
     r = np.random.default_rng(p).standard_normal(U.ndof)
     want = 0.7 * U.asm(r)[pi]
     for prec, tol in ((fdmpc.FDM_PREC_FP64, 1e-11), (fdmpc.FDM_PREC_FP32, 1e-4)):
-        G = fdmpc.HexGpu(H, precision=prec, omega=0.7, pc=fdmpc.FDM_PC_ASM)
+        G = fdmpc.HexGpu(H, precision=prec, omega=0.7, pc=fdmpc.FDM_PC_ASM, patch_form=form)
         z = _N(G.asm_apply(_T(r[pi])))
-        record("hex_asm_%s_p%d_%s" % (name, p, "fp64" if prec == fdmpc.FDM_PREC_FP64 else "fp32"),
+        record("hex_asm_%s_p%d_%s_form%d" % (name, p, "fp64" if prec == fdmpc.FDM_PREC_FP64 else "fp32", form),
                relerr=_relerr(z, want))
         assert _relerr(z, want) <= tol
         G.close()
+
+
+def test_dense_form_on_the_largest_stars(fdmpc):
+    """The dense form's widest register column sums (interfaces above 512):
+    p = 6 on the m = 3 unstructured mesh (largest interface 571) against the
+    Schur-coupling form's sweep (both exact star solves, each pinned to the
+    oracle on the meshes above), FP64."""
+    X, cells = inputs.unstructured_hex_mesh(3, 2, 5)
+    H = fdmpc.HexMesh(X.shape[0], cells, 6)
+    H.factor(X)
+    r = _T(np.random.default_rng(77).standard_normal(H.nnode))
+    out = []
+    for form in (0, 2):
+        G = fdmpc.HexGpu(H, omega=1.0, pc=fdmpc.FDM_PC_ASM, patch_form=form)
+        assert G.sizes()[5] > 512
+        out.append(_N(G.asm_apply(r)))
+        G.close()
+    record("hex_asm_dense_vs_sc_p6", relerr=_relerr(out[0], out[1]))
+    assert _relerr(out[0], out[1]) <= 1e-11
 
 
 @pytest.mark.parametrize("name", sorted(MESHES))
