@@ -90,8 +90,9 @@ template <typename T, typename Tin>
 void launch_hex_op_cells(const HexDev<T> &d, const Tin *u, T *Y, cudaStream_t st);
 template <typename T, typename Tout>
 void launch_hex_gather(const HexDev<T> &d, const T *Y, const Tout *rsub, Tout *y, cudaStream_t st);
+// rc = P^T r (Cc: [nc][8] per-cell corner sums, scratch)
 template <typename T>
-void launch_hex_coarse_restrict(const HexDev<T> &d, const T *r, T *rc, cudaStream_t st);
+void launch_hex_coarse_restrict(const HexDev<T> &d, const T *r, T *Cc, T *rc, cudaStream_t st);
 template <typename T>
 void launch_hex_coarse_prolong(const HexDev<T> &d, const T *xc, T *x, cudaStream_t st);  // x += P xc
 

@@ -557,10 +557,10 @@ void hex_vcycle(fdm_hexgpu *c, const T *r, T *z, T *x1, T *t, T *w, T *cr, T *cx
   hex_asm<T>(c, r, x1, c->omega, st);
   hex_op<T>(c, x1, r, t, st);
   if (c->nco > 0) {
-    launch_hex_coarse_restrict<T>(c->dev<T>(), t, cr, st);
+    launch_hex_coarse_restrict<T>(c->dev<T>(), t, c->Y<T>(), cr, st);  // Y: scratch of the corner sums
     launch_dense_symv<T>(c->nco, c->dev<T>().Acinv, cr, cx, st);
     launch_hex_coarse_prolong<T>(c->dev<T>(), cx, x1, st);
-    c->launches += 3;
+    c->launches += 4;
   }
   hex_op<T>(c, x1, r, t, st);
   hex_asm<T>(c, t, w, c->omega, st);

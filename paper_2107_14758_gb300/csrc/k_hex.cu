@@ -373,23 +373,49 @@ __device__ __forceinline__ T hat_at(const T *xi, int n, int l, int corner) {
   return hx * hy * hz;
 }
 
-// rc = P^T r: per coarse unknown, its Q1 function times r over the cells
-// around its vertex (r / multiplicity counts every node once)
+// rc = P^T r in two deterministic steps: per cell (one CTA) the 8 corner
+// sums C_e[c] = sum_l hat_c(l) r_l / multiplicity_l over its nodes (a fixed
+// tree over the threads), then per coarse unknown the sum of C over the
+// (cell, corner) pairs of its vertex in cell order (r / multiplicity counts
+// every node once)
 template <typename T>
-__global__ void k_hex_coarse_restrict(HexDev<T> d, const T *__restrict__ r, T *__restrict__ rc) {
+__global__ void __launch_bounds__(128) k_hex_coarse_cells(HexDev<T> d, const T *__restrict__ r, T *__restrict__ Cc) {
+  __shared__ T red[8][128];
+  const int n = d.n, n3 = n * n * n, e = blockIdx.x, tid = threadIdx.x;
+  const T *xi = d.tab + htab(HTAB_XI, n);
+  const int *cn = d.cell_nodes + (int64_t)e * n3;
+  T acc[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc[c] = 0;
+  for (int l = tid; l < n3; l += 128) {
+    const int g = cn[l];
+    if (d.dirichlet[g]) continue;
+    const T v = r[g] * d.inv_mult[g];
+    const int i = l % n, j = (l / n) % n, k = l / (n * n);
+    const T hx[2] = {T(0.5) * (T(1) - xi[i]), T(0.5) * (T(1) + xi[i])};
+    const T hy[2] = {T(0.5) * (T(1) - xi[j]), T(0.5) * (T(1) + xi[j])};
+    const T hz[2] = {T(0.5) * (T(1) - xi[k]), T(0.5) * (T(1) + xi[k])};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] += hx[c & 1] * hy[(c >> 1) & 1] * hz[c >> 2] * v;
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) red[c][tid] = acc[c];
+  __syncthreads();
+  for (int w = 64; w > 0; w >>= 1) {
+    if (tid < w)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) red[c][tid] += red[c][tid + w];
+    __syncthreads();
+  }
+  if (tid < 8) Cc[8 * (int64_t)e + tid] = red[tid][0];
+}
+
+template <typename T>
+__global__ void k_hex_coarse_sum(HexDev<T> d, const T *__restrict__ Cc, T *__restrict__ rc) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= d.nco) return;
-  const int n = d.n, n3 = n * n * n;
-  const T *xi = d.tab + htab(HTAB_XI, n);
   T s = 0;
-  for (int64_t q = d.vcell_ptr[k]; q < d.vcell_ptr[k + 1]; ++q) {
-    const int e = d.vcell[q] >> 3, corner = d.vcell[q] & 7;
-    const int *cn = d.cell_nodes + (int64_t)e * n3;
-    for (int l = 0; l < n3; ++l) {
-      const int g = cn[l];
-      if (!d.dirichlet[g]) s += hat_at(xi, n, l, corner) * r[g] * d.inv_mult[g];
-    }
-  }
+  for (int64_t q = d.vcell_ptr[k]; q < d.vcell_ptr[k + 1]; ++q) s += Cc[d.vcell[q]];
   rc[k] = s;
 }
 
@@ -434,9 +460,10 @@ void launch_hex_gather(const HexDev<T> &d, const T *Y, const Tout *rsub, Tout *y
 }
 
 template <typename T>
-void launch_hex_coarse_restrict(const HexDev<T> &d, const T *r, T *rc, cudaStream_t st) {
+void launch_hex_coarse_restrict(const HexDev<T> &d, const T *r, T *Cc, T *rc, cudaStream_t st) {
   if (d.nco <= 0) return;
-  k_hex_coarse_restrict<T><<<(d.nco + 127) / 128, 128, 0, st>>>(d, r, rc);
+  k_hex_coarse_cells<T><<<d.nc, 128, 0, st>>>(d, r, Cc);
+  k_hex_coarse_sum<T><<<(d.nco + 127) / 128, 128, 0, st>>>(d, Cc, rc);
 }
 
 template <typename T>
@@ -453,7 +480,7 @@ void launch_hex_coarse_prolong(const HexDev<T> &d, const T *xc, T *x, cudaStream
   template void launch_hex_interp<T, T>(const HexDev<T> &, const T *, const T *, double, T *, cudaStream_t); \
   template void launch_hex_op_cells<T, T>(const HexDev<T> &, const T *, T *, cudaStream_t);               \
   template void launch_hex_gather<T, T>(const HexDev<T> &, const T *, const T *, T *, cudaStream_t);       \
-  template void launch_hex_coarse_restrict<T>(const HexDev<T> &, const T *, T *, cudaStream_t);            \
+  template void launch_hex_coarse_restrict<T>(const HexDev<T> &, const T *, T *, T *, cudaStream_t);       \
   template void launch_hex_coarse_prolong<T>(const HexDev<T> &, const T *, T *, cudaStream_t);
 FDM_HEX_INST(double)
 FDM_HEX_INST(float)
