@@ -162,6 +162,11 @@ typedef struct {
                          3 = two rows, only the lower-block values staged (six CTAs per SM);
                          4 = two rows, nothing staged, the patch's whole value block prefetched
                          into L2 when its CTA starts (six CTAs per SM) */
+  int tensor_core;    /* 1: the SIPG star solves of the FP32 preconditioner (and sipg_patch_solve in
+                         FP32) run their six 1D contractions on the tensor cores (tcgen05.mma,
+                         TF32 inputs rounded to nearest, FP32 accumulation in tensor memory); DQ_7
+                         only (FDM_EINVAL at set-up otherwise); a completion wait that runs out
+                         gives FDM_ETIMEOUT.  0 (default): FP32 CUDA-core contractions */
 } fdm_options;
 
 /* Fills the defaults listed above. */

@@ -225,6 +225,12 @@ void launch_sipg_op(const SipgDev<T> &d, const Tin *u, T *F, const double *rsub,
 template <typename T, typename Tin, typename Tout>
 void launch_sipg_patch(const SipgDev<T> &d, int color, int nblocks, const int *vlist, const Tin *r, Tout *z,
                        T *zpatch, double omega, cudaStream_t st);
+// the same stars' solves with the six 1D contractions on the tensor cores
+// (tcgen05, TF32 in, FP32 accumulation); DQ_7 only; status: 1 when a bounded
+// completion wait ran out
+template <typename Tin, typename Tout>
+void launch_sipg_patch_tc(const SipgDev<float> &d, int color, int nblocks, const int *vlist, const Tin *r, Tout *z,
+                          float *zpatch, double omega, uint64_t timeout_ns, int *status, cudaStream_t st);
 template <typename T, typename Tin>
 void launch_sipg_restrict(const SipgDev<T> &d, const Tin *r, const int *cfree, T *cellbuf, T *rc, cudaStream_t st);
 template <typename T>

@@ -38,6 +38,8 @@ struct fdm_sipg {
   float *f1 = nullptr, *f3 = nullptr, *zp32 = nullptr;
   double *partial = nullptr, *dots = nullptr, *sc = nullptr;
   int *vlist = nullptr;
+  int *status = nullptr;  // 1 when a bounded wait of the tensor-core star solve ran out
+  bool tc = false;        // star solves of the FP32 preconditioner on the tensor cores
   int vcap = 0;
   int64_t zcap = 0;
   int64_t launches = 0;
@@ -84,6 +86,19 @@ void sipg_op(fdm_sipg *s, const Tin *u, T *y, const double *rsub, cudaStream_t s
   s->launches += 2;
 }
 
+uint64_t sipg_timeout_ns(const fdm_sipg *s) { return (uint64_t)(std::max(s->opt.wait_timeout_s, 0.0) * 1e9); }
+
+// the status word of the bounded waits: FDM_ETIMEOUT (and cleared) when set
+void sipg_check_status(fdm_sipg *s) {
+  if (!s->status) return;
+  int h = 0;
+  FDM_CUDA(cudaMemcpy(&h, s->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    FDM_CUDA(cudaMemset(s->status, 0, sizeof(int)));
+    fail(FDM_ETIMEOUT, "a bounded wait of the tensor-core star solve ran out");
+  }
+}
+
 // z = omega ASM(r) (+ addv): the 8 vertex parity classes in a fixed order
 template <typename T, typename Tin, typename Tout>
 void sipg_asm(fdm_sipg *s, const Tin *r, Tout *z, double omega, cudaStream_t st, const T *addv = nullptr) {
@@ -97,6 +112,14 @@ void sipg_asm(fdm_sipg *s, const Tin *r, Tout *z, double omega, cudaStream_t st,
   }
   for (int color = 0; color < 8; ++color)
     if (s->color_blocks[color] > 0) {
+      if constexpr (std::is_same<T, float>::value) {
+        if (s->tc) {
+          launch_sipg_patch_tc<Tin, Tout>(s->d32, color, s->color_blocks[color], nullptr, r, z, nullptr, omega,
+                                          sipg_timeout_ns(s), s->status, st);
+          s->launches += 1;
+          continue;
+        }
+      }
       launch_sipg_patch<T, Tin, Tout>(s->dev<T>(), color, s->color_blocks[color], nullptr, r, z, nullptr, omega, st);
       s->launches += 1;
     }
@@ -245,6 +268,9 @@ int fdm_sipg_setup(const fdm_mesh *mesh, int p, double eta, const fdm_options *o
     s->p = p;
     s->n = p + 1;
     s->eta = eta > 0.0 ? eta : p * (p + 1.0);
+    if (s->opt.tensor_core && p != 7)
+      fail(FDM_EINVAL, "fdm_sipg_setup: the tensor-core star solve covers DQ_7 (p = 7) only");
+    s->tc = s->opt.tensor_core != 0;
     for (int a = 0; a < 3; ++a) s->nc[a] = ncs[a];
     const int n = s->n, m = 2 * n, ncell = ncs[0] * ncs[1] * ncs[2];
     s->ndof = (int64_t)ncell * n * n * n;
@@ -299,6 +325,8 @@ int fdm_sipg_setup(const fdm_mesh *mesh, int p, double eta, const fdm_options *o
       s->color_blocks[color] = cnt;
     }
     const size_t fn = (size_t)ncell * 12 * n * n;
+    s->status = s->alloc<int>(1);
+    FDM_CUDA(cudaMemset(s->status, 0, sizeof(int)));
     s->F64 = s->alloc<double>(fn);
     s->cb64 = s->alloc<double>(8 * (size_t)ncell);
     s->cb32 = s->alloc<float>(8 * (size_t)ncell);
@@ -379,7 +407,10 @@ int sipg_patch_solve(fdm_sipg *s, const double *r, int nv, const int *vertices, 
         s->zp32 = s->alloc<float>((size_t)nv * m3);
         s->zcap = (int64_t)nv * m3;
       }
-      launch_sipg_patch<float, double, float>(s->d32, 0, nv, s->vlist, r, s->f1, s->zp32, 1.0, st);
+      if (s->tc)
+        launch_sipg_patch_tc<double, float>(s->d32, 0, nv, s->vlist, r, s->f1, s->zp32, 1.0, sipg_timeout_ns(s),
+                                            s->status, st);
+      else launch_sipg_patch<float, double, float>(s->d32, 0, nv, s->vlist, r, s->f1, s->zp32, 1.0, st);
       launch_convert<float, double>((int64_t)nv * m3, s->zp32, out, st);
     }
     s->launches += 1;
@@ -460,6 +491,7 @@ int sipg_pcg_solve(fdm_sipg *s, const double *b, double *x, double rtol, int max
     cudaEventDestroy(e1);
     FDM_CUDA(cudaMemcpy(hsc, s->sc, sizeof hsc, cudaMemcpyDeviceToHost));
     if (hsc[8] != 0.0) bad = 1;
+    sipg_check_status(s);
     if (info) {
       info->iterations = it;
       info->converged = conv;
@@ -490,6 +522,13 @@ int fdm_sipg_query(fdm_sipg *s, int what, void *out, size_t *len) {
     };
     switch (what) {
       case FDM_Q_NDOF: { int64_t v = s->ndof; put(&v, sizeof v); break; }
+      case FDM_Q_STATUS: {  // the tensor-core star solve's status word (read and cleared)
+        int v = 0;
+        FDM_CUDA(cudaMemcpy(&v, s->status, sizeof(int), cudaMemcpyDeviceToHost));
+        FDM_CUDA(cudaMemset(s->status, 0, sizeof(int)));
+        put(&v, sizeof v);
+        break;
+      }
       case FDM_Q_OMEGA: put(&s->omega, sizeof(double)); break;
       case FDM_Q_LAMBDA: { double v[2] = {s->lmin, s->lmax}; put(v, sizeof v); break; }
       case FDM_Q_LAUNCHES: { int64_t v = s->launches; s->launches = 0; put(&v, sizeof v); break; }

@@ -60,7 +60,7 @@ class fdm_options(C.Structure):
                 ("inject_stall", C.c_int), ("patch_prefetch", C.c_int), ("pcg_graph", C.c_int),
                 ("patch_l2_hints", C.c_int), ("autotune", C.c_int), ("patch_rows_per_warp", C.c_int),
                 ("patch_form", C.c_int), ("coarse_levels", C.c_int), ("gmg_nu", C.c_int),
-                ("gmg_omega", C.c_double), ("sc_variant", C.c_int)]
+                ("gmg_omega", C.c_double), ("sc_variant", C.c_int), ("tensor_core", C.c_int)]
 
 
 class fdm_solve_info(C.Structure):
@@ -680,7 +680,8 @@ class Sipg:
     device (ndof = cells * (p+1)^3)."""
 
     def __init__(self, p, xv, yv, zv, eta=0.0, precision=FDM_PREC_FP32, pc=FDM_PC_VCYCLE, omega=0.0,
-                 lanczos_start=None, lanczos_steps=20, flexible_beta=-1, coarse_levels=-1, stream=None):
+                 lanczos_start=None, lanczos_steps=20, flexible_beta=-1, coarse_levels=-1, tensor_core=0,
+                 wait_timeout_s=1.0, stream=None):
         self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (xv, yv, zv)]
         mesh = fdm_mesh()
         mesh.nx, mesh.ny, mesh.nz = len(xv) - 1, len(yv) - 1, len(zv) - 1
@@ -689,6 +690,8 @@ class Sipg:
         opt.precision, opt.pc, opt.omega, opt.lanczos_steps = precision, pc, omega, lanczos_steps
         opt.flexible_beta = flexible_beta
         opt.coarse_levels = coarse_levels
+        opt.tensor_core = tensor_core
+        opt.wait_timeout_s = wait_timeout_s
         if lanczos_start is not None:
             s = np.ascontiguousarray(lanczos_start, dtype=np.float64)
             self._keep.append(s)
@@ -757,6 +760,12 @@ class Sipg:
     def launches(self):
         out = np.zeros(1, dtype=np.int64)
         fdm_sipg_query(self.h, FDM_Q_LAUNCHES, out)
+        return int(out[0])
+
+    def status(self):
+        """The tensor-core star solve's status word (1: a bounded wait ran out); reading clears it."""
+        out = np.zeros(1, dtype=np.int32)
+        fdm_sipg_query(self.h, FDM_Q_STATUS, out)
         return int(out[0])
 
 

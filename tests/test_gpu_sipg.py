@@ -199,3 +199,57 @@ def test_zero_rhs_and_invalid():
         fdmpc.Sipg(2, [0, 1], [0, .5, 1], [0, .5, 1])
     with pytest.raises(fdmpc.FdmError):
         fdmpc.Sipg(2, [0, .5, .4], [0, .5, 1], [0, .5, 1])
+
+
+# ---------------------------------------------------------------- tensor-core star solves (DQ_7)
+# TF32 inputs rounded to nearest carry a relative error of at most u = 2^-11;
+# each of the six passes rounds its input line and its matrix (2u per product
+# term), and the eigenvector matrices are B-orthonormal rather than orthogonal
+# (a growth factor of a few through the passes): 12 u x 3 ~ 2e-2 bounds the
+# relative error of one star solve and of one relaxation sweep.
+TC_TOL = 2e-2
+
+
+def test_tensor_core_star_solves(Sipg):
+    """The tcgen05 (TF32, FP32 accumulation) star solves against the oracle's
+    dense Cholesky of the star matrix, on a graded 3^3 DQ_7 mesh (all 8
+    interior stars)."""
+    from tests.record import record
+    xv, yv, zv = inputs.graded_vertices(3, 23)
+    ref = Sipg(7, xv, yv, zv)
+    r = np.random.default_rng(24).standard_normal(ref.N)
+    verts = [(a, b, c) for c in (1, 2) for b in (1, 2) for a in (1, 2)]
+    gpu = fdmpc.Sipg(7, xv, yv, zv, precision=FP32, tensor_core=1)
+    got = N(gpu.patch_solve(T(r), verts))
+    errs = [relerr(got[k], ref.patch_solve(v, r)) for k, v in enumerate(verts)]
+    record("sipg_tc_star", worst=max(errs))
+    assert max(errs) <= TC_TOL
+    assert gpu.status() == 0
+
+
+def test_tensor_core_sweep_and_pcg():
+    """A relaxation sweep with the tensor-core star solves against the FP32
+    CUDA-core sweep (TF32 tolerance), and the mixed-precision PCG with it:
+    the FP64 true residual 1e-8 with at most one more iteration than with the
+    CUDA-core star solves."""
+    from tests.record import record
+    xv, yv, zv = inputs.graded_vertices(4, 25)
+    b = torch.randn(4 ** 3 * 512, dtype=torch.float64, device=DEV, generator=torch.Generator(device=DEV).manual_seed(3))
+    start = inputs.lanczos_start(4 ** 3 * 512)
+    cc = fdmpc.Sipg(7, xv, yv, zv, precision=FP32, lanczos_start=start)
+    tc = fdmpc.Sipg(7, xv, yv, zv, precision=FP32, lanczos_start=start, tensor_core=1)
+    z0, z1 = N(cc.asm_apply(b)), N(tc.asm_apply(b))
+    _, i0 = cc.pcg_solve(b, rtol=1e-8, maxit=500)
+    _, i1 = tc.pcg_solve(b, rtol=1e-8, maxit=500)
+    record("sipg_tc_sweep", relerr=relerr(z1, z0), its_cuda_core=i0.iterations, its_tensor_core=i1.iterations,
+           omega_rel=abs(tc.omega - cc.omega) / cc.omega)
+    assert relerr(z1, z0) <= TC_TOL
+    assert i1.converged and i1.true_rnorm <= 1e-8 * i1.rnorm0
+    assert i1.iterations <= i0.iterations + 1
+    assert tc.status() == 0
+
+
+def test_tensor_core_only_at_dq7():
+    with pytest.raises(fdmpc.FdmError) as e:
+        fdmpc.Sipg(3, *MESH, precision=FP32, tensor_core=1)
+    assert e.value.code == fdmpc.FDM_EINVAL
