@@ -73,6 +73,15 @@ def rank_rhs_seed(base_seed, rank):
     return base_seed + 1000 * rank
 
 
+def _peak_bf16():
+    """Dense bf16 tensor peak in TFLOP/s: the measured burst figure, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1900.0
+
+
 def _peak_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -636,8 +645,9 @@ def bench_sipg(dev, fdmpc, inputs):
     stars = 15 ** 3
     out = {"workload": "SIPG DQ_7, 16^3 graded cells (widths U(0.5, 1.5), seed 7), %d values, b ~ N(0,1)" % ndof}
     b = torch.randn(ndof, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(7))
-    for name, prec in (("mixed", fdmpc.FDM_PREC_FP32), ("fp64", fdmpc.FDM_PREC_FP64)):
-        s = fdmpc.Sipg(p, xv, yv, zv, precision=prec, lanczos_start=inputs.lanczos_start(ndof))
+    for name, prec, tcore in (("mixed", fdmpc.FDM_PREC_FP32, 0), ("mixed_tensor_core", fdmpc.FDM_PREC_FP32, 1),
+                              ("fp64", fdmpc.FDM_PREC_FP64, 0)):
+        s = fdmpc.Sipg(p, xv, yv, zv, precision=prec, lanczos_start=inputs.lanczos_start(ndof), tensor_core=tcore)
         x = torch.empty_like(b)
         info = s.pcg_solve(b, x, rtol=RTOL, maxit=1000)[1]
         torch.cuda.synchronize()
@@ -651,7 +661,7 @@ def bench_sipg(dev, fdmpc, inputs):
         ms = e0.elapsed_time(e1) / 3
         out[name] = {"ms_per_solve": ms, "solve_dofs_per_s": ndof / (ms * 1e-3), "iterations": info.iterations,
                      "true_rel_residual": info.true_rnorm / info.rnorm0, "omega": s.omega}
-        if name == "mixed":
+        if name.startswith("mixed"):
             z = torch.empty_like(b)
             for _ in range(3):
                 s.asm_apply(b, z)
@@ -664,12 +674,22 @@ def bench_sipg(dev, fdmpc, inputs):
             ms_sweep = e0.elapsed_time(e1) / 20
             flops = 2.0 * 6 * m ** 4 * stars
             tflops = flops / (ms_sweep * 1e-3) * 1e-12
-            out["fp32_sweep"] = {"ms": ms_sweep, "gflop": flops * 1e-9, "tflops": tflops,
-                                 "roofline": {"bound": "alu", "achieved": tflops, "peak": FP32_ALU_TFLOPS,
-                                              "unit": "TFLOP/s", "frac": tflops / FP32_ALU_TFLOPS,
-                                              "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}}
+            if tcore:  # the contractions on the tensor cores: against the TF32 tensor peak
+                tf32_peak = _peak_bf16() * 0.5
+                out["tf32_sweep"] = {"ms": ms_sweep, "gflop": flops * 1e-9, "tflops": tflops,
+                                     "roofline": {"bound": "tensor", "achieved": tflops, "peak": tf32_peak,
+                                                  "unit": "TFLOP/s", "frac": tflops / tf32_peak,
+                                                  "peak_kind": "measured dense bf16 x 0.5 (nominal TF32/BF16 "
+                                                               "ratio 1.1/2.25 PFLOP/s)"}}
+            else:
+                out["fp32_sweep"] = {"ms": ms_sweep, "gflop": flops * 1e-9, "tflops": tflops,
+                                     "roofline": {"bound": "alu", "achieved": tflops, "peak": FP32_ALU_TFLOPS,
+                                                  "unit": "TFLOP/s", "frac": tflops / FP32_ALU_TFLOPS,
+                                                  "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x "
+                                                               "2.07 GHz"}}
         s.close()
     out["mixed_over_fp64"] = out["mixed"]["solve_dofs_per_s"] / out["fp64"]["solve_dofs_per_s"]
+    out["tensor_core_over_cuda_core_sweep"] = out["fp32_sweep"]["ms"] / out["tf32_sweep"]["ms"]
     return out
 
 

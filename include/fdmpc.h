@@ -350,9 +350,16 @@ void fdm_elast_destroy(fdm_elast *e);
  * conforming problem: opt->coarse_levels); preconditioner selected by
  * opt->pc (FDM_PC_ASM: omega ASM; FDM_PC_VCYCLE: the hybrid V(1,1)) in
  * opt->precision; omega from opt->lanczos_steps CG-Lanczos steps on
- * ASM^{-1} A unless opt->omega > 0.  Errors as for the scalar problem
- * (FDM_ENOTSPD if a star pencil is not positive definite: eta too small);
- * fdm_sipg_last_error. */
+ * ASM^{-1} A unless opt->omega > 0.  A relaxation sweep solves every star in
+ * one launch into a per-star buffer ((2p+2)^3 values per star, allocated on
+ * first use) and sums each value over the stars holding it in a fixed corner
+ * order (default), or with opt->patch_kernel = 1 in eight launches, one per
+ * vertex parity class, that add into z; opt->tensor_core = 1 moves the star
+ * solves' contractions to the tensor cores (DQ_7, FP32 preconditioner).
+ * Errors as for the scalar problem (FDM_ENOTSPD if a star pencil is not
+ * positive definite: eta too small; FDM_ETIMEOUT from sipg_pcg_solve when a
+ * bounded wait of the tensor-core star solve ran out, FDM_Q_STATUS reads and
+ * clears that flag); fdm_sipg_last_error. */
 typedef struct fdm_sipg fdm_sipg;
 int fdm_sipg_setup(const fdm_mesh *mesh, int p, double eta, const fdm_options *opt, fdm_sipg **out, void *stream);
 /* y = A u */

@@ -516,6 +516,42 @@ void launch_sipg_patch(const SipgDev<T> &d, int color, int nblocks, const int *v
     fail(FDM_EINVAL, "SIPG patch solve: unsupported degree");
 }
 
+// z = (addv or 0) + omega * (sum of the star solutions holding each value),
+// the stars of all interior vertices solved in one launch into zp[star][(2n)^3]
+// (stars lexicographic over the interior vertices, star values x fastest):
+// per value the up to 8 stars of its cell's corners in a fixed order
+template <typename T, typename Tout>
+__global__ void k_sipg_star_gather(SipgDev<T> d, const T *__restrict__ zp, T omega, const T *__restrict__ addv,
+                                   Tout *__restrict__ z) {
+  const int n = d.n, n3 = n * n * n, m = 2 * n;
+  const int64_t total = (int64_t)d.ncell * n3;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int cell = (int)(idx / n3), l = (int)(idx % n3);
+    const int cx = cell % d.nx, cy = (cell / d.nx) % d.ny, cz = cell / (d.nx * d.ny);
+    const int i = l % n, j = (l / n) % n, k = l / (n * n);
+    T acc = 0;
+    for (int c = 0; c < 2; ++c)
+      for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) {
+          const int vx = cx + a, vy = cy + b, vz = cz + c;
+          if (vx < 1 || vy < 1 || vz < 1 || vx > d.nx - 1 || vy > d.ny - 1 || vz > d.nz - 1) continue;
+          const int64_t star = (vx - 1) + (int64_t)(d.nx - 1) * ((vy - 1) + (int64_t)(d.ny - 1) * (vz - 1));
+          const int X = (1 - a) * n + i, Y = (1 - b) * n + j, Z = (1 - c) * n + k;
+          acc += zp[star * m * m * m + X + m * (Y + m * Z)];
+        }
+    z[idx] = Tout((addv ? addv[idx] : T(0)) + omega * acc);
+  }
+}
+
+template <typename T, typename Tout>
+void launch_sipg_star_gather(const SipgDev<T> &d, const T *zp, double omega, const T *addv, Tout *z,
+                             cudaStream_t st) {
+  const int64_t total = (int64_t)d.ncell * d.n * d.n * d.n;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 16));
+  k_sipg_star_gather<T, Tout><<<blocks, 256, 0, st>>>(d, zp, T(omega), addv, z);
+}
+
 template <typename T, typename Tin>
 void launch_sipg_restrict(const SipgDev<T> &d, const Tin *r, const int *cfree, T *cellbuf, T *rc, cudaStream_t st) {
   if (!dispatch_sipg(d.n, [&](auto NC) {
@@ -552,6 +588,14 @@ template void launch_sipg_patch<float, float, double>(const SipgDev<float> &, in
                                                       double *, float *, double, cudaStream_t);
 template void launch_sipg_patch<float, double, double>(const SipgDev<float> &, int, int, const int *,
                                                        const double *, double *, float *, double, cudaStream_t);
+template void launch_sipg_patch<float, float, float>(const SipgDev<float> &, int, int, const int *, const float *,
+                                                     float *, float *, double, cudaStream_t);
+template void launch_sipg_star_gather<double, double>(const SipgDev<double> &, const double *, double,
+                                                     const double *, double *, cudaStream_t);
+template void launch_sipg_star_gather<float, float>(const SipgDev<float> &, const float *, double, const float *,
+                                                   float *, cudaStream_t);
+template void launch_sipg_star_gather<float, double>(const SipgDev<float> &, const float *, double, const float *,
+                                                    double *, cudaStream_t);
 template void launch_sipg_restrict<double, double>(const SipgDev<double> &, const double *, const int *, double *,
                                                    double *, cudaStream_t);
 template void launch_sipg_restrict<float, float>(const SipgDev<float> &, const float *, const int *, float *, float *,

@@ -225,6 +225,11 @@ void launch_sipg_op(const SipgDev<T> &d, const Tin *u, T *F, const double *rsub,
 template <typename T, typename Tin, typename Tout>
 void launch_sipg_patch(const SipgDev<T> &d, int color, int nblocks, const int *vlist, const Tin *r, Tout *z,
                        T *zpatch, double omega, cudaStream_t st);
+// z = (addv or 0) + omega * sum of the star solutions zp[star][(2n)^3] of all
+// interior vertices (lexicographic) holding each value, in a fixed order
+template <typename T, typename Tout>
+void launch_sipg_star_gather(const SipgDev<T> &d, const T *zp, double omega, const T *addv, Tout *z,
+                             cudaStream_t st);
 // the same stars' solves with the six 1D contractions on the tensor cores
 // (tcgen05, TF32 in, FP32 accumulation); DQ_7 only; status: 1 when a bounded
 // completion wait ran out

@@ -39,6 +39,11 @@ struct fdm_sipg {
   double *partial = nullptr, *dots = nullptr, *sc = nullptr;
   int *vlist = nullptr;
   int *status = nullptr;  // 1 when a bounded wait of the tensor-core star solve ran out
+  int *vall = nullptr;    // all interior vertices, lexicographic: the stars of the one-launch sweep
+  int nstar_all = 0;
+  bool one_launch = true;  // every star in one launch into zpa, then a per-value gather
+  double *zpa64 = nullptr;
+  float *zpa32 = nullptr;
   bool tc = false;        // star solves of the FP32 preconditioner on the tensor cores
   int vcap = 0;
   int64_t zcap = 0;
@@ -100,8 +105,36 @@ void sipg_check_status(fdm_sipg *s) {
 }
 
 // z = omega ASM(r) (+ addv): the 8 vertex parity classes in a fixed order
+template <typename T>
+T *sipg_zpa(fdm_sipg *s) {
+  if constexpr (sizeof(T) == 8) {
+    if (!s->zpa64) s->zpa64 = s->alloc<double>((size_t)s->nstar_all * 8 * s->n * s->n * s->n);
+    return s->zpa64;
+  } else {
+    if (!s->zpa32) s->zpa32 = s->alloc<float>((size_t)s->nstar_all * 8 * s->n * s->n * s->n);
+    return s->zpa32;
+  }
+}
+
 template <typename T, typename Tin, typename Tout>
 void sipg_asm(fdm_sipg *s, const Tin *r, Tout *z, double omega, cudaStream_t st, const T *addv = nullptr) {
+  if (s->one_launch && s->nstar_all > 0 &&
+      (std::is_same<T, Tout>::value || std::is_same<Tout, double>::value)) {
+    // every star in one launch into its own output, then a deterministic gather per value
+    T *zpa = sipg_zpa<T>(s);
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (s->tc) {
+        launch_sipg_patch_tc<Tin, float>(s->d32, 0, s->nstar_all, s->vall, r, nullptr, zpa, 1.0, sipg_timeout_ns(s),
+                                         s->status, st);
+        done = true;
+      }
+    }
+    if (!done) launch_sipg_patch<T, Tin, T>(s->dev<T>(), 0, s->nstar_all, s->vall, r, nullptr, zpa, 1.0, st);
+    launch_sipg_star_gather<T, Tout>(s->dev<T>(), zpa, omega, addv, z, st);
+    s->launches += 2;
+    return;
+  }
   if (addv) {
     if constexpr (std::is_same<T, double>::value && std::is_same<Tout, double>::value) ctx_copy(s->ndof, addv, z, st);
     else if constexpr (!std::is_same<T, Tout>::value) launch_convert<T, Tout>(s->ndof, addv, z, st);
@@ -327,6 +360,15 @@ int fdm_sipg_setup(const fdm_mesh *mesh, int p, double eta, const fdm_options *o
     const size_t fn = (size_t)ncell * 12 * n * n;
     s->status = s->alloc<int>(1);
     FDM_CUDA(cudaMemset(s->status, 0, sizeof(int)));
+    {  // the interior vertices, lexicographic (the stars of the one-launch sweep)
+      std::vector<int> va;
+      for (int vz = 1; vz < ncs[2]; ++vz)
+        for (int vy = 1; vy < ncs[1]; ++vy)
+          for (int vx = 1; vx < ncs[0]; ++vx) va.push_back(vx + (ncs[0] + 1) * (vy + (ncs[1] + 1) * vz));
+      s->nstar_all = (int)va.size();
+      if (!va.empty()) s->vall = s->upload(va);
+      s->one_launch = s->opt.patch_kernel != 1;
+    }
     s->F64 = s->alloc<double>(fn);
     s->cb64 = s->alloc<double>(8 * (size_t)ncell);
     s->cb32 = s->alloc<float>(8 * (size_t)ncell);
