@@ -411,6 +411,15 @@ void fdm_sipg_destroy(fdm_sipg *s);
  * than two cells or more than 2^31 - 1 nodes; fdm_hexmesh_last_error. */
 typedef struct fdm_hexmesh fdm_hexmesh;
 int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_hexmesh **out);
+/* The same with a natural (homogeneous Neumann, traction-free) condition on
+ * part of the boundary (Sec. 4.1's clamped face with the others free):
+ * dirichlet_vertex[nv] (HOST) marks vertices; a boundary face is Dirichlet when
+ * its 4 corner vertices are marked (the closure of the Dirichlet faces holds
+ * the Dirichlet nodes), the other boundary faces are natural, so the stars of
+ * vertices on them keep their boundary nodes, and the Q1 coarse space keeps
+ * their vertices.  NULL: every boundary face is Dirichlet (fdm_hexmesh_create). */
+int fdm_hexmesh_create_bc(int nv, int nc, const int *cells, int p, const unsigned char *dirichlet_vertex,
+                          fdm_hexmesh **out);
 #define FDM_HQ_NNODE 1          /* int64: number of nodes */
 #define FDM_HQ_CELL_NODES 2     /* int32[nc][(p+1)^3]: node of each cell-local GLL node (i + n (j + n k)) */
 #define FDM_HQ_CELL_FDM 3       /* int32[nc][(p+1)^3]: global FDM function of each cell-local FDM function */
@@ -488,6 +497,11 @@ int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_hexmesh **ou
  * Schur complement in the class's fill.  FDM_ENOTSPD for a pivot <= 0,
  * FDM_EINVAL for degenerate geometry or nv other than at creation. */
 int fdm_hexmesh_factor(fdm_hexmesh *h, int nv, const double *X, const double *kappa_q);
+/* The same for the coefficient kappa_q diag(kaxes) (HOST, 3 positive values:
+ * a constant diagonal tensor in physical axes, e.g. the SDC blocks of
+ * Sec. 4.1, mu + (mu + lam) delta_aj): G = kappa |det J| J^{-1} diag(kaxes) J^{-T}.
+ * kaxes NULL: fdm_hexmesh_factor.  FDM_EINVAL for a value <= 0. */
+int fdm_hexmesh_factor_axes(fdm_hexmesh *h, int nv, const double *X, const double *kappa_q, const double *kaxes);
 /* Copies `what` into out (HOST); *len is the capacity in bytes on input and
  * the size written on output (out NULL: the size only). */
 int fdm_hexmesh_query(fdm_hexmesh *h, int what, void *out, size_t *len);

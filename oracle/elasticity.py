@@ -15,14 +15,21 @@ d_i u_i; block (i, j), i != j, is mu d_j v_i d_i u_j + lam d_i v_i d_j u_j.
 On a box cell with half-widths L and volume factor vol = L_x L_y L_z every
 term is a Kronecker product of 1D matrices: A_hat (int l' l'), B_hat
 (int l l) and C_hat (int l_k' l_l: test derivative, trial value), scaled by
-vol / (L_a L_b).  The Dirichlet boundary is the whole of the boundary (all
-three components), as for the scalar problem.
+vol / (L_a L_b).  Dirichlet faces (all three components clamped): the whole
+boundary by default, or the faces of the dirichlet_faces mask (bit 2a: the
+face at the lower end of axis a, bit 2a + 1: the upper end); the other faces
+are traction-free, the natural condition of the weak form (Sec. 4.1 clamps
+x_1 = 0 only).
 
 SDC relaxation: the block-diagonal A_SDC = diag(A_11, A_22, A_33) (Section
 4.1).  Block A_jj is the scalar operator with per-axis coefficients
 mu + (mu + lam) delta_aj, which is separable on box cells, so it takes the
 scalar vertex-star FDM/sparse relaxation with the per-cell surrogate
-mu_a^(j) = (mu + (mu + lam) delta_aj) vol / L_a^2, exactly.
+mu_a^(j) = (mu + (mu + lam) delta_aj) vol / L_a^2, exactly.  With traction-free
+faces the relaxation is taken as its definition: additive Schwarz over the
+vertex stars (the free nodes within p - 1 of the vertex along every axis:
+on a traction-free face the star keeps its boundary nodes) with the dense
+GLL-basis star matrices of A_jj, which the FDM-basis solve equals on box cells.
 
 Preconditioner: the hybrid V(1,1) of the scalar problem (Section 2.5) with
 the SDC relaxation, the elasticity residual, and the vector Q1 Galerkin
@@ -53,8 +60,9 @@ def _kron_cells(M, U):
 class Elasticity:
     """Q_p elasticity on a tensor mesh of box cells, clamped on the boundary."""
 
-    def __init__(self, p, xv, yv, zv, mu, lam):
+    def __init__(self, p, xv, yv, zv, mu, lam, dirichlet_faces=63):
         self.p, self.mu, self.lam = p, float(mu), float(lam)
+        self.dfaces = int(dirichlet_faces)
         self.v = [np.asarray(a, dtype=np.float64) for a in (xv, yv, zv)]
         self.nc = [len(a) - 1 for a in self.v]
         self.Nn = [c * p + 1 for c in self.nc]
@@ -67,9 +75,24 @@ class Elasticity:
         L = np.stack(np.meshgrid(h[0], h[1], h[2], indexing="ij"), axis=-1)   # [cx, cy, cz, 3]
         self.L = np.transpose(L, (2, 1, 0, 3)).reshape(-1, 3)                # [cell, 3]
         self.vol = self.L.prod(axis=1)
-        m = np.ones(self.Nn[::-1], dtype=bool)
-        m[0], m[-1], m[:, 0], m[:, -1], m[:, :, 0], m[:, :, -1] = (False,) * 6
+        m = np.ones(self.Nn[::-1], dtype=bool)   # [z, y, x]
+        df = self.dfaces
+        if df & 1: m[:, :, 0] = False
+        if df & 2: m[:, :, -1] = False
+        if df & 4: m[:, 0] = False
+        if df & 8: m[:, -1] = False
+        if df & 16: m[0] = False
+        if df & 32: m[-1] = False
         self.free = m.ravel()
+        # free Q1 vertices (not on a Dirichlet face), x fastest
+        vm = np.ones([c + 1 for c in self.nc][::-1], dtype=bool)
+        if df & 1: vm[:, :, 0] = False
+        if df & 2: vm[:, :, -1] = False
+        if df & 4: vm[:, 0] = False
+        if df & 8: vm[:, -1] = False
+        if df & 16: vm[0] = False
+        if df & 32: vm[-1] = False
+        self.vfree = vm
         # cell -> grid node index table [cell, z, y, x]
         n = p + 1
         idx = []
@@ -127,19 +150,73 @@ class Elasticity:
         return np.where(self.free, np.outer(np.asarray(f, dtype=np.float64), m), 0.0)
 
     # ------------------------------------------------------------ SDC relaxation
-    def setup_sdc(self):
+    def block_matrix(self, j):
+        """The SDC block A_jj on all grid nodes (sparse CSR, natural boundary)."""
+        import scipy.sparse as sp
+        n = self.p + 1
+        A, B = self.A1, self.B1
+        rows, cols, vals = [], [], []
+        coef = np.full(3, self.mu)
+        coef[j] += self.mu + self.lam
+        for e in range(self.cidx.shape[0]):
+            K = np.zeros((n ** 3, n ** 3))
+            for d in range(3):
+                M = [B, B, B]
+                M[d] = A
+                K += coef[d] * self.vol[e] / self.L[e, d] ** 2 * np.kron(M[2], np.kron(M[1], M[0]))
+            g = self.cidx[e].ravel()
+            rows.append(np.repeat(g, n ** 3))
+            cols.append(np.tile(g, n ** 3))
+            vals.append(K.ravel())
+        return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                             shape=(self.N, self.N))
+
+    def star_nodes(self, v):
+        """Free grid nodes within p - 1 of vertex v = (vx, vy, vz) along every axis."""
+        p = self.p
+        rng = [np.arange(max(0, p * v[a] - p + 1), min(self.Nn[a] - 1, p * v[a] + p - 1) + 1) for a in range(3)]
+        g = (rng[0][None, None, :] + self.Nn[0] * (rng[1][None, :, None] + self.Nn[1] * rng[2][:, None, None])).ravel()
+        return g[self.free[g]]
+
+    def setup_sdc(self, definition=False):
+        """definition: additive Schwarz with the dense GLL-basis star matrices
+        even where the boundary is clamped everywhere (else the scalar FDM
+        oracle's star solves, which equal them on box cells)."""
         self.comps = []
+        self.stars = None
+        if self.dfaces == 63 and not definition:
+            for j in range(3):
+                P = Problem(self.p, *self.v)
+                P.set_mu(self.sdc_mu(j))
+                P.setup_patches()
+                P.set_omega(1.0)
+                self.comps.append(P)
+            return
+        import scipy.linalg as sl
+        self.stars = []
         for j in range(3):
-            P = Problem(self.p, *self.v)
-            P.set_mu(self.sdc_mu(j))
-            P.setup_patches()
-            P.set_omega(1.0)
-            self.comps.append(P)
+            Aj = self.block_matrix(j)
+            facs = []
+            for vz in range(self.nc[2] + 1):
+                for vy in range(self.nc[1] + 1):
+                    for vx in range(self.nc[0] + 1):
+                        g = self.star_nodes((vx, vy, vz))
+                        if len(g):
+                            facs.append((g, sl.cho_factor(Aj[g][:, g].toarray())))
+            self.stars.append(facs)
 
     def sdc(self, r):
         """Undamped additive Schwarz with the SDC blocks: [ASM_j(r_j)]."""
         r = np.asarray(r, dtype=np.float64).reshape(3, self.N)
-        return np.stack([self.comps[j].asm_apply(r[j]) for j in range(3)])
+        if self.stars is None:
+            return np.stack([self.comps[j].asm_apply(r[j]) for j in range(3)])
+        import scipy.linalg as sl
+        z = np.zeros((3, self.N))
+        for j in range(3):
+            rj = np.where(self.free, r[j], 0.0)
+            for g, fac in self.stars[j]:
+                z[j, g] += sl.cho_solve(fac, rj[g])
+        return z
 
     # ------------------------------------------------------------ coarse space
     def _hat(self, a):
@@ -162,7 +239,7 @@ class Elasticity:
         out = np.zeros((3, self.N))
         for a in range(3):
             X = np.zeros(nv[::-1])
-            X[1:-1, 1:-1, 1:-1] = xc[a].reshape(nv[2] - 2, nv[1] - 2, nv[0] - 2)
+            X[self.vfree] = xc[a]
             out[a] = np.einsum("zc,yb,xa,cba->zyx", W[2], W[1], W[0], X).ravel()
         return np.where(self.free, out, 0.0)
 
@@ -173,12 +250,12 @@ class Elasticity:
         for a in range(3):
             R = r[a].reshape(self.Nn[::-1])
             X = np.einsum("zc,yb,xa,zyx->cba", W[2], W[1], W[0], R)
-            out.append(X[1:-1, 1:-1, 1:-1].ravel())
+            out.append(X[self.vfree])
         return np.stack(out)
 
     def setup_coarse(self):
         """A_c = P^T A P (vector Q1 Galerkin), column by column."""
-        nq = (self.nc[0] - 1) * (self.nc[1] - 1) * (self.nc[2] - 1)
+        nq = int(self.vfree.sum())
         m = 3 * nq
         Ac = np.zeros((m, m))
         for J in range(m):

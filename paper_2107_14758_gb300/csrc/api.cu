@@ -90,7 +90,7 @@ bool scw_fits(const fdm_ctx *c, bool fp32, int threads) {
 __global__ void k_mask_dirichlet(Grid g, double *v) {
   for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < g.ndof; id += (int64_t)gridDim.x * blockDim.x) {
     int x = int(id % g.N[0]), y = int((id / g.N[0]) % g.N[1]), z = int(id / ((int64_t)g.N[0] * g.N[1]));
-    if (x == 0 || y == 0 || z == 0 || x == g.N[0] - 1 || y == g.N[1] - 1 || z == g.N[2] - 1) v[id] = 0.0;
+    if (node_dirichlet(g, x, y, z)) v[id] = 0.0;
   }
 }
 void mask_dirichlet(const Grid &g, double *v, cudaStream_t st) {

@@ -37,7 +37,17 @@ struct Grid {
   int N[3];
   int64_t ndof;
   int ncell;
+  // Dirichlet faces: bit 2a for the face at the lower end of axis a, bit 2a+1 for
+  // the upper end (63 = the whole boundary, the default); the other boundary
+  // faces are traction-free / natural (used by the elasticity context)
+  int dmask = 63;
 };
+
+// whether grid node (x, y, z) lies on a Dirichlet face
+__host__ __device__ inline bool node_dirichlet(const Grid &g, int x, int y, int z) {
+  return ((g.dmask & 1) && x == 0) || ((g.dmask & 2) && x == g.N[0] - 1) || ((g.dmask & 4) && y == 0) ||
+         ((g.dmask & 8) && y == g.N[1] - 1) || ((g.dmask & 16) && z == 0) || ((g.dmask & 32) && z == g.N[2] - 1);
+}
 
 __host__ __device__ inline int64_t gidx(const Grid &g, int x, int y, int z) {
   return x + (int64_t)g.N[0] * (y + (int64_t)g.N[1] * z);

@@ -497,6 +497,15 @@ void build_cell_maps(fdm_hexmesh *h, const Builder &B) {
 }
 
 // Dirichlet nodes: the closure of every face that belongs to one cell
+// whether the 4 corner vertices of a boundary face make it a Dirichlet face
+template <typename F>
+bool dirichlet_face(const fdm_hexmesh *h, const F &corners) {
+  if (h->dvert.empty()) return true;
+  for (int v : corners)
+    if (!h->dvert[v]) return false;
+  return true;
+}
+
 void mark_dirichlet(fdm_hexmesh *h, const Builder &B) {
   const int n = h->n, n3 = n * n * n, p = h->p;
   h->dirichlet.assign(B.nnode, 0);
@@ -504,6 +513,7 @@ void mark_dirichlet(fdm_hexmesh *h, const Builder &B) {
     for (int d = 0; d < 3; ++d)
       for (int s = 0; s < 2; ++s) {
         if (B.fcount.at(Builder::face_key(B.face_corners(e, d, s))) != 1) continue;
+        if (!dirichlet_face(h, B.face_corners(e, d, s))) continue;
         for (int k = 0; k < n; ++k)
           for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) {
@@ -782,6 +792,11 @@ void build_inverse_maps(fdm_hexmesh *h) {
 }  // namespace
 
 extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_hexmesh **out) {
+  return fdm_hexmesh_create_bc(nv, nc, cells, p, nullptr, out);
+}
+
+extern "C" int fdm_hexmesh_create_bc(int nv, int nc, const int *cells, int p, const unsigned char *dirichlet_vertex,
+                                     fdm_hexmesh **out) {
   if (!out) return FDM_EINVAL;
   *out = nullptr;
   if (nv < 8 || nc < 1 || !cells || p < 1 || p > 15) {
@@ -795,6 +810,7 @@ extern "C" int fdm_hexmesh_create(int nv, int nc, const int *cells, int p, fdm_h
     h->nv = nv;
     h->nc = nc;
     h->cells.assign(cells, cells + 8 * (size_t)nc);
+    if (dirichlet_vertex) h->dvert.assign(dirichlet_vertex, dirichlet_vertex + nv);
     const fdm::Basis1D basis = fdm::make_basis(p);
     h->Af = basis.Af;
     h->Bf = basis.Bf;
@@ -885,7 +901,7 @@ void coarse_vertices(fdm_hexmesh *h) {
         ++fc[f];
       }
   for (auto &kv : fc)
-    if (kv.second == 1)
+    if (kv.second == 1 && dirichlet_face(h, kv.first))
       for (int v : kv.first) bnd[v] = 1;
   for (int c : h->cells) used[c] = 1;
   h->coarse_of.assign(h->nv, -1);
@@ -899,7 +915,8 @@ void coarse_vertices(fdm_hexmesh *h) {
 // the averaged surrogate mu_d = (1/8) sum_q w_q G_dd (Section 2.7), the
 // stiffness factors w_q G, and the Q1 Galerkin operator (P^T A P cell by cell
 // is the Q1 stiffness of the same quadrature: the trilinear functions lie in Q_p)
-void cell_geometry(fdm_hexmesh *h, const double *X, const double *kappa_q) {
+void cell_geometry(fdm_hexmesh *h, const double *X, const double *kappa_q, const double *kaxes) {
+  const double ka[3] = {kaxes ? kaxes[0] : 1.0, kaxes ? kaxes[1] : 1.0, kaxes ? kaxes[2] : 1.0};
   const int q = h->n, q3 = q * q * q, nc = h->nc;
   const int nco = (int)std::lround(std::sqrt((double)h->coarse.size()));
   h->mu.assign((size_t)nc * 3, 0.0);
@@ -935,7 +952,7 @@ void cell_geometry(fdm_hexmesh *h, const double *X, const double *kappa_q) {
           for (int d = 0; d < 3; ++d)
             for (int f = 0; f < 3; ++f) {
               double s = 0.0;
-              for (int i = 0; i < 3; ++i) s += C[i][d] * C[i][f];
+              for (int i = 0; i < 3; ++i) s += C[i][d] * ka[i] * C[i][f];
               G[d][f] = kap * s / std::fabs(det);
             }
           for (int d = 0; d < 3; ++d) h->mu[3 * (size_t)e + d] += w * G[d][d] / 8.0;
@@ -1131,13 +1148,20 @@ void factor_stars(fdm_hexmesh *h, const std::vector<std::vector<int>> &vcells) {
 }  // namespace
 
 extern "C" int fdm_hexmesh_factor(fdm_hexmesh *h, int nv, const double *X, const double *kappa_q) {
+  return fdm_hexmesh_factor_axes(h, nv, X, kappa_q, nullptr);
+}
+
+extern "C" int fdm_hexmesh_factor_axes(fdm_hexmesh *h, int nv, const double *X, const double *kappa_q,
+                                       const double *kaxes) {
   if (!h || !X || nv != h->nv) {
     if (h) h->err = "fdm_hexmesh_factor: need the mesh's nv vertex coordinates";
     return FDM_EINVAL;
   }
   try {
     coarse_vertices(h);
-    cell_geometry(h, X, kappa_q);
+    if (kaxes && !(kaxes[0] > 0.0 && kaxes[1] > 0.0 && kaxes[2] > 0.0))
+      fdm::fail(FDM_EINVAL, "fdm_hexmesh_factor_axes: the axis coefficients must be positive");
+    cell_geometry(h, X, kappa_q, kaxes);
     std::vector<std::vector<int>> vcells(h->nv);
     for (int e = 0; e < h->nc; ++e)
       for (int k = 0; k < 8; ++k) vcells[h->cells[8 * (size_t)e + k]].push_back(e);

@@ -52,6 +52,8 @@ struct fdm_hexmesh {
   std::vector<int32_t> node_cells;      // e * (p+1)^3 + l of every cell-local node of each node, by cell
   // kept for the numeric set-up
   std::vector<int> cells;            // [nc][8]
+  std::vector<uint8_t> dvert;        // [nv] Dirichlet vertices (empty: every boundary face is Dirichlet);
+                                     // a boundary face is Dirichlet when its 4 vertices are marked
   std::vector<double> Af, Bf, xq, wq;
   // numeric set-up (fdm_hexmesh_factor)
   std::vector<double> mu;            // [nc][3] averaged surrogate coefficients

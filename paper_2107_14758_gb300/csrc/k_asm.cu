@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(256) k_restrict_fdm(Grid g, const Tin *__restr
   for (int idx = threadIdx.x; idx < n3; idx += blockDim.x) {
     int i = idx % n, j = (idx / n) % n, k = idx / (n * n);
     int gx = cx * p + i, gy = cy * p + j, gz = cz * p + k;
-    bool dir = gx == 0 || gy == 0 || gz == 0 || gx == g.N[0] - 1 || gy == g.N[1] - 1 || gz == g.N[2] - 1;
+    bool dir = node_dirichlet(g, gx, gy, gz);
     int mult = ((i == 0 && cx > 0) || (i == p && cx < g.nx - 1) ? 2 : 1) *
                ((j == 0 && cy > 0) || (j == p && cy < g.ny - 1) ? 2 : 1) *
                ((k == 0 && cz > 0) || (k == p && cz < g.nz - 1) ? 2 : 1);
@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(256) k_interp_fdm(InterpArgs<T> a, double omeg
     int i = idx % n, j = (idx / n) % n, k = idx / (n * n);
     if ((i == 0 && ce[0] > 0) || (j == 0 && ce[1] > 0) || (k == 0 && ce[2] > 0)) continue;  // not owner
     int gx = ce[0] * p + i, gy = ce[1] * p + j, gz = ce[2] * p + k;
-    bool dir = gx == 0 || gy == 0 || gz == 0 || gx == g.N[0] - 1 || gy == g.N[1] - 1 || gz == g.N[2] - 1;
+    bool dir = node_dirichlet(g, gx, gy, gz);
     z[gidx(g, gx, gy, gz)] = dir ? Tout(0) : Tout(omega * b1[idx]);
   }
 }

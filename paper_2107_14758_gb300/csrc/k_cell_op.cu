@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_box_op(Grid g, c
     for (int idx = l; idx < N3; idx += L) {
       const int i = idx % N, j = (idx / N) % N, k = idx / (N * N);
       const int gx = cx * P + i, gy = cy * P + j, gz = cz * P + k;
-      const bool dir = gx == 0 || gy == 0 || gz == 0 || gx == g.N[0] - 1 || gy == g.N[1] - 1 || gz == g.N[2] - 1;
+      const bool dir = node_dirichlet(g, gx, gy, gz);
       U[pid<N>(i, j, k)] = dir ? T(0) : T(u[gidx(g, gx, gy, gz)]);
     }
   }
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_gen_op(Grid g, c
     for (int idx = l; idx < N3; idx += L) {
       const int i = idx % N, j = (idx / N) % N, k = idx / (N * N);
       const int gx = cx * P + i, gy = cy * P + j, gz = cz * P + k;
-      const bool dir = gx == 0 || gy == 0 || gz == 0 || gx == g.N[0] - 1 || gy == g.N[1] - 1 || gz == g.N[2] - 1;
+      const bool dir = node_dirichlet(g, gx, gy, gz);
       U[pid<N>(i, j, k)] = dir ? T(0) : T(u[gidx(g, gx, gy, gz)]);
     }
   }
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(128) k_gather_t(Grid g, const T *__restrict__ 
   const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y, gz = blockIdx.z;
   if (gx >= g.N[0]) return;
   const int64_t id = gx + (int64_t)g.N[0] * (gy + (int64_t)g.N[1] * gz);
-  if (gx == 0 || gy == 0 || gz == 0 || gx == g.N[0] - 1 || gy == g.N[1] - 1 || gz == g.N[2] - 1) {
+  if (node_dirichlet(g, gx, gy, gz)) {
     y[id] = Tout(0);
     return;
   }

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_restrict_t(Grid 
     for (int idx = l; idx < N3; idx += L) {  // W_K r_K, W = 1 / multiplicity, Dirichlet entries 0
       const int i = idx % N, j = (idx / N) % N, k = idx / (N * N);
       const int gx = cx * P + i, gy = cy * P + j, gz = cz * P + k;
-      const bool dir = gx == 0 || gy == 0 || gz == 0 || gx == g.N[0] - 1 || gy == g.N[1] - 1 || gz == g.N[2] - 1;
+      const bool dir = node_dirichlet(g, gx, gy, gz);
       const int mult = ((i == 0 && cx > 0) || (i == P && cx < g.nx - 1) ? 2 : 1) *
                        ((j == 0 && cy > 0) || (j == P && cy < g.ny - 1) ? 2 : 1) *
                        ((k == 0 && cz > 0) || (k == P && cz < g.nz - 1) ? 2 : 1);
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_interp_t(InterpA
     const int i = idx % N, j = (idx / N) % N, k = idx / (N * N);
     if ((i == 0 && ce[0] > 0) || (j == 0 && ce[1] > 0) || (k == 0 && ce[2] > 0)) continue;  // not owner
     const int gx = ce[0] * P + i, gy = ce[1] * P + j, gz = ce[2] * P + k;
-    const bool dir = gx == 0 || gy == 0 || gz == 0 || gx == g.N[0] - 1 || gy == g.N[1] - 1 || gz == g.N[2] - 1;
+    const bool dir = node_dirichlet(g, gx, gy, gz);
     const int64_t id = gidx(g, gx, gy, gz);
     // z = omega * relaxation, plus a.addv where given (the V-cycle's pre-smoothed x1)
     z[id] = dir ? Tout(0) : (a.addv ? Tout(a.addv[id] + T(omega) * V[pid<N>(i, j, k)]) : Tout(omega * V[pid<N>(i, j, k)]));
@@ -322,6 +322,7 @@ bool launch_interp_fast(const InterpArgs<T> &a, double omega, Tout *z, cudaStrea
 
 template <typename T, typename Tin>
 bool launch_coarse_restrict_fast(const Grid &g, const Tin *r, const T *tab, T *cellbuf, cudaStream_t st) {
+  if (g.dmask != 63) return false;  // specialised for the all-Dirichlet boundary
   if constexpr (!std::is_same<T, Tin>::value) {
     return false;
   } else {
@@ -336,6 +337,7 @@ bool launch_coarse_restrict_fast(const Grid &g, const Tin *r, const T *tab, T *c
 template <typename T, typename Tout>
 bool launch_coarse_prolong_fast(const Grid &g, const T *xc, const T *tab, const int *cfree, Tout *z, bool accumulate,
                                 cudaStream_t st) {
+  if (g.dmask != 63) return false;  // specialised for the all-Dirichlet boundary
   if constexpr (!std::is_same<T, Tout>::value) {
     return false;
   } else {

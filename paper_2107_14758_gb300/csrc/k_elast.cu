@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(EL_THREADS) k_elast_grad(Grid g, const Tin *__
   for (int o = threadIdx.x; o < n3; o += blockDim.x) {
     const int i = o % n, j = (o / n) % n, k = o / (n * n);
     const int gx = cx * p + i, gy = cy * p + j, gz = cz * p + k;
-    const bool dir = gx == 0 || gy == 0 || gz == 0 || gx == g.N[0] - 1 || gy == g.N[1] - 1 || gz == g.N[2] - 1;
+    const bool dir = node_dirichlet(g, gx, gy, gz);
     U[o] = dir ? T(0) : T(ub[gidx(g, gx, gy, gz)]);  // Dirichlet entries of the input are ignored
   }
   __syncthreads();

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) k_operator_cells(OpArgs a, int mass, cons
   for (int idx = threadIdx.x; idx < n3; idx += blockDim.x) {
     int i = idx % n, j = (idx / n) % n, k = idx / (n * n);
     int gx = cx * p + i, gy = cy * p + j, gz = cz * p + k;
-    bool dir = gx == 0 || gy == 0 || gz == 0 || gx == g.N[0] - 1 || gy == g.N[1] - 1 || gz == g.N[2] - 1;
+    bool dir = node_dirichlet(g, gx, gy, gz);
     b0[idx] = dir ? T(0) : T(u[gidx(g, gx, gy, gz)]);
   }
   __syncthreads();
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(256) k_coarse_restrict_cells(Grid g, const Tin
   for (int idx = threadIdx.x; idx < n3; idx += blockDim.x) {
     int i = idx % n, j = (idx / n) % n, k = idx / (n * n);
     int gx = cx * p + i, gy = cy * p + j, gz = cz * p + k;
-    bool dir = gx == 0 || gy == 0 || gz == 0 || gx == g.N[0] - 1 || gy == g.N[1] - 1 || gz == g.N[2] - 1;
+    bool dir = node_dirichlet(g, gx, gy, gz);
     if (dir) continue;
     int mult = ((i == 0 && cx > 0) || (i == p && cx < g.nx - 1) ? 2 : 1) *
                ((j == 0 && cy > 0) || (j == p && cy < g.ny - 1) ? 2 : 1) *
@@ -400,7 +400,7 @@ __global__ void k_coarse_prolong(Grid g, const T *__restrict__ xc, const T *__re
     int i = idx % n, j = (idx / n) % n, k = idx / (n * n);
     if ((i == 0 && ce[0] > 0) || (j == 0 && ce[1] > 0) || (k == 0 && ce[2] > 0)) continue;
     int gx = ce[0] * p + i, gy = ce[1] * p + j, gz = ce[2] * p + k;
-    bool dir = gx == 0 || gy == 0 || gz == 0 || gx == g.N[0] - 1 || gy == g.N[1] - 1 || gz == g.N[2] - 1;
+    bool dir = node_dirichlet(g, gx, gy, gz);
     T hx[2] = {T(0.5) * (T(1) - xi[i]), T(0.5) * (T(1) + xi[i])};
     T hy[2] = {T(0.5) * (T(1) - xi[j]), T(0.5) * (T(1) + xi[j])};
     T hz[2] = {T(0.5) * (T(1) - xi[k]), T(0.5) * (T(1) + xi[k])};

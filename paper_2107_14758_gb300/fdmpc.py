@@ -128,6 +128,8 @@ def load():
     L.fdm_sipg_destroy.argtypes = [vp]
     L.fdm_sipg_destroy.restype = None
     L.fdm_hexmesh_create.argtypes = [C.c_int, C.c_int, ip, C.c_int, C.POINTER(vp)]
+    L.fdm_hexmesh_create_bc.argtypes = [C.c_int, C.c_int, ip, C.c_int, vp, C.POINTER(vp)]
+    L.fdm_hexmesh_factor_axes.argtypes = [vp, C.c_int, dp, dp, dp]
     L.fdm_hexmesh_query.argtypes = [vp, C.c_int, vp, C.POINTER(C.c_size_t)]
     L.fdm_hexmesh_factor.argtypes = [vp, C.c_int, dp, dp]
     L.fdm_hexmesh_last_error.argtypes = [vp]
@@ -775,12 +777,18 @@ class HexMesh:
     cell-to-global FDM map and the stars' surrogate patterns.  Host arrays
     only; needs no GPU."""
 
-    def __init__(self, nv, cells, p):
+    def __init__(self, nv, cells, p, dirichlet_vertex=None):
+        """dirichlet_vertex: None (every boundary face Dirichlet) or a bool array
+        over the vertices; a boundary face is Dirichlet when its 4 vertices are
+        marked, the other boundary faces are natural."""
         L = load()
         cells = np.ascontiguousarray(cells, dtype=np.int32)
         self.p, self.n, self.nc = p, p + 1, cells.shape[0]
         h = C.c_void_p()
-        rc = L.fdm_hexmesh_create(int(nv), self.nc, cells.ctypes.data_as(C.POINTER(C.c_int)), p, C.byref(h))
+        dv = None if dirichlet_vertex is None else np.ascontiguousarray(dirichlet_vertex, dtype=np.uint8)
+        self._dv = dv
+        rc = L.fdm_hexmesh_create_bc(int(nv), self.nc, cells.ctypes.data_as(C.POINTER(C.c_int)), p,
+                                     None if dv is None else dv.ctypes.data_as(C.c_void_p), C.byref(h))
         if rc < 0:
             raise FdmError(rc, L.fdm_hexmesh_last_error(None).decode())
         self.h = h
@@ -854,13 +862,16 @@ class HexMesh:
                for k in range(len(first))]
         return cls, nint, per
 
-    def factor(self, X, kappa_q=None):
-        """Numeric set-up (fdm_hexmesh_factor); returns (mu[nc,3], per star
-        (D, L values in its class's fill pattern))."""
+    def factor(self, X, kappa_q=None, kaxes=None):
+        """Numeric set-up (fdm_hexmesh_factor, or fdm_hexmesh_factor_axes with
+        the diagonal coefficient kaxes); returns (mu[nc,3], per star (D, L
+        values in its class's fill pattern))."""
         L = load()
         X = np.ascontiguousarray(X, dtype=np.float64)
         kq = None if kappa_q is None else np.ascontiguousarray(kappa_q, dtype=np.float64)
-        rc = L.fdm_hexmesh_factor(self.h, X.shape[0], _dptr(X), None if kq is None else _dptr(kq))
+        ka = None if kaxes is None else np.ascontiguousarray(kaxes, dtype=np.float64)
+        rc = L.fdm_hexmesh_factor_axes(self.h, X.shape[0], _dptr(X), None if kq is None else _dptr(kq),
+                                       None if ka is None else _dptr(ka))
         if rc < 0:
             raise FdmError(rc, L.fdm_hexmesh_last_error(self.h).decode())
         mu = self.query(FDM_HQ_MU, np.float64).reshape(self.nc, 3)

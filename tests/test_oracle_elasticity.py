@@ -162,3 +162,77 @@ def test_iterations_grow_with_lambda(el):
     for k in range(1, 4):
         ratio = (its[k] / its[0]) / (paper[k] / paper[0])
         assert 0.5 <= ratio <= 2.0, (its, paper)
+
+
+# ---------------------------------------------------------------- traction-free faces (Sec. 4.1, Table 3)
+def test_star_definition_equals_fdm_relaxation_when_clamped(el):
+    """The relaxation by its definition (dense GLL-basis star matrices of each
+    SDC block, the form used with traction-free faces) equals the scalar FDM
+    oracle's relaxation when every face is clamped."""
+    xv, yv, zv = inputs.graded_vertices(3, 64)
+    r = np.random.default_rng(8).standard_normal((3, (3 * 3 + 1) ** 3))
+    out = []
+    for definition in (False, True):
+        E = el.Elasticity(3, xv, yv, zv, 1.0, 7.0)
+        E.setup_sdc(definition=definition)
+        out.append(E.sdc(np.where(E.free, r, 0.0)))
+    assert np.abs(out[1] - out[0]).max() <= 1e-11 * np.abs(out[0]).max()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_traction_free_apply_vs_bruteforce(el, p):
+    """With x_1 = 0 clamped and the other faces traction-free (the natural
+    condition), the operator is the brute-force matrix on the nodes off that
+    face; with no face clamped it annihilates the rigid-body modes."""
+    xv, yv, zv = np.array([0, 0.3, 1.0]), np.array([0, 0.45, 0.8]), np.array([0, 0.2, 0.7, 1.1])
+    mu, lam = 0.8, 3.7
+    K = bf.dense_elasticity(p, xv, yv, zv, mu, lam)
+    E = el.Elasticity(p, xv, yv, zv, mu, lam, dirichlet_faces=1)
+    x, y, z = _grid_coords(p, xv, yv, zv, bf.gll_nodes(p))
+    assert np.array_equal(E.free, x > 0)
+    free = np.tile(E.free, 3)
+    u = np.where(free, np.random.default_rng(p).standard_normal(3 * E.N), 0.0)
+    ref = np.where(free, K @ u, 0.0)
+    assert np.abs(E.apply(u).ravel() - ref).max() <= 1e-12 * np.abs(ref).max()
+    F = el.Elasticity(p, xv, yv, zv, mu, lam, dirichlet_faces=0)
+    zero = np.zeros_like(x)
+    for m in ([-y, x, zero], [zero, -z, y], [z, zero, -x], [zero + 1, zero, zero]):
+        um = np.concatenate(m)
+        assert np.abs(F.apply(um)).max() <= 1e-12 * np.abs(K).max() * np.abs(um).max()
+
+
+def test_traction_free_pcg_matches_direct_solve(el):
+    p = 2
+    xv, yv, zv = inputs.graded_vertices(3, 65)
+    E = el.Elasticity(p, xv, yv, zv, 1.0, 5.0, dirichlet_faces=1)
+    E.setup_sdc()
+    E.setup_coarse()
+    E.lanczos_omega(inputs.lanczos_start(3 * E.N))
+    K = bf.dense_elasticity(p, xv, yv, zv, 1.0, 5.0)
+    free = np.tile(E.free, 3)
+    b = E.body_force([0.0, -0.02, 0.0]).ravel()
+    xd = np.zeros(3 * E.N)
+    xd[free] = np.linalg.solve(K[np.ix_(free, free)], b[free])
+    x, it, conv = E.pcg(b, rtol=1e-10, maxit=400)
+    assert conv
+    assert np.linalg.norm(x.ravel() - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+def test_table3_setting(el):
+    """Table 3's configuration (the unit cube clamped on x_1 = 0 and
+    traction-free elsewhere, mu = 1, body force -0.02 e_2), here on a uniform
+    4^3 mesh at p = 3: the PCG iteration counts for lambda = 0, 1, 10, 100 are
+    the paper's printed ones (tests/golden/table3_elasticity_3d.txt: 20, 22,
+    39, 114) within 5 % + 1."""
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table3_elasticity_3d.txt")
+    rows = {int(l.split()[0]): [int(v) for v in l.split()[1:]] for l in open(golden)
+            if l.strip() and not l.startswith("#")}
+    xv = np.linspace(0, 1, 5)
+    for k, lam in enumerate((0.0, 1.0, 10.0, 100.0)):
+        E = el.Elasticity(3, xv, xv, xv, 1.0, lam, dirichlet_faces=1)
+        E.setup_sdc()
+        E.setup_coarse()
+        E.lanczos_omega(inputs.lanczos_start(3 * E.N))
+        _, it, conv = E.pcg(E.body_force([0.0, -0.02, 0.0]), rtol=1e-8, maxit=800)
+        assert conv
+        assert abs(it - rows[3][k]) <= 0.05 * rows[3][k] + 1, (lam, it, rows[3][k])
