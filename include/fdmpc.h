@@ -320,6 +320,31 @@ int fdm_surrogate_apply(fdm_ctx *ctx, const float *w, int judge, int *nfallback,
 typedef struct fdm_elast fdm_elast;
 int fdm_elast_setup(const fdm_mesh *mesh, int p, double mu, double lambda, const fdm_options *opt,
                     fdm_elast **out, void *stream);
+/* The same, clamped only on the faces in dirichlet_faces and traction-free
+ * (the natural condition) on the others, as in Sec. 4.1's tests (x_1 = 0
+ * clamped: dirichlet_faces = 1): bit 2a is the face at the lower end of axis a
+ * (a = 0, 1, 2 for x, y, z), bit 2a+1 the upper end; 63 = every face
+ * (fdm_elast_setup).  At least one face is clamped (1..63), so that A is
+ * positive definite.  The nodes on traction-free faces are unknowns; the star
+ * of a vertex holds the free nodes within p - 1 of it along each axis (on a
+ * traction-free face its boundary nodes), and the Q1 coarse space has every
+ * vertex off the clamped faces.  sdc_form selects how the SDC blocks' star systems are
+ * solved (both exact, so both give the same relaxation up to rounding):
+ *   FDM_SDC_FDM_SPARSE  the scalar problem's vertex-star FDM/sparse relaxation
+ *                       (every face clamped only);
+ *   FDM_SDC_STAR_FDM    the star-local fast diagonalisation: block j's star
+ *                       matrix is the Kronecker sum sum_a c_a A_a (x) M_b (x) M_c
+ *                       of the star's 1D stiffness and mass (c_a = mu + (mu +
+ *                       lambda) delta_aj), inverted as (S (x) S (x) S) D^{-1}
+ *                       (S (x) S (x) S)^T with the 1D generalised eigenvectors;
+ *                       stars up to 29 nodes per axis in shared memory;
+ *   FDM_SDC_AUTO        FDM/sparse with every face clamped, else star FDM.
+ * FDM_EINVAL for a mask or form outside these. */
+#define FDM_SDC_AUTO 0
+#define FDM_SDC_FDM_SPARSE 1
+#define FDM_SDC_STAR_FDM 2
+int fdm_elast_setup_bc(const fdm_mesh *mesh, int p, double mu, double lambda, int dirichlet_faces, int sdc_form,
+                       const fdm_options *opt, fdm_elast **out, void *stream);
 /* y = A u */
 int elast_apply(fdm_elast *e, const double *u_dev, double *y_dev, void *stream);
 /* z = P^{-1} r (the preconditioner selected by opt->pc) */
@@ -327,7 +352,8 @@ int elast_pc_apply(fdm_elast *e, const double *r_dev, double *z_dev, void *strea
 /* PCG from x = 0 to ||r||_2 <= rtol ||b||_2 (as pcg_solve, host-driven loop) */
 int elast_pcg_solve(fdm_elast *e, const double *b_dev, double *x_dev, double rtol, int maxit,
                     fdm_solve_info *info, void *stream);
-/* FDM_Q_NDOF (int64, nodes per component), FDM_Q_OMEGA, FDM_Q_LAMBDA, FDM_Q_LAUNCHES */
+/* FDM_Q_NDOF (int64, nodes per component), FDM_Q_OMEGA, FDM_Q_LAMBDA, FDM_Q_LAUNCHES,
+ * FDM_Q_RECURSIVE_ITS */
 int fdm_elast_query(fdm_elast *e, int what, void *out, size_t *len);
 const char *fdm_elast_last_error(const fdm_elast *e);
 void fdm_elast_destroy(fdm_elast *e);
@@ -595,6 +621,9 @@ void fdm_hex_destroy(fdm_hexgpu *ctx);
                                   the free vertices, x fastest) */
 #define FDM_Q_ALGO_BYTES_LFORM 27 /* double[2]: FDM_Q_ALGO_BYTES' patch-solve bytes (FP64, FP32) of the L
                                      form, whichever form the context uses */
+#define FDM_Q_RECURSIVE_ITS 28  /* int32[2] (fdm_elast_query): for the last elast_pcg_solve, the iteration
+                                   at which the recursive residual first met the test (-1: never) and
+                                   the number of true-residual checks that did not */
 /* timers of FDM_Q_KERNEL_TIMES */
 #define FDM_T_RESTRICT 0  /* basis change to the FDM basis */
 #define FDM_T_PATCH 1     /* patch gather + condense + triangular solves + back-substitution */

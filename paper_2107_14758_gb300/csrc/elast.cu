@@ -12,26 +12,41 @@
 #include "ctx.h"
 
 // ====================================================================== linear elasticity (Section 4.1)
-// Primal formulation on box cells, clamped on the whole boundary; vectors are
-// component-major [3][ndof].  The SDC relaxation is block-Jacobi over the
-// displacement components: block j is the scalar operator with per-axis
-// coefficients mu + (mu + lam) delta_aj, separable on box cells, so each block
-// is a scalar context whose vertex-star FDM/sparse relaxation uses the exact
-// surrogate mu_a^(j) = (mu + (mu + lam) delta_aj) vol / L_a^2.  The V(1,1)
-// cycle uses the elasticity residual and the vector Q1 Galerkin coarse
-// problem, which on box cells is the Q1 elasticity stiffness (exactly
-// integrated by 2 Gauss points per axis), solved through its dense inverse.
+// Primal formulation on box cells, clamped on the faces of a mask (the others
+// traction-free: the natural condition); vectors are component-major
+// [3][ndof].  The SDC relaxation is block-Jacobi over the displacement
+// components: block j is the scalar operator with per-axis coefficients
+// c_a = mu + (mu + lam) delta_aj, separable on box cells.  With every face
+// clamped each block is a scalar context whose vertex-star FDM/sparse
+// relaxation uses the exact surrogate mu_a^(j) = c_a vol / L_a^2; otherwise (or
+// on request) the star solves use the star-local fast diagonalisation, exact
+// for the block's constant coefficient, with the stars of vertices on
+// traction-free faces keeping their boundary nodes.  Both invert the same star
+// matrices.  The V(1,1) cycle uses the elasticity residual and the vector Q1
+// Galerkin coarse problem over the vertices off the clamped faces, which on box
+// cells is the Q1 elasticity stiffness (exactly integrated by 2 Gauss points
+// per axis), solved through its dense inverse.
 struct fdm_elast {
   fdm_ctx *comp[3] = {nullptr, nullptr, nullptr};
   fdm_options opt;
   double mu = 1.0, lam = 0.0, omega = 1.0, lmin = 0.0, lmax = 0.0;
   Grid g{};
   int64_t n = 0;  // grid nodes per component
+  bool star = false;  // SDC star solves by the star-local FDM (else the scalar contexts)
   std::string err;
   std::vector<void *> allocs;
   double *Lc = nullptr;
+  double *tab64 = nullptr;
+  float *tab32 = nullptr;
   double *wq64 = nullptr;
   float *wq32 = nullptr;
+  int *cfree = nullptr;  // [nv] coarse vertex of each vertex or -1
+  double *cb64 = nullptr;
+  float *cb32 = nullptr;
+  StarFdmDev<double> sf64;
+  StarFdmDev<float> sf32;
+  double *X64 = nullptr;
+  float *X32 = nullptr;
   double *G64 = nullptr, *E64 = nullptr;
   float *G32 = nullptr, *E32 = nullptr;
   int nq = 0, m = 0;  // free Q1 vertices, coarse unknowns 3 nq
@@ -41,6 +56,7 @@ struct fdm_elast {
   float *f1 = nullptr, *f3 = nullptr;
   double *partial = nullptr, *dots = nullptr, *sc = nullptr;
   int64_t launches = 0;
+  int rec_its = -1, rec_misses = 0;  // the last solve's first recursive convergence, failed true checks
   size_t alloc_bytes = 0;  // device bytes allocated through alloc()
   template <typename T>
   T *alloc(size_t k) {
@@ -56,6 +72,10 @@ struct fdm_elast {
   }
   template <typename T> T *G() const;
   template <typename T> T *E() const;
+  template <typename T> const T *tab() const;
+  template <typename T> T *cb() const;
+  template <typename T> const StarFdmDev<T> &sf() const;
+  template <typename T> T *X() const;
   template <typename T> const T *wq() const;
   template <typename T> const T *Ainv() const;
   template <typename T> T *rc() const;
@@ -65,6 +85,14 @@ struct fdm_elast {
     for (void *ptr : allocs) cudaFree(ptr);
   }
 };
+template <> const double *fdm_elast::tab<double>() const { return tab64; }
+template <> const float *fdm_elast::tab<float>() const { return tab32; }
+template <> double *fdm_elast::cb<double>() const { return cb64; }
+template <> float *fdm_elast::cb<float>() const { return cb32; }
+template <> const StarFdmDev<double> &fdm_elast::sf<double>() const { return sf64; }
+template <> const StarFdmDev<float> &fdm_elast::sf<float>() const { return sf32; }
+template <> double *fdm_elast::X<double>() const { return X64; }
+template <> float *fdm_elast::X<float>() const { return X32; }
 template <> double *fdm_elast::G<double>() const { return G64; }
 template <> float *fdm_elast::G<float>() const { return G32; }
 template <> double *fdm_elast::E<double>() const { return E64; }
@@ -93,7 +121,7 @@ void mask3(const fdm_elast *e, double *v, cudaStream_t st) {
 // y = A u (rsub == nullptr) or y = rsub - A u, in precision T
 template <typename T, typename Tin>
 void elast_op(fdm_elast *e, const Tin *u, T *y, const double *rsub, cudaStream_t st) {
-  launch_elast_cells<T, Tin>(e->g, u, e->comp[0]->tab<T>(), e->wq<T>(), e->Lc, e->mu, e->lam, e->G<T>(), e->E<T>(), st);
+  launch_elast_cells<T, Tin>(e->g, u, e->tab<T>(), e->wq<T>(), e->Lc, e->mu, e->lam, e->G<T>(), e->E<T>(), st);
   const int64_t cn = (int64_t)e->g.ncell * e->g.n * e->g.n * e->g.n;
   for (int a = 0; a < 3; ++a)
     launch_gather_cells<T, T>(e->g, e->E<T>() + a * cn, rsub ? rsub + a * e->n : nullptr, y + a * e->n, st);
@@ -103,6 +131,12 @@ void elast_op(fdm_elast *e, const Tin *u, T *y, const double *rsub, cudaStream_t
 // z = omega S(r): the three scalar relaxations (precision T inside)
 template <typename T, typename Tin, typename Tout>
 void elast_sdc(fdm_elast *e, const Tin *r, Tout *z, double omega, cudaStream_t st, const T *addv = nullptr) {
+  if (e->star) {
+    launch_star_fdm_solve<T, Tin>(e->sf<T>(), r, e->X<T>(), 3, st);
+    launch_star_fdm_gather<T, Tout>(e->sf<T>(), e->X<T>(), omega, addv, z, 3, st);
+    e->launches += 2;
+    return;
+  }
   for (int a = 0; a < 3; ++a) {
     fdm_ctx *c = e->comp[a];
     c->launches = 0;
@@ -113,15 +147,11 @@ void elast_sdc(fdm_elast *e, const Tin *r, Tout *z, double omega, cudaStream_t s
 
 template <typename T>
 void elast_coarse(fdm_elast *e, const T *r1, T *x1, cudaStream_t st) {
-  for (int a = 0; a < 3; ++a) {
-    fdm_ctx *c = e->comp[a];
-    launch_coarse_restrict<T, T>(c->g, r1 + a * e->n, c->tab<T>(), c->cfree, e->rc<T>() + a * e->nq, c->cb<T>(), st);
-  }
+  for (int a = 0; a < 3; ++a)
+    launch_coarse_restrict<T, T>(e->g, r1 + a * e->n, e->tab<T>(), e->cfree, e->rc<T>() + a * e->nq, e->cb<T>(), st);
   launch_dense_symv<T>(e->m, e->Ainv<T>(), e->rc<T>(), e->xc<T>(), st);
-  for (int a = 0; a < 3; ++a) {
-    fdm_ctx *c = e->comp[a];
-    launch_coarse_prolong<T, T>(c->g, e->xc<T>() + a * e->nq, c->tab<T>(), c->cfree, x1 + a * e->n, true, st);
-  }
+  for (int a = 0; a < 3; ++a)
+    launch_coarse_prolong<T, T>(e->g, e->xc<T>() + a * e->nq, e->tab<T>(), e->cfree, x1 + a * e->n, true, st);
   e->launches += 10;
 }
 
@@ -163,34 +193,48 @@ __global__ void k_permute_sym(int m, int nq, const double *__restrict__ in, doub
 // vector Q1 coarse problem: cell stiffness of Q1 elasticity by 2-point Gauss
 // (exact on box cells), banded Cholesky in vertex-interleaved order, dense
 // inverse on the device, permuted to component-major order
-void elast_setup_coarse(fdm_elast *e, cudaStream_t st) {
-  const fdm_ctx *c0 = e->comp[0];
-  const int nx = e->g.nx, ny = e->g.ny, nz = e->g.nz, nvx = nx + 1, nvy = ny + 1;
-  const int mx = nx - 1, my = ny - 1;
-  e->nq = c0->nc;
+void elast_setup_coarse(fdm_elast *e, const std::vector<double> *vert, cudaStream_t st) {
+  const int nx = e->g.nx, ny = e->g.ny, nz = e->g.nz, nvx = nx + 1, nvy = ny + 1, nv = nvx * nvy * (nz + 1);
+  // the coarse unknowns: the vertices off the clamped faces, in vertex order
+  std::vector<int> cfree(nv, -1);
+  int nq = 0;
+  for (int v = 0; v < nv; ++v) {
+    const int vx = v % nvx, vy = (v / nvx) % nvy, vz = v / (nvx * nvy);
+    if (!node_dirichlet(e->g, vx * e->g.p, vy * e->g.p, vz * e->g.p)) cfree[v] = nq++;
+  }
+  e->cfree = e->upload(cfree);
+  e->cb64 = e->alloc<double>((size_t)8 * e->g.ncell);
+  e->cb32 = e->alloc<float>((size_t)8 * e->g.ncell);
+  e->nq = nq;
   e->m = 3 * e->nq;
   e->rc64 = e->alloc<double>(e->m);
   e->xc64 = e->alloc<double>(e->m);
   e->rc32 = e->alloc<float>(e->m);
   e->xc32 = e->alloc<float>(e->m);
   if (e->m == 0) return;
-  const int m = e->m, bw = 3 * (1 + mx + mx * my) + 2;
+  // half-bandwidth of the vertex-interleaved numbering: the widest index span of a cell
+  int span = 0;
+  for (int c = 0; c < e->g.ncell; ++c) {
+    const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
+    int lo = nq, hi = -1;
+    for (int s = 0; s < 8; ++s) {
+      const int f = cfree[(cx + (s & 1)) + nvx * ((cy + ((s >> 1) & 1)) + nvy * (cz + (s >> 2)))];
+      if (f >= 0) lo = std::min(lo, f), hi = std::max(hi, f);
+    }
+    if (hi >= 0) span = std::max(span, hi - lo);
+  }
+  const int m = e->m, bw = 3 * span + 2;
   std::vector<double> Lb((size_t)m * (bw + 1), 0.0);
   const double gp = 1.0 / std::sqrt(3.0);
   for (int cz = 0; cz < nz; ++cz)
     for (int cy = 0; cy < ny; ++cy)
       for (int cx = 0; cx < nx; ++cx) {
-        const double L[3] = {0.5 * (c0->vert[0][cx + 1] - c0->vert[0][cx]), 0.5 * (c0->vert[1][cy + 1] - c0->vert[1][cy]),
-                             0.5 * (c0->vert[2][cz + 1] - c0->vert[2][cz])};
+        const double L[3] = {0.5 * (vert[0][cx + 1] - vert[0][cx]), 0.5 * (vert[1][cy + 1] - vert[1][cy]),
+                             0.5 * (vert[2][cz + 1] - vert[2][cz])};
         const double vol = L[0] * L[1] * L[2];
         int f[8];
-        for (int s = 0; s < 8; ++s) {
-          const int vx = cx + (s & 1), vy = cy + ((s >> 1) & 1), vz = cz + (s >> 2);
-          const bool inner = vx > 0 && vy > 0 && vz > 0 && vx < nx && vy < ny && vz < nz;
-          f[s] = inner ? (vx - 1) + mx * ((vy - 1) + my * (vz - 1)) : -1;
-        }
-        (void)nvx;
-        (void)nvy;
+        for (int s = 0; s < 8; ++s)
+          f[s] = cfree[(cx + (s & 1)) + nvx * ((cy + ((s >> 1) & 1)) + nvy * (cz + (s >> 2)))];
         double K[24][24] = {};
         for (int qp = 0; qp < 8; ++qp) {
           const double xi[3] = {(qp & 1) ? gp : -gp, ((qp >> 1) & 1) ? gp : -gp, (qp >> 2) ? gp : -gp};
@@ -231,6 +275,99 @@ void elast_setup_coarse(fdm_elast *e, cudaStream_t st) {
   launch_convert<double, float>((int64_t)m * m, e->Ainv64, e->Ainv32, st);
   FDM_CUDA(cudaStreamSynchronize(st));
   FDM_CUDA(cudaGetLastError());
+}
+
+// The star-local FDM of the SDC blocks: per axis a and vertex coordinate v the
+// 1D star (the free nodes within p - 1 of the vertex: strictly between the
+// neighbouring vertices, with the boundary node at a traction-free end and
+// without it at a clamped one), its stiffness and mass assembled from
+// A_e = A_hat / L_e and M_e = L_e B_hat over its cells and their generalised
+// eigenpairs; per vertex (the vertices on clamped faces included, as in the
+// FDM/sparse relaxation) a star with its block of the star-solution buffer.
+void setup_star_fdm(fdm_elast *e, const Basis1D &b, const std::vector<double> *vert) {
+  const Grid &g = e->g;
+  const int p = g.p, n = g.n;
+  const int ncell[3] = {g.nx, g.ny, g.nz};
+  std::vector<double> tab;
+  std::vector<int> lo[3], len[3], soff[3];
+  int maxlen = 0;
+  for (int a = 0; a < 3; ++a) {
+    const int na = ncell[a];
+    const bool nat_lo = !(g.dmask & (1 << (2 * a))), nat_hi = !(g.dmask & (1 << (2 * a + 1)));
+    lo[a].assign(na + 1, 0);
+    len[a].assign(na + 1, 0);
+    soff[a].assign(na + 1, 0);
+    for (int v = 0; v <= na; ++v) {
+      // the free nodes within p - 1 of the vertex
+      const int l0 = v == 0 ? (nat_lo ? 0 : 1) : (v - 1) * p + 1;
+      const int l1 = v == na ? (nat_hi ? na * p : na * p - 1) : (v + 1) * p - 1;
+      const int m = l1 - l0 + 1;
+      if (m <= 0) continue;  // p = 1 at a clamped end
+      std::vector<double> A((size_t)m * m, 0.0), M((size_t)m * m, 0.0), S((size_t)m * m), lam(m);
+      for (int c = v - 1; c <= v; ++c) {
+        if (c < 0 || c >= na) continue;
+        const double L = 0.5 * (vert[a][c + 1] - vert[a][c]);
+        for (int i = 0; i < n; ++i)
+          for (int k = 0; k < n; ++k) {
+            const int gi = c * p + i - l0, gk = c * p + k - l0;
+            if (gi < 0 || gi >= m || gk < 0 || gk >= m) continue;
+            A[(size_t)gi * m + gk] += b.A[i * n + k] / L;
+            M[(size_t)gi * m + gk] += L * b.B[i * n + k];
+          }
+      }
+      sym_gen_eig(m, A.data(), M.data(), S.data(), lam.data());
+      lo[a][v] = l0;
+      len[a][v] = m;
+      soff[a][v] = (int)tab.size();
+      tab.insert(tab.end(), S.begin(), S.end());
+      tab.insert(tab.end(), lam.begin(), lam.end());
+      maxlen = std::max(maxlen, m);
+    }
+  }
+  const int nvx = g.nx + 1, nvy = g.ny + 1, nv = nvx * nvy * (g.nz + 1);
+  std::vector<int> vstar(nv, -1), svert;
+  std::vector<int64_t> off;
+  int64_t tot = 0;
+  for (int v = 0; v < nv; ++v) {
+    const int vc[3] = {v % nvx, (v / nvx) % nvy, v / (nvx * nvy)};
+    const int64_t sz = (int64_t)len[0][vc[0]] * len[1][vc[1]] * len[2][vc[2]];
+    if (sz == 0) continue;
+    vstar[v] = (int)svert.size();
+    svert.push_back(v);
+    off.push_back(tot);
+    tot += sz;
+  }
+  StarFdmDev<double> d;
+  d.g = g;
+  for (int a = 0; a < 3; ++a) {
+    d.ax[a].lo = e->upload(lo[a]);
+    d.ax[a].len = e->upload(len[a]);
+    d.ax[a].soff = e->upload(soff[a]);
+  }
+  d.vstar = e->upload(vstar);
+  d.svert = e->upload(svert);
+  d.off = e->upload(off);
+  d.xstride = tot;
+  d.nstar = (int)svert.size();
+  d.maxlen = maxlen;
+  for (int j = 0; j < 3; ++j)
+    for (int a = 0; a < 3; ++a) d.c[j][a] = e->mu + (a == j ? e->mu + e->lam : 0.0);
+  if (star_fdm_smem(maxlen, sizeof(double)) > 227 * 1024)
+    fail(FDM_EINVAL, "fdm_elast_setup: star larger than the shared memory of one CTA");
+  e->sf64 = d;
+  e->sf64.tab = e->upload(tab);
+  e->X64 = e->alloc<double>((size_t)3 * tot);
+  e->sf32.g = d.g;
+  for (int a = 0; a < 3; ++a) e->sf32.ax[a] = d.ax[a];
+  e->sf32.vstar = d.vstar;
+  e->sf32.svert = d.svert;
+  e->sf32.off = d.off;
+  e->sf32.xstride = d.xstride;
+  e->sf32.nstar = d.nstar;
+  e->sf32.maxlen = d.maxlen;
+  std::memcpy(e->sf32.c, d.c, sizeof d.c);
+  e->sf32.tab = e->upload(std::vector<float>(tab.begin(), tab.end()));
+  if (e->opt.precision == FDM_PREC_FP32) e->X32 = e->alloc<float>((size_t)3 * tot);
 }
 
 // omega from k CG-Lanczos steps on A_SDC^{-1} A (undamped SDC relaxation), FP64
@@ -288,11 +425,22 @@ extern "C" {
 // ---------------------------------------------------------------- linear elasticity (Section 4.1)
 int fdm_elast_setup(const fdm_mesh *mesh, int p, double mu, double lam, const fdm_options *opt, fdm_elast **out,
                     void *stream) {
+  return fdm_elast_setup_bc(mesh, p, mu, lam, 63, FDM_SDC_AUTO, opt, out, stream);
+}
+
+int fdm_elast_setup_bc(const fdm_mesh *mesh, int p, double mu, double lam, int dirichlet_faces, int sdc_form,
+                       const fdm_options *opt, fdm_elast **out, void *stream) {
   if (!out) return FDM_EINVAL;
   *out = nullptr;
   if (!mesh || !mesh->xv || !mesh->yv || !mesh->zv || mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || p < 1 ||
       p > 15 || !(mu > 0.0) || !(lam >= 0.0) || !std::isfinite(mu) || !std::isfinite(lam)) {
     ctx_last_error() = "fdm_elast_setup: invalid mesh, degree (1..15) or Lame parameters (mu > 0, lambda >= 0)";
+    return FDM_EINVAL;
+  }
+  if (dirichlet_faces < 1 || dirichlet_faces > 63 || sdc_form < FDM_SDC_AUTO || sdc_form > FDM_SDC_STAR_FDM ||
+      (sdc_form == FDM_SDC_FDM_SPARSE && dirichlet_faces != 63)) {
+    ctx_last_error() = "fdm_elast_setup: dirichlet_faces must be 1..63 (some face clamped) and the FDM/sparse form "
+                       "needs every face clamped";
     return FDM_EINVAL;
   }
   if (mesh->jac) {
@@ -308,7 +456,24 @@ int fdm_elast_setup(const fdm_mesh *mesh, int p, double mu, double lam, const fd
     if (e->opt.flexible_beta < 0) e->opt.flexible_beta = e->opt.precision == FDM_PREC_FP32 ? 1 : 0;
     e->mu = mu;
     e->lam = lam;
+    e->star = sdc_form == FDM_SDC_STAR_FDM || (sdc_form == FDM_SDC_AUTO && dirichlet_faces != 63);
     const int nx = mesh->nx, ny = mesh->ny, nz = mesh->nz, ncell = nx * ny * nz;
+    std::vector<double> vert[3] = {std::vector<double>(mesh->xv, mesh->xv + nx + 1),
+                                   std::vector<double>(mesh->yv, mesh->yv + ny + 1),
+                                   std::vector<double>(mesh->zv, mesh->zv + nz + 1)};
+    for (int a = 0; a < 3; ++a)
+      for (size_t v = 0; v + 1 < vert[a].size(); ++v)
+        if (!(vert[a][v + 1] > vert[a][v])) fail(FDM_EINVAL, "fdm_elast_setup: vertex coordinates must increase");
+    Grid &g = e->g;
+    g.p = p;
+    g.n = p + 1;
+    g.nx = nx; g.ny = ny; g.nz = nz;
+    g.N[0] = nx * p + 1; g.N[1] = ny * p + 1; g.N[2] = nz * p + 1;
+    g.ndof = (int64_t)g.N[0] * g.N[1] * g.N[2];
+    g.ncell = ncell;
+    g.dmask = dirichlet_faces;
+    e->n = g.ndof;
+    const Basis1D basis = make_basis(p);
     std::vector<double> L(3 * (size_t)ncell);
     for (int cz = 0; cz < nz; ++cz)
       for (int cy = 0; cy < ny; ++cy)
@@ -325,7 +490,7 @@ int fdm_elast_setup(const fdm_mesh *mesh, int p, double mu, double lam, const fd
     copt.lanczos_start = nullptr;
     copt.pcg_graph = 0;
     copt.kernel_timing = 0;
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < 3 && !e->star; ++a) {
       std::vector<double> mua(3 * (size_t)ncell);
       for (int c = 0; c < ncell; ++c) {
         const double vol = L[3 * c] * L[3 * c + 1] * L[3 * c + 2];
@@ -336,11 +501,25 @@ int fdm_elast_setup(const fdm_mesh *mesh, int p, double mu, double lam, const fd
       const int rc = fdm_setup(mesh, p, &cf, &copt, &e->comp[a], stream);
       if (rc != FDM_OK) fail(rc, "SDC block " + std::to_string(a) + ": " + ctx_last_error());
     }
-    e->g = e->comp[0]->g;
-    e->n = e->g.ndof;
+    if (e->star) setup_star_fdm(e, basis, vert);
+    // the 1D tables (layout of tab_off) and the Gauss weights of the operator
+    std::vector<double> t(tab_size(g.n), 0.0);
+    auto put = [&](int which, const std::vector<double> &M) {
+      std::copy(M.begin(), M.end(), t.begin() + tab_off(which, g.n));
+    };
+    put(TAB_A, basis.A);
+    put(TAB_B, basis.B);
+    put(TAB_AF, basis.Af);
+    put(TAB_BF, basis.Bf);
+    put(TAB_T, basis.T);
+    put(TAB_VQ, basis.Vq);
+    put(TAB_DQ, basis.Dq);
+    std::copy(basis.xi.begin(), basis.xi.end(), t.begin() + tab_off(TAB_XI, g.n));
+    e->tab64 = e->upload(t);
+    e->tab32 = e->upload(std::vector<float>(t.begin(), t.end()));
     e->Lc = e->upload(L);
-    e->wq64 = e->upload(e->comp[0]->basis.wq);
-    e->wq32 = e->upload(std::vector<float>(e->comp[0]->basis.wq.begin(), e->comp[0]->basis.wq.end()));
+    e->wq64 = e->upload(basis.wq);
+    e->wq32 = e->upload(std::vector<float>(basis.wq.begin(), basis.wq.end()));
     const size_t cn = (size_t)ncell * e->g.n * e->g.n * e->g.n;
     e->G64 = e->alloc<double>(9 * cn);
     e->E64 = e->alloc<double>(3 * cn);
@@ -354,7 +533,7 @@ int fdm_elast_setup(const fdm_mesh *mesh, int p, double mu, double lam, const fd
     e->partial = e->alloc<double>(2 * DOT_BLOCKS);
     e->dots = e->alloc<double>(4);
     e->sc = e->alloc<double>(16);
-    elast_setup_coarse(e, st);
+    elast_setup_coarse(e, vert, st);
     if (e->opt.omega > 0.0) e->omega = e->opt.omega;
     else elast_lanczos(e, e->opt.lanczos_start, st);
     FDM_CUDA(cudaStreamSynchronize(st));
@@ -410,6 +589,8 @@ int elast_pcg_solve(fdm_elast *e, const double *b, double *x, double rtol, int m
     const double nb = std::sqrt(h[0]);
     double nr = nb;
     int it = 0, conv = nb == 0.0, bad = 0;
+    e->rec_its = conv ? 0 : -1;
+    e->rec_misses = 0;
     double *z = e->z, *zold = e->zold;
     if (!conv) {
       elast_pc(e, e->r, z, st);
@@ -432,6 +613,7 @@ int elast_pcg_solve(fdm_elast *e, const double *b, double *x, double rtol, int m
         if (nr <= rtol * nb) {
           // converged on the recursive residual: replace it by the true one,
           // r = b - A x, and stop only if that meets the test too
+          if (e->rec_its < 0) e->rec_its = it;
           elast_op<double, double>(e, x, e->r, b, st);
           mask3(e, e->r, st);
           launch_dot(n3, e->r, e->r, e->partial, e->dots + 2, st);
@@ -441,6 +623,7 @@ int elast_pcg_solve(fdm_elast *e, const double *b, double *x, double rtol, int m
           nr = std::sqrt(h[0]);
           if (!std::isfinite(nr)) { bad = 1; break; }
           if (nr <= rtol * nb) { conv = 1; break; }
+          ++e->rec_misses;
           if (it >= maxit) break;
         }
         std::swap(z, zold);
@@ -460,6 +643,7 @@ int elast_pcg_solve(fdm_elast *e, const double *b, double *x, double rtol, int m
     FDM_CUDA(cudaMemcpy(hsc, e->sc, sizeof hsc, cudaMemcpyDeviceToHost));
     if (hsc[8] != 0.0) bad = 1;
     for (fdm_ctx *c : e->comp) {
+      if (!c) continue;
       int hstat = 0;
       FDM_CUDA(cudaMemcpy(&hstat, c->status, sizeof(int), cudaMemcpyDeviceToHost));
       if (hstat) {
@@ -501,6 +685,7 @@ int fdm_elast_query(fdm_elast *e, int what, void *out, size_t *len) {
       case FDM_Q_OMEGA: put(&e->omega, sizeof(double)); break;
       case FDM_Q_LAMBDA: { double v[2] = {e->lmin, e->lmax}; put(v, sizeof v); break; }
       case FDM_Q_LAUNCHES: { int64_t v = e->launches; e->launches = 0; put(&v, sizeof v); break; }
+      case FDM_Q_RECURSIVE_ITS: { int32_t v[2] = {e->rec_its, e->rec_misses}; put(v, sizeof v); break; }
       default: fail(FDM_EINVAL, "fdm_elast_query: unknown quantity");
     }
   } catch (const Error &err) { return handle_elast(e, err); }

@@ -307,14 +307,15 @@ __global__ void __launch_bounds__(128) k_gather_t(Grid g, const T *__restrict__ 
     return;
   }
   const int gc[3] = {gx, gy, gz};
+  const int ncl[3] = {g.nx, g.ny, g.nz};
   int cA[3][2], lA[3][2], cnt[3];
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
     const int q = gc[ax] / P, rm = gc[ax] - q * P;
-    if (rm == 0) {  // on a cell face along this axis (interior node: both neighbours exist)
-      cA[ax][0] = q - 1; lA[ax][0] = P;
-      cA[ax][1] = q;     lA[ax][1] = 0;
-      cnt[ax] = 2;
+    if (rm == 0) {  // on a cell face along this axis: the cells on either side that exist
+      cnt[ax] = 0;  // (one at a traction-free boundary face)
+      if (q > 0) { cA[ax][cnt[ax]] = q - 1; lA[ax][cnt[ax]++] = P; }
+      if (q < ncl[ax]) { cA[ax][cnt[ax]] = q; lA[ax][cnt[ax]++] = 0; }
     } else {
       cA[ax][0] = q; lA[ax][0] = rm;
       cnt[ax] = 1;

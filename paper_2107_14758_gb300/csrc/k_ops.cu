@@ -150,12 +150,11 @@ __global__ void k_gather_nodes(Grid g, const T *__restrict__ E, Tout *__restrict
   const int n = g.n, p = g.p, n3 = n * n * n;
   for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < g.ndof; id += (int64_t)gridDim.x * blockDim.x) {
     int gc[3] = {int(id % g.N[0]), int((id / g.N[0]) % g.N[1]), int(id / ((int64_t)g.N[0] * g.N[1]))};
-    bool dir = false;
+    const bool dir = node_dirichlet(g, gc[0], gc[1], gc[2]);
     int cA[3][2], lA[3][2], cnt[3];
     const int ncl[3] = {g.nx, g.ny, g.nz};
     for (int ax = 0; ax < 3; ++ax) {
       int v = gc[ax];
-      if (v == 0 || v == g.N[ax] - 1) dir = true;
       cnt[ax] = 0;
       if (v % p == 0) {
         int vv = v / p;

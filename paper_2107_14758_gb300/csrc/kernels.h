@@ -198,6 +198,45 @@ size_t elast_smem(int n);
 template <typename T, typename Tin>
 void launch_elast_cells(const Grid &g, const Tin *u, const T *tab, const T *wq, const double *Lc, double mu, double lam,
                         T *G, T *E, cudaStream_t st);
+// Star-local fast diagonalisation on box cells for a scalar block with a
+// constant coefficient diag(c) (the SDC blocks of Section 4.1, c_a = mu +
+// (mu + lam) delta_aj): the star matrix of vertex v is the Kronecker sum
+// sum_a c_a A_a (x) M_b (x) M_c of its 1D star matrices, so
+// A_v^{-1} = (S_x (x) S_y (x) S_z) D^{-1} (S_x (x) S_y (x) S_z)^T with the 1D
+// generalised eigenpairs A_a S_a = M_a S_a Lam_a, S_a^T M_a S_a = I, and
+// D = sum_a c_a Lam_a.  A 1D star spans the free nodes within p - 1 of its
+// vertex: a vertex on a natural (traction-free) end keeps its boundary node, one
+// on a Dirichlet end loses it (its star is empty for p = 1).
+constexpr int STAR_FDM_MAX_LEN = 29;  // 2 p - 1 for p <= 15
+struct StarFdmAxis {
+  const int *lo = nullptr;    // [n_a + 1] first node of the 1D star of vertex coordinate v
+  const int *len = nullptr;   // [n_a + 1] its nodes (0: empty)
+  const int *soff = nullptr;  // [n_a + 1] offset in tab of S (len x len, row-major, column i =
+                              // eigenvector i), the eigenvalues following at soff + len^2
+};
+template <typename T>
+struct StarFdmDev {
+  Grid g;                        // the grid with its Dirichlet face mask
+  StarFdmAxis ax[3];
+  const T *tab = nullptr;        // the 1D stars' S and eigenvalues
+  const int *vstar = nullptr;    // [(nx+1)(ny+1)(nz+1)] star of each vertex or -1 (empty)
+  const int *svert = nullptr;    // [nstar] vertex of each star
+  const int64_t *off = nullptr;  // [nstar] first value of each star's block in X
+  int64_t xstride = 0;           // values of one component's star blocks
+  int nstar = 0, maxlen = 0;
+  double c[3][3] = {};           // c[j][a]: coefficient of axis a in block j
+};
+// X[j xstride + off[s] + local] = A_s^{-1} R_s r_j for every star s and block
+// j < ncomp (r: component-major [ncomp][ndof])
+template <typename T, typename Tin>
+void launch_star_fdm_solve(const StarFdmDev<T> &d, const Tin *r, T *X, int ncomp, cudaStream_t st);
+// z_j = omega sum_s R_s^T X_s (+ addv_j), summed per node over its stars in
+// lexicographic order of their vertices; Dirichlet nodes 0
+template <typename T, typename Tout>
+void launch_star_fdm_gather(const StarFdmDev<T> &d, const T *X, double omega, const T *addv, Tout *z, int ncomp,
+                            cudaStream_t st);
+size_t star_fdm_smem(int maxlen, size_t elem);
+
 // SIPG on DQ_p box cells (Section 5): cell-major vectors, (p+1)^3 values per cell
 constexpr int SIPG_MAX_N = 11;  // p <= 10
 template <typename T>

@@ -18,12 +18,13 @@ FDM_OK, FDM_EINVAL, FDM_ENOMEM, FDM_ENOTSPD, FDM_ENOCONV, FDM_ENAN, FDM_ETIMEOUT
     0, -1, -2, -3, -4, -5, -6, -7)
 FDM_PREC_FP64, FDM_PREC_FP32 = 0, 1
 FDM_PC_NONE, FDM_PC_ASM, FDM_PC_VCYCLE = 0, 1, 2
+FDM_SDC_AUTO, FDM_SDC_FDM_SPARSE, FDM_SDC_STAR_FDM = 0, 1, 2
 FDM_SURR_AVERAGED, FDM_SURR_EXTERNAL = 0, 1
 (FDM_Q_NDOF, FDM_Q_OMEGA, FDM_Q_LAMBDA, FDM_Q_MU, FDM_Q_NPATCH, FDM_Q_PATCH_CLASS, FDM_Q_CLASS_INFO,
  FDM_Q_GAMMA_ORDER, FDM_Q_FACTOR_NNZ, FDM_Q_PATTERN, FDM_Q_FACTOR, FDM_Q_BASIS, FDM_Q_FACTOR_BYTES,
  FDM_Q_SETUP_SECONDS, FDM_Q_KERNEL_TIMES, FDM_Q_LAUNCHES, FDM_Q_ALGO_BYTES, FDM_Q_STATUS,
  FDM_Q_SURR_FEATURES, FDM_Q_SURR_LABELS, FDM_Q_SURR_BOUNDS, FDM_Q_MUBAR, FDM_Q_SURR_OUTPUT, FDM_Q_TUNING,
- FDM_Q_GMG_LEVELS, FDM_Q_GMG_STENCIL, FDM_Q_ALGO_BYTES_LFORM) = range(1, 28)
+ FDM_Q_GMG_LEVELS, FDM_Q_GMG_STENCIL, FDM_Q_ALGO_BYTES_LFORM, FDM_Q_RECURSIVE_ITS) = range(1, 29)
 (FDM_HQ_NNODE, FDM_HQ_CELL_NODES, FDM_HQ_CELL_FDM, FDM_HQ_CELL_SIGN, FDM_HQ_DIRICHLET, FDM_HQ_NSTAR,
  FDM_HQ_STAR_VERTEX, FDM_HQ_STAR_PTR, FDM_HQ_STAR_NODES, FDM_HQ_PATTERN_PTR, FDM_HQ_PATTERN_ROWPTR,
  FDM_HQ_PATTERN_COLPTR, FDM_HQ_PATTERN_COLS, FDM_HQ_STAR_NINT, FDM_HQ_STAR_CLASS, FDM_HQ_NCLASS,
@@ -109,6 +110,8 @@ def load():
     L.fdm_destroy.restype = None
     L.fdm_elast_setup.argtypes = [C.POINTER(fdm_mesh), C.c_int, C.c_double, C.c_double, C.POINTER(fdm_options),
                                   C.POINTER(vp), vp]
+    L.fdm_elast_setup_bc.argtypes = [C.POINTER(fdm_mesh), C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
+                                     C.POINTER(fdm_options), C.POINTER(vp), vp]
     for f in ("elast_apply", "elast_pc_apply"):
         getattr(L, f).argtypes = [vp, vp, vp, vp]
     L.elast_pcg_solve.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.POINTER(fdm_solve_info), vp]
@@ -231,6 +234,13 @@ def _check_elast(rc, e=None):
 def fdm_elast_setup(mesh, p, mu, lam, opt, stream=None):
     h = C.c_void_p()
     _check_elast(load().fdm_elast_setup(C.byref(mesh), p, mu, lam, C.byref(opt), C.byref(h), _stream(stream)))
+    return h
+
+
+def fdm_elast_setup_bc(mesh, p, mu, lam, dirichlet_faces, sdc_form, opt, stream=None):
+    h = C.c_void_p()
+    _check_elast(load().fdm_elast_setup_bc(C.byref(mesh), p, mu, lam, dirichlet_faces, sdc_form, C.byref(opt),
+                                           C.byref(h), _stream(stream)))
     return h
 
 
@@ -609,10 +619,13 @@ class Context:
 
 class Elasticity:
     """Owns one primal linear-elasticity problem (fdm_elast): box cells,
-    clamped boundary, vectors [3 * ndof] component-major on the device."""
+    clamped on the faces of dirichlet_faces (bit 2a: lower end of axis a, 2a+1:
+    upper; 63 = all) and traction-free on the others, vectors [3 * ndof]
+    component-major on the device; sdc_form one of FDM_SDC_*."""
 
     def __init__(self, p, xv, yv, zv, mu, lam, precision=FDM_PREC_FP32, pc=FDM_PC_VCYCLE, omega=0.0,
-                 lanczos_start=None, lanczos_steps=20, flexible_beta=-1, patch_threads=0, stream=None):
+                 lanczos_start=None, lanczos_steps=20, flexible_beta=-1, patch_threads=0, stream=None,
+                 dirichlet_faces=63, sdc_form=0):
         self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (xv, yv, zv)]
         mesh = fdm_mesh()
         mesh.nx, mesh.ny, mesh.nz = len(xv) - 1, len(yv) - 1, len(zv) - 1
@@ -628,7 +641,8 @@ class Elasticity:
         self.p = p
         self.N = (mesh.nx * p + 1, mesh.ny * p + 1, mesh.nz * p + 1)
         self.ndof = self.N[0] * self.N[1] * self.N[2]
-        self.h = fdm_elast_setup(mesh, p, mu, lam, opt, stream)
+        self.dirichlet_faces = dirichlet_faces
+        self.h = fdm_elast_setup_bc(mesh, p, mu, lam, dirichlet_faces, sdc_form, opt, stream)
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
@@ -664,6 +678,13 @@ class Elasticity:
         out = np.zeros(1)
         fdm_elast_query(self.h, FDM_Q_OMEGA, out)
         return float(out[0])
+
+    def recursive_iterations(self):
+        """(iteration at which the last solve's recursive residual first met
+        the test or -1, true-residual checks that did not)."""
+        out = np.zeros(2, dtype=np.int32)
+        fdm_elast_query(self.h, FDM_Q_RECURSIVE_ITS, out)
+        return int(out[0]), int(out[1])
 
     def lanczos_extremes(self):
         out = np.zeros(2)

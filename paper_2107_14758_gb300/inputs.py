@@ -61,6 +61,24 @@ def gll_points(p):
     return np.concatenate([[-1.0], inner, [1.0]])
 
 
+def body_force_load(xv, yv, zv, p, f):
+    """Load vector [3][ndof] (component-major, x fastest) of a constant body
+    force f: b_a(node) = f_a int phi_node, the integral of the GLL Lagrange
+    function being (GLL weight) x (half-width) per cell and axis, summed over
+    the cells holding the node; the solver ignores the clamped entries."""
+    xi = gll_points(p)
+    w = 2.0 / (p * (p + 1) * _leg.Legendre.basis(p)(xi) ** 2)
+    ints = []
+    for v in (xv, yv, zv):
+        v = np.asarray(v, dtype=np.float64)
+        m = np.zeros((len(v) - 1) * p + 1)
+        for c in range(len(v) - 1):
+            m[c * p:(c + 1) * p + 1] += 0.5 * (v[c + 1] - v[c]) * w
+        ints.append(m)
+    mass = np.einsum("k,j,i->kji", ints[2], ints[1], ints[0]).ravel()
+    return np.outer(np.asarray(f, dtype=np.float64), mass)
+
+
 def node_coords(v, p):
     """Physical coordinates of the GLL nodes along one axis."""
     xi = gll_points(p)
