@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfdmpc.so")
-SOURCES = ["api.cu", "k_asm.cu", "k_stream.cu", "k_ops.cu", "k_factor.cu", "k_surr.cu", "k_cell_op.cu", "k_cell_ri.cu", "k_cluster.cu", "k_gmg.cu", "k_elast.cu", "elast.cu", "k_sipg.cu", "sipg.cu", "noalloc.cu", "k_patch_warp.cu", "basis1d.cpp", "topology.cpp", "gmg.cpp", "sipg_host.cpp", "hexmesh.cpp", "partition.cpp", "k_hex.cu", "hexgpu.cu", "k_sipg_tc.cu", "k_star_fdm.cu"]
+SOURCES = ["api.cu", "k_asm.cu", "k_stream.cu", "k_ops.cu", "k_factor.cu", "k_surr.cu", "k_cell_op.cu", "k_cell_ri.cu", "k_cluster.cu", "k_gmg.cu", "k_elast.cu", "elast.cu", "k_sipg.cu", "sipg.cu", "noalloc.cu", "k_patch_warp.cu", "basis1d.cpp", "topology.cpp", "gmg.cpp", "sipg_host.cpp", "hexmesh.cpp", "partition.cpp", "k_hex.cu", "hexgpu.cu", "k_sipg_tc.cu", "k_star_fdm.cu", "k_surr_kappa.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

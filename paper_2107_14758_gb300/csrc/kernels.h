@@ -336,6 +336,19 @@ void launch_surr_label(int ncell, int n, const double *Gw, const double *wq, con
                        double *F0, double *F1, cudaStream_t st);
 void launch_surr_bound(int ncell, int n, const double *Gw, const double *wq, const double *mu, double *F,
                        cudaStream_t st);
+// labels scored by the Lanczos estimate of kappa(A~_P^{-1} A_P) on each cell's
+// interior patch: compass search over the scaling ratios, centred spectrum.
+// cstar [cell][3]; F [cell][2] log kappa at mubar and at the label; evals
+// [cell] (may be null) the estimates taken.  Degrees 2..PATCH_KAPPA_PMAX.
+constexpr int PATCH_KAPPA_STEPS = 20;       // CG-Lanczos steps per estimate
+constexpr double PATCH_KAPPA_S0 = 0.5;      // first compass step (log mu)
+constexpr double PATCH_KAPPA_SMIN = 1.0 / 256.0;
+constexpr int PATCH_KAPPA_ROUNDS = 48;
+constexpr double PATCH_KAPPA_IMPROVE = 1e-12;  // a move must lower log kappa by more than this
+constexpr int PATCH_KAPPA_PMAX = 10;
+void launch_surr_patch_label(int ncell, int p, const double *Gw, const double *tab, const double *S,
+                             const double *lam, const double *mubar, double *cstar, double *F, int *evals,
+                             cudaStream_t st);
 int mlp_blocks(int ncell);
 // forward (label == nullptr) or forward + loss + per-CTA partial gradient
 void launch_mlp(int ncell, const float *P, const float *feat, const float *label, float *out, float *partial,
