@@ -775,12 +775,47 @@ def bench_deformed(dev, fdmpc, inputs):
     out = {"workload": "q8_deformed12: 12^3 deformed hex mesh, kappa = exp(G), Q8, %d free dofs, N(0,1) load" % free,
            "mixed_solve_dofs_per_s": free / (ms * 1e-3), "mixed_iterations": info.iterations,
            "lanczos_cond_averaged": hi / lo}
-    # learned surrogate: trained on the GPU on three smaller problems of the family, applied here
-    train = [fdmpc.Context(8, *inputs.uniform_vertices(4), jac=t["jac"], kappa=t["kappa"], samples27=t["samples27"],
-                           omega=1.0) for t in (inputs.deformed_problem(4, 8, s) for s in (101, 102, 103))]
+    # the two label kinds applied directly here (mu = mu_avg exp(c)): what each target is worth
+    direct = {}
+    for name, kind in (("theorem1", fdmpc.FDM_LABEL_THEOREM1), ("patch_kappa", fdmpc.FDM_LABEL_PATCH_KAPPA)):
+        c = make(fdmpc.FDM_PREC_FP32)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        lab, score = c.select_labels(kind)
+        torch.cuda.synchronize()
+        label_s = time.time() - t0
+        c.surrogate_load(c.mubar() * np.exp(lab))
+        lo_k, hi_k = c.lanczos_extremes()
+        _, info_k = _timed_solves(c, b, x, 1, DEFORMED_MAXIT)
+        direct[name] = {"iterations": info_k.iterations, "lanczos_cond": hi_k / lo_k, "label_seconds": label_s,
+                        "mean_criterion_avg_label": [float(score[0].mean()), float(score[1].mean())]}
+        c.close()
+    # learned surrogate: training problems of the family (12^3 Q8, seeds 101-103: the workload's cell
+    # size against the coefficient's wavelengths); each label kind is scored by PCG iterations with its
+    # labels applied to them, and the better kind is the target
+    tw = [inputs.deformed_problem(12, 8, s) for s in (101, 102, 103)]
+    train = [fdmpc.Context(8, t["xv"], t["yv"], t["zv"], jac=t["jac"], kappa=t["kappa"], samples27=t["samples27"],
+                           omega=1.0) for t in tw]
+    score_its = {}
+    for name, kind in (("theorem1", fdmpc.FDM_LABEL_THEOREM1), ("patch_kappa", fdmpc.FDM_LABEL_PATCH_KAPPA)):
+        its = 0
+        for t, ctx_t in zip(tw, train):
+            lab, _ = ctx_t.select_labels(kind)
+            s_ = fdmpc.Context(8, t["xv"], t["yv"], t["zv"], jac=t["jac"], kappa=t["kappa"],
+                               samples27=t["samples27"], precision=fdmpc.FDM_PREC_FP32,
+                               lanczos_start=inputs.lanczos_start((12 * 8 + 1) ** 3))
+            s_.surrogate_load(s_.mubar() * np.exp(lab))
+            bt = torch.tensor(inputs.normal_rhs(s_.ndof, 5), device=dev)
+            its += s_.pcg_solve(bt, torch.empty_like(bt), rtol=RTOL, maxit=DEFORMED_MAXIT,
+                                raise_on_noconv=False)[1].iterations
+            s_.close()
+        score_its[name] = its
+    best = min(score_its, key=score_its.get)
+    for ctx_t in train:
+        ctx_t.select_labels(fdmpc.FDM_LABEL_THEOREM1 if best == "theorem1" else fdmpc.FDM_LABEL_PATCH_KAPPA)
     torch.cuda.synchronize()
     t0 = time.time()
-    wts, hist = fdmpc.fdm_surrogate_train([t.h for t in train], inputs.mlp_init(7), 300, 2e-3, 1e-4)
+    wts, hist = fdmpc.fdm_surrogate_train([t.h for t in train], inputs.mlp_init(7), 1000, 2e-3, 1e-4)
     torch.cuda.synchronize()
     train_s = time.time() - t0
     for t in train:
@@ -793,7 +828,9 @@ def bench_deformed(dev, fdmpc, inputs):
     raw.close()
     nf2, kept = ctx.surrogate_apply(wts, judge=1)
     ms2, info2 = _timed_solves(ctx, b, x, 3, DEFORMED_MAXIT)
-    out.update({"learned": {"train_cells": 3 * 64, "train_steps": 300, "train_seconds": train_s,
+    out.update({"labels_applied_directly": direct,
+                "learned": {"label_kind_pcg_score_on_training_problems": score_its, "trained_on": best,
+                            "train_cells": 3 * 1728, "train_steps": 1000, "train_seconds": train_s,
                             "train_loss_first_last": [hist[0], hist[-1]],
                             "mean_cell_bound_log_ratio": {"averaged": float(F[0].mean()), "label": float(F[1].mean()),
                                                           "network": float(F[2].mean())},

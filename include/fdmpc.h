@@ -261,7 +261,8 @@ int fdm_surrogate_load(fdm_ctx *ctx, const double *mu_host, void *stream);
  * 27-point average of M_aa; and the correlations M_ab / sqrt(M_aa M_bb) for
  * ab = 01, 02, 12.  Network: 189 -> 64 (tanh) -> 64 (tanh) -> 3 (linear),
  * FP32 weights packed as W1[64][189], b1[64], W2[64][64], b2[64], W3[3][64],
- * b3[3] (FDM_MLP_NPARAM floats; W[out][in]).  Training label per cell:
+ * b3[3] (FDM_MLP_NPARAM floats; W[out][in]).  Training label per cell (the
+ * default, FDM_LABEL_THEOREM1; see fdm_surrogate_labels for the other kind):
  * c* = log(mu_opt / mu_avg) with mu_opt the scalings that minimise the ratio hi/lo
  * of Theorem 1's bound lo a~ <= a <= hi a~ (the extreme eigenvalues of
  * diag(mu)^{-1/2} M_q diag(mu)^{-1/2} over the cell's (p+1)^3 Gauss points),
@@ -277,10 +278,39 @@ int fdm_surrogate_load(fdm_ctx *ctx, const double *mu_host, void *stream);
  * loss (HOST, may be NULL).  Synchronises `stream`. */
 int fdm_surrogate_grad(fdm_ctx *ctx, const float *w, float *grad, double *loss, void *stream);
 
+/* Training labels.  FDM_LABEL_THEOREM1 (the default): the per-cell optimum of
+ * Theorem 1's bound ratio above.  FDM_LABEL_PATCH_KAPPA: each candidate mu is
+ * scored by the Lanczos estimate of kappa(A~_P(mu)^{-1} A_P) on the cell's
+ * interior patch P (the functions of the cell's interior, homogeneous
+ * Dirichlet on its boundary): A_P the true cell stiffness (Gauss quadrature
+ * with kappa Ghat), A~_P(mu) the separable surrogate's interior block, which
+ * the interior FDM basis S = S_1 (x) S_1 (x) S_1 diagonalises:
+ * A~_P = S^{-T} D S^{-1}, D = mu_x lam_i + mu_y lam_j + mu_z lam_k.  The
+ * estimate: min(48, (p-1)^3) steps of Lanczos with full reorthogonalisation
+ * (two Gram-Schmidt passes) on D^{-1/2} S^T A_P S D^{-1/2} from
+ * r0[i] = frac(i 2654435769 / 2^32) - 1/2, ended early when the next vector's
+ * norm is below 1e-10 times the largest diagonal entry; the extreme
+ * eigenvalues of the Lanczos matrix (bisection) estimate lambda_min,
+ * lambda_max.  With mu = mu_avg exp((0, t1, t2) + gamma), (t1, t2) minimises
+ * log(lambda_max / lambda_min) by compass search from 0 (step 1/2, the best
+ * of the four moves +-step that lowers it by more than 1e-9 is taken, else the
+ * step halves, until it is below 1/256 or after 48 rounds) and gamma =
+ * log(lambda_min lambda_max) / 2 centres the labelled spectrum.  Degrees 2..8
+ * (FDM_EINVAL otherwise).
+ * fdm_surrogate_labels computes the labels of `kind` (once per context) and
+ * selects them for this context's fdm_surrogate_grad and fdm_surrogate_train.
+ * labels (HOST, 3 ncell: c per cell, may be NULL); score (HOST, 2 ncell, may
+ * be NULL): per cell the label's criterion at mu_avg, then at the label
+ * (THEOREM1: log(hi/lo) of the bound; PATCH_KAPPA: log(lambda_max/lambda_min)).
+ * Synchronises `stream`. */
+#define FDM_LABEL_THEOREM1 0
+#define FDM_LABEL_PATCH_KAPPA 1
+int fdm_surrogate_labels(fdm_ctx *ctx, int kind, double *labels, double *score, void *stream);
+
 /* Trains the network on every cell of the k contexts (all on the current
  * device): `steps` full-batch Adam steps (beta1 0.9, beta2 0.999, eps 1e-8,
  * bias-corrected, step size lr, decoupled weight decay weight_decay >= 0)
- * from w_init (HOST).  w_out (HOST) receives the weights, loss_hist (HOST,
+ * from w_init (HOST), against each context's selected labels.  w_out (HOST) receives the weights, loss_hist (HOST,
  * steps + 1 doubles, may be NULL) the loss before each step and after the
  * last.  Device scratch is allocated and freed inside the call.
  * Synchronises `stream`. */

@@ -13,15 +13,21 @@ the cell boundary).  Plain definitions throughout:
   on the interior GLL functions, assembled densely from the Gauss points;
 * A~_P(mu) = mu_x B (x) B (x) A + mu_y B (x) A (x) B + mu_z A (x) B (x) B on the
   interior block of the reference 1D stiffness A and mass B;
-* the estimate: K steps of conjugate gradients on A_P x = r0 preconditioned by
-  A~_P^{-1} (dense solves), from the fixed start vector r0 below; the CG
-  coefficients give the Lanczos tridiagonal matrix of A~_P^{-1} A_P, whose
-  extreme eigenvalues (numpy's symmetric tridiagonal routine) estimate
-  lambda_min and lambda_max;
+* the estimate: Lanczos with full reorthogonalisation (two classical
+  Gram-Schmidt passes per step), K = min(48, m) steps from the fixed start
+  vector r0 below, on the symmetric form C = D^{-1/2} S^T A_P S D^{-1/2} of
+  A~_P^{-1} A_P, where S = S_1 (x) S_1 (x) S_1 is the interior FDM basis
+  (A_II S_1 = B_II S_1 Lam, S_1^T B_II S_1 = I, Section 2.3) and
+  D = mu_x lam_i + mu_y lam_j + mu_z lam_k, so that A~_P = S^{-T} D S^{-1};
+  the run stops early once the next Lanczos vector's norm falls below 1e-10
+  times the largest diagonal entry; the extreme eigenvalues of the Lanczos
+  tridiagonal matrix (numpy's symmetric routine) estimate lambda_min and
+  lambda_max;
 * the label: mu = mubar exp(c), c = (0, t1, t2) + gamma (1, 1, 1); (t1, t2)
   minimises log(lambda_max / lambda_min) by compass search from 0 (the four
-  moves +-s along t1 then t2 are scored, the best strictly better one is
-  taken, else s is halved; s from 1/2 down to below 1/256, at most 48 rounds),
+  moves +-s along t1 then t2 are scored, the best one that lowers it by more
+  than 1e-9 is taken, else s is halved; s from 1/2 down to below 1/256, at
+  most 48 rounds),
   and gamma = log(lambda_min lambda_max) / 2 centres the spectrum of the
   labelled patch (lambda_min lambda_max = 1), as the Theorem 1 labels centre
   their bound.
@@ -30,11 +36,12 @@ import numpy as np
 
 from . import basis1d, gauss, lagrange
 
-LANCZOS_STEPS = 20
+LANCZOS_STEPS = 48
 SEARCH_S0 = 0.5
 SEARCH_SMIN = 1.0 / 256.0
 SEARCH_ROUNDS = 48
-IMPROVE = 1e-12  # a move must lower log kappa by more than this
+IMPROVE = 1e-9  # a move must lower log kappa by more than this
+BREAKDOWN = 1e-10  # relative norm of the next Lanczos vector that ends the run
 
 
 def start_vector(m):
@@ -66,6 +73,11 @@ class CellPatches:
         self.w = np.kron(wg, np.kron(wg, wg))
         Ai, Bi = b["A"][1:p, 1:p], b["B"][1:p, 1:p]
         self.K = [np.kron(Bi, np.kron(Bi, Ai)), np.kron(Bi, np.kron(Ai, Bi)), np.kron(Ai, np.kron(Bi, Bi))]
+        self.S3 = np.kron(b["S"], np.kron(b["S"], b["S"]))
+        lam = b["lam"]
+        self.lam3 = [np.kron(np.ones(p - 1), np.kron(np.ones(p - 1), lam)),
+                     np.kron(np.ones(p - 1), np.kron(lam, np.ones(p - 1))),
+                     np.kron(lam, np.kron(np.ones(p - 1), np.ones(p - 1)))]
         self.m = (p - 1) ** 3
         self.r0 = start_vector(self.m)
 
@@ -81,39 +93,38 @@ class CellPatches:
     def surrogate_matrix(self, mu):
         return mu[0] * self.K[0] + mu[1] * self.K[1] + mu[2] * self.K[2]
 
-    def lanczos(self, A, At, steps=LANCZOS_STEPS):
-        """(lambda_min, lambda_max) estimates of At^{-1} A from `steps` PCG steps."""
-        r = self.r0.copy()
-        z = np.linalg.solve(At, r)
-        d = z.copy()
-        rz = r @ z
+    def symmetric_form(self, A, mu):
+        """C = D^{-1/2} S^T A S D^{-1/2}, similar to A~(mu)^{-1} A."""
+        D = mu[0] * self.lam3[0] + mu[1] * self.lam3[1] + mu[2] * self.lam3[2]
+        R = self.S3 / np.sqrt(D)[None, :]
+        return R.T @ A @ R
+
+    def lanczos(self, A, mu, steps=LANCZOS_STEPS):
+        """(lambda_min, lambda_max) estimates of A~(mu)^{-1} A."""
+        C = self.symmetric_form(A, mu)
+        K = min(steps, self.m)
+        V = [self.r0 / np.linalg.norm(self.r0)]
         al, be = [], []
-        for _ in range(min(steps, self.m)):
-            if not rz > 0.0:
+        for k in range(K):
+            w = C @ V[k]
+            al.append(w @ V[k])
+            w = w - al[k] * V[k] - (be[k - 1] * V[k - 1] if k > 0 else 0.0)
+            for _ in range(2):
+                Vm = np.array(V)
+                w = w - Vm.T @ (Vm @ w)
+            b = np.linalg.norm(w)
+            if k == K - 1 or not b > BREAKDOWN * max(abs(x) for x in al):
                 break
-            q = A @ d
-            dq = d @ q
-            if not dq > 0.0:
-                break
-            alpha = rz / dq
-            al.append(alpha)
-            r = r - alpha * q
-            z = np.linalg.solve(At, r)
-            rzn = r @ z
-            beta = rzn / rz
-            be.append(beta)
-            rz = rzn
-            d = z + beta * d
+            be.append(b)
+            V.append(w / b)
         k = len(al)
-        dd = np.array([1.0 / al[j] + (be[j - 1] / al[j - 1] if j > 0 else 0.0) for j in range(k)])
-        ee = np.array([np.sqrt(be[j]) / al[j] for j in range(k - 1)])
-        T = np.diag(dd) + np.diag(ee, 1) + np.diag(ee, -1)
+        T = np.diag(al) + np.diag(be[:k - 1], 1) + np.diag(be[:k - 1], -1)
         ev = np.linalg.eigvalsh(T)
         return ev[0], ev[-1]
 
     def log_kappa(self, e, c, A=None):
         A = self.true_matrix(e) if A is None else A
-        lo, hi = self.lanczos(A, self.surrogate_matrix(self.mubar[e] * np.exp(c)))
+        lo, hi = self.lanczos(A, self.mubar[e] * np.exp(c))
         return np.log(hi / lo), lo, hi
 
     def label(self, e):

@@ -1367,6 +1367,35 @@ void ensure_labels(fdm_ctx *c, cudaStream_t st) {
   c->cstar = cs;
 }
 
+// labels scored by the Lanczos condition number of each cell's interior patch,
+// computed once per context
+void ensure_kappa_labels(fdm_ctx *c, cudaStream_t st) {
+  if (c->ckap) return;
+  const int ncell = c->g.ncell, p = c->p;
+  if (p < 2 || p > PATCH_KAPPA_PMAX) fail(FDM_EINVAL, "patch-condition labels need p in 2..8");
+  c->S64 = c->upload(c->basis.S);
+  c->lam64 = c->upload(c->basis.lam);
+  double *ck = c->alloc<double>(3 * (size_t)ncell);
+  c->Fkap = c->alloc<double>(2 * (size_t)ncell);
+  c->label32k = c->alloc<float>(3 * (size_t)ncell);
+  launch_surr_patch_label(ncell, p, c->Gw64, c->tab64, c->S64, c->lam64, c->mubar, ck, c->Fkap, nullptr, st);
+  launch_convert<double, float>(3 * (int64_t)ncell, ck, c->label32k, st);
+  FDM_CUDA(cudaStreamSynchronize(st));
+  FDM_CUDA(cudaGetLastError());
+  c->launches += 2;
+  c->ckap = ck;
+}
+
+// the training labels the context has selected
+const float *train_labels(fdm_ctx *c, cudaStream_t st) {
+  if (c->label_kind == FDM_LABEL_PATCH_KAPPA) {
+    ensure_kappa_labels(c, st);
+    return c->label32k;
+  }
+  ensure_labels(c, st);
+  return c->label32;
+}
+
 // device buffers of one training run, released on every exit path
 struct DevScratch {
   std::vector<void *> p;
@@ -1731,14 +1760,14 @@ int fdm_surrogate_grad(fdm_ctx *c, const float *w_host, float *grad_host, double
   try {
     need_surrogate_data(c);
     cudaStream_t st = (cudaStream_t)stream;
-    ensure_labels(c, st);
+    const float *lab = train_labels(c, st);
     const int ncell = c->g.ncell, nblk = mlp_blocks(ncell);
     DevScratch s;
     float *P = s.get<float>(MLP_NPARAM), *g = s.get<float>(MLP_NPARAM), *out = s.get<float>(3 * (size_t)ncell);
     float *partial = s.get<float>((size_t)nblk * MLP_NPARAM), *lossp = s.get<float>(nblk);
     double *dl = s.get<double>(1);
     FDM_CUDA(cudaMemcpyAsync(P, w_host, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice, st));
-    launch_mlp(ncell, P, c->feat, c->label32, out, partial, lossp, st);
+    launch_mlp(ncell, P, c->feat, lab, out, partial, lossp, st);
     launch_mlp_reduce(nblk, partial, lossp, g, dl, st);
     c->launches += 2;
     FDM_CUDA(cudaMemcpyAsync(grad_host, g, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost, st));
@@ -1746,6 +1775,42 @@ int fdm_surrogate_grad(fdm_ctx *c, const float *w_host, float *grad_host, double
     FDM_CUDA(cudaMemcpyAsync(&l, dl, sizeof(double), cudaMemcpyDeviceToHost, st));
     FDM_CUDA(cudaStreamSynchronize(st));
     if (loss) *loss = l;
+  } catch (const Error &e) { return handle(c, e); }
+  return FDM_OK;
+}
+
+int fdm_surrogate_labels(fdm_ctx *c, int kind, double *labels_host, double *score_host, void *stream) {
+  if (!c || (kind != FDM_LABEL_THEOREM1 && kind != FDM_LABEL_PATCH_KAPPA)) return FDM_EINVAL;
+  try {
+    need_surrogate_data(c);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ncell = c->g.ncell;
+    const double *lab, *F0, *F1;
+    if (kind == FDM_LABEL_PATCH_KAPPA) {
+      ensure_kappa_labels(c, st);
+      lab = c->ckap;
+    } else {
+      ensure_labels(c, st);
+      lab = c->cstar;
+    }
+    c->label_kind = kind;
+    if (labels_host)
+      FDM_CUDA(cudaMemcpy(labels_host, lab, sizeof(double) * 3 * (size_t)ncell, cudaMemcpyDeviceToHost));
+    if (score_host) {
+      std::vector<double> h(2 * (size_t)ncell);
+      if (kind == FDM_LABEL_PATCH_KAPPA) {
+        FDM_CUDA(cudaMemcpy(h.data(), c->Fkap, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int e = 0; e < ncell; ++e) {
+          score_host[e] = h[2 * (size_t)e];
+          score_host[ncell + e] = h[2 * (size_t)e + 1];
+        }
+      } else {
+        F0 = c->F0;
+        F1 = c->F1;
+        FDM_CUDA(cudaMemcpy(score_host, F0, sizeof(double) * ncell, cudaMemcpyDeviceToHost));
+        FDM_CUDA(cudaMemcpy(score_host + ncell, F1, sizeof(double) * ncell, cudaMemcpyDeviceToHost));
+      }
+    }
   } catch (const Error &e) { return handle(c, e); }
   return FDM_OK;
 }
@@ -1763,7 +1828,7 @@ int fdm_surrogate_train(int k, fdm_ctx *const *ctxs, const float *w_init, int st
     for (int i = 0; i < k; ++i) {
       if (!ctxs[i]) fail(FDM_EINVAL, "fdm_surrogate_train: null context");
       need_surrogate_data(ctxs[i]);
-      ensure_labels(ctxs[i], st);
+      train_labels(ctxs[i], st);
       ntot += ctxs[i]->g.ncell;
     }
     if (ntot > (int64_t)1 << 26) fail(FDM_EINVAL, "fdm_surrogate_train: too many cells");
@@ -1775,8 +1840,8 @@ int fdm_surrogate_train(int k, fdm_ctx *const *ctxs, const float *w_init, int st
       const int nc = ctxs[i]->g.ncell;
       FDM_CUDA(cudaMemcpyAsync(X + off * MLP_NIN, ctxs[i]->feat, sizeof(float) * MLP_NIN * nc,
                                cudaMemcpyDeviceToDevice, st));
-      FDM_CUDA(cudaMemcpyAsync(Y + off * 3, ctxs[i]->label32, sizeof(float) * 3 * nc, cudaMemcpyDeviceToDevice,
-                               st));
+      FDM_CUDA(cudaMemcpyAsync(Y + off * 3, train_labels(ctxs[i], st), sizeof(float) * 3 * nc,
+                               cudaMemcpyDeviceToDevice, st));
       off += nc;
     }
     float *P = s.get<float>(MLP_NPARAM), *g = s.get<float>(MLP_NPARAM), *m = s.get<float>(MLP_NPARAM),

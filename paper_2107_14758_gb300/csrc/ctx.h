@@ -100,6 +100,10 @@ struct fdm_ctx {
   float *feat = nullptr;        // network inputs [ncell][189] (with samples27)
   double *cstar = nullptr, *F0 = nullptr, *F1 = nullptr;  // labels and bound ratios (on first use)
   float *label32 = nullptr;
+  // labels scored by the interior patch's Lanczos condition number (on request)
+  int label_kind = 0;  // FDM_LABEL_*: the labels fdm_surrogate_grad / _train use
+  double *ckap = nullptr, *Fkap = nullptr, *S64 = nullptr, *lam64 = nullptr;
+  float *label32k = nullptr;
   float *surr_c = nullptr;      // network outputs of the last fdm_surrogate_apply
   int *d_count = nullptr;
   double *Fcur = nullptr;       // bound ratios at the current mu (queries)

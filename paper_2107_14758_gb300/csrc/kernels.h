@@ -340,12 +340,13 @@ void launch_surr_bound(int ncell, int n, const double *Gw, const double *wq, con
 // interior patch: compass search over the scaling ratios, centred spectrum.
 // cstar [cell][3]; F [cell][2] log kappa at mubar and at the label; evals
 // [cell] (may be null) the estimates taken.  Degrees 2..PATCH_KAPPA_PMAX.
-constexpr int PATCH_KAPPA_STEPS = 20;       // CG-Lanczos steps per estimate
-constexpr double PATCH_KAPPA_S0 = 0.5;      // first compass step (log mu)
+constexpr int PATCH_KAPPA_STEPS = 48;          // Lanczos steps per estimate (at most)
+constexpr double PATCH_KAPPA_BREAKDOWN = 1e-10;  // relative norm of the next vector that ends a run
+constexpr double PATCH_KAPPA_S0 = 0.5;         // first compass step (log mu)
 constexpr double PATCH_KAPPA_SMIN = 1.0 / 256.0;
 constexpr int PATCH_KAPPA_ROUNDS = 48;
-constexpr double PATCH_KAPPA_IMPROVE = 1e-12;  // a move must lower log kappa by more than this
-constexpr int PATCH_KAPPA_PMAX = 10;
+constexpr double PATCH_KAPPA_IMPROVE = 1e-9;   // a move must lower log kappa by more than this
+constexpr int PATCH_KAPPA_PMAX = 8;            // the Lanczos vectors stay in shared memory
 void launch_surr_patch_label(int ncell, int p, const double *Gw, const double *tab, const double *S,
                              const double *lam, const double *mubar, double *cstar, double *F, int *evals,
                              cudaStream_t st);

@@ -19,6 +19,7 @@ FDM_OK, FDM_EINVAL, FDM_ENOMEM, FDM_ENOTSPD, FDM_ENOCONV, FDM_ENAN, FDM_ETIMEOUT
 FDM_PREC_FP64, FDM_PREC_FP32 = 0, 1
 FDM_PC_NONE, FDM_PC_ASM, FDM_PC_VCYCLE = 0, 1, 2
 FDM_SDC_AUTO, FDM_SDC_FDM_SPARSE, FDM_SDC_STAR_FDM = 0, 1, 2
+FDM_LABEL_THEOREM1, FDM_LABEL_PATCH_KAPPA = 0, 1
 FDM_SURR_AVERAGED, FDM_SURR_EXTERNAL = 0, 1
 (FDM_Q_NDOF, FDM_Q_OMEGA, FDM_Q_LAMBDA, FDM_Q_MU, FDM_Q_NPATCH, FDM_Q_PATCH_CLASS, FDM_Q_CLASS_INFO,
  FDM_Q_GAMMA_ORDER, FDM_Q_FACTOR_NNZ, FDM_Q_PATTERN, FDM_Q_FACTOR, FDM_Q_BASIS, FDM_Q_FACTOR_BYTES,
@@ -102,6 +103,7 @@ def load():
     fp = C.POINTER(C.c_float)
     L.fdm_surrogate_grad.argtypes = [vp, fp, fp, dp, vp]
     L.fdm_surrogate_train.argtypes = [C.c_int, C.POINTER(vp), fp, C.c_int, C.c_double, C.c_double, fp, dp, vp]
+    L.fdm_surrogate_labels.argtypes = [vp, C.c_int, dp, dp, vp]
     L.fdm_surrogate_apply.argtypes = [vp, fp, C.c_int, ip, ip, vp]
     L.fdm_query.argtypes = [vp, C.c_int, vp, C.POINTER(C.c_size_t)]
     L.fdm_last_error.argtypes = [vp]
@@ -371,6 +373,15 @@ def fdm_surrogate_grad(ctx, w, stream=None):
     return g, loss.value
 
 
+def fdm_surrogate_labels(ctx, ncell, kind, stream=None):
+    """(labels [ncell][3], score [2][ncell]) of the label kind FDM_LABEL_*,
+    which becomes the context's training labels."""
+    lab = np.zeros((ncell, 3))
+    score = np.zeros((2, ncell))
+    _check(load().fdm_surrogate_labels(ctx, kind, _dptr(lab), _dptr(score), _stream(stream)), ctx)
+    return lab, score
+
+
 def fdm_surrogate_train(ctxs, w_init, steps, lr, weight_decay=0.0, stream=None):
     """Trains on every cell of the contexts; returns (weights, loss history)."""
     w = _weights(w_init)
@@ -519,6 +530,11 @@ class Context:
 
     def surrogate_labels(self):
         return self.query(FDM_Q_SURR_LABELS, np.float64, 3 * self.ncell).reshape(self.ncell, 3)
+
+    def select_labels(self, kind):
+        """Computes and selects the training labels of kind FDM_LABEL_*:
+        (labels [ncell][3], score [2][ncell] at mu_avg and at the label)."""
+        return fdm_surrogate_labels(self.h, self.ncell, kind)
 
     def surrogate_bounds(self):
         """(F at mu_avg, F at the label, F at the current mu), F = log(hi/lo) per cell."""
