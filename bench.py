@@ -522,6 +522,15 @@ def bench_gpu(args):
             "p15_sweep_target": "<= 450 us per FP32 sweep, >= 0.5 of measured HBM",
             "unstructured_q7": {k: (secondary.get("unstructured", {}).get("mixed", {}) or {}).get(k)
                                 for k in ("solve_dofs_per_s", "iterations", "true_rel_residual")},
+            "deformed_q8": {"averaged_mixed_dofs_per_s": secondary.get("deformed", {}).get("mixed_solve_dofs_per_s"),
+                            "learned_judged_dofs_per_s": (secondary.get("deformed", {}).get("learned") or {}).get(
+                                "judged_solve_dofs_per_s"),
+                            "fp64_dofs_per_s": secondary.get("deformed", {}).get("fp64_solve_dofs_per_s"),
+                            "iterations_averaged_learned": [
+                                secondary.get("deformed", {}).get("mixed_iterations"),
+                                (secondary.get("deformed", {}).get("learned") or {}).get("judged_iterations")]},
+            "elasticity_table3_setting_p15": (secondary.get("elasticity", {}).get("iterations_traction_free_x0") or
+                                              {}).get("p=15"),
             "cpu_oracle_same_config_dofs_per_s": cpu["value"] if cpu else None}
         print(json.dumps(line), flush=True)
     ctx.close()
