@@ -38,8 +38,8 @@ FALLBACK_HBM_GBS = 6800.0
 # graded Q7 (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture,
 # summarised in profiles/patch_solve_q7_graded16.md), valid while the kernel
 # source k_asm.cu has the recorded sha256; null otherwise.
-PROFILED_TRAFFIC = {"kernel_source_sha256": "ad23636d1fd46583739d27dff466d95787f2c30f791b8bc2ec86084533f54867",
-                    "dram_bytes_per_launch": 0.3375e9,
+PROFILED_TRAFFIC = {"kernel_source_sha256": "7b09899072be12a241bcb679d1f49e641d0fe85b05caf64016a2e7b4a20a635b",
+                    "dram_bytes_per_launch": 0.33754e9,
                     "source": "profiles/patch_solve_q7_graded16.md (one ncu capture, same kernel source)"}
 
 
