@@ -911,7 +911,8 @@ def bench_unstructured(dev, fdmpc, inputs, peak):
 
 def bench_batched(dev, fdmpc, inputs, reps=3):
     """64 independent graded problems (n in 2..10, p in 3..15) solved in one CUDA
-    graph: aggregate DoF/s and per-solve latency (device timer)."""
+    graph (smaller problems at higher kernel priority): aggregate DoF/s and
+    per-solve latency (device timer); then the same problems one after another."""
     import torch
     probs = inputs.batch_problems(64, 1000)
     ctxs, bs = [], []
@@ -941,11 +942,30 @@ def bench_batched(dev, fdmpc, inputs, reps=3):
     ms = float(np.median(times))
     worst = max(i.true_rnorm / i.rnorm0 for i in infos)
     fdmpc.fdm_batch_destroy(batch)
+    # the same problems one after another (each its own device-driven solve): the time the batch
+    # would take without sharing the GPU, and the throughput by degree
+    seq_ms, by_p = 0.0, {}
+    for c, b, x, w in zip(ctxs, bs, xs, probs):
+        c.pcg_solve(b, x, rtol=RTOL, maxit=MAXIT)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(torch.cuda.current_stream())
+        c.pcg_solve(b, x, rtol=RTOL, maxit=MAXIT)
+        e1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        seq_ms += t
+        d = by_p.setdefault(w["p"], [0, 0.0])
+        d[0] += _free_dofs(c.N)
+        d[1] += t
     for c in ctxs:
         c.close()
     return {"workload": "64 graded problems, n^3 cells n in 2..10, Q_p p in 3..15 (seeds 1000..1063), "
                         "%d free dofs in total, mixed precision, one CUDA graph" % free,
             "aggregate_dofs_per_s": free / (ms * 1e-3), "batch_ms": ms,
+            "one_after_another_ms": seq_ms, "one_after_another_dofs_per_s": free / (seq_ms * 1e-3),
+            "one_after_another_dofs_per_s_by_degree": {str(p): v[0] / (v[1] * 1e-3) for p, v in sorted(by_p.items())},
             "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
             "iterations_min_max": [min(i.iterations for i in infos), max(i.iterations for i in infos)],
             "worst_true_rel_residual": worst, "setup_seconds": setup_s}

@@ -1173,6 +1173,36 @@ cudaGraphNode_t graph_leaf(cudaGraph_t g) {
   return leaf;
 }
 
+// the scheduling priority of every kernel node of a captured graph
+void set_kernel_priority(cudaGraph_t g, int prio) {
+  size_t nn = 0;
+  FDM_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  FDM_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+  cudaKernelNodeAttrValue v{};
+  v.priority = prio;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    FDM_CUDA(cudaGraphNodeGetType(nd, &t));
+    if (t == cudaGraphNodeTypeKernel) FDM_CUDA(cudaGraphKernelNodeSetAttribute(nd, cudaLaunchAttributePriority, &v));
+  }
+}
+
+// per problem its kernels' priority: the smaller a problem (free dofs), the
+// higher, so that small problems finish early while the larger ones fill the
+// SMs they leave; the device's priority levels are spread over the size ranks
+std::vector<int> batch_priorities(const std::vector<fdm_ctx *> &ctxs) {
+  const int k = (int)ctxs.size();
+  int least = 0, greatest = 0;
+  FDM_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  std::vector<int> order(k), prio(k, least);
+  for (int i = 0; i < k; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ctxs[a]->g.ndof < ctxs[b]->g.ndof; });
+  const int levels = least - greatest + 1;
+  for (int r = 0; r < k; ++r) prio[order[r]] = greatest + (int)((int64_t)r * levels / k);
+  return prio;
+}
+
 void build_batch_graph(fdm_batch *B, const double *const *bv, double *const *xv, double rtol, int maxit) {
   B->release_graph();
   B->init_kernels.clear();
@@ -1194,6 +1224,7 @@ void build_batch_graph(fdm_batch *B, const double *const *bv, double *const *xv,
     kp.kernelParams = args;
     FDM_CUDA(cudaGraphAddKernelNode(&t0, G, nullptr, 0, &kp));
   }
+  const std::vector<int> prio = batch_priorities(B->ctxs);
   for (int i = 0; i < k; ++i) {
     fdm_ctx *c = B->ctxs[i];
     const int64_t n = c->g.ndof;
@@ -1216,6 +1247,7 @@ void build_batch_graph(fdm_batch *B, const double *const *bv, double *const *xv,
       size_t nk = 0;
       FDM_CUDA(cudaGraphGetNodes(gi, nullptr, &nk));
       B->init_kernels.push_back(nk + 1);  // + the start kernel below
+      set_kernel_priority(gi, prio[i]);
       FDM_CUDA(cudaGraphAddChildGraphNode(&ni, G, &t0, 1, gi));
       FDM_CUDA(cudaGraphDestroy(gi));
       cudaGraphConditionalHandle h;
@@ -1229,6 +1261,9 @@ void build_batch_graph(fdm_batch *B, const double *const *bv, double *const *xv,
         kp.blockDim = dim3(32);
         kp.kernelParams = args;
         FDM_CUDA(cudaGraphAddKernelNode(&nb, G, &ni, 1, &kp));
+        cudaKernelNodeAttrValue v{};
+        v.priority = prio[i];
+        FDM_CUDA(cudaGraphKernelNodeSetAttribute(nb, cudaLaunchAttributePriority, &v));
       }
       cudaGraphNodeParams cp{};
       cp.type = cudaGraphNodeTypeConditional;
@@ -1245,6 +1280,7 @@ void build_batch_graph(fdm_batch *B, const double *const *bv, double *const *xv,
       size_t nbk = 0;
       FDM_CUDA(cudaGraphGetNodes(body, nullptr, &nbk));
       B->body_kernels.push_back(nbk);
+      set_kernel_priority(body, prio[i]);
       // the true-residual check, run when the recursive residual has converged
       cudaGraphNode_t leaf = graph_leaf(body), nv;
       cudaGraphNodeParams vp{};
@@ -1260,6 +1296,7 @@ void build_batch_graph(fdm_batch *B, const double *const *bv, double *const *xv,
       size_t nvk = 0;
       FDM_CUDA(cudaGraphGetNodes(vbody, nullptr, &nvk));
       B->verify_kernels.push_back(nvk);
+      set_kernel_priority(vbody, prio[i]);
     } catch (...) {
       c->capturing = false;
       cudaStreamCaptureStatus cs;
@@ -1274,7 +1311,7 @@ void build_batch_graph(fdm_batch *B, const double *const *bv, double *const *xv,
     c->capturing = false;
     c->launches = counted;
   }
-  FDM_CUDA(cudaGraphInstantiate(&B->exec, G, 0));
+  FDM_CUDA(cudaGraphInstantiate(&B->exec, G, cudaGraphInstantiateFlagUseNodePriority));
   B->key_b.assign(bv, bv + k);
   B->key_x.assign(xv, xv + k);
   B->key_rtol = rtol;

@@ -108,6 +108,10 @@ def test_batched_edge_cases():
         fdmpc.fdm_batch_destroy(batch)
 
 
+def _free(ctx):
+    return (ctx.N[0] - 2) * (ctx.N[1] - 2) * (ctx.N[2] - 2)
+
+
 def test_full_batch_workload():
     """The 64-problem workload as the benchmark runs it (n in 2..10, p in
     3..15, mixed precision, autotuned patch solves, one graph): every solve
@@ -128,6 +132,12 @@ def test_full_batch_workload():
         record("batched_full_worst", true_rel=max(i.true_rnorm / i.rnorm0 for i in infos))
         for info in infos:
             assert info.converged and info.true_rnorm <= 1e-8 * info.rnorm0
+        # the smaller problems run at higher kernel priority: the smallest quarter is done
+        # before the largest quarter
+        lat = np.array([i.seconds for i in infos])
+        size = np.array([_free(c) for c in ctxs])
+        order = np.argsort(size)
+        assert np.median(lat[order[:16]]) < np.median(lat[order[-16:]])
         small = sorted(range(64), key=lambda i: (len(probs[i]["xv"]) - 1) ** 3 * probs[i]["p"] ** 3)[:4]
         for i in small:
             w = probs[i]
