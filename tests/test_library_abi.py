@@ -77,7 +77,14 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert L.fdm_elast_setup(ctypes.byref(mesh), 3, 1.0, 1.0, ctypes.byref(o), ctypes.byref(h), None) == \
         fdmpc.FDM_EINVAL
     assert "box cells" in L.fdm_elast_last_error(None).decode()
+    mesh.jac = None
+    # boundary mask and SDC form: no face clamped, bits beyond the six faces, the
+    # FDM/sparse form with a traction-free face, an unknown form
+    for mask, form in ((0, 0), (64, 0), (1, fdmpc.FDM_SDC_FDM_SPARSE), (63, 3)):
+        assert L.fdm_elast_setup_bc(ctypes.byref(mesh), 3, 1.0, 1.0, mask, form, ctypes.byref(o), ctypes.byref(h),
+                                    None) == fdmpc.FDM_EINVAL
     assert L.elast_apply(None, None, None, None) == fdmpc.FDM_EINVAL
+    assert L.fdm_surrogate_labels(None, fdmpc.FDM_LABEL_PATCH_KAPPA, None, None, None) == fdmpc.FDM_EINVAL
 
 
 def test_sipg_and_noalloc_arguments_rejected_without_gpu(lib):
