@@ -531,6 +531,9 @@ def bench_gpu(args):
                                 (secondary.get("deformed", {}).get("learned") or {}).get("judged_iterations")]},
             "elasticity_table3_setting_p15": (secondary.get("elasticity", {}).get("iterations_traction_free_x0") or
                                               {}).get("p=15"),
+            "batched": {k: secondary.get("batched", {}).get(k)
+                        for k in ("aggregate_dofs_per_s", "one_after_another_dofs_per_s", "latency_ms_p50",
+                                  "latency_ms_p99")},
             "cpu_oracle_same_config_dofs_per_s": cpu["value"] if cpu else None}
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -79,9 +79,13 @@ void launch_hex_assemble(const HexDev<T> &d, const T *CE, T *rc, cudaStream_t st
 template <typename T>
 void launch_hex_star_solve(const HexDev<T> &d, const T *rc, T *X, int maxG, cudaStream_t st);
 // the dense form: x_G = S_G^{-1} g_G with the lower triangle of S_G^{-1} by rows
-// (row r at zoff[r], padded to a multiple of 4 values)
+// (row r at zoff[r], padded to a multiple of 4 values); list: the star indices
+// of three size bins (interfaces up to 256, 512, 1024 values) one after the
+// other, count and the largest interface of each bin; bins: mask of the bins
+// to launch (bit b = bin b), the largest first
 template <typename T>
-void launch_hex_star_dense(const HexDev<T> &d, const T *rc, T *X, int maxG, cudaStream_t st);
+void launch_hex_star_dense(const HexDev<T> &d, const T *rc, T *X, const int *list, const int count[3],
+                           const int maxg[3], unsigned bins, cudaStream_t st);
 template <typename T>
 void launch_hex_slot_stars(const HexDev<T> &d, const T *X, T *zf, cudaStream_t st);
 template <typename T, typename Tout>

@@ -27,6 +27,12 @@ using namespace fdm;
 struct fdm_hexgpu {
   fdm_options opt{};
   int p = 0, n = 0, nc = 0, nv = 0, nstar = 0, nco = 0, maxG = 0;
+  int *bin_list = nullptr;  // dense form: star indices by interface-size bin, largest first in each
+  int bin_count[3] = {0, 0, 0}, bin_maxg[3] = {0, 0, 0};
+  // the largest bin runs on a second stream beside the others (it has too few
+  // stars to fill the GPU alone); fork and join events
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int64_t nnode = 0, nxtot = 0, nval = 0;
   bool dense = true;  // interface solves with the dense S_G^{-1} (else the Schur-coupling form)
   std::vector<void *> allocs;
@@ -73,6 +79,9 @@ struct fdm_hexgpu {
     else return reinterpret_cast<T *>(b);
   }
   ~fdm_hexgpu() {
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (aux) cudaStreamDestroy(aux);
     for (void *p : allocs) cudaFree(p);
   }
 };
@@ -434,6 +443,28 @@ void setup(fdm_hexgpu *c, const fdm_hexmesh *h, cudaStream_t st) {
     fail(FDM_EINVAL, "fdm_hex_setup: the mesh has no Schur-coupling factors (call fdm_hexmesh_factor first)");
   c->nxtot = xo;
   c->nstar = nstar;
+  {  // size bins of the dense interface solves, each largest first
+    std::vector<int> order(nstar);
+    for (int k = 0; k < nstar; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return stars[a].nG > stars[b].nG; });
+    std::vector<int> bins[3];
+    for (int k : order) {
+      const int nG = stars[k].nG, b = nG <= 256 ? 0 : (nG <= 512 ? 1 : 2);
+      bins[b].push_back(k);
+      c->bin_maxg[b] = std::max(c->bin_maxg[b], nG);
+    }
+    std::vector<int> all;
+    for (int b = 0; b < 3; ++b) {
+      c->bin_count[b] = (int)bins[b].size();
+      all.insert(all.end(), bins[b].begin(), bins[b].end());
+    }
+    c->bin_list = c->upload(all);
+    if (c->dense && c->bin_count[2] > 0 && c->bin_count[0] + c->bin_count[1] > 0) {
+      FDM_CUDA(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+      FDM_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+      FDM_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    }
+  }
   std::vector<int> ct;
   std::vector<HexClassDev> classes(ncls);
   for (int cl = 0; cl < ncls; ++cl) build_class(h, cl, std::max(cls_nG[cl], 0), ct, classes[cl]);
@@ -543,11 +574,22 @@ void hex_asm(fdm_hexgpu *c, const T *r, T *z, double omega, cudaStream_t st) {
   const HexDev<T> &d = c->dev<T>();
   launch_hex_restrict<T, T>(d, r, c->E<T>(), st);
   launch_hex_assemble<T>(d, c->E<T>(), c->rc<T>(), st);
-  if (c->dense) launch_hex_star_dense<T>(d, c->rc<T>(), c->X<T>(), c->maxG, st);
-  else launch_hex_star_solve<T>(d, c->rc<T>(), c->X<T>(), c->maxG, st);
+  if (c->dense && c->aux && c->bin_count[2] > 0 && c->bin_count[0] + c->bin_count[1] > 0) {
+    FDM_CUDA(cudaEventRecord(c->ev_fork, st));
+    FDM_CUDA(cudaStreamWaitEvent(c->aux, c->ev_fork, 0));
+    launch_hex_star_dense<T>(d, c->rc<T>(), c->X<T>(), c->bin_list, c->bin_count, c->bin_maxg, 4u, c->aux);
+    FDM_CUDA(cudaEventRecord(c->ev_join, c->aux));
+    launch_hex_star_dense<T>(d, c->rc<T>(), c->X<T>(), c->bin_list, c->bin_count, c->bin_maxg, 3u, st);
+    FDM_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
+  } else if (c->dense) {
+    launch_hex_star_dense<T>(d, c->rc<T>(), c->X<T>(), c->bin_list, c->bin_count, c->bin_maxg, 7u, st);
+  } else {
+    launch_hex_star_solve<T>(d, c->rc<T>(), c->X<T>(), c->maxG, st);
+  }
   launch_hex_slot_stars<T>(d, c->X<T>(), c->zf<T>(), st);
   launch_hex_interp<T, T>(d, c->E<T>(), c->zf<T>(), omega, z, st);
-  c->launches += 5;
+  const int solves = c->dense ? (c->bin_count[0] > 0) + (c->bin_count[1] > 0) + (c->bin_count[2] > 0) : 1;
+  c->launches += 4 + solves;
 }
 
 // hybrid V(1,1) in precision T: x1 = w S r, x1 += P Ac^{-1} P^T (r - A x1), z = x1 + w S (r - A x1)

@@ -515,10 +515,11 @@ __device__ __forceinline__ H4<double> ld4s(const double *p) {
 // entries times g_r as column sums in registers; the warps' column sums are
 // added in warp order after the row dots (deterministic).
 template <typename T, int NQ, int RB>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : (NQ >= 8 ? 2 : 3)) k_hex_star_dense(HexDev<T> d, const T *__restrict__ rc,
-                                                                          T *__restrict__ X, int cap) {
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : 2) k_hex_star_dense(HexDev<T> d, const T *__restrict__ rc,
+                                                                              T *__restrict__ X,
+                                                                              const int *__restrict__ list, int cap) {
   extern __shared__ __align__(16) unsigned char smem_[];
-  const HexStarDev S = d.stars[blockIdx.x];
+  const HexStarDev S = d.stars[list[blockIdx.x]];
   const int nG = S.nG;
   if (nG == 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -593,25 +594,30 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 1 : (NQ >= 8 ? 2 : 3)) k
 
 }  // namespace
 
-template <typename T>
-void launch_hex_star_dense(const HexDev<T> &d, const T *rc, T *X, int maxG, cudaStream_t st) {
-  if (d.nstar <= 0) return;
-  const int cap = (maxG + 3) & ~3;
+template <typename T, int NQ, int RB>
+void star_dense_bin(const HexDev<T> &d, const T *rc, T *X, const int *list, int count, int maxg, cudaStream_t st) {
+  if (count <= 0) return;
+  const int cap = (maxg + 3) & ~3;
   const size_t sm = sizeof(T) * 10 * (size_t)cap;
-  if (maxG <= 256) {
-    hex_set_smem(k_hex_star_dense<T, 2, 4>, sm);
-    k_hex_star_dense<T, 2, 4><<<d.nstar, 256, sm, st>>>(d, rc, X, cap);
-  } else if (maxG <= 512) {
-    hex_set_smem(k_hex_star_dense<T, 4, 2>, sm);
-    k_hex_star_dense<T, 4, 2><<<d.nstar, 256, sm, st>>>(d, rc, X, cap);
-  } else if (maxG <= 1024) {
-    hex_set_smem(k_hex_star_dense<T, 8, 1>, sm);
-    k_hex_star_dense<T, 8, 1><<<d.nstar, 256, sm, st>>>(d, rc, X, cap);
-  } else {
-    fail(FDM_EINVAL, "dense star solve: interface larger than 1024");
-  }
+  hex_set_smem(k_hex_star_dense<T, NQ, RB>, sm);
+  k_hex_star_dense<T, NQ, RB><<<count, 256, sm, st>>>(d, rc, X, list, cap);
 }
-template void launch_hex_star_dense<double>(const HexDev<double> &, const double *, double *, int, cudaStream_t);
-template void launch_hex_star_dense<float>(const HexDev<float> &, const float *, float *, int, cudaStream_t);
+
+// the stars in three launches by interface size (at most 256, 512, 1024 values),
+// each with the column groups per lane that its rows need and more rows in
+// flight per warp where the rows are short
+template <typename T>
+void launch_hex_star_dense(const HexDev<T> &d, const T *rc, T *X, const int *list, const int count[3],
+                           const int maxg[3], unsigned bins, cudaStream_t st) {
+  if (d.nstar <= 0) return;
+  if (maxg[2] > 1024) fail(FDM_EINVAL, "dense star solve: interface larger than 1024");
+  if (bins & 4u) star_dense_bin<T, 8, 2>(d, rc, X, list + count[0] + count[1], count[2], maxg[2], st);
+  if (bins & 2u) star_dense_bin<T, 4, 4>(d, rc, X, list + count[0], count[1], maxg[1], st);
+  if (bins & 1u) star_dense_bin<T, 2, 8>(d, rc, X, list, count[0], maxg[0], st);
+}
+template void launch_hex_star_dense<double>(const HexDev<double> &, const double *, double *, const int *,
+                                            const int[3], const int[3], unsigned, cudaStream_t);
+template void launch_hex_star_dense<float>(const HexDev<float> &, const float *, float *, const int *, const int[3],
+                                           const int[3], unsigned, cudaStream_t);
 
 }  // namespace fdm
