@@ -532,8 +532,8 @@ def bench_gpu(args):
             "elasticity_table3_setting_p15": (secondary.get("elasticity", {}).get("iterations_traction_free_x0") or
                                               {}).get("p=15"),
             "batched": {k: secondary.get("batched", {}).get(k)
-                        for k in ("aggregate_dofs_per_s", "one_after_another_dofs_per_s", "latency_ms_p50",
-                                  "latency_ms_p99")},
+                        for k in ("aggregate_dofs_per_s", "one_after_another_dofs_per_s", "fp64_aggregate_dofs_per_s",
+                                  "latency_ms_p50", "latency_ms_p99")},
             "cpu_oracle_same_config_dofs_per_s": cpu["value"] if cpu else None}
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -964,8 +964,28 @@ def bench_batched(dev, fdmpc, inputs, reps=3):
         d[1] += t
     for c in ctxs:
         c.close()
+    # the same batch with the FP64 preconditioner (the plain FP64 form, same rtol on the true residual)
+    c64 = [fdmpc.Context(w["p"], w["xv"], w["yv"], w["zv"], precision=fdmpc.FDM_PREC_FP64,
+                         lanczos_start=inputs.lanczos_start(((len(w["xv"]) - 1) * w["p"] + 1) ** 3), autotune=1)
+           for w in probs]
+    b64 = fdmpc.fdm_batch_setup([c.h for c in c64])
+    fdmpc.pcg_solve_batched(b64, bs, xs, RTOL, MAXIT)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(torch.cuda.current_stream())
+    inf64 = fdmpc.pcg_solve_batched(b64, bs, xs, RTOL, MAXIT)
+    e1.record(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    worst64 = max(i.true_rnorm / i.rnorm0 for i in inf64)
+    fdmpc.fdm_batch_destroy(b64)
+    for c in c64:
+        c.close()
     return {"workload": "64 graded problems, n^3 cells n in 2..10, Q_p p in 3..15 (seeds 1000..1063), "
                         "%d free dofs in total, mixed precision, one CUDA graph" % free,
+            "fp64_batch_ms": ms64, "fp64_aggregate_dofs_per_s": free / (ms64 * 1e-3),
+            "fp64_worst_true_rel_residual": worst64, "mixed_over_fp64": ms64 / ms,
             "aggregate_dofs_per_s": free / (ms * 1e-3), "batch_ms": ms,
             "one_after_another_ms": seq_ms, "one_after_another_dofs_per_s": free / (seq_ms * 1e-3),
             "one_after_another_dofs_per_s_by_degree": {str(p): v[0] / (v[1] * 1e-3) for p, v in sorted(by_p.items())},
