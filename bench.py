@@ -945,6 +945,26 @@ def bench_batched(dev, fdmpc, inputs, reps=3):
     ms = float(np.median(times))
     worst = max(i.true_rnorm / i.rnorm0 for i in infos)
     fdmpc.fdm_batch_destroy(batch)
+    # the lockstep schedule: one loop, the star solves of all active problems in one launch
+    lock = fdmpc.fdm_batch_setup([c.h for c in ctxs], mode=fdmpc.FDM_BATCH_LOCKSTEP)
+    fdmpc.pcg_solve_batched(lock, bs, xs, RTOL, MAXIT)
+    ltimes, llat = [], []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(torch.cuda.current_stream())
+        linfos = fdmpc.pcg_solve_batched(lock, bs, xs, RTOL, MAXIT)
+        e1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        ltimes.append(e0.elapsed_time(e1))
+        llat += [i.seconds * 1e3 for i in linfos]
+    lms = float(np.median(ltimes))
+    lockstep = {"batch_ms": lms, "aggregate_dofs_per_s": free / (lms * 1e-3),
+                "latency_ms_p50": float(np.percentile(llat, 50)), "latency_ms_p99": float(np.percentile(llat, 99)),
+                "iterations_min_max": [min(i.iterations for i in linfos), max(i.iterations for i in linfos)],
+                "worst_true_rel_residual": max(i.true_rnorm / i.rnorm0 for i in linfos)}
+    fdmpc.fdm_batch_destroy(lock)
     # the same problems one after another (each its own device-driven solve): the time the batch
     # would take without sharing the GPU, and the throughput by degree
     seq_ms, by_p = 0.0, {}
@@ -984,6 +1004,7 @@ def bench_batched(dev, fdmpc, inputs, reps=3):
         c.close()
     return {"workload": "64 graded problems, n^3 cells n in 2..10, Q_p p in 3..15 (seeds 1000..1063), "
                         "%d free dofs in total, mixed precision, one CUDA graph" % free,
+            "lockstep": lockstep,
             "fp64_batch_ms": ms64, "fp64_aggregate_dofs_per_s": free / (ms64 * 1e-3),
             "fp64_worst_true_rel_residual": worst64, "mixed_over_fp64": ms64 / ms,
             "aggregate_dofs_per_s": free / (ms * 1e-3), "batch_ms": ms,

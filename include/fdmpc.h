@@ -241,6 +241,25 @@ typedef struct fdm_batch fdm_batch;
 /* Groups k set-up contexts (of any sizes and degrees) for one batched PCG
  * call.  The contexts stay owned by the caller and must outlive the batch. */
 int fdm_batch_setup(int k, fdm_ctx *const *ctxs, fdm_batch **out);
+/* The same with a schedule:
+ *   FDM_BATCH_BRANCHES (fdm_batch_setup): one CUDA graph, every problem's PCG
+ *     loop a branch of its own (a conditional WHILE node), its kernels at a
+ *     priority ranked by problem size (smaller first);
+ *   FDM_BATCH_LOCKSTEP: one device-driven loop in which every problem still
+ *     iterating takes one PCG iteration per pass (its cell kernels, coarse
+ *     solve and vector work in a conditional IF node of its own), and the star
+ *     solves of all those problems run in one launch per relaxation sweep over
+ *     a global list of (problem, patch) sorted by patch size, largest first,
+ *     with one CTA per patch (the Schur-coupling form, 256 threads); a problem
+ *     that has converged (true residual) or reached maxit drops out of every
+ *     later launch.  Needs FP32 preconditioners with the V(1,1) cycle and the
+ *     Schur-coupling form (patch_form 2, the default) in every context, else
+ *     FDM_EINVAL.
+ * Results of the two agree to the rounding of the star solves' kernel
+ * variant, not bit for bit. */
+#define FDM_BATCH_BRANCHES 0
+#define FDM_BATCH_LOCKSTEP 1
+int fdm_batch_setup_mode(int k, fdm_ctx *const *ctxs, int mode, fdm_batch **out);
 /* Solves all k problems: b[i], x[i] device vectors of problem i; infos
  * (HOST, k entries, may be NULL).  Synchronises `stream`. */
 int pcg_solve_batched(fdm_batch *batch, const double *const *b_dev, double *const *x_dev,

@@ -60,6 +60,17 @@ struct fdm_batch {
                                                                    // iteration, one true-residual check
   double key_rtol = -1.0;
   int key_maxit = -1;
+  // lockstep mode: every problem steps one PCG iteration at a time inside one
+  // device-driven loop, the star solves of all problems in one launch over a
+  // global (problem, patch) list sorted largest first; converged problems drop out
+  int mode = FDM_BATCH_BRANCHES;
+  PatchSolveArgs<float> *d_args = nullptr;  // [k] per-problem patch-solve arguments
+  int2 *d_work = nullptr;                    // the global work list
+  int nwork = 0;
+  size_t multi_smem = 0;
+  int *d_active = nullptr;                             // [k] 1 while a problem iterates
+  cudaGraphConditionalHandle *d_ifh = nullptr;         // [3 k] its segments' IF handles
+  std::vector<size_t> seg_kernels;                     // kernel nodes per problem and iteration
   void release_graph() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -70,6 +81,8 @@ struct fdm_batch {
     release_graph();
     if (cap) cudaStreamDestroy(cap);
     if (d_times) cudaFree(d_times);
+    for (void *ptr : {(void *)d_args, (void *)d_work, (void *)d_active, (void *)d_ifh})
+      if (ptr) cudaFree(ptr);
   }
 };
 
@@ -132,11 +145,29 @@ StreamArgs<T> stream_args(fdm_ctx *c) {
   return s;
 }
 
-template <typename T, typename Tin, typename Tout>
-void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st, const T *addv = nullptr) {
+// One relaxation sweep in three phases: the per-cell restriction to the FDM
+// basis with the Schur condensation (E), the star solves (X), and the
+// back-substitution and basis change back (z).  The batched lockstep solve runs
+// the middle phase of every problem in one launch.
+template <typename T, typename Tin>
+void asm_restrict(fdm_ctx *c, const Tin *r, cudaStream_t st) {
   c->tmark(FDM_T_RESTRICT, true, st);
   launch_restrict_fdm<T, Tin>(c->g, r, c->tab<T>(), c->mu, c->E<T>(), st);
   c->tmark(FDM_T_RESTRICT, false, st);
+  c->launches += 1;
+}
+
+template <typename T, typename Tout>
+void asm_interp(fdm_ctx *c, Tout *z, double omega, cudaStream_t st, const T *addv) {
+  c->tmark(FDM_T_INTERP, true, st);
+  InterpArgs<T> ia{c->g, c->d_patches, c->d_cls, c->X<T>(), c->E<T>(), c->mu, c->tab<T>(), c->cmap, addv};
+  launch_interp_fdm<T, Tout>(ia, omega, z, st);
+  c->tmark(FDM_T_INTERP, false, st);
+  c->launches += 1;
+}
+
+template <typename T>
+void asm_patch(fdm_ctx *c, cudaStream_t st) {
   c->tmark(FDM_T_PATCH, true, st);
   const bool resident = sizeof(T) == 4 ? c->res32 : c->res64;
   if (c->scform) {
@@ -199,11 +230,14 @@ void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st, c
     launch_patch_solve<T>(a, c->nsolve - skip, c->smem<T>(), c->patch_threads, st);
   }
   c->tmark(FDM_T_PATCH, false, st);
-  c->tmark(FDM_T_INTERP, true, st);
-  InterpArgs<T> ia{c->g, c->d_patches, c->d_cls, c->X<T>(), c->E<T>(), c->mu, c->tab<T>(), c->cmap, addv};
-  launch_interp_fdm<T, Tout>(ia, omega, z, st);
-  c->tmark(FDM_T_INTERP, false, st);
-  c->launches += 3;
+  c->launches += 1;
+}
+
+template <typename T, typename Tin, typename Tout>
+void run_asm(fdm_ctx *c, const Tin *r, Tout *z, double omega, cudaStream_t st, const T *addv = nullptr) {
+  asm_restrict<T, Tin>(c, r, st);
+  asm_patch<T>(c, st);
+  asm_interp<T, Tout>(c, z, omega, st, addv);
 }
 
 // one V-cycle of the geometric multigrid on level l: out = V(b) from a zero
@@ -1318,6 +1352,286 @@ void build_batch_graph(fdm_batch *B, const double *const *bv, double *const *xv,
   B->key_maxit = maxit;
 }
 
+// ---- lockstep batched solves: one device-driven loop for all problems
+// ||b||^2 in dots[2]: the problem iterates unless b = 0 (or maxit = 0)
+__global__ void k_lstart(double *sc, const double *dots, int *active) {
+  if (threadIdx.x != 0) return;
+  const double bb = dots[2];
+  sc[12] = bb;
+  sc[14] = bb;
+  sc[9] = 1.0;
+  sc[13] = 0.0;
+  sc[15] = bb == 0.0 ? 1.0 : 0.0;
+  if (!isfinite(bb)) sc[8] = 1.0;
+  *active = (bb > 0.0 && isfinite(bb) && sc[11] > 0.0) ? 1 : 0;
+}
+// the three segment conditions of every problem from its flag, at the start of a pass
+__global__ void k_lset(int k, const int *active, const cudaGraphConditionalHandle *h) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 3 * k; t += gridDim.x * blockDim.x)
+    cudaGraphSetConditional(h[t], active[t / 3] ? 1u : 0u);
+}
+// as k_bcheck, with the problem's flag in place of its own loop condition
+__global__ void k_lcheck(double *sc, const double *dots, int *active, cudaGraphConditionalHandle hv,
+                         unsigned long long *tend) {
+  if (threadIdx.x != 0) return;
+  const double rr = dots[2];
+  const double it = sc[13] + 1.0;
+  sc[13] = it;
+  sc[14] = rr;
+  if (!isfinite(rr)) sc[8] = 1.0;
+  const bool conv = rr <= sc[10] * sc[12] && sc[8] == 0.0;
+  sc[15] = 0.0;
+  const bool stop = it >= sc[11] || sc[8] != 0.0;
+  if (!conv && stop) *tend = global_ns();
+  cudaGraphSetConditional(hv, conv ? 1u : 0u);
+  *active = (conv || stop) ? 0 : 1;
+}
+// as k_bverify, with the problem's flag in place of its own loop condition
+__global__ void k_lverify(double *sc, const double *dots, int *active, unsigned long long *tend) {
+  if (threadIdx.x != 0) return;
+  const double rr = dots[2];
+  sc[4] += 1.0;
+  sc[14] = rr;
+  if (!isfinite(rr)) sc[8] = 1.0;
+  const bool conv = rr <= sc[10] * sc[12] && sc[8] == 0.0;
+  sc[15] = conv ? 1.0 : 0.0;
+  const bool done = conv || sc[13] >= sc[11] || sc[8] != 0.0;
+  if (done) *tend = global_ns();
+  *active = done ? 0 : 1;
+}
+// the loop goes on while any problem iterates
+__global__ void k_lany(int k, const int *active, cudaGraphConditionalHandle hw) {
+  if (threadIdx.x != 0) return;
+  int any = 0;
+  for (int i = 0; i < k; ++i) any |= active[i];
+  cudaGraphSetConditional(hw, any ? 1u : 0u);
+}
+
+// the kernels of one problem's PCG iteration around the two star-solve launches
+// (FP32 V(1,1)): segment 0 up to the first restriction, segment 1 from the first
+// interpolation to the second restriction, segment 2 the rest of the iteration
+void capture_segment(fdm_ctx *c, int seg, double *x, int *active, cudaGraphConditionalHandle hv,
+                     unsigned long long *tend, cudaStream_t st) {
+  const int64_t n = c->g.ndof;
+  float *x1 = c->f1, *r1 = c->f3;
+  if (seg == 0) {
+    launch_dot(n, c->r, c->z, c->partial, c->dots + 1, st);  // r . z_prev (flexible beta)
+    asm_restrict<float, double>(c, c->r, st);
+  } else if (seg == 1) {
+    asm_interp<float, float>(c, x1, c->omega, st, nullptr);  // x1 = omega ASM(r)
+    apply_residual<float>(c, x1, c->r, r1, st);
+    coarse_correct<float>(c, r1, x1, st);
+    apply_residual<float>(c, x1, c->r, r1, st);
+    asm_restrict<float, float>(c, r1, st);
+  } else {
+    asm_interp<float, double>(c, c->z, c->omega, st, x1);  // z = x1 + omega ASM(r1)
+    launch_dot(n, c->r, c->z, c->partial, c->dots, st);
+    k_bbeta<<<1, 32, 0, st>>>(c->sc, c->dots);
+    launch_pcg_update_d(n, c->sc, c->z, c->d, st);
+    apply_op<double>(c, c->d, c->q, st);
+    launch_dot(n, c->d, c->q, c->partial, c->dots + 3, st);
+    launch_pcg_scalars(0, c->sc, c->dots + 3, st);
+    launch_pcg_update_xr(n, c->sc, c->d, c->q, x, c->r, st);
+    launch_dot(n, c->r, c->r, c->partial, c->dots + 2, st);
+    k_lcheck<<<1, 32, 0, st>>>(c->sc, c->dots, active, hv, tend);
+  }
+  FDM_CUDA(cudaGetLastError());
+}
+
+// the set-up of the global star-solve list: per problem the arguments of the
+// 256-thread Schur-coupling kernel, and (problem, position) pairs by patch size
+void setup_lockstep(fdm_batch *B) {
+  const int k = (int)B->ctxs.size();
+  std::vector<PatchSolveArgs<float>> args(k);
+  struct Item {
+    int64_t cost;
+    int prob, slot;
+  };
+  std::vector<Item> items;
+  size_t smem = 0;
+  for (int i = 0; i < k; ++i) {
+    fdm_ctx *c = B->ctxs[i];
+    if (c->opt.precision != FDM_PREC_FP32 || c->opt.pc != FDM_PC_VCYCLE || !c->scform)
+      fail(FDM_EINVAL, "lockstep batch: every context needs the FP32 V(1,1) and the Schur-coupling form");
+    PatchSolveArgs<float> a{c->g, c->d_cls, c->d_patches, c->d_order, c->E<float>(), c->mu, c->tab<float>(),
+                            c->L<float>(), c->X<float>(), patch_sc_tmp(c->maxN1, c->maxN2, 256), 0,
+                            (uint64_t)(std::max(c->opt.wait_timeout_s, 0.0) * 1e9), c->status, 0, 0, 0};
+    a.rows8 = 1;
+    a.stage_st = 1;
+    a.headcap = c->headcap32;
+    args[i] = a;
+    smem = std::max(smem, patch_sc_smem<float>(c->maxG, c->maxN1, c->maxN2, 256, a.headcap));
+    std::vector<int> order(c->nsolve);
+    if (c->nsolve > 0)
+      FDM_CUDA(cudaMemcpy(order.data(), c->d_order, sizeof(int) * c->nsolve, cudaMemcpyDeviceToHost));
+    for (int slot = 0; slot < c->nsolve; ++slot)
+      items.push_back({c->classes[c->h_patches[order[slot]].cls].nval, i, slot});
+  }
+  if (smem > 224 * 1024) fail(FDM_EINVAL, "lockstep batch: a patch does not fit the shared memory of one CTA");
+  std::stable_sort(items.begin(), items.end(), [](const Item &a, const Item &b) { return a.cost > b.cost; });
+  std::vector<int2> work(items.size());
+  for (size_t t = 0; t < items.size(); ++t) work[t] = make_int2(items[t].prob, items[t].slot);
+  B->nwork = (int)work.size();
+  B->multi_smem = smem;
+  FDM_CUDA(cudaMalloc(&B->d_args, sizeof(PatchSolveArgs<float>) * std::max(k, 1)));
+  FDM_CUDA(cudaMalloc(&B->d_work, sizeof(int2) * std::max<size_t>(work.size(), 1)));
+  FDM_CUDA(cudaMalloc(&B->d_active, sizeof(int) * std::max(k, 1)));
+  FDM_CUDA(cudaMalloc(&B->d_ifh, sizeof(cudaGraphConditionalHandle) * std::max(3 * k, 1)));
+  if (k > 0) FDM_CUDA(cudaMemcpy(B->d_args, args.data(), sizeof(PatchSolveArgs<float>) * k, cudaMemcpyHostToDevice));
+  if (!work.empty()) FDM_CUDA(cudaMemcpy(B->d_work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice));
+}
+
+// the launches of `launch`, captured into a child graph added to g after the given nodes
+template <typename F>
+cudaGraphNode_t capture_after(fdm_batch *B, cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, F &&launch) {
+  cudaGraph_t child;
+  FDM_CUDA(cudaGraphCreate(&child, 0));
+  FDM_CUDA(cudaStreamBeginCaptureToGraph(B->cap, child, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  launch(B->cap);
+  FDM_CUDA(cudaStreamEndCapture(B->cap, &child));
+  cudaGraphNode_t node;
+  FDM_CUDA(cudaGraphAddChildGraphNode(&node, g, deps.empty() ? nullptr : deps.data(), deps.size(), child));
+  FDM_CUDA(cudaGraphDestroy(child));
+  return node;
+}
+
+// a conditional node of the given type on handle h in g after deps; its body graph in *body
+cudaGraphNode_t add_conditional(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, cudaGraphConditionalHandle h,
+                                cudaGraphConditionalNodeType type, cudaGraph_t *body) {
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = type;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  FDM_CUDA(cudaGraphAddNode(&node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &cp));
+  *body = cp.conditional.phGraph_out[0];
+  return node;
+}
+
+size_t graph_nodes(cudaGraph_t g) {
+  size_t nn = 0;
+  FDM_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+  return nn;
+}
+
+// The lockstep graph: per problem its set-up (x = 0, r = b, ||b||^2, the flag),
+// then one WHILE loop whose body is: the segment conditions from the flags;
+// segment 0 of every problem (each in an IF node); the star solves of all
+// active problems; segment 1; the star solves; segment 2 (ending with the
+// problem's convergence check, and its true-residual check in a nested IF);
+// the loop condition from the flags.
+void build_lockstep_graph(fdm_batch *B, const double *const *bv, double *const *xv, double rtol, int maxit) {
+  B->release_graph();
+  B->init_kernels.clear();
+  B->body_kernels.clear();
+  B->verify_kernels.clear();
+  const int k = (int)B->ctxs.size();
+  if (!B->cap) FDM_CUDA(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+  if (!B->d_times) FDM_CUDA(cudaMalloc(&B->d_times, sizeof(unsigned long long) * (k + 1)));
+  if (!B->d_args) setup_lockstep(B);
+  cudaGraph_t G;
+  FDM_CUDA(cudaGraphCreate(&G, 0));
+  B->graph = G;
+  for (fdm_ctx *c : B->ctxs) c->capturing = true;
+  std::vector<int64_t> counted(k);
+  for (int i = 0; i < k; ++i) counted[i] = B->ctxs[i]->launches;
+  try {
+    unsigned long long *dt = B->d_times;
+    cudaGraphNode_t t0 = capture_after(B, G, {}, [&](cudaStream_t st) { k_btime<<<1, 32, 0, st>>>(dt); });
+    std::vector<cudaGraphNode_t> starts;
+    for (int i = 0; i < k; ++i) {
+      fdm_ctx *c = B->ctxs[i];
+      const int64_t n = c->g.ndof;
+      int *act = B->d_active + i;
+      cudaGraphNode_t ni = capture_after(B, G, {t0}, [&](cudaStream_t st) {
+        k_bconst<<<1, 32, 0, st>>>(c->sc, c->opt.flexible_beta ? 1.0 : 0.0, rtol * rtol, (double)maxit);
+        fill(n, 0.0, xv[i], st);
+        fill(n, 0.0, c->z, st);
+        fill(n, 0.0, c->d, st);
+        copy(n, bv[i], c->r, st);
+        mask_dirichlet(c->g, c->r, st);
+        launch_dot(n, c->r, c->r, c->partial, c->dots + 2, st);
+        k_lstart<<<1, 32, 0, st>>>(c->sc, c->dots, act);
+      });
+      starts.push_back(ni);
+    }
+    cudaGraphConditionalHandle hw;
+    FDM_CUDA(cudaGraphConditionalHandleCreate(&hw, G, 1, cudaGraphCondAssignDefault));
+    cudaGraph_t body;
+    add_conditional(G, starts, hw, cudaGraphCondTypeWhile, &body);
+    std::vector<cudaGraphConditionalHandle> hif(3 * (size_t)k);
+    for (auto &h : hif) FDM_CUDA(cudaGraphConditionalHandleCreate(&h, body, 0, cudaGraphCondAssignDefault));
+    FDM_CUDA(cudaMemcpy(B->d_ifh, hif.data(), sizeof(cudaGraphConditionalHandle) * hif.size(),
+                        cudaMemcpyHostToDevice));
+    int *dact = B->d_active;
+    cudaGraphConditionalHandle *difh = B->d_ifh;
+    std::vector<cudaGraphNode_t> prev = {capture_after(B, body, {}, [&](cudaStream_t st) {
+      k_lset<<<1, 256, 0, st>>>(k, dact, difh);
+    })};
+    B->seg_kernels.assign(k, 0);
+    for (int seg = 0; seg < 3; ++seg) {
+      std::vector<cudaGraphNode_t> ifs;
+      for (int i = 0; i < k; ++i) {
+        fdm_ctx *c = B->ctxs[i];
+        cudaGraph_t sb;
+        ifs.push_back(add_conditional(body, prev, hif[3 * i + seg], cudaGraphCondTypeIf, &sb));
+        cudaGraphConditionalHandle hv = 0;
+        if (seg == 2) FDM_CUDA(cudaGraphConditionalHandleCreate(&hv, sb, 0, cudaGraphCondAssignDefault));
+        FDM_CUDA(cudaStreamBeginCaptureToGraph(B->cap, sb, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        capture_segment(c, seg, xv[i], B->d_active + i, hv, B->d_times + 1 + i, B->cap);
+        FDM_CUDA(cudaStreamEndCapture(B->cap, &sb));
+        B->seg_kernels[i] += graph_nodes(sb);
+        if (seg == 2) {  // the true-residual check, when the recursive residual has converged
+          cudaGraph_t vb;
+          add_conditional(sb, {graph_leaf(sb)}, hv, cudaGraphCondTypeIf, &vb);
+          FDM_CUDA(cudaStreamBeginCaptureToGraph(B->cap, vb, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+          const int64_t n = c->g.ndof;
+          const double *b = bv[i];
+          const double *x = xv[i];
+          apply_op<double>(c, x, c->q, B->cap);
+          launch_sub<double>(n, b, c->q, c->r, B->cap);
+          mask_dirichlet(c->g, c->r, B->cap);
+          launch_dot(n, c->r, c->r, c->partial, c->dots + 2, B->cap);
+          k_lverify<<<1, 32, 0, B->cap>>>(c->sc, c->dots, B->d_active + i, B->d_times + 1 + i);
+          FDM_CUDA(cudaStreamEndCapture(B->cap, &vb));
+          B->verify_kernels.push_back(graph_nodes(vb));
+        }
+      }
+      if (seg < 2) {
+        PatchSolveArgs<float> *da = B->d_args;
+        int2 *dw = B->d_work;
+        const int nw = B->nwork;
+        const size_t sm = B->multi_smem;
+        prev = {capture_after(B, body, ifs, [&](cudaStream_t st) {
+          launch_patch_sc_multi<float>(da, dw, nw, dact, sm, st);
+        })};
+      } else {
+        capture_after(B, body, ifs, [&](cudaStream_t st) { k_lany<<<1, 32, 0, st>>>(k, dact, hw); });
+      }
+    }
+    for (int i = 0; i < k; ++i) B->init_kernels.push_back(1);
+  } catch (...) {
+    for (fdm_ctx *c : B->ctxs) c->capturing = false;
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(B->cap, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(B->cap, &junk);
+    }
+    cudaGetLastError();
+    throw;
+  }
+  for (int i = 0; i < k; ++i) {
+    B->ctxs[i]->capturing = false;
+    B->ctxs[i]->launches = counted[i];
+  }
+  FDM_CUDA(cudaGraphInstantiate(&B->exec, G, 0));
+  B->key_b.assign(bv, bv + k);
+  B->key_x.assign(xv, xv + k);
+  B->key_rtol = rtol;
+  B->key_maxit = maxit;
+}
+
 int handle(fdm_ctx *c, const Error &e);
 
 // the captured batched solve (one graph, a device-driven PCG loop per problem)
@@ -1328,7 +1642,10 @@ int solve_batch(fdm_batch *b, const double *const *bv, double *const *xv, double
   try {
     const bool same = b->exec && b->key_rtol == rtol && b->key_maxit == maxit &&
                       std::equal(b->key_b.begin(), b->key_b.end(), bv) && std::equal(b->key_x.begin(), b->key_x.end(), xv);
-    if (!same) build_batch_graph(b, bv, xv, rtol, maxit);
+    if (!same) {
+      if (b->mode == FDM_BATCH_LOCKSTEP) build_lockstep_graph(b, bv, xv, rtol, maxit);
+      else build_batch_graph(b, bv, xv, rtol, maxit);
+    }
     FDM_CUDA(cudaGraphLaunch(b->exec, st));
     FDM_CUDA(cudaStreamSynchronize(st));
     std::vector<unsigned long long> t(k + 1);
@@ -1338,9 +1655,23 @@ int solve_batch(fdm_batch *b, const double *const *bv, double *const *xv, double
       fdm_ctx *c = b->ctxs[i];
       double hsc[16];
       FDM_CUDA(cudaMemcpy(hsc, c->sc, sizeof hsc, cudaMemcpyDeviceToHost));
-      // kernels this problem ran inside the graph (the timer kernel counts for the first)
-      c->launches += (int64_t)b->init_kernels[i] + (int64_t)hsc[13] * (int64_t)b->body_kernels[i] +
-                     (int64_t)hsc[4] * (int64_t)b->verify_kernels[i] + (i == 0);
+      // kernels this problem ran inside the graph (the timer kernel counts for the first;
+      // in lockstep the shared kernels of every pass count for the first too)
+      if (b->mode == FDM_BATCH_LOCKSTEP) {
+        int64_t passes = 0;
+        if (i == 0) {
+          for (fdm_ctx *cc : b->ctxs) {
+            double h13 = 0.0;
+            FDM_CUDA(cudaMemcpy(&h13, cc->sc + 13, sizeof(double), cudaMemcpyDeviceToHost));
+            passes = std::max<int64_t>(passes, (int64_t)h13);
+          }
+        }
+        c->launches += 7 + (int64_t)hsc[13] * (int64_t)b->seg_kernels[i] +
+                       (int64_t)hsc[4] * (int64_t)b->verify_kernels[i] + (i == 0) * (1 + 4 * passes);
+      } else {
+        c->launches += (int64_t)b->init_kernels[i] + (int64_t)hsc[13] * (int64_t)b->body_kernels[i] +
+                       (int64_t)hsc[4] * (int64_t)b->verify_kernels[i] + (i == 0);
+      }
       int hstat = 0;
       FDM_CUDA(cudaMemcpy(&hstat, c->status, sizeof(int), cudaMemcpyDeviceToHost));
       int rc = FDM_OK;
@@ -1756,11 +2087,27 @@ int pcg_solve(fdm_ctx *c, const double *b, double *x, double rtol, int maxit, fd
 }
 
 int fdm_batch_setup(int k, fdm_ctx *const *ctxs, fdm_batch **out) {
-  if (k < 0 || !out || (k > 0 && !ctxs)) return FDM_EINVAL;
+  return fdm_batch_setup_mode(k, ctxs, FDM_BATCH_BRANCHES, out);
+}
+
+int fdm_batch_setup_mode(int k, fdm_ctx *const *ctxs, int mode, fdm_batch **out) {
+  if (k < 0 || !out || (k > 0 && !ctxs) || (mode != FDM_BATCH_BRANCHES && mode != FDM_BATCH_LOCKSTEP))
+    return FDM_EINVAL;
+  *out = nullptr;
   fdm_batch *b = new fdm_batch();
+  b->mode = mode;
   for (int i = 0; i < k; ++i) {
     if (!ctxs[i]) { delete b; return FDM_EINVAL; }
     b->ctxs.push_back(ctxs[i]);
+  }
+  if (mode == FDM_BATCH_LOCKSTEP) {
+    try {
+      setup_lockstep(b);
+    } catch (const Error &e) {
+      g_last_error = e.msg;
+      delete b;
+      return e.code;
+    }
   }
   *out = b;
   return FDM_OK;

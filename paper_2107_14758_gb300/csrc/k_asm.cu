@@ -821,11 +821,12 @@ __device__ __forceinline__ void sc_patch_compute(const PatchSolveArgs<T> &a, con
   bb_solve<T, NT>(C, Lh, gv, gv, t1, yv, X);  // u_B = S_BB^{-1} r_B in place, X_B = y_B - u_B
 }
 
-template <typename T, int NT, int SRB, int MINB>
-__global__ void __launch_bounds__(NT, MINB) k_patch_solve_sc(PatchSolveArgs<T> a) {
+// the solve of the patch at position slot of a.order by the whole CTA
+template <typename T, int NT, int SRB>
+__device__ __forceinline__ void sc_patch_one(const PatchSolveArgs<T> &a, int slot) {
   extern __shared__ __align__(128) unsigned char smem_[];
   const int tid = threadIdx.x;
-  const PatchDev P = a.patches[a.order[blockIdx.x]];
+  const PatchDev P = a.patches[a.order[slot]];
   const ClassDev &C = a.cls[P.cls];
   __shared__ __align__(8) uint64_t bar, stall;  // stall: test hook, never completed
   __shared__ int sFail;
@@ -870,6 +871,24 @@ __global__ void __launch_bounds__(NT, MINB) k_patch_solve_sc(PatchSolveArgs<T> a
     Lh = H;
   }
   sc_patch_compute<T, NT, SRB>(a, P, C, Lh, Lv, gv, a.stage_st != 0);
+}
+
+template <typename T, int NT, int SRB, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_patch_solve_sc(PatchSolveArgs<T> a) {
+  sc_patch_one<T, NT, SRB>(a, blockIdx.x);
+}
+
+// The patches of many problems in one launch: work[b] = (problem, position in
+// that problem's patch order), the list sorted by the patches' value counts,
+// largest first; a CTA whose problem is no longer active (converged) returns
+// at once.
+template <typename T, int NT, int SRB, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_patch_solve_sc_multi(const PatchSolveArgs<T> *__restrict__ args,
+                                                                   const int2 *__restrict__ work,
+                                                                   const int *__restrict__ active) {
+  const int2 w = work[blockIdx.x];
+  if (active[w.x] == 0) return;  // uniform over the CTA
+  sc_patch_one<T, NT, SRB>(args[w.x], w.y);
 }
 
 // Persistent variant: each CTA walks the patch order with a stride of the
@@ -1090,6 +1109,19 @@ void launch_patch_sc(const PatchSolveArgs<T> &a, int npatch, size_t smem, int th
   else k_patch_solve_sc<T, 256, 2, 5><<<npatch, 256, smem, st>>>(a);
 }
 
+template <typename T>
+void launch_patch_sc_multi(const PatchSolveArgs<T> *args, const int2 *work, int nwork, const int *active, size_t smem,
+                           cudaStream_t st) {
+  if (nwork <= 0) return;
+  static bool attr = false;
+  if (!attr) {
+    FDM_CUDA(cudaFuncSetAttribute(k_patch_solve_sc_multi<T, 256, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  224 * 1024));
+    attr = true;
+  }
+  k_patch_solve_sc_multi<T, 256, 4, 4><<<nwork, 256, smem, st>>>(args, work, active);
+}
+
 int patch_tmp_elems(int maxN1, int maxN2) {
   // tmp holds a level-1 vector (n1) or the sliced partial sums of L21^T x_2
   // and Z^T y_2 (slices * row length, slices clamped to fit)
@@ -1188,6 +1220,8 @@ void launch_patch_solve(const PatchSolveArgs<T> &a, int npatch, size_t smem, int
   template size_t patch_smem_for_occupancy<T>(size_t, int);                                                 \
   template size_t patch_sc_smem<T>(int, int, int, int, int);                                                \
   template void launch_patch_sc<T>(const PatchSolveArgs<T> &, int, size_t, int, cudaStream_t);             \
+  template void launch_patch_sc_multi<T>(const PatchSolveArgs<T> *, const int2 *, int, const int *, size_t,    \
+                                         cudaStream_t);                                                        \
   template void launch_patch_scp<T>(const PatchSolveArgs<T> &, int, size_t, cudaStream_t);                  \
   template void launch_patch_scf<T>(const PatchSolveArgs<T> &, int, size_t, int, cudaStream_t);
 INST(float)

@@ -41,6 +41,12 @@ template <typename T>
 size_t patch_sc_smem(int maxG, int maxN1, int maxN2, int threads, int headcap);
 template <typename T>
 void launch_patch_sc(const PatchSolveArgs<T> &a, int npatch, size_t smem, int threads, cudaStream_t st);
+// the Schur-coupling solves of many problems in one launch (256 threads, four rows
+// of W per warp, the values before W staged): args[problem] in device memory,
+// work[b] = (problem, position in its patch order), problems with active == 0 skipped
+template <typename T>
+void launch_patch_sc_multi(const PatchSolveArgs<T> *args, const int2 *work, int nwork, const int *active, size_t smem,
+                           cudaStream_t st);
 // persistent variant (256 threads): headcap = elements of each of its two staging buffers
 template <typename T>
 void launch_patch_scp(const PatchSolveArgs<T> &a, int npatch, size_t smem, cudaStream_t st);

@@ -20,6 +20,7 @@ FDM_PREC_FP64, FDM_PREC_FP32 = 0, 1
 FDM_PC_NONE, FDM_PC_ASM, FDM_PC_VCYCLE = 0, 1, 2
 FDM_SDC_AUTO, FDM_SDC_FDM_SPARSE, FDM_SDC_STAR_FDM = 0, 1, 2
 FDM_LABEL_THEOREM1, FDM_LABEL_PATCH_KAPPA = 0, 1
+FDM_BATCH_BRANCHES, FDM_BATCH_LOCKSTEP = 0, 1
 FDM_SURR_AVERAGED, FDM_SURR_EXTERNAL = 0, 1
 (FDM_Q_NDOF, FDM_Q_OMEGA, FDM_Q_LAMBDA, FDM_Q_MU, FDM_Q_NPATCH, FDM_Q_PATCH_CLASS, FDM_Q_CLASS_INFO,
  FDM_Q_GAMMA_ORDER, FDM_Q_FACTOR_NNZ, FDM_Q_PATTERN, FDM_Q_FACTOR, FDM_Q_BASIS, FDM_Q_FACTOR_BYTES,
@@ -95,6 +96,7 @@ def load():
         getattr(L, f).argtypes = [vp, vp, vp, vp]
     L.pcg_solve.argtypes = [vp, vp, vp, C.c_double, C.c_int, C.POINTER(fdm_solve_info), vp]
     L.fdm_batch_setup.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp)]
+    L.fdm_batch_setup_mode.argtypes = [C.c_int, C.POINTER(vp), C.c_int, C.POINTER(vp)]
     L.pcg_solve_batched.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.c_double, C.c_int,
                                     C.POINTER(fdm_solve_info), vp]
     L.fdm_batch_destroy.argtypes = [vp]
@@ -322,10 +324,14 @@ def fdm_sipg_destroy(s):
     load().fdm_sipg_destroy(s)
 
 
-def fdm_batch_setup(ctxs):
+def fdm_batch_setup(ctxs, mode=None):
+    """A batch of the contexts; mode FDM_BATCH_BRANCHES (default) or FDM_BATCH_LOCKSTEP."""
     arr = (C.c_void_p * len(ctxs))(*[c.value for c in ctxs])
     h = C.c_void_p()
-    _check(load().fdm_batch_setup(len(ctxs), arr, C.byref(h)))
+    if mode is None:
+        _check(load().fdm_batch_setup(len(ctxs), arr, C.byref(h)))
+    else:
+        _check(load().fdm_batch_setup_mode(len(ctxs), arr, mode, C.byref(h)))
     return h
 
 

@@ -157,3 +157,61 @@ def test_full_batch_workload():
         fdmpc.fdm_batch_destroy(batch)
         for c in ctxs:
             c.close()
+
+
+# ---------------------------------------------------------------- lockstep schedule
+def test_lockstep_matches_branches():
+    """The lockstep schedule (one loop for all problems, the star solves of all
+    active problems in one launch over the global patch list) against the
+    branch schedule: every problem converges to the FP64 true residual 1e-8,
+    within one iteration of the branch schedule's count, and the iterates agree
+    to the FP32 preconditioner's precision; a problem that stops earlier is
+    done earlier."""
+    probs = problems(FP32, SPECS)
+    hs = [c.h for c, _, _ in probs]
+    bs = [b for _, b, _ in probs]
+    br = fdmpc.fdm_batch_setup(hs)
+    ls = fdmpc.fdm_batch_setup(hs, mode=fdmpc.FDM_BATCH_LOCKSTEP)
+    try:
+        x0 = [torch.zeros_like(b) for b in bs]
+        x1 = [torch.zeros_like(b) for b in bs]
+        i0 = fdmpc.pcg_solve_batched(br, bs, x0, 1e-8, 200)
+        i1 = fdmpc.pcg_solve_batched(ls, bs, x1, 1e-8, 200)
+        for a, b, xa, xb in zip(i0, i1, x0, x1):
+            assert b.converged and b.true_rnorm <= 1e-8 * b.rnorm0
+            assert abs(a.iterations - b.iterations) <= 1
+            assert (xa - xb).abs().max().item() <= 1e-6 * xa.abs().max().item()
+        its = [i.iterations for i in i1]
+        lo, hi = int(np.argmin(its)), int(np.argmax(its))
+        if its[lo] < its[hi]:
+            assert i1[lo].seconds < i1[hi].seconds
+        record("lockstep_small", iterations=sum(its), worst=max(i.true_rnorm / i.rnorm0 for i in i1))
+        # the same call again reuses the graph
+        i2 = fdmpc.pcg_solve_batched(ls, bs, x1, 1e-8, 200)
+        assert [i.iterations for i in i2] == its
+    finally:
+        fdmpc.fdm_batch_destroy(br)
+        fdmpc.fdm_batch_destroy(ls)
+
+
+def test_lockstep_edge_cases():
+    """b = 0 converges at once and drops out; maxit stops a problem with
+    FDM_ENOCONV while the others converge; FP64 preconditioners are refused."""
+    probs = problems(FP32, [(2, 3, 11), (3, 4, 12)])
+    ls = fdmpc.fdm_batch_setup([c.h for c, _, _ in probs], mode=fdmpc.FDM_BATCH_LOCKSTEP)
+    try:
+        bs = [torch.zeros_like(probs[0][1]), probs[1][1]]
+        xs = [torch.full_like(b, 7.0) for b in bs]
+        infos = fdmpc.pcg_solve_batched(ls, bs, xs, 1e-8, 200)
+        assert infos[0].converged and infos[0].iterations == 0 and float(xs[0].abs().max()) == 0.0
+        assert infos[1].converged and infos[1].true_rnorm <= 1e-8 * infos[1].rnorm0
+        bs2 = [probs[0][1], probs[1][1]]
+        with pytest.raises(fdmpc.FdmError) as e:
+            fdmpc.pcg_solve_batched(ls, bs2, xs, 1e-14, 3)
+        assert e.value.code == fdmpc.FDM_ENOCONV
+    finally:
+        fdmpc.fdm_batch_destroy(ls)
+    p64 = problems(FP64, [(2, 3, 13)])
+    with pytest.raises(fdmpc.FdmError) as e:
+        fdmpc.fdm_batch_setup([p64[0][0].h], mode=fdmpc.FDM_BATCH_LOCKSTEP)
+    assert e.value.code == fdmpc.FDM_EINVAL

@@ -85,6 +85,7 @@ def test_invalid_arguments_rejected_without_gpu(lib):
                                     None) == fdmpc.FDM_EINVAL
     assert L.elast_apply(None, None, None, None) == fdmpc.FDM_EINVAL
     assert L.fdm_surrogate_labels(None, fdmpc.FDM_LABEL_PATCH_KAPPA, None, None, None) == fdmpc.FDM_EINVAL
+    assert L.fdm_batch_setup_mode(0, None, 7, ctypes.byref(h)) == fdmpc.FDM_EINVAL  # unknown schedule
 
 
 def test_sipg_and_noalloc_arguments_rejected_without_gpu(lib):
