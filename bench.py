@@ -248,6 +248,58 @@ def oracle_single_core(n=6):
             "sample": "the same family on a %d^3 mesh (Q7, %d free dofs), one OpenMP thread" % (n, d["free"])}
 
 
+def oracle_secondary():
+    """The FP64 oracle on bounded samples of the secondary workloads' families
+    (all host cores): per family its PCG solve rate and the sample."""
+    import oracle
+    from oracle import elasticity as oel, sipg as osg, unstructured as oun
+    from paper_2107_14758_gb300 import inputs
+    oracle.build()
+    out = {}
+
+    def timed(setup, solve):
+        t0 = time.perf_counter()
+        setup()
+        t1 = time.perf_counter()
+        it = solve()
+        t2 = time.perf_counter()
+        return t1 - t0, t2 - t1, it
+
+    xv = np.linspace(0, 1, 5)
+    E = oel.Elasticity(3, xv, xv, xv, 1.0, 1.0, dirichlet_faces=1)
+    bE = E.body_force([0.0, -0.02, 0.0]).ravel()
+    su, so, it = timed(lambda: (E.setup_sdc(), E.setup_coarse(), E.lanczos_omega(inputs.lanczos_start(3 * E.N))),
+                       lambda: E.pcg(bE, rtol=RTOL, maxit=MAXIT)[1])
+    free = 3 * int(E.free.sum())
+    out["elasticity"] = {"value": free / so, "unit": "DoF/s", "solve_s": so, "setup_s": su, "iterations": it,
+                         "sample": "4^3 uniform, p = 3, lambda = 1, x_1 = 0 clamped, %d free dofs" % free}
+    sv = inputs.graded_vertices(4, 7)
+    S = osg.Sipg(3, *sv)
+    bS = np.random.default_rng(8).standard_normal(S.N)
+    su, so, it = timed(lambda: (S.setup_patches(), S.setup_coarse(), S.lanczos_omega(inputs.lanczos_start(S.N))),
+                       lambda: S.pcg(bS, rtol=RTOL, maxit=MAXIT)[1])
+    out["sipg"] = {"value": S.N / so, "unit": "DoF/s", "solve_s": so, "setup_s": su, "iterations": it,
+                   "sample": "DQ_3 on 4^3 graded cells, %d values" % S.N}
+    X, cells = inputs.unstructured_hex_mesh(3, 2, 5)
+    U = oun.HexProblem(5, X, cells)
+    bU = U.mass_apply(np.ones(U.ndof))
+    su, so, it = timed(lambda: (U.setup_patches(), U.setup_coarse(), U.lanczos_omega(inputs.lanczos_start(U.ndof))),
+                       lambda: U.pcg(bU, rtol=RTOL, maxit=MAXIT)[1])
+    free = int(U.free.sum())
+    out["unstructured"] = {"value": free / so, "unit": "DoF/s", "solve_s": so, "setup_s": su, "iterations": it,
+                           "sample": "extruded unstructured mesh m = 3, 2 layers (%d cells), Q5, %d free dofs"
+                                     % (cells.shape[0], free)}
+    w = inputs.deformed_problem(4, 8, 4)
+    P = oracle.Problem(8, w["xv"], w["yv"], w["zv"], jac=w["jac"], kappa=w["kappa"])
+    bP = P.mass_apply(inputs.normal_rhs(P.ndof, 4))
+    su, so, it = timed(lambda: (P.setup_patches(), P.setup_coarse(), P.lanczos_omega(inputs.lanczos_start(P.ndof))),
+                       lambda: P.pcg(bP, rtol=RTOL, maxit=DEFORMED_MAXIT)[1])
+    free = _free_dofs(P.N)
+    out["deformed"] = {"value": free / so, "unit": "DoF/s", "solve_s": so, "setup_s": su, "iterations": it,
+                       "sample": "4^3 deformed mesh, kappa = exp(G), Q8, %d free dofs" % free}
+    return out
+
+
 SAMPLE_TEXT = ("the benchmark workload itself (16^3 graded mesh, Q7, 1,367,631 free dofs, the same b, PCG + "
                "V(1,1), rtol 1e-8) in the FP64 oracle on all host cores; one step = one full PCG solve; "
                "DoF/s = free dofs / solve wall time, set-up excluded (reported as setup_s)")
@@ -467,6 +519,11 @@ def bench_gpu(args):
                "sample": SAMPLE_TEXT, "same_config": True, "solve_s": t, "setup_s": setup_cpu,
                "iterations": it, "single_core": oracle_single_core()}
         del P
+        if not args.no_extra:
+            try:
+                cpu["secondary"] = oracle_secondary()
+            except Exception as exc:  # reported, not fatal
+                cpu["secondary"] = {"error": "%s: %s" % (type(exc).__name__, exc)}
 
     if rank == 0:
         line = {"metric": "pcg_solve_dofs_per_s", "value": value, "unit": "DoF/s", "n_gpus": ws,
