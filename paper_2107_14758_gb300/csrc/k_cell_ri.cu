@@ -169,61 +169,69 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_interp_t(InterpA
   }
   __syncthreads();
   // large cells walk compact lists of their boundary and interior nodes (all lanes
-  // busy: 26 % faster at N = 16); small ones the whole cube with a test per node,
-  // which keeps the rings' columns coalesced (6 % faster at N = 8)
-  constexpr bool compact = N >= 12;
-  constexpr int NI = (N - 2) * (N - 2) * (N - 2), NB = compact ? N3 - NI : N3;
-  if (valid) {  // interface-type nodes: the sum of the stars' interface solutions
-    for (int t = l; t < NB; t += L) {
-      int li[3];
-      if (compact) {
-        boundary_node<N>(t, li[0], li[1], li[2]);
-      } else {
-        li[0] = t % N;
-        li[1] = (t / N) % N;
-        li[2] = t / (N * N);
-        if (li[0] > 0 && li[0] < P && li[1] > 0 && li[1] < P && li[2] > 0 && li[2] < P) continue;
-      }
-      const int idx = li[0] + N * (li[1] + N * li[2]);
-      T acc = 0;
+  // busy: 26 % faster at N = 16); small ones the whole cube with a test per node
+  // (the compact lists measured 34 % slower at N = 8)
+  constexpr int NI = (N - 2) * (N - 2) * (N - 2), NB = N3 - NI;
+  constexpr int M = N > 2 ? N - 2 : 1;  // interior nodes per axis (none for N = 2: no iteration)
+  // interface-type nodes: the sum of the stars' interface solutions
+  auto interface_node = [&](const int li[3]) {
+    const int idx = li[0] + N * (li[1] + N * li[2]);
+    T acc = 0;
 #pragma unroll
-      for (int o = 0; o < 8; ++o) {
-        const int k = a.cmap[(sCls[c][o] * 8 + o) * N3 + idx];
-        if (k >= 0) acc += a.X[sOff[c][o] + k];
-      }
-      U[pid<N>(li[0], li[1], li[2])] = acc;
+    for (int o = 0; o < 8; ++o) {
+      const int k = a.cmap[(sCls[c][o] * 8 + o) * N3 + idx];
+      if (k >= 0) acc += a.X[sOff[c][o] + k];
     }
-  }
-  __syncthreads();
-  if (valid) {  // interior nodes: (8 r(m) - sum over the 6 face nodes of A_mf z(f)) / A_mm
-    const T *Ek = a.E + (int64_t)cell * N3;
-    constexpr int M = N > 2 ? N - 2 : 1;  // interior nodes per axis (none for N = 2: no iteration)
-    for (int t = l; t < (compact ? NI : N3); t += L) {  // the interior nodes, x fastest
-      int li[3];
-      if (compact) {
-        li[0] = 1 + t % M;
-        li[1] = 1 + (t / M) % M;
-        li[2] = 1 + t / (M * M);
-      } else {
-        li[0] = t % N;
-        li[1] = (t / N) % N;
-        li[2] = t / (N * N);
-        if (!(li[0] > 0 && li[0] < P && li[1] > 0 && li[1] < P && li[2] > 0 && li[2] < P)) continue;
-      }
-      const int idx = li[0] + N * (li[1] + N * li[2]);
-      T s = T(8) * Ek[idx];
+    U[pid<N>(li[0], li[1], li[2])] = acc;
+  };
+  // interior nodes: (8 r(m) - sum over the 6 face nodes of A_mf z(f)) / A_mm
+  const T *Ek = a.E + (int64_t)(valid ? cell : 0) * N3;
+  auto interior_node = [&](const int li[3]) {
+    const int idx = li[0] + N * (li[1] + N * li[2]);
+    T s = T(8) * Ek[idx];
 #pragma unroll
-      for (int ax = 0; ax < 3; ++ax) {
-        const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
-        const T mu_ax = ax == 0 ? m0 : (ax == 1 ? m1 : m2);
-        const T tang = mu_ax * sBf[li[t1] * N + li[t1]] * sBf[li[t2] * N + li[t2]];
-        int q0[3] = {li[0], li[1], li[2]}, qp[3] = {li[0], li[1], li[2]};
-        q0[ax] = 0;
-        qp[ax] = P;
-        s -= tang * sAf[0 * N + li[ax]] * U[pid<N>(q0[0], q0[1], q0[2])];
-        s -= tang * sAf[P * N + li[ax]] * U[pid<N>(qp[0], qp[1], qp[2])];
+    for (int ax = 0; ax < 3; ++ax) {
+      const int t1 = ax == 0 ? 1 : 0, t2 = ax == 2 ? 1 : 2;
+      const T mu_ax = ax == 0 ? m0 : (ax == 1 ? m1 : m2);
+      const T tang = mu_ax * sBf[li[t1] * N + li[t1]] * sBf[li[t2] * N + li[t2]];
+      int q0[3] = {li[0], li[1], li[2]}, qp[3] = {li[0], li[1], li[2]};
+      q0[ax] = 0;
+      qp[ax] = P;
+      s -= tang * sAf[0 * N + li[ax]] * U[pid<N>(q0[0], q0[1], q0[2])];
+      s -= tang * sAf[P * N + li[ax]] * U[pid<N>(qp[0], qp[1], qp[2])];
+    }
+    U[pid<N>(li[0], li[1], li[2])] = s / diag_ii<T, N>(sAf, sBf, m0, m1, m2, li[0], li[1], li[2]);
+  };
+  if constexpr (N >= 12) {
+    if (valid) {
+      for (int t = l; t < NB; t += L) {
+        int li[3];
+        boundary_node<N>(t, li[0], li[1], li[2]);
+        interface_node(li);
       }
-      U[pid<N>(li[0], li[1], li[2])] = s / diag_ii<T, N>(sAf, sBf, m0, m1, m2, li[0], li[1], li[2]);
+    }
+    __syncthreads();
+    if (valid) {
+      for (int t = l; t < NI; t += L) {  // x fastest
+        const int li[3] = {1 + t % M, 1 + (t / M) % M, 1 + t / (M * M)};
+        interior_node(li);
+      }
+    }
+  } else {
+    if (valid) {
+      for (int idx = l; idx < N3; idx += L) {
+        const int li[3] = {idx % N, (idx / N) % N, idx / (N * N)};
+        const bool onb = li[0] == 0 || li[0] == P || li[1] == 0 || li[1] == P || li[2] == 0 || li[2] == P;
+        if (onb) interface_node(li);
+      }
+    }
+    __syncthreads();
+    if (valid) {
+      for (int idx = l; idx < N3; idx += L) {
+        const int li[3] = {idx % N, (idx / N) % N, idx / (N * N)};
+        const bool onb = li[0] == 0 || li[0] == P || li[1] == 0 || li[1] == P || li[2] == 0 || li[2] == P;
+        if (!onb) interior_node(li);
+      }
     }
   }
   __syncthreads();
