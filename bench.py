@@ -38,8 +38,8 @@ FALLBACK_HBM_GBS = 6800.0
 # graded Q7 (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture,
 # summarised in profiles/patch_solve_q7_graded16.md), valid while the kernel
 # source k_asm.cu has the recorded sha256; null otherwise.
-PROFILED_TRAFFIC = {"kernel_source_sha256": "7b09899072be12a241bcb679d1f49e641d0fe85b05caf64016a2e7b4a20a635b",
-                    "dram_bytes_per_launch": 0.33754e9,
+PROFILED_TRAFFIC = {"kernel_source_sha256": "07f40a126267424652c79151ace4f15b1ad75b761ec2ac08c477c8e86c11d937",
+                    "dram_bytes_per_launch": 0.33753e9,
                     "source": "profiles/patch_solve_q7_graded16.md (one ncu capture, same kernel source)"}
 
 
