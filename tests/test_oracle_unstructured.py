@@ -226,18 +226,17 @@ def _corner_jacobians(X, cells):
 
 def test_kershaw_like_mesh_is_harder():
     """On a Kershaw-type distorted mesh (a valid mesh: every corner Jacobian
-    positive) the iteration counts grow with p, while on the Cartesian mesh of
-    the same size they stay flat: the trend of Table 1's Kershaw column
-    (tests/golden/table1_kershaw_3d.txt: 54, 98, 131 at p = 3, 7, 15), whose
-    text says the method is not p-robust there."""
-    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table1_kershaw_3d.txt")
-    paper = {int(l.split()[0]): int(l.split()[1]) for l in open(golden) if l.strip() and not l.startswith("#")}
-    assert paper[3] < paper[7] < paper[15]
+    positive) the iteration counts rise with p over p = 2, 3, 5, while on the
+    Cartesian mesh of the same size they stay flat: the trend that Table 1's
+    Kershaw column shows and that its text describes as a loss of p-robustness.
+    The fixture tests/golden/table1_kershaw_3d.txt (54, 98, 131 at p = 3, 7, 15)
+    is context only: the paper's Kershaw mesh is a stronger distortion on a
+    larger mesh, so its absolute counts are not expected here."""
     its = {}
-    for name, (X, cells) in (("cartesian", inputs.tensor_hex_mesh(*inputs.uniform_vertices(6))),
-                             ("kershaw", inputs.kershaw_like_mesh(6, 0.3))):
+    for name, (X, cells) in (("cartesian", inputs.tensor_hex_mesh(*inputs.uniform_vertices(4))),
+                             ("kershaw", inputs.kershaw_like_mesh(4, 0.3))):
         assert _corner_jacobians(X, cells).min() > 0
-        for p in (2, 3):
+        for p in (2, 3, 5):
             U = HexProblem(p, X, cells)
             U.setup_patches()
             U.setup_coarse()
@@ -246,6 +245,10 @@ def test_kershaw_like_mesh_is_harder():
             x, it, conv = U.pcg(b, maxit=500)
             assert conv
             its[name, p] = it
-    assert abs(its["cartesian", 3] - its["cartesian", 2]) <= 1
-    assert its["kershaw", 3] > its["kershaw", 2] >= its["cartesian", 2]
-    assert its["kershaw", 3] >= 1.5 * its["cartesian", 3]
+    cart = [its["cartesian", p] for p in (2, 3, 5)]
+    kers = [its["kershaw", p] for p in (2, 3, 5)]
+    assert max(cart) - min(cart) <= 2 and abs(cart[2] - cart[1]) <= 1
+    assert kers[0] < kers[1] < kers[2]
+    assert kers[0] >= cart[0]
+    assert kers[1] >= 1.5 * cart[1]
+    assert kers[2] / cart[2] > kers[1] / cart[1]
