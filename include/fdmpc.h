@@ -659,8 +659,10 @@ void fdm_hex_destroy(fdm_hexgpu *ctx);
                                   at mu* (NaN without samples27) and at the current mu */
 #define FDM_Q_MUBAR 22         /* double[3*ncell]: averaged surrogate mu_avg (curved cells) */
 #define FDM_Q_SURR_OUTPUT 23   /* float[3*ncell]: network outputs c of the last fdm_surrogate_apply */
-#define FDM_Q_TUNING 24        /* double[8]: autotuner choice: patch kernel (1 classic, 3 resident),
-                                  threads, eight rows per warp (0/1), sweep time (us), candidates
+#define FDM_Q_TUNING 24        /* double[8]: autotuner choice: patch kernel (L form: 1 one CTA per
+                                  patch, 3 resident; Schur-coupling form: 5 one CTA per patch,
+                                  6 persistent, 7 fully staged persistent, 8 one warp per patch),
+                                  threads, rows-per-warp variant, sweep time (us), candidates
                                   timed; zeros without autotune */
 #define FDM_Q_GMG_LEVELS 25    /* int32[1 + 4 (L+1)]: coarsenings L of the Q1 multigrid (0 = exact
                                   coarse solve), then per level cells nx, ny, nz and unknowns nf */

@@ -118,6 +118,31 @@ __device__ __forceinline__ V4<double> load4(const double *p) {
   double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
   return {a.x, a.y, b.x, b.y};
 }
+// read-once streams (the W block of the patch solve): 128-bit global loads
+// that do not allocate in L1, so that the class index tables stay there
+__device__ __forceinline__ V4<float> load4_stream(const float *p) {
+  V4<float> v;
+  asm("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p));
+  return v;
+}
+__device__ __forceinline__ V4<double> load4_stream(const double *p) {
+  V4<double> v;
+  asm("ld.global.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  asm("ld.global.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(v.z), "=d"(v.w) : "l"(p + 2));
+  return v;
+}
+__device__ __forceinline__ float load_na(const float *p) {
+  float v;
+  asm("ld.global.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double load_na(const double *p) {
+  double v;
+  asm("ld.global.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
 __device__ __forceinline__ void store4(float *p, const V4<float> &v) {
   *reinterpret_cast<float4 *>(p) = make_float4(v.x, v.y, v.z, v.w);
 }
@@ -688,6 +713,7 @@ __device__ __forceinline__ void sym_apply(const ClassDev &C, const T *Wv, const 
   // 128-bit shared accesses where v and the accumulators are 16-byte aligned
   // (acc always is; v = g_T is when the lower block has a multiple of 4 rows)
   const bool vec = ((reinterpret_cast<uintptr_t>(v) | reinterpret_cast<uintptr_t>(acc)) & 15) == 0;
+  const bool wglob = __isGlobal(Wv);  // W streams from global memory (else staged in shared memory)
   for (int r0 = warp * RB; r0 < n2; r0 += NW * RB) {
     T rs[RB], vr[RB];
     int ngu[RB];
@@ -706,7 +732,8 @@ __device__ __forceinline__ void sym_apply(const ClassDev &C, const T *Wv, const 
     for (int q4 = lane; q4 < ngmax; q4 += 32) {
       V4<T> w[RB];
 #pragma unroll
-      for (int u = 0; u < RB; ++u) w[u] = q4 < ngu[u] ? load4(row[u] + 4 * q4) : V4<T>{0, 0, 0, 0};
+      for (int u = 0; u < RB; ++u)
+        w[u] = q4 < ngu[u] ? (wglob ? load4_stream(row[u] + 4 * q4) : load4(row[u] + 4 * q4)) : V4<T>{0, 0, 0, 0};
       const int cb = 4 * q4;
       const V4<T> vv = vec ? load4(v + cb) : V4<T>{v[cb], v[cb + 1], v[cb + 2], v[cb + 3]};  // padding of W is zero
       T c0 = 0, c1 = 0, c2 = 0, c3 = 0;
@@ -768,15 +795,27 @@ __device__ __forceinline__ void sc_gather(const PatchSolveArgs<T> &a, const Patc
                  g.nx * (star_cell_along(C.full[1], P.v[1], g.ny, 0) + g.ny * star_cell_along(C.full[2], P.v[2], g.nz, 0));
   const int sy = g.nx, sz = g.nx * g.ny;
   const T *E = a.E;
+  // the eight codes of a dof in two 16-byte loads, then all its cell values in
+  // flight at once; summed in code order up to the first -1
   for (int k = tid; k < nG; k += NT) {
-    const int *src = C.gsrc + 8 * k;
-    T r = 0;
-    for (int e = 0; e < 8; ++e) {
-      const int code = src[e];
-      if (code < 0) break;
-      const int slot = code >> 16;
+    const int4 c0 = reinterpret_cast<const int4 *>(C.gsrc + 8 * k)[0];
+    const int4 c1 = reinterpret_cast<const int4 *>(C.gsrc + 8 * k)[1];
+    const int code[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+    T e[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int cd = code[q];
+      const int slot = cd >> 16;
       const int cell = lo + (slot & 1) + ((slot >> 1) & 1) * sy + (slot >> 2) * sz;
-      r += E[(int64_t)cell * n3 + (code & 0xffff)];
+      const T *ep = cd >= 0 ? E + (int64_t)cell * n3 + (cd & 0xffff) : E;  // a valid address either way
+      e[q] = cd >= 0 ? load_na(ep) : T(0);
+    }
+    T r = 0;
+    bool live = true;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      live = live && code[q] >= 0;
+      r += live ? e[q] : T(0);
     }
     gv[k] = r;
   }
