@@ -120,27 +120,29 @@ __device__ __forceinline__ V4<double> load4(const double *p) {
 }
 // read-once streams (the W block of the patch solve): 128-bit global loads
 // that do not allocate in L1, so that the class index tables stay there
+// (volatile: never speculated, since a caller may hold a shared-memory W and
+// take the generic path instead)
 __device__ __forceinline__ V4<float> load4_stream(const float *p) {
   V4<float> v;
-  asm("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+  asm volatile("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
       : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
       : "l"(p));
   return v;
 }
 __device__ __forceinline__ V4<double> load4_stream(const double *p) {
   V4<double> v;
-  asm("ld.global.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
-  asm("ld.global.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(v.z), "=d"(v.w) : "l"(p + 2));
+  asm volatile("ld.global.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  asm volatile("ld.global.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(v.z), "=d"(v.w) : "l"(p + 2));
   return v;
 }
 __device__ __forceinline__ float load_na(const float *p) {
   float v;
-  asm("ld.global.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  asm volatile("ld.global.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
   return v;
 }
 __device__ __forceinline__ double load_na(const double *p) {
   double v;
-  asm("ld.global.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  asm volatile("ld.global.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
   return v;
 }
 __device__ __forceinline__ void store4(float *p, const V4<float> &v) {
@@ -490,7 +492,6 @@ __global__ void __launch_bounds__(NT, 1) k_patch_resident(PatchSolveArgs<T> a, i
   if (tid == 0) {
     bulk::mbar_init(&bar[0], 1);
     bulk::mbar_init(&bar[1], 1);
-    bulk::mbar_init(&bar[2], 1);
     bulk::fence_mbar_init();
     sFail = 0;
   }
@@ -969,6 +970,7 @@ __global__ void __launch_bounds__(NT, MINB) k_patch_solve_scp(PatchSolveArgs<T> 
   if (tid == 0) {
     bulk::mbar_init(&bar[0], 1);
     bulk::mbar_init(&bar[1], 1);
+    bulk::mbar_init(&bar[2], 1);  // the test hook's barrier is a valid one that nothing completes
     bulk::fence_mbar_init();
     sFail = 0;
     sPend[0] = sPend[1] = 0;
