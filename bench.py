@@ -38,8 +38,8 @@ FALLBACK_HBM_GBS = 6800.0
 # graded Q7 (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture,
 # summarised in profiles/patch_solve_q7_graded16.md), valid while the kernel
 # source k_asm.cu has the recorded sha256; null otherwise.
-PROFILED_TRAFFIC = {"kernel_source_sha256": "92ae7faa5c0a6892ce2252412e36f1f2c4531d8cff6dd3c7a30551e615d18c82",
-                    "dram_bytes_per_launch": 0.34399e9,
+PROFILED_TRAFFIC = {"kernel_source_sha256": "2b4aaf171d58b34b08b3b44559a3cc2774f39bf782c7ce6d48e9bd638376db3e",
+                    "dram_bytes_per_launch": 0.34421e9,
                     "source": "profiles/patch_solve_q7_graded16.md (one ncu capture, same kernel source)"}
 
 

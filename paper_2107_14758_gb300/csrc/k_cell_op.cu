@@ -86,12 +86,11 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_box_op(Grid g, c
   const bool valid = cell < g.ncell;
   EO<T, N>::build(tab + tab_off(TAB_A, N), tA, threadIdx.x, blockDim.x);
   EO<T, N>::build(tab + tab_off(TAB_B, N), tB, threadIdx.x, blockDim.x);
-  T mu0 = 0, mu1 = 0, mu2 = 0;
+  // the cell's three coefficients, converted once per cell (read after the first barrier)
+  __shared__ T sMu[CPB][3];
+  if (l < 3) sMu[c][l] = valid ? T(mub[3 * cell + l]) : T(0);
   if (valid) {
     const int cx = cell % g.nx, cy = (cell / g.nx) % g.ny, cz = cell / (g.nx * g.ny);
-    mu0 = T(mub[3 * cell]);
-    mu1 = T(mub[3 * cell + 1]);
-    mu2 = T(mub[3 * cell + 2]);
     for (int idx = l; idx < N3; idx += L) {
       const int i = idx % N, j = (idx / N) % N, k = idx / (N * N);
       const int gx = cx * P + i, gy = cy * P + j, gz = cz * P + k;
@@ -100,6 +99,7 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_box_op(Grid g, c
     }
   }
   __syncthreads();
+  const T mu0 = sMu[c][0], mu1 = sMu[c][1], mu2 = sMu[c][2];
   const int a = l % N, b = l / N;
   {  // x: B1 = Bx u, B2 = Ax u
     T x[N];

@@ -33,15 +33,14 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_restrict_t(Grid 
     sAf[i] = tab[tab_off(TAB_AF, N) + i];
     sBf[i] = tab[tab_off(TAB_BF, N) + i];
   }
+  // the cell's three coefficients, converted once per cell (read after the first barrier)
+  __shared__ T sMu[CPB][3];
+  if (l < 3) sMu[c][l] = valid ? T(mug[3 * cell + l]) : T(0);
   int cx = 0, cy = 0, cz = 0;
-  T m0 = 0, m1 = 0, m2 = 0;
   if (valid) {
     cx = cell % g.nx;
     cy = (cell / g.nx) % g.ny;
     cz = cell / (g.nx * g.ny);
-    m0 = T(mug[3 * cell]);
-    m1 = T(mug[3 * cell + 1]);
-    m2 = T(mug[3 * cell + 2]);
     for (int idx = l; idx < N3; idx += L) {  // W_K r_K, W = 1 / multiplicity, Dirichlet entries 0
       const int i = idx % N, j = (idx / N) % N, k = idx / (N * N);
       const int gx = cx * P + i, gy = cy * P + j, gz = cz * P + k;
@@ -54,6 +53,7 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_restrict_t(Grid 
     }
   }
   __syncthreads();
+  const T m0 = sMu[c][0], m1 = sMu[c][1], m2 = sMu[c][2];
   line_pass<T, N, true>(U, V, sT, 0, l);
   __syncthreads();
   line_pass<T, N, true>(V, U, sT, 1, l);
@@ -145,15 +145,14 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_interp_t(InterpA
     sBf[i] = a.tab[tab_off(TAB_BF, N) + i];
   }
   int ce[3] = {0, 0, 0};
-  T m0 = 0, m1 = 0, m2 = 0;
   if (valid) {
     ce[0] = cell % g.nx;
     ce[1] = (cell / g.nx) % g.ny;
     ce[2] = cell / (g.nx * g.ny);
-    m0 = T(a.mu[3 * cell]);
-    m1 = T(a.mu[3 * cell + 1]);
-    m2 = T(a.mu[3 * cell + 2]);
   }
+  // the cell's three coefficients, converted once per cell (read after the next barrier)
+  __shared__ T sMu[CPB][3];
+  if (l < 3) sMu[c][l] = valid ? T(a.mu[3 * cell + l]) : T(0);
   // the stars of the cell's 8 corners: class and offset of their solutions
   __shared__ int sCls[cells_per_cta<N>()][8];
   __shared__ int64_t sOff[cells_per_cta<N>()][8];
@@ -168,6 +167,7 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_interp_t(InterpA
     }
   }
   __syncthreads();
+  const T m0 = sMu[c][0], m1 = sMu[c][1], m2 = sMu[c][2];
   // large cells walk compact lists of their boundary and interior nodes (all lanes
   // busy: 26 % faster at N = 16); small ones the whole cube with a test per node
   // (the compact lists measured 34 % slower at N = 8)
@@ -242,6 +242,7 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_interp_t(InterpA
   line_pass<T, N, false>(U, V, sT, 2, l);
   __syncthreads();
   if (!valid) return;
+  const T om = T(omega);  // omega in the kernel's precision
   for (int idx = l; idx < N3; idx += L) {
     const int i = idx % N, j = (idx / N) % N, k = idx / (N * N);
     if ((i == 0 && ce[0] > 0) || (j == 0 && ce[1] > 0) || (k == 0 && ce[2] > 0)) continue;  // not owner
@@ -249,7 +250,8 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_interp_t(InterpA
     const bool dir = node_dirichlet(g, gx, gy, gz);
     const int64_t id = gidx(g, gx, gy, gz);
     // z = omega * relaxation, plus a.addv where given (the V-cycle's pre-smoothed x1)
-    z[id] = dir ? Tout(0) : (a.addv ? Tout(a.addv[id] + T(omega) * V[pid<N>(i, j, k)]) : Tout(omega * V[pid<N>(i, j, k)]));
+    const T zv = a.addv ? a.addv[id] + om * V[pid<N>(i, j, k)] : om * V[pid<N>(i, j, k)];
+    z[id] = dir ? Tout(0) : Tout(zv);
   }
 }
 
