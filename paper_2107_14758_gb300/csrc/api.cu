@@ -457,6 +457,8 @@ void setup_tables(fdm_ctx *c) {
   put(TAB_VQ, b.Vq);
   put(TAB_DQ, b.Dq);
   std::copy(b.xi.begin(), b.xi.end(), t.begin() + tab_off(TAB_XI, n));
+  put(TAB_VE, b.Ve);
+  std::copy(b.lame.begin(), b.lame.end(), t.begin() + tab_off(TAB_LE, n));
   c->tab64 = c->upload(t);
   std::vector<float> tf(t.begin(), t.end());
   c->tab32 = c->upload(tf);

@@ -271,6 +271,72 @@ void chol_lower(int m, std::vector<double> &a) {
 
 }  // namespace
 
+// The generalised eigenpairs of the whole-element pencil (A, B): A s = lam B s,
+// S^T B S = I (Section 2.3's fast diagonalisation on all n nodes), as the rows
+// of V = S^T B (so that A = V^T diag(lam) V and B = V^T V).  A and B are
+// symmetric about the element centre, so every mode is even or odd there; the
+// modes are ordered even first (ascending lam within each group), and each row
+// of V is made exactly even or odd (averaged with its mirror image), since the
+// kernels read only its first ceil(n/2) entries.
+void cell_modes(Basis1D &b) {
+  const int n = b.n;
+  std::vector<double> L = b.B, C(n * n, 0.0), W(n * n, 0.0);
+  chol_lower(n, L);
+  for (int c = 0; c < n; ++c)  // W = L^{-1} A
+    for (int i = 0; i < n; ++i) {
+      double s = b.A[i * n + c];
+      for (int k = 0; k < i; ++k) s -= L[i * n + k] * W[k * n + c];
+      W[i * n + c] = s / L[i * n + i];
+    }
+  for (int c = 0; c < n; ++c)  // C = L^{-1} W^T = L^{-1} A L^{-T}
+    for (int i = 0; i < n; ++i) {
+      double s = W[c * n + i];
+      for (int k = 0; k < i; ++k) s -= L[i * n + k] * C[k * n + c];
+      C[i * n + c] = s / L[i * n + i];
+    }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j) C[i * n + j] = C[j * n + i] = 0.5 * (C[i * n + j] + C[j * n + i]);
+  std::vector<double> ev;
+  sym_eig(n, C, ev);  // eigenvectors q in the columns of C
+  std::vector<double> S(n * n);
+  for (int j = 0; j < n; ++j)  // s = L^{-T} q
+    for (int i = n - 1; i >= 0; --i) {
+      double v = C[i * n + j];
+      for (int k = i + 1; k < n; ++k) v -= L[k * n + i] * S[k * n + j];
+      S[i * n + j] = v / L[i * n + i];
+    }
+  std::vector<int> even, odd;
+  for (int j = 0; j < n; ++j) {
+    double sym = 0.0, nrm = 0.0;
+    for (int i = 0; i < n; ++i) {
+      sym += S[i * n + j] * S[(n - 1 - i) * n + j];
+      nrm += S[i * n + j] * S[i * n + j];
+    }
+    if (std::fabs(std::fabs(sym) - nrm) > 1e-8 * nrm) fail(FDM_EINVAL, "basis: an element mode is neither even nor odd");
+    (sym > 0 ? even : odd).push_back(j);
+  }
+  auto by_lam = [&](int a, int c) { return ev[a] < ev[c]; };
+  std::sort(even.begin(), even.end(), by_lam);
+  std::sort(odd.begin(), odd.end(), by_lam);
+  if ((int)even.size() != (n + 1) / 2) fail(FDM_EINVAL, "basis: unexpected number of even element modes");
+  std::vector<int> ord = even;
+  ord.insert(ord.end(), odd.begin(), odd.end());
+  b.Ve.assign(n * n, 0.0);
+  b.lame.assign(n, 0.0);
+  for (int k = 0; k < n; ++k) {
+    const int j = ord[k];
+    const double par = k < (n + 1) / 2 ? 1.0 : -1.0;
+    b.lame[k] = ev[j];
+    std::vector<double> v(n, 0.0);
+    for (int c = 0; c < n; ++c)
+      for (int i = 0; i < n; ++i) v[c] += S[i * n + j] * b.B[i * n + c];
+    for (int c = 0; c < n; ++c) {
+      const int cm = n - 1 - c;
+      b.Ve[k * n + c] = c == cm ? (par > 0 ? v[c] : 0.0) : 0.5 * (v[c] + par * v[cm]);
+    }
+  }
+}
+
 Basis1D make_basis(int p) {
   if (p < 1 || p > PMAX) fail(FDM_EINVAL, "degree p must be in [1, 31]");
   Basis1D b;
@@ -383,6 +449,7 @@ Basis1D make_basis(int p) {
         b.Bf[i * n + j] = 0.0;
       }
     }
+  cell_modes(b);
   return b;
 }
 

@@ -18,10 +18,13 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // 1D tables in precision T for one degree, laid out as consecutive n x n
-// row-major blocks: A, B, Af, Bf, T, Vq, Dq, then the n GLL nodes.
-enum { TAB_A = 0, TAB_B = 1, TAB_AF = 2, TAB_BF = 3, TAB_T = 4, TAB_VQ = 5, TAB_DQ = 6, TAB_XI = 7 };
+// row-major blocks: A, B, Af, Bf, T, Vq, Dq, then the n GLL nodes (in the
+// eighth block), the element modes V (rows, even modes first) and their n
+// eigenvalues.
+enum { TAB_A = 0, TAB_B = 1, TAB_AF = 2, TAB_BF = 3, TAB_T = 4, TAB_VQ = 5, TAB_DQ = 6, TAB_XI = 7, TAB_VE = 8,
+       TAB_LE = 9 };
 __host__ __device__ inline int tab_off(int which, int n) { return which * n * n; }
-__host__ __device__ inline int tab_size(int n) { return 7 * n * n + n; }
+__host__ __device__ inline int tab_size(int n) { return 9 * n * n + n; }
 
 // Per-patch description on the device.
 struct PatchDev {

@@ -515,6 +515,8 @@ int fdm_elast_setup_bc(const fdm_mesh *mesh, int p, double mu, double lam, int d
     put(TAB_VQ, basis.Vq);
     put(TAB_DQ, basis.Dq);
     std::copy(basis.xi.begin(), basis.xi.end(), t.begin() + tab_off(TAB_XI, g.n));
+    put(TAB_VE, basis.Ve);
+    std::copy(basis.lame.begin(), basis.lame.end(), t.begin() + tab_off(TAB_LE, g.n));
     e->tab64 = e->upload(t);
     e->tab32 = e->upload(std::vector<float>(t.begin(), t.end()));
     e->Lc = e->upload(L);

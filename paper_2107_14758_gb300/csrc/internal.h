@@ -43,7 +43,9 @@ struct Basis1D {
   std::vector<double> T;               // u_gll = T u_fdm (n x n)
   std::vector<double> Af, Bf;          // T^T A T, T^T B T with exact structural zeros
   std::vector<double> Vq, Dq;          // Lagrange values / derivatives at Gauss points (q x n)
+  std::vector<double> Ve, lame;        // element modes: V = S^T B by rows (even modes first), eigenvalues
 };
+void cell_modes(Basis1D &b);  // fills Ve, lame from A, B
 Basis1D make_basis(int p);  // throws via fail() on error
 
 // ---------------------------------------------------------------- geometric multigrid (Q1 problem)

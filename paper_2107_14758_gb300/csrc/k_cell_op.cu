@@ -173,6 +173,140 @@ __global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_box_op(Grid g, c
   }
 }
 
+// ------------------------------------------------------------------ box cells, element modes
+// The same box-cell stiffness in the 1D generalised eigenbasis of (A, B)
+// (Section 2.3's fast diagonalisation, applied as an operator): with the
+// modes V = S^T B by rows, A = V^T diag(lam) V and B = V^T V, so
+//   y_K = (V^T)^{(x)3} D V^{(x)3} u_K,  D_ijk = mu1 lam_i + mu2 lam_j + mu3 lam_k
+// (i along x): three forward passes, the diagonal, three backward passes, six
+// line passes against seven, with no coefficient products inside them.  Modes
+// are even or odd about the element centre and stored even first, so a
+// forward pass contracts the half sums of a line with the even modes and the
+// half differences with the odd ones, and a backward pass forms each node
+// pair from its even and odd mode sums: n^2 / 2 multiply-adds per line.
+// Passes run in place (each thread reads its whole line before writing it):
+// forward along z and y, then along x the forward pass, the diagonal and the
+// backward pass in registers, then backward along y and z, the last one
+// writing the cell-local result in natural layout.
+template <typename T, int N>
+__device__ __forceinline__ int line_at(int axis, int m, int a, int b) {
+  return axis == 0 ? pid<N>(m, a, b) : (axis == 1 ? pid<N>(a, m, b) : pid<N>(a, b, m));
+}
+// nodes -> modes along one line
+template <typename T, int N>
+__device__ __forceinline__ void modes_fwd(const T *V, const T (&x)[N], T (&w)[N]) {
+  constexpr int H = N / 2, NE = (N + 1) / 2;
+  T sp[NE], dm[H > 0 ? H : 1];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    sp[j] = x[j] + x[N - 1 - j];
+    dm[j] = x[j] - x[N - 1 - j];
+  }
+  if (N % 2 == 1) sp[H] = x[H];
+#pragma unroll
+  for (int k = 0; k < NE; ++k) {
+    T acc = 0;
+#pragma unroll
+    for (int j = 0; j < NE; ++j) acc = mad(V[k * N + j], sp[j], acc);
+    w[k] = acc;
+  }
+#pragma unroll
+  for (int k = NE; k < N; ++k) {
+    T acc = 0;
+#pragma unroll
+    for (int j = 0; j < H; ++j) acc = mad(V[k * N + j], dm[j], acc);
+    w[k] = acc;
+  }
+}
+// modes -> nodes along one line
+template <typename T, int N>
+__device__ __forceinline__ void modes_bwd(const T *V, const T (&w)[N], T (&x)[N]) {
+  constexpr int H = N / 2, NE = (N + 1) / 2;
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    T e = 0, o = 0;
+#pragma unroll
+    for (int k = 0; k < NE; ++k) e = mad(V[k * N + i], w[k], e);
+#pragma unroll
+    for (int k = NE; k < N; ++k) o = mad(V[k * N + i], w[k], o);
+    x[i] = e + o;
+    x[N - 1 - i] = e - o;
+  }
+  if (N % 2 == 1) {
+    T e = 0;
+#pragma unroll
+    for (int k = 0; k < NE; ++k) e = mad(V[k * N + H], w[k], e);
+    x[H] = e;
+  }
+}
+
+template <typename T, typename Tin, int N>
+__global__ void __launch_bounds__(cells_per_cta<N>() * N * N) k_box_op_modes(Grid g, const double *__restrict__ mub,
+                                                                             const T *__restrict__ tab,
+                                                                             const Tin *__restrict__ u,
+                                                                             T *__restrict__ E) {
+  extern __shared__ __align__(16) unsigned char smem_[];
+  constexpr int P = N - 1, L = N * N, CPB = cells_per_cta<N>(), PS = psize<N>(), N3 = N * N * N;
+  T *sV = reinterpret_cast<T *>(smem_), *sLam = sV + N * N;
+  const int c = threadIdx.x / L, l = threadIdx.x % L;
+  T *U = sLam + N + c * PS;
+  const int cell = blockIdx.x * CPB + c;
+  const bool valid = cell < g.ncell;
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) sV[i] = tab[tab_off(TAB_VE, N) + i];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sLam[i] = tab[tab_off(TAB_LE, N) + i];
+  __shared__ T sMu[CPB][3];
+  if (l < 3) sMu[c][l] = valid ? T(mub[3 * cell + l]) : T(0);
+  if (valid) {
+    const int cx = cell % g.nx, cy = (cell / g.nx) % g.ny, cz = cell / (g.nx * g.ny);
+    for (int idx = l; idx < N3; idx += L) {
+      const int i = idx % N, j = (idx / N) % N, k = idx / (N * N);
+      const int gx = cx * P + i, gy = cy * P + j, gz = cz * P + k;
+      const bool dir = node_dirichlet(g, gx, gy, gz);
+      U[pid<N>(i, j, k)] = dir ? T(0) : T(u[gidx(g, gx, gy, gz)]);
+    }
+  }
+  __syncthreads();
+  const int a = l % N, b = l / N;
+  T x[N], w[N];
+#pragma unroll
+  for (int axis = 2; axis >= 1; --axis) {  // forward along z, then y
+#pragma unroll
+    for (int m = 0; m < N; ++m) x[m] = U[line_at<T, N>(axis, m, a, b)];
+    modes_fwd<T, N>(sV, x, w);
+#pragma unroll
+    for (int m = 0; m < N; ++m) U[line_at<T, N>(axis, m, a, b)] = w[m];
+    __syncthreads();
+  }
+  {  // along x: forward, D (y mode a, z mode b), backward
+#pragma unroll
+    for (int m = 0; m < N; ++m) x[m] = U[pid<N>(m, a, b)];
+    modes_fwd<T, N>(sV, x, w);
+    const T mu0 = sMu[c][0], cl = sMu[c][1] * sLam[a] + sMu[c][2] * sLam[b];
+#pragma unroll
+    for (int m = 0; m < N; ++m) w[m] *= mad(mu0, sLam[m], cl);
+    modes_bwd<T, N>(sV, w, x);
+#pragma unroll
+    for (int m = 0; m < N; ++m) U[pid<N>(m, a, b)] = x[m];
+  }
+  __syncthreads();
+  {  // backward along y
+#pragma unroll
+    for (int m = 0; m < N; ++m) w[m] = U[pid<N>(a, m, b)];
+    modes_bwd<T, N>(sV, w, x);
+#pragma unroll
+    for (int m = 0; m < N; ++m) U[pid<N>(a, m, b)] = x[m];
+  }
+  __syncthreads();
+  if (valid) {  // backward along z, cell-local result in natural layout
+#pragma unroll
+    for (int m = 0; m < N; ++m) w[m] = U[pid<N>(a, b, m)];
+    modes_bwd<T, N>(sV, w, x);
+    T *out = E + (int64_t)cell * N3;
+#pragma unroll
+    for (int m = 0; m < N; ++m) out[a + N * (b + N * m)] = x[m];
+  }
+}
+
 // ------------------------------------------------------------------ curved cells
 // Gauss quadrature with n points per direction (Section 2.7):
 // y = sum_q grad_hat phi . (w_q kappa Ghat_q) grad_hat u, with V[q][m] = l_m(x_q) and
@@ -348,6 +482,10 @@ bool launch_box_op_fast(const OpArgs &a, const Tin *u, Tout *y, T *E, cudaStream
         set_smem(k_gen_op<T, Tin, N>, sm);
         k_gen_op<T, Tin, N><<<(a.g.ncell + CPB - 1) / CPB, CPB * N * N, sm, st>>>(
             a.g, tab, reinterpret_cast<const T *>(a.Gw), u, E);
+      } else if (std::is_same<T, double>::value) {  // FP64: bound by the FP64 pipe, six passes
+        const size_t sm = sizeof(T) * (N * N + N + (size_t)CPB * psize<N>());
+        set_smem(k_box_op_modes<T, Tin, N>, sm);
+        k_box_op_modes<T, Tin, N><<<(a.g.ncell + CPB - 1) / CPB, CPB * N * N, sm, st>>>(a.g, a.mu_box, tab, u, E);
       } else {
         const size_t sm = sizeof(T) * (2 * EO<T, N>::S + (size_t)CPB * 2 * psize<N>());
         set_smem(k_box_op<T, Tin, N>, sm);

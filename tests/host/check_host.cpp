@@ -175,6 +175,8 @@ static int basis(int argc, char **argv) {
   put("T", b.T);
   put("Af", b.Af);
   put("Bf", b.Bf);
+  put("Ve", b.Ve);
+  put("lame", b.lame);
   return 0;
 }
 

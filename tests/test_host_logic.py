@@ -9,6 +9,7 @@ import os
 import shutil
 import subprocess
 
+import numpy as np
 import pytest
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -107,6 +108,66 @@ def test_sipg_star_is_kronecker_sum_of_pencils(checker):
         D = (Z["lam"][:, None, None] + Y["lam"][None, :, None] + X["lam"][None, None, :]).ravel()
         inv = Sk @ np.diag(1.0 / D) @ Sk.T
         assert np.abs(inv @ Av - np.eye(len(D))).max() <= 1e-10
+
+
+def _modes_apply(V, lam, mu, U):
+    """The pass order of the element-mode box stiffness, in numpy: forward along
+    z and y, along x forward, D, backward, then backward along y and z.  U is
+    indexed [z, y, x]; V holds the modes by rows (even modes first), of which
+    the passes use only the first half of each row, as the kernel does."""
+    n = len(lam)
+    H, NE = n // 2, (n + 1) // 2
+
+    def fwd(x):
+        sp = np.array([x[j] + x[n - 1 - j] for j in range(H)] + ([x[H]] if n % 2 else []))
+        dm = np.array([x[j] - x[n - 1 - j] for j in range(H)])
+        return np.array([V[k, :NE] @ sp for k in range(NE)] + [V[k, :H] @ dm for k in range(NE, n)])
+
+    def bwd(w):
+        x = np.zeros(n)
+        for i in range(H):
+            e, o = V[:NE, i] @ w[:NE], V[NE:, i] @ w[NE:]
+            x[i], x[n - 1 - i] = e + o, e - o
+        if n % 2:
+            x[H] = V[:NE, H] @ w[:NE]
+        return x
+
+    W = U.copy()
+    W = np.apply_along_axis(fwd, 0, W)  # z
+    W = np.apply_along_axis(fwd, 1, W)  # y
+    W = np.apply_along_axis(fwd, 2, W)  # x
+    W = W * (mu[0] * lam[None, None, :] + mu[1] * lam[None, :, None] + mu[2] * lam[:, None, None])
+    W = np.apply_along_axis(bwd, 2, W)
+    W = np.apply_along_axis(bwd, 1, W)
+    return np.apply_along_axis(bwd, 0, W)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 7, 10, 15])
+def test_library_element_modes(checker, p):
+    """The element modes of the FP64 box stiffness (V = S^T B by rows, even
+    modes first, with S^T B S = I and A S = B S diag(lam)): V^T diag(lam) V
+    reproduces A_hat and V^T V reproduces B_hat, every row is exactly even or
+    odd about the element centre, and the kernel's pass order (forward along
+    z, y, x, the diagonal mu1 lam_i + mu2 lam_j + mu3 lam_k, backward along x,
+    y, z, half rows only) gives the Kronecker form of the box-cell stiffness."""
+    r = subprocess.run([checker, "basis", str(p)], capture_output=True, text=True, check=True)
+    lib = {}
+    for line in r.stdout.splitlines():
+        k, *v = line.split()
+        lib[k] = np.array([float(x) for x in v])
+    n = p + 1
+    A, B, V, lam = lib["A"].reshape(n, n), lib["B"].reshape(n, n), lib["Ve"].reshape(n, n), lib["lame"]
+    NE = (n + 1) // 2
+    assert np.abs(V.T @ np.diag(lam) @ V - A).max() <= 1e-13 * np.abs(A).max()
+    assert np.abs(V.T @ V - B).max() <= 1e-14 * np.abs(B).max()
+    assert np.array_equal(V[:NE], V[:NE, ::-1]) and np.array_equal(V[NE:], -V[NE:, ::-1])
+    assert np.all(np.diff(lam[:NE]) > 0) and np.all(np.diff(lam[NE:]) > 0) and abs(lam[0]) <= 1e-12 * lam.max()
+    rng = np.random.default_rng(p)
+    U = rng.standard_normal((n, n, n))
+    mu = rng.uniform(0.2, 3.0, 3)
+    K = (mu[0] * np.kron(B, np.kron(B, A)) + mu[1] * np.kron(B, np.kron(A, B)) + mu[2] * np.kron(A, np.kron(B, B)))
+    y = (K @ U.ravel()).reshape(n, n, n)
+    assert np.abs(_modes_apply(V, lam, mu, U) - y).max() <= 1e-13 * np.abs(y).max()
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4, 7, 10, 15])
