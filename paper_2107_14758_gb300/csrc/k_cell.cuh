@@ -10,8 +10,9 @@
 // broadcast).  Several cells share a CTA when n is small.
 //
 //   box stiffness (eq. (kron), Section 2.2): y_K = mu1 (B (x) B (x) A) u_K
-//     + mu2 (B (x) A (x) B) u_K + mu3 (A (x) B (x) B) u_K in 7 line passes;
-//     cell-local results, summed over cells by a node gather.
+//     + mu2 (B (x) A (x) B) u_K + mu3 (A (x) B (x) B) u_K in 7 line passes
+//     (FP32), or in the element eigenbasis of (A, B) in 6 passes and a
+//     diagonal (FP64); cell-local results, summed over cells by a node gather.
 //   restrict (Section 2.4): E_K = (T^T)^{(x)3} (W_K r_K), then the cell's share
 //     of the Schur condensation on its face nodes.
 //   interp (Sections 2.4-2.6): interface values summed over the 8 stars,
