@@ -140,6 +140,21 @@ def test_stiffness_and_mass_box():
     assert relerr(N(ctx.mass_apply(T(u))), ref.mass_apply(u)) <= 1e-12
 
 
+@pytest.mark.parametrize("p", list(range(1, 16)))
+def test_stiffness_box_every_degree(p):
+    """The FP64 box stiffness (the element-eigenbasis kernel, specialised on
+    n = p + 1: odd n takes its middle-node terms, even n not) against the
+    oracle's Kronecker apply at every degree, on a 3 x 2 x 2 graded mesh (12
+    cells: a partly filled last CTA where several cells share one)."""
+    xv = np.array([0.0, 0.3, 0.55, 1.0])
+    yv = np.array([0.0, 0.6, 1.0])
+    zv = np.array([0.0, 0.45, 1.0])
+    ctx, ref, _ = pair(p, xv, yv, zv, patches=False, coarse=False, omega=1.0)
+    for seed in (3, 4):  # two calls in a row
+        u = np.random.default_rng(seed).standard_normal(ref.ndof)
+        assert relerr(N(ctx.stiffness_apply(T(u))), ref.stiffness_apply(u)) <= 1e-12
+
+
 @pytest.mark.parametrize("p", [2, 4])
 def test_stiffness_curved(p):
     n = 3
