@@ -1,5 +1,7 @@
 // Cell operators specialised on n: box-cell stiffness (even-odd form), curved-cell
 // stiffness (Gauss quadrature) and the node gather; helpers in k_cell.cuh.
+#include <algorithm>
+
 #include "k_cell.cuh"
 
 namespace fdm {
@@ -468,6 +470,86 @@ __global__ void __launch_bounds__(128) k_gather_t(Grid g, const T *__restrict__ 
 }  // namespace
 
 
+// The same direct stiffness summation by cell rows: a thread takes the n - 1
+// nodes of one cell along one x node row (the last cell also the row's end
+// node), works out the row's y and z cells once, loads each cell row's n
+// values together, and sums exactly as k_gather_t does (the (z, y) cell pairs
+// in the same nested order, along x the left cell before its own), so the
+// results are identical; the rows of a block go through shared memory and are
+// written back in node order.
+template <typename T, typename Tout, int N>
+__global__ void __launch_bounds__(256) k_gather_rows(Grid g, const T *__restrict__ E, const double *__restrict__ rsub,
+                                                     Tout *__restrict__ y, int rows_per_block) {
+  extern __shared__ __align__(16) unsigned char smem_[];
+  constexpr int P = N - 1, N3 = N * N * N;
+  T *rowbuf = reinterpret_cast<T *>(smem_);  // rows_per_block x N0
+  const int N0 = g.N[0], nrow = g.N[1] * g.N[2], nx = g.nx;
+  const int r0 = blockIdx.x * rows_per_block;
+  const int nr = min(rows_per_block, nrow - r0);
+  for (int t = threadIdx.x; t < nr * nx; t += blockDim.x) {
+    const int rl = t / nx, cx = t - rl * nx, row = r0 + rl;
+    const int gy = row % g.N[1], gz = row / g.N[1];
+    int cy[2], ly[2], cz[2], lz[2], ny_ = 0, nz_ = 0;
+    {
+      const int q = gy / P, rm = gy - q * P;
+      if (rm == 0) {
+        if (q > 0) { cy[ny_] = q - 1; ly[ny_++] = P; }
+        if (q < g.ny) { cy[ny_] = q; ly[ny_++] = 0; }
+      } else { cy[0] = q; ly[0] = rm; ny_ = 1; }
+    }
+    {
+      const int q = gz / P, rm = gz - q * P;
+      if (rm == 0) {
+        if (q > 0) { cz[nz_] = q - 1; lz[nz_++] = P; }
+        if (q < g.nz) { cz[nz_] = q; lz[nz_++] = 0; }
+      } else { cz[0] = q; lz[0] = rm; nz_ = 1; }
+    }
+    T s[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) s[i] = 0;
+    for (int a2 = 0; a2 < nz_; ++a2)
+      for (int a1 = 0; a1 < ny_; ++a1) {
+        const int64_t cyz = (int64_t)g.nx * (cy[a1] + g.ny * cz[a2]);
+        const int lyz = N * (ly[a1] + N * lz[a2]);
+        const T *own = E + (cyz + cx) * N3 + lyz;
+        T v[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = own[i];
+        if (cx > 0) s[0] += E[(cyz + cx - 1) * N3 + lyz + P];
+#pragma unroll
+        for (int i = 0; i < N; ++i) s[i] += v[i];
+      }
+    T *rb = rowbuf + (size_t)rl * N0 + cx * P;
+#pragma unroll
+    for (int i = 0; i < P; ++i) rb[i] = s[i];
+    if (cx == nx - 1) rb[P] = s[P];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nr * N0; t += blockDim.x) {
+    const int rl = t / N0, gx = t - rl * N0, row = r0 + rl;
+    const int gy = row % g.N[1], gz = row / g.N[1];
+    const int64_t id = gx + (int64_t)N0 * row;
+    const T sv = rowbuf[t];
+    y[id] = node_dirichlet(g, gx, gy, gz) ? Tout(0) : (rsub ? Tout(T(rsub[id]) - sv) : Tout(sv));
+  }
+}
+
+// rows per block of the row gather (0: the node gather instead)
+inline int gather_rows_per_block(const Grid &g, size_t elem) {
+  const int rpb = std::max(1, std::min(64, 256 / std::max(g.nx, 1)));
+  return (size_t)rpb * g.N[0] * elem <= 48 * 1024 ? rpb : 0;
+}
+template <typename T, typename Tout, int N>
+void launch_gather_node_sums(const Grid &g, const T *E, const double *rsub, Tout *y, cudaStream_t st) {
+  const int rpb = gather_rows_per_block(g, sizeof(T));
+  if (rpb > 0) {
+    const int nrow = g.N[1] * g.N[2];
+    k_gather_rows<T, Tout, N><<<(nrow + rpb - 1) / rpb, 256, (size_t)rpb * g.N[0] * sizeof(T), st>>>(g, E, rsub, y, rpb);
+  } else {
+    k_gather_t<T, Tout, N><<<dim3((g.N[0] + 127) / 128, g.N[1], g.N[2]), 128, 0, st>>>(g, E, rsub, y);
+  }
+}
+
 template <typename T, typename Tin, typename Tout>
 bool launch_box_op_fast(const OpArgs &a, const Tin *u, Tout *y, T *E, cudaStream_t st, const double *rsub) {
   if constexpr (!std::is_same<T, Tin>::value) {
@@ -491,7 +573,7 @@ bool launch_box_op_fast(const OpArgs &a, const Tin *u, Tout *y, T *E, cudaStream
         set_smem(k_box_op<T, Tin, N>, sm);
         k_box_op<T, Tin, N><<<(a.g.ncell + CPB - 1) / CPB, CPB * N * N, sm, st>>>(a.g, a.mu_box, tab, u, E);
       }
-      k_gather_t<T, Tout, N><<<dim3((a.g.N[0] + 127) / 128, a.g.N[1], a.g.N[2]), 128, 0, st>>>(a.g, E, rsub, y);
+      launch_gather_node_sums<T, Tout, N>(a.g, E, rsub, y, st);
     });
   }
 }
@@ -500,7 +582,7 @@ template <typename T, typename Tout>
 void launch_gather_cells(const Grid &g, const T *E, const double *rsub, Tout *y, cudaStream_t st) {
   if (!dispatch_n(g.n, [&](auto NC) {
         constexpr int N = decltype(NC)::value;
-        k_gather_t<T, Tout, N><<<dim3((g.N[0] + 127) / 128, g.N[1], g.N[2]), 128, 0, st>>>(g, E, rsub, y);
+        launch_gather_node_sums<T, Tout, N>(g, E, rsub, y, st);
       }))
     fail(FDM_EINVAL, "node gather: unsupported degree");
 }
